@@ -1,0 +1,251 @@
+"""Python front end of the FP64 CPU oracle (regc_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+baseline of the benchmark.  The CUDA library never imports or links this.
+
+``build()`` compiles regc_oracle.c with gcc into ``oracle/_build/liboracle.so``
+(plain -O2, no fused multiply-add contraction, OpenMP over walkers).  The
+``Oracle`` class wraps one problem statement and a set of walkers held in
+numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "liboracle.so")
+SRC = os.path.join(HERE, "regc_oracle.c")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (a no-op when it is up to date)."""
+    os.makedirs(BUILD, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)
+            and os.path.getmtime(LIB) >= os.path.getmtime(os.path.join(HERE, "regc_oracle.h"))):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _System(C.Structure):
+    _fields_ = [
+        ("n_types", C.c_int),
+        ("eps", (C.c_double * 4) * 4),
+        ("sigma", (C.c_double * 4) * 4),
+        ("rc", C.c_double),
+        ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+        ("periodic_z", C.c_int),
+        ("z_lo", C.c_double), ("z_hi", C.c_double),
+        ("n_surf", C.c_int),
+        ("surf_xyz", C.POINTER(C.c_double)),
+        ("surf_type", C.POINTER(C.c_int)),
+        ("L", C.c_int), ("M", C.c_int),
+        ("kT", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
+        ("lambda0", C.c_double),
+        ("nmax", C.c_int), ("moves_per_sweep", C.c_int),
+        ("max_disp", C.c_double), ("p_disp", C.c_double),
+        ("seed", C.c_uint64),
+        ("e_lo", C.c_double), ("e_bin", C.c_double),
+        ("n_e_bins", C.c_int),
+        ("mutation", C.c_int),
+    ]
+
+
+class _Hist(C.Structure):
+    _fields_ = [
+        ("hN", C.POINTER(C.c_int64)),
+        ("hNE", C.POINTER(C.c_int64)),
+        ("omega", C.POINTER(C.c_int64)),
+        ("moments", C.POINTER(C.c_double)),
+        ("e_out", C.POINTER(C.c_int64)),
+    ]
+
+
+MOVE_DTYPE = np.dtype([
+    ("type", np.int32), ("index", np.int32), ("accepted", np.int32), ("status", np.int32),
+    ("dE", np.float64), ("log_alpha", np.float64), ("ln_u", np.float64),
+    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("pad", np.int32),
+])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp, ip, i64p = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+        sp = C.POINTER(_System)
+        _lib.oracle_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+        _lib.oracle_phi.argtypes = [sp, C.c_int, C.c_int, C.c_double]
+        _lib.oracle_phi.restype = C.c_double
+        _lib.oracle_particle_energy.argtypes = [sp, dp, C.c_int, C.c_double, C.c_double,
+                                                C.c_double, C.c_int, dp, dp, ip]
+        _lib.oracle_particle_energy.restype = C.c_double
+        _lib.oracle_total_energy.argtypes = [sp, dp, C.c_int]
+        _lib.oracle_total_energy.restype = C.c_double
+        _lib.oracle_log_alpha.argtypes = [sp, C.c_int, C.c_int, C.c_int, C.c_double]
+        _lib.oracle_log_alpha.restype = C.c_double
+        _lib.oracle_exchange_log_alpha.argtypes = [sp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                   C.c_double, C.c_double]
+        _lib.oracle_exchange_log_alpha.restype = C.c_double
+        _lib.oracle_sweeps.argtypes = [sp, C.c_int, dp, ip, dp, ip, C.c_uint32, C.c_int,
+                                       C.POINTER(_Hist), C.c_void_p, i64p, C.c_int]
+        _lib.oracle_sweeps.restype = C.c_int
+        _lib.oracle_exchange.argtypes = [sp, C.c_uint32, ip, dp, ip, ip, i64p]
+        _lib.oracle_exchange.restype = C.c_int
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: ctr is 4 uint32 words, key is 2."""
+    c = np.asarray(ctr, np.uint32).copy()
+    k = np.asarray(key, np.uint32).copy()
+    out = np.zeros(4, np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+class Oracle:
+    """FP64 REGC sampler over the walkers of one problem statement.
+
+    State (numpy, owned here): pos [S, nmax, 3], n [S], energy [S],
+    state_of_walker [S], walker_of_state [S], sweep counter t, exchange
+    counter e, histograms and acceptance counters."""
+
+    def __init__(self, problem, pos=None, n=None, mutation: int = 0, n_threads: int = 0):
+        self.p = problem
+        S, nmax = problem.S, problem.nmax
+        self._kT = np.ascontiguousarray(problem.kT, np.float64)
+        self._mu = np.ascontiguousarray(problem.mu, np.float64)
+        self._sxyz = np.ascontiguousarray(problem.surf_xyz, np.float64).reshape(-1)
+        self._stype = np.ascontiguousarray(problem.surf_type, np.int32)
+        if len(self._stype) == 0:
+            self._sxyz = np.zeros(3)
+            self._stype = np.zeros(1, np.int32)
+        s = _System()
+        s.n_types = problem.n_types
+        for i in range(4):
+            for j in range(4):
+                s.eps[i][j] = float(problem.eps[i, j])
+                s.sigma[i][j] = float(problem.sigma[i, j])
+        s.rc = problem.rc
+        s.Lx, s.Ly, s.Lz = problem.Lx, problem.Ly, problem.Lz
+        s.periodic_z = int(problem.periodic_z)
+        s.z_lo, s.z_hi = problem.z_lo, problem.z_hi
+        s.n_surf = problem.n_surf
+        s.surf_xyz = _ptr(self._sxyz, C.c_double)
+        s.surf_type = _ptr(self._stype, C.c_int32)
+        s.L, s.M = problem.L, problem.M
+        s.kT = _ptr(self._kT, C.c_double)
+        s.mu = _ptr(self._mu, C.c_double)
+        s.lambda0 = problem.lambda0
+        s.nmax, s.moves_per_sweep = problem.nmax, problem.moves_per_sweep
+        s.max_disp, s.p_disp = problem.max_disp, problem.p_disp
+        s.seed = int(problem.seed)
+        s.e_lo, s.e_bin, s.n_e_bins = problem.e_lo, problem.e_bin, problem.n_e_bins
+        s.mutation = int(mutation)
+        self.sys = s
+        self.n_threads = int(n_threads)
+        self.pos = np.zeros((S, nmax, 3)) if pos is None else np.array(pos, np.float64).reshape(S, nmax, 3)
+        self.n = np.zeros(S, np.int32) if n is None else np.array(n, np.int32)
+        self.energy = np.array([self.total_energy(w) for w in range(S)])
+        self.state_of_walker = np.arange(S, dtype=np.int32)
+        self.walker_of_state = np.arange(S, dtype=np.int32)
+        self.t = 0
+        self.e = 0
+        self.reset_histograms()
+        self.counts = np.zeros((S, 3, 2), np.int64)
+        self.ex_counts = np.zeros((S, 4, 2), np.int64)
+
+    def reset_histograms(self):
+        p = self.p
+        self.hN = np.zeros((p.S, p.nmax + 1), np.int64)
+        self.hNE = np.zeros((p.nmax + 1, p.n_e_bins), np.int64)
+        self.omega = np.zeros(p.S, np.int64)
+        self.moments = np.zeros((p.S, 4))
+        self.e_out = np.zeros(p.S, np.int64)
+
+    # -- single-function access for the pins
+    def phi(self, ti, tj, r2):
+        return lib().oracle_phi(C.byref(self.sys), ti, tj, r2)
+
+    def total_energy(self, w):
+        pos = np.ascontiguousarray(self.pos[w])
+        return lib().oracle_total_energy(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]))
+
+    def particle_energy(self, w, xyz, skip=-1):
+        pos = np.ascontiguousarray(self.pos[w])
+        sa, band = C.c_double(0), C.c_double(0)
+        npairs = C.c_int32(0)
+        e = lib().oracle_particle_energy(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]),
+                                         float(xyz[0]), float(xyz[1]), float(xyz[2]), int(skip),
+                                         C.byref(sa), C.byref(band), C.byref(npairs))
+        return e, sa.value, band.value, npairs.value
+
+    def log_alpha(self, move_type, state, n, dE):
+        return lib().oracle_log_alpha(C.byref(self.sys), move_type, state, n, dE)
+
+    def exchange_log_alpha(self, sa, sb, na, nb, ea, eb):
+        return lib().oracle_exchange_log_alpha(C.byref(self.sys), sa, sb, na, nb, ea, eb)
+
+    # -- the sampler
+    def sweeps(self, n_sweeps: int, hist: bool = True, trace: bool = False):
+        p = self.p
+        S = p.S
+        tr = np.zeros((S, n_sweeps, p.moves_per_sweep), MOVE_DTYPE) if trace else None
+        h = None
+        if hist:
+            h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
+                      _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
+                      _ptr(self.e_out, C.c_int64))
+        rc = lib().oracle_sweeps(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
+                                 _ptr(self.n, C.c_int32), _ptr(self.energy, C.c_double),
+                                 _ptr(self.state_of_walker, C.c_int32), C.c_uint32(self.t),
+                                 n_sweeps, C.byref(h) if h is not None else None,
+                                 tr.ctypes.data if tr is not None else None,
+                                 _ptr(self.counts, C.c_int64), self.n_threads)
+        if rc != 0:
+            raise ValueError("oracle_sweeps rejected its arguments")
+        self.t += n_sweeps
+        return tr
+
+    def exchange(self):
+        acc = lib().oracle_exchange(C.byref(self.sys), C.c_uint32(self.e), _ptr(self.n, C.c_int32),
+                                    _ptr(self.energy, C.c_double),
+                                    _ptr(self.state_of_walker, C.c_int32),
+                                    _ptr(self.walker_of_state, C.c_int32),
+                                    _ptr(self.ex_counts, C.c_int64))
+        if acc < 0:
+            raise ValueError("oracle_exchange rejected its arguments")
+        self.e += 1
+        return acc
+
+    def run(self, n_sweeps: int, exchange_every: int = 10, hist: bool = True):
+        """Alternate blocks of exchange_every sweeps with an exchange attempt."""
+        done = 0
+        while done < n_sweeps:
+            k = min(exchange_every, n_sweeps - done) if exchange_every > 0 else n_sweeps - done
+            self.sweeps(k, hist=hist)
+            done += k
+            if exchange_every > 0 and k == exchange_every:
+                self.exchange()
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,451 @@
+/*
+ * regc_oracle.c -- FP64 CPU oracle of the REGCMC sampler (arXiv:1908.11118).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark, never by the library.  It is written
+ * for a reader who checks it against the paper line by line:
+ *   - every energy is a plain double sum over all partners (no cell lists,
+ *     no tiling, no reordering);
+ *   - every acceptance rule is the paper's equation in log form;
+ *   - walkers are independent between exchanges, so the only parallelism is
+ *     an OpenMP loop over walkers.
+ *
+ * Random numbers: one counter-based generator, Philox4x32-10 (Salmon, Moraes,
+ * Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), written
+ * here from its published definition.  Block keyed by (seed), counter
+ * (move k, sweep t, walker w, stream):
+ *   stream 0 (block A): A0 move kind, A1..A3 displacement / insertion uniforms
+ *   stream 1 (block B): B0 particle index, B1 acceptance uniform,
+ *                       B2 top bit = grand-canonical direction, B3 spare
+ *   stream 2: exchange type and parity, counter (e, 0, 0, 2)
+ *   stream 3: exchange uniform of the pair whose lower state index is a,
+ *             counter (e, a, 0, 3)
+ *
+ * Planted-mistake switches (oracle_system.mutation, zero in real use) exist so
+ * that the tests can show each pin detects the mistake it is meant to catch:
+ *   1   exchange: sign of the chemical-potential term flipped
+ *   2   exchange: (beta_a/beta_b)^{3/2 dN} factor dropped
+ *   4   insertion/removal: Lambda^1 instead of Lambda^3
+ *   8   insertion: the 1/(N+1) factor dropped
+ *   16  pair potential: the factor 4 dropped
+ *   32  minimum image not applied along y
+ *   64  removal: energy taken of particle i but particle (i+1) mod N removed
+ */
+#include "regc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- Philox */
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    /* Philox4x32 round (Salmon et al. 2011): two 32x32->64 multiplications
+     * by the constants 0xD2511F53 and 0xCD9E8D57 act on words 0 and 2; the
+     * high halves are mixed with words 1, 3 and the round key; the key is
+     * advanced by the Weyl increments 0x9E3779B9, 0xBB67AE85 between rounds. */
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void draw(const oracle_system *sys, uint32_t c0, uint32_t c1, uint32_t c2,
+                 uint32_t c3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)sys->seed, (uint32_t)(sys->seed >> 32)};
+    oracle_philox4x32_10(ctr, key, out);
+}
+
+/* 24-bit uniform in [0, 1), exact in binary32 */
+static double u24(uint32_t a) { return (double)(a >> 8) * (1.0 / 16777216.0); }
+/* uniform in (0, 1) for acceptance tests */
+static double u32_open(uint32_t a) { return ((double)a + 0.5) * (1.0 / 4294967296.0); }
+/* round through binary32 */
+static double f32(double v) { return (double)(float)v; }
+
+/* ------------------------------------------------------------- potential */
+
+double oracle_phi(const oracle_system *sys, int ti, int tj, double r2)
+{
+    /* Lennard-Jones 12-6 (Appendix, force field), truncated: zero at r >= rc */
+    if (r2 >= sys->rc * sys->rc) return 0.0;
+    double sig = sys->sigma[ti][tj];
+    double s2 = sig * sig / r2;
+    double s6 = s2 * s2 * s2;
+    double pref = (sys->mutation & 16) ? 1.0 : 4.0;
+    return pref * sys->eps[ti][tj] * (s6 * s6 - s6);
+}
+
+static double min_image(double d, double box)
+{
+    return d - box * nearbyint(d / box);
+}
+
+static double pair_r2(const oracle_system *sys, double xa, double ya, double za,
+                      double xb, double yb, double zb)
+{
+    double dx = min_image(xa - xb, sys->Lx);
+    double dy = (sys->mutation & 32) ? (ya - yb) : min_image(ya - yb, sys->Ly);
+    double dz = sys->periodic_z ? min_image(za - zb, sys->Lz) : (za - zb);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+static void account(const oracle_system *sys, int ti, int tj, double r2, double phi,
+                    double *sum_abs, double *band, int *n_pairs)
+{
+    double rc2 = sys->rc * sys->rc;
+    if (sum_abs) *sum_abs += fabs(phi);
+    if (n_pairs && r2 < rc2) *n_pairs += 1;
+    if (band && fabs(r2 - rc2) < 4e-6 * rc2) {
+        double sr = sys->sigma[ti][tj] / sys->rc;
+        double s6 = pow(sr, 6.0);
+        *band += fabs(4.0 * sys->eps[ti][tj] * (s6 * s6 - s6));
+    }
+}
+
+/* Interaction energy of a mobile particle at (x, y, z) with every surface atom
+ * and every mobile particle j != skip (the moved particle's energy entering
+ * E(R; N) in Eq. Ngrand). */
+double oracle_particle_energy(const oracle_system *sys, const double *pos, int n,
+                              double x, double y, double z, int skip,
+                              double *sum_abs, double *band, int *n_pairs)
+{
+    double e = 0.0;
+    for (int a = 0; a < sys->n_surf; ++a) {
+        const double *ra = sys->surf_xyz + 3 * a;
+        int ta = sys->surf_type[a];
+        double r2 = pair_r2(sys, x, y, z, ra[0], ra[1], ra[2]);
+        double phi = oracle_phi(sys, 0, ta, r2);
+        account(sys, 0, ta, r2, phi, sum_abs, band, n_pairs);
+        e += phi;
+    }
+    for (int j = 0; j < n; ++j) {
+        if (j == skip) continue;
+        const double *rj = pos + 3 * j;
+        double r2 = pair_r2(sys, x, y, z, rj[0], rj[1], rj[2]);
+        double phi = oracle_phi(sys, 0, 0, r2);
+        account(sys, 0, 0, r2, phi, sum_abs, band, n_pairs);
+        e += phi;
+    }
+    return e;
+}
+
+/* E(R; N): all mobile-mobile pairs i < j plus all mobile-surface pairs.  The
+ * slab is frozen, so surface-surface pairs are constant and left out. */
+double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
+{
+    double e = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *ri = pos + 3 * i;
+        for (int a = 0; a < sys->n_surf; ++a) {
+            const double *ra = sys->surf_xyz + 3 * a;
+            e += oracle_phi(sys, 0, sys->surf_type[a],
+                            pair_r2(sys, ri[0], ri[1], ri[2], ra[0], ra[1], ra[2]));
+        }
+        for (int j = i + 1; j < n; ++j) {
+            const double *rj = pos + 3 * j;
+            e += oracle_phi(sys, 0, 0, pair_r2(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2]));
+        }
+    }
+    return e;
+}
+
+/* ---------------------------------------------------------- acceptance */
+
+static double kT_of(const oracle_system *sys, int state) { return sys->kT[state / sys->M]; }
+static double mu_of(const oracle_system *sys, int state) { return sys->mu[state % sys->M]; }
+
+static double ln_lambda(const oracle_system *sys, double kT)
+{
+    /* Lambda = h / sqrt(2 pi m kT) (Eq. Ngrand); in reduced units lambda0/sqrt(kT) */
+    return log(sys->lambda0) - 0.5 * log(kT);
+}
+
+static double volume(const oracle_system *sys)
+{
+    return sys->Lx * sys->Ly * (sys->z_hi - sys->z_lo);
+}
+
+/* log of the Metropolis acceptance ratio of a move that changes the energy by
+ * dE, for a walker with n mobile particles before the move:
+ *   type 0, displacement (Sec. II.A.3):   -beta dE
+ *   type 1, insertion   (Sec. II.A.1):   ln[V / (Lambda^3 (n+1))] + beta (mu - dE)
+ *   type 2, removal     (Sec. II.A.1):   ln[Lambda^3 n / V] - beta (mu + dE)
+ * (the insertion exponent is read as beta[mu - (E_{N+1} - E_N)]). */
+double oracle_log_alpha(const oracle_system *sys, int type, int state, int n, double dE)
+{
+    double kT = kT_of(sys, state), beta = 1.0 / kT, mu = mu_of(sys, state);
+    double lam_pow = (sys->mutation & 4) ? 1.0 : 3.0;
+    double lnL = ln_lambda(sys, kT);
+    double lnV = log(volume(sys));
+    if (type == 0) return -beta * dE;
+    if (type == 1) {
+        double ln_n1 = (sys->mutation & 8) ? 0.0 : log((double)(n + 1));
+        return lnV - lam_pow * lnL - ln_n1 + beta * (mu - dE);
+    }
+    return lam_pow * lnL + log((double)n) - lnV - beta * (mu + dE);
+}
+
+/* log acceptance of swapping the configurations of states a and b (Eq. Pacc),
+ * where state a holds (na, ea) and state b holds (nb, eb):
+ *   1.5 (na - nb) ln(beta_a / beta_b) - (beta_a - beta_b)(eb - ea)
+ *     - (beta_a mu_a - beta_b mu_b)(na - nb)
+ * (the leading minus of the printed exponent is read as covering both terms). */
+double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
+                                 int na, int nb, double ea, double eb)
+{
+    double ba = 1.0 / kT_of(sys, sa), bb = 1.0 / kT_of(sys, sb);
+    double ma = mu_of(sys, sa), mb = mu_of(sys, sb);
+    double dn = (double)(na - nb);
+    double lam = (sys->mutation & 2) ? 0.0 : 1.5 * dn * log(ba / bb);
+    double mu_term = (ba * ma - bb * mb) * dn;
+    if (sys->mutation & 1) mu_term = -mu_term;
+    return lam - (ba - bb) * (eb - ea) - mu_term;
+}
+
+/* ---------------------------------------------------------------- sweeps */
+
+static void observe(const oracle_system *sys, oracle_hist *h, int state, int n, double e)
+{
+    if (!h) return;
+    int nb = sys->nmax + 1;
+    if (h->hN) h->hN[(int64_t)state * nb + n] += 1;
+    if (h->omega) h->omega[state] += 1;
+    if (h->moments) {
+        double *m = h->moments + 4 * (int64_t)state;
+        m[0] += n;
+        m[1] += (double)n * n;
+        m[2] += e;
+        m[3] += e * e;
+    }
+    if (h->hNE) {
+        double k = floor((e - sys->e_lo) / sys->e_bin);
+        if (k >= 0.0 && k < (double)sys->n_e_bins) {
+            int64_t idx = (int64_t)n * sys->n_e_bins + (int64_t)k;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            h->hNE[idx] += 1;
+        } else if (h->e_out) {
+            h->e_out[state] += 1;
+        }
+    }
+}
+
+static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr,
+                         double *e_ptr, int state, uint32_t t0, int n_sweeps,
+                         oracle_hist *hist, oracle_move *trace, int64_t *counts)
+{
+    const double lx = sys->Lx, ly = sys->Ly, lz = sys->Lz;
+    const double delta = f32(sys->max_disp);
+    const double height = f32(sys->z_hi - sys->z_lo);
+    double p = sys->p_disp < 0.0 ? 0.0 : (sys->p_disp > 1.0 ? 1.0 : sys->p_disp);
+    const uint64_t th_disp = (uint64_t)floor(p * 4294967296.0);
+    const double beta = 1.0 / kT_of(sys, state);
+    int n = *n_ptr;
+    double e = *e_ptr;
+
+    for (int ts = 0; ts < n_sweeps; ++ts) {
+        uint32_t t = t0 + (uint32_t)ts;
+        for (int k = 0; k < sys->moves_per_sweep; ++k) {
+            uint32_t A[4], B[4];
+            draw(sys, (uint32_t)k, t, (uint32_t)w, 0u, A);
+            draw(sys, (uint32_t)k, t, (uint32_t)w, 1u, B);
+            oracle_move mv;
+            memset(&mv, 0, sizeof mv);
+            mv.ln_u = log(u32_open(B[1]));
+            if ((uint64_t)A[0] < th_disp) {
+                mv.type = 0;
+            } else {
+                /* removal if y1 < 0.5, else insertion (Sec. II.A.1) */
+                mv.type = (B[2] >> 31) == 0u ? 2 : 1;
+            }
+            double nx = 0, ny = 0, nz = 0;  /* new position (displace/insert) */
+            int i = -1;
+            if (mv.type == 0) {
+                /* Metropolis displacement (Sec. II.A.3): random atom, uniform
+                 * displacement in a cube of half-edge max_disp */
+                if (n == 0) { mv.status = 1; goto decided; }
+                i = (int)(((uint64_t)B[0] * (uint64_t)n) >> 32);
+                mv.index = i;
+                double d[3];
+                for (int c = 0; c < 3; ++c) d[c] = f32(delta * f32(2.0 * u24(A[1 + c]) - 1.0));
+                const double *ri = pos + 3 * i;
+                nx = f32(ri[0] + d[0]);
+                ny = f32(ri[1] + d[1]);
+                nz = f32(ri[2] + d[2]);
+                if (nx < 0.0) nx = f32(nx + lx);
+                if (nx >= lx) nx = f32(nx - lx);
+                if (ny < 0.0) ny = f32(ny + ly);
+                if (ny >= ly) ny = f32(ny - ly);
+                if (sys->periodic_z) {
+                    if (nz < 0.0) nz = f32(nz + lz);
+                    if (nz >= lz) nz = f32(nz - lz);
+                } else if (nz < sys->z_lo || nz > sys->z_hi) {
+                    mv.status = 2;
+                    goto decided;
+                }
+                double e_new = oracle_particle_energy(sys, pos, n, nx, ny, nz, i,
+                                                      &mv.sum_abs, &mv.band, &mv.n_pairs);
+                double e_old = oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
+                                                      &mv.sum_abs, &mv.band, &mv.n_pairs);
+                mv.dE = e_new - e_old;
+                mv.log_alpha = -beta * mv.dE;
+            } else if (mv.type == 1) {
+                /* insertion at a uniform point of the region (Sec. II.A.1) */
+                if (n == sys->nmax) { mv.status = 1; goto decided; }
+                mv.index = n;
+                nx = f32(lx * u24(A[1]));
+                ny = f32(ly * u24(A[2]));
+                nz = f32(sys->z_lo + f32(height * u24(A[3])));
+                if (nx >= lx) nx = f32(nx - lx);
+                if (ny >= ly) ny = f32(ny - ly);
+                if (sys->periodic_z && nz >= lz) nz = f32(nz - lz);
+                mv.dE = oracle_particle_energy(sys, pos, n, nx, ny, nz, -1,
+                                               &mv.sum_abs, &mv.band, &mv.n_pairs);
+                mv.log_alpha = oracle_log_alpha(sys, 1, state, n, mv.dE);
+            } else {
+                /* removal of particle i, (i-1)/N <= y2 < i/N (Sec. II.A.1) */
+                if (n == 0) { mv.status = 1; goto decided; }
+                i = (int)(((uint64_t)B[0] * (uint64_t)n) >> 32);
+                mv.index = i;
+                const double *ri = pos + 3 * i;
+                mv.dE = -oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
+                                                &mv.sum_abs, &mv.band, &mv.n_pairs);
+                mv.log_alpha = oracle_log_alpha(sys, 2, state, n, mv.dE);
+            }
+            mv.accepted = mv.ln_u < mv.log_alpha;
+            if (mv.accepted) {
+                if (mv.type == 0) {
+                    double *ri = pos + 3 * i;
+                    ri[0] = nx; ri[1] = ny; ri[2] = nz;
+                } else if (mv.type == 1) {
+                    double *rn = pos + 3 * n;
+                    rn[0] = nx; rn[1] = ny; rn[2] = nz;
+                    n += 1;
+                } else {
+                    int gone = (sys->mutation & 64) ? (i + 1) % n : i;
+                    memcpy(pos + 3 * gone, pos + 3 * (n - 1), 3 * sizeof(double));
+                    n -= 1;
+                }
+                e += mv.dE;
+            }
+        decided:
+            if (counts) {
+                counts[6 * (int64_t)w + 2 * mv.type] += 1;
+                counts[6 * (int64_t)w + 2 * mv.type + 1] += mv.accepted;
+            }
+            if (trace) trace[((int64_t)ts * sys->moves_per_sweep + k)] = mv;
+        }
+        observe(sys, hist, state, n, e);
+    }
+    *n_ptr = n;
+    *e_ptr = e;
+}
+
+/* Run n_sweeps sweeps of moves_per_sweep trial moves on every walker, the
+ * walkers' states held fixed (they change only at exchanges).  pos is
+ * [n_walkers][nmax][3]; trace, if given, is [n_walkers][n_sweeps][moves_per_sweep];
+ * counts, if given, is [n_walkers][3 move types][trials, accepts].
+ * Returns 0, or -1 on invalid arguments. */
+int oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32_t *n,
+                  double *energy, const int32_t *state_of_walker, uint32_t t0,
+                  int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                  int64_t *counts, int n_threads)
+{
+    int S = sys->L * sys->M;
+    if (n_walkers != S || sys->nmax < 1 || sys->moves_per_sweep < 0 || n_sweeps < 0) return -1;
+    char *seen = (char *)calloc((size_t)S, 1);
+    for (int w = 0; w < S; ++w) {
+        int s = state_of_walker[w];
+        if (s < 0 || s >= S || seen[s] || n[w] < 0 || n[w] > sys->nmax) { free(seen); return -1; }
+        seen[s] = 1;
+    }
+    free(seen);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int w = 0; w < S; ++w) {
+        oracle_move *tr = trace ? trace + (int64_t)w * n_sweeps * sys->moves_per_sweep : NULL;
+        sweep_walker(sys, w, pos + (int64_t)w * sys->nmax * 3, n + w, energy + w,
+                     state_of_walker[w], t0, n_sweeps, hist, tr, counts);
+    }
+    (void)n_threads;
+    return 0;
+}
+
+/* ------------------------------------------------------------- exchange */
+
+/* One collective replica-exchange attempt number e (Sec. II.A.2).  One of four
+ * neighbour directions on the (T, mu) grid is drawn with probability 1/4
+ * (T, mu, diagonal, anti-diagonal) together with a parity bit; every state
+ * (l, m) whose row (column, for the mu direction) has that parity is paired
+ * with its neighbour (l + dl, m + dm) if it exists.  Each pair swaps its
+ * configurations with the probability of Eq. Pacc; a swap moves the state
+ * labels of the two walkers, not their coordinates.
+ * ex_counts, if given, is [S][4][attempts, accepts] indexed by the lower state.
+ * Returns the number of accepted swaps, or -1 on invalid arguments. */
+int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
+                    const double *energy, int32_t *state_of_walker,
+                    int32_t *walker_of_state, int64_t *ex_counts)
+{
+    static const int DL[4] = {1, 0, 1, 1};
+    static const int DM[4] = {0, 1, 1, -1};
+    int L = sys->L, M = sys->M, S = L * M;
+    for (int s = 0; s < S; ++s) {
+        int w = walker_of_state[s];
+        if (w < 0 || w >= S || state_of_walker[w] != s) return -1;
+    }
+    uint32_t C[4];
+    draw(sys, e, 0u, 0u, 2u, C);
+    int type = (int)(((uint64_t)C[0] * 4u) >> 32);
+    int parity = (int)(C[1] >> 31);
+    int accepted = 0;
+    for (int l = 0; l < L; ++l) {
+        for (int m = 0; m < M; ++m) {
+            int key = DL[type] ? l : m;
+            if ((key & 1) != parity) continue;
+            int l2 = l + DL[type], m2 = m + DM[type];
+            if (l2 < 0 || l2 >= L || m2 < 0 || m2 >= M) continue;
+            int a = l * M + m, b = l2 * M + m2;
+            int wa = walker_of_state[a], wb = walker_of_state[b];
+            double la = oracle_exchange_log_alpha(sys, a, b, n[wa], n[wb], energy[wa], energy[wb]);
+            uint32_t D[4];
+            draw(sys, e, (uint32_t)a, 0u, 3u, D);
+            int acc = log(u32_open(D[0])) < la;
+            if (ex_counts) {
+                ex_counts[8 * (int64_t)a + 2 * type] += 1;
+                ex_counts[8 * (int64_t)a + 2 * type + 1] += acc;
+            }
+            if (acc) {
+                walker_of_state[a] = wb;
+                walker_of_state[b] = wa;
+                state_of_walker[wa] = b;
+                state_of_walker[wb] = a;
+                accepted += 1;
+            }
+        }
+    }
+    return accepted;
+}

@@ -1,0 +1,112 @@
+/*
+ * regc_oracle.h -- FP64 CPU oracle of the replica-exchange grand-canonical
+ * Monte Carlo (REGCMC) sampler of Zhou, Scheffler & Ghiringhelli,
+ * "Determining Surface Phase Diagrams Including Anharmonic Effects"
+ * (arXiv:1908.11118).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the CUDA library
+ * against a plain, slow, obviously correct restatement of the method.  Only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header, table or constant with the CUDA path.
+ *
+ * Everything is double precision.  Particle coordinates are kept on values
+ * that are exactly representable in binary32 (every coordinate update is
+ * rounded through float), so that a binary32 implementation that performs
+ * the same coordinate arithmetic holds bit-identical configurations while
+ * its accept/reject decisions agree with this one.
+ */
+#ifndef REGC_ORACLE_H
+#define REGC_ORACLE_H
+#include <stdint.h>
+
+#define ORACLE_MAX_TYPES 4
+
+/* Problem statement: the potential, the surface, the gas region and the
+ * (T, mu) grid (Sec. I: the method takes only the potential-energy function
+ * and the T and mu ranges as inputs). */
+typedef struct {
+    /* truncated Lennard-Jones 12-6 pair potential (Appendix, force field):
+     * phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] for r < rc, else 0.
+     * Type 0 is the mobile (grand-canonical) species; surface atoms carry
+     * types 1..n_types-1. */
+    int    n_types;
+    double eps[ORACLE_MAX_TYPES][ORACLE_MAX_TYPES];
+    double sigma[ORACLE_MAX_TYPES][ORACLE_MAX_TYPES];
+    double rc;
+    /* box: x and y periodic; z periodic only if periodic_z */
+    double Lx, Ly, Lz;
+    int    periodic_z;
+    /* region available to mobile particles, z_lo <= z <= z_hi (Sec. III.A:
+     * insertion only in the zone above the top surface layer) */
+    double z_lo, z_hi;
+    /* frozen surface atoms (species A of Sec. III.A) */
+    int           n_surf;
+    const double *surf_xyz;   /* [n_surf][3] */
+    const int    *surf_type;  /* [n_surf]    */
+    /* replica grid S = L x M, state s = l*M + m (Sec. II.A.2) */
+    int           L, M;
+    const double *kT;         /* [L] */
+    const double *mu;         /* [M] */
+    double        lambda0;    /* thermal wavelength Lambda(kT) = lambda0/sqrt(kT) */
+    /* move set */
+    int    nmax;              /* capacity: insertion at N = nmax is rejected */
+    int    moves_per_sweep;
+    double max_disp;          /* half-edge of the displacement cube */
+    double p_disp;            /* probability of a displacement; GC gets the rest, 50/50 */
+    uint64_t seed;            /* Philox key */
+    /* pooled (N, E) histogram: bin k covers [e_lo + k*e_bin, e_lo + (k+1)*e_bin) */
+    double e_lo, e_bin;
+    int    n_e_bins;
+    /* planted-mistake switches for sensitivity tests of the pins; 0 in all
+     * real use (bit meanings in regc_oracle.c) */
+    int    mutation;
+} oracle_system;
+
+/* One trial move as the oracle executed it. */
+typedef struct {
+    int32_t type;       /* 0 displace, 1 insert, 2 delete */
+    int32_t index;      /* particle touched (insert: the new slot N) */
+    int32_t accepted;   /* 1 accepted, 0 rejected */
+    int32_t status;     /* 0 energy evaluated, 1 rejected at the N boundary,
+                           2 displacement left the region */
+    double  dE;         /* energy change of the move (0 unless status 0) */
+    double  log_alpha;  /* log of the acceptance ratio (status 0 only) */
+    double  ln_u;       /* log of the acceptance uniform */
+    double  sum_abs;    /* sum of |phi| over every pair entering dE */
+    double  band;       /* sum of |phi(rc)| over pairs with r^2 within 4e-6 rc^2 of rc^2 */
+    int32_t n_pairs;    /* pairs with r < rc entering dE */
+    int32_t pad;
+} oracle_move;
+
+/* Histograms filled once per sweep, at the walker's current state. */
+typedef struct {
+    int64_t *hN;        /* [S][nmax+1] occupation counts of N            */
+    int64_t *hNE;       /* [nmax+1][n_e_bins] pooled (N, E-bin) counts   */
+    int64_t *omega;     /* [S] observations per state                    */
+    double  *moments;   /* [S][4]: sum N, sum N^2, sum E, sum E^2        */
+    int64_t *e_out;     /* [S] observations with E outside the E window  */
+} oracle_hist;
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+void   oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double oracle_phi(const oracle_system *sys, int ti, int tj, double r2);
+double oracle_particle_energy(const oracle_system *sys, const double *pos, int n,
+                              double x, double y, double z, int skip,
+                              double *sum_abs, double *band, int *n_pairs);
+double oracle_total_energy(const oracle_system *sys, const double *pos, int n);
+double oracle_log_alpha(const oracle_system *sys, int type, int state, int n, double dE);
+double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
+                                 int na, int nb, double ea, double eb);
+int    oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32_t *n,
+                     double *energy, const int32_t *state_of_walker, uint32_t t0,
+                     int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                     int64_t *counts, int n_threads);
+int    oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
+                       const double *energy, int32_t *state_of_walker,
+                       int32_t *walker_of_state, int64_t *ex_counts);
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module builds problem statements (surface slab, box, gas region, (T, mu)
+grid, move settings) and seeded initial walker configurations.  It holds none
+of the sampler's arithmetic: no pair potential, no acceptance rule, no random
+stream of the method.  Every geometric value is rounded to binary32 here, once,
+so that the FP64 oracle and the FP32 GPU path start from identical numbers.
+
+Workloads (reduced Lennard-Jones units, k_B = eps_gg = sigma_gg = m = 1):
+
+* ``fcc100_small`` -- frozen fcc(100) slab of 4x4x2 atoms (32 atoms, in-layer
+  nearest-neighbour distance 1.5625), periodic 6.25 x 6.25 box, gas region
+  from the top layer to a hard wall at z = 10, eps_sg = 2, rc = 2.5,
+  4 kT (0.6-1.5 geometric) x 4 mu (-6..-2), Nmax 32, 20 moves per sweep.
+* ``fcc111_paper_scale`` -- frozen fcc(111) slab of 12x12x4 atoms (576 atoms,
+  ABC stacking), 18.75 x 16.238 box, gas region 12 high above the top layer,
+  eps_sg in {1, 2, 3}, 32 x 32 (kT, mu) states, Nmax 512.  This stands in for
+  the paper's LJ A18 slab in a B gas (Sec. III.A) in reduced units.
+* ``tiny_box`` -- a few surface atoms in a small box, Nmax <= 2, for
+  brute-force partition-function checks.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+F32 = np.float32
+
+
+def f32(x):
+    """Round a scalar or array to binary32 and return it as float64."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+@dataclasses.dataclass
+class Problem:
+    """A REGC problem statement: potential, surface, box, grid, move settings."""
+
+    n_types: int
+    eps: np.ndarray          # [4, 4] float64 (binary32 values)
+    sigma: np.ndarray        # [4, 4]
+    rc: float
+    Lx: float
+    Ly: float
+    Lz: float
+    periodic_z: int
+    z_lo: float
+    z_hi: float
+    surf_xyz: np.ndarray     # [n_surf, 3] float64 (binary32 values)
+    surf_type: np.ndarray    # [n_surf] int32, values 1..n_types-1
+    kT: np.ndarray           # [L] float64
+    mu: np.ndarray           # [M] float64
+    lambda0: float
+    nmax: int
+    moves_per_sweep: int
+    max_disp: float
+    p_disp: float
+    seed: int
+    e_lo: float
+    e_bin: float
+    n_e_bins: int
+    name: str = "custom"
+
+    @property
+    def L(self) -> int:
+        return int(len(self.kT))
+
+    @property
+    def M(self) -> int:
+        return int(len(self.mu))
+
+    @property
+    def S(self) -> int:
+        return self.L * self.M
+
+    @property
+    def n_surf(self) -> int:
+        return int(len(self.surf_type))
+
+    @property
+    def volume(self) -> float:
+        return self.Lx * self.Ly * (self.z_hi - self.z_lo)
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+def _pair_tables(eps_gg, sig_gg, eps_sg, sig_sg):
+    eps = np.zeros((4, 4))
+    sig = np.ones((4, 4))
+    eps[0, 0] = eps_gg
+    sig[0, 0] = sig_gg
+    eps[0, 1] = eps[1, 0] = eps_sg
+    sig[0, 1] = sig[1, 0] = sig_sg
+    return f32(eps), f32(sig)
+
+
+def fcc100_slab(nx: int, ny: int, layers: int, s: float):
+    """fcc(100) slab: square in-layer lattice of spacing s, alternate layers
+    shifted by (s/2, s/2), layer spacing s/sqrt(2).  Returns (xyz, Lx, Ly, z_top)."""
+    dz = s / math.sqrt(2.0)
+    pts = []
+    for k in range(layers):
+        off = 0.5 * s if (k % 2) else 0.0
+        for j in range(ny):
+            for i in range(nx):
+                pts.append(((i * s + off) % (nx * s), (j * s + off) % (ny * s), k * dz))
+    xyz = f32(np.array(pts))
+    return xyz, float(f32(nx * s)), float(f32(ny * s)), float(f32((layers - 1) * dz))
+
+
+def fcc111_slab(nx: int, ny: int, layers: int, s: float):
+    """fcc(111) slab in a rectangular supercell of nx columns and ny (even) rows
+    of a hexagonal layer with nearest-neighbour distance s; ABC stacking with
+    layer spacing s*sqrt(2/3).  Returns (xyz, Lx, Ly, z_top)."""
+    if ny % 2:
+        raise ValueError("fcc111_slab needs an even number of rows")
+    h = s * math.sqrt(3.0) / 2.0
+    lx, ly = nx * s, ny * h
+    dz = s * math.sqrt(2.0 / 3.0)
+    shifts = [(0.0, 0.0), (0.5 * s, h / 3.0), (s, 2.0 * h / 3.0)]
+    pts = []
+    for k in range(layers):
+        sx, sy = shifts[k % 3]
+        for j in range(ny):
+            for i in range(nx):
+                x = i * s + (0.5 * s if (j % 2) else 0.0) + sx
+                y = j * h + sy
+                pts.append((x % lx, y % ly, k * dz))
+    xyz = f32(np.array(pts))
+    xyz[:, 0] = np.where(xyz[:, 0] >= f32(lx), 0.0, xyz[:, 0])
+    xyz[:, 1] = np.where(xyz[:, 1] >= f32(ly), 0.0, xyz[:, 1])
+    return xyz, float(f32(lx)), float(f32(ly)), float(f32((layers - 1) * dz))
+
+
+def kT_grid(L: int, lo: float = 0.6, hi: float = 1.5) -> np.ndarray:
+    if L == 1:
+        return np.array([lo])
+    return lo * (hi / lo) ** (np.arange(L) / (L - 1))
+
+
+def mu_grid(M: int, lo: float = -6.0, hi: float = -2.0) -> np.ndarray:
+    if M == 1:
+        return np.array([lo])
+    return lo + (hi - lo) * np.arange(M) / (M - 1)
+
+
+def fcc100_small(L: int = 4, M: int = 4, nmax: int = 32, eps_sg: float = 2.0,
+                 seed: int = 0) -> Problem:
+    """The 16-replica fcc(100) workload (4x4x2 slab, 6.25 x 6.25 x 10 box)."""
+    xyz, lx, ly, ztop = fcc100_slab(4, 4, 2, 1.5625)
+    eps, sig = _pair_tables(1.0, 1.0, eps_sg, 1.0)
+    return Problem(
+        n_types=2, eps=eps, sigma=sig, rc=2.5, Lx=lx, Ly=ly, Lz=10.0, periodic_z=0,
+        z_lo=ztop, z_hi=10.0, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
+        max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
+        e_lo=-float(nmax) * 12.0, e_bin=0.05,
+        n_e_bins=int(round(float(nmax) * 13.0 / 0.05)), name="fcc100_small")
+
+
+def fcc111_paper_scale(L: int = 32, M: int = 32, nmax: int = 512, eps_sg: float = 2.0,
+                       seed: int = 0) -> Problem:
+    """The 1024-replica fcc(111) workload (12x12x4 slab, gas 12 high, Nmax 512)."""
+    xyz, lx, ly, ztop = fcc111_slab(12, 12, 4, 1.5625)
+    eps, sig = _pair_tables(1.0, 1.0, eps_sg, 1.0)
+    zhi = float(f32(ztop + 12.0))
+    return Problem(
+        n_types=2, eps=eps, sigma=sig, rc=2.5, Lx=lx, Ly=ly, Lz=zhi, periodic_z=0,
+        z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
+        max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
+        e_lo=-float(nmax) * 14.0, e_bin=0.5,
+        n_e_bins=int(round(float(nmax) * 15.0 / 0.5)), name="fcc111_paper_scale")
+
+
+def tiny_box(nmax: int = 2, rc: float = 1.5, eps_sg: float = 1.0, eps_gg: float = 1.0,
+             kT=(1.0,), mu=(-1.0,), seed: int = 0) -> Problem:
+    """A 3 x 3 box with two surface atoms under a gas region 1.0 <= z <= 2.6,
+    for brute-force partition functions with Nmax <= 2."""
+    xyz = f32(np.array([[0.75, 0.75, 0.0], [2.25, 2.25, 0.0]]))
+    eps, sig = _pair_tables(eps_gg, 1.0, eps_sg, 1.0)
+    return Problem(
+        n_types=2, eps=eps, sigma=sig, rc=float(f32(rc)), Lx=3.0, Ly=3.0, Lz=2.6,
+        periodic_z=0, z_lo=1.0, z_hi=2.6, surf_xyz=xyz,
+        surf_type=np.ones(2, np.int32), kT=np.asarray(kT, float), mu=np.asarray(mu, float),
+        lambda0=1.0, nmax=nmax, moves_per_sweep=20, max_disp=0.3, p_disp=1.0 / 3.0,
+        seed=seed, e_lo=-40.0, e_bin=0.05, n_e_bins=1600, name="tiny_box")
+
+
+def ideal_gas(problem: Problem) -> Problem:
+    """The same problem with every interaction switched off (eps = 0)."""
+    return problem.replace(eps=np.zeros((4, 4)), name=problem.name + "_ideal")
+
+
+def initial_walkers(problem: Problem, n_init, seed: int, min_dist: float = 0.9):
+    """Seeded initial configurations: walker w gets n_init[w] particles at
+    uniform positions of the gas region, no two closer than min_dist (and no
+    particle closer than min_dist to a surface atom), coordinates in binary32.
+    Returns (pos [S, nmax, 3] float64, n [S] int32)."""
+    rng = np.random.default_rng(seed)
+    S, nmax = problem.S, problem.nmax
+    n_init = np.broadcast_to(np.asarray(n_init, dtype=np.int64), (S,))
+    pos = np.zeros((S, nmax, 3))
+    n = np.zeros(S, np.int32)
+    box = np.array([problem.Lx, problem.Ly, problem.Lz])
+    per = np.array([True, True, bool(problem.periodic_z)])
+    for w in range(S):
+        pts = []
+        tries = 0
+        while len(pts) < n_init[w] and tries < 200000:
+            tries += 1
+            p = f32([rng.uniform(0, problem.Lx), rng.uniform(0, problem.Ly),
+                     rng.uniform(problem.z_lo, problem.z_hi)])
+            if p[0] >= problem.Lx or p[1] >= problem.Ly or p[2] > problem.z_hi:
+                continue
+            others = np.array(pts + [list(a) for a in problem.surf_xyz]).reshape(-1, 3)
+            if len(others):
+                d = p - others
+                d = np.where(per, d - box * np.round(d / box), d)
+                if np.min(np.sum(d * d, axis=1)) < min_dist * min_dist:
+                    continue
+            pts.append(list(p))
+        if len(pts) < n_init[w]:
+            raise ValueError("could not place the requested particles")
+        if pts:
+            pos[w, :len(pts)] = np.array(pts)
+        n[w] = len(pts)
+    return pos, n
