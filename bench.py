@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark: GCMC trial moves/s over all replicas of the REGC sampler.
+
+Workload (the paper-scale LJ surface-gas system): frozen fcc(111) slab of
+12x12x4 atoms, gas region 12 high, eps_sg = 2, 32 kT x 32 mu = 1024 replicas,
+Nmax 512, 20 trial moves per sweep.  Initial walkers: N ~ U{0..256} particles
+on a jittered lattice (seeded), then untimed equilibration sweeps.
+
+One step = 10 sweeps of every replica (one sweep-kernel launch) followed by one
+collective replica-exchange attempt (one exchange-kernel launch).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+own arm: device-timed (CUDA events on the library's stream) steps, with the L2
+flushed (256 MB memset) before every timed step; the JSON line adds the
+FP32-ALU roofline of the sweep kernel, the end-to-end rate through the C ABI
+with host buffers, sampled SM clocks, and the FP64 CPU oracle timed on a
+bounded sample on the host cores.
+reference arm: the FP64 CPU oracle on the same workload and metric.
+Under torchrun (N > 1) every rank runs its own independent 1024-replica grid
+(seed = rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+SWEEPS_PER_STEP = 10
+FLOPS_PER_PAIR = 20            # dx,dy,dz 3, xy minimum image 4, r^2 5, r^-2 1, s^6 3, 4eps s^6(s^6-1) 4
+SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+METRIC = "GCMC trial moves/s over all replicas"
+WORKLOAD = ("fcc111 12x12x4 slab + LJ gas, 32 kT x 32 mu = 1024 replicas, Nmax 512, "
+            "20 moves/sweep; step = 10 sweeps + 1 replica-exchange attempt")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--equil", type=int, default=500, help="untimed equilibration sweeps")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def combine_rank_results(times_ms, moves_per_rank):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    t = max(times_ms)
+    return sum(moves_per_rank) / (t / 1e3), t
+
+
+def fp32_peak():
+    """FP32 ALU peak: measured if the peaks file has one, else unit counts x clock."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("fp32_tflops", "fp32_tflops_sustained"):
+                if k in d:
+                    return float(d[k]), "measured (%s)" % k
+        except Exception:
+            pass
+    return SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12, \
+        "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = [r.split(",") for r in open(self.file.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) > 8
+                          for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def initial_state(p, seed):
+    rng = np.random.default_rng(seed)
+    n0 = rng.integers(0, p.nmax // 2 + 1, p.S)
+    return W.lattice_walkers(p, n0, seed=seed)
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0):
+    """Run the FP64 oracle on the workload in steps of 10 sweeps + exchange
+    until `seconds` have passed.  Returns (moves/s, steps timed, threads)."""
+    from oracle import oracle as O
+    O.build()
+    orc = O.Oracle(p, pos=pos, n=n)
+    for _ in range(warmup):
+        orc.run(SWEEPS_PER_STEP, exchange_every=SWEEPS_PER_STEP, hist=True)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        orc.run(SWEEPS_PER_STEP, exchange_every=SWEEPS_PER_STEP, hist=True)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and steps >= min_steps) or (max_steps and steps >= max_steps):
+            break
+    moves = steps * p.S * SWEEPS_PER_STEP * p.moves_per_sweep
+    return moves / el, steps, el, os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = W.fcc111_paper_scale(seed=0)
+    pos, n = initial_state(p, 0)
+    rate, steps, el, cores = time_oracle(p, pos, n, seconds=0.0, min_steps=args.steps,
+                                         max_steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "moves/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "start": "seeded lattice state, no equilibration"},
+        "cpu_baseline": {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
+                         "sample": "full 1024-replica workload, %d steps of 10 sweeps + exchange" % steps},
+        "e2e": {"value": rate, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- own arm
+
+def run_own(args):
+    import torch
+
+    from paper_1908_11118_gb300 import Regc
+    from paper_1908_11118_gb300 import build as B
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = W.fcc111_paper_scale(seed=rank)
+    pos0, n0 = initial_state(p, rank)
+    stream = torch.cuda.Stream()
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos0, n0)
+    g.run(args.equil, exchange_every=SWEEPS_PER_STEP)
+    for _ in range(args.warmup):
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    mv0, _, pr0 = g.counters()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        g.sweep(SWEEPS_PER_STEP)
+        ev[k][1].record(stream)
+        g.exchange()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    sweep_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    mv1, _, pr1 = g.counters()
+    total_ms = float(sum(step_ms))
+    moves = p.S * SWEEPS_PER_STEP * p.moves_per_sweep * K
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_max = float(t.item())
+    else:
+        total_max = total_ms
+    value = moves * world / (total_max / 1e3)
+    accepted = int((mv1[:, :, 1] - mv0[:, :, 1]).sum())
+    pairs = int(pr1[0] - pr0[0])
+    cand = int(pr1[1] - pr0[1])
+    mean_sweep_s = sum(sweep_ms) / K / 1e3
+    achieved = pairs / K * FLOPS_PER_PAIR / mean_sweep_s / 1e12
+    peak, peak_src = fp32_peak()
+
+    # end to end through the C ABI with host buffers: full walker state in,
+    # full walker state and energies out, every step
+    pos_h, n_h, e_h, sow_h = g.get_walkers()
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_walkers(pos_h, n_h, sow_h)
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+        pos_h, n_h, e_h, sow_h = g.get_walkers()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = p.S * p.nmax * 16 + p.S * 4 * 2
+    d2h = p.S * p.nmax * 16 + p.S * (4 + 8 + 4) + 4
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            rate, steps, el, cores = time_oracle(p, pos0, n0, seconds=args.cpu_seconds)
+            cpu = {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
+                   "sample": "full 1024-replica workload from the seeded lattice state, "
+                             "%d steps of 10 sweeps + exchange (%.1f s)" % (steps, el)}
+        line = {
+            "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "equilibration_sweeps": args.equil,
+                       "l2": "flushed (256 MB memset) before every timed step",
+                       "precision": "pair energies f32, totals exact 64-bit fixed point, acceptance f64"},
+            "accepted_moves_per_s": accepted * world / (total_max / 1e3),
+            "pair_interactions_per_s": pairs * world / (total_max / 1e3),
+            "candidate_pairs_per_s": cand * world / (total_max / 1e3),
+            "roofline": {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src,
+                         "work": "%d flop/pair x pairs within rc (%.3g per launch)" % (FLOPS_PER_PAIR, pairs / K),
+                         "launch_ms": mean_sweep_s * 1e3},
+            "e2e": {"value": p.S * SWEEPS_PER_STEP * p.moves_per_sweep * world / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * K,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * regc.h -- C ABI of the GB300 (sm_103a) replica-exchange grand-canonical
+ * Monte Carlo (REGCMC) library.
+ *
+ * Method: Y. Zhou, M. Scheffler, L. M. Ghiringhelli, "Determining Surface
+ * Phase Diagrams Including Anharmonic Effects", arXiv:1908.11118.
+ *   Sec. II.A    -- the REGC cycle: grand-canonical moves, replica exchange,
+ *                   canonical diffusion, iterated
+ *   Sec. II.A.1  -- insertion / removal and their acceptance probabilities
+ *   Sec. II.A.2  -- the extended (T, mu) ensemble and the swap rule (Eq. Pacc)
+ *   Sec. II.A.3  -- Metropolis displacement
+ *   Sec. II.B    -- MBAR reweighting to phase diagrams (Eqs. textbook,
+ *                   grandpot, normlizationconstant)
+ *   Appendix     -- the Lennard-Jones 12-6 force field
+ *
+ * Conventions common to every entry point:
+ *   - Reduced units: k_B = 1, energies in eps, lengths in sigma.
+ *   - Every call returns a regc_status; nothing aborts or exits.  A CUDA error
+ *     makes the handle's status sticky: later calls on that handle return it.
+ *   - Pointers named host_* or documented "host" are host memory owned by the
+ *     caller; inputs are copied before the call returns, outputs are written
+ *     before it returns (the call synchronises its stream when it returns
+ *     data).  The library allocates and frees its own device memory.
+ *   - All device work of a handle is issued on the CUDA stream given to
+ *     regc_init_grid (NULL = the legacy default stream).
+ *   - One handle must not be used by two host threads at once.
+ *
+ * Move and random-number conventions (needed to reproduce a run exactly):
+ *   Philox4x32-10 (Salmon et al., SC'11), key = (seed low, seed high) words.
+ *   Trial move k of sweep t of walker w draws two blocks,
+ *     A = Philox(ctr = (k, t, w, 0)), B = Philox(ctr = (k, t, w, 1)):
+ *     A0 < floor(p_disp 2^32)      -> displacement, else grand-canonical move,
+ *     B2 >> 31 == 0                -> removal, else insertion (y1 < 0.5 -> removal),
+ *     i = (B0 * N) >> 32           -> particle picked by displacement / removal,
+ *     U24(a) = (a >> 8) 2^-24      -> displacement d_c = max_disp (2 U24(A_{c+1}) - 1),
+ *                                     insertion point (Lx U24(A1), Ly U24(A2),
+ *                                     z_lo + (z_hi - z_lo) U24(A3)),
+ *     u = (B1 + 0.5) 2^-32         -> accept iff ln u < ln(acceptance ratio).
+ *   Coordinates are binary32 and every coordinate operation is one IEEE
+ *   round-to-nearest binary32 operation, in the order written above.
+ *   Exchange number e draws C = Philox((e, 0, 0, 2)) (direction (C0 * 4) >> 32,
+ *   parity C1 >> 31) and, for the pair whose lower state index is a,
+ *   D = Philox((e, a, 0, 3)), u = (D0 + 0.5) 2^-32.
+ */
+#ifndef REGC_H
+#define REGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define REGC_API __attribute__((visibility("default")))
+#else
+#define REGC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct regc_handle regc_handle;   /* opaque; owned by the library */
+
+typedef enum {
+    REGC_OK = 0,
+    REGC_EINVAL = -1,     /* an argument is out of range; nothing was changed    */
+    REGC_ENOMEM = -2,     /* a device or host allocation failed                  */
+    REGC_ECUDA = -3,      /* a CUDA call failed (sticky on the handle)           */
+    REGC_ETIMEOUT = -4,   /* a bounded device wait gave up (sticky)              */
+    REGC_ECAPACITY = -5,  /* a cell of a walker's cell list overflowed (sticky):
+                             the move that needed the slot was rejected, so the
+                             chain from that point on is not the exact one       */
+    REGC_ENUMERIC = -6    /* a non-finite or out-of-range energy was detected    */
+} regc_status;
+
+/* Truncated Lennard-Jones 12-6 pair potential (Appendix, force field):
+ * phi_ij(r) = 4 eps[ti][tj] ((sigma[ti][tj]/r)^12 - (sigma[ti][tj]/r)^6) for
+ * r < rc, 0 otherwise.  Type 0 is the mobile, grand-canonical species (B of
+ * Sec. III.A); frozen surface atoms carry types 1..n_types-1 (A).  Tables are
+ * symmetric; entries outside n_types are ignored. */
+typedef struct {
+    int   n_types;          /* 1..4 */
+    float eps[4][4];
+    float sigma[4][4];
+    float rc;               /* > 0; Lx, Ly (and Lz if periodic) must be >= 2 rc */
+} regc_potential;
+
+/* Frozen surface slab and the box (Sec. II.A.1: the subsystem of volume V in
+ * contact with the reservoir; Sec. III.A: insertion only in the zone above the
+ * topmost surface layer).  x and y are periodic with periods Lx, Ly.  Mobile
+ * particles live in z_lo <= z <= z_hi; if periodic_z, z is periodic with period
+ * Lz and the region is the whole box (z_lo = 0, z_hi = Lz required).
+ * V = Lx Ly (z_hi - z_lo) enters the acceptance rules. */
+typedef struct {
+    int          n_atoms;   /* >= 0 */
+    const float *xyz;       /* host [n_atoms][3]; x in [0, Lx), y in [0, Ly) */
+    const int   *type;      /* host [n_atoms]; 1..n_types-1                  */
+    float        Lx, Ly, Lz;
+    int          periodic_z;
+    float        z_lo, z_hi;
+} regc_surface;
+
+/* The (T, mu) grid of replicas (Sec. II.A.2: S = L x M states; state
+ * s = l M + m holds (kT[l], mu[m])) and the move set. */
+typedef struct {
+    int           L, M;             /* L * M <= 65536 */
+    const double *kT;               /* host [L], > 0  */
+    const double *mu;               /* host [M]       */
+    double        lambda0;          /* Lambda(kT) = lambda0 / sqrt(kT) (Eq. Ngrand) */
+    int           nmax;             /* 1..4096: insertion at N = nmax is rejected   */
+    int           moves_per_sweep;  /* 1..1024 trial moves per sweep                */
+    float         max_disp;         /* half-edge of the displacement cube (Sec. II.A.3) */
+    double        p_disp;           /* probability of a displacement move, [0, 1]   */
+    double        e_lo, e_bin;      /* pooled (N, E) histogram: bin k covers        */
+    int           n_e_bins;         /*   [e_lo + k e_bin, e_lo + (k+1) e_bin)       */
+} regc_grid_spec;
+
+/* One trial move, as recorded by regc_sweep_traced. */
+typedef struct {
+    int32_t type;        /* 0 displacement, 1 insertion, 2 removal                 */
+    int32_t index;       /* particle moved or removed; insertion: the new slot N  */
+    int32_t accepted;    /* 1 if accepted                                          */
+    int32_t status;      /* 0 energy evaluated, 1 rejected at N = 0 or N = nmax,
+                            2 displacement left [z_lo, z_hi]                       */
+    double  dE;          /* energy change of the move (status 0)                   */
+    double  log_alpha;   /* ln of the acceptance ratio (status 0)                  */
+    double  ln_u;        /* ln of the acceptance uniform                           */
+    double  sum_abs;     /* unused by the GPU path (0)                             */
+    double  band;        /* unused by the GPU path (0)                             */
+    int32_t n_pairs;     /* pairs with r < rc that entered dE                      */
+    int32_t pad;
+} regc_move_record;
+
+/* Create a handle: copies the problem statement, builds the surface lookup
+ * tables and the per-state constants, allocates the walker state and the
+ * histograms on the device and sets every walker to N = 0 at state s = w.
+ * seed keys every Philox stream.  cuda_stream is a cudaStream_t (or NULL).
+ * Errors: REGC_EINVAL (bad sizes, box smaller than 2 rc, nmax beyond the
+ * shared-memory budget of one walker), REGC_ENOMEM, REGC_ECUDA.  On error
+ * *out is NULL. */
+REGC_API regc_status regc_init_grid(const regc_potential *pot, const regc_surface *surf,
+                           const regc_grid_spec *grid, uint64_t seed, void *cuda_stream,
+                           regc_handle **out);
+
+/* Run n_sweeps sweeps (n_sweeps x moves_per_sweep trial moves) on every walker
+ * (Sec. II.A.1 insertion/removal, Sec. II.A.3 displacement) at the walkers'
+ * current states, and observe each walker once per sweep into its state's
+ * histograms: hN[s][N] += 1, omega[s] += 1, moments[s] += (N, N^2, E, E^2),
+ * pooled hNE[N][bin(E)] += 1 (Sec. II.B: samples Omega_{l,m} per state).
+ * Asynchronous on the handle's stream.  Errors: REGC_EINVAL (n_sweeps < 0),
+ * the handle's sticky status. */
+REGC_API regc_status regc_sweep(regc_handle *h, int n_sweeps);
+
+/* As regc_sweep, and write one record per trial move to host memory:
+ * trace is [S walkers][n_sweeps][moves_per_sweep].  Synchronous.  Intended
+ * for move-by-move comparison with a reference implementation. */
+REGC_API regc_status regc_sweep_traced(regc_handle *h, int n_sweeps, regc_move_record *trace);
+
+/* One collective replica-exchange attempt (Sec. II.A.2, Eq. Pacc): a direction
+ * (T, mu, diagonal, anti-diagonal) and a parity are drawn; every state of that
+ * parity swaps with its neighbour in that direction with probability
+ * min[1, (b_a/b_b)^{3/2 (N_a - N_b)} exp(-(b_a - b_b)(E_b - E_a)
+ *                                          - (b_a mu_a - b_b mu_b)(N_a - N_b))],
+ * where state a holds (N_a, E_a).  A swap exchanges the walkers' state labels.
+ * Asynchronous.  The exchange counter advances by one per call. */
+REGC_API regc_status regc_exchange(regc_handle *h);
+
+/* Copy the histograms to caller-owned host buffers (any may be NULL):
+ * hN [S][nmax+1], hNE [nmax+1][n_e_bins], omega [S], moments [S][4]
+ * (sum N, sum N^2, sum E, sum E^2), e_out [S] (observations with E outside
+ * the E window).  Synchronous. */
+REGC_API regc_status regc_histograms(regc_handle *h, int64_t *hN, int64_t *hNE, int64_t *omega,
+                            double *moments, int64_t *e_out);
+
+/* Zero every histogram and counter (not the walkers). */
+REGC_API regc_status regc_reset_histograms(regc_handle *h);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+REGC_API void regc_free(regc_handle *h);
+
+/* ---------------------------------------------------------- extensions */
+
+/* Replace the walkers' configurations: pos [S][nmax][3] (binary32, x in
+ * [0, Lx), y in [0, Ly), z in [z_lo, z_hi]), n [S] in 0..nmax, and optionally
+ * state_of_walker [S] (a permutation of 0..S-1; NULL keeps the current labels).
+ * Energies are recomputed on the device.  Host buffers.  Errors: REGC_EINVAL
+ * (coordinates outside the region, N out of range, not a permutation, two
+ * particles closer than 0.25 sigma). */
+REGC_API regc_status regc_set_walkers(regc_handle *h, const float *pos, const int32_t *n,
+                             const int32_t *state_of_walker);
+
+/* Read the walkers: pos [S][nmax][3] (entries beyond N undefined), n [S],
+ * energy [S] (the running total E(R; N), all mobile-mobile and mobile-surface
+ * pairs), state_of_walker [S].  Any may be NULL.  Synchronous. */
+REGC_API regc_status regc_get_walkers(regc_handle *h, float *pos, int32_t *n, double *energy,
+                             int32_t *state_of_walker);
+
+/* Recompute every walker's energy from scratch and report the largest
+ * |running total - recomputed| in *max_drift (0 when the bookkeeping is exact).
+ * The running totals are not changed.  Returns REGC_ENUMERIC if an energy is
+ * not finite.  Synchronous. */
+REGC_API regc_status regc_check_energy(regc_handle *h, double *max_drift);
+
+/* Counters (host buffers, any may be NULL): moves [S walkers][3 types][trials,
+ * accepts]; exchanges [S lower states][4 directions][attempts, accepts];
+ * pairs [2]: pairs within rc evaluated, candidate pairs examined, summed over
+ * walkers since the last reset.  Synchronous. */
+REGC_API regc_status regc_counters(regc_handle *h, int64_t *moves, int64_t *exchanges, int64_t *pairs);
+
+/* MBAR reweighting of the handle's pooled histogram (Sec. II.B).  Solves the
+ * self-consistent equations of Eq. normlizationconstant over the occupied
+ * (N, E) bins with the reduced potential
+ *   u_s(N, E) = beta_s (E - mu_s N) + 3 N ln Lambda_s          (Eq. grandpot
+ * plus the thermal-wavelength factor of Eq. Ngrand, needed across temperatures),
+ * then evaluates the nq query states (kT_q, mu_q): N_mean [nq], pN [nq][nmax+1]
+ * (probability of each N, Eq. textbook with chi = [N = i]).  f_states [S]
+ * receives the state free energies (f_0 = 0).  Any output may be NULL.
+ * Iterates until max |delta f| < tol or max_iter iterations; *iters, if not
+ * NULL, receives the count.  FP64 log-sum-exp on the device.  Synchronous. */
+REGC_API regc_status regc_reweight(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
+                          double tol, int max_iter, double *N_mean, double *pN,
+                          double *f_states, int *iters);
+
+/* Stand-alone MBAR solve over caller-supplied pooled bins (host buffers):
+ * S states (kT [S], mu [S], omega [S] observations), B bins (N_b [B], E_b [B],
+ * H_b [B] > 0 counts).  Outputs f [S] (f_0 = 0) and D [B], the log denominators
+ * D_b = ln sum_k omega_k exp(f_k - u_k(b)).  Runs on cuda_stream. */
+REGC_API regc_status regc_mbar_solve(int S, const double *kT, const double *mu, double lambda0,
+                            const double *omega, int B, const int32_t *N_b,
+                            const double *E_b, const double *H_b, double tol,
+                            int max_iter, double *f, double *D, int *iters,
+                            void *cuda_stream);
+
+/* Stand-alone MBAR query: with D [B] from regc_mbar_solve, reweight to Q
+ * states; outputs N_mean [Q], pN [Q][nmax+1], f_q [Q] (any may be NULL). */
+REGC_API regc_status regc_mbar_query(int Q, const double *kT_q, const double *mu_q, double lambda0,
+                            int B, const int32_t *N_b, const double *E_b, const double *H_b,
+                            const double *D, int nmax, double *N_mean, double *pN,
+                            double *f_q, void *cuda_stream);
+
+/* Human-readable name of a status. */
+REGC_API const char *regc_status_string(regc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REGC_H */

@@ -1,0 +1,108 @@
+"""ctypes declarations of the C ABI in include/regc.h.
+
+The shared library is built in-tree (paper_1908_11118_gb300/_build/libregc.so)
+by paper_1908_11118_gb300/build.py.  There is no other implementation: if the
+library is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libregc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "regc.h")
+
+REGC_OK = 0
+STATUS = {0: "REGC_OK", -1: "REGC_EINVAL", -2: "REGC_ENOMEM", -3: "REGC_ECUDA",
+          -4: "REGC_ETIMEOUT", -5: "REGC_ECAPACITY", -6: "REGC_ENUMERIC"}
+
+
+class RegcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s returned %s" % (where, STATUS.get(status, status)))
+        self.status = status
+
+
+class Potential(C.Structure):
+    _fields_ = [("n_types", C.c_int), ("eps", (C.c_float * 4) * 4),
+                ("sigma", (C.c_float * 4) * 4), ("rc", C.c_float)]
+
+
+class Surface(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("xyz", C.POINTER(C.c_float)), ("type", C.POINTER(C.c_int)),
+                ("Lx", C.c_float), ("Ly", C.c_float), ("Lz", C.c_float), ("periodic_z", C.c_int),
+                ("z_lo", C.c_float), ("z_hi", C.c_float)]
+
+
+class GridSpec(C.Structure):
+    _fields_ = [("L", C.c_int), ("M", C.c_int), ("kT", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double)), ("lambda0", C.c_double), ("nmax", C.c_int),
+                ("moves_per_sweep", C.c_int), ("max_disp", C.c_float), ("p_disp", C.c_double),
+                ("e_lo", C.c_double), ("e_bin", C.c_double), ("n_e_bins", C.c_int)]
+
+
+class MoveRecord(C.Structure):
+    _fields_ = [("type", C.c_int32), ("index", C.c_int32), ("accepted", C.c_int32),
+                ("status", C.c_int32), ("dE", C.c_double), ("log_alpha", C.c_double),
+                ("ln_u", C.c_double), ("sum_abs", C.c_double), ("band", C.c_double),
+                ("n_pairs", C.c_int32), ("pad", C.c_int32)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+_fp = C.POINTER(C.c_float)
+_h = C.c_void_p
+
+SIGNATURES = {
+    "regc_init_grid": ([C.POINTER(Potential), C.POINTER(Surface), C.POINTER(GridSpec), C.c_uint64,
+                        C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "regc_sweep": ([_h, C.c_int], C.c_int),
+    "regc_sweep_traced": ([_h, C.c_int, C.c_void_p], C.c_int),
+    "regc_exchange": ([_h], C.c_int),
+    "regc_histograms": ([_h, _lp, _lp, _lp, _dp, _lp], C.c_int),
+    "regc_reset_histograms": ([_h], C.c_int),
+    "regc_free": ([_h], None),
+    "regc_set_walkers": ([_h, _fp, _ip, _ip], C.c_int),
+    "regc_get_walkers": ([_h, _fp, _ip, _dp, _ip], C.c_int),
+    "regc_check_energy": ([_h, _dp], C.c_int),
+    "regc_counters": ([_h, _lp, _lp, _lp], C.c_int),
+    "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
+    "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
+                         C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
+    "regc_mbar_query": ([C.c_int, _dp, _dp, C.c_double, C.c_int, _ip, _dp, _dp, _dp, C.c_int,
+                         _dp, _dp, _dp, C.c_void_p], C.c_int),
+    "regc_status_string": ([C.c_int], C.c_char_p),
+}
+
+_lib = None
+
+
+def declared_symbols(header: str = HEADER):
+    """Entry points declared in include/regc.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(regc_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """The loaded library (raises if it has not been built or cannot load)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libregc.so is not built (run paper_1908_11118_gb300/build.py or "
+                               "__graft_entry__.build()); there is no fallback implementation")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != REGC_OK:
+        raise RegcError(status, where)

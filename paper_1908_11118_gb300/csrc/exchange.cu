@@ -1,0 +1,53 @@
+// exchange.cu -- collective replica exchange on the (T, mu) grid (sm_103a).
+//
+// Sec. II.A.2: one of four neighbour directions (T, mu, diagonal,
+// anti-diagonal) is drawn with probability 1/4 together with a parity bit.
+// Every state (l, m) whose row (column, for the mu direction) has that parity
+// is paired with (l + dl, m + dm); pairs are disjoint, so one thread per pair
+// decides and swaps without races.  The swap rule is Eq. Pacc in log form,
+// evaluated in FP64; a swap exchanges the two walkers' state labels.
+#include "launch.h"
+
+namespace regc {
+namespace {
+
+__global__ void __launch_bounds__(1024) exchange_kernel(const __grid_constant__ ExchangeParams X, uint32_t e) {
+    const U4 C = philox(e, 0u, 0u, 2u, X.key0, X.key1);
+    const int type = (int)(((unsigned long long)C.x * 4ull) >> 32);
+    const int parity = (int)(C.y >> 31);
+    const int dl = type == 1 ? 0 : 1;
+    const int dm = type == 0 ? 0 : (type == 3 ? -1 : 1);
+    const int S = X.L * X.M;
+    for (int a = threadIdx.x; a < S; a += blockDim.x) {
+        const int l = a / X.M, m = a - (a / X.M) * X.M;
+        const int key = dl ? l : m;
+        if ((key & 1) != parity) continue;
+        const int l2 = l + dl, m2 = m + dm;
+        if (l2 >= X.L || m2 < 0 || m2 >= X.M) continue;
+        const int b = l2 * X.M + m2;
+        const int wa = X.walker_of_state[a], wb = X.walker_of_state[b];
+        const double dn = (double)(X.n[wa] - X.n[wb]);
+        const double ea = (double)X.efix[wa] * kFixUnit, eb = (double)X.efix[wb] * kFixUnit;
+        const double la = 1.5 * dn * (X.lnbeta[a] - X.lnbeta[b]) - (X.beta[a] - X.beta[b]) * (eb - ea) -
+                          (X.bmu[a] - X.bmu[b]) * dn;
+        const U4 D = philox(e, (uint32_t)a, 0u, 3u, X.key0, X.key1);
+        const bool acc = log(((double)D.x + 0.5) * 2.3283064365386963e-10) < la;
+        X.ex_counts[8 * a + 2 * type] += 1;
+        X.ex_counts[8 * a + 2 * type + 1] += acc;
+        if (acc) {
+            X.walker_of_state[a] = wb;
+            X.walker_of_state[b] = wa;
+            X.state_of_walker[wa] = b;
+            X.state_of_walker[wb] = a;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s) {
+    exchange_kernel<<<1, 1024, 0, s>>>(X, e);
+    return cudaGetLastError();
+}
+
+}  // namespace regc

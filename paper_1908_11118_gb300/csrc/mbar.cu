@@ -1,0 +1,372 @@
+// mbar.cu -- FP64 MBAR reweighting on the device (Sec. II.B), sm_103a.
+//
+// The self-consistent equations of Eq. normlizationconstant, pooled over the
+// occupied (N, E) bins b with counts H_b, in log form:
+//   D_b = ln sum_k Omega_k exp(f_k - u_k(b))        (one thread per bin)
+//   f_s = -ln sum_b H_b exp(-u_s(b) - D_b)           (one block per state)
+// with f_0 = 0 after each iteration.  Sums are log-sum-exp in FP64 with an
+// online maximum; terms more than 50 below the running maximum are skipped
+// (their total weight is below the FP64 rounding of the sum).
+// Query states reuse the D_b: the weight of bin b at state q is
+// H_b exp(-u_q(b) - D_b + f_q), giving <N> and p_N (Eq. textbook with the
+// phase indicator chi_i = [N = i]).
+#include <math.h>
+
+#include "mbar.h"
+
+namespace regc {
+namespace {
+
+constexpr double kSkip = 50.0;
+
+struct Lse {
+    double m, s;
+};
+
+__device__ __forceinline__ void lse_add(Lse& L, double x) {
+    if (x > L.m) {
+        L.s = L.s * exp(L.m - x) + 1.0;
+        L.m = x;
+    } else if (x > L.m - kSkip) {
+        L.s += exp(x - L.m);
+    }
+}
+
+__device__ __forceinline__ Lse lse_merge(Lse a, Lse b) {
+    if (b.m == -INFINITY) return a;
+    if (a.m == -INFINITY) return b;
+    const double m = fmax(a.m, b.m);
+    return Lse{m, a.s * exp(a.m - m) + b.s * exp(b.m - m)};
+}
+
+__device__ __forceinline__ Lse warp_merge(Lse L) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Lse other{__shfl_xor_sync(0xffffffffu, L.m, o), __shfl_xor_sync(0xffffffffu, L.s, o)};
+        L = lse_merge(L, other);
+    }
+    return L;
+}
+
+// Merge across a block (blockDim a multiple of 32, <= 1024); result valid in all threads.
+__device__ Lse block_merge(Lse L) {
+    __shared__ double sm[32], ss[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    L = warp_merge(L);
+    __syncthreads();
+    if (lane == 0) {
+        sm[warp] = L.m;
+        ss[warp] = L.s;
+    }
+    __syncthreads();
+    Lse r{-INFINITY, 0.0};
+    if (lane < nw) r = Lse{sm[lane], ss[lane]};
+    r = warp_merge(r);
+    return r;
+}
+
+__device__ double block_sum(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+constexpr int kTile = 1024;
+
+// D_b = ln sum_k exp(lnom_k + f_k - a_k E_b - c_k N_b)
+__global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev m, int always) {
+    if (!always && m.state[0]) return;
+    __shared__ double sa[kTile], sc[kTile], sg[kTile];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = b < m.B;
+    const double E = act ? m.E_b[b] : 0.0;
+    const double N = act ? (double)m.N_b[b] : 0.0;
+    Lse L{-INFINITY, 0.0};
+    for (int k0 = 0; k0 < m.S; k0 += kTile) {
+        const int nk = min(kTile, m.S - k0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            sa[k] = m.a[k0 + k];
+            sc[k] = m.c[k0 + k];
+            sg[k] = m.lnom[k0 + k] + m.f[k0 + k];
+        }
+        __syncthreads();
+        if (act)
+            for (int k = 0; k < nk; ++k) lse_add(L, sg[k] - fma(sa[k], E, sc[k] * N));
+    }
+    if (act) m.D[b] = L.m + log(L.s);
+}
+
+// f_new_s = -ln sum_b exp(lnH_b - a_s E_b - c_s N_b - D_b)
+__global__ void __launch_bounds__(256) f_kernel(const __grid_constant__ MbarDev m) {
+    if (m.state[0]) return;
+    const int s = blockIdx.x;
+    const double a = m.a[s], c = m.c[s];
+    Lse L{-INFINITY, 0.0};
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
+        lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+    L = block_merge(L);
+    if (threadIdx.x == 0) m.f_new[s] = -(L.m + log(L.s));
+}
+
+// Gauge f_0 = 0, convergence test, f <- f_new.
+__global__ void __launch_bounds__(1024) norm_kernel(const __grid_constant__ MbarDev m, double tol) {
+    if (m.state[0]) return;
+    const double f0 = m.f_new[0];
+    double d = 0.0;
+    for (int s = threadIdx.x; s < m.S; s += blockDim.x) d = fmax(d, fabs((m.f_new[s] - f0) - m.f[s]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (threadIdx.x == 0) sh[0] = r;
+    }
+    __syncthreads();
+    d = sh[0];
+    for (int s = threadIdx.x; s < m.S; s += blockDim.x) m.f[s] = m.f_new[s] - f0;
+    if (threadIdx.x == 0) {
+        m.delta[0] = d;
+        m.state[1] += 1;
+        if (d < tol) m.state[0] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) query_kernel(const __grid_constant__ MbarDev m, const double* a_q,
+                                                    const double* c_q, int nmax, double* n_mean,
+                                                    double* pN, double* f_q) {
+    extern __shared__ double hist[];   // [nmax + 1]
+    const int q = blockIdx.x;
+    const double a = a_q[q], c = c_q[q];
+    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) hist[n] = 0.0;
+    Lse L{-INFINITY, 0.0};
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
+        lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+    L = block_merge(L);
+    const double fq = -(L.m + log(L.s));
+    double nsum = 0.0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x) {
+        const double x = m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b] + fq;
+        if (x > -745.0) {
+            const double w = exp(x);
+            const int n = m.N_b[b];
+            nsum += w * (double)n;
+            if (pN && n <= nmax) atomicAdd(&hist[n], w);
+        }
+    }
+    nsum = block_sum(nsum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (n_mean) n_mean[q] = nsum;
+        if (f_q) f_q[q] = fq;
+    }
+    if (pN)
+        for (int n = threadIdx.x; n <= nmax; n += blockDim.x) pN[size_t(q) * (nmax + 1) + n] = hist[n];
+}
+
+// ------------------------------------------------------------- compaction
+
+constexpr int kChunk = 1024;  // elements per block, 256 threads x 4
+
+__global__ void __launch_bounds__(256) count_kernel(const unsigned long long* h, long long n, int* counts) {
+    const long long base = (long long)blockIdx.x * kChunk;
+    int c = 0;
+    for (int k = 0; k < 4; ++k) {
+        const long long i = base + threadIdx.x * 4 + k;
+        c += (i < n && h[i] != 0ull);
+    }
+    c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+    __shared__ int sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of counts[nblk] in place, total -> *total (one block)
+__global__ void __launch_bounds__(1024) scan_kernel(int* counts, int nblk, int* total) {
+    __shared__ int carry;
+    __shared__ int wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblk ? counts[i] : 0;
+        int x = v;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int y = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += t;
+            }
+            wsum[lane] = y;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+        if (i < nblk) counts[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) write_kernel(const unsigned long long* h, long long n, int nbins,
+                                                    double e_lo, double e_bin, const int* offsets,
+                                                    int* N_b, double* E_b, double* lnH) {
+    const long long base = (long long)blockIdx.x * kChunk;
+    int c = 0;
+    for (int k = 0; k < 4; ++k) {
+        const long long i = base + threadIdx.x * 4 + k;
+        c += (i < n && h[i] != 0ull);
+    }
+    // block exclusive scan of c
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    __shared__ int wsum[8];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    int out = offsets[blockIdx.x] + before + x - c;
+    for (int k = 0; k < 4; ++k) {
+        const long long i = base + threadIdx.x * 4 + k;
+        if (i < n && h[i] != 0ull) {
+            const long long nn = i / nbins, kb = i - nn * nbins;
+            N_b[out] = (int)nn;
+            E_b[out] = e_lo + ((double)kb + 0.5) * e_bin;
+            lnH[out] = log((double)h[i]);
+            ++out;
+        }
+    }
+}
+
+// a = beta, c = 3 ln Lambda - beta mu, lnom = ln Omega (-inf when Omega = 0);
+// Omega from omega_d (double) or omega_u (uint64), either may be null.
+__global__ void prep_states_kernel(int S, const double* kT, const double* mu, double lambda0,
+                                   const double* omega_d, const unsigned long long* omega_u, double* a,
+                                   double* c, double* lnom) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double b = 1.0 / kT[s];
+    a[s] = b;
+    c[s] = 3.0 * (log(lambda0) - 0.5 * log(kT[s])) - b * mu[s];
+    if (lnom) {
+        const double om = omega_d ? omega_d[s] : (omega_u ? (double)omega_u[s] : 0.0);
+        lnom[s] = om > 0.0 ? log(om) : -INFINITY;
+    }
+}
+
+__global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) lnH[b] = log(H[b]);
+}
+
+}  // namespace
+
+cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s) {
+    cudaError_t err;
+    const int batch = 16;
+    int host_state[2] = {0, 0};
+    err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(m.f, 0, size_t(m.S) * sizeof(double), s);
+    if (err != cudaSuccess) return err;
+    const int dgrid = (m.B + 255) / 256;
+    int launched = 0;
+    while (launched < max_iter) {
+        const int nb = min(batch, max_iter - launched);
+        for (int i = 0; i < nb; ++i) {
+            d_kernel<<<dgrid, 256, 0, s>>>(m, 0);
+            f_kernel<<<m.S, 256, 0, s>>>(m);
+            norm_kernel<<<1, 1024, 0, s>>>(m, tol);
+        }
+        launched += nb;
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        err = cudaMemcpyAsync(host_state, m.state, sizeof(host_state), cudaMemcpyDeviceToHost, s);
+        if (err != cudaSuccess) return err;
+        err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) return err;
+        if (host_state[0]) break;
+    }
+    d_kernel<<<dgrid, 256, 0, s>>>(m, 1);  // D_b of the final f
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (iters_out) *iters_out = host_state[1];
+    return cudaSuccess;
+}
+
+cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, int nmax,
+                           double* n_mean, double* pN, double* f_q, cudaStream_t s) {
+    if (Q <= 0) return cudaSuccess;
+    const size_t smem = size_t(nmax + 1) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    query_kernel<<<Q, 256, smem, s>>>(m, a_q, c_q, nmax, n_mean, pN, f_q);
+    return cudaGetLastError();
+}
+
+size_t compact_scratch_ints(long long n) { return size_t((n + kChunk - 1) / kChunk) + 1; }
+
+cudaError_t compact_count_dev(const unsigned long long* hist, long long n, int* scratch, int* count_out,
+                              cudaStream_t s) {
+    const int nblk = (int)((n + kChunk - 1) / kChunk);
+    if (nblk == 0) return cudaMemsetAsync(count_out, 0, sizeof(int), s);
+    count_kernel<<<nblk, 256, 0, s>>>(hist, n, scratch);
+    scan_kernel<<<1, 1024, 0, s>>>(scratch, nblk, count_out);
+    return cudaGetLastError();
+}
+
+cudaError_t compact_write_dev(const unsigned long long* hist, long long n, int nbins, double e_lo, double e_bin,
+                              const int* scratch, int* N_b, double* E_b, double* lnH, cudaStream_t s) {
+    const int nblk = (int)((n + kChunk - 1) / kChunk);
+    if (nblk == 0) return cudaSuccess;
+    write_kernel<<<nblk, 256, 0, s>>>(hist, n, nbins, e_lo, e_bin, scratch, N_b, E_b, lnH);
+    return cudaGetLastError();
+}
+
+cudaError_t mbar_prep_states(int S, const double* kT, const double* mu, double lambda0, const double* omega_d,
+                             const unsigned long long* omega_u, double* a, double* c, double* lnom, cudaStream_t s) {
+    if (S <= 0) return cudaSuccess;
+    prep_states_kernel<<<(S + 255) / 256, 256, 0, s>>>(S, kT, mu, lambda0, omega_d, omega_u, a, c, lnom);
+    return cudaGetLastError();
+}
+
+cudaError_t mbar_prep_bins(int B, const double* H, double* lnH, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    prep_bins_kernel<<<(B + 255) / 256, 256, 0, s>>>(B, H, lnH);
+    return cudaGetLastError();
+}
+
+}  // namespace regc

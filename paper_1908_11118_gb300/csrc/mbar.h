@@ -1,0 +1,57 @@
+// mbar.h -- device MBAR reweighting (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace regc {
+
+// Device arrays of one MBAR problem: S states, B pooled bins.  The reduced
+// potential of state s at bin b is u_s(b) = a[s] E_b + c[s] N_b with
+// a = beta, c = 3 ln Lambda - beta mu.
+struct MbarDev {
+    int S, B;
+    const double* a;       // [S]
+    const double* c;       // [S]
+    const double* lnom;    // [S] ln Omega_s (-inf when Omega_s = 0)
+    const int* N_b;        // [B]
+    const double* E_b;     // [B]
+    const double* lnH;     // [B]
+    double* f;             // [S] current free energies (gauge f_0 = 0)
+    double* f_new;         // [S]
+    double* D;             // [B]
+    double* delta;         // [1] max |f_new - f| of the last iteration
+    int* state;            // [2] {converged flag, iterations done}
+};
+
+// Iterate the self-consistent equations from f = 0 until max |df| < tol or
+// max_iter iterations.  Synchronises the stream every `batch` iterations.
+cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out,
+                           cudaStream_t s);
+
+// Reweight to Q query states given on the device as (a_q, c_q):
+// N_mean [Q], pN [Q][nmax+1], f_q [Q] (device, any may be null).
+cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q,
+                           int nmax, double* N_mean, double* pN, double* f_q, cudaStream_t s);
+
+// Compact the non-empty bins of a pooled histogram hist[n] (row-major in
+// (N, E-bin), nbins E-bins per N) into N_b, E_b (bin centres), lnH (ln
+// counts), in row-major order.  compact_count_dev writes the per-block
+// offsets to scratch (compact_scratch_ints(n) ints) and the number of
+// non-empty bins to *count_out (device); compact_write_dev then fills the
+// arrays.
+size_t compact_scratch_ints(long long n);
+cudaError_t compact_count_dev(const unsigned long long* hist, long long n, int* scratch, int* count_out,
+                              cudaStream_t s);
+cudaError_t compact_write_dev(const unsigned long long* hist, long long n, int nbins, double e_lo, double e_bin,
+                              const int* scratch, int* N_b, double* E_b, double* lnH, cudaStream_t s);
+
+// State constants on the device: a = 1/kT, c = 3 ln(lambda0/sqrt(kT)) - mu/kT,
+// lnom = ln Omega (-inf for Omega = 0; skipped when lnom is null).  kT, mu are
+// per state (device); Omega from omega_d (double) or omega_u (uint64).
+cudaError_t mbar_prep_states(int S, const double* kT, const double* mu, double lambda0, const double* omega_d,
+                             const unsigned long long* omega_u, double* a, double* c, double* lnom, cudaStream_t s);
+// lnH = ln H (device).
+cudaError_t mbar_prep_bins(int B, const double* H, double* lnH, cudaStream_t s);
+
+}  // namespace regc

@@ -1,0 +1,768 @@
+// regc_api.cu -- the C ABI of the REGC library (host side).
+//
+// Validates arguments, derives the per-state constants of the acceptance
+// rules (Sec. II.A.1, Eq. Ngrand), lays out the device state, and launches the
+// kernels of sweep.cu, exchange.cu and mbar.cu on the handle's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "launch.h"
+#include "mbar.h"
+
+using namespace regc;
+
+struct regc_handle {
+    cudaStream_t stream = nullptr;
+    int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0, wpc = 1;
+    double lambda0 = 1.0, e_lo = 0.0, e_bin = 1.0;
+    float Lx = 0, Ly = 0, Lz = 0, z_lo = 0, z_hi = 0;
+    int periodic_z = 0;
+    std::vector<double> kT_state, mu_state;   // per state
+    double* d_kT_state = nullptr;
+    double* d_mu_state = nullptr;
+    SweepParams P{};
+    ExchangeParams X{};
+    uint32_t t = 0, e = 0;
+    regc_status sticky = REGC_OK;
+    std::vector<void*> allocs;
+    int* d_error = nullptr;
+    long long* d_fix = nullptr;               // scratch [S] for energy recomputes
+    size_t smem_per_walker = 0;
+};
+
+namespace {
+
+constexpr size_t kMaxSmem = 232448;  // 227 KB per block on sm_103a
+
+regc_status cuda_fail(regc_handle* h, cudaError_t e) {
+    if (e == cudaSuccess) return REGC_OK;
+    if (h && h->sticky == REGC_OK) h->sticky = (e == cudaErrorMemoryAllocation) ? REGC_ENOMEM : REGC_ECUDA;
+    return e == cudaErrorMemoryAllocation ? REGC_ENOMEM : REGC_ECUDA;
+}
+
+template <class T>
+regc_status dalloc(regc_handle* h, T** p, size_t count) {
+    void* v = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->allocs.push_back(v);
+    e = cudaMemsetAsync(v, 0, bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    *p = static_cast<T*>(v);
+    return REGC_OK;
+}
+
+template <class T>
+regc_status upload(regc_handle* h, T* dst, const T* src, size_t count) {
+    if (count == 0) return REGC_OK;
+    return cuda_fail(h, cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+}
+
+// Synchronise and fold the device error word into the sticky status.
+regc_status sync_check(regc_handle* h) {
+    if (h->sticky != REGC_OK) return h->sticky;
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (err & ERR_TIMEOUT) h->sticky = REGC_ETIMEOUT;
+    else if (err & ERR_CAPACITY) h->sticky = REGC_ECAPACITY;
+    else if (err & ERR_NUMERIC) h->sticky = REGC_ENUMERIC;
+    return h->sticky;
+}
+
+int cells_along(double len, double rc) {
+    const int n = (int)floor(len / (rc * 1.00001));
+    return n < 1 ? 1 : n;
+}
+
+// Hard-core guard radius^2 of a pair type: pairs closer than this have
+// phi > T = 1e6 max(eps_max, kT_max, 1), so every move creating one has an
+// acceptance probability far below 2^-33 and is rejected outright; the guard
+// also keeps every accepted pair term inside the fixed-point range.
+float hard_core_r2(double eps, double sigma, double T) {
+    if (eps <= 0.0) return 0.0f;
+    double lo = 1e-3, hi = 1.0;   // x = r / sigma
+    for (int it = 0; it < 200; ++it) {
+        const double x = 0.5 * (lo + hi);
+        const double s6 = 1.0 / pow(x, 6.0);
+        const double phi = 4.0 * eps * (s6 * s6 - s6);
+        if (phi > T) lo = x;
+        else hi = x;
+    }
+    const double r = lo * sigma;
+    return (float)(r * r);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* regc_status_string(regc_status s) {
+    switch (s) {
+        case REGC_OK: return "ok";
+        case REGC_EINVAL: return "invalid argument";
+        case REGC_ENOMEM: return "out of memory";
+        case REGC_ECUDA: return "CUDA error";
+        case REGC_ETIMEOUT: return "device wait timed out";
+        case REGC_ECAPACITY: return "cell-list capacity exceeded";
+        case REGC_ENUMERIC: return "non-finite or out-of-range energy";
+    }
+    return "unknown status";
+}
+
+void regc_free(regc_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, const regc_grid_spec* grid,
+                           uint64_t seed, void* cuda_stream, regc_handle** out) {
+    if (!out) return REGC_EINVAL;
+    *out = nullptr;
+    if (!pot || !surf || !grid) return REGC_EINVAL;
+    // ---- validation
+    const int nt = pot->n_types;
+    if (nt < 1 || nt > 4 || !(pot->rc > 0.0f)) return REGC_EINVAL;
+    double eps_max = 0.0;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) {
+            if (!(pot->eps[i][j] >= 0.0f) || !(pot->eps[i][j] <= 2000.0f) || !(pot->sigma[i][j] > 0.0f))
+                return REGC_EINVAL;
+            eps_max = std::max(eps_max, (double)pot->eps[i][j]);
+        }
+    const double rc = pot->rc;
+    if (!(surf->Lx >= 2 * rc) || !(surf->Ly >= 2 * rc) || !(surf->z_hi > surf->z_lo)) return REGC_EINVAL;
+    if (surf->periodic_z && (!(surf->Lz >= 2 * rc) || surf->z_lo != 0.0f || surf->z_hi != surf->Lz))
+        return REGC_EINVAL;
+    if (surf->n_atoms < 0 || (surf->n_atoms > 0 && (!surf->xyz || !surf->type))) return REGC_EINVAL;
+    for (int a = 0; a < surf->n_atoms; ++a) {
+        const float* r = surf->xyz + 3 * a;
+        if (surf->type[a] < 1 || surf->type[a] >= nt) return REGC_EINVAL;
+        if (!(r[0] >= 0.0f && r[0] < surf->Lx && r[1] >= 0.0f && r[1] < surf->Ly) || !std::isfinite(r[2]))
+            return REGC_EINVAL;
+    }
+    if (grid->L < 1 || grid->M < 1 || (long long)grid->L * grid->M > 65536 || !grid->kT || !grid->mu)
+        return REGC_EINVAL;
+    double kT_max = 0.0;
+    for (int l = 0; l < grid->L; ++l) {
+        if (!(grid->kT[l] > 0.0) || !(grid->kT[l] <= 2000.0)) return REGC_EINVAL;
+        kT_max = std::max(kT_max, grid->kT[l]);
+    }
+    for (int m = 0; m < grid->M; ++m)
+        if (!std::isfinite(grid->mu[m])) return REGC_EINVAL;
+    if (grid->nmax < 1 || grid->nmax > 4096 || grid->moves_per_sweep < 1 || grid->moves_per_sweep > 1024)
+        return REGC_EINVAL;
+    if (!(grid->max_disp >= 0.0f) || !(grid->p_disp >= 0.0 && grid->p_disp <= 1.0) || !(grid->lambda0 > 0.0))
+        return REGC_EINVAL;
+    if (!(grid->e_bin > 0.0) || grid->n_e_bins < 1 || !std::isfinite(grid->e_lo)) return REGC_EINVAL;
+    if ((long long)(grid->nmax + 1) * grid->n_e_bins > (1LL << 31)) return REGC_EINVAL;
+
+    // ---- geometry of the cell list
+    const int periodic_z = surf->periodic_z ? 1 : 0;
+    const double hz = periodic_z ? surf->Lz : (double)surf->z_hi - (double)surf->z_lo;
+    CellGrid cg{};
+    cg.ncx = cells_along(surf->Lx, rc);
+    cg.ncy = cells_along(surf->Ly, rc);
+    cg.ncz = cells_along(hz, rc);
+    if ((long long)cg.ncx * cg.ncy * cg.ncz > 65535) return REGC_EINVAL;
+    cg.ncell = cg.ncx * cg.ncy * cg.ncz;
+    cg.icx = (float)(cg.ncx / (double)surf->Lx);
+    cg.icy = (float)(cg.ncy / (double)surf->Ly);
+    cg.icz = (float)(cg.ncz / hz);
+    const double vcell = (double)surf->Lx / cg.ncx * ((double)surf->Ly / cg.ncy) * (hz / cg.ncz);
+    cg.cap = std::min(grid->nmax, std::max(8, (int)ceil(1.6 * vcell) + 8));
+    const size_t spw = sweep_smem_per_walker(grid->nmax, cg.ncell, cg.cap);
+    if (spw > kMaxSmem) return REGC_EINVAL;
+
+    regc_handle* h = new (std::nothrow) regc_handle;
+    if (!h) return REGC_ENOMEM;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->L = grid->L;
+    h->M = grid->M;
+    h->S = grid->L * grid->M;
+    h->nmax = grid->nmax;
+    h->mps = grid->moves_per_sweep;
+    h->n_e_bins = grid->n_e_bins;
+    h->lambda0 = grid->lambda0;
+    h->e_lo = grid->e_lo;
+    h->e_bin = grid->e_bin;
+    h->Lx = surf->Lx;
+    h->Ly = surf->Ly;
+    h->Lz = surf->Lz;
+    h->z_lo = surf->z_lo;
+    h->z_hi = surf->z_hi;
+    h->periodic_z = periodic_z;
+    h->smem_per_walker = spw;
+    // walkers per CTA: as many as keep one CTA within 64 KB of shared memory
+    h->wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / spw));
+    const int S = h->S;
+
+    // ---- per-state constants of the acceptance rules
+    const double V = (double)surf->Lx * (double)surf->Ly * ((double)surf->z_hi - (double)surf->z_lo);
+    const double lnV = log(V);
+    std::vector<double> beta(S), c_ins(S), c_del(S), bmu(S), lnbeta(S);
+    h->kT_state.resize(S);
+    h->mu_state.resize(S);
+    for (int s = 0; s < S; ++s) {
+        const double kT = grid->kT[s / grid->M], mu = grid->mu[s % grid->M];
+        const double b = 1.0 / kT;
+        const double lnL = log(grid->lambda0) - 0.5 * log(kT);
+        beta[s] = b;
+        c_ins[s] = lnV - 3.0 * lnL + b * mu;
+        c_del[s] = 3.0 * lnL - lnV - b * mu;
+        bmu[s] = b * mu;
+        lnbeta[s] = log(b);
+        h->kT_state[s] = kT;
+        h->mu_state[s] = mu;
+    }
+    std::vector<double> ln_tab(grid->nmax + 2, 0.0);
+    for (int k = 1; k < grid->nmax + 2; ++k) ln_tab[k] = log((double)k);
+
+    // ---- surface columns (atoms within rc of any point of a column)
+    SurfaceTab st{};
+    st.nsx = std::max(1, (int)floor(surf->Lx / 0.6));
+    st.nsy = std::max(1, (int)floor(surf->Ly / 0.6));
+    st.isx = (float)(st.nsx / (double)surf->Lx);
+    st.isy = (float)(st.nsy / (double)surf->Ly);
+    const double wx = (double)surf->Lx / st.nsx, wy = (double)surf->Ly / st.nsy;
+    const double reach = rc * 1.0001 + 1e-4;
+    std::vector<float4> all(surf->n_atoms);
+    double zmax = -INFINITY;
+    std::vector<int> relevant;
+    for (int a = 0; a < surf->n_atoms; ++a) {
+        const float* r = surf->xyz + 3 * a;
+        all[a] = make_float4(r[0], r[1], r[2], (float)surf->type[a]);
+        if (periodic_z || r[2] > surf->z_lo - reach) {
+            relevant.push_back(a);
+            zmax = std::max(zmax, (double)r[2]);
+        }
+    }
+    st.z_reach = relevant.empty() ? -INFINITY : (float)(zmax + rc * 1.00001 + 1e-4);
+    std::vector<int> col_off(st.nsx * st.nsy + 1, 0);
+    std::vector<float4> col_atoms;
+    for (int iy = 0; iy < st.nsy; ++iy)
+        for (int ix = 0; ix < st.nsx; ++ix) {
+            const double cx = (ix + 0.5) * wx, cy = (iy + 0.5) * wy;
+            for (int a : relevant) {
+                double dx = (double)surf->xyz[3 * a] - cx, dy = (double)surf->xyz[3 * a + 1] - cy;
+                dx -= surf->Lx * nearbyint(dx / surf->Lx);
+                dy -= surf->Ly * nearbyint(dy / surf->Ly);
+                const double ex = std::max(0.0, fabs(dx) - 0.5 * wx), ey = std::max(0.0, fabs(dy) - 0.5 * wy);
+                if (ex * ex + ey * ey < reach * reach) col_atoms.push_back(all[a]);
+            }
+            col_off[iy * st.nsx + ix + 1] = (int)col_atoms.size();
+        }
+
+    // ---- pair tables
+    const double T = 1e6 * std::max(std::max(eps_max, kT_max), 1.0);
+    SweepParams& P = h->P;
+    P.gg = PairTab{4.0f * pot->eps[0][0], pot->sigma[0][0] * pot->sigma[0][0],
+                   hard_core_r2(pot->eps[0][0], pot->sigma[0][0], T)};
+    for (int t = 0; t < 4; ++t) {
+        const int tt = t < nt ? t : 0;
+        P.gs[t] = PairTab{4.0f * pot->eps[0][tt], pot->sigma[0][tt] * pot->sigma[0][tt],
+                          hard_core_r2(pot->eps[0][tt], pot->sigma[0][tt], T)};
+    }
+    P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 1.0f, (float)(1.0 / surf->Lx),
+                   (float)(1.0 / surf->Ly), periodic_z ? (float)(1.0 / surf->Lz) : 0.0f, periodic_z,
+                   surf->z_lo, surf->z_hi, surf->z_hi - surf->z_lo, (float)(rc * rc)};
+    P.cg = cg;
+    P.max_disp = grid->max_disp;
+    P.th_disp = (unsigned long long)floor(grid->p_disp * 4294967296.0);
+    P.S = S;
+    P.nmax = grid->nmax;
+    P.mps = grid->moves_per_sweep;
+    P.key0 = (uint32_t)seed;
+    P.key1 = (uint32_t)(seed >> 32);
+    P.e_lo = grid->e_lo;
+    P.e_bin = grid->e_bin;
+    P.n_e_bins = grid->n_e_bins;
+    P.smem_per_walker = (int)spw;
+
+    // ---- device memory
+    regc_status st_ = REGC_OK;
+#define TRY(x)                         \
+    do {                               \
+        st_ = (x);                     \
+        if (st_ != REGC_OK) {          \
+            regc_free(h);              \
+            return st_;                \
+        }                              \
+    } while (0)
+    double *d_beta, *d_cins, *d_cdel, *d_ln, *d_bmu, *d_lnbeta;
+    int* d_coloff;
+    float4 *d_colat, *d_all;
+    TRY(dalloc(h, &d_beta, S));
+    TRY(dalloc(h, &d_cins, S));
+    TRY(dalloc(h, &d_cdel, S));
+    TRY(dalloc(h, &d_bmu, S));
+    TRY(dalloc(h, &d_lnbeta, S));
+    TRY(dalloc(h, &d_ln, ln_tab.size()));
+    TRY(dalloc(h, &h->d_kT_state, S));
+    TRY(dalloc(h, &h->d_mu_state, S));
+    TRY(dalloc(h, &d_coloff, col_off.size()));
+    TRY(dalloc(h, &d_colat, col_atoms.size()));
+    TRY(dalloc(h, &d_all, all.size()));
+    TRY(upload(h, d_beta, beta.data(), S));
+    TRY(upload(h, d_cins, c_ins.data(), S));
+    TRY(upload(h, d_cdel, c_del.data(), S));
+    TRY(upload(h, d_bmu, bmu.data(), S));
+    TRY(upload(h, d_lnbeta, lnbeta.data(), S));
+    TRY(upload(h, d_ln, ln_tab.data(), ln_tab.size()));
+    TRY(upload(h, h->d_kT_state, h->kT_state.data(), S));
+    TRY(upload(h, h->d_mu_state, h->mu_state.data(), S));
+    TRY(upload(h, d_coloff, col_off.data(), col_off.size()));
+    TRY(upload(h, d_colat, col_atoms.data(), col_atoms.size()));
+    TRY(upload(h, d_all, all.data(), all.size()));
+    st.col_off = d_coloff;
+    st.atoms = d_colat;
+    st.all = d_all;
+    st.n_all = surf->n_atoms;
+    P.st = st;
+    P.beta = d_beta;
+    P.c_ins = d_cins;
+    P.c_del = d_cdel;
+    P.ln_tab = d_ln;
+    int *d_n, *d_sow, *d_wos;
+    long long *d_efix, *d_mc, *d_exc;
+    float4* d_pos;
+    TRY(dalloc(h, &d_pos, (size_t)S * grid->nmax));
+    TRY(dalloc(h, &d_n, S));
+    TRY(dalloc(h, &d_efix, S));
+    TRY(dalloc(h, &d_sow, S));
+    TRY(dalloc(h, &d_wos, S));
+    TRY(dalloc(h, &d_mc, (size_t)S * 6));
+    TRY(dalloc(h, &d_exc, (size_t)S * 8));
+    TRY(dalloc(h, &P.hN, (size_t)S * (grid->nmax + 1)));
+    TRY(dalloc(h, &P.omega, S));
+    TRY(dalloc(h, &P.moments, (size_t)S * 4));
+    TRY(dalloc(h, &P.hNE, (size_t)(grid->nmax + 1) * grid->n_e_bins));
+    TRY(dalloc(h, &P.e_out, S));
+    TRY(dalloc(h, &P.pair_counts, 2));
+    TRY(dalloc(h, &h->d_error, 1));
+    TRY(dalloc(h, &h->d_fix, S));
+    std::vector<int> ident(S);
+    for (int s = 0; s < S; ++s) ident[s] = s;
+    TRY(upload(h, d_sow, ident.data(), S));
+    TRY(upload(h, d_wos, ident.data(), S));
+    P.pos = d_pos;
+    P.n = d_n;
+    P.efix = d_efix;
+    P.state_of_walker = d_sow;
+    P.move_counts = d_mc;
+    P.error = h->d_error;
+    P.trace = nullptr;
+    h->X = ExchangeParams{grid->L, grid->M, P.key0, P.key1, d_beta, d_bmu, d_lnbeta, d_n, d_efix, d_sow, d_wos, d_exc};
+    TRY(cuda_fail(h, cudaStreamSynchronize(h->stream)));
+#undef TRY
+    *out = h;
+    return REGC_OK;
+}
+
+regc_status regc_sweep(regc_handle* h, int n_sweeps) {
+    if (!h || n_sweeps < 0) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (n_sweeps == 0) return REGC_OK;
+    SweepParams P = h->P;
+    P.t0 = h->t;
+    P.n_sweeps = n_sweeps;
+    P.trace = nullptr;
+    const regc_status st = cuda_fail(h, launch_sweep(P, h->wpc, h->stream));
+    if (st == REGC_OK) h->t += (uint32_t)n_sweeps;
+    return st;
+}
+
+regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* trace) {
+    if (!h || n_sweeps < 0 || (n_sweeps > 0 && !trace)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (n_sweeps == 0) return REGC_OK;
+    const size_t n = (size_t)h->S * n_sweeps * h->mps;
+    regc_move_record* d_trace = nullptr;
+    regc_status st = cuda_fail(h, cudaMallocAsync(&d_trace, n * sizeof(regc_move_record), h->stream));
+    if (st != REGC_OK) return st;
+    SweepParams P = h->P;
+    P.t0 = h->t;
+    P.n_sweeps = n_sweeps;
+    P.trace = d_trace;
+    st = cuda_fail(h, launch_sweep(P, h->wpc, h->stream));
+    if (st == REGC_OK) {
+        h->t += (uint32_t)n_sweeps;
+        st = cuda_fail(h, cudaMemcpyAsync(trace, d_trace, n * sizeof(regc_move_record), cudaMemcpyDeviceToHost,
+                                          h->stream));
+    }
+    cudaFreeAsync(d_trace, h->stream);
+    const regc_status st2 = sync_check(h);
+    return st != REGC_OK ? st : st2;
+}
+
+regc_status regc_exchange(regc_handle* h) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const regc_status st = cuda_fail(h, launch_exchange(h->X, h->e, h->stream));
+    if (st == REGC_OK) h->e += 1;
+    return st;
+}
+
+regc_status regc_histograms(regc_handle* h, int64_t* hN, int64_t* hNE, int64_t* omega, double* moments,
+                            int64_t* e_out) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const size_t S = h->S;
+    cudaError_t e = cudaSuccess;
+    auto get = [&](void* dst, const void* src, size_t bytes) {
+        if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+    };
+    get(hN, h->P.hN, S * (h->nmax + 1) * 8);
+    get(hNE, h->P.hNE, (size_t)(h->nmax + 1) * h->n_e_bins * 8);
+    get(omega, h->P.omega, S * 8);
+    get(moments, h->P.moments, S * 4 * 8);
+    get(e_out, h->P.e_out, S * 8);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_reset_histograms(regc_handle* h) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const size_t S = h->S;
+    cudaError_t e = cudaSuccess;
+    auto zero = [&](void* p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, h->stream);
+    };
+    zero(h->P.hN, S * (h->nmax + 1) * 8);
+    zero(h->P.hNE, (size_t)(h->nmax + 1) * h->n_e_bins * 8);
+    zero(h->P.omega, S * 8);
+    zero(h->P.moments, S * 4 * 8);
+    zero(h->P.e_out, S * 8);
+    zero(h->P.move_counts, S * 6 * 8);
+    zero(h->X.ex_counts, S * 8 * 8);
+    zero(h->P.pair_counts, 2 * 8);
+    return cuda_fail(h, e);
+}
+
+regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n, const int32_t* sow) {
+    if (!h || !pos || !n) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const int S = h->S, nmax = h->nmax;
+    std::vector<float4> p4((size_t)S * nmax, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int w = 0; w < S; ++w) {
+        if (n[w] < 0 || n[w] > nmax) return REGC_EINVAL;
+        for (int i = 0; i < n[w]; ++i) {
+            const float* r = pos + ((size_t)w * nmax + i) * 3;
+            const bool okx = r[0] >= 0.0f && r[0] < h->Lx, oky = r[1] >= 0.0f && r[1] < h->Ly;
+            const bool okz = h->periodic_z ? (r[2] >= 0.0f && r[2] < h->Lz) : (r[2] >= h->z_lo && r[2] <= h->z_hi);
+            if (!(okx && oky && okz)) return REGC_EINVAL;
+            p4[(size_t)w * nmax + i] = make_float4(r[0], r[1], r[2], 0.0f);
+        }
+    }
+    std::vector<int> wos(S, -1);
+    if (sow) {
+        for (int w = 0; w < S; ++w) {
+            if (sow[w] < 0 || sow[w] >= S || wos[sow[w]] >= 0) return REGC_EINVAL;
+            wos[sow[w]] = w;
+        }
+    }
+    regc_status st = upload(h, h->P.pos, p4.data(), p4.size());
+    if (st == REGC_OK) st = upload(h, h->P.n, n, S);
+    if (st == REGC_OK && sow) {
+        st = upload(h, h->X.state_of_walker, sow, S);
+        if (st == REGC_OK) st = upload(h, h->X.walker_of_state, wos.data(), S);
+    }
+    if (st != REGC_OK) return st;
+    st = cuda_fail(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
+    if (st == REGC_OK) st = cuda_fail(h, launch_energy(h->P, h->P.efix, 1, h->stream));
+    if (st != REGC_OK) return st;
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (err & ERR_OVERLAP) {
+        // leave a consistent state behind: no walker holds particles
+        cudaMemsetAsync(h->P.n, 0, S * sizeof(int), h->stream);
+        cudaMemsetAsync(h->P.efix, 0, S * sizeof(long long), h->stream);
+        cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
+        cudaStreamSynchronize(h->stream);
+        return REGC_EINVAL;
+    }
+    return REGC_OK;
+}
+
+regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* energy, int32_t* sow) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const int S = h->S, nmax = h->nmax;
+    std::vector<float4> p4;
+    std::vector<long long> ef;
+    cudaError_t e = cudaSuccess;
+    if (pos) {
+        p4.resize((size_t)S * nmax);
+        e = cudaMemcpyAsync(p4.data(), h->P.pos, p4.size() * sizeof(float4), cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, h->P.n, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (energy && e == cudaSuccess) {
+        ef.resize(S);
+        e = cudaMemcpyAsync(ef.data(), h->P.efix, S * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (sow && e == cudaSuccess)
+        e = cudaMemcpyAsync(sow, h->X.state_of_walker, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    const regc_status st = sync_check(h);
+    if (st != REGC_OK) return st;
+    if (pos)
+        for (size_t i = 0; i < p4.size(); ++i) {
+            pos[3 * i] = p4[i].x;
+            pos[3 * i + 1] = p4[i].y;
+            pos[3 * i + 2] = p4[i].z;
+        }
+    if (energy)
+        for (int w = 0; w < S; ++w) energy[w] = (double)ef[w] * kFixUnit;
+    return REGC_OK;
+}
+
+regc_status regc_check_energy(regc_handle* h, double* max_drift) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    regc_status st = cuda_fail(h, launch_energy(h->P, h->d_fix, 0, h->stream));
+    if (st != REGC_OK) return st;
+    std::vector<long long> a(h->S), b(h->S);
+    cudaError_t e = cudaMemcpyAsync(a.data(), h->d_fix, h->S * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.data(), h->P.efix, h->S * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    st = sync_check(h);
+    if (st != REGC_OK) return st;
+    double d = 0.0;
+    for (int w = 0; w < h->S; ++w) d = std::max(d, fabs((double)(a[w] - b[w]) * kFixUnit));
+    if (max_drift) *max_drift = d;
+    return REGC_OK;
+}
+
+regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, int64_t* pairs) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    cudaError_t e = cudaSuccess;
+    if (moves) e = cudaMemcpyAsync(moves, h->P.move_counts, (size_t)h->S * 6 * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (exchanges && e == cudaSuccess)
+        e = cudaMemcpyAsync(exchanges, h->X.ex_counts, (size_t)h->S * 8 * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (pairs && e == cudaSuccess)
+        e = cudaMemcpyAsync(pairs, h->P.pair_counts, 2 * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- MBAR
+
+namespace {
+
+struct MbarBuffers {
+    std::vector<void*> ptrs;
+    cudaStream_t s;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        if (err == cudaSuccess) err = cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(T), s);
+        if (err == cudaSuccess) ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~MbarBuffers() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
+    }
+};
+
+regc_status status_of(cudaError_t e) {
+    return e == cudaSuccess ? REGC_OK : (e == cudaErrorMemoryAllocation ? REGC_ENOMEM : REGC_ECUDA);
+}
+
+// Solve over bins already on the device, then answer Q host queries.
+cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double tol, int max_iter, int* iters,
+                            double* f_host, double* D_host, int Q, const double* kT_q, const double* mu_q,
+                            int nmax, double* N_mean, double* pN, double* f_q) {
+    cudaStream_t s = buf.s;
+    m.f = buf.get<double>(m.S);
+    m.f_new = buf.get<double>(m.S);
+    m.D = buf.get<double>(m.B);
+    m.delta = buf.get<double>(1);
+    m.state = buf.get<int>(2);
+    if (buf.err != cudaSuccess) return buf.err;
+    cudaError_t e = mbar_solve_dev(m, tol, max_iter, iters, s);
+    if (e != cudaSuccess) return e;
+    if (f_host) e = cudaMemcpyAsync(f_host, m.f, m.S * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && D_host) e = cudaMemcpyAsync(D_host, m.D, m.B * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if (Q > 0) {
+        double* d_kq = buf.get<double>(Q);
+        double* d_mq = buf.get<double>(Q);
+        double* a_q = buf.get<double>(Q);
+        double* c_q = buf.get<double>(Q);
+        double* d_nm = buf.get<double>(Q);
+        double* d_pn = buf.get<double>((size_t)Q * (nmax + 1));
+        double* d_fq = buf.get<double>(Q);
+        if (buf.err != cudaSuccess) return buf.err;
+        e = cudaMemcpyAsync(d_kq, kT_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_mq, mu_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = mbar_prep_states(Q, d_kq, d_mq, lambda0, nullptr, nullptr, a_q, c_q, nullptr, s);
+        if (e == cudaSuccess) e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
+        if (e == cudaSuccess && N_mean) e = cudaMemcpyAsync(N_mean, d_nm, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && pN)
+            e = cudaMemcpyAsync(pN, d_pn, (size_t)Q * (nmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && f_q) e = cudaMemcpyAsync(f_q, d_fq, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const double* mu_q, double tol, int max_iter,
+                          double* N_mean, double* pN, double* f_states, int* iters) {
+    if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;
+    for (int q = 0; q < nq; ++q)
+        if (!(kT_q[q] > 0.0) || !std::isfinite(mu_q[q])) return REGC_EINVAL;
+    regc_status st = sync_check(h);
+    if (st != REGC_OK) return st;
+    MbarBuffers buf;
+    buf.s = h->stream;
+    const long long n = (long long)(h->nmax + 1) * h->n_e_bins;
+    int* scratch = buf.get<int>(compact_scratch_ints(n));
+    int* d_count = buf.get<int>(1);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    cudaError_t e = compact_count_dev(h->P.hNE, n, scratch, d_count, h->stream);
+    int B = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&B, d_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return status_of(e);
+    if (B == 0) return REGC_EINVAL;   // nothing observed yet
+    MbarDev m{};
+    m.S = h->S;
+    m.B = B;
+    int* N_b = buf.get<int>(B);
+    double* E_b = buf.get<double>(B);
+    double* lnH = buf.get<double>(B);
+    double* a = buf.get<double>(h->S);
+    double* c = buf.get<double>(h->S);
+    double* lnom = buf.get<double>(h->S);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    e = compact_write_dev(h->P.hNE, n, h->n_e_bins, h->e_lo, h->e_bin, scratch, N_b, E_b, lnH, h->stream);
+    if (e == cudaSuccess)
+        e = mbar_prep_states(h->S, h->d_kT_state, h->d_mu_state, h->lambda0, nullptr, h->P.omega, a, c, lnom, h->stream);
+    if (e != cudaSuccess) return status_of(e);
+    m.a = a;
+    m.c = c;
+    m.lnom = lnom;
+    m.N_b = N_b;
+    m.E_b = E_b;
+    m.lnH = lnH;
+    e = solve_and_query(buf, m, h->lambda0, tol, max_iter, iters, f_states, nullptr, nq, kT_q, mu_q, h->nmax, N_mean,
+                        pN, nullptr);
+    return status_of(e);
+}
+
+regc_status regc_mbar_solve(int S, const double* kT, const double* mu, double lambda0, const double* omega, int B,
+                            const int32_t* N_b, const double* E_b, const double* H_b, double tol, int max_iter,
+                            double* f, double* D, int* iters, void* cuda_stream) {
+    if (S < 1 || B < 1 || !kT || !mu || !omega || !N_b || !E_b || !H_b || !(tol > 0.0) || max_iter < 1 ||
+        !(lambda0 > 0.0))
+        return REGC_EINVAL;
+    for (int s = 0; s < S; ++s)
+        if (!(kT[s] > 0.0) || !std::isfinite(mu[s]) || !(omega[s] >= 0.0)) return REGC_EINVAL;
+    for (int b = 0; b < B; ++b)
+        if (!(H_b[b] > 0.0) || N_b[b] < 0 || !std::isfinite(E_b[b])) return REGC_EINVAL;
+    MbarBuffers buf;
+    buf.s = static_cast<cudaStream_t>(cuda_stream);
+    double* d_kT = buf.get<double>(S);
+    double* d_mu = buf.get<double>(S);
+    double* d_om = buf.get<double>(S);
+    double* a = buf.get<double>(S);
+    double* c = buf.get<double>(S);
+    double* lnom = buf.get<double>(S);
+    int* d_N = buf.get<int>(B);
+    double* d_E = buf.get<double>(B);
+    double* d_H = buf.get<double>(B);
+    double* lnH = buf.get<double>(B);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    cudaError_t e = cudaMemcpyAsync(d_kT, kT, S * sizeof(double), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mu, mu, S * sizeof(double), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_om, omega, S * sizeof(double), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_N, N_b, B * sizeof(int), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_E, E_b, B * sizeof(double), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_H, H_b, B * sizeof(double), cudaMemcpyHostToDevice, buf.s);
+    if (e == cudaSuccess) e = mbar_prep_states(S, d_kT, d_mu, lambda0, d_om, nullptr, a, c, lnom, buf.s);
+    if (e == cudaSuccess) e = mbar_prep_bins(B, d_H, lnH, buf.s);
+    if (e != cudaSuccess) return status_of(e);
+    MbarDev m{};
+    m.S = S;
+    m.B = B;
+    m.a = a;
+    m.c = c;
+    m.lnom = lnom;
+    m.N_b = d_N;
+    m.E_b = d_E;
+    m.lnH = lnH;
+    e = solve_and_query(buf, m, lambda0, tol, max_iter, iters, f, D, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr);
+    return status_of(e);
+}
+
+regc_status regc_mbar_query(int Q, const double* kT_q, const double* mu_q, double lambda0, int B,
+                            const int32_t* N_b, const double* E_b, const double* H_b, const double* D, int nmax,
+                            double* N_mean, double* pN, double* f_q, void* cuda_stream) {
+    if (Q < 1 || B < 1 || !kT_q || !mu_q || !N_b || !E_b || !H_b || !D || nmax < 0 || !(lambda0 > 0.0))
+        return REGC_EINVAL;
+    for (int q = 0; q < Q; ++q)
+        if (!(kT_q[q] > 0.0) || !std::isfinite(mu_q[q])) return REGC_EINVAL;
+    for (int b = 0; b < B; ++b)
+        if (!(H_b[b] > 0.0) || N_b[b] < 0 || !std::isfinite(E_b[b]) || !std::isfinite(D[b])) return REGC_EINVAL;
+    MbarBuffers buf;
+    buf.s = static_cast<cudaStream_t>(cuda_stream);
+    int* d_N = buf.get<int>(B);
+    double* d_E = buf.get<double>(B);
+    double* d_H = buf.get<double>(B);
+    double* lnH = buf.get<double>(B);
+    double* d_D = buf.get<double>(B);
+    double* d_kq = buf.get<double>(Q);
+    double* d_mq = buf.get<double>(Q);
+    double* a_q = buf.get<double>(Q);
+    double* c_q = buf.get<double>(Q);
+    double* d_nm = buf.get<double>(Q);
+    double* d_pn = buf.get<double>((size_t)Q * (nmax + 1));
+    double* d_fq = buf.get<double>(Q);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    cudaStream_t s = buf.s;
+    cudaError_t e = cudaMemcpyAsync(d_N, N_b, B * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_E, E_b, B * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_H, H_b, B * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_D, D, B * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_kq, kT_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mq, mu_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = mbar_prep_bins(B, d_H, lnH, s);
+    if (e == cudaSuccess) e = mbar_prep_states(Q, d_kq, d_mq, lambda0, nullptr, nullptr, a_q, c_q, nullptr, s);
+    if (e != cudaSuccess) return status_of(e);
+    MbarDev m{};
+    m.S = 0;
+    m.B = B;
+    m.N_b = d_N;
+    m.E_b = d_E;
+    m.lnH = lnH;
+    m.D = d_D;
+    e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
+    if (e == cudaSuccess && N_mean) e = cudaMemcpyAsync(N_mean, d_nm, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && pN)
+        e = cudaMemcpyAsync(pN, d_pn, (size_t)Q * (nmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && f_q) e = cudaMemcpyAsync(f_q, d_fq, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return status_of(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// regc_internal.cuh -- device-side building blocks of the REGC library (sm_103a).
+//
+// Shared by the kernels of this library only.  Nothing here is visible through
+// the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/regc.h"
+
+namespace regc {
+
+// Error bits of the per-handle device error word.
+enum : int {
+    ERR_CAPACITY = 1,   // a cell of a walker's cell list was full
+    ERR_OVERLAP = 2,    // two particles closer than the hard-core guard radius
+    ERR_TIMEOUT = 4,    // a bounded wait on an mbarrier gave up
+    ERR_NUMERIC = 8,    // a non-finite energy
+};
+
+// Energies are accumulated as 64-bit fixed-point integers in units of 2^-32
+// eps.  Every pair term is a binary32 value phi rounded once to that grid, so a
+// sum does not depend on the order in which pairs are visited and a running
+// total built from move energies equals the from-scratch sum exactly.
+constexpr float kFixScale = 4294967296.0f;          // 2^32
+constexpr double kFixUnit = 1.0 / 4294967296.0;     // 2^-32
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products (multipliers 0xD2511F53, 0xCD9E8D57) with the key
+// bumped by the Weyl constants 0x9E3779B9, 0xBB67AE85 between rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+#endif
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// 24-bit uniform in [0, 1), exact in binary32.
+__device__ __forceinline__ float u24(uint32_t a) { return (float)(a >> 8) * (1.0f / 16777216.0f); }
+
+// ------------------------------------------------------------ parameters
+
+struct PairTab {
+    float eps4;   // 4 eps_ij
+    float sig2;   // sigma_ij^2
+    float rhc2;   // hard-core guard radius^2 (0 when eps_ij = 0)
+};
+
+struct Geometry {
+    float Lx, Ly, Lz;      // periods
+    float iLx, iLy, iLz;   // 1 / period
+    int periodic_z;
+    float z_lo, z_hi;
+    float height;          // binary32(z_hi - z_lo)
+    float rc2;
+};
+
+struct CellGrid {
+    int ncx, ncy, ncz, ncell, cap;
+    float icx, icy, icz;   // cells per unit length
+};
+
+struct SurfaceTab {
+    int nsx, nsy;          // surface column grid
+    float isx, isy;        // columns per unit length
+    float z_reach;         // surface atoms are out of reach at z >= z_reach
+    const int* col_off;    // [nsx*nsy + 1]
+    const float4* atoms;   // x, y, z, type (as float)
+    const float4* all;     // every surface atom (energy recompute)
+    int n_all;
+};
+
+struct SweepParams {
+    Geometry g;
+    CellGrid cg;
+    SurfaceTab st;
+    PairTab gg;            // mobile-mobile
+    PairTab gs[4];         // mobile-surface by surface type
+    float max_disp;
+    unsigned long long th_disp;   // displacement if A0 < th_disp (0 .. 2^32)
+    int S, nmax, mps;
+    uint32_t key0, key1;
+    const double* beta;    // [S] per state
+    const double* c_ins;   // [S] ln V - 3 ln Lambda_s + beta_s mu_s
+    const double* c_del;   // [S] 3 ln Lambda_s - ln V - beta_s mu_s
+    const double* ln_tab;  // [nmax + 2] ln k
+    float4* pos;           // [S][nmax]
+    int* n;                // [S]
+    long long* efix;       // [S]
+    const int* state_of_walker;
+    unsigned long long* hN;       // [S][nmax+1]
+    unsigned long long* omega;    // [S]
+    double* moments;              // [S][4]
+    unsigned long long* hNE;      // [nmax+1][n_e_bins]
+    unsigned long long* e_out;    // [S]
+    double e_lo, e_bin;
+    int n_e_bins;
+    long long* move_counts;       // [S][6]
+    unsigned long long* pair_counts;  // [2]
+    int* error;
+    regc_move_record* trace;      // device [S][n_sweeps][mps] or null
+    uint32_t t0;
+    int n_sweeps;
+    int smem_per_walker;          // bytes
+};
+
+struct ExchangeParams {
+    int L, M;
+    uint32_t key0, key1;
+    const double* beta;    // [S]
+    const double* bmu;     // [S] beta_s mu_s
+    const double* lnbeta;  // [S]
+    const int* n;
+    const long long* efix;
+    int* state_of_walker;
+    int* walker_of_state;
+    long long* ex_counts;  // [S][8]
+};
+
+// ----------------------------------------------------------- pair energy
+// Fixed-point energy of one pair, phi(r) for r < rc, with the minimum image
+// along periodic axes.  Written with explicit round-to-nearest intrinsics so
+// that the value is the same wherever it is inlined and symmetric under
+// exchanging the two particles.
+__device__ __forceinline__ long long pair_fix(float qx, float qy, float qz, float4 p,
+                                              const Geometry& g, const PairTab& t,
+                                              int& n_in, int& overlap) {
+    float dx = __fsub_rn(qx, p.x);
+    float dy = __fsub_rn(qy, p.y);
+    float dz = __fsub_rn(qz, p.z);
+    dx = __fmaf_rn(-g.Lx, rintf(__fmul_rn(dx, g.iLx)), dx);
+    dy = __fmaf_rn(-g.Ly, rintf(__fmul_rn(dy, g.iLy)), dy);
+    if (g.periodic_z) dz = __fmaf_rn(-g.Lz, rintf(__fmul_rn(dz, g.iLz)), dz);
+    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+    long long v = 0;
+    if (r2 < g.rc2) {
+        const float s2 = __fdividef(t.sig2, r2);
+        const float s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
+        const float phi = __fmul_rn(t.eps4, __fmaf_rn(s6, s6, -s6));
+        v = __float2ll_rn(__fmul_rn(phi, kFixScale));
+        n_in += 1;
+        overlap |= (r2 < t.rhc2);
+    }
+    return v;
+}
+
+__device__ __forceinline__ const PairTab& surf_tab(const SweepParams& P, float type_f) {
+    const int t = (int)type_f;
+    return P.gs[t & 3];
+}
+
+// Warp-wide sum of a 64-bit integer.
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+    return __reduce_add_sync(0xffffffffu, (unsigned)v);
+}
+
+}  // namespace regc

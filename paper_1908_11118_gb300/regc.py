@@ -1,0 +1,208 @@
+"""Thin Python binding of the REGC C ABI (argument marshalling only).
+
+Every step of the sampler and of the reweighting runs in the CUDA library;
+this module converts numpy arrays and problem statements to the C structs of
+include/regc.h and back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import check
+
+MOVE_DTYPE = np.dtype([
+    ("type", np.int32), ("index", np.int32), ("accepted", np.int32), ("status", np.int32),
+    ("dE", np.float64), ("log_alpha", np.float64), ("ln_u", np.float64),
+    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("pad", np.int32),
+])
+
+
+def _p(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(int(stream.cuda_stream))   # torch.cuda.Stream
+
+
+class Regc:
+    """One REGC run: the walkers of an L x M (kT, mu) grid on one GPU.
+
+    ``problem`` is any object with the fields of a problem statement (potential
+    tables eps/sigma/rc/n_types, box Lx/Ly/Lz/periodic_z, region z_lo/z_hi,
+    surface surf_xyz/surf_type, grid kT/mu/lambda0, nmax, moves_per_sweep,
+    max_disp, p_disp, seed, E-histogram e_lo/e_bin/n_e_bins).  ``stream`` is a
+    torch.cuda.Stream, a raw cudaStream_t integer, or None (default stream)."""
+
+    def __init__(self, problem, stream=None):
+        L = _lib.lib()
+        self.p = problem
+        pot = _lib.Potential()
+        pot.n_types = int(problem.n_types)
+        for i in range(4):
+            for j in range(4):
+                pot.eps[i][j] = float(problem.eps[i][j])
+                pot.sigma[i][j] = float(problem.sigma[i][j])
+        pot.rc = float(problem.rc)
+        self._sxyz = np.ascontiguousarray(np.asarray(problem.surf_xyz, np.float32).reshape(-1, 3))
+        self._stype = np.ascontiguousarray(np.asarray(problem.surf_type, np.int32))
+        surf = _lib.Surface(len(self._stype), _p(self._sxyz, C.c_float), _p(self._stype, C.c_int32),
+                            float(problem.Lx), float(problem.Ly), float(problem.Lz),
+                            int(problem.periodic_z), float(problem.z_lo), float(problem.z_hi))
+        self._kT = np.ascontiguousarray(problem.kT, np.float64)
+        self._mu = np.ascontiguousarray(problem.mu, np.float64)
+        grid = _lib.GridSpec(len(self._kT), len(self._mu), _p(self._kT, C.c_double),
+                             _p(self._mu, C.c_double), float(problem.lambda0), int(problem.nmax),
+                             int(problem.moves_per_sweep), float(problem.max_disp),
+                             float(problem.p_disp), float(problem.e_lo), float(problem.e_bin),
+                             int(problem.n_e_bins))
+        h = C.c_void_p()
+        check(L.regc_init_grid(C.byref(pot), C.byref(surf), C.byref(grid), C.c_uint64(int(problem.seed)),
+                               _stream_handle(stream), C.byref(h)), "regc_init_grid")
+        self._h = h
+        self.S = len(self._kT) * len(self._mu)
+        self.nmax = int(problem.nmax)
+        self.mps = int(problem.moves_per_sweep)
+        self.n_e_bins = int(problem.n_e_bins)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().regc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the sampler
+    def sweep(self, n_sweeps: int):
+        check(_lib.lib().regc_sweep(self._h, int(n_sweeps)), "regc_sweep")
+
+    def sweep_traced(self, n_sweeps: int) -> np.ndarray:
+        tr = np.zeros((self.S, n_sweeps, self.mps), MOVE_DTYPE)
+        check(_lib.lib().regc_sweep_traced(self._h, int(n_sweeps), tr.ctypes.data), "regc_sweep_traced")
+        return tr
+
+    def exchange(self):
+        check(_lib.lib().regc_exchange(self._h), "regc_exchange")
+
+    def run(self, n_sweeps: int, exchange_every: int = 10):
+        """Blocks of exchange_every sweeps, each followed by one exchange attempt."""
+        done = 0
+        while done < n_sweeps:
+            k = min(exchange_every, n_sweeps - done) if exchange_every > 0 else n_sweeps - done
+            self.sweep(k)
+            done += k
+            if exchange_every > 0 and k == exchange_every:
+                self.exchange()
+
+    # -- state
+    def set_walkers(self, pos, n, state_of_walker=None):
+        pos = np.ascontiguousarray(np.asarray(pos, np.float32).reshape(self.S, self.nmax, 3))
+        n = np.ascontiguousarray(np.asarray(n, np.int32))
+        sow = None if state_of_walker is None else np.ascontiguousarray(np.asarray(state_of_walker, np.int32))
+        check(_lib.lib().regc_set_walkers(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(sow, C.c_int32)),
+              "regc_set_walkers")
+
+    def get_walkers(self):
+        pos = np.zeros((self.S, self.nmax, 3), np.float32)
+        n = np.zeros(self.S, np.int32)
+        e = np.zeros(self.S)
+        sow = np.zeros(self.S, np.int32)
+        check(_lib.lib().regc_get_walkers(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(e, C.c_double),
+                                          _p(sow, C.c_int32)), "regc_get_walkers")
+        return pos, n, e, sow
+
+    def check_energy(self) -> float:
+        d = C.c_double(0)
+        check(_lib.lib().regc_check_energy(self._h, C.byref(d)), "regc_check_energy")
+        return d.value
+
+    def counters(self):
+        mv = np.zeros((self.S, 3, 2), np.int64)
+        ex = np.zeros((self.S, 4, 2), np.int64)
+        pr = np.zeros(2, np.int64)
+        check(_lib.lib().regc_counters(self._h, _p(mv, C.c_int64), _p(ex, C.c_int64), _p(pr, C.c_int64)),
+              "regc_counters")
+        return mv, ex, pr
+
+    def histograms(self):
+        hN = np.zeros((self.S, self.nmax + 1), np.int64)
+        hNE = np.zeros((self.nmax + 1, self.n_e_bins), np.int64)
+        om = np.zeros(self.S, np.int64)
+        mo = np.zeros((self.S, 4))
+        eo = np.zeros(self.S, np.int64)
+        check(_lib.lib().regc_histograms(self._h, _p(hN, C.c_int64), _p(hNE, C.c_int64), _p(om, C.c_int64),
+                                         _p(mo, C.c_double), _p(eo, C.c_int64)), "regc_histograms")
+        return {"hN": hN, "hNE": hNE, "omega": om, "moments": mo, "e_out": eo}
+
+    def reset_histograms(self):
+        check(_lib.lib().regc_reset_histograms(self._h), "regc_reset_histograms")
+
+    def reweight(self, kT_q, mu_q, tol: float = 1e-10, max_iter: int = 100000):
+        kq = np.ascontiguousarray(kT_q, np.float64)
+        mq = np.ascontiguousarray(mu_q, np.float64)
+        Q = len(kq)
+        nm = np.zeros(Q)
+        pN = np.zeros((Q, self.nmax + 1))
+        f = np.zeros(self.S)
+        it = C.c_int32(0)
+        check(_lib.lib().regc_reweight(self._h, Q, _p(kq, C.c_double), _p(mq, C.c_double), tol, max_iter,
+                                       _p(nm, C.c_double), _p(pN, C.c_double), _p(f, C.c_double),
+                                       C.byref(it)), "regc_reweight")
+        return nm, pN, f, it.value
+
+
+def mbar_solve(kT, mu, lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter=100000, stream=None):
+    """Device MBAR solve over pooled bins; returns (f [S], D [B], iterations)."""
+    kT = np.ascontiguousarray(kT, np.float64)
+    mu = np.ascontiguousarray(mu, np.float64)
+    om = np.ascontiguousarray(omega, np.float64)
+    N_b = np.ascontiguousarray(N_b, np.int32)
+    E_b = np.ascontiguousarray(E_b, np.float64)
+    H_b = np.ascontiguousarray(H_b, np.float64)
+    S, B = len(kT), len(N_b)
+    f = np.zeros(S)
+    D = np.zeros(B)
+    it = C.c_int32(0)
+    check(_lib.lib().regc_mbar_solve(S, _p(kT, C.c_double), _p(mu, C.c_double), float(lambda0),
+                                     _p(om, C.c_double), B, _p(N_b, C.c_int32), _p(E_b, C.c_double),
+                                     _p(H_b, C.c_double), tol, max_iter, _p(f, C.c_double),
+                                     _p(D, C.c_double), C.byref(it), _stream_handle(stream)),
+          "regc_mbar_solve")
+    return f, D, it.value
+
+
+def mbar_query(kT_q, mu_q, lambda0, N_b, E_b, H_b, D, nmax, stream=None):
+    """Device MBAR reweighting to query states; returns (<N> [Q], p_N [Q, nmax+1], f_q [Q])."""
+    kq = np.ascontiguousarray(kT_q, np.float64)
+    mq = np.ascontiguousarray(mu_q, np.float64)
+    N_b = np.ascontiguousarray(N_b, np.int32)
+    E_b = np.ascontiguousarray(E_b, np.float64)
+    H_b = np.ascontiguousarray(H_b, np.float64)
+    D = np.ascontiguousarray(D, np.float64)
+    Q = len(kq)
+    nm = np.zeros(Q)
+    pN = np.zeros((Q, nmax + 1))
+    fq = np.zeros(Q)
+    check(_lib.lib().regc_mbar_query(Q, _p(kq, C.c_double), _p(mq, C.c_double), float(lambda0), len(N_b),
+                                     _p(N_b, C.c_int32), _p(E_b, C.c_double), _p(H_b, C.c_double),
+                                     _p(D, C.c_double), int(nmax), _p(nm, C.c_double), _p(pN, C.c_double),
+                                     _p(fq, C.c_double), _stream_handle(stream)), "regc_mbar_query")
+    return nm, pN, fq
