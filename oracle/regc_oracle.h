@@ -72,7 +72,7 @@ typedef struct {
     double  dE;         /* energy change of the move (0 unless status 0) */
     double  log_alpha;  /* log of the acceptance ratio (status 0 only) */
     double  ln_u;       /* log of the acceptance uniform */
-    double  sum_abs;    /* sum of |phi| over every pair entering dE */
+    double  sum_abs;    /* sum of 4 eps [(s/r)^12 + (s/r)^6] over pairs entering dE */
     double  band;       /* sum of |phi(rc)| over pairs with r^2 within 4e-6 rc^2 of rc^2 */
     int32_t n_pairs;    /* pairs with r < rc entering dE */
     int32_t pad;

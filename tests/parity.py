@@ -8,8 +8,11 @@ so a decision may differ only when the oracle's ln u lies within the energy
 tolerance of its log acceptance ratio (a near-tie); after such a divergence
 the two chains are no longer comparable for that walker.
 
-Energy tolerance (per move): |dE_gpu - dE_oracle| <= 1e-5 max(|dE|, sum |phi|)
-plus the step of phi at rc for every pair within 4e-6 rc^2 of the cutoff.
+Energy tolerance (per move): |dE_gpu - dE_oracle| <= 1e-5 max(|dE|, T), where
+T = sum over the pairs entering dE of 4 eps [(sigma/r)^12 + (sigma/r)^6] (the
+two terms of the LJ pair energy cancel near r = sigma, so |phi| alone would
+understate the binary32 rounding), plus the step of phi at rc for every pair
+within 4e-6 rc^2 of the cutoff.
 """
 import numpy as np
 
