@@ -63,6 +63,15 @@ class Problem:
     n_e_bins: int
     name: str = "custom"
 
+    def __post_init__(self):
+        # the C ABI carries these as binary32: round them here, once, so that
+        # both implementations start from the same numbers
+        for k in ("rc", "Lx", "Ly", "Lz", "z_lo", "z_hi", "max_disp"):
+            setattr(self, k, float(f32(getattr(self, k))))
+        self.eps = f32(self.eps)
+        self.sigma = f32(self.sigma)
+        self.surf_xyz = f32(np.asarray(self.surf_xyz, dtype=np.float64).reshape(-1, 3))
+
     @property
     def L(self) -> int:
         return int(len(self.kT))
