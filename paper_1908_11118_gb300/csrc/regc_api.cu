@@ -246,17 +246,43 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         }
     }
     st.z_reach = relevant.empty() ? -INFINITY : (float)(zmax + rc * 1.00001 + 1e-4);
+    // Each column lists every periodic image of every relevant atom that comes
+    // within reach of the column.  An image at x_a - Lx is stored shifted (exact
+    // when x_a >= Lx/2, and the image is out of reach otherwise); an image at
+    // x_a + Lx is stored unshifted with a flag that shifts the query by -Lx
+    // instead (exact for every query that can reach it).  Likewise for y and,
+    // in a periodic box, z.
     std::vector<int> col_off(st.nsx * st.nsy + 1, 0);
     std::vector<float4> col_atoms;
+    const int nzi = periodic_z ? 1 : 0;
     for (int iy = 0; iy < st.nsy; ++iy)
         for (int ix = 0; ix < st.nsx; ++ix) {
-            const double cx = (ix + 0.5) * wx, cy = (iy + 0.5) * wy;
+            const double x0 = ix * wx, x1 = (ix + 1) * wx, y0 = iy * wy, y1 = (iy + 1) * wy;
             for (int a : relevant) {
-                double dx = (double)surf->xyz[3 * a] - cx, dy = (double)surf->xyz[3 * a + 1] - cy;
-                dx -= surf->Lx * nearbyint(dx / surf->Lx);
-                dy -= surf->Ly * nearbyint(dy / surf->Ly);
-                const double ex = std::max(0.0, fabs(dx) - 0.5 * wx), ey = std::max(0.0, fabs(dy) - 0.5 * wy);
-                if (ex * ex + ey * ey < reach * reach) col_atoms.push_back(all[a]);
+                const float* r = surf->xyz + 3 * a;
+                for (int sx = -1; sx <= 1; ++sx)
+                    for (int sy = -1; sy <= 1; ++sy)
+                        for (int sz = -nzi; sz <= nzi; ++sz) {
+                            const double ax = (double)r[0] + sx * (double)surf->Lx;
+                            const double ay = (double)r[1] + sy * (double)surf->Ly;
+                            const double ex = std::max(0.0, std::max(x0 - ax, ax - x1));
+                            const double ey = std::max(0.0, std::max(y0 - ay, ay - y1));
+                            if (ex * ex + ey * ey >= reach * reach) continue;
+                            unsigned bits = (unsigned)surf->type[a];
+                            float bx = r[0], by = r[1], bz = r[2];
+                            if (sx < 0) bx = r[0] - surf->Lx;
+                            if (sx > 0) bits |= 4u;
+                            if (sy < 0) by = r[1] - surf->Ly;
+                            if (sy > 0) bits |= 8u;
+                            if (sz < 0) bz = r[2] - surf->Lz;
+                            if (sz > 0) bits |= 16u;
+                            float4 v;
+                            v.x = bx;
+                            v.y = by;
+                            v.z = bz;
+                            memcpy(&v.w, &bits, sizeof(float));
+                            col_atoms.push_back(v);
+                        }
             }
             col_off[iy * st.nsx + ix + 1] = (int)col_atoms.size();
         }
@@ -271,9 +297,9 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         P.gs[t] = PairTab{4.0f * pot->eps[0][tt], pot->sigma[0][tt] * pot->sigma[0][tt],
                           hard_core_r2(pot->eps[0][tt], pot->sigma[0][tt], T)};
     }
-    P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 1.0f, (float)(1.0 / surf->Lx),
-                   (float)(1.0 / surf->Ly), periodic_z ? (float)(1.0 / surf->Lz) : 0.0f, periodic_z,
-                   surf->z_lo, surf->z_hi, surf->z_hi - surf->z_lo, (float)(rc * rc)};
+    P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 0.0f, 0.5f * surf->Lx, 0.5f * surf->Ly,
+                   periodic_z ? 0.5f * surf->Lz : 0.0f, periodic_z, surf->z_lo, surf->z_hi,
+                   surf->z_hi - surf->z_lo, (float)(rc * rc)};
     P.cg = cg;
     P.max_disp = grid->max_disp;
     P.th_disp = (unsigned long long)floor(grid->p_disp * 4294967296.0);

@@ -72,7 +72,7 @@ struct PairTab {
 
 struct Geometry {
     float Lx, Ly, Lz;      // periods
-    float iLx, iLy, iLz;   // 1 / period
+    float hLx, hLy, hLz;   // half periods
     int periodic_z;
     float z_lo, z_hi;
     float height;          // binary32(z_hi - z_lo)
@@ -89,8 +89,10 @@ struct SurfaceTab {
     float isx, isy;        // columns per unit length
     float z_reach;         // surface atoms are out of reach at z >= z_reach
     const int* col_off;    // [nsx*nsy + 1]
-    const float4* atoms;   // x, y, z, type (as float)
-    const float4* all;     // every surface atom (energy recompute)
+    const float4* atoms;   // images listed per column: x, y, z of the image
+                           // (shifted by -L where exact), w = bits: type (0-1),
+                           // query shifted by -Lx (2), -Ly (3), -Lz (4)
+    const float4* all;     // every surface atom, w = type (energy recompute)
     int n_all;
 };
 
@@ -142,19 +144,12 @@ struct ExchangeParams {
 };
 
 // ----------------------------------------------------------- pair energy
-// Fixed-point energy of one pair, phi(r) for r < rc, with the minimum image
-// along periodic axes.  Written with explicit round-to-nearest intrinsics so
-// that the value is the same wherever it is inlined and symmetric under
-// exchanging the two particles.
-__device__ __forceinline__ long long pair_fix(float qx, float qy, float qz, float4 p,
-                                              const Geometry& g, const PairTab& t,
-                                              int& n_in, int& overlap) {
-    float dx = __fsub_rn(qx, p.x);
-    float dy = __fsub_rn(qy, p.y);
-    float dz = __fsub_rn(qz, p.z);
-    dx = __fmaf_rn(-g.Lx, rintf(__fmul_rn(dx, g.iLx)), dx);
-    dy = __fmaf_rn(-g.Ly, rintf(__fmul_rn(dy, g.iLy)), dy);
-    if (g.periodic_z) dz = __fmaf_rn(-g.Lz, rintf(__fmul_rn(dz, g.iLz)), dz);
+// Fixed-point energy of one pair from its displacement (dx, dy, dz): phi(r)
+// for r < rc.  Written with explicit round-to-nearest intrinsics so that the
+// value is the same wherever it is inlined, and symmetric under exchanging
+// the two particles (dx -> -dx).
+__device__ __forceinline__ long long pair_fix_d(float dx, float dy, float dz, const Geometry& g,
+                                                const PairTab& t, int& n_in, int& overlap) {
     const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
     long long v = 0;
     if (r2 < g.rc2) {
@@ -168,9 +163,19 @@ __device__ __forceinline__ long long pair_fix(float qx, float qy, float qz, floa
     return v;
 }
 
-__device__ __forceinline__ const PairTab& surf_tab(const SweepParams& P, float type_f) {
-    const int t = (int)type_f;
-    return P.gs[t & 3];
+// Minimum-image displacement q - p along a periodic axis of period L, rounded
+// once: when the nearest image lies across the boundary, the shifted operand
+// (q - L when q > L/2, p - L when p > L/2) is exact (Sterbenz), so only the
+// final subtraction rounds.
+__device__ __forceinline__ float min_image_exact(float q, float p, float L, float hL) {
+    const float e = __fsub_rn(q, p);
+    if (e > hL) return __fsub_rn(__fsub_rn(q, L), p);
+    if (e < -hL) return __fsub_rn(q, __fsub_rn(p, L));
+    return e;
+}
+
+__device__ __forceinline__ const PairTab& surf_tab(const SweepParams& P, int type) {
+    return P.gs[type & 3];
 }
 
 // Warp-wide sum of a 64-bit integer.

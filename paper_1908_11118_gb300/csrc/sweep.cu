@@ -24,10 +24,20 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
+// A non-empty cell of the stencil of the moved particle: its first index in
+// the flattened candidate list and the periodic shifts of its image.  The
+// displacement to a partner p in this cell is (q - oA) - (p - oB) per axis;
+// oA, oB are 0 or the period, and each shifted operand is exact (Sterbenz),
+// so the displacement is rounded once.
+struct StEntry {
+    int cell, excl;
+    float oAx, oBx, oAy, oBy, oAz, oBz;
+};
+
 struct WalkerSmem {
     float4* pos;        // [nmax]  x, y, z, (cell << 16 | slot) as bits
     uint64_t* bar;      // mbarrier of the position copy
-    int2* stencil;      // [32]    non-empty stencil cells: (cell, first flat index)
+    StEntry* stencil;   // [32]
     uint16_t* cnt;      // [ncell]
     uint16_t* slots;    // [ncell][cap] particle indices
 };
@@ -41,8 +51,8 @@ __device__ inline WalkerSmem carve(char* base, const SweepParams& P) {
     off += align16(size_t(P.nmax) * 16);
     w.bar = reinterpret_cast<uint64_t*>(base + off);
     off += 16;
-    w.stencil = reinterpret_cast<int2*>(base + off);
-    off += 32 * sizeof(int2);
+    w.stencil = reinterpret_cast<StEntry*>(base + off);
+    off += 32 * sizeof(StEntry);
     w.cnt = reinterpret_cast<uint16_t*>(base + off);
     off += align16(size_t(P.cg.ncell) * 2);
     w.slots = reinterpret_cast<uint16_t*>(base + off);
@@ -107,36 +117,44 @@ __device__ __forceinline__ int cell_of(const SweepParams& P, float x, float y, f
 
 __device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Cell handled by this lane in the stencil of cell `cell` (-1 if none), and
-// the stencil size.  Periodic axes with fewer than three cells list each cell
-// once, so that no partner is counted twice.
-__device__ __forceinline__ int stencil_cell(const SweepParams& P, int cell, int lane, int& nst) {
+// Stencil entry handled by this lane for the cell `cell` of the moved
+// particle (cell = -1 if the lane has none) and the stencil size.  Periodic
+// axes always contribute three images (-1, 0, +1); with fewer than three
+// cells along an axis the same cell appears with different shifts, which
+// evaluates every periodic image of its particles (at most one of them can be
+// within rc, because every period is at least 2 rc).
+__device__ __forceinline__ StEntry stencil_entry(const SweepParams& P, int cell, int lane, int& nst) {
     const int ncx = P.cg.ncx, ncy = P.cg.ncy, ncz = P.cg.ncz;
     const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
-    const int nxs = ncx >= 3 ? 3 : ncx, nys = ncy >= 3 ? 3 : ncy;
-    int zfirst, nzs;
-    if (P.g.periodic_z) {
-        nzs = ncz >= 3 ? 3 : ncz;
-        zfirst = 0;
-    } else {
+    int zfirst = 0, nzs = 3;
+    if (!P.g.periodic_z) {
         zfirst = max(0, cz - 1);
         nzs = min(ncz - 1, cz + 1) - zfirst + 1;
     }
-    nst = nxs * nys * nzs;
-    if (lane >= nst) return -1;
-    const int lx = lane % nxs, ly = (lane / nxs) % nys, lz = lane / (nxs * nys);
-    const int ix = nxs == 3 ? wrap_idx(cx - 1 + lx, ncx) : lx;
-    const int iy = nys == 3 ? wrap_idx(cy - 1 + ly, ncy) : ly;
-    int iz;
-    if (P.g.periodic_z) iz = nzs == 3 ? wrap_idx(cz - 1 + lz, ncz) : lz;
-    else iz = zfirst + lz;
-    return (iz * ncy + iy) * ncx + ix;
+    nst = 9 * nzs;
+    StEntry e{-1, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (lane >= nst) return e;
+    const int lx = lane % 3, ly = (lane / 3) % 3, lz = lane / 9;
+    int ix = cx - 1 + lx, iy = cy - 1 + ly, iz;
+    if (ix < 0) { ix += ncx; e.oBx = P.g.Lx; }
+    else if (ix >= ncx) { ix -= ncx; e.oAx = P.g.Lx; }
+    if (iy < 0) { iy += ncy; e.oBy = P.g.Ly; }
+    else if (iy >= ncy) { iy -= ncy; e.oAy = P.g.Ly; }
+    if (P.g.periodic_z) {
+        iz = cz - 1 + lz;
+        if (iz < 0) { iz += ncz; e.oBz = P.g.Lz; }
+        else if (iz >= ncz) { iz -= ncz; e.oAz = P.g.Lz; }
+    } else {
+        iz = zfirst + lz;
+    }
+    e.cell = (iz * ncy + iy) * ncx + ix;
+    return e;
 }
 
 // Energy of NQ positions (sharing one stencil cell) against the mobile
 // particles of the stencil, skipping particle `skip`.  The candidate list is
-// the concatenation of the non-empty stencil cells; lane j of a batch takes
-// flat index base + j and finds its cell from the OR-reduced mask of cell
+// the concatenation of the non-empty stencil entries; lane j of a batch takes
+// flat index base + j and finds its entry from the OR-reduced mask of entry
 // starts inside the batch.
 template <int NQ>
 __device__ __forceinline__ void mobile_energy(const SweepParams& P, const WalkerSmem& W, int cell,
@@ -144,8 +162,8 @@ __device__ __forceinline__ void mobile_energy(const SweepParams& P, const Walker
                                               const float (&qz)[NQ], int skip, long long (&acc)[NQ],
                                               int& n_in, int& n_cand, int& overlap, int lane) {
     int nst;
-    const int sc = stencil_cell(P, cell, lane, nst);
-    const int c = sc >= 0 ? (int)W.cnt[sc] : 0;
+    StEntry se = stencil_entry(P, cell, lane, nst);
+    const int c = se.cell >= 0 ? (int)W.cnt[se.cell] : 0;
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -155,7 +173,10 @@ __device__ __forceinline__ void mobile_energy(const SweepParams& P, const Walker
     const int excl = incl - c;
     const int total = __shfl_sync(FULL, incl, 31);
     const unsigned nonempty = __ballot_sync(FULL, c > 0);
-    if (c > 0) W.stencil[__popc(nonempty & lanemask_lt(lane))] = make_int2(sc, excl);
+    if (c > 0) {
+        se.excl = excl;
+        W.stencil[__popc(nonempty & lanemask_lt(lane))] = se;
+    }
     __syncwarp();
     int started = 0;
     for (int base = 0; base < total; base += 32) {
@@ -165,13 +186,20 @@ __device__ __forceinline__ void mobile_energy(const SweepParams& P, const Walker
         const int j = base + lane;
         if (j < total) {
             const int r = started + __popc(starts & lanemask_le(lane)) - 1;
-            const int2 ce = W.stencil[r];
-            const int pj = W.slots[ce.x * P.cg.cap + (j - ce.y)];
+            const StEntry& e = W.stencil[r];
+            const int pj = W.slots[e.cell * P.cg.cap + (j - e.excl)];
             if (pj != skip) {
                 const float4 p = W.pos[pj];
+                const float bx = __fsub_rn(p.x, e.oBx), by = __fsub_rn(p.y, e.oBy);
+                const float bz = __fsub_rn(p.z, e.oBz);
                 n_cand += NQ;
 #pragma unroll
-                for (int k = 0; k < NQ; ++k) acc[k] += pair_fix(qx[k], qy[k], qz[k], p, P.g, P.gg, n_in, overlap);
+                for (int k = 0; k < NQ; ++k) {
+                    const float dx = __fsub_rn(__fsub_rn(qx[k], e.oAx), bx);
+                    const float dy = __fsub_rn(__fsub_rn(qy[k], e.oAy), by);
+                    const float dz = __fsub_rn(__fsub_rn(qz[k], e.oAz), bz);
+                    acc[k] += pair_fix_d(dx, dy, dz, P.g, P.gg, n_in, overlap);
+                }
             }
         }
         started += __popc(starts);
@@ -179,8 +207,11 @@ __device__ __forceinline__ void mobile_energy(const SweepParams& P, const Walker
     __syncwarp();
 }
 
-// Energy of NQ positions (sharing one surface column) against the frozen
-// surface atoms listed for that column.
+// Energy of NQ positions (sharing one surface column) against the images of
+// frozen surface atoms listed for that column.  Each listed image carries the
+// exact shifts of its displacement: the stored coordinate is already shifted
+// by -L where that is exact, and the flag bits ask for the query to be
+// shifted by -L instead.
 template <int NQ>
 __device__ __forceinline__ void surface_energy(const SweepParams& P, int col, const float (&qx)[NQ],
                                                const float (&qy)[NQ], const float (&qz)[NQ],
@@ -189,10 +220,18 @@ __device__ __forceinline__ void surface_energy(const SweepParams& P, int col, co
     const int beg = P.st.col_off[col], end = P.st.col_off[col + 1];
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
-        const PairTab& t = surf_tab(P, a.w);
+        const unsigned bits = __float_as_uint(a.w);
+        const PairTab& t = surf_tab(P, (int)(bits & 3u));
+        const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
+        const float sz = (bits & 16u) ? P.g.Lz : 0.f;
         n_cand += NQ;
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) acc[k] += pair_fix(qx[k], qy[k], qz[k], a, P.g, t, n_in, overlap);
+        for (int k = 0; k < NQ; ++k) {
+            const float dx = __fsub_rn(__fsub_rn(qx[k], sx), a.x);
+            const float dy = __fsub_rn(__fsub_rn(qy[k], sy), a.y);
+            const float dz = __fsub_rn(__fsub_rn(qz[k], sz), a.z);
+            acc[k] += pair_fix_d(dx, dy, dz, P.g, t, n_in, overlap);
+        }
     }
 }
 
@@ -554,8 +593,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     }
 }
 
+// Displacement q - p with the exact minimum image on periodic axes.
+__device__ __forceinline__ void disp_exact(const Geometry& g, float4 q, float4 p, float& dx, float& dy, float& dz) {
+    dx = min_image_exact(q.x, p.x, g.Lx, g.hLx);
+    dy = min_image_exact(q.y, p.y, g.Ly, g.hLy);
+    dz = g.periodic_z ? min_image_exact(q.z, p.z, g.Lz, g.hLz) : __fsub_rn(q.z, p.z);
+}
+
 // From-scratch energy of every walker: all pairs i < j and all particle-surface
-// pairs, with the same pair function as the sweep.
+// pairs, with the nearest periodic image.  Every pair within rc gets the same
+// rounded displacement, hence the same fixed-point term, as in the sweep.
 __global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ SweepParams P, long long* out,
                                                      int check_overlap) {
     const int lane = threadIdx.x & 31;
@@ -565,12 +612,17 @@ __global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ Swe
     const float4* pos = P.pos + size_t(w) * P.nmax;
     long long acc = 0;
     int n_in = 0, overlap = 0;
+    float dx, dy, dz;
     for (int i = 0; i < N; ++i) {
         const float4 pi = pos[i];
-        for (int j = i + 1 + lane; j < N; j += 32) acc += pair_fix(pi.x, pi.y, pi.z, pos[j], P.g, P.gg, n_in, overlap);
+        for (int j = i + 1 + lane; j < N; j += 32) {
+            disp_exact(P.g, pi, pos[j], dx, dy, dz);
+            acc += pair_fix_d(dx, dy, dz, P.g, P.gg, n_in, overlap);
+        }
         for (int a = lane; a < P.st.n_all; a += 32) {
             const float4 at = P.st.all[a];
-            acc += pair_fix(pi.x, pi.y, pi.z, at, P.g, surf_tab(P, at.w), n_in, overlap);
+            disp_exact(P.g, pi, at, dx, dy, dz);
+            acc += pair_fix_d(dx, dy, dz, P.g, surf_tab(P, (int)at.w), n_in, overlap);
         }
     }
     acc = warp_sum_ll(acc);
@@ -584,7 +636,7 @@ __global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ Swe
 }  // namespace
 
 size_t sweep_smem_per_walker(int nmax, int ncell, int cap) {
-    return align16(size_t(nmax) * 16) + 16 + 32 * sizeof(int2) + align16(size_t(ncell) * 2) +
+    return align16(size_t(nmax) * 16) + 16 + 32 * sizeof(StEntry) + align16(size_t(ncell) * 2) +
            align16(size_t(ncell) * cap * 2);
 }
 
