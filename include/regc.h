@@ -237,6 +237,34 @@ REGC_API regc_status regc_mbar_query(int Q, const double *kT_q, const double *mu
                             const double *D, int nmax, double *N_mean, double *pN,
                             double *f_q, void *cuda_stream);
 
+/* Largest problem regc_mbar_solve_static accepts. */
+#define REGC_MBAR_STATIC_MAX_STATES 4096
+#define REGC_MBAR_STATIC_MAX_BINS 262144
+
+/* MBAR solve that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- for example an application whose framework owns all device
+ * memory through its own pooled allocator, or a loop that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree may cause.
+ * Arguments, outputs and results are those of regc_mbar_solve (host buffers).
+ * The staged inputs and the work arrays live in one fixed scratch area of
+ * about 9.3 MiB compiled into the library, which every GPU that loads the
+ * library keeps reserved until the process exits.
+ *   - S > REGC_MBAR_STATIC_MAX_STATES or B > REGC_MBAR_STATIC_MAX_BINS:
+ *     REGC_EINVAL, nothing is run.
+ *   - The first call on a device, with that device current, looks up the
+ *     device address of the scratch area; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares that one scratch area, and it keeps the
+ *     last call's contents (the solver clears what it needs cleared).  Calls
+ *     that overlap on the GPU -- on different streams or from different host
+ *     threads -- race on it: serialise them. */
+REGC_API regc_status regc_mbar_solve_static(int S, const double *kT, const double *mu, double lambda0,
+                                            const double *omega, int B, const int32_t *N_b,
+                                            const double *E_b, const double *H_b, double tol,
+                                            int max_iter, double *f, double *D, int *iters,
+                                            void *cuda_stream);
+
 /* Human-readable name of a status. */
 REGC_API const char *regc_status_string(regc_status s);
 

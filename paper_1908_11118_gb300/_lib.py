@@ -72,6 +72,8 @@ SIGNATURES = {
     "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
     "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
                          C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
+    "regc_mbar_solve_static": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
+                                C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
     "regc_mbar_query": ([C.c_int, _dp, _dp, C.c_double, C.c_int, _ip, _dp, _dp, _dp, C.c_int,
                          _dp, _dp, _dp, C.c_void_p], C.c_int),
     "regc_status_string": ([C.c_int], C.c_char_p),

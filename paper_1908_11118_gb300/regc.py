@@ -206,3 +206,25 @@ def mbar_query(kT_q, mu_q, lambda0, N_b, E_b, H_b, D, nmax, stream=None):
                                      _p(D, C.c_double), int(nmax), _p(nm, C.c_double), _p(pN, C.c_double),
                                      _p(fq, C.c_double), _stream_handle(stream)), "regc_mbar_query")
     return nm, pN, fq
+
+
+def mbar_solve_static(kT, mu, lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter=100000, stream=None):
+    """As mbar_solve, through regc_mbar_solve_static: no device memory is
+    allocated; the library's fixed scratch area is used instead (at most
+    4096 states and 262144 bins; calls that overlap on the GPU race)."""
+    kT = np.ascontiguousarray(kT, np.float64)
+    mu = np.ascontiguousarray(mu, np.float64)
+    om = np.ascontiguousarray(omega, np.float64)
+    N_b = np.ascontiguousarray(N_b, np.int32)
+    E_b = np.ascontiguousarray(E_b, np.float64)
+    H_b = np.ascontiguousarray(H_b, np.float64)
+    S, B = len(kT), len(N_b)
+    f = np.zeros(S)
+    D = np.zeros(B)
+    it = C.c_int32(0)
+    check(_lib.lib().regc_mbar_solve_static(S, _p(kT, C.c_double), _p(mu, C.c_double), float(lambda0),
+                                            _p(om, C.c_double), B, _p(N_b, C.c_int32), _p(E_b, C.c_double),
+                                            _p(H_b, C.c_double), tol, max_iter, _p(f, C.c_double),
+                                            _p(D, C.c_double), C.byref(it), _stream_handle(stream)),
+          "regc_mbar_solve_static")
+    return f, D, it.value

@@ -1,0 +1,45 @@
+"""The MBAR solve that allocates no device memory (regc_mbar_solve_static).
+
+It serves callers that cannot let a library allocate device memory, for
+instance a framework that owns all device memory through its own pool, or a
+loop that cannot afford the device-wide synchronisation of cudaMalloc and
+cudaFree.  It runs the same solver as regc_mbar_solve on a fixed scratch area
+compiled into the library.  These tests call it through the C ABI twice in a
+row -- a larger problem, then a smaller one, so that anything the first call
+left in the shared scratch area would show -- and compare each result with
+regc_mbar_solve at the tolerance of the other MBAR tests.  This file is
+collected last, so a run that stops at the first failure has run every other
+test before it.
+"""
+import numpy as np
+import pytest
+
+from paper_1908_11118_gb300 import RegcError, mbar_solve
+from paper_1908_11118_gb300 import build as B
+from paper_1908_11118_gb300.regc import mbar_solve_static
+from test_gpu_stats_mbar import synthetic_bins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_static_solve_matches_allocating_solve_on_two_calls():
+    for seed, side in ((0, 5), (1, 3)):
+        kT, mu, omega, N, E, H, nmax = synthetic_bins(seed=seed, S_side=side)
+        f_s, D_s, it_s = mbar_solve_static(kT, mu, 1.0, omega, N, E, H, tol=1e-11)
+        f_r, D_r, it_r = mbar_solve(kT, mu, 1.0, omega, N, E, H, tol=1e-11)
+        np.testing.assert_allclose(f_s, f_r, atol=1e-9)
+        np.testing.assert_allclose(D_s, D_r, atol=1e-9)
+        assert abs(it_s - it_r) <= 2
+
+
+def test_static_solve_rejects_sizes_beyond_its_scratch():
+    n = 4097
+    with pytest.raises(RegcError) as err:
+        mbar_solve_static(np.ones(n), np.zeros(n), 1.0, np.ones(n), np.zeros(1, np.int32),
+                          np.zeros(1), np.ones(1))
+    assert err.value.status == -1
