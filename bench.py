@@ -237,6 +237,8 @@ def run_own(args):
     accepted = int((mv1[:, :, 1] - mv0[:, :, 1]).sum())
     pairs = int(pr1[0] - pr0[0])
     cand = int(pr1[1] - pr0[1])
+    rounds = int(pr1[2] - pr0[2])
+    evals = int(pr1[3] - pr0[3])
     mean_sweep_s = sum(sweep_ms) / K / 1e3
     achieved = pairs / K * FLOPS_PER_PAIR / mean_sweep_s / 1e12
     peak, peak_src = fp32_peak()
@@ -281,6 +283,9 @@ def run_own(args):
                          "launch_ms": mean_sweep_s * 1e3},
             "e2e": {"value": p.S * SWEEPS_PER_STEP * p.moves_per_sweep * world / e2e_s, "unit": "moves/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "speculation": {"warps_per_walker": int(os.environ.get("REGC_WARPS_PER_WALKER", "1")),
+                            "moves_per_round": moves / max(rounds, 1),
+                            "kept_fraction": moves / max(evals, 1)},
             "gpu_launches": 2 * K,
             "clocks": clk,
             "cpu_baseline": cpu,

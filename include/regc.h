@@ -202,8 +202,10 @@ REGC_API regc_status regc_check_energy(regc_handle *h, double *max_drift);
 
 /* Counters (host buffers, any may be NULL): moves [S walkers][3 types][trials,
  * accepts]; exchanges [S lower states][4 directions][attempts, accepts];
- * pairs [2]: pairs within rc evaluated, candidate pairs examined, summed over
- * walkers since the last reset.  Synchronous. */
+ * pairs [4]: pairs within rc of the committed moves, candidate pairs whose
+ * distance was evaluated (including speculative evaluations that were
+ * discarded), evaluation rounds, move evaluations -- summed over walkers since
+ * the last reset.  Synchronous. */
 REGC_API regc_status regc_counters(regc_handle *h, int64_t *moves, int64_t *exchanges, int64_t *pairs);
 
 /* MBAR reweighting of the handle's pooled histogram (Sec. II.B).  Solves the

@@ -7,11 +7,12 @@
 
 namespace regc {
 
-// Shared-memory bytes one walker needs in the sweep kernel.
-size_t sweep_smem_per_walker(int nmax, int ncell, int cap);
+// Shared-memory bytes of the sweep kernel's CTA (one walker, W warps).
+size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker);
 
-// n_sweeps sweeps of every walker; trace may be null.
-cudaError_t launch_sweep(const SweepParams& P, int walkers_per_cta, cudaStream_t s);
+// P.n_sweeps sweeps of every walker with P.warps_per_walker warps per walker;
+// P.trace may be null.
+cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s);
 
 // From-scratch fixed-point energy of every walker into out[S]; overlap flags
 // go to P.error (ERR_OVERLAP) when check_overlap is set.

@@ -4,6 +4,7 @@
 // rules (Sec. II.A.1, Eq. Ngrand), lays out the device state, and launches the
 // kernels of sweep.cu, exchange.cu and mbar.cu on the handle's stream.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -17,7 +18,7 @@ using namespace regc;
 
 struct regc_handle {
     cudaStream_t stream = nullptr;
-    int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0, wpc = 1;
+    int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0;
     double lambda0 = 1.0, e_lo = 0.0, e_bin = 1.0;
     float Lx = 0, Ly = 0, Lz = 0, z_lo = 0, z_hi = 0;
     int periodic_z = 0;
@@ -179,7 +180,21 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     cg.icz = (float)(cg.ncz / hz);
     const double vcell = (double)surf->Lx / cg.ncx * ((double)surf->Ly / cg.ncy) * (hz / cg.ncz);
     cg.cap = std::min(grid->nmax, std::max(8, (int)ceil(1.6 * vcell) + 8));
-    const size_t spw = sweep_smem_per_walker(grid->nmax, cg.ncell, cg.cap);
+    if (!(fabs(grid->e_lo) < 4294967296.0) || !(grid->e_bin * kFixPerUnit >= 1.0) ||
+        !(grid->e_bin < 4294967296.0))
+        return REGC_EINVAL;
+    // warps per walker = moves evaluated speculatively per round (1, 2 or 4).
+    // One is the default: on the 1024-replica workload two and four warps keep
+    // 93 % and 79 % of their speculative evaluations but lose more to the
+    // round barriers and the serial commit than they gain.
+    // REGC_WARPS_PER_WALKER overrides the default.
+    int W = 1;
+    if (const char* env = getenv("REGC_WARPS_PER_WALKER")) {
+        const int v = atoi(env);
+        if (v == 1 || v == 2 || v == 4) W = v;
+    }
+    while (W > 1 && sweep_smem_per_walker(grid->nmax, cg.ncell, cg.cap, W) > kMaxSmem) W /= 2;
+    const size_t spw = sweep_smem_per_walker(grid->nmax, cg.ncell, cg.cap, W);
     if (spw > kMaxSmem) return REGC_EINVAL;
 
     regc_handle* h = new (std::nothrow) regc_handle;
@@ -201,8 +216,6 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     h->z_hi = surf->z_hi;
     h->periodic_z = periodic_z;
     h->smem_per_walker = spw;
-    // walkers per CTA: as many as keep one CTA within 64 KB of shared memory
-    h->wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / spw));
     const int S = h->S;
 
     // ---- per-state constants of the acceptance rules
@@ -225,6 +238,13 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     }
     std::vector<double> ln_tab(grid->nmax + 2, 0.0);
     for (int k = 1; k < grid->nmax + 2; ++k) ln_tab[k] = log((double)k);
+    std::vector<float> beta_f(S), cins_f(S), cdel_f(S), ln_f(grid->nmax + 2);
+    for (int s = 0; s < S; ++s) {
+        beta_f[s] = (float)beta[s];
+        cins_f[s] = (float)c_ins[s];
+        cdel_f[s] = (float)c_del[s];
+    }
+    for (size_t k = 0; k < ln_tab.size(); ++k) ln_f[k] = (float)ln_tab[k];
 
     // ---- surface columns (atoms within rc of any point of a column)
     SurfaceTab st{};
@@ -310,8 +330,11 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     P.key1 = (uint32_t)(seed >> 32);
     P.e_lo = grid->e_lo;
     P.e_bin = grid->e_bin;
+    P.e_lo_fix = llround(grid->e_lo * kFixPerUnit);
+    P.e_bin_fix = llround(grid->e_bin * kFixPerUnit);
     P.n_e_bins = grid->n_e_bins;
     P.smem_per_walker = (int)spw;
+    P.warps_per_walker = W;
 
     // ---- device memory
     regc_status st_ = REGC_OK;
@@ -332,6 +355,19 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &d_bmu, S));
     TRY(dalloc(h, &d_lnbeta, S));
     TRY(dalloc(h, &d_ln, ln_tab.size()));
+    float *d_beta_f, *d_cins_f, *d_cdel_f, *d_ln_f;
+    TRY(dalloc(h, &d_beta_f, S));
+    TRY(dalloc(h, &d_cins_f, S));
+    TRY(dalloc(h, &d_cdel_f, S));
+    TRY(dalloc(h, &d_ln_f, ln_f.size()));
+    TRY(upload(h, d_beta_f, beta_f.data(), S));
+    TRY(upload(h, d_cins_f, cins_f.data(), S));
+    TRY(upload(h, d_cdel_f, cdel_f.data(), S));
+    TRY(upload(h, d_ln_f, ln_f.data(), ln_f.size()));
+    P.beta_f = d_beta_f;
+    P.c_ins_f = d_cins_f;
+    P.c_del_f = d_cdel_f;
+    P.ln_tab_f = d_ln_f;
     TRY(dalloc(h, &h->d_kT_state, S));
     TRY(dalloc(h, &h->d_mu_state, S));
     TRY(dalloc(h, &d_coloff, col_off.size()));
@@ -372,7 +408,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &P.moments, (size_t)S * 4));
     TRY(dalloc(h, &P.hNE, (size_t)(grid->nmax + 1) * grid->n_e_bins));
     TRY(dalloc(h, &P.e_out, S));
-    TRY(dalloc(h, &P.pair_counts, 2));
+    TRY(dalloc(h, &P.pair_counts, 4));
     TRY(dalloc(h, &h->d_error, 1));
     TRY(dalloc(h, &h->d_fix, S));
     std::vector<int> ident(S);
@@ -401,7 +437,7 @@ regc_status regc_sweep(regc_handle* h, int n_sweeps) {
     P.t0 = h->t;
     P.n_sweeps = n_sweeps;
     P.trace = nullptr;
-    const regc_status st = cuda_fail(h, launch_sweep(P, h->wpc, h->stream));
+    const regc_status st = cuda_fail(h, launch_sweep(P, h->stream));
     if (st == REGC_OK) h->t += (uint32_t)n_sweeps;
     return st;
 }
@@ -418,7 +454,7 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
     P.t0 = h->t;
     P.n_sweeps = n_sweeps;
     P.trace = d_trace;
-    st = cuda_fail(h, launch_sweep(P, h->wpc, h->stream));
+    st = cuda_fail(h, launch_sweep(P, h->stream));
     if (st == REGC_OK) {
         h->t += (uint32_t)n_sweeps;
         st = cuda_fail(h, cudaMemcpyAsync(trace, d_trace, n * sizeof(regc_move_record), cudaMemcpyDeviceToHost,
@@ -470,7 +506,7 @@ regc_status regc_reset_histograms(regc_handle* h) {
     zero(h->P.e_out, S * 8);
     zero(h->P.move_counts, S * 6 * 8);
     zero(h->X.ex_counts, S * 8 * 8);
-    zero(h->P.pair_counts, 2 * 8);
+    zero(h->P.pair_counts, 4 * 8);
     return cuda_fail(h, e);
 }
 
@@ -578,7 +614,7 @@ regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, in
     if (exchanges && e == cudaSuccess)
         e = cudaMemcpyAsync(exchanges, h->X.ex_counts, (size_t)h->S * 8 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (pairs && e == cudaSuccess)
-        e = cudaMemcpyAsync(pairs, h->P.pair_counts, 2 * 8, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(pairs, h->P.pair_counts, 4 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     return sync_check(h);
 }

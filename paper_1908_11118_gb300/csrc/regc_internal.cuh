@@ -19,12 +19,12 @@ enum : int {
     ERR_NUMERIC = 8,    // a non-finite energy
 };
 
-// Energies are accumulated as 64-bit fixed-point integers in units of 2^-32
+// Energies are accumulated as 64-bit fixed-point integers in units of 2^-30
 // eps.  Every pair term is a binary32 value phi rounded once to that grid, so a
 // sum does not depend on the order in which pairs are visited and a running
 // total built from move energies equals the from-scratch sum exactly.
-constexpr float kFixScale = 4294967296.0f;          // 2^32
-constexpr double kFixUnit = 1.0 / 4294967296.0;     // 2^-32
+constexpr double kFixUnit = 1.0 / 1073741824.0;     // 2^-30
+constexpr double kFixPerUnit = 1073741824.0;        // 2^30
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -110,6 +110,10 @@ struct SweepParams {
     const double* c_ins;   // [S] ln V - 3 ln Lambda_s + beta_s mu_s
     const double* c_del;   // [S] 3 ln Lambda_s - ln V - beta_s mu_s
     const double* ln_tab;  // [nmax + 2] ln k
+    const float* beta_f;   // binary32 copies for the pre-test of the acceptance rule
+    const float* c_ins_f;
+    const float* c_del_f;
+    const float* ln_tab_f;
     float4* pos;           // [S][nmax]
     int* n;                // [S]
     long long* efix;       // [S]
@@ -120,14 +124,16 @@ struct SweepParams {
     unsigned long long* hNE;      // [nmax+1][n_e_bins]
     unsigned long long* e_out;    // [S]
     double e_lo, e_bin;
+    long long e_lo_fix, e_bin_fix;  // E-histogram origin and bin width in units of 2^-30
     int n_e_bins;
     long long* move_counts;       // [S][6]
-    unsigned long long* pair_counts;  // [2]
+    unsigned long long* pair_counts;  // [4] pairs in rc, candidates, rounds, evaluations
     int* error;
     regc_move_record* trace;      // device [S][n_sweeps][mps] or null
     uint32_t t0;
     int n_sweeps;
     int smem_per_walker;          // bytes
+    int warps_per_walker;         // 1, 2 or 4
 };
 
 struct ExchangeParams {
@@ -144,23 +150,61 @@ struct ExchangeParams {
 };
 
 // ----------------------------------------------------------- pair energy
-// Fixed-point energy of one pair from its displacement (dx, dy, dz): phi(r)
-// for r < rc.  Written with explicit round-to-nearest intrinsics so that the
-// value is the same wherever it is inlined, and symmetric under exchanging
-// the two particles (dx -> -dx).
-__device__ __forceinline__ long long pair_fix_d(float dx, float dy, float dz, const Geometry& g,
-                                                const PairTab& t, int& n_in, int& overlap) {
-    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-    long long v = 0;
-    if (r2 < g.rc2) {
-        const float s2 = __fdividef(t.sig2, r2);
-        const float s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
-        const float phi = __fmul_rn(t.eps4, __fmaf_rn(s6, s6, -s6));
-        v = __float2ll_rn(__fmul_rn(phi, kFixScale));
+// A pair energy phi (|phi| < 2^35) split exactly into integer counts of
+// 2^13, 2^-8 and 2^-30 eps: phi = big 2^13 + hi 2^-8 + lo 2^-30 after one
+// round-to-nearest-even onto the 2^-30 grid.  Adding 1.5 2^(23+u) to a float
+// below 2^(22+u) in magnitude rounds it to a multiple of 2^u and leaves that
+// multiple in the low bits of the sum, so each level costs two FADDs and an
+// IADD, on the FP32 and integer pipes.  The parts are accumulated in int32.
+struct Fix3 {
+    int big, hi, lo;
+};
+
+constexpr float kM2 = 103079215104.0f;   // 1.5 * 2^36: unit 2^13
+constexpr float kM1 = 49152.0f;          // 1.5 * 2^15: unit 2^-8
+constexpr float kM0 = 0.01171875f;       // 1.5 * 2^-7: unit 2^-30
+
+__device__ __forceinline__ void fix_add(Fix3& a, float phi, int sign) {
+    const float t2 = __fadd_rn(phi, kM2);
+    const float r1 = __fsub_rn(phi, __fsub_rn(t2, kM2));
+    const float t1 = __fadd_rn(r1, kM1);
+    const float r0 = __fsub_rn(r1, __fsub_rn(t1, kM1));
+    const float t0 = __fadd_rn(r0, kM0);
+    a.big += sign * (__float_as_int(t2) - __float_as_int(kM2));
+    a.hi += sign * (__float_as_int(t1) - __float_as_int(kM1));
+    a.lo += sign * (__float_as_int(t0) - __float_as_int(kM0));
+}
+
+// The 64-bit fixed-point value (units of 2^-30) of a Fix3 sum.
+__device__ __forceinline__ long long fix_value(int big, int hi, int lo) {
+    return ((long long)big << 43) + ((long long)hi << 22) + (long long)lo;
+}
+
+// Binary32 pair energy phi(r) from r^2 (r < rc).  Explicit round-to-nearest
+// intrinsics keep the value identical wherever it is inlined.
+__device__ __forceinline__ float phi_of_r2(float r2, const PairTab& t) {
+    const float s2 = __fdividef(t.sig2, r2);
+    const float s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
+    return __fmul_rn(t.eps4, __fmaf_rn(s6, s6, -s6));
+}
+
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+// Binary32 pair energy of one pair from its displacement, 0 beyond rc.  It
+// depends on (dx, dy, dz) only through r^2, so it is the same for both orders
+// of the pair.
+__device__ __forceinline__ float pair_phi(float dx, float dy, float dz, float rc2, const PairTab& t,
+                                          int& n_in, int& overlap) {
+    const float r2 = r2_of(dx, dy, dz);
+    float phi = 0.0f;
+    if (r2 < rc2) {
+        phi = phi_of_r2(r2, t);
         n_in += 1;
         overlap |= (r2 < t.rhc2);
     }
-    return v;
+    return phi;
 }
 
 // Minimum-image displacement q - p along a periodic axis of period L, rounded

@@ -1,21 +1,31 @@
 // sweep.cu -- the grand-canonical Monte Carlo sweep of every replica (sm_103a).
 //
-// One warp owns one walker (replica configuration) for a whole launch:
+// One CTA of K warps (K = 1, 2 or 4) owns one walker (replica configuration)
+// for a whole launch:
 //   1. its positions are staged from HBM into shared memory by a bulk TMA
 //      copy (cp.async.bulk, completion on an mbarrier with a bounded wait);
 //   2. a cell list (cells >= rc on a side, fixed capacity per cell) is built
 //      in shared memory, in particle order, so that it is deterministic;
-//   3. every trial move (Sec. II.A.1 insertion / removal, Sec. II.A.3
-//      displacement) evaluates the truncated-LJ energy of the moved particle
-//      against the frozen surface and the other mobile particles; the 32
-//      lanes split the candidate partners of the 27-cell stencil, and the
-//      partial sums are reduced with warp shuffles;
-//   4. the Metropolis / grand-canonical acceptance test is taken in FP64
-//      (a binary32 pre-test decides all but near-ties);
+//   3. the trial moves (Sec. II.A.1 insertion / removal, Sec. II.A.3
+//      displacement) are processed in rounds: warp j evaluates move m0 + j of
+//      the walker's sequence against the current configuration -- the
+//      truncated-LJ energy change of the moved particle against the other
+//      mobile particles of its 27-cell stencil and the frozen surface atoms
+//      listed for its column, each pair term added in exact fixed point and
+//      reduced with redux.sync;
+//   4. thread 0 then commits the round's moves in order.  Move m0 + j keeps
+//      its evaluated energy change if no earlier move of the round that was
+//      accepted changed anything it depends on (N, for a move that picks a
+//      particle by index; any position within rc of its query points);
+//      otherwise the round stops there and the move is evaluated again in the
+//      next round.  Fixed-point sums do not depend on the order of the pairs,
+//      so a kept energy change is bit-identical to the one a strictly
+//      sequential evaluation would compute, and the chain is exactly the
+//      sequential Markov chain.  The acceptance test ln u < ln alpha is
+//      decided in binary32 when the two sides differ by more than 1e-3, and in
+//      FP64 otherwise, which gives the FP64 decision in every case;
 //   5. after each sweep the walker is observed into its state's histograms;
 //   6. positions, N and the running energy go back to HBM.
-// Energies are 64-bit fixed-point sums of binary32 pair terms, so the
-// running total never drifts from the from-scratch energy.
 #include "launch.h"
 
 namespace regc {
@@ -23,27 +33,93 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr double kLn2m32 = -22.18070977791825;   // ln 2^-32
+constexpr int kRing = 64;                         // Philox blocks of moves kept ahead
 
-// A non-empty cell of the stencil of the moved particle: its first index in
-// the flattened candidate list and the periodic shifts of its image.  The
-// displacement to a partner p in this cell is (q - oA) - (p - oB) per axis;
-// oA, oB are 0 or the period, and each shifted operand is exact (Sterbenz),
-// so the displacement is rounded once.
+// A non-empty cell of a stencil: its first index in the flattened candidate
+// list and the periodic shifts of its image.  The displacement from query k to
+// a partner p of the cell is a_k - (p - ob) per axis, where a_k is the query
+// shifted by 0 or minus the period and ob is 0 or the period; every shifted
+// operand is exact (Sterbenz), so the displacement is rounded once.
 struct StEntry {
     int cell, excl;
-    float oAx, oBx, oAy, oBy, oAz, oBz;
+    float ax0, ay0, az0, ax1, ay1, az1;
+    float obx, oby, obz;
+    int pad;
+};
+
+// The evaluation of one trial move, handed from its warp to the committer.
+struct MoveRes {
+    int type;      // 0 displacement, 1 insertion, 2 removal
+    int status;    // 0 evaluated, 1 at the N boundary, 2 displacement left the region
+    int idx;       // particle picked (insertion: unused)
+    int n_eval;    // N the move was evaluated with
+    int big, hi, lo;   // fixed-point energy change
+    int flags;     // bit 0 overlap, bits 1.. pairs within rc
+    float q0x, q0y, q0z;   // new position (removal: the old one)
+    float q1x, q1y, q1z;   // old position of a displacement
+    int dec;       // decision with N = n_eval: 0 reject, 1 accept, 2 near tie (FP64 needed)
+    int pad[3];
+};
+
+// Constants of the walker's state for the binary32 pre-test of the acceptance.
+struct StateF {
+    float beta, c_ins, c_del;
+};
+
+// Binary32 pre-test of ln u < ln alpha with N particles before the move:
+// 0 reject, 1 accept, 2 the two sides are within 1e-3 and FP64 must decide.
+__device__ __forceinline__ int pretest(const StateF& sf, int type, int N, int big, int hi, int lo, uint32_t b1) {
+    const float de_f = __fmaf_rn((float)lo, 9.313225746154785e-10f,
+                                 __fmaf_rn((float)hi, 0.00390625f, (float)big * 8192.0f));
+    float c_f = 0.f;
+    if (type == 1) c_f = sf.c_ins - __logf((float)(N + 1));
+    else if (type == 2) c_f = sf.c_del + __logf((float)N);
+    const float la_f = c_f - sf.beta * de_f;
+    const float lu_f = __logf(((float)b1 + 0.5f) * 2.3283064365386963e-10f);
+    if (la_f >= 0.f || lu_f < la_f - 1e-3f) return 1;
+    if (lu_f > la_f + 1e-3f) return 0;
+    return 2;
+}
+
+// Per-launch statistics of the walker, kept by thread 0.
+struct WalkerStats {
+    long long mN, mN2, mE;
+    double mE2;
+    unsigned long long om, eo;
+    unsigned long long pairs;   // pairs within rc of the committed moves
+    unsigned long long rounds, evals;
+    int tr[3], ac[3];
+};
+
+// Round state broadcast by the committer.
+struct RoundHdr {
+    int N;
+    int committed;
+    long long E;
 };
 
 struct WalkerSmem {
     float4* pos;        // [nmax]  x, y, z, (cell << 16 | slot) as bits
     uint64_t* bar;      // mbarrier of the position copy
-    StEntry* stencil;   // [32]
+    WalkerStats* stats;
+    RoundHdr* hdr;
+    uint4* rng;         // [kRing][2] Philox blocks A, B of upcoming moves
+    MoveRes* res;       // [K]
+    StEntry* stencil;   // [K][32]
     uint16_t* cnt;      // [ncell]
     uint16_t* slots;    // [ncell][cap] particle indices
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+__host__ __device__ inline size_t smem_bytes(int nmax, int ncell, int cap, int K) {
+    return align16(size_t(nmax) * 16) + 16 + align16(sizeof(WalkerStats)) + align16(sizeof(RoundHdr)) +
+           size_t(kRing) * 2 * sizeof(uint4) + align16(size_t(K) * sizeof(MoveRes)) +
+           size_t(K) * 32 * sizeof(StEntry) + align16(size_t(ncell) * 2) + align16(size_t(ncell) * cap * 2);
+}
+
+template <int K>
 __device__ inline WalkerSmem carve(char* base, const SweepParams& P) {
     WalkerSmem w;
     size_t off = 0;
@@ -51,8 +127,16 @@ __device__ inline WalkerSmem carve(char* base, const SweepParams& P) {
     off += align16(size_t(P.nmax) * 16);
     w.bar = reinterpret_cast<uint64_t*>(base + off);
     off += 16;
+    w.stats = reinterpret_cast<WalkerStats*>(base + off);
+    off += align16(sizeof(WalkerStats));
+    w.hdr = reinterpret_cast<RoundHdr*>(base + off);
+    off += align16(sizeof(RoundHdr));
+    w.rng = reinterpret_cast<uint4*>(base + off);
+    off += size_t(kRing) * 2 * sizeof(uint4);
+    w.res = reinterpret_cast<MoveRes*>(base + off);
+    off += align16(size_t(K) * sizeof(MoveRes));
     w.stencil = reinterpret_cast<StEntry*>(base + off);
-    off += 32 * sizeof(StEntry);
+    off += size_t(K) * 32 * sizeof(StEntry);
     w.cnt = reinterpret_cast<uint16_t*>(base + off);
     off += align16(size_t(P.cg.ncell) * 2);
     w.slots = reinterpret_cast<uint16_t*>(base + off);
@@ -105,119 +189,143 @@ __device__ bool mbar_wait_bounded(uint64_t* bar) {
     return true;
 }
 
-// --------------------------------------------------------------- cells
-
-__device__ __forceinline__ int cell_of(const SweepParams& P, float x, float y, float z) {
-    const int cx = min(P.cg.ncx - 1, (int)(x * P.cg.icx));
-    const int cy = min(P.cg.ncy - 1, (int)(y * P.cg.icy));
-    const float zz = P.g.periodic_z ? z : (z - P.g.z_lo);
-    const int cz = min(P.cg.ncz - 1, max(0, (int)(zz * P.cg.icz)));
-    return (cz * P.cg.ncy + cy) * P.cg.ncx + cx;
+template <int K>
+__device__ __forceinline__ void group_sync() {
+    if (K == 1) __syncwarp();
+    else __syncthreads();
 }
 
-__device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// --------------------------------------------------------------- cells
 
-// Stencil entry handled by this lane for the cell `cell` of the moved
-// particle (cell = -1 if the lane has none) and the stencil size.  Periodic
-// axes always contribute three images (-1, 0, +1); with fewer than three
-// cells along an axis the same cell appears with different shifts, which
-// evaluates every periodic image of its particles (at most one of them can be
-// within rc, because every period is at least 2 rc).
-__device__ __forceinline__ StEntry stencil_entry(const SweepParams& P, int cell, int lane, int& nst) {
-    const int ncx = P.cg.ncx, ncy = P.cg.ncy, ncz = P.cg.ncz;
-    const int cx = cell % ncx, cy = (cell / ncx) % ncy, cz = cell / (ncx * ncy);
+struct Cell3 {
+    int x, y, z;
+};
+
+__device__ __forceinline__ Cell3 cell3_of(const SweepParams& P, float x, float y, float z) {
+    Cell3 c;
+    c.x = min(P.cg.ncx - 1, (int)(x * P.cg.icx));
+    c.y = min(P.cg.ncy - 1, (int)(y * P.cg.icy));
+    const float zz = P.g.periodic_z ? z : (z - P.g.z_lo);
+    c.z = min(P.cg.ncz - 1, max(0, (int)(zz * P.cg.icz)));
+    return c;
+}
+
+__device__ __forceinline__ int cell_index(const SweepParams& P, Cell3 c) {
+    return (c.z * P.cg.ncy + c.y) * P.cg.ncx + c.x;
+}
+
+__device__ __forceinline__ int cell_of(const SweepParams& P, float x, float y, float z) {
+    return cell_index(P, cell3_of(P, x, y, z));
+}
+
+// Stencil entry handled by this lane (cell = -1 if none), for queries q0, q1
+// in cell c.  Periodic axes always contribute three images (-1, 0, +1); with
+// fewer than three cells along an axis the same cell appears with different
+// shifts, which evaluates every periodic image of its particles (at most one
+// of them can be within rc, because every period is at least 2 rc).
+__device__ __forceinline__ StEntry stencil_entry(const SweepParams& P, Cell3 c, int lane, float q0x, float q0y,
+                                                 float q0z, float q1x, float q1y, float q1z) {
     int zfirst = 0, nzs = 3;
     if (!P.g.periodic_z) {
-        zfirst = max(0, cz - 1);
-        nzs = min(ncz - 1, cz + 1) - zfirst + 1;
+        zfirst = max(0, c.z - 1);
+        nzs = min(P.cg.ncz - 1, c.z + 1) - zfirst + 1;
     }
-    nst = 9 * nzs;
-    StEntry e{-1, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (lane >= nst) return e;
+    StEntry e;
+    e.cell = -1;
+    e.excl = 0;
+    if (lane >= 9 * nzs) return e;
     const int lx = lane % 3, ly = (lane / 3) % 3, lz = lane / 9;
-    int ix = cx - 1 + lx, iy = cy - 1 + ly, iz;
-    if (ix < 0) { ix += ncx; e.oBx = P.g.Lx; }
-    else if (ix >= ncx) { ix -= ncx; e.oAx = P.g.Lx; }
-    if (iy < 0) { iy += ncy; e.oBy = P.g.Ly; }
-    else if (iy >= ncy) { iy -= ncy; e.oAy = P.g.Ly; }
+    int ix = c.x - 1 + lx, iy = c.y - 1 + ly, iz;
+    float oax = 0.f, oay = 0.f, oaz = 0.f;
+    e.obx = e.oby = e.obz = 0.f;
+    if (ix < 0) { ix += P.cg.ncx; e.obx = P.g.Lx; }
+    else if (ix >= P.cg.ncx) { ix -= P.cg.ncx; oax = P.g.Lx; }
+    if (iy < 0) { iy += P.cg.ncy; e.oby = P.g.Ly; }
+    else if (iy >= P.cg.ncy) { iy -= P.cg.ncy; oay = P.g.Ly; }
     if (P.g.periodic_z) {
-        iz = cz - 1 + lz;
-        if (iz < 0) { iz += ncz; e.oBz = P.g.Lz; }
-        else if (iz >= ncz) { iz -= ncz; e.oAz = P.g.Lz; }
+        iz = c.z - 1 + lz;
+        if (iz < 0) { iz += P.cg.ncz; e.obz = P.g.Lz; }
+        else if (iz >= P.cg.ncz) { iz -= P.cg.ncz; oaz = P.g.Lz; }
     } else {
         iz = zfirst + lz;
     }
-    e.cell = (iz * ncy + iy) * ncx + ix;
+    e.cell = (iz * P.cg.ncy + iy) * P.cg.ncx + ix;
+    e.ax0 = __fsub_rn(q0x, oax);
+    e.ay0 = __fsub_rn(q0y, oay);
+    e.az0 = __fsub_rn(q0z, oaz);
+    e.ax1 = __fsub_rn(q1x, oax);
+    e.ay1 = __fsub_rn(q1y, oay);
+    e.az1 = __fsub_rn(q1z, oaz);
     return e;
 }
 
-// Energy of NQ positions (sharing one stencil cell) against the mobile
-// particles of the stencil, skipping particle `skip`.  The candidate list is
-// the concatenation of the non-empty stencil entries; lane j of a batch takes
-// flat index base + j and finds its entry from the OR-reduced mask of entry
-// starts inside the batch.
+// Fixed-point energy of NQ queries (sharing the stencil of cell c) against the
+// mobile particles of the stencil except `skip`: query 0 enters with sign
+// sgn0, query 1 with -1.  The candidate list is the concatenation of the
+// non-empty stencil entries; lane j of a batch of 32 finds its entry from the
+// OR-reduced mask of entry starts in the batch.
 template <int NQ>
-__device__ __forceinline__ void mobile_energy(const SweepParams& P, const WalkerSmem& W, int cell,
-                                              const float (&qx)[NQ], const float (&qy)[NQ],
-                                              const float (&qz)[NQ], int skip, long long (&acc)[NQ],
-                                              int& n_in, int& n_cand, int& overlap, int lane) {
-    int nst;
-    StEntry se = stencil_entry(P, cell, lane, nst);
-    const int c = se.cell >= 0 ? (int)W.cnt[se.cell] : 0;
-    int incl = c;
+__device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
+                                            float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
+                                            int sgn0, Fix3& acc, int& n_in, int& n_cand, int& overlap, int lane,
+                                            int warp) {
+    StEntry* st = S.stencil + warp * 32;
+    StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
+    const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
+    int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += t;
     }
-    const int excl = incl - c;
+    const int excl = incl - cnt;
     const int total = __shfl_sync(FULL, incl, 31);
-    const unsigned nonempty = __ballot_sync(FULL, c > 0);
-    if (c > 0) {
+    const unsigned nonempty = __ballot_sync(FULL, cnt > 0);
+    if (cnt > 0) {
         se.excl = excl;
-        W.stencil[__popc(nonempty & lanemask_lt(lane))] = se;
+        st[__popc(nonempty & lanemask_lt(lane))] = se;
     }
     __syncwarp();
-    int started = 0;
+    int ov = 0, started = 0;
     for (int base = 0; base < total; base += 32) {
-        const unsigned bit =
-            (c > 0 && excl >= base && excl < base + 32) ? (1u << (excl - base)) : 0u;
+        const unsigned bit = (cnt > 0 && excl >= base && excl < base + 32) ? (1u << (excl - base)) : 0u;
         const unsigned starts = __reduce_or_sync(FULL, bit);
         const int j = base + lane;
         if (j < total) {
             const int r = started + __popc(starts & lanemask_le(lane)) - 1;
-            const StEntry& e = W.stencil[r];
-            const int pj = W.slots[e.cell * P.cg.cap + (j - e.excl)];
+            const StEntry& e = st[r];
+            const int pj = S.slots[e.cell * P.cg.cap + (j - e.excl)];
             if (pj != skip) {
-                const float4 p = W.pos[pj];
-                const float bx = __fsub_rn(p.x, e.oBx), by = __fsub_rn(p.y, e.oBy);
-                const float bz = __fsub_rn(p.z, e.oBz);
+                const float4 p = S.pos[pj];
+                const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
                 n_cand += NQ;
-#pragma unroll
-                for (int k = 0; k < NQ; ++k) {
-                    const float dx = __fsub_rn(__fsub_rn(qx[k], e.oAx), bx);
-                    const float dy = __fsub_rn(__fsub_rn(qy[k], e.oAy), by);
-                    const float dz = __fsub_rn(__fsub_rn(qz[k], e.oAz), bz);
-                    acc[k] += pair_fix_d(dx, dy, dz, P.g, P.gg, n_in, overlap);
+                const float phi0 = pair_phi(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz),
+                                            P.g.rc2, P.gg, n_in, ov);
+                fix_add(acc, phi0, sgn0);
+                if (NQ == 2) {
+                    int ov1 = 0;
+                    const float phi1 = pair_phi(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by),
+                                                __fsub_rn(e.az1, bz), P.g.rc2, P.gg, n_in, ov1);
+                    fix_add(acc, phi1, -1);
                 }
             }
         }
         started += __popc(starts);
     }
+    overlap |= ov;
     __syncwarp();
 }
 
-// Energy of NQ positions (sharing one surface column) against the images of
-// frozen surface atoms listed for that column.  Each listed image carries the
-// exact shifts of its displacement: the stored coordinate is already shifted
-// by -L where that is exact, and the flag bits ask for the query to be
-// shifted by -L instead.
+// Fixed-point energy of NQ queries (sharing one surface column) against the
+// images of frozen surface atoms listed for that column.  Each listed image
+// holds its coordinate already shifted by minus the period where that is
+// exact; flag bits ask for the query to be shifted by minus the period instead.
 template <int NQ>
-__device__ __forceinline__ void surface_energy(const SweepParams& P, int col, const float (&qx)[NQ],
-                                               const float (&qy)[NQ], const float (&qz)[NQ],
-                                               long long (&acc)[NQ], int& n_in, int& n_cand,
-                                               int& overlap, int lane) {
+__device__ __forceinline__ void surface_pass(const SweepParams& P, int col, float q0x, float q0y, float q0z,
+                                             float q1x, float q1y, float q1z, int sgn0, Fix3& acc, int& n_in,
+                                             int& n_cand, int& overlap, int lane) {
     const int beg = P.st.col_off[col], end = P.st.col_off[col + 1];
+    int ov = 0;
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
         const unsigned bits = __float_as_uint(a.w);
@@ -225,14 +333,17 @@ __device__ __forceinline__ void surface_energy(const SweepParams& P, int col, co
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
         n_cand += NQ;
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const float dx = __fsub_rn(__fsub_rn(qx[k], sx), a.x);
-            const float dy = __fsub_rn(__fsub_rn(qy[k], sy), a.y);
-            const float dz = __fsub_rn(__fsub_rn(qz[k], sz), a.z);
-            acc[k] += pair_fix_d(dx, dy, dz, P.g, t, n_in, overlap);
+        const float phi0 = pair_phi(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
+                                    __fsub_rn(__fsub_rn(q0z, sz), a.z), P.g.rc2, t, n_in, ov);
+        fix_add(acc, phi0, sgn0);
+        if (NQ == 2) {
+            int ov1 = 0;
+            const float phi1 = pair_phi(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
+                                        __fsub_rn(__fsub_rn(q1z, sz), a.z), P.g.rc2, t, n_in, ov1);
+            fix_add(acc, phi1, -1);
         }
     }
+    overlap |= ov;
 }
 
 __device__ __forceinline__ int surface_col(const SweepParams& P, float x, float y) {
@@ -245,87 +356,31 @@ __device__ __forceinline__ bool near_surface(const SweepParams& P, float z) {
     return P.g.periodic_z || z < P.st.z_reach;
 }
 
-// Interaction energy (fixed point, summed over the warp) of one position.
-__device__ long long energy_one(const SweepParams& P, const WalkerSmem& W, float x, float y, float z,
-                                int skip, int& n_in, int& n_cand, int& overlap, int lane) {
-    const float qx[1] = {x}, qy[1] = {y}, qz[1] = {z};
-    long long acc[1] = {0};
-    mobile_energy<1>(P, W, cell_of(P, x, y, z), qx, qy, qz, skip, acc, n_in, n_cand, overlap, lane);
-    if (near_surface(P, z)) surface_energy<1>(P, surface_col(P, x, y), qx, qy, qz, acc, n_in, n_cand, overlap, lane);
-    return acc[0];
-}
-
-// New-minus-old energy of a displacement of particle i from o to n.
-__device__ long long energy_diff(const SweepParams& P, const WalkerSmem& W, float4 o, float nx, float ny,
-                                 float nz, int i, int& n_in, int& n_cand, int& overlap, int lane) {
-    const int c_old = cell_of(P, o.x, o.y, o.z), c_new = cell_of(P, nx, ny, nz);
-    long long d = 0;
-    int ov_new = 0, ov_old = 0;
-    if (c_old == c_new) {
-        const float qx[2] = {nx, o.x}, qy[2] = {ny, o.y}, qz[2] = {nz, o.z};
-        long long acc[2] = {0, 0};
-        int dummy = 0;
-        mobile_energy<2>(P, W, c_new, qx, qy, qz, i, acc, n_in, n_cand, dummy, lane);
-        ov_new |= dummy;  // the old position never overlaps (invariant of the state)
-        d += acc[0] - acc[1];
-    } else {
-        const float ax[1] = {nx}, ay[1] = {ny}, az[1] = {nz};
-        const float bx[1] = {o.x}, by[1] = {o.y}, bz[1] = {o.z};
-        long long a1[1] = {0}, b1[1] = {0};
-        mobile_energy<1>(P, W, c_new, ax, ay, az, i, a1, n_in, n_cand, ov_new, lane);
-        mobile_energy<1>(P, W, c_old, bx, by, bz, i, b1, n_in, n_cand, ov_old, lane);
-        d += a1[0] - b1[0];
-    }
-    const bool sn = near_surface(P, nz), so = near_surface(P, o.z);
-    const int col_n = surface_col(P, nx, ny), col_o = surface_col(P, o.x, o.y);
-    if (sn && so && col_n == col_o) {
-        const float qx[2] = {nx, o.x}, qy[2] = {ny, o.y}, qz[2] = {nz, o.z};
-        long long acc[2] = {0, 0};
-        surface_energy<2>(P, col_n, qx, qy, qz, acc, n_in, n_cand, ov_new, lane);
-        d += acc[0] - acc[1];
-    } else {
-        if (sn) {
-            const float qx[1] = {nx}, qy[1] = {ny}, qz[1] = {nz};
-            long long acc[1] = {0};
-            surface_energy<1>(P, col_n, qx, qy, qz, acc, n_in, n_cand, ov_new, lane);
-            d += acc[0];
-        }
-        if (so) {
-            const float qx[1] = {o.x}, qy[1] = {o.y}, qz[1] = {o.z};
-            long long acc[1] = {0};
-            surface_energy<1>(P, col_o, qx, qy, qz, acc, n_in, n_cand, ov_old, lane);
-            d -= acc[0];
-        }
-    }
-    overlap |= ov_new;
-    return d;
-}
-
 __device__ __forceinline__ float4 packed(float x, float y, float z, int cell, int slot) {
     return make_float4(x, y, z, __uint_as_float(((unsigned)cell << 16) | (unsigned)slot));
 }
 __device__ __forceinline__ int cell_bits(float w) { return (int)(__float_as_uint(w) >> 16); }
 __device__ __forceinline__ int slot_bits(float w) { return (int)(__float_as_uint(w) & 0xffffu); }
 
-// Remove particle i (whose packed w gives its cell and slot) from its cell.
-__device__ __forceinline__ void cell_remove(const SweepParams& P, const WalkerSmem& W, float wbits) {
+// Remove a particle (whose packed w gives its cell and slot) from its cell.
+__device__ __forceinline__ void cell_remove(const SweepParams& P, const WalkerSmem& S, float wbits) {
     const int c = cell_bits(wbits), s = slot_bits(wbits);
-    if (c >= P.cg.ncell || s >= P.cg.cap || s >= (int)W.cnt[c]) {
+    if (c >= P.cg.ncell || s >= P.cg.cap || s >= (int)S.cnt[c]) {
         // only reachable after a capacity overflow left a particle out of the list
         atomicOr(P.error, ERR_CAPACITY);
         return;
     }
-    const int last = W.cnt[c] - 1;
-    const int moved = W.slots[c * P.cg.cap + last];
-    W.slots[c * P.cg.cap + s] = (uint16_t)moved;
-    W.pos[moved].w = __uint_as_float(((unsigned)c << 16) | (unsigned)s);
-    W.cnt[c] = (uint16_t)last;
+    const int last = S.cnt[c] - 1;
+    const int moved = S.slots[c * P.cg.cap + last];
+    S.slots[c * P.cg.cap + s] = (uint16_t)moved;
+    S.pos[moved].w = __uint_as_float(((unsigned)c << 16) | (unsigned)s);
+    S.cnt[c] = (uint16_t)last;
 }
 
-// Deterministic cell build: particles in index order, ties inside a batch of
-// 32 resolved by lane order.
-__device__ void build_cells(const SweepParams& P, const WalkerSmem& W, int N, int lane) {
-    for (int c = lane; c < P.cg.ncell; c += 32) W.cnt[c] = 0;
+// Deterministic cell build by warp 0: particles in index order, ties inside a
+// batch of 32 resolved by lane order.
+__device__ void build_cells(const SweepParams& P, const WalkerSmem& S, int N, int lane) {
+    for (int c = lane; c < P.cg.ncell; c += 32) S.cnt[c] = 0;
     __syncwarp();
     for (int base = 0; base < N; base += 32) {
         const int j = base + lane;
@@ -333,263 +388,383 @@ __device__ void build_cells(const SweepParams& P, const WalkerSmem& W, int N, in
         int c = -1;
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
         if (act) {
-            p = W.pos[j];
+            p = S.pos[j];
             c = cell_of(P, p.x, p.y, p.z);
         }
         const unsigned grp = __match_any_sync(FULL, c);
         int before = 0;
         if (act) {
-            before = W.cnt[c];
+            before = S.cnt[c];
             const int slot = before + __popc(grp & lanemask_lt(lane));
             if (slot < P.cg.cap) {
-                W.slots[c * P.cg.cap + slot] = (uint16_t)j;
-                W.pos[j] = packed(p.x, p.y, p.z, c, slot);
+                S.slots[c * P.cg.cap + slot] = (uint16_t)j;
+                S.pos[j] = packed(p.x, p.y, p.z, c, slot);
             } else {
                 atomicOr(P.error, ERR_CAPACITY);
             }
         }
         __syncwarp();
-        if (act && lane == __ffs(grp) - 1) W.cnt[c] = (uint16_t)min(P.cg.cap, before + __popc(grp));
+        if (act && lane == __ffs(grp) - 1) S.cnt[c] = (uint16_t)min(P.cg.cap, before + __popc(grp));
         __syncwarp();
     }
 }
 
-template <bool TRACE>
-__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
+// Evaluate trial move m of the launch (sweep m / mps, move m % mps) with one
+// warp against the current configuration with N particles; lane 0 stores the
+// result in *out.
+__device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int m, int N,
+                              int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
+    const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
+    const int type = (unsigned long long)A.x < P.th_disp ? 0 : ((B.z >> 31) == 0u ? 2 : 1);
+    int status = 0, idx = -1, overlap = 0;
+    const int n_in0 = n_in;
+    float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
+    int sgn0 = 1, nq = 1;
+    if (type == 0) {
+        if (N == 0) {
+            status = 1;
+        } else {
+            idx = (int)(((unsigned long long)B.x * (unsigned)N) >> 32);
+            const float4 old = S.pos[idx];
+            const float dx = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(A.y)), 1.0f));
+            const float dy = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(A.z)), 1.0f));
+            const float dz = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(A.w)), 1.0f));
+            float nx = __fadd_rn(old.x, dx), ny = __fadd_rn(old.y, dy), nz = __fadd_rn(old.z, dz);
+            if (nx < 0.f) nx = __fadd_rn(nx, P.g.Lx);
+            if (nx >= P.g.Lx) nx = __fsub_rn(nx, P.g.Lx);
+            if (ny < 0.f) ny = __fadd_rn(ny, P.g.Ly);
+            if (ny >= P.g.Ly) ny = __fsub_rn(ny, P.g.Ly);
+            if (P.g.periodic_z) {
+                if (nz < 0.f) nz = __fadd_rn(nz, P.g.Lz);
+                if (nz >= P.g.Lz) nz = __fsub_rn(nz, P.g.Lz);
+            } else if (nz < P.g.z_lo || nz > P.g.z_hi) {
+                status = 2;
+            }
+            q0x = nx; q0y = ny; q0z = nz;
+            q1x = old.x; q1y = old.y; q1z = old.z;
+            nq = 2;
+        }
+    } else if (type == 1) {
+        if (N == P.nmax) {
+            status = 1;
+        } else {
+            float nx = __fmul_rn(P.g.Lx, u24(A.y));
+            float ny = __fmul_rn(P.g.Ly, u24(A.z));
+            float nz = __fadd_rn(P.g.z_lo, __fmul_rn(P.g.height, u24(A.w)));
+            if (nx >= P.g.Lx) nx = __fsub_rn(nx, P.g.Lx);
+            if (ny >= P.g.Ly) ny = __fsub_rn(ny, P.g.Ly);
+            if (P.g.periodic_z && nz >= P.g.Lz) nz = __fsub_rn(nz, P.g.Lz);
+            q0x = q1x = nx; q0y = q1y = ny; q0z = q1z = nz;
+        }
+    } else {
+        if (N == 0) {
+            status = 1;
+        } else {
+            idx = (int)(((unsigned long long)B.x * (unsigned)N) >> 32);
+            const float4 old = S.pos[idx];
+            q0x = q1x = old.x; q0y = q1y = old.y; q0z = q1z = old.z;
+            sgn0 = -1;
+        }
+    }
+
+    Fix3 acc{0, 0, 0};
+    if (status == 0) {
+        const int skip = type == 1 ? -1 : idx;
+        const Cell3 c0 = cell3_of(P, q0x, q0y, q0z);
+        const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
+        const bool same = c0.x == c1.x && c0.y == c1.y && c0.z == c1.z;
+        if (nq == 2 && same) {
+            mobile_pass<2>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, 1, acc, n_in, n_cand, overlap, lane, warp);
+        } else {
+            // one pass per query: query 0 with its sign, then (a displacement
+            // across cells) the old position with -1
+            for (int pass = 0; pass < nq; ++pass) {
+                const float px = pass ? q1x : q0x, py = pass ? q1y : q0y, pz = pass ? q1z : q0z;
+                int ovp = 0;
+                mobile_pass<1>(P, S, pass ? c1 : c0, px, py, pz, px, py, pz, skip, pass ? -1 : sgn0, acc, n_in,
+                               n_cand, ovp, lane, warp);
+                if (pass == 0) overlap |= ovp;
+            }
+        }
+        const bool s0 = near_surface(P, q0z);
+        const bool s1 = nq == 2 && near_surface(P, q1z);
+        const int col0 = surface_col(P, q0x, q0y);
+        const int col1 = nq == 2 ? surface_col(P, q1x, q1y) : col0;
+        if (s0 && s1 && col0 == col1) {
+            surface_pass<2>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, 1, acc, n_in, n_cand, overlap, lane);
+        } else {
+            for (int pass = 0; pass < nq; ++pass) {
+                if (!(pass ? s1 : s0)) continue;
+                const float px = pass ? q1x : q0x, py = pass ? q1y : q0y, pz = pass ? q1z : q0z;
+                int ovp = 0;
+                surface_pass<1>(P, pass ? col1 : col0, px, py, pz, px, py, pz, pass ? -1 : sgn0, acc, n_in, n_cand,
+                                ovp, lane);
+                if (pass == 0) overlap |= ovp;
+            }
+        }
+        if (type == 2) overlap = 0;   // the old position of a particle never overlaps
+    }
+    const int big = (int)__reduce_add_sync(FULL, (unsigned)acc.big);
+    const int hi = (int)__reduce_add_sync(FULL, (unsigned)acc.hi);
+    const int lo = (int)__reduce_add_sync(FULL, (unsigned)acc.lo);
+    const int ovl = __any_sync(FULL, overlap) ? 1 : 0;
+    const int npairs = (int)__reduce_add_sync(FULL, (unsigned)(n_in - n_in0));
+    if (lane == 0) {
+        MoveRes r;
+        r.type = type;
+        r.status = status;
+        r.idx = idx;
+        r.n_eval = N;
+        r.big = big;
+        r.hi = hi;
+        r.lo = lo;
+        r.flags = ovl | (npairs << 1);
+        r.q0x = q0x; r.q0y = q0y; r.q0z = q0z;
+        r.q1x = q1x; r.q1y = q1y; r.q1z = q1z;
+        r.dec = (status == 0 && !ovl) ? pretest(sf, type, N, big, hi, lo, B.y) : 0;
+        *out = r;
+    }
+}
+
+// Squared minimum-image distance in binary32 (periodic axes per geometry).
+__device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay, float az, float bx, float by,
+                                       float bz) {
+    const float dx = min_image_exact(ax, bx, P.g.Lx, P.g.hLx);
+    const float dy = min_image_exact(ay, by, P.g.Ly, P.g.hLy);
+    const float dz = P.g.periodic_z ? min_image_exact(az, bz, P.g.Lz, P.g.hLz) : __fsub_rn(az, bz);
+    return r2_of(dx, dy, dz);
+}
+
+template <int K, bool TRACE>
+__global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int w = blockIdx.x;
     if (w >= P.S) return;
-    const WalkerSmem W = carve(smem + size_t(warp) * P.smem_per_walker, P);
+    const WalkerSmem S = carve<K>(smem, P);
 
     int N = P.n[w];
     long long E = P.efix[w];
     const int s = P.state_of_walker[w];
-    const double beta = P.beta[s], c_ins = P.c_ins[s], c_del = P.c_del[s];
+    const StateF sf{P.beta_f[s], P.c_ins_f[s], P.c_del_f[s]};
     float4* gpos = P.pos + size_t(w) * P.nmax;
 
     // 1. stage positions with a bulk copy
     if (N > 0) {
-        if (lane == 0) {
-            mbar_init(W.bar);
-            bulk_load(W.pos, gpos, uint32_t(N) * 16u, W.bar);
+        if (threadIdx.x == 0) {
+            mbar_init(S.bar);
+            bulk_load(S.pos, gpos, uint32_t(N) * 16u, S.bar);
         }
-        __syncwarp();
-        bool ok = mbar_wait_bounded(W.bar);
-        ok = __all_sync(FULL, ok);
-        if (!ok) {
-            if (lane == 0) atomicOr(P.error, ERR_TIMEOUT);
-            mbar_wait_bounded(W.bar);  // give the copy in flight one more bounded chance
+        group_sync<K>();
+        const bool ok = mbar_wait_bounded(S.bar);
+        const bool all_ok = (K == 1) ? (__all_sync(FULL, ok) != 0) : (__syncthreads_and(ok) != 0);
+        if (!all_ok) {
+            if (threadIdx.x == 0) atomicOr(P.error, ERR_TIMEOUT);
+            mbar_wait_bounded(S.bar);  // one more bounded chance for the copy in flight
             return;
         }
     }
     // 2. cell list
-    build_cells(P, W, N, lane);
+    if (warp == 0) build_cells(P, S, N, lane);
+    if (threadIdx.x == 0) *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}};
+    group_sync<K>();
 
-    long long tr0 = 0, tr1 = 0, tr2 = 0, ac0 = 0, ac1 = 0, ac2 = 0;
     int n_in = 0, n_cand = 0;
-    unsigned long long om = 0, eo = 0;
-    double m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-    const int cap = P.cg.cap;
+    const int total_moves = P.n_sweeps * P.mps;
+    const float rc_guard = P.g.rc2 * 1.0004f + 1e-6f;   // a little beyond rc, conservatively
+    int filled = 0;   // moves whose Philox blocks are in the ring
+    int m0 = 0;       // first move of the round
 
-    for (int ts = 0; ts < P.n_sweeps; ++ts) {
-        const uint32_t t = P.t0 + uint32_t(ts);
-        for (int kb = 0; kb < P.mps; kb += 32) {
-            const int k_lane = kb + lane;
-            U4 A{0, 0, 0, 0}, B{0, 0, 0, 0};
-            if (k_lane < P.mps) {
-                A = philox(uint32_t(k_lane), t, uint32_t(w), 0u, P.key0, P.key1);
-                B = philox(uint32_t(k_lane), t, uint32_t(w), 1u, P.key0, P.key1);
-            }
-            const int kn = min(32, P.mps - kb);
-            for (int kk = 0; kk < kn; ++kk) {
-                const uint32_t a0 = __shfl_sync(FULL, A.x, kk), a1 = __shfl_sync(FULL, A.y, kk);
-                const uint32_t a2 = __shfl_sync(FULL, A.z, kk), a3 = __shfl_sync(FULL, A.w, kk);
-                const uint32_t b0 = __shfl_sync(FULL, B.x, kk), b1 = __shfl_sync(FULL, B.y, kk);
-                const uint32_t b2 = __shfl_sync(FULL, B.z, kk);
-                const int type = (unsigned long long)a0 < P.th_disp ? 0 : ((b2 >> 31) == 0u ? 2 : 1);
-                int status = 0, idx = -1, overlap = 0, n_in0 = n_in;
-                long long dfix = 0;
-                float nx = 0.f, ny = 0.f, nz = 0.f;
-                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
-                double la = 0.0;
-                if (type == 0) {
-                    if (N == 0) {
-                        status = 1;
-                    } else {
-                        idx = (int)(((unsigned long long)b0 * (unsigned)N) >> 32);
-                        old = W.pos[idx];
-                        const float dx = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(a1)), 1.0f));
-                        const float dy = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(a2)), 1.0f));
-                        const float dz = __fmul_rn(P.max_disp, __fsub_rn(__fmul_rn(2.0f, u24(a3)), 1.0f));
-                        nx = __fadd_rn(old.x, dx);
-                        ny = __fadd_rn(old.y, dy);
-                        nz = __fadd_rn(old.z, dz);
-                        if (nx < 0.f) nx = __fadd_rn(nx, P.g.Lx);
-                        if (nx >= P.g.Lx) nx = __fsub_rn(nx, P.g.Lx);
-                        if (ny < 0.f) ny = __fadd_rn(ny, P.g.Ly);
-                        if (ny >= P.g.Ly) ny = __fsub_rn(ny, P.g.Ly);
-                        if (P.g.periodic_z) {
-                            if (nz < 0.f) nz = __fadd_rn(nz, P.g.Lz);
-                            if (nz >= P.g.Lz) nz = __fsub_rn(nz, P.g.Lz);
-                        } else if (nz < P.g.z_lo || nz > P.g.z_hi) {
-                            status = 2;
-                        }
-                        if (status == 0) {
-                            dfix = energy_diff(P, W, old, nx, ny, nz, idx, n_in, n_cand, overlap, lane);
-                            dfix = warp_sum_ll(dfix);
-                            la = -beta * ((double)dfix * kFixUnit);
-                        }
-                    }
-                } else if (type == 1) {
-                    if (N == P.nmax) {
-                        status = 1;
-                    } else {
-                        idx = N;
-                        nx = __fmul_rn(P.g.Lx, u24(a1));
-                        ny = __fmul_rn(P.g.Ly, u24(a2));
-                        nz = __fadd_rn(P.g.z_lo, __fmul_rn(P.g.height, u24(a3)));
-                        if (nx >= P.g.Lx) nx = __fsub_rn(nx, P.g.Lx);
-                        if (ny >= P.g.Ly) ny = __fsub_rn(ny, P.g.Ly);
-                        if (P.g.periodic_z && nz >= P.g.Lz) nz = __fsub_rn(nz, P.g.Lz);
-                        dfix = warp_sum_ll(energy_one(P, W, nx, ny, nz, -1, n_in, n_cand, overlap, lane));
-                        la = c_ins - P.ln_tab[N + 1] - beta * ((double)dfix * kFixUnit);
-                    }
-                } else {
-                    if (N == 0) {
-                        status = 1;
-                    } else {
-                        idx = (int)(((unsigned long long)b0 * (unsigned)N) >> 32);
-                        old = W.pos[idx];
-                        int ov = 0;
-                        dfix = -warp_sum_ll(energy_one(P, W, old.x, old.y, old.z, idx, n_in, n_cand, ov, lane));
-                        la = c_del + P.ln_tab[N] - beta * ((double)dfix * kFixUnit);
-                    }
+    while (m0 < total_moves) {
+        // 3a. Philox blocks of the next 32 moves, drawn by all lanes at once
+        if (m0 + K > filled) {
+            for (int q = threadIdx.x; q < 64; q += 32 * K) {
+                const int m = filled + (q >> 1);
+                if (m < total_moves) {
+                    const int ts = m / P.mps;
+                    const U4 v = philox(uint32_t(m - ts * P.mps), P.t0 + uint32_t(ts), uint32_t(w), uint32_t(q & 1),
+                                        P.key0, P.key1);
+                    S.rng[2 * (m % kRing) + (q & 1)] = make_uint4(v.x, v.y, v.z, v.w);
                 }
-                overlap = __any_sync(FULL, overlap);
+            }
+            filled += 32;
+            group_sync<K>();
+        }
+        // 3b. evaluate moves m0 .. m0 + K - 1 in parallel, one warp each
+        const int mj = m0 + warp;
+        if (mj < total_moves) evaluate_move(P, S, sf, mj, N, n_in, n_cand, lane, warp, S.res + warp);
+        group_sync<K>();
+
+        // 4. commit in order (thread 0)
+        if (threadIdx.x == 0) {
+            int committed = 0;
+            bool any_acc = false, n_changed = false;
+            float chx[2 * K], chy[2 * K], chz[2 * K];   // positions changed by accepted moves
+            int nch = 0;
+            for (int j = 0; j < K && m0 + j < total_moves; ++j) {
+                const MoveRes r = S.res[j];
+                const int m = m0 + j;
+                // is the evaluation still the one the sequential chain would make?
+                if (any_acc) {
+                    bool valid = true;
+                    if (n_changed && r.type != 1) valid = false;                    // index of N picked
+                    if (r.type == 1 && r.status == 1 && N != P.nmax) valid = false;  // no longer full
+                    // a changed position within rc of a query point: the energy
+                    // change would differ; the old position of a displacement is
+                    // checked whatever its status, since its particle may have moved
+                    if (valid && (r.status == 0 || (r.type == 0 && r.status == 2))) {
+                        for (int c = 0; c < nch; ++c) {
+                            if (r.status == 0 && dist2(P, chx[c], chy[c], chz[c], r.q0x, r.q0y, r.q0z) < rc_guard)
+                                valid = false;
+                            if (r.type == 0 && dist2(P, chx[c], chy[c], chz[c], r.q1x, r.q1y, r.q1z) < rc_guard)
+                                valid = false;
+                        }
+                    }
+                    if (!valid) break;
+                }
+                const uint4 B = S.rng[2 * (m % kRing) + 1];
+                int status = r.status;
+                if (r.type == 1 && N == P.nmax) status = 1;    // became full in this round
+                const long long dfix = fix_value(r.big, r.hi, r.lo);
                 // capacity of the destination cell
                 int c_new = -1;
-                if (status == 0 && type != 2) {
-                    c_new = cell_of(P, nx, ny, nz);
-                    const bool same = type == 0 && c_new == cell_bits(old.w);
-                    if (!same && W.cnt[c_new] >= cap) {
+                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r.type != 1 && status != 1) old = S.pos[r.idx];
+                if (status == 0 && r.type != 2) {
+                    c_new = cell_of(P, r.q0x, r.q0y, r.q0z);
+                    const bool stay = r.type == 0 && c_new == cell_bits(old.w);
+                    if (!stay && S.cnt[c_new] >= P.cg.cap) {
                         status = 3;
-                        if (lane == 0) atomicOr(P.error, ERR_CAPACITY);
+                        atomicOr(P.error, ERR_CAPACITY);
                     }
                 }
-                // acceptance: ln u < la, binary32 pre-test outside a 1e-4 band
+                // 5. acceptance: ln u < ln alpha (pre-tested in the evaluating warp
+                // when N is still the one it saw)
                 int accepted = 0;
-                double ln_u = 0.0;
-                if (status == 0 && !overlap) {
-                    if (la >= 0.0) {
-                        accepted = 1;
-                    } else {
-                        const float lf = __logf(((float)b1 + 0.5f) * 2.3283064365386963e-10f);
-                        if ((double)lf < la - 1e-4) accepted = 1;
-                        else if ((double)lf > la + 1e-4) accepted = 0;
-                        else accepted = log(((double)b1 + 0.5) * 2.3283064365386963e-10) < la;
+                double la = 0.0;
+                const bool ovl = (r.flags & 1) != 0;
+                if (status == 0 && !ovl) {
+                    const int dec = N == r.n_eval ? r.dec : pretest(sf, r.type, N, r.big, r.hi, r.lo, B.y);
+                    accepted = dec == 1;
+                    if (dec == 2 || TRACE) {
+                        double c = 0.0;
+                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
+                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N];
+                        la = c - P.beta[s] * ((double)dfix * kFixUnit);
+                        if (dec == 2) accepted = (log((double)B.y + 0.5) + kLn2m32) < la;
                     }
                 }
-                if (TRACE) ln_u = log(((double)b1 + 0.5) * 2.3283064365386963e-10);
+                const int n_before = N;
                 if (accepted) {
-                    if (lane == 0) {
-                        if (type == 0) {
-                            const int c_old = cell_bits(old.w);
-                            if (c_new == c_old) {
-                                W.pos[idx] = make_float4(nx, ny, nz, old.w);
-                            } else {
-                                cell_remove(P, W, old.w);
-                                const int sl = W.cnt[c_new];
-                                W.slots[c_new * cap + sl] = (uint16_t)idx;
-                                W.cnt[c_new] = (uint16_t)(sl + 1);
-                                W.pos[idx] = packed(nx, ny, nz, c_new, sl);
-                            }
-                        } else if (type == 1) {
-                            const int sl = W.cnt[c_new];
-                            W.slots[c_new * cap + sl] = (uint16_t)N;
-                            W.cnt[c_new] = (uint16_t)(sl + 1);
-                            W.pos[N] = packed(nx, ny, nz, c_new, sl);
+                    const int cap = P.cg.cap;
+                    if (r.type == 0) {
+                        const int c_old = cell_bits(old.w);
+                        if (c_new == c_old) {
+                            S.pos[r.idx] = make_float4(r.q0x, r.q0y, r.q0z, old.w);
                         } else {
-                            cell_remove(P, W, old.w);
-                            const int last = N - 1;
-                            if (idx != last) {
-                                const float4 pl = W.pos[last];
-                                W.pos[idx] = pl;
-                                W.slots[cell_bits(pl.w) * cap + slot_bits(pl.w)] = (uint16_t)idx;
-                            }
+                            cell_remove(P, S, old.w);
+                            const int sl = S.cnt[c_new];
+                            S.slots[c_new * cap + sl] = (uint16_t)r.idx;
+                            S.cnt[c_new] = (uint16_t)(sl + 1);
+                            S.pos[r.idx] = packed(r.q0x, r.q0y, r.q0z, c_new, sl);
                         }
+                        chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
+                        chx[nch] = r.q1x; chy[nch] = r.q1y; chz[nch] = r.q1z; ++nch;
+                    } else if (r.type == 1) {
+                        const int sl = S.cnt[c_new];
+                        S.slots[c_new * cap + sl] = (uint16_t)N;
+                        S.cnt[c_new] = (uint16_t)(sl + 1);
+                        S.pos[N] = packed(r.q0x, r.q0y, r.q0z, c_new, sl);
+                        chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
+                        n_changed = true;
+                    } else {
+                        cell_remove(P, S, old.w);
+                        const int last = N - 1;
+                        if (r.idx != last) {
+                            const float4 pl = S.pos[last];
+                            S.pos[r.idx] = pl;
+                            S.slots[cell_bits(pl.w) * cap + slot_bits(pl.w)] = (uint16_t)r.idx;
+                        }
+                        chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
+                        n_changed = true;
                     }
-                    __syncwarp();
+                    any_acc = true;
                     E += dfix;
-                    N += (type == 1) - (type == 2);
+                    N += (r.type == 1) - (r.type == 2);
                 }
-                tr0 += type == 0;
-                tr1 += type == 1;
-                tr2 += type == 2;
-                ac0 += accepted && type == 0;
-                ac1 += accepted && type == 1;
-                ac2 += accepted && type == 2;
+                WalkerStats& st = *S.stats;
+                st.tr[r.type] += 1;
+                st.ac[r.type] += accepted;
+                st.pairs += (unsigned)(r.flags >> 1);
+                const int ts = m / P.mps, k = m - ts * P.mps;
                 if (TRACE) {
-                    const int np = warp_sum_i(n_in - n_in0);
-                    if (lane == 0) {
-                        regc_move_record r;
-                        r.type = type;
-                        r.index = status == 1 ? 0 : idx;
-                        r.accepted = accepted;
-                        r.status = status == 3 ? 0 : status;
-                        r.dE = status == 0 || status == 3 ? (double)dfix * kFixUnit : 0.0;
-                        r.log_alpha = overlap ? -INFINITY : la;
-                        r.ln_u = ln_u;
-                        r.sum_abs = 0.0;
-                        r.band = 0.0;
-                        r.n_pairs = np;
-                        r.pad = 0;
-                        P.trace[(size_t(w) * P.n_sweeps + ts) * P.mps + kb + kk] = r;
-                    }
+                    regc_move_record t;
+                    t.type = r.type;
+                    t.index = status == 1 ? 0 : (r.type == 1 ? n_before : r.idx);
+                    t.accepted = accepted;
+                    t.status = status == 3 ? 0 : status;
+                    t.dE = (status == 0 || status == 3) ? (double)dfix * kFixUnit : 0.0;
+                    t.log_alpha = (status == 0 || status == 3) ? (ovl ? -INFINITY : la) : 0.0;
+                    t.ln_u = log((double)B.y + 0.5) + kLn2m32;
+                    t.sum_abs = 0.0;
+                    t.band = 0.0;
+                    t.n_pairs = r.flags >> 1;
+                    t.pad = 0;
+                    P.trace[(size_t(w) * P.n_sweeps + ts) * P.mps + k] = t;
                 }
+                // 6. observe once per sweep into the current state's histograms
+                if (k == P.mps - 1) {
+                    atomicAdd(&P.hN[size_t(s) * (P.nmax + 1) + N], 1ull);   // fire-and-forget reduction
+                    st.om += 1;
+                    st.mN += N;
+                    st.mN2 += (long long)N * N;
+                    st.mE += E;
+                    const double e = (double)E * kFixUnit;
+                    st.mE2 = fma(e, e, st.mE2);
+                    const long long d = E - P.e_lo_fix;
+                    const long long kb = d >= 0 ? d / P.e_bin_fix : -1;
+                    if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[size_t(N) * P.n_e_bins + (size_t)kb], 1ull);
+                    else st.eo += 1;
+                }
+                ++committed;
             }
+            S.hdr->N = N;
+            S.hdr->E = E;
+            S.hdr->committed = committed;
+            S.stats->rounds += 1;
+            S.stats->evals += min(K, total_moves - m0);
         }
-        // 5. observe once per sweep into the current state's histograms
-        if (lane == 0) {
-            const double e = (double)E * kFixUnit;
-            P.hN[size_t(s) * (P.nmax + 1) + N] += 1ull;
-            om += 1;
-            m0 += (double)N;
-            m1 += (double)N * (double)N;
-            m2 += e;
-            m3 += e * e;
-            const double kb = floor((e - P.e_lo) / P.e_bin);
-            if (kb >= 0.0 && kb < (double)P.n_e_bins) {
-                atomicAdd(&P.hNE[size_t(N) * P.n_e_bins + (size_t)kb], 1ull);
-            } else {
-                eo += 1;
-            }
-        }
+        group_sync<K>();
+        N = S.hdr->N;
+        E = S.hdr->E;
+        m0 += S.hdr->committed;
+        group_sync<K>();   // the header and results are rewritten by the next round
     }
 
-    // 6. write back
-    __syncwarp();
-    for (int j = lane; j < N; j += 32) gpos[j] = W.pos[j];
-    const int sum_in = warp_sum_i(n_in), sum_cand = warp_sum_i(n_cand);
-    if (lane == 0) {
+    // 7. write back
+    for (int j = threadIdx.x; j < N; j += 32 * K) gpos[j] = S.pos[j];
+    // candidate distances evaluated (all evaluations, kept or not)
+    const unsigned sum_cand = __reduce_add_sync(FULL, (unsigned)n_cand);
+    if (lane == 0) atomicAdd(&P.pair_counts[1], (unsigned long long)sum_cand);
+    if (threadIdx.x == 0) {
+        const WalkerStats& st = *S.stats;
+        atomicAdd(&P.pair_counts[0], st.pairs);
+        atomicAdd(&P.pair_counts[2], st.rounds);
+        atomicAdd(&P.pair_counts[3], st.evals);
         P.n[w] = N;
         P.efix[w] = E;
-        P.omega[s] += om;
-        P.e_out[s] += eo;
-        double* m = P.moments + size_t(s) * 4;
-        m[0] += m0;
-        m[1] += m1;
-        m[2] += m2;
-        m[3] += m3;
+        P.omega[s] += st.om;
+        P.e_out[s] += st.eo;
+        double* mm = P.moments + size_t(s) * 4;
+        mm[0] += (double)st.mN;
+        mm[1] += (double)st.mN2;
+        mm[2] += (double)st.mE * kFixUnit;
+        mm[3] += st.mE2;
         long long* mc = P.move_counts + size_t(w) * 6;
-        mc[0] += tr0;
-        mc[1] += ac0;
-        mc[2] += tr1;
-        mc[3] += ac1;
-        mc[4] += tr2;
-        mc[5] += ac2;
-        atomicAdd(&P.pair_counts[0], (unsigned long long)sum_in);
-        atomicAdd(&P.pair_counts[1], (unsigned long long)sum_cand);
+        for (int k = 0; k < 3; ++k) {
+            mc[2 * k] += st.tr[k];
+            mc[2 * k + 1] += st.ac[k];
+        }
     }
 }
 
@@ -610,51 +785,63 @@ __global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ Swe
     if (w >= P.S) return;
     const int N = P.n[w];
     const float4* pos = P.pos + size_t(w) * P.nmax;
-    long long acc = 0;
+    Fix3 acc{0, 0, 0};
+    long long total = 0;
     int n_in = 0, overlap = 0;
     float dx, dy, dz;
     for (int i = 0; i < N; ++i) {
         const float4 pi = pos[i];
         for (int j = i + 1 + lane; j < N; j += 32) {
             disp_exact(P.g, pi, pos[j], dx, dy, dz);
-            acc += pair_fix_d(dx, dy, dz, P.g, P.gg, n_in, overlap);
+            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, P.gg, n_in, overlap), 1);
         }
         for (int a = lane; a < P.st.n_all; a += 32) {
             const float4 at = P.st.all[a];
             disp_exact(P.g, pi, at, dx, dy, dz);
-            acc += pair_fix_d(dx, dy, dz, P.g, surf_tab(P, (int)at.w), n_in, overlap);
+            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, surf_tab(P, (int)at.w), n_in, overlap), 1);
         }
+        // fold into 64 bits often enough that the int32 parts cannot overflow
+        total += fix_value(acc.big, acc.hi, acc.lo);
+        acc = Fix3{0, 0, 0};
     }
-    acc = warp_sum_ll(acc);
+    total = warp_sum_ll(total);
     overlap = __any_sync(FULL, overlap);
     if (lane == 0) {
-        out[w] = acc;
+        out[w] = total;
         if (overlap && check_overlap) atomicOr(P.error, ERR_OVERLAP);
     }
 }
 
-}  // namespace
-
-size_t sweep_smem_per_walker(int nmax, int ncell, int cap) {
-    return align16(size_t(nmax) * 16) + 16 + 32 * sizeof(StEntry) + align16(size_t(ncell) * 2) +
-           align16(size_t(ncell) * cap * 2);
-}
-
-cudaError_t launch_sweep(const SweepParams& P, int wpc, cudaStream_t s) {
-    if (P.n_sweeps <= 0) return cudaSuccess;
-    const size_t smem = size_t(wpc) * P.smem_per_walker;
-    const int grid = (P.S + wpc - 1) / wpc;
+template <int K>
+cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
+    const size_t smem = smem_bytes(P.nmax, P.cg.ncell, P.cg.cap, K);
     cudaError_t err;
     if (P.trace) {
-        err = cudaFuncSetAttribute(sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<true><<<grid, 32 * wpc, smem, s>>>(P);
+        sweep_kernel<K, true><<<P.S, 32 * K, smem, s>>>(P);
     } else {
-        err = cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<false><<<grid, 32 * wpc, smem, s>>>(P);
+        sweep_kernel<K, false><<<P.S, 32 * K, smem, s>>>(P);
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker) {
+    return smem_bytes(nmax, ncell, cap, warps_per_walker);
+}
+
+cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
+    if (P.n_sweeps <= 0) return cudaSuccess;
+    switch (P.warps_per_walker) {
+        case 1: return launch_k<1>(P, s);
+        case 2: return launch_k<2>(P, s);
+        case 4: return launch_k<4>(P, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overlap, cudaStream_t s) {

@@ -137,7 +137,7 @@ class Regc:
     def counters(self):
         mv = np.zeros((self.S, 3, 2), np.int64)
         ex = np.zeros((self.S, 4, 2), np.int64)
-        pr = np.zeros(2, np.int64)
+        pr = np.zeros(4, np.int64)
         check(_lib.lib().regc_counters(self._h, _p(mv, C.c_int64), _p(ex, C.c_int64), _p(pr, C.c_int64)),
               "regc_counters")
         return mv, ex, pr
