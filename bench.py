@@ -70,6 +70,22 @@ def combine_rank_results(times_ms, moves_per_rank):
     return sum(moves_per_rank) / (t / 1e3), t
 
 
+def job_throughput(local_ms, local_moves, world, device):
+    """Whole-job throughput across the process group: every rank contributes
+    its moves and timed milliseconds; the job time is the slowest rank's.
+    Returns (moves/s over all ranks, max ms)."""
+    if world == 1:
+        return combine_rank_results([local_ms], [local_moves])
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(local_moves)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    tmax = float(t.item())
+    return float(m.item()) / (tmax / 1e3), tmax
+
+
 def fp32_peak():
     """FP32 ALU peak: measured if the peaks file has one, else unit counts x clock."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -227,13 +243,7 @@ def run_own(args):
     mv1, _, pr1 = g.counters()
     total_ms = float(sum(step_ms))
     moves = p.S * SWEEPS_PER_STEP * p.moves_per_sweep * K
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_max = float(t.item())
-    else:
-        total_max = total_ms
-    value = moves * world / (total_max / 1e3)
+    value, total_max = job_throughput(total_ms, moves, world, "cuda")
     accepted = int((mv1[:, :, 1] - mv0[:, :, 1]).sum())
     pairs = int(pr1[0] - pr0[0])
     cand = int(pr1[1] - pr0[1])
