@@ -59,6 +59,8 @@ class _System(C.Structure):
         ("e_lo", C.c_double), ("e_bin", C.c_double),
         ("n_e_bins", C.c_int),
         ("mutation", C.c_int),
+        ("da", C.c_int),
+        ("sur_theta", C.POINTER(C.c_double)),
     ]
 
 
@@ -75,7 +77,8 @@ class _Hist(C.Structure):
 MOVE_DTYPE = np.dtype([
     ("type", np.int32), ("index", np.int32), ("accepted", np.int32), ("status", np.int32),
     ("dE", np.float64), ("log_alpha", np.float64), ("ln_u", np.float64),
-    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("pad", np.int32),
+    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("stage1", np.int32),
+    ("dE_sur", np.float64), ("ln_u1", np.float64),
 ])
 
 _lib = None
@@ -105,6 +108,9 @@ def lib():
         _lib.oracle_sweeps.restype = C.c_int
         _lib.oracle_exchange.argtypes = [sp, C.c_uint32, ip, dp, ip, ip, i64p]
         _lib.oracle_exchange.restype = C.c_int
+        _lib.oracle_surrogate_energy.argtypes = [sp, dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                                 C.c_int, dp]
+        _lib.oracle_surrogate_energy.restype = C.c_double
     return _lib
 
 
@@ -128,7 +134,8 @@ class Oracle:
     state_of_walker [S], walker_of_state [S], sweep counter t, exchange
     counter e, histograms and acceptance counters."""
 
-    def __init__(self, problem, pos=None, n=None, mutation: int = 0, n_threads: int = 0):
+    def __init__(self, problem, pos=None, n=None, mutation: int = 0, n_threads: int = 0,
+                 surrogate=None):
         self.p = problem
         S, nmax = problem.S, problem.nmax
         self._kT = np.ascontiguousarray(problem.kT, np.float64)
@@ -160,6 +167,11 @@ class Oracle:
         s.seed = int(problem.seed)
         s.e_lo, s.e_bin, s.n_e_bins = problem.e_lo, problem.e_bin, problem.n_e_bins
         s.mutation = int(mutation)
+        self._theta = None
+        if surrogate is not None:
+            self._theta = np.ascontiguousarray(surrogate, np.float64)
+            s.da = 1
+            s.sur_theta = _ptr(self._theta, C.c_double)
         self.sys = s
         self.n_threads = int(n_threads)
         self.pos = np.zeros((S, nmax, 3)) if pos is None else np.array(pos, np.float64).reshape(S, nmax, 3)
@@ -197,6 +209,17 @@ class Oracle:
                                          float(xyz[0]), float(xyz[1]), float(xyz[2]), int(skip),
                                          C.byref(sa), C.byref(band), C.byref(npairs))
         return e, sa.value, band.value, npairs.value
+
+    def surrogate_energy(self, w, xyz, skip=-1):
+        """Surrogate energy e~ of a particle at xyz in walker w, and its features."""
+        if self._theta is None:
+            raise ValueError("no surrogate weights")
+        pos = np.ascontiguousarray(self.pos[w])
+        feat = np.zeros(16)
+        e = lib().oracle_surrogate_energy(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]),
+                                          float(xyz[0]), float(xyz[1]), float(xyz[2]), int(skip),
+                                          _ptr(feat, C.c_double))
+        return e, feat
 
     def log_alpha(self, move_type, state, n, dE):
         return lib().oracle_log_alpha(C.byref(self.sys), move_type, state, n, dE)

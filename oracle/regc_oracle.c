@@ -30,7 +30,17 @@
  *   16  pair potential: the factor 4 dropped
  *   32  minimum image not applied along y
  *   64  removal: energy taken of particle i but particle (i+1) mod N removed
+ *   128 delayed acceptance: stage 2 without the -dE~ correction
+ *
+ * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
+ * is first screened with the surrogate energy change dE~ (stage 1: accept iff
+ * ln u1 < the acceptance log ratio with dE~ in place of dE, u1 from B3); a
+ * move that passes is accepted iff ln u2 < -beta (dE - dE~) (stage 2, u2 from
+ * B1).  dE~ is built from the surrogate energy e~ of the moved particle at its
+ * new and old positions, so it changes sign under the reverse move and the
+ * chain keeps the distribution of Eq. Ngrand for any network weights.
  */
+#define _GNU_SOURCE
 #include "regc_oracle.h"
 
 #include <math.h>
@@ -175,6 +185,63 @@ double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
             e += oracle_phi(sys, 0, 0, pair_r2(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2]));
         }
     }
+    return e;
+}
+
+/* ------------------------------------------------------------- surrogate */
+
+#define SUR_NF 16
+#define SUR_NH 64
+
+static double silu(double x) { return x / (1.0 + exp(-x)); }
+
+/* Surrogate energy e~ of a mobile particle at (x, y, z): 16 Gaussian radial
+ * features over every surface atom and mobile particle j != skip within rc,
+ * G_k = sum_j eps_0j exp(-eta (r_j - c_k)^2) (cos(pi r_j / rc) + 1) / 2 with
+ * c_k = 0.8 + 1.7 k / 15 and eta = 1 / (2 (1.7/15)^2), then the network
+ * 16 -> 64 -> 64 -> 1 with SiLU hidden layers.  feat, if given, receives G. */
+double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int n,
+                               double x, double y, double z, int skip, double *feat)
+{
+    const double rc = sys->rc, width = 1.7 / 15.0, eta = 1.0 / (2.0 * width * width);
+    double G[SUR_NF];
+    for (int k = 0; k < SUR_NF; ++k) G[k] = 0.0;
+    for (int j = -sys->n_surf; j < n; ++j) {
+        const double *r;
+        int t;
+        if (j < 0) {
+            r = sys->surf_xyz + 3 * (j + sys->n_surf);
+            t = sys->surf_type[j + sys->n_surf];
+        } else {
+            if (j == skip) continue;
+            r = pos + 3 * j;
+            t = 0;
+        }
+        double d = sqrt(pair_r2(sys, x, y, z, r[0], r[1], r[2]));
+        if (d >= rc) continue;
+        double fc = 0.5 * (cos(M_PI * d / rc) + 1.0) * sys->eps[0][t];
+        for (int k = 0; k < SUR_NF; ++k) {
+            double c = 0.8 + 1.7 * k / 15.0;
+            G[k] += exp(-eta * (d - c) * (d - c)) * fc;
+        }
+    }
+    if (feat)
+        for (int k = 0; k < SUR_NF; ++k) feat[k] = G[k];
+    const double *W1 = sys->sur_theta, *b1 = W1 + SUR_NF * SUR_NH, *W2 = b1 + SUR_NH;
+    const double *b2 = W2 + SUR_NH * SUR_NH, *W3 = b2 + SUR_NH, *b3 = W3 + SUR_NH;
+    double h1[SUR_NH], h2[SUR_NH];
+    for (int u = 0; u < SUR_NH; ++u) {
+        double z1 = b1[u];
+        for (int k = 0; k < SUR_NF; ++k) z1 += W1[k * SUR_NH + u] * G[k];
+        h1[u] = silu(z1);
+    }
+    for (int v = 0; v < SUR_NH; ++v) {
+        double z2 = b2[v];
+        for (int u = 0; u < SUR_NH; ++u) z2 += W2[u * SUR_NH + v] * h1[u];
+        h2[v] = silu(z2);
+    }
+    double e = b3[0];
+    for (int v = 0; v < SUR_NH; ++v) e += W3[v] * h2[v];
     return e;
 }
 
@@ -342,7 +409,26 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
                                                 &mv.sum_abs, &mv.band, &mv.n_pairs);
                 mv.log_alpha = oracle_log_alpha(sys, 2, state, n, mv.dE);
             }
-            mv.accepted = mv.ln_u < mv.log_alpha;
+            if (sys->da) {
+                /* stage 1 with the surrogate energy change */
+                if (mv.type == 0) {
+                    const double *ri = pos + 3 * i;
+                    mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, i, NULL) -
+                                oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
+                } else if (mv.type == 1) {
+                    mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, -1, NULL);
+                } else {
+                    const double *ri = pos + 3 * i;
+                    mv.dE_sur = -oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
+                }
+                mv.ln_u1 = log(u32_open(B[3]));
+                mv.stage1 = mv.ln_u1 < oracle_log_alpha(sys, mv.type, state, n, mv.dE_sur);
+                /* stage 2: the exact correction */
+                double corr = (sys->mutation & 128) ? 0.0 : mv.dE_sur;
+                mv.accepted = mv.stage1 && mv.ln_u < -beta * (mv.dE - corr);
+            } else {
+                mv.accepted = mv.ln_u < mv.log_alpha;
+            }
             if (mv.accepted) {
                 if (mv.type == 0) {
                     double *ri = pos + 3 * i;

@@ -60,6 +60,10 @@ typedef struct {
     /* planted-mistake switches for sensitivity tests of the pins; 0 in all
      * real use (bit meanings in regc_oracle.c) */
     int    mutation;
+    /* delayed acceptance: when da != 0, sur_theta holds the 5313 parameters
+     * of the surrogate network (layout in oracle/surrogate.py) */
+    int           da;
+    const double *sur_theta;
 } oracle_system;
 
 /* One trial move as the oracle executed it. */
@@ -75,7 +79,9 @@ typedef struct {
     double  sum_abs;    /* sum of 4 eps [(s/r)^12 + (s/r)^6] over pairs entering dE */
     double  band;       /* sum of |phi(rc)| over pairs with r^2 within 4e-6 rc^2 of rc^2 */
     int32_t n_pairs;    /* pairs with r < rc entering dE */
-    int32_t pad;
+    int32_t stage1;     /* delayed acceptance: 1 if the surrogate stage accepted */
+    double  dE_sur;     /* delayed acceptance: surrogate energy change */
+    double  ln_u1;      /* delayed acceptance: ln of the stage-1 uniform */
 } oracle_move;
 
 /* Histograms filled once per sweep, at the walker's current state. */
@@ -96,6 +102,8 @@ double oracle_particle_energy(const oracle_system *sys, const double *pos, int n
                               double x, double y, double z, int skip,
                               double *sum_abs, double *band, int *n_pairs);
 double oracle_total_energy(const oracle_system *sys, const double *pos, int n);
+double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int n,
+                               double x, double y, double z, int skip, double *feat);
 double oracle_log_alpha(const oracle_system *sys, int type, int state, int n, double dE);
 double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
                                  int na, int nb, double ea, double eb);
