@@ -121,13 +121,19 @@ typedef struct {
     int32_t accepted;    /* 1 if accepted                                          */
     int32_t status;      /* 0 energy evaluated, 1 rejected at N = 0 or N = nmax,
                             2 displacement left [z_lo, z_hi]                       */
-    double  dE;          /* energy change of the move (status 0)                   */
-    double  log_alpha;   /* ln of the acceptance ratio (status 0)                  */
+    double  dE;          /* energy change of the move (status 0); NaN when delayed
+                            acceptance rejected the move at stage 1 (dE is then
+                            never computed)                                        */
+    double  log_alpha;   /* ln of the plain acceptance ratio (status 0), -inf for a
+                            move inside the hard-core guard, NaN with dE           */
     double  ln_u;        /* ln of the acceptance uniform                           */
     double  sum_abs;     /* unused by the GPU path (0)                             */
     double  band;        /* unused by the GPU path (0)                             */
     int32_t n_pairs;     /* pairs with r < rc that entered dE                      */
-    int32_t pad;
+    int32_t stage1;      /* delayed acceptance: 1 if the surrogate stage accepted
+                            (always 1 otherwise)                                   */
+    double  dE_sur;      /* delayed acceptance: surrogate energy change            */
+    double  ln_u1;       /* ln of the stage-1 uniform (from B3)                    */
 } regc_move_record;
 
 /* Create a handle: copies the problem statement, builds the surface lookup
@@ -202,10 +208,11 @@ REGC_API regc_status regc_check_energy(regc_handle *h, double *max_drift);
 
 /* Counters (host buffers, any may be NULL): moves [S walkers][3 types][trials,
  * accepts]; exchanges [S lower states][4 directions][attempts, accepts];
- * pairs [4]: pairs within rc of the committed moves, candidate pairs whose
+ * pairs [6]: pairs within rc of the committed moves, candidate pairs whose
  * distance was evaluated (including speculative evaluations that were
- * discarded), evaluation rounds, move evaluations -- summed over walkers since
- * the last reset.  Synchronous. */
+ * discarded), evaluation rounds, move evaluations, moves screened by the
+ * surrogate (delayed acceptance), moves that passed the screen -- summed over
+ * walkers since the last reset.  Synchronous. */
 REGC_API regc_status regc_counters(regc_handle *h, int64_t *moves, int64_t *exchanges, int64_t *pairs);
 
 /* MBAR reweighting of the handle's pooled histogram (Sec. II.B).  Solves the
@@ -266,6 +273,86 @@ REGC_API regc_status regc_mbar_solve_static(int S, const double *kT, const doubl
                                             const double *E_b, const double *H_b, double tol,
                                             int max_iter, double *f, double *D, int *iters,
                                             void *cuda_stream);
+
+/* ---------------------------------------------------- learned surrogate
+ *
+ * The paper has no surrogate.  These entry points add a delayed-acceptance
+ * (Christen & Fox 2005) form of the sweep: every evaluated move is first
+ * screened with the surrogate energy change dE~ (stage 1: accept iff
+ * ln u1 < the log acceptance ratio of Sec. II.A.1 / II.A.3 with dE~ in place
+ * of dE, u1 from the fourth word of the move's second Philox block); only a
+ * move that passes gets its exact energy change dE and is accepted iff
+ * ln u2 < -beta (dE - dE~) (stage 2, u2 the plain acceptance uniform).  dE~ is
+ * e~(new) - e~(old) (insertion: e~(new); removal: -e~(old)), antisymmetric
+ * under the reverse move, so the chain keeps the distribution of Eq. Ngrand
+ * whatever the network's weights.
+ *
+ * e~(r) is a 16 -> 64 -> 64 -> 1 network with SiLU hidden layers on 16
+ * Gaussian radial features of the neighbours within rc:
+ *   G_k = sum_j eps_0j exp(-eta (r_j - c_k)^2) (cos(pi r_j / rc) + 1) / 2,
+ *   c_k = 0.8 + 1.7 k / 15 (k = 0..15), eta = 1 / (2 (1.7 / 15)^2).
+ * Parameters: REGC_SURROGATE_PARAMS binary32 values, row-major
+ *   W1 [16][64], b1 [64], W2 [64][64], b2 [64], W3 [64], b3,
+ * z1 = G W1 + b1, h1 = silu(z1), z2 = h1 W2 + b2, e~ = silu(z2) W3 + b3.
+ * The sweep uses an inference copy with the weights rounded to bfloat16
+ * (nearest, ties to even) and the biases in binary32; features and
+ * activations are binary32. */
+#define REGC_SURROGATE_PARAMS 5313
+
+/* Load the surrogate's binary32 parameters theta [REGC_SURROGATE_PARAMS]
+ * (host) as the training master copy, refresh the inference copy and reset
+ * the optimiser's moments and step count.  Allocates the surrogate's device
+ * buffers on first use.  Errors: REGC_EINVAL (NULL or non-finite value). */
+REGC_API regc_status regc_surrogate_set(regc_handle *h, const float *theta);
+
+/* Copy the master parameters to theta [REGC_SURROGATE_PARAMS] (host).
+ * Errors: REGC_EINVAL (no surrogate loaded).  Synchronous. */
+REGC_API regc_status regc_surrogate_get(regc_handle *h, float *theta);
+
+/* Sweep mode: 0 plain Metropolis (the default), 1 delayed acceptance with the
+ * loaded surrogate (one warp per walker).  Errors: REGC_EINVAL (mode 1 with no
+ * surrogate loaded, other modes). */
+REGC_API regc_status regc_set_mode(regc_handle *h, int mode);
+
+/* Surrogate energy e~ of a test particle at each of n_query positions
+ * xyz [n_query][3] (host, inside the region) against every particle of
+ * walker `walker` and every surface atom, nearest periodic image;
+ * e_out [n_query] and, if not NULL, features [n_query][16] (host).
+ * Synchronous. */
+REGC_API regc_status regc_surrogate_eval(regc_handle *h, int walker, int n_query, const float *xyz,
+                                         float *e_out, float *features);
+
+/* Append training rows to the handle's data set, a ring of `capacity` rows
+ * allocated on the first call (later calls pass the same capacity, or 0).
+ * Each walker gives `particles` rows for particles spread evenly over its
+ * index range (features of the particle against all the others and the
+ * surface; target its exact interaction energy) and `probes` rows for
+ * uniform random points of the region (Philox stream 5; target the energy a
+ * test particle there would have); a walker with N = 0 gives probes only.
+ * Targets are clipped from above at e_clip.  *n_rows (may be NULL) receives
+ * the number of rows held.  Asynchronous apart from the count. */
+REGC_API regc_status regc_surrogate_harvest(regc_handle *h, int particles, int probes, float e_clip,
+                                            int capacity, int64_t *n_rows);
+
+/* Copy the data set (X [n][16], y [n], n = rows held, in ring order) to host
+ * buffers of at least `max_rows` rows; *n_rows receives n.  Synchronous. */
+REGC_API regc_status regc_surrogate_dataset(regc_handle *h, int64_t max_rows, float *X, float *y,
+                                            int64_t *n_rows);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * the mean squared error of mini-batches of `batch` rows drawn uniformly from
+ * the data set (Philox stream 6), on the device; then refresh the inference
+ * copy.  loss [steps] (host, may be NULL) receives each step's mini-batch
+ * loss before its update.  Errors: REGC_EINVAL (empty data set, no
+ * surrogate, batch < 1).  Synchronous. */
+REGC_API regc_status regc_surrogate_train(regc_handle *h, int steps, int batch, float lr, float *loss);
+
+/* Stateless: the mean squared error of the network with parameters theta
+ * [REGC_SURROGATE_PARAMS] on n rows X [n][16], y [n] (host) and its gradient
+ * grad [REGC_SURROGATE_PARAMS] (host), computed by the training kernels in
+ * binary32.  Runs on cuda_stream.  Synchronous. */
+REGC_API regc_status regc_surrogate_gradient(int n, const float *theta, const float *X, const float *y,
+                                             float *loss, float *grad, void *cuda_stream);
 
 /* Human-readable name of a status. */
 REGC_API const char *regc_status_string(regc_status s);

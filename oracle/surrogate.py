@@ -62,6 +62,26 @@ def to_bf16(theta) -> np.ndarray:
     return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def weight_mask() -> np.ndarray:
+    """True for the entries of theta that are weights (W1, W2, W3), False for
+    the biases."""
+    m = np.zeros(N_PARAMS, bool)
+    W1, b1, W2, b2, W3, b3 = unpack(np.arange(N_PARAMS, dtype=np.float64))
+    for w in (W1, W2, W3):
+        m[np.asarray(w, np.int64).ravel()] = True
+    return m
+
+
+def inference_params(theta) -> np.ndarray:
+    """The parameters the sampler's network uses: weights rounded to bfloat16,
+    biases rounded to binary32."""
+    theta = np.asarray(theta, np.float64)
+    out = np.asarray(theta, np.float32).astype(np.float64)
+    m = weight_mask()
+    out[m] = to_bf16(theta[m])
+    return out
+
+
 def cutoff(r, rc):
     return np.where(r < rc, 0.5 * (np.cos(np.pi * r / rc) + 1.0), 0.0)
 

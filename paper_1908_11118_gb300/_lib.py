@@ -47,7 +47,8 @@ class MoveRecord(C.Structure):
     _fields_ = [("type", C.c_int32), ("index", C.c_int32), ("accepted", C.c_int32),
                 ("status", C.c_int32), ("dE", C.c_double), ("log_alpha", C.c_double),
                 ("ln_u", C.c_double), ("sum_abs", C.c_double), ("band", C.c_double),
-                ("n_pairs", C.c_int32), ("pad", C.c_int32)]
+                ("n_pairs", C.c_int32), ("stage1", C.c_int32), ("dE_sur", C.c_double),
+                ("ln_u1", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -76,8 +77,18 @@ SIGNATURES = {
                                 C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
     "regc_mbar_query": ([C.c_int, _dp, _dp, C.c_double, C.c_int, _ip, _dp, _dp, _dp, C.c_int,
                          _dp, _dp, _dp, C.c_void_p], C.c_int),
+    "regc_surrogate_set": ([_h, _fp], C.c_int),
+    "regc_surrogate_get": ([_h, _fp], C.c_int),
+    "regc_set_mode": ([_h, C.c_int], C.c_int),
+    "regc_surrogate_eval": ([_h, C.c_int, C.c_int, _fp, _fp, _fp], C.c_int),
+    "regc_surrogate_harvest": ([_h, C.c_int, C.c_int, C.c_float, C.c_int, _lp], C.c_int),
+    "regc_surrogate_dataset": ([_h, C.c_int64, _fp, _fp, _lp], C.c_int),
+    "regc_surrogate_train": ([_h, C.c_int, C.c_int, C.c_float, _fp], C.c_int),
+    "regc_surrogate_gradient": ([C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_void_p], C.c_int),
     "regc_status_string": ([C.c_int], C.c_char_p),
 }
+
+SURROGATE_PARAMS = 5313
 
 _lib = None
 

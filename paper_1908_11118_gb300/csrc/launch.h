@@ -22,4 +22,42 @@ cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overla
 // One collective exchange attempt number e.
 cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s);
 
+// ------------------------------------------------------------ surrogate
+// Device buffers of the surrogate's BF16 inference copy.
+struct SurrogateStore {
+    __nv_bfloat16* w1;   // [64][16]
+    float* b1;           // [64]
+    __nv_bfloat16* w2;   // [64][64]
+    float* b2;           // [64]
+    __nv_bfloat16* w3;   // [64]
+    float* b3;           // [1]
+};
+
+// FP32 master parameters theta[5313] -> the inference copy.
+cudaError_t surrogate_pack(const float* theta, const SurrogateStore& st, cudaStream_t s);
+
+// Surrogate energies e_out[Q] and features f_out[Q][16] of Q positions q
+// (x, y, z) against every particle of walker w and the surface.
+cudaError_t surrogate_eval(const SweepParams& P, int w, int Q, const float4* q, float* e_out, float* f_out,
+                           cudaStream_t s);
+
+// S * (parts + probes) training rows (features X[.][16], targets y = min(e, clip))
+// written to the ring of cap rows starting at row base.
+cudaError_t surrogate_harvest(const SweepParams& P, int parts, int probes, float clip, uint32_t round, float* X,
+                              float* y, int base, int cap, cudaStream_t s);
+
+// Floats of the per-CTA gradient scratch of surrogate_step for n rows.
+size_t surrogate_partial_floats(int n);
+
+// Gradient of the mean squared error of n rows (idx[t] or t) at theta_in into
+// grad (may be null) and the sum of squared residuals into *loss; then, when
+// adam_t > 0, Adam step number adam_t with learning rate lr on theta, m, v.
+cudaError_t surrogate_step(const float* theta_in, const float* X, const float* y, const int* idx, int n,
+                           float* partial, float* grad, float* loss, float* theta, float* m, float* v, int adam_t,
+                           float lr, cudaStream_t s);
+
+// batch uniform row indices in [0, count) for training step `step`.
+cudaError_t surrogate_batch_index(int* idx, int batch, int count, uint32_t step, uint32_t k0, uint32_t k1,
+                                  cudaStream_t s);
+
 }  // namespace regc

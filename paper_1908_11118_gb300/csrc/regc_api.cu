@@ -33,6 +33,17 @@ struct regc_handle {
     int* d_error = nullptr;
     long long* d_fix = nullptr;               // scratch [S] for energy recomputes
     size_t smem_per_walker = 0;
+    // learned surrogate (delayed acceptance)
+    bool has_sur = false;
+    float* d_theta = nullptr;                 // [5313] binary32 master parameters
+    float* d_adam_m = nullptr;
+    float* d_adam_v = nullptr;
+    int adam_t = 0;
+    SurrogateStore sur{};
+    float* d_X = nullptr;                     // data set ring [cap][16]
+    float* d_y = nullptr;                     // [cap]
+    int ds_cap = 0, ds_count = 0, ds_next = 0;
+    uint32_t harvest_round = 0;
 };
 
 namespace {
@@ -311,15 +322,15 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     const double T = 1e6 * std::max(std::max(eps_max, kT_max), 1.0);
     SweepParams& P = h->P;
     P.gg = PairTab{4.0f * pot->eps[0][0], pot->sigma[0][0] * pot->sigma[0][0],
-                   hard_core_r2(pot->eps[0][0], pot->sigma[0][0], T)};
+                   hard_core_r2(pot->eps[0][0], pot->sigma[0][0], T), pot->eps[0][0]};
     for (int t = 0; t < 4; ++t) {
         const int tt = t < nt ? t : 0;
         P.gs[t] = PairTab{4.0f * pot->eps[0][tt], pot->sigma[0][tt] * pot->sigma[0][tt],
-                          hard_core_r2(pot->eps[0][tt], pot->sigma[0][tt], T)};
+                          hard_core_r2(pot->eps[0][tt], pot->sigma[0][tt], T), pot->eps[0][tt]};
     }
     P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 0.0f, 0.5f * surf->Lx, 0.5f * surf->Ly,
                    periodic_z ? 0.5f * surf->Lz : 0.0f, periodic_z, surf->z_lo, surf->z_hi,
-                   surf->z_hi - surf->z_lo, (float)(rc * rc)};
+                   surf->z_hi - surf->z_lo, (float)(rc * rc), (float)rc};
     P.cg = cg;
     P.max_disp = grid->max_disp;
     P.th_disp = (unsigned long long)floor(grid->p_disp * 4294967296.0);
@@ -408,7 +419,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &P.moments, (size_t)S * 4));
     TRY(dalloc(h, &P.hNE, (size_t)(grid->nmax + 1) * grid->n_e_bins));
     TRY(dalloc(h, &P.e_out, S));
-    TRY(dalloc(h, &P.pair_counts, 4));
+    TRY(dalloc(h, &P.pair_counts, 6));
     TRY(dalloc(h, &h->d_error, 1));
     TRY(dalloc(h, &h->d_fix, S));
     std::vector<int> ident(S);
@@ -506,7 +517,7 @@ regc_status regc_reset_histograms(regc_handle* h) {
     zero(h->P.e_out, S * 8);
     zero(h->P.move_counts, S * 6 * 8);
     zero(h->X.ex_counts, S * 8 * 8);
-    zero(h->P.pair_counts, 4 * 8);
+    zero(h->P.pair_counts, 6 * 8);
     return cuda_fail(h, e);
 }
 
@@ -614,9 +625,194 @@ regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, in
     if (exchanges && e == cudaSuccess)
         e = cudaMemcpyAsync(exchanges, h->X.ex_counts, (size_t)h->S * 8 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (pairs && e == cudaSuccess)
-        e = cudaMemcpyAsync(pairs, h->P.pair_counts, 4 * 8, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(pairs, h->P.pair_counts, 6 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     return sync_check(h);
+}
+
+// ------------------------------------------------------------- surrogate
+
+regc_status regc_surrogate_set(regc_handle* h, const float* theta) {
+    if (!h || !theta) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    for (int i = 0; i < REGC_SURROGATE_PARAMS; ++i)
+        if (!std::isfinite(theta[i])) return REGC_EINVAL;
+    regc_status st = REGC_OK;
+    if (!h->has_sur) {
+        const size_t np = REGC_SURROGATE_PARAMS;
+        if (st == REGC_OK) st = dalloc(h, &h->d_theta, np);
+        if (st == REGC_OK) st = dalloc(h, &h->d_adam_m, np);
+        if (st == REGC_OK) st = dalloc(h, &h->d_adam_v, np);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.w1, 64 * 16);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.b1, 64);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.w2, 64 * 64);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.b2, 64);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.w3, 64);
+        if (st == REGC_OK) st = dalloc(h, &h->sur.b3, 1);
+        if (st != REGC_OK) return st;
+        h->P.net = SurrogateDev{h->sur.w1, h->sur.b1, h->sur.w2, h->sur.b2, h->sur.w3, h->sur.b3};
+        h->has_sur = true;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->d_theta, theta, REGC_SURROGATE_PARAMS * sizeof(float),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_adam_m, 0, REGC_SURROGATE_PARAMS * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_adam_v, 0, REGC_SURROGATE_PARAMS * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = surrogate_pack(h->d_theta, h->sur, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->adam_t = 0;
+    return cuda_fail(h, e);
+}
+
+regc_status regc_surrogate_get(regc_handle* h, float* theta) {
+    if (!h || !theta) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (!h->has_sur) return REGC_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(theta, h->d_theta, REGC_SURROGATE_PARAMS * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_set_mode(regc_handle* h, int mode) {
+    if (!h || (mode != 0 && mode != 1)) return REGC_EINVAL;
+    if (mode == 1 && !h->has_sur) return REGC_EINVAL;
+    h->P.delayed = mode;
+    return REGC_OK;
+}
+
+regc_status regc_surrogate_eval(regc_handle* h, int walker, int n_query, const float* xyz, float* e_out,
+                                float* features) {
+    if (!h || walker < 0 || walker >= h->S || n_query < 0 || (n_query > 0 && (!xyz || !e_out)))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (!h->has_sur) return REGC_EINVAL;
+    if (n_query == 0) return REGC_OK;
+    std::vector<float4> q(n_query);
+    for (int i = 0; i < n_query; ++i) {
+        const float* r = xyz + 3 * i;
+        const bool okx = r[0] >= 0.0f && r[0] < h->Lx, oky = r[1] >= 0.0f && r[1] < h->Ly;
+        const bool okz = h->periodic_z ? (r[2] >= 0.0f && r[2] < h->Lz) : (r[2] >= h->z_lo && r[2] <= h->z_hi);
+        if (!(okx && oky && okz)) return REGC_EINVAL;
+        q[i] = make_float4(r[0], r[1], r[2], 0.0f);
+    }
+    float4* d_q = nullptr;
+    float *d_e = nullptr, *d_f = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_q, n_query * sizeof(float4), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_e, n_query * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_f, (size_t)n_query * 16 * sizeof(float), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_q, q.data(), n_query * sizeof(float4), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = surrogate_eval(h->P, walker, n_query, d_q, d_e, d_f, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(e_out, d_e, n_query * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && features)
+        e = cudaMemcpyAsync(features, d_f, (size_t)n_query * 16 * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (d_q) cudaFreeAsync(d_q, h->stream);
+    if (d_e) cudaFreeAsync(d_e, h->stream);
+    if (d_f) cudaFreeAsync(d_f, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_surrogate_harvest(regc_handle* h, int particles, int probes, float e_clip, int capacity,
+                                   int64_t* n_rows) {
+    if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (h->ds_cap == 0) {
+        if (capacity < 1) return REGC_EINVAL;
+        regc_status st = dalloc(h, &h->d_X, (size_t)capacity * 16);
+        if (st == REGC_OK) st = dalloc(h, &h->d_y, (size_t)capacity);
+        if (st != REGC_OK) return st;
+        h->ds_cap = capacity;
+    } else if (capacity != 0 && capacity != h->ds_cap) {
+        return REGC_EINVAL;
+    }
+    const long long rows = (long long)h->S * (particles + probes);
+    if (rows > (1LL << 31) - 1) return REGC_EINVAL;
+    const regc_status st = cuda_fail(h, surrogate_harvest(h->P, particles, probes, e_clip, h->harvest_round, h->d_X,
+                                                          h->d_y, h->ds_next, h->ds_cap, h->stream));
+    if (st != REGC_OK) return st;
+    h->harvest_round += 1;
+    h->ds_next = (int)((h->ds_next + rows) % h->ds_cap);
+    h->ds_count = (int)std::min<long long>(h->ds_cap, h->ds_count + rows);
+    if (n_rows) *n_rows = h->ds_count;
+    return REGC_OK;
+}
+
+regc_status regc_surrogate_dataset(regc_handle* h, int64_t max_rows, float* X, float* y, int64_t* n_rows) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (n_rows) *n_rows = h->ds_count;
+    if ((X || y) && max_rows < h->ds_count) return REGC_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (X && h->ds_count > 0)
+        e = cudaMemcpyAsync(X, h->d_X, (size_t)h->ds_count * 16 * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (y && h->ds_count > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(y, h->d_y, (size_t)h->ds_count * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_surrogate_train(regc_handle* h, int steps, int batch, float lr, float* loss) {
+    if (!h || steps < 0 || batch < 1 || !(lr >= 0.0f) || !std::isfinite(lr)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (!h->has_sur || h->ds_count == 0) return REGC_EINVAL;
+    if (steps == 0) return REGC_OK;
+    int* d_idx = nullptr;
+    float *d_part = nullptr, *d_loss = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_idx, batch * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_part, surrogate_partial_floats(batch) * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_loss, steps * sizeof(float), h->stream);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        h->adam_t += 1;
+        e = surrogate_batch_index(d_idx, batch, h->ds_count, (uint32_t)h->adam_t, h->P.key0, h->P.key1, h->stream);
+        if (e == cudaSuccess)
+            e = surrogate_step(h->d_theta, h->d_X, h->d_y, d_idx, batch, d_part, nullptr, d_loss + k, h->d_theta,
+                               h->d_adam_m, h->d_adam_v, h->adam_t, lr, h->stream);
+    }
+    if (e == cudaSuccess) e = surrogate_pack(h->d_theta, h->sur, h->stream);
+    std::vector<float> lsum(steps);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lsum.data(), d_loss, steps * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (d_idx) cudaFreeAsync(d_idx, h->stream);
+    if (d_part) cudaFreeAsync(d_part, h->stream);
+    if (d_loss) cudaFreeAsync(d_loss, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    const regc_status st = sync_check(h);
+    if (st == REGC_OK && loss)
+        for (int k = 0; k < steps; ++k) loss[k] = lsum[k] / (float)batch;
+    return st;
+}
+
+regc_status regc_surrogate_gradient(int n, const float* theta, const float* X, const float* y, float* loss,
+                                    float* grad, void* cuda_stream) {
+    if (n < 1 || !theta || !X || !y) return REGC_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    float *d_theta = nullptr, *d_X = nullptr, *d_y = nullptr, *d_part = nullptr, *d_grad = nullptr,
+          *d_loss = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_theta, REGC_SURROGATE_PARAMS * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_X, (size_t)n * 16 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_y, (size_t)n * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_part, surrogate_partial_floats(n) * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_grad, REGC_SURROGATE_PARAMS * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_loss, sizeof(float), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_theta, theta, REGC_SURROGATE_PARAMS * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_X, X, (size_t)n * 16 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, y, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = surrogate_step(d_theta, d_X, d_y, nullptr, n, d_part, d_grad, d_loss, nullptr, nullptr, nullptr, 0, 0.0f,
+                           s);
+    float l = 0.0f;
+    if (e == cudaSuccess && grad)
+        e = cudaMemcpyAsync(grad, d_grad, REGC_SURROGATE_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, d_loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    for (float* p : {d_theta, d_X, d_y, d_part, d_grad, d_loss})
+        if (p) cudaFreeAsync(p, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? REGC_ENOMEM : REGC_ECUDA;
+    if (loss) *loss = l / (float)n;
+    return REGC_OK;
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 // the C ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,6 +69,18 @@ struct PairTab {
     float eps4;   // 4 eps_ij
     float sig2;   // sigma_ij^2
     float rhc2;   // hard-core guard radius^2 (0 when eps_ij = 0)
+    float eps;    // eps_ij (the surrogate's neighbour weight)
+};
+
+// The surrogate network's BF16 inference copy (unit-major weights, FP32
+// biases); see surrogate.cuh.
+struct SurrogateDev {
+    const __nv_bfloat16* w1;   // [64][16]: unit u's 16 input weights
+    const float* b1;           // [64]
+    const __nv_bfloat16* w2;   // [64][64]: unit v's 64 input weights
+    const float* b2;           // [64]
+    const __nv_bfloat16* w3;   // [64]
+    const float* b3;           // [1]
 };
 
 struct Geometry {
@@ -77,6 +90,7 @@ struct Geometry {
     float z_lo, z_hi;
     float height;          // binary32(z_hi - z_lo)
     float rc2;
+    float rc;
 };
 
 struct CellGrid {
@@ -127,13 +141,16 @@ struct SweepParams {
     long long e_lo_fix, e_bin_fix;  // E-histogram origin and bin width in units of 2^-30
     int n_e_bins;
     long long* move_counts;       // [S][6]
-    unsigned long long* pair_counts;  // [4] pairs in rc, candidates, rounds, evaluations
+    unsigned long long* pair_counts;  // [6] pairs in rc, candidates, rounds, evaluations,
+                                      //     surrogate-screened moves, stage-1 passes
     int* error;
     regc_move_record* trace;      // device [S][n_sweeps][mps] or null
     uint32_t t0;
     int n_sweeps;
     int smem_per_walker;          // bytes
     int warps_per_walker;         // 1, 2 or 4
+    int delayed;                  // 1: two-stage delayed acceptance with the surrogate
+    SurrogateDev net;             // the surrogate (delayed acceptance)
 };
 
 struct ExchangeParams {

@@ -1,0 +1,341 @@
+// surrogate.cu -- the learned surrogate of the delayed-acceptance sweep (sm_103a).
+//
+// The paper has no surrogate.  This file holds:
+//   * pack_kernel: FP32 master parameters -> the BF16 inference layout;
+//   * eval_kernel: the surrogate energy (and features) of arbitrary positions
+//     in one walker, one warp per position, over every partner (no cells);
+//   * harvest_kernel: training rows (features, clipped exact interaction
+//     energy) of particles of every walker and of random probe positions;
+//   * grad_kernel / reduce_adam_kernel: one step of mini-batch training -- the
+//     forward and backward passes of 128 rows per CTA in shared memory, the
+//     per-CTA gradients summed in a fixed order, and Adam on the FP32 masters.
+#include "launch.h"
+#include "surrogate.cuh"
+
+namespace regc {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kRows = 128;           // rows per training CTA (one per thread)
+constexpr int kLd = kNH + 1;         // padded row stride of the activation tiles
+constexpr int kLdX = kNF + 1;        // padded row stride of the feature tile
+
+__global__ void pack_kernel(const float* theta, __nv_bfloat16* w1, float* b1, __nv_bfloat16* w2, float* b2,
+                            __nv_bfloat16* w3, float* b3) {
+    const float* W1 = theta;
+    const float* B1 = W1 + kNF * kNH;
+    const float* W2 = B1 + kNH;
+    const float* B2 = W2 + kNH * kNH;
+    const float* W3 = B2 + kNH;
+    const float* B3 = W3 + kNH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNH * kNH; i += gridDim.x * blockDim.x) {
+        const int v = i / kNH, u = i % kNH;          // unit v, input u
+        w2[i] = __float2bfloat16_rn(W2[u * kNH + v]);
+        if (i < kNH * kNF) {
+            const int uu = i / kNF, k = i % kNF;     // unit uu, input k
+            w1[i] = __float2bfloat16_rn(W1[k * kNH + uu]);
+        }
+        if (i < kNH) {
+            b1[i] = B1[i];
+            b2[i] = B2[i];
+            w3[i] = __float2bfloat16_rn(W3[i]);
+        }
+        if (i == 0) b3[0] = B3[0];
+    }
+}
+
+// Displacement q - p with the exact minimum image on periodic axes.
+__device__ __forceinline__ float r2_exact(const Geometry& g, float qx, float qy, float qz, float4 p) {
+    const float dx = min_image_exact(qx, p.x, g.Lx, g.hLx);
+    const float dy = min_image_exact(qy, p.y, g.Ly, g.hLy);
+    const float dz = g.periodic_z ? min_image_exact(qz, p.z, g.Lz, g.hLz) : __fsub_rn(qz, p.z);
+    return r2_of(dx, dy, dz);
+}
+
+// Features (per lane, before the warp sum) and exact binary32 interaction
+// energy (warp sum) of a position against every partner of walker w.
+__device__ float features_all(const SweepParams& P, int w, int N, float qx, float qy, float qz, int skip,
+                              float (&F)[kNF], int lane) {
+    const float4* pos = P.pos + size_t(w) * P.nmax;
+    float e = 0.f;
+    for (int j = lane; j < N; j += 32) {
+        if (j == skip) continue;
+        const float r2 = r2_exact(P.g, qx, qy, qz, pos[j]);
+        if (r2 < P.g.rc2) {
+            add_features(F, r2, P.gg.eps, P.g.rc);
+            e += phi_of_r2(r2, P.gg);
+        }
+    }
+    for (int a = lane; a < P.st.n_all; a += 32) {
+        const float4 at = P.st.all[a];
+        const PairTab& t = surf_tab(P, (int)at.w);
+        const float r2 = r2_exact(P.g, qx, qy, qz, at);
+        if (r2 < P.g.rc2) {
+            add_features(F, r2, t.eps, P.g.rc);
+            e += phi_of_r2(r2, t);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+    return e;
+}
+
+__global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ SweepParams P, int w, int Q,
+                                                   const float4* q, float* e_out, float* f_out) {
+    __shared__ __align__(16) float scratch[4][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 4 + warp;
+    if (i >= Q) return;
+    const float4 x = q[i];
+    float F[kNF];
+#pragma unroll
+    for (int k = 0; k < kNF; ++k) F[k] = 0.f;
+    features_all(P, w, P.n[w], x.x, x.y, x.z, -1, F, lane);
+    const float g = warp_reduce16(F, lane);
+    if ((lane & 1) == 0) f_out[size_t(i) * kNF + (lane >> 1)] = g;
+    const float e = mlp_forward(P.net, g, scratch[warp], lane);
+    if (lane == 0) e_out[i] = e;
+}
+
+// Row r of a harvest: walker r / per_w, slot r % per_w; the first `parts`
+// slots are particles of the walker (evenly spaced indices), the rest (and
+// every slot of an empty walker) random probe positions of the gas region
+// (Philox stream 5).  Rows go to a ring of `cap` rows starting at `base`.
+__global__ void __launch_bounds__(128) harvest_kernel(const __grid_constant__ SweepParams P, int parts, int probes,
+                                                      float clip, uint32_t round, float* X, float* y, int base,
+                                                      int cap) {
+    const int lane = threadIdx.x & 31;
+    const int per_w = parts + probes;
+    const long long r = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (r >= (long long)P.S * per_w) return;
+    const int w = (int)(r / per_w), slot = (int)(r % per_w);
+    const long long out = (base + r) % cap;
+    const int N = P.n[w];
+    float qx, qy, qz;
+    int skip = -1;
+    if (slot < parts && N > 0) {
+        skip = (int)(((long long)slot * N) / parts);
+        const float4 p = P.pos[size_t(w) * P.nmax + skip];
+        qx = p.x; qy = p.y; qz = p.z;
+    } else {
+        const U4 u = philox(uint32_t(slot), uint32_t(w), round, 5u, P.key0, P.key1);
+        qx = __fmul_rn(P.g.Lx, u24(u.x));
+        qy = __fmul_rn(P.g.Ly, u24(u.y));
+        qz = __fadd_rn(P.g.z_lo, __fmul_rn(P.g.height, u24(u.z)));
+        if (qx >= P.g.Lx) qx = 0.f;
+        if (qy >= P.g.Ly) qy = 0.f;
+        if (P.g.periodic_z && qz >= P.g.Lz) qz = 0.f;
+    }
+    float F[kNF];
+#pragma unroll
+    for (int k = 0; k < kNF; ++k) F[k] = 0.f;
+    const float e = features_all(P, w, N, qx, qy, qz, skip, F, lane);
+    const float g = warp_reduce16(F, lane);
+    if ((lane & 1) == 0) X[out * kNF + (lane >> 1)] = g;
+    if (lane == 0) y[out] = fminf(e, clip);
+}
+
+__device__ __forceinline__ float dsilu_f(float x) {
+    const float s = 1.0f / (1.0f + expf(-x));
+    return s * (1.0f + x * (1.0f - s));
+}
+
+// Forward and backward pass of up to kRows rows (row t = idx[t] or base + t)
+// with FP32 parameters theta; writes this CTA's gradient of
+// sum_t (e_t - y_t)^2 * scale into partial[blockIdx.x][5313] and its sum of
+// squared residuals into partial_loss[blockIdx.x].
+__global__ void __launch_bounds__(kRows) grad_kernel(const float* theta, const float* X, const float* yv,
+                                                     const int* idx, int n, float scale, float* partial,
+                                                     float* partial_loss) {
+    extern __shared__ __align__(16) float sm[];
+    float* Wsh = sm;                                  // [5313] parameters
+    float* Xs = Wsh + ((kNParams + 3) & ~3);          // [kRows][kLdX]
+    float* Z1 = Xs + kRows * kLdX;                    // [kRows][kLd] z1, later dz1
+    float* H1 = Z1 + kRows * kLd;                     // [kRows][kLd] h1
+    float* Z2 = H1 + kRows * kLd;                     // [kRows][kLd] z2, later dz2
+    float* gsh = Z2 + kRows * kLd;                    // [kRows] d loss / d e
+    const int t = threadIdx.x;
+    const int row0 = blockIdx.x * kRows;
+    for (int i = t; i < kNParams; i += kRows) Wsh[i] = theta[i];
+    const int row = row0 + t;
+    const bool act = row < n;
+    const int src = act ? (idx ? idx[row] : row) : 0;
+    for (int k = 0; k < kNF; ++k) Xs[t * kLdX + k] = act ? X[size_t(src) * kNF + k] : 0.f;
+    __syncthreads();
+    const float* W1 = Wsh;
+    const float* b1 = W1 + kNF * kNH;
+    const float* W2 = b1 + kNH;
+    const float* b2 = W2 + kNH * kNH;
+    const float* W3 = b2 + kNH;
+    const float b3 = W3[kNH];
+    // forward, one row per thread
+    for (int u = 0; u < kNH; ++u) {
+        float z = b1[u];
+        for (int k = 0; k < kNF; ++k) z = fmaf(W1[k * kNH + u], Xs[t * kLdX + k], z);
+        Z1[t * kLd + u] = z;
+        H1[t * kLd + u] = z / (1.0f + expf(-z));
+    }
+    float out = b3;
+    for (int v = 0; v < kNH; ++v) {
+        float z = b2[v];
+        for (int u = 0; u < kNH; ++u) z = fmaf(W2[u * kNH + v], H1[t * kLd + u], z);
+        Z2[t * kLd + v] = z;
+        out = fmaf(W3[v], z / (1.0f + expf(-z)), out);
+    }
+    const float res = act ? out - yv[src] : 0.f;
+    gsh[t] = 2.0f * res * scale;
+    float* G = partial + size_t(blockIdx.x) * kNParams;
+    float* gW1 = G;
+    float* gb1 = gW1 + kNF * kNH;
+    float* gW2 = gb1 + kNH;
+    float* gb2 = gW2 + kNH * kNH;
+    float* gW3 = gb2 + kNH;
+    __syncthreads();
+    // d loss / d W3, b3 (threads 0..63 own one unit each)
+    if (t < kNH) {
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) {
+            const float z = Z2[r * kLd + t];
+            acc = fmaf(gsh[r], z / (1.0f + expf(-z)), acc);
+        }
+        gW3[t] = acc;
+    } else if (t == kNH) {
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) acc += gsh[r];
+        gW3[kNH] = acc;   // b3
+    }
+    __syncthreads();
+    // dz2 = g W3 silu'(z2), in place
+    for (int v = 0; v < kNH; ++v) {
+        const float z = Z2[t * kLd + v];
+        Z2[t * kLd + v] = gsh[t] * W3[v] * dsilu_f(z);
+    }
+    __syncthreads();
+    // d W2 [u][v] = sum_r h1[r][u] dz2[r][v]; d b2
+    for (int i = t; i < kNH * kNH; i += kRows) {
+        const int u = i / kNH, v = i % kNH;
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) acc = fmaf(H1[r * kLd + u], Z2[r * kLd + v], acc);
+        gW2[i] = acc;
+    }
+    if (t < kNH) {
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) acc += Z2[r * kLd + t];
+        gb2[t] = acc;
+    }
+    __syncthreads();
+    // dz1 = (W2 dz2) silu'(z1), in place of z1
+    for (int u = 0; u < kNH; ++u) {
+        float acc = 0.f;
+        for (int v = 0; v < kNH; ++v) acc = fmaf(W2[u * kNH + v], Z2[t * kLd + v], acc);
+        Z1[t * kLd + u] = acc * dsilu_f(Z1[t * kLd + u]);
+    }
+    __syncthreads();
+    // d W1 [k][u] = sum_r x[r][k] dz1[r][u]; d b1
+    for (int i = t; i < kNF * kNH; i += kRows) {
+        const int k = i / kNH, u = i % kNH;
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) acc = fmaf(Xs[r * kLdX + k], Z1[r * kLd + u], acc);
+        gW1[i] = acc;
+    }
+    if (t < kNH) {
+        float acc = 0.f;
+        for (int r = 0; r < kRows; ++r) acc += Z1[r * kLd + t];
+        gb1[t] = acc;
+    }
+    // sum of squared residuals
+    float sq = res * res;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
+    __shared__ float wsum[kRows / 32];
+    if ((t & 31) == 0) wsum[t >> 5] = sq;
+    __syncthreads();
+    if (t == 0) {
+        float tot = 0.f;
+        for (int k = 0; k < kRows / 32; ++k) tot += wsum[k];
+        partial_loss[blockIdx.x] = tot;
+    }
+}
+
+// Sum the per-CTA gradients in a fixed order; optionally take an Adam step.
+__global__ void reduce_adam_kernel(const float* partial, const float* partial_loss, int nblk, float* grad,
+                                   float* loss, float* theta, float* m, float* v, int adam_t, float lr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        float tot = 0.f;
+        for (int b = 0; b < nblk; ++b) tot += partial_loss[b];
+        *loss = tot;
+    }
+    if (i >= kNParams) return;
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += partial[size_t(b) * kNParams + i];
+    if (grad) grad[i] = g;
+    if (adam_t > 0) {
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / (1.f - powf(b1, (float)adam_t));
+        const float vh = vi / (1.f - powf(b2, (float)adam_t));
+        theta[i] -= lr * mh / (sqrtf(vh) + eps);
+    }
+}
+
+// Random row indices of a training step (Philox stream 6).
+__global__ void batch_index_kernel(int* idx, int batch, int count, uint32_t step, uint32_t k0, uint32_t k1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    const U4 u = philox(uint32_t(i), step, 0u, 6u, k0, k1);
+    idx[i] = (int)(((unsigned long long)u.x * (unsigned)count) >> 32);
+}
+
+size_t grad_smem() {
+    return (size_t(((kNParams + 3) & ~3)) + kRows * kLdX + 3 * kRows * kLd + kRows) * sizeof(float);
+}
+
+}  // namespace
+
+cudaError_t surrogate_pack(const float* theta, const SurrogateStore& st, cudaStream_t s) {
+    pack_kernel<<<16, 256, 0, s>>>(theta, st.w1, st.b1, st.w2, st.b2, st.w3, st.b3);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_eval(const SweepParams& P, int w, int Q, const float4* q, float* e_out, float* f_out,
+                           cudaStream_t s) {
+    if (Q <= 0) return cudaSuccess;
+    eval_kernel<<<(Q + 3) / 4, 128, 0, s>>>(P, w, Q, q, e_out, f_out);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_harvest(const SweepParams& P, int parts, int probes, float clip, uint32_t round, float* X,
+                              float* y, int base, int cap, cudaStream_t s) {
+    const long long rows = (long long)P.S * (parts + probes);
+    if (rows <= 0 || cap <= 0) return cudaSuccess;
+    harvest_kernel<<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(P, parts, probes, clip, round, X, y, base, cap);
+    return cudaGetLastError();
+}
+
+size_t surrogate_partial_floats(int n) { return size_t((n + kRows - 1) / kRows) * (kNParams + 1); }
+
+cudaError_t surrogate_step(const float* theta_in, const float* X, const float* y, const int* idx, int n,
+                           float* partial, float* grad, float* loss, float* theta, float* m, float* v, int adam_t,
+                           float lr, cudaStream_t s) {
+    const int nblk = (n + kRows - 1) / kRows;
+    const size_t smem = grad_smem();
+    cudaError_t err = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    float* partial_loss = partial + size_t(nblk) * kNParams;
+    grad_kernel<<<nblk, kRows, smem, s>>>(theta_in, X, y, idx, n, 1.0f / (float)n, partial, partial_loss);
+    reduce_adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(partial, partial_loss, nblk, grad, loss, theta, m, v,
+                                                              adam_t, lr);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_batch_index(int* idx, int batch, int count, uint32_t step, uint32_t k0, uint32_t k1,
+                                  cudaStream_t s) {
+    batch_index_kernel<<<(batch + 255) / 256, 256, 0, s>>>(idx, batch, count, step, k0, k1);
+    return cudaGetLastError();
+}
+
+}  // namespace regc

@@ -27,6 +27,7 @@
 //   5. after each sweep the walker is observed into its state's histograms;
 //   6. positions, N and the running energy go back to HBM.
 #include "launch.h"
+#include "surrogate.cuh"
 
 namespace regc {
 namespace {
@@ -59,7 +60,9 @@ struct MoveRes {
     float q0x, q0y, q0z;   // new position (removal: the old one)
     float q1x, q1y, q1z;   // old position of a displacement
     int dec;       // decision with N = n_eval: 0 reject, 1 accept, 2 near tie (FP64 needed)
-    int pad[3];
+    int stage1;    // delayed acceptance: 1 if the surrogate stage accepted
+    float dE_sur;  // delayed acceptance: surrogate energy change
+    int pad;
 };
 
 // Constants of the walker's state for the binary32 pre-test of the acceptance.
@@ -89,6 +92,7 @@ struct WalkerStats {
     unsigned long long om, eo;
     unsigned long long pairs;   // pairs within rc of the committed moves
     unsigned long long rounds, evals;
+    unsigned long long screened, passed;   // delayed acceptance: stage-1 screens and passes
     int tr[3], ac[3];
 };
 
@@ -107,6 +111,7 @@ struct WalkerSmem {
     uint4* rng;         // [kRing][2] Philox blocks A, B of upcoming moves
     MoveRes* res;       // [K]
     StEntry* stencil;   // [K][32]
+    float* scratch;     // [K][64] surrogate activations
     uint16_t* cnt;      // [ncell]
     uint16_t* slots;    // [ncell][cap] particle indices
 };
@@ -116,7 +121,8 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(
 __host__ __device__ inline size_t smem_bytes(int nmax, int ncell, int cap, int K) {
     return align16(size_t(nmax) * 16) + 16 + align16(sizeof(WalkerStats)) + align16(sizeof(RoundHdr)) +
            size_t(kRing) * 2 * sizeof(uint4) + align16(size_t(K) * sizeof(MoveRes)) +
-           size_t(K) * 32 * sizeof(StEntry) + align16(size_t(ncell) * 2) + align16(size_t(ncell) * cap * 2);
+           size_t(K) * 32 * sizeof(StEntry) + size_t(K) * 64 * sizeof(float) + align16(size_t(ncell) * 2) +
+           align16(size_t(ncell) * cap * 2);
 }
 
 template <int K>
@@ -137,6 +143,8 @@ __device__ inline WalkerSmem carve(char* base, const SweepParams& P) {
     off += align16(size_t(K) * sizeof(MoveRes));
     w.stencil = reinterpret_cast<StEntry*>(base + off);
     off += size_t(K) * 32 * sizeof(StEntry);
+    w.scratch = reinterpret_cast<float*>(base + off);
+    off += size_t(K) * 64 * sizeof(float);
     w.cnt = reinterpret_cast<uint16_t*>(base + off);
     off += align16(size_t(P.cg.ncell) * 2);
     w.slots = reinterpret_cast<uint16_t*>(base + off);
@@ -346,6 +354,78 @@ __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, floa
     overlap |= ov;
 }
 
+// Surrogate features of NQ queries (sharing the stencil of cell c) from the
+// mobile particles of the stencil except `skip`, accumulated per lane.
+template <int NQ>
+__device__ __forceinline__ void feature_mobile(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
+                                               float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
+                                               float (&F0)[kNF], float (&F1)[kNF], int lane, int warp) {
+    StEntry* st = S.stencil + warp * 32;
+    StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
+    const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(FULL, incl, 31);
+    const unsigned nonempty = __ballot_sync(FULL, cnt > 0);
+    if (cnt > 0) {
+        se.excl = excl;
+        st[__popc(nonempty & lanemask_lt(lane))] = se;
+    }
+    __syncwarp();
+    int started = 0;
+    for (int base = 0; base < total; base += 32) {
+        const unsigned bit = (cnt > 0 && excl >= base && excl < base + 32) ? (1u << (excl - base)) : 0u;
+        const unsigned starts = __reduce_or_sync(FULL, bit);
+        const int j = base + lane;
+        if (j < total) {
+            const int r = started + __popc(starts & lanemask_le(lane)) - 1;
+            const StEntry& e = st[r];
+            const int pj = S.slots[e.cell * P.cg.cap + (j - e.excl)];
+            if (pj != skip) {
+                const float4 p = S.pos[pj];
+                const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
+                const float r20 = r2_of(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz));
+                if (r20 < P.g.rc2) add_features(F0, r20, P.gg.eps, P.g.rc);
+                if (NQ == 2) {
+                    const float r21 = r2_of(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by), __fsub_rn(e.az1, bz));
+                    if (r21 < P.g.rc2) add_features(F1, r21, P.gg.eps, P.g.rc);
+                }
+            }
+        }
+        started += __popc(starts);
+    }
+    __syncwarp();
+}
+
+// Surrogate features of NQ queries (sharing one surface column) from the
+// images of frozen surface atoms listed for that column.
+template <int NQ>
+__device__ __forceinline__ void feature_surface(const SweepParams& P, int col, float q0x, float q0y, float q0z,
+                                                float q1x, float q1y, float q1z, float (&F0)[kNF],
+                                                float (&F1)[kNF], int lane) {
+    const int beg = P.st.col_off[col], end = P.st.col_off[col + 1];
+    for (int j = beg + lane; j < end; j += 32) {
+        const float4 a = __ldg(&P.st.atoms[j]);
+        const unsigned bits = __float_as_uint(a.w);
+        const PairTab& t = surf_tab(P, (int)(bits & 3u));
+        const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
+        const float sz = (bits & 16u) ? P.g.Lz : 0.f;
+        const float r20 = r2_of(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
+                                __fsub_rn(__fsub_rn(q0z, sz), a.z));
+        if (r20 < P.g.rc2) add_features(F0, r20, t.eps, P.g.rc);
+        if (NQ == 2) {
+            const float r21 = r2_of(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
+                                    __fsub_rn(__fsub_rn(q1z, sz), a.z));
+            if (r21 < P.g.rc2) add_features(F1, r21, t.eps, P.g.rc);
+        }
+    }
+}
+
 __device__ __forceinline__ int surface_col(const SweepParams& P, float x, float y) {
     const int sx = min(P.st.nsx - 1, (int)(x * P.st.isx));
     const int sy = min(P.st.nsy - 1, (int)(y * P.st.isy));
@@ -412,7 +492,8 @@ __device__ void build_cells(const SweepParams& P, const WalkerSmem& S, int N, in
 // Evaluate trial move m of the launch (sweep m / mps, move m % mps) with one
 // warp against the current configuration with N particles; lane 0 stores the
 // result in *out.
-__device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int m, int N,
+template <bool DA>
+__device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int s, int m, int N,
                               int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
     const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
     const int type = (unsigned long long)A.x < P.th_disp ? 0 : ((B.z >> 31) == 0u ? 2 : 1);
@@ -467,8 +548,53 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         }
     }
 
+    // delayed acceptance, stage 1: the surrogate energy change dE~
+    int stage1 = 1;
+    float dEs = 0.f;
+    if (DA && status == 0) {
+        float F0[kNF], F1[kNF];
+#pragma unroll
+        for (int k = 0; k < kNF; ++k) F0[k] = F1[k] = 0.f;
+        const int skip = type == 1 ? -1 : idx;
+        const Cell3 c0 = cell3_of(P, q0x, q0y, q0z);
+        const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
+        if (nq == 2 && c0.x == c1.x && c0.y == c1.y && c0.z == c1.z) {
+            feature_mobile<2>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, F0, F1, lane, warp);
+        } else {
+            feature_mobile<1>(P, S, c0, q0x, q0y, q0z, q0x, q0y, q0z, skip, F0, F1, lane, warp);
+            if (nq == 2) feature_mobile<1>(P, S, c1, q1x, q1y, q1z, q1x, q1y, q1z, skip, F1, F0, lane, warp);
+        }
+        const bool s0 = near_surface(P, q0z), s1 = nq == 2 && near_surface(P, q1z);
+        const int col0 = surface_col(P, q0x, q0y), col1 = nq == 2 ? surface_col(P, q1x, q1y) : col0;
+        if (s0 && s1 && col0 == col1) {
+            feature_surface<2>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, F0, F1, lane);
+        } else {
+            if (s0) feature_surface<1>(P, col0, q0x, q0y, q0z, q0x, q0y, q0z, F0, F1, lane);
+            if (s1) feature_surface<1>(P, col1, q1x, q1y, q1z, q1x, q1y, q1z, F1, F0, lane);
+        }
+        float* scratch = S.scratch + warp * 64;
+        const float e0 = mlp_forward(P.net, warp_reduce16(F0, lane), scratch, lane);
+        float e1 = 0.f;
+        if (nq == 2) e1 = mlp_forward(P.net, warp_reduce16(F1, lane), scratch, lane);
+        dEs = type == 1 ? e0 : (type == 2 ? -e0 : e0 - e1);
+        // ln u1 < ln alpha with dE~ in place of dE (u1 from B3)
+        float c_f = 0.f;
+        if (type == 1) c_f = sf.c_ins - __logf((float)(N + 1));
+        else if (type == 2) c_f = sf.c_del + __logf((float)N);
+        const float la1 = c_f - sf.beta * dEs;
+        const float lu1 = __logf(((float)B.w + 0.5f) * 2.3283064365386963e-10f);
+        if (la1 >= 0.f || lu1 < la1 - 1e-3f) stage1 = 1;
+        else if (lu1 > la1 + 1e-3f) stage1 = 0;
+        else {
+            double c = 0.0;
+            if (type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
+            else if (type == 2) c = P.c_del[s] + P.ln_tab[N];
+            stage1 = (log((double)B.w + 0.5) + kLn2m32) < c - P.beta[s] * (double)dEs;
+        }
+    }
+
     Fix3 acc{0, 0, 0};
-    if (status == 0) {
+    if (status == 0 && stage1) {
         const int skip = type == 1 ? -1 : idx;
         const Cell3 c0 = cell3_of(P, q0x, q0y, q0z);
         const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
@@ -521,7 +647,24 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         r.flags = ovl | (npairs << 1);
         r.q0x = q0x; r.q0y = q0y; r.q0z = q0z;
         r.q1x = q1x; r.q1y = q1y; r.q1z = q1z;
-        r.dec = (status == 0 && !ovl) ? pretest(sf, type, N, big, hi, lo, B.y) : 0;
+        r.stage1 = stage1;
+        r.dE_sur = dEs;
+        if (!DA) {
+            r.dec = (status == 0 && !ovl) ? pretest(sf, type, N, big, hi, lo, B.y) : 0;
+        } else if (status != 0 || ovl || !stage1) {
+            r.dec = 0;
+        } else {
+            // stage 2: ln u2 < -beta (dE - dE~) (u2 from B1)
+            const float de_f = __fmaf_rn((float)lo, 9.313225746154785e-10f,
+                                         __fmaf_rn((float)hi, 0.00390625f, (float)big * 8192.0f));
+            const float la2 = -sf.beta * (de_f - dEs);
+            const float lu2 = __logf(((float)B.y + 0.5f) * 2.3283064365386963e-10f);
+            if (la2 >= 0.f || lu2 < la2 - 1e-3f) r.dec = 1;
+            else if (lu2 > la2 + 1e-3f) r.dec = 0;
+            else
+                r.dec = (log((double)B.y + 0.5) + kLn2m32) <
+                        -P.beta[s] * ((double)fix_value(big, hi, lo) * kFixUnit - (double)dEs);
+        }
         *out = r;
     }
 }
@@ -535,7 +678,7 @@ __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay,
     return r2_of(dx, dy, dz);
 }
 
-template <int K, bool TRACE>
+template <int K, bool TRACE, bool DA>
 __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -566,7 +709,8 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
     }
     // 2. cell list
     if (warp == 0) build_cells(P, S, N, lane);
-    if (threadIdx.x == 0) *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}};
+    if (threadIdx.x == 0)
+        *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}};
     group_sync<K>();
 
     int n_in = 0, n_cand = 0;
@@ -592,7 +736,7 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
         }
         // 3b. evaluate moves m0 .. m0 + K - 1 in parallel, one warp each
         const int mj = m0 + warp;
-        if (mj < total_moves) evaluate_move(P, S, sf, mj, N, n_in, n_cand, lane, warp, S.res + warp);
+        if (mj < total_moves) evaluate_move<DA>(P, S, sf, s, mj, N, n_in, n_cand, lane, warp, S.res + warp);
         group_sync<K>();
 
         // 4. commit in order (thread 0)
@@ -643,7 +787,18 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
                 int accepted = 0;
                 double la = 0.0;
                 const bool ovl = (r.flags & 1) != 0;
-                if (status == 0 && !ovl) {
+                if (DA && status == 0) {
+                    // both stages were decided by the evaluating warp (one warp per walker)
+                    accepted = !ovl && r.dec == 1;
+                    S.stats->screened += 1;
+                    S.stats->passed += r.stage1;
+                    if (TRACE) {
+                        double c = 0.0;
+                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
+                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N];
+                        la = r.stage1 ? c - P.beta[s] * ((double)dfix * kFixUnit) : (double)NAN;
+                    }
+                } else if (status == 0 && !ovl) {
                     const int dec = N == r.n_eval ? r.dec : pretest(sf, r.type, N, r.big, r.hi, r.lo, B.y);
                     accepted = dec == 1;
                     if (dec == 2 || TRACE) {
@@ -704,12 +859,15 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
                     t.accepted = accepted;
                     t.status = status == 3 ? 0 : status;
                     t.dE = (status == 0 || status == 3) ? (double)dfix * kFixUnit : 0.0;
+                    if (DA && status == 0 && !r.stage1) t.dE = (double)NAN;
                     t.log_alpha = (status == 0 || status == 3) ? (ovl ? -INFINITY : la) : 0.0;
                     t.ln_u = log((double)B.y + 0.5) + kLn2m32;
                     t.sum_abs = 0.0;
                     t.band = 0.0;
                     t.n_pairs = r.flags >> 1;
-                    t.pad = 0;
+                    t.stage1 = DA ? r.stage1 : 1;
+                    t.dE_sur = DA ? (double)r.dE_sur : 0.0;
+                    t.ln_u1 = log((double)B.w + 0.5) + kLn2m32;
                     P.trace[(size_t(w) * P.n_sweeps + ts) * P.mps + k] = t;
                 }
                 // 6. observe once per sweep into the current state's histograms
@@ -751,6 +909,8 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
         atomicAdd(&P.pair_counts[0], st.pairs);
         atomicAdd(&P.pair_counts[2], st.rounds);
         atomicAdd(&P.pair_counts[3], st.evals);
+        atomicAdd(&P.pair_counts[4], st.screened);
+        atomicAdd(&P.pair_counts[5], st.passed);
         P.n[w] = N;
         P.efix[w] = E;
         P.omega[s] += st.om;
@@ -812,18 +972,18 @@ __global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ Swe
     }
 }
 
-template <int K>
+template <int K, bool DA>
 cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
     const size_t smem = smem_bytes(P.nmax, P.cg.ncell, P.cg.cap, K);
     cudaError_t err;
     if (P.trace) {
-        err = cudaFuncSetAttribute(sweep_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, true, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, true><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, true, DA><<<P.S, 32 * K, smem, s>>>(P);
     } else {
-        err = cudaFuncSetAttribute(sweep_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, false, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, false><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, false, DA><<<P.S, 32 * K, smem, s>>>(P);
     }
     return cudaGetLastError();
 }
@@ -836,10 +996,11 @@ size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker)
 
 cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
     if (P.n_sweeps <= 0) return cudaSuccess;
+    if (P.delayed) return launch_k<1, true>(P, s);   // delayed acceptance: one warp per walker
     switch (P.warps_per_walker) {
-        case 1: return launch_k<1>(P, s);
-        case 2: return launch_k<2>(P, s);
-        case 4: return launch_k<4>(P, s);
+        case 1: return launch_k<1, false>(P, s);
+        case 2: return launch_k<2, false>(P, s);
+        case 4: return launch_k<4, false>(P, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -16,8 +16,11 @@ from ._lib import check
 MOVE_DTYPE = np.dtype([
     ("type", np.int32), ("index", np.int32), ("accepted", np.int32), ("status", np.int32),
     ("dE", np.float64), ("log_alpha", np.float64), ("ln_u", np.float64),
-    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("pad", np.int32),
+    ("sum_abs", np.float64), ("band", np.float64), ("n_pairs", np.int32), ("stage1", np.int32),
+    ("dE_sur", np.float64), ("ln_u1", np.float64),
 ])
+assert MOVE_DTYPE.itemsize == C.sizeof(_lib.MoveRecord)
+SURROGATE_PARAMS = _lib.SURROGATE_PARAMS
 
 
 def _p(a, ctype):
@@ -137,10 +140,52 @@ class Regc:
     def counters(self):
         mv = np.zeros((self.S, 3, 2), np.int64)
         ex = np.zeros((self.S, 4, 2), np.int64)
-        pr = np.zeros(4, np.int64)
+        pr = np.zeros(6, np.int64)
         check(_lib.lib().regc_counters(self._h, _p(mv, C.c_int64), _p(ex, C.c_int64), _p(pr, C.c_int64)),
               "regc_counters")
         return mv, ex, pr
+
+    # -- learned surrogate (delayed acceptance)
+    def surrogate_set(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(SURROGATE_PARAMS))
+        check(_lib.lib().regc_surrogate_set(self._h, _p(th, C.c_float)), "regc_surrogate_set")
+
+    def surrogate_get(self) -> np.ndarray:
+        th = np.zeros(SURROGATE_PARAMS, np.float32)
+        check(_lib.lib().regc_surrogate_get(self._h, _p(th, C.c_float)), "regc_surrogate_get")
+        return th
+
+    def set_mode(self, delayed: bool):
+        check(_lib.lib().regc_set_mode(self._h, 1 if delayed else 0), "regc_set_mode")
+
+    def surrogate_eval(self, walker: int, xyz):
+        q = np.ascontiguousarray(np.asarray(xyz, np.float32).reshape(-1, 3))
+        e = np.zeros(len(q), np.float32)
+        f = np.zeros((len(q), 16), np.float32)
+        check(_lib.lib().regc_surrogate_eval(self._h, int(walker), len(q), _p(q, C.c_float), _p(e, C.c_float),
+                                             _p(f, C.c_float)), "regc_surrogate_eval")
+        return e, f
+
+    def surrogate_harvest(self, particles: int, probes: int, e_clip: float, capacity: int = 0) -> int:
+        n = C.c_int64(0)
+        check(_lib.lib().regc_surrogate_harvest(self._h, int(particles), int(probes), float(e_clip),
+                                                int(capacity), C.byref(n)), "regc_surrogate_harvest")
+        return n.value
+
+    def surrogate_dataset(self):
+        n = C.c_int64(0)
+        check(_lib.lib().regc_surrogate_dataset(self._h, 0, None, None, C.byref(n)), "regc_surrogate_dataset")
+        X = np.zeros((n.value, 16), np.float32)
+        y = np.zeros(n.value, np.float32)
+        check(_lib.lib().regc_surrogate_dataset(self._h, n.value, _p(X, C.c_float), _p(y, C.c_float),
+                                                C.byref(n)), "regc_surrogate_dataset")
+        return X, y
+
+    def surrogate_train(self, steps: int, batch: int, lr: float) -> np.ndarray:
+        loss = np.zeros(steps, np.float32)
+        check(_lib.lib().regc_surrogate_train(self._h, int(steps), int(batch), float(lr), _p(loss, C.c_float)),
+              "regc_surrogate_train")
+        return loss
 
     def histograms(self):
         hN = np.zeros((self.S, self.nmax + 1), np.int64)
@@ -167,6 +212,20 @@ class Regc:
                                        _p(nm, C.c_double), _p(pN, C.c_double), _p(f, C.c_double),
                                        C.byref(it)), "regc_reweight")
         return nm, pN, f, it.value
+
+
+def surrogate_gradient(theta, X, y, stream=None):
+    """Mean squared error of the surrogate with parameters theta on rows (X, y)
+    and its gradient, from the library's training kernels."""
+    th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(SURROGATE_PARAMS))
+    X = np.ascontiguousarray(np.asarray(X, np.float32).reshape(-1, 16))
+    y = np.ascontiguousarray(np.asarray(y, np.float32).reshape(-1))
+    g = np.zeros(SURROGATE_PARAMS, np.float32)
+    loss = C.c_float(0)
+    check(_lib.lib().regc_surrogate_gradient(len(y), _p(th, C.c_float), _p(X, C.c_float), _p(y, C.c_float),
+                                             C.byref(loss), _p(g, C.c_float), _stream_handle(stream)),
+          "regc_surrogate_gradient")
+    return float(loss.value), g
 
 
 def mbar_solve(kT, mu, lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter=100000, stream=None):

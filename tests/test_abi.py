@@ -5,6 +5,7 @@ argument checks of regc_init_grid happen before any CUDA call, so invalid
 problem statements are rejected here too.
 """
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -81,3 +82,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         _lib.lib()
+
+
+def test_move_record_layout_matches_header(tmp_path):
+    """The binding's trace dtype has the size and field offsets of the C struct."""
+    import subprocess
+    from paper_1908_11118_gb300.regc import MOVE_DTYPE
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    fields = MOVE_DTYPE.names
+    src = tmp_path / "layout.c"
+    body = "".join('printf("%%zu\\n", offsetof(regc_move_record, %s));\n' % f for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "regc.h"\nint main(void){\n'
+                   'printf("%zu\\n", sizeof(regc_move_record));\n' + body + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == MOVE_DTYPE.itemsize
+    assert out[1:] == [MOVE_DTYPE.fields[f][1] for f in fields]
