@@ -43,6 +43,8 @@ SWEEPS_PER_STEP = 10
 FLOPS_PER_PAIR = 20            # dx,dy,dz 3, xy minimum image 4, r^2 5, r^-2 1, s^6 3, 4eps s^6(s^6-1) 4
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 METRIC = "GCMC trial moves/s over all replicas"
+DA_SMALL = ("fcc100 4x4x2 slab in a 6.25 x 6.25 x 10 box (hard wall at the top), 4 kT x 4 mu = 16 "
+            "replicas, Nmax 32, 20 moves/sweep; step = 10 sweeps + 1 replica-exchange attempt")
 WORKLOAD = ("fcc111 12x12x4 slab + LJ gas, 32 kT x 32 mu = 1024 replicas, Nmax 512, "
             "20 moves/sweep; step = 10 sweeps + 1 replica-exchange attempt")
 
@@ -56,6 +58,10 @@ def parse_args(argv=None):
     ap.add_argument("--equil", type=int, default=500, help="untimed equilibration sweeps")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--da", type=int, default=1, help="1: add the plain vs delayed-acceptance comparison")
+    ap.add_argument("--da-train-steps", type=int, default=3000)
+    ap.add_argument("--da-steps-small", type=int, default=1000)
+    ap.add_argument("--da-steps-large", type=int, default=60)
     return ap.parse_args(argv)
 
 
@@ -191,6 +197,99 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------- delayed acceptance arm
+
+DA_ROWS_PER_WALKER = (8, 8)     # particle rows, probe rows per walker per harvest
+DA_CLIP = 8.0                   # training targets clipped from above (eps units)
+
+
+def timed_run(g, torch, stream, flush, steps, n_batches):
+    """steps of (10 sweeps + exchange), device-timed per step with the L2
+    flushed before each; batch means of <N> per state.  Returns
+    (seconds, trial moves, accepted moves, pair counters delta, per-state
+    batch-mean <N> [n_batches, S])."""
+    g.reset_histograms()
+    nv = np.arange(g.nmax + 1)
+    per = max(1, steps // n_batches)
+    ev = []
+    nb = []
+    prev = g.histograms()["hN"]
+    for k in range(per * n_batches):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+        e1.record(stream)
+        ev.append((e0, e1))
+        if (k + 1) % per == 0:
+            h = g.histograms()["hN"]
+            d = h - prev
+            prev = h
+            nb.append((d @ nv) / np.maximum(d.sum(axis=1), 1))
+    torch.cuda.synchronize()
+    secs = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    mv, _, pr = g.counters()
+    return secs, int(mv[:, :, 0].sum()), int(mv[:, :, 1].sum()), pr, np.array(nb)
+
+
+def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_steps, timed_steps, seed=0):
+    """Train the surrogate on rows the plain sampler generates, then time the
+    plain and the delayed-acceptance sweep from the same state."""
+    from paper_1908_11118_gb300 import Regc
+
+    rng = np.random.default_rng(seed)
+    pos0, n0 = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos0, n0)
+    g.surrogate_init(seed=seed, scale=1.0)
+    g.run(200, exchange_every=SWEEPS_PER_STEP)
+    per = p.S * sum(DA_ROWS_PER_WALKER)
+    harvests = max(1, -(-rows_target // per))
+    t0 = time.perf_counter()
+    rows = 0
+    for _ in range(harvests):
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+        rows = g.surrogate_harvest(*DA_ROWS_PER_WALKER, DA_CLIP, capacity=harvests * per)
+    torch.cuda.synchronize()
+    t_harvest = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = g.surrogate_train(train_steps, 1024, 1e-3)
+    t_train = time.perf_counter() - t0
+    state = g.get_walkers()
+    res = {}
+    for mode in ("plain", "delayed"):
+        g.set_walkers(state[0], state[1], state[3])
+        g.set_mode(mode == "delayed")
+        g.run(50, exchange_every=SWEEPS_PER_STEP)
+        secs, trials, acc, pr, nb = timed_run(g, torch, stream, flush, timed_steps, 20)
+        se = nb.std(axis=0, ddof=1) / np.sqrt(len(nb))
+        exact = int(pr[5]) if mode == "delayed" else int(pr[3])
+        res[mode] = {"trial_moves_per_s": trials / secs, "accepted_moves_per_s": acc / secs,
+                     "acceptance": acc / trials, "exact_evaluations_per_accepted_move": exact / max(acc, 1),
+                     "screen_pass_fraction": (int(pr[5]) / max(int(pr[4]), 1)) if mode == "delayed" else None,
+                     "mean_N_stderr": float(np.mean(se)), "seconds": secs, "trial_moves": trials}
+    g.set_mode(False)
+    g.close()
+    pl, da = res["plain"], res["delayed"]
+    # cost of reaching a given <N> error scales as time x stderr^2
+    speedup = (pl["seconds"] * pl["mean_N_stderr"] ** 2) / (da["seconds"] * da["mean_N_stderr"] ** 2)
+    return {
+        "workload": name,
+        "training": {"rows": rows, "harvests": harvests, "rows_per_walker_per_harvest": list(DA_ROWS_PER_WALKER),
+                     "target_clip": DA_CLIP, "steps": train_steps, "batch": 1024, "lr": 1e-3,
+                     "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-100:])),
+                     "harvest_s": t_harvest, "train_s": t_train},
+        "plain": pl, "delayed": da,
+        "trial_moves_ratio": da["trial_moves_per_s"] / pl["trial_moves_per_s"],
+        "accepted_moves_ratio": da["accepted_moves_per_s"] / pl["accepted_moves_per_s"],
+        "equal_N_error_speedup": speedup,
+        "timed_steps": timed_steps,
+    }
+
+
 # ---------------------------------------------------------------- own arm
 
 def run_own(args):
@@ -268,6 +367,13 @@ def run_own(args):
     h2d = p.S * p.nmax * 16 + p.S * 4 * 2
     d2h = p.S * p.nmax * 16 + p.S * (4 + 8 + 4) + 4
 
+    da = None
+    if args.da and rank == 0:
+        da = [delayed_acceptance_arm(W.fcc100_small(seed=0), DA_SMALL, torch, stream, flush, 1_000_000,
+                                     args.da_train_steps, args.da_steps_small),
+              delayed_acceptance_arm(p, WORKLOAD, torch, stream, flush, 1_000_000, args.da_train_steps,
+                                     args.da_steps_large)]
+
     line = None
     if rank == 0:
         cpu = None
@@ -299,6 +405,7 @@ def run_own(args):
             "gpu_launches": 2 * K,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "surrogate_da": da,
         }
         print(json.dumps(line), flush=True)
     g.close()

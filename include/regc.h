@@ -305,6 +305,11 @@ REGC_API regc_status regc_mbar_solve_static(int S, const double *kT, const doubl
  * buffers on first use.  Errors: REGC_EINVAL (NULL or non-finite value). */
 REGC_API regc_status regc_surrogate_set(regc_handle *h, const float *theta);
 
+/* Seeded initial parameters on the device: every weight normal with standard
+ * deviation scale / sqrt(fan-in) (Box-Muller on Philox stream 7 keyed by
+ * seed), every bias zero; as regc_surrogate_set otherwise. */
+REGC_API regc_status regc_surrogate_init(regc_handle *h, uint64_t seed, float scale);
+
 /* Copy the master parameters to theta [REGC_SURROGATE_PARAMS] (host).
  * Errors: REGC_EINVAL (no surrogate loaded).  Synchronous. */
 REGC_API regc_status regc_surrogate_get(regc_handle *h, float *theta);

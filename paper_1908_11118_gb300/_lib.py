@@ -79,6 +79,7 @@ SIGNATURES = {
                          _dp, _dp, _dp, C.c_void_p], C.c_int),
     "regc_surrogate_set": ([_h, _fp], C.c_int),
     "regc_surrogate_get": ([_h, _fp], C.c_int),
+    "regc_surrogate_init": ([_h, C.c_uint64, C.c_float], C.c_int),
     "regc_set_mode": ([_h, C.c_int], C.c_int),
     "regc_surrogate_eval": ([_h, C.c_int, C.c_int, _fp, _fp, _fp], C.c_int),
     "regc_surrogate_harvest": ([_h, C.c_int, C.c_int, C.c_float, C.c_int, _lp], C.c_int),

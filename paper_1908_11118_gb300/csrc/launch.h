@@ -56,6 +56,10 @@ cudaError_t surrogate_step(const float* theta_in, const float* X, const float* y
                            float* partial, float* grad, float* loss, float* theta, float* m, float* v, int adam_t,
                            float lr, cudaStream_t s);
 
+// Seeded initial parameters (normal weights of standard deviation
+// scale / sqrt(fan-in), zero biases) into theta[5313].
+cudaError_t surrogate_init(float* theta, float scale, uint32_t k0, uint32_t k1, cudaStream_t s);
+
 // batch uniform row indices in [0, count) for training step `step`.
 cudaError_t surrogate_batch_index(int* idx, int batch, int count, uint32_t step, uint32_t k0, uint32_t k1,
                                   cudaStream_t s);

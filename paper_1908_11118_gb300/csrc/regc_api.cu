@@ -632,35 +632,59 @@ regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, in
 
 // ------------------------------------------------------------- surrogate
 
-regc_status regc_surrogate_set(regc_handle* h, const float* theta) {
-    if (!h || !theta) return REGC_EINVAL;
-    if (h->sticky != REGC_OK) return h->sticky;
-    for (int i = 0; i < REGC_SURROGATE_PARAMS; ++i)
-        if (!std::isfinite(theta[i])) return REGC_EINVAL;
-    regc_status st = REGC_OK;
-    if (!h->has_sur) {
-        const size_t np = REGC_SURROGATE_PARAMS;
-        if (st == REGC_OK) st = dalloc(h, &h->d_theta, np);
-        if (st == REGC_OK) st = dalloc(h, &h->d_adam_m, np);
-        if (st == REGC_OK) st = dalloc(h, &h->d_adam_v, np);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.w1, 64 * 16);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.b1, 64);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.w2, 64 * 64);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.b2, 64);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.w3, 64);
-        if (st == REGC_OK) st = dalloc(h, &h->sur.b3, 1);
-        if (st != REGC_OK) return st;
-        h->P.net = SurrogateDev{h->sur.w1, h->sur.b1, h->sur.w2, h->sur.b2, h->sur.w3, h->sur.b3};
-        h->has_sur = true;
-    }
-    cudaError_t e = cudaMemcpyAsync(h->d_theta, theta, REGC_SURROGATE_PARAMS * sizeof(float),
-                                    cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_adam_m, 0, REGC_SURROGATE_PARAMS * sizeof(float), h->stream);
+namespace {
+
+regc_status surrogate_alloc(regc_handle* h) {
+    if (h->has_sur) return REGC_OK;
+    const size_t np = REGC_SURROGATE_PARAMS;
+    regc_status st = dalloc(h, &h->d_theta, np);
+    if (st == REGC_OK) st = dalloc(h, &h->d_adam_m, np);
+    if (st == REGC_OK) st = dalloc(h, &h->d_adam_v, np);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.w1, 64 * 16);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.b1, 64);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.w2, 64 * 64);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.b2, 64);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.w3, 64);
+    if (st == REGC_OK) st = dalloc(h, &h->sur.b3, 1);
+    if (st != REGC_OK) return st;
+    h->P.net = SurrogateDev{h->sur.w1, h->sur.b1, h->sur.w2, h->sur.b2, h->sur.w3, h->sur.b3};
+    h->has_sur = true;
+    return REGC_OK;
+}
+
+// Reset the optimiser and refresh the inference copy after new master parameters.
+regc_status surrogate_loaded(regc_handle* h) {
+    cudaError_t e = cudaMemsetAsync(h->d_adam_m, 0, REGC_SURROGATE_PARAMS * sizeof(float), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_adam_v, 0, REGC_SURROGATE_PARAMS * sizeof(float), h->stream);
     if (e == cudaSuccess) e = surrogate_pack(h->d_theta, h->sur, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     h->adam_t = 0;
     return cuda_fail(h, e);
+}
+
+}  // namespace
+
+regc_status regc_surrogate_init(regc_handle* h, uint64_t seed, float scale) {
+    if (!h || !(scale >= 0.0f) || !std::isfinite(scale)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const regc_status st = surrogate_alloc(h);
+    if (st != REGC_OK) return st;
+    const cudaError_t e = surrogate_init(h->d_theta, scale, (uint32_t)seed, (uint32_t)(seed >> 32), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return surrogate_loaded(h);
+}
+
+regc_status regc_surrogate_set(regc_handle* h, const float* theta) {
+    if (!h || !theta) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    for (int i = 0; i < REGC_SURROGATE_PARAMS; ++i)
+        if (!std::isfinite(theta[i])) return REGC_EINVAL;
+    regc_status st = surrogate_alloc(h);
+    if (st != REGC_OK) return st;
+    const cudaError_t e = cudaMemcpyAsync(h->d_theta, theta, REGC_SURROGATE_PARAMS * sizeof(float),
+                                          cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return surrogate_loaded(h);
 }
 
 regc_status regc_surrogate_get(regc_handle* h, float* theta) {

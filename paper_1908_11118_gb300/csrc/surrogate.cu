@@ -282,6 +282,28 @@ __global__ void reduce_adam_kernel(const float* partial, const float* partial_lo
     }
 }
 
+// Seeded initial parameters: every weight normal with standard deviation
+// scale / sqrt(fan-in) (Box-Muller on Philox stream 7, counter (i, 0, 0, 7)),
+// every bias zero.
+__global__ void init_kernel(float* theta, float scale, uint32_t k0, uint32_t k1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    const int o1 = kNF * kNH, o2 = o1 + kNH, o3 = o2 + kNH * kNH, o4 = o3 + kNH, o5 = o4 + kNH;
+    float fan = 0.f;
+    if (i < o1) fan = (float)kNF;
+    else if (i >= o2 && i < o3) fan = (float)kNH;
+    else if (i >= o4 && i < o5) fan = (float)kNH;
+    if (fan == 0.f) {
+        theta[i] = 0.f;
+        return;
+    }
+    const U4 u = philox(uint32_t(i), 0u, 0u, 7u, k0, k1);
+    const float u1 = ((float)(u.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = (float)(u.y >> 8) * (1.0f / 16777216.0f);
+    const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    theta[i] = z * scale * rsqrtf(fan);
+}
+
 // Random row indices of a training step (Philox stream 6).
 __global__ void batch_index_kernel(int* idx, int batch, int count, uint32_t step, uint32_t k0, uint32_t k1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,6 +351,11 @@ cudaError_t surrogate_step(const float* theta_in, const float* X, const float* y
     grad_kernel<<<nblk, kRows, smem, s>>>(theta_in, X, y, idx, n, 1.0f / (float)n, partial, partial_loss);
     reduce_adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(partial, partial_loss, nblk, grad, loss, theta, m, v,
                                                               adam_t, lr);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_init(float* theta, float scale, uint32_t k0, uint32_t k1, cudaStream_t s) {
+    init_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(theta, scale, k0, k1);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,9 @@ class Regc:
         th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(SURROGATE_PARAMS))
         check(_lib.lib().regc_surrogate_set(self._h, _p(th, C.c_float)), "regc_surrogate_set")
 
+    def surrogate_init(self, seed: int, scale: float = 1.0):
+        check(_lib.lib().regc_surrogate_init(self._h, C.c_uint64(int(seed)), float(scale)), "regc_surrogate_init")
+
     def surrogate_get(self) -> np.ndarray:
         th = np.zeros(SURROGATE_PARAMS, np.float32)
         check(_lib.lib().regc_surrogate_get(self._h, _p(th, C.c_float)), "regc_surrogate_get")

@@ -376,3 +376,25 @@ def test_training_lowers_loss_and_trained_network_screens():
     assert ev_trained < ev_untrained
     # the trained screen passes moves the exact stage then accepts
     assert acc(mv_t) / pr_t[5] > acc(mv_u) / max(pr_u[5], 1)
+
+
+def test_seeded_initial_parameters():
+    p = W.fcc100_small(L=1, M=1)
+    g = Regc(p)
+    g.surrogate_init(seed=3, scale=1.0)
+    a = g.surrogate_get()
+    g.surrogate_init(seed=3, scale=1.0)
+    assert np.array_equal(a, g.surrogate_get())
+    g.surrogate_init(seed=4, scale=2.0)
+    b = g.surrogate_get()
+    m = SG.weight_mask()
+    assert np.all(a[~m] == 0.0) and np.all(b[~m] == 0.0)
+    W1, _, W2, _, W3, _ = SG.unpack(a)
+    for w, fan in ((W1, 16), (W2, 64), (W3, 64)):
+        z = np.ravel(w) * math.sqrt(fan)
+        # mean 0 and variance 1 within 5 standard errors
+        assert abs(z.mean()) < 5 / math.sqrt(z.size)
+        assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    z = np.ravel(SG.unpack(b)[2]) * 8.0 / 2.0
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    assert not np.array_equal(np.ravel(SG.unpack(b)[2]) / 2.0, np.ravel(W2))
