@@ -92,19 +92,23 @@ def job_throughput(local_ms, local_moves, world, device):
     return float(m.item()) / (tmax / 1e3), tmax
 
 
-def fp32_peak():
-    """FP32 ALU peak: measured if the peaks file has one, else unit counts x clock."""
+def fp32_peak(stream=None):
+    """FP32 ALU peak: the peaks file's, if it has one; else measured here by the
+    library's FFMA-loop probe; the unit-count figure is printed beside it."""
+    derived = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
             d = json.load(open(path))
             for k in ("fp32_tflops", "fp32_tflops_sustained"):
                 if k in d:
-                    return float(d[k]), "measured (%s)" % k
+                    return float(d[k]), "MEASURED_PEAKS.json (%s)" % k
         except Exception:
             pass
-    return SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12, \
-        "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+    from paper_1908_11118_gb300 import probe_fp32_peak
+    best = max(probe_fp32_peak(20000, stream) for _ in range(3))
+    return best, ("measured on this GPU: FFMA-loop probe (regc_probe_fp32_peak, best of 3); unit-count figure "
+                  "152 SMs x 128 lanes x 2 flop x 2070 MHz = %.1f TFLOP/s" % derived)
 
 
 class ClockSampler:
@@ -157,12 +161,13 @@ def initial_state(p, seed):
 
 # ------------------------------------------------------------- CPU oracle
 
-def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0):
+def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0, threads=0):
     """Run the FP64 oracle on the workload in steps of 10 sweeps + exchange
-    until `seconds` have passed.  Returns (moves/s, steps timed, threads)."""
+    until `seconds` have passed.  Returns (moves/s, steps timed, seconds,
+    threads used)."""
     from oracle import oracle as O
     O.build()
-    orc = O.Oracle(p, pos=pos, n=n)
+    orc = O.Oracle(p, pos=pos, n=n, n_threads=threads)
     for _ in range(warmup):
         orc.run(SWEEPS_PER_STEP, exchange_every=SWEEPS_PER_STEP, hist=True)
     steps, t0 = 0, time.perf_counter()
@@ -173,7 +178,7 @@ def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0):
         if (el >= seconds and steps >= min_steps) or (max_steps and steps >= max_steps):
             break
     moves = steps * p.S * SWEEPS_PER_STEP * p.moves_per_sweep
-    return moves / el, steps, el, os.cpu_count()
+    return moves / el, steps, el, (threads if threads > 0 else os.cpu_count())
 
 
 def run_reference(args):
@@ -259,13 +264,14 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
     loss = g.surrogate_train(train_steps, 1024, 1e-3)
     t_train = time.perf_counter() - t0
     state = g.get_walkers()
-    res = {}
+    res, se_of, mean_of = {}, {}, {}
     for mode in ("plain", "delayed"):
         g.set_walkers(state[0], state[1], state[3])
         g.set_mode(mode == "delayed")
         g.run(50, exchange_every=SWEEPS_PER_STEP)
         secs, trials, acc, pr, nb = timed_run(g, torch, stream, flush, timed_steps, 20)
         se = nb.std(axis=0, ddof=1) / np.sqrt(len(nb))
+        se_of[mode], mean_of[mode] = se, nb.mean(axis=0)
         exact = int(pr[5]) if mode == "delayed" else int(pr[3])
         res[mode] = {"trial_moves_per_s": trials / secs, "accepted_moves_per_s": acc / secs,
                      "acceptance": acc / trials, "exact_evaluations_per_accepted_move": exact / max(acc, 1),
@@ -274,8 +280,15 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
     g.set_mode(False)
     g.close()
     pl, da = res["plain"], res["delayed"]
-    # cost of reaching a given <N> error scales as time x stderr^2
-    speedup = (pl["seconds"] * pl["mean_N_stderr"] ** 2) / (da["seconds"] * da["mean_N_stderr"] ** 2)
+    # efficiency per state: eta = 1 / (stderr(<N>)^2 x time); states whose N
+    # never moved (stderr 0) carry no information and are left out
+    sp, sd = np.asarray(se_of["plain"]), np.asarray(se_of["delayed"])
+    ok = (sp > 0) & (sd > 0)
+    ratio = (sp[ok] ** 2 * pl["seconds"]) / (sd[ok] ** 2 * da["seconds"])
+    # time for every state's stderr to reach 0.02 max(1, <N>)
+    for mode, se in se_of.items():
+        tgt = 0.02 * np.maximum(1.0, mean_of[mode])
+        res[mode]["seconds_to_stderr_2pct_all_states"] = float(res[mode]["seconds"] * np.max((se / tgt) ** 2))
     return {
         "workload": name,
         "training": {"rows": rows, "harvests": harvests, "rows_per_walker_per_harvest": list(DA_ROWS_PER_WALKER),
@@ -285,7 +298,9 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
         "plain": pl, "delayed": da,
         "trial_moves_ratio": da["trial_moves_per_s"] / pl["trial_moves_per_s"],
         "accepted_moves_ratio": da["accepted_moves_per_s"] / pl["accepted_moves_per_s"],
-        "equal_N_error_speedup": speedup,
+        "eta_ratio_median": float(np.median(ratio)) if ratio.size else None,
+        "eta_ratio_worst": float(np.min(ratio)) if ratio.size else None,
+        "eta_states": int(ratio.size),
         "timed_steps": timed_steps,
     }
 
@@ -350,7 +365,7 @@ def run_own(args):
     evals = int(pr1[3] - pr0[3])
     mean_sweep_s = sum(sweep_ms) / K / 1e3
     achieved = pairs / K * FLOPS_PER_PAIR / mean_sweep_s / 1e12
-    peak, peak_src = fp32_peak()
+    peak, peak_src = fp32_peak(stream)
 
     # end to end through the C ABI with host buffers: full walker state in,
     # full walker state and energies out, every step
@@ -379,9 +394,12 @@ def run_own(args):
         cpu = None
         if world == 1:
             rate, steps, el, cores = time_oracle(p, pos0, n0, seconds=args.cpu_seconds)
+            rate1, steps1, el1, _ = time_oracle(p, pos0, n0, seconds=args.cpu_seconds / 4, threads=1)
             cpu = {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
                    "sample": "full 1024-replica workload from the seeded lattice state, "
-                             "%d steps of 10 sweeps + exchange (%.1f s)" % (steps, el)}
+                             "%d steps of 10 sweeps + exchange (%.1f s)" % (steps, el),
+                   "value_1_thread": rate1,
+                   "sample_1_thread": "%d steps on one thread (%.1f s)" % (steps1, el1)}
         line = {
             "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_max / K, "higher_is_better": True,

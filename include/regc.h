@@ -359,6 +359,14 @@ REGC_API regc_status regc_surrogate_train(regc_handle *h, int steps, int batch, 
 REGC_API regc_status regc_surrogate_gradient(int n, const float *theta, const float *X, const float *y,
                                              float *loss, float *grad, void *cuda_stream);
 
+/* ----------------------------------------------------------- measurement */
+
+/* FP32 peak of the current GPU, measured: an FFMA-loop kernel (8 independent
+ * chains per thread, 8 CTAs of 256 threads per SM, `iters` x 128 FMA per
+ * thread) timed with CUDA events on cuda_stream after one warm-up launch.
+ * *tflops receives 2 x FMAs / time in TFLOP/s.  Synchronous. */
+REGC_API regc_status regc_probe_fp32_peak(int iters, void *cuda_stream, double *tflops);
+
 /* Human-readable name of a status. */
 REGC_API const char *regc_status_string(regc_status s);
 

@@ -283,8 +283,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     // x_a + Lx is stored unshifted with a flag that shifts the query by -Lx
     // instead (exact for every query that can reach it).  Likewise for y and,
     // in a periodic box, z.
-    std::vector<int> col_off(st.nsx * st.nsy + 1, 0);
-    std::vector<float4> col_atoms;
+    std::vector<std::vector<float4>> cols(st.nsx * st.nsy);
     const int nzi = periodic_z ? 1 : 0;
     for (int iy = 0; iy < st.nsy; ++iy)
         for (int ix = 0; ix < st.nsx; ++ix) {
@@ -312,11 +311,24 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
                             v.y = by;
                             v.z = bz;
                             memcpy(&v.w, &bits, sizeof(float));
-                            col_atoms.push_back(v);
+                            cols[iy * st.nsx + ix].push_back(v);
                         }
             }
-            col_off[iy * st.nsx + ix + 1] = (int)col_atoms.size();
         }
+    // fixed-stride layout: every column padded to the same multiple of 32
+    // slots with entries out of reach (z = 1e30, flag bit 5)
+    size_t widest = 0;
+    for (const auto& c : cols) widest = std::max(widest, c.size());
+    st.stride = (int)std::max<size_t>(32, (widest + 31) / 32 * 32);
+    float4 pad;
+    pad.x = 0.0f;
+    pad.y = 0.0f;
+    pad.z = 1e30f;
+    const unsigned pad_bits = 32u;
+    memcpy(&pad.w, &pad_bits, sizeof(float));
+    std::vector<float4> col_atoms(cols.size() * (size_t)st.stride, pad);
+    for (size_t c = 0; c < cols.size(); ++c)
+        std::copy(cols[c].begin(), cols[c].end(), col_atoms.begin() + c * (size_t)st.stride);
 
     // ---- pair tables
     const double T = 1e6 * std::max(std::max(eps_max, kT_max), 1.0);
@@ -358,7 +370,6 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         }                              \
     } while (0)
     double *d_beta, *d_cins, *d_cdel, *d_ln, *d_bmu, *d_lnbeta;
-    int* d_coloff;
     float4 *d_colat, *d_all;
     TRY(dalloc(h, &d_beta, S));
     TRY(dalloc(h, &d_cins, S));
@@ -381,7 +392,6 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     P.ln_tab_f = d_ln_f;
     TRY(dalloc(h, &h->d_kT_state, S));
     TRY(dalloc(h, &h->d_mu_state, S));
-    TRY(dalloc(h, &d_coloff, col_off.size()));
     TRY(dalloc(h, &d_colat, col_atoms.size()));
     TRY(dalloc(h, &d_all, all.size()));
     TRY(upload(h, d_beta, beta.data(), S));
@@ -392,10 +402,8 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(upload(h, d_ln, ln_tab.data(), ln_tab.size()));
     TRY(upload(h, h->d_kT_state, h->kT_state.data(), S));
     TRY(upload(h, h->d_mu_state, h->mu_state.data(), S));
-    TRY(upload(h, d_coloff, col_off.data(), col_off.size()));
     TRY(upload(h, d_colat, col_atoms.data(), col_atoms.size()));
     TRY(upload(h, d_all, all.data(), all.size()));
-    st.col_off = d_coloff;
     st.atoms = d_colat;
     st.all = d_all;
     st.n_all = surf->n_atoms;

@@ -102,10 +102,11 @@ struct SurfaceTab {
     int nsx, nsy;          // surface column grid
     float isx, isy;        // columns per unit length
     float z_reach;         // surface atoms are out of reach at z >= z_reach
-    const int* col_off;    // [nsx*nsy + 1]
-    const float4* atoms;   // images listed per column: x, y, z of the image
-                           // (shifted by -L where exact), w = bits: type (0-1),
-                           // query shifted by -Lx (2), -Ly (3), -Lz (4)
+    int stride;            // slots per column, a multiple of 32
+    const float4* atoms;   // [nsx*nsy][stride] images listed per column: x, y, z
+                           // of the image (shifted by -L where exact), w = bits:
+                           // type (0-1), query shifted by -Lx (2), -Ly (3),
+                           // -Lz (4), padding slot (5; z = 1e30, out of reach)
     const float4* all;     // every surface atom, w = type (energy recompute)
     int n_all;
 };

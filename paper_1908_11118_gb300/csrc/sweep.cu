@@ -332,7 +332,7 @@ template <int NQ>
 __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, float q0x, float q0y, float q0z,
                                              float q1x, float q1y, float q1z, int sgn0, Fix3& acc, int& n_in,
                                              int& n_cand, int& overlap, int lane) {
-    const int beg = P.st.col_off[col], end = P.st.col_off[col + 1];
+    const int beg = col * P.st.stride, end = beg + P.st.stride;
     int ov = 0;
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
@@ -408,7 +408,7 @@ template <int NQ>
 __device__ __forceinline__ void feature_surface(const SweepParams& P, int col, float q0x, float q0y, float q0z,
                                                 float q1x, float q1y, float q1z, float (&F0)[kNF],
                                                 float (&F1)[kNF], int lane) {
-    const int beg = P.st.col_off[col], end = P.st.col_off[col + 1];
+    const int beg = col * P.st.stride, end = beg + P.st.stride;
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
         const unsigned bits = __float_as_uint(a.w);
