@@ -57,7 +57,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--equil", type=int, default=500, help="untimed equilibration sweeps")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--da", type=int, default=1, help="1: add the plain vs delayed-acceptance comparison")
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
@@ -367,20 +367,29 @@ def run_own(args):
     achieved = pairs / K * FLOPS_PER_PAIR / mean_sweep_s / 1e12
     peak, peak_src = fp32_peak(stream)
 
-    # end to end through the C ABI with host buffers: full walker state in,
-    # full walker state and energies out, every step
-    pos_h, n_h, e_h, sow_h = g.get_walkers()
+    # end to end through the C ABI with pinned host buffers: full walker state
+    # in (set_walkers: positions, N, labels; energies recomputed on the device),
+    # one step, full walker state and energies out, every step
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+    host = (pinned((p.S, p.nmax, 3), torch.float32), pinned((p.S,), torch.int32),
+            pinned((p.S,), torch.float64), pinned((p.S,), torch.int32))
+    g.get_walkers(out=host)
+    pos_h, n_h, e_h, sow_h = host
     e2e_steps = max(1, args.e2e_steps)
+    for _ in range(2):   # warm-up of the host path
+        g.set_walkers(pos_h, n_h, sow_h)
+        g.get_walkers(out=host)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         g.set_walkers(pos_h, n_h, sow_h)
         g.sweep(SWEEPS_PER_STEP)
         g.exchange()
-        pos_h, n_h, e_h, sow_h = g.get_walkers()
+        g.get_walkers(out=host)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = p.S * p.nmax * 16 + p.S * 4 * 2
-    d2h = p.S * p.nmax * 16 + p.S * (4 + 8 + 4) + 4
+    h2d = p.S * p.nmax * 12 + p.S * 4 * 2
+    d2h = p.S * p.nmax * 12 + p.S * (4 + 8 + 4) + 4
 
     da = None
     if args.da and rank == 0:

@@ -186,11 +186,14 @@ REGC_API void regc_free(regc_handle *h);
 /* ---------------------------------------------------------- extensions */
 
 /* Replace the walkers' configurations: pos [S][nmax][3] (binary32, x in
- * [0, Lx), y in [0, Ly), z in [z_lo, z_hi]), n [S] in 0..nmax, and optionally
- * state_of_walker [S] (a permutation of 0..S-1; NULL keeps the current labels).
- * Energies are recomputed on the device.  Host buffers.  Errors: REGC_EINVAL
- * (coordinates outside the region, N out of range, not a permutation, two
- * particles closer than 0.25 sigma). */
+ * [0, Lx), y in [0, Ly), z in [z_lo, z_hi]; entries beyond n[w] ignored),
+ * n [S] in 0..nmax, and optionally state_of_walker [S] (a permutation of
+ * 0..S-1; NULL keeps the current labels).  Host buffers (pinned memory makes
+ * the copy asynchronous and fast).  The positions are copied once and checked
+ * and repacked on the device; energies are recomputed on the device.
+ * Synchronous.  Errors: REGC_EINVAL -- N out of range or not a permutation
+ * (nothing changed), or a coordinate outside the region or a pair inside the
+ * hard-core guard radius (every walker is then left empty, N = 0). */
 REGC_API regc_status regc_set_walkers(regc_handle *h, const float *pos, const int32_t *n,
                              const int32_t *state_of_walker);
 

@@ -19,6 +19,14 @@ cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s);
 cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overlap,
                           cudaStream_t s);
 
+// Caller positions xyz [S][nmax][3] -> pos [S][nmax] (zeros beyond n[w]);
+// coordinates outside the region set ERR_INPUT in *error.
+cudaError_t pack_walkers(const float* xyz, const int* n, int S, int nmax, const Geometry& g, float4* pos, int* error,
+                         cudaStream_t s);
+
+// pos [count] -> xyz [count][3].
+cudaError_t unpack_walkers(const float4* pos, long long count, float* xyz, cudaStream_t s);
+
 // One collective exchange attempt number e.
 cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s);
 

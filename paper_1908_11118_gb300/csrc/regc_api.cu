@@ -32,6 +32,7 @@ struct regc_handle {
     std::vector<void*> allocs;
     int* d_error = nullptr;
     long long* d_fix = nullptr;               // scratch [S] for energy recomputes
+    float* d_xyz = nullptr;                   // staging [S][nmax][3] for walker I/O
     size_t smem_per_walker = 0;
     // learned surrogate (delayed acceptance)
     bool has_sur = false;
@@ -430,6 +431,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &P.pair_counts, 6));
     TRY(dalloc(h, &h->d_error, 1));
     TRY(dalloc(h, &h->d_fix, S));
+    TRY(dalloc(h, &h->d_xyz, (size_t)S * grid->nmax * 3));
     std::vector<int> ident(S);
     for (int s = 0; s < S; ++s) ident[s] = s;
     TRY(upload(h, d_sow, ident.data(), S));
@@ -533,17 +535,8 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
     if (!h || !pos || !n) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
-    std::vector<float4> p4((size_t)S * nmax, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int w = 0; w < S; ++w) {
+    for (int w = 0; w < S; ++w)
         if (n[w] < 0 || n[w] > nmax) return REGC_EINVAL;
-        for (int i = 0; i < n[w]; ++i) {
-            const float* r = pos + ((size_t)w * nmax + i) * 3;
-            const bool okx = r[0] >= 0.0f && r[0] < h->Lx, oky = r[1] >= 0.0f && r[1] < h->Ly;
-            const bool okz = h->periodic_z ? (r[2] >= 0.0f && r[2] < h->Lz) : (r[2] >= h->z_lo && r[2] <= h->z_hi);
-            if (!(okx && oky && okz)) return REGC_EINVAL;
-            p4[(size_t)w * nmax + i] = make_float4(r[0], r[1], r[2], 0.0f);
-        }
-    }
     std::vector<int> wos(S, -1);
     if (sow) {
         for (int w = 0; w < S; ++w) {
@@ -551,21 +544,22 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
             wos[sow[w]] = w;
         }
     }
-    regc_status st = upload(h, h->P.pos, p4.data(), p4.size());
-    if (st == REGC_OK) st = upload(h, h->P.n, n, S);
-    if (st == REGC_OK && sow) {
-        st = upload(h, h->X.state_of_walker, sow, S);
-        if (st == REGC_OK) st = upload(h, h->X.walker_of_state, wos.data(), S);
-    }
-    if (st != REGC_OK) return st;
-    st = cuda_fail(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream));
-    if (st == REGC_OK) st = cuda_fail(h, launch_energy(h->P, h->P.efix, 1, h->stream));
-    if (st != REGC_OK) return st;
+    // one copy of the caller's buffer; repacking and the coordinate checks run on the device
+    cudaError_t e = cudaMemcpyAsync(h->d_xyz, pos, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.n, n, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && sow)
+        e = cudaMemcpyAsync(h->X.state_of_walker, sow, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && sow)
+        e = cudaMemcpyAsync(h->X.walker_of_state, wos.data(), S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = pack_walkers(h->d_xyz, h->P.n, S, nmax, h->P.g, h->P.pos, h->d_error, h->stream);
+    if (e == cudaSuccess) e = launch_energy(h->P, h->P.efix, 1, h->stream);
     int err = 0;
-    cudaError_t e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
-    if (err & ERR_OVERLAP) {
+    if (err & (ERR_OVERLAP | ERR_INPUT)) {
         // leave a consistent state behind: no walker holds particles
         cudaMemsetAsync(h->P.n, 0, S * sizeof(int), h->stream);
         cudaMemsetAsync(h->P.efix, 0, S * sizeof(long long), h->stream);
@@ -580,12 +574,13 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
-    std::vector<float4> p4;
     std::vector<long long> ef;
     cudaError_t e = cudaSuccess;
     if (pos) {
-        p4.resize((size_t)S * nmax);
-        e = cudaMemcpyAsync(p4.data(), h->P.pos, p4.size() * sizeof(float4), cudaMemcpyDeviceToHost, h->stream);
+        e = unpack_walkers(h->P.pos, (long long)S * nmax, h->d_xyz, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pos, h->d_xyz, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                h->stream);
     }
     if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, h->P.n, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (energy && e == cudaSuccess) {
@@ -597,12 +592,6 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
     if (e != cudaSuccess) return cuda_fail(h, e);
     const regc_status st = sync_check(h);
     if (st != REGC_OK) return st;
-    if (pos)
-        for (size_t i = 0; i < p4.size(); ++i) {
-            pos[3 * i] = p4[i].x;
-            pos[3 * i + 1] = p4[i].y;
-            pos[3 * i + 2] = p4[i].z;
-        }
     if (energy)
         for (int w = 0; w < S; ++w) energy[w] = (double)ef[w] * kFixUnit;
     return REGC_OK;

@@ -18,6 +18,7 @@ enum : int {
     ERR_OVERLAP = 2,    // two particles closer than the hard-core guard radius
     ERR_TIMEOUT = 4,    // a bounded wait on an mbarrier gave up
     ERR_NUMERIC = 8,    // a non-finite energy
+    ERR_INPUT = 16,     // a caller-supplied coordinate outside the region
 };
 
 // Energies are accumulated as 64-bit fixed-point integers in units of 2^-30

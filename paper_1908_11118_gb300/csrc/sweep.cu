@@ -936,39 +936,56 @@ __device__ __forceinline__ void disp_exact(const Geometry& g, float4 q, float4 p
 }
 
 // From-scratch energy of every walker: all pairs i < j and all particle-surface
-// pairs, with the nearest periodic image.  Every pair within rc gets the same
-// rounded displacement, hence the same fixed-point term, as in the sweep.
-__global__ void __launch_bounds__(256) energy_kernel(const __grid_constant__ SweepParams P, long long* out,
-                                                     int check_overlap) {
-    const int lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= P.S) return;
+// pairs, with the nearest periodic image.  One CTA of kEnergyWarps warps per
+// walker, warp k taking particles i = k mod kEnergyWarps; the surface partners
+// of a particle come from its column of the surface table, exactly as in the
+// sweep.  Every pair within rc gets the same rounded displacement, hence the
+// same fixed-point term, as in the sweep, and fixed-point sums do not depend on
+// the order, so the result equals the sweep's running total exactly.
+constexpr int kEnergyWarps = 4;
+
+__global__ void __launch_bounds__(32 * kEnergyWarps) energy_kernel(const __grid_constant__ SweepParams P,
+                                                                   long long* out, int check_overlap) {
+    __shared__ long long part[kEnergyWarps];
+    __shared__ int ovl[kEnergyWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = blockIdx.x;
     const int N = P.n[w];
     const float4* pos = P.pos + size_t(w) * P.nmax;
-    Fix3 acc{0, 0, 0};
     long long total = 0;
     int n_in = 0, overlap = 0;
     float dx, dy, dz;
-    for (int i = 0; i < N; ++i) {
+    for (int i = warp; i < N; i += kEnergyWarps) {
+        Fix3 acc{0, 0, 0};
         const float4 pi = pos[i];
         for (int j = i + 1 + lane; j < N; j += 32) {
             disp_exact(P.g, pi, pos[j], dx, dy, dz);
             fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, P.gg, n_in, overlap), 1);
         }
-        for (int a = lane; a < P.st.n_all; a += 32) {
-            const float4 at = P.st.all[a];
-            disp_exact(P.g, pi, at, dx, dy, dz);
-            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, surf_tab(P, (int)at.w), n_in, overlap), 1);
+        if (near_surface(P, pi.z)) {
+            int n_cand = 0;
+            surface_pass<1>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, acc, n_in,
+                            n_cand, overlap, lane);
         }
-        // fold into 64 bits often enough that the int32 parts cannot overflow
+        // fold into 64 bits per particle, so that the int32 parts cannot overflow
         total += fix_value(acc.big, acc.hi, acc.lo);
-        acc = Fix3{0, 0, 0};
     }
     total = warp_sum_ll(total);
     overlap = __any_sync(FULL, overlap);
     if (lane == 0) {
-        out[w] = total;
-        if (overlap && check_overlap) atomicOr(P.error, ERR_OVERLAP);
+        part[warp] = total;
+        ovl[warp] = overlap;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        int o = 0;
+        for (int k = 0; k < kEnergyWarps; ++k) {
+            t += part[k];
+            o |= ovl[k];
+        }
+        out[w] = t;
+        if (o && check_overlap) atomicOr(P.error, ERR_OVERLAP);
     }
 }
 
@@ -1006,8 +1023,7 @@ cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
 }
 
 cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overlap, cudaStream_t s) {
-    const int wpc = 4;
-    energy_kernel<<<(P.S + wpc - 1) / wpc, 32 * wpc, 0, s>>>(P, out, check_overlap);
+    energy_kernel<<<P.S, 32 * kEnergyWarps, 0, s>>>(P, out, check_overlap);
     return cudaGetLastError();
 }
 

@@ -123,11 +123,19 @@ class Regc:
         check(_lib.lib().regc_set_walkers(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(sow, C.c_int32)),
               "regc_set_walkers")
 
-    def get_walkers(self):
-        pos = np.zeros((self.S, self.nmax, 3), np.float32)
-        n = np.zeros(self.S, np.int32)
-        e = np.zeros(self.S)
-        sow = np.zeros(self.S, np.int32)
+    def get_walkers(self, out=None):
+        """(pos [S][nmax][3] float32, n [S] int32, energy [S] float64,
+        state_of_walker [S] int32); `out` may supply those four arrays (for
+        example views of pinned host memory) to be filled in place."""
+        if out is None:
+            pos = np.zeros((self.S, self.nmax, 3), np.float32)
+            n = np.zeros(self.S, np.int32)
+            e = np.zeros(self.S)
+            sow = np.zeros(self.S, np.int32)
+        else:
+            pos, n, e, sow = out
+            assert pos.dtype == np.float32 and pos.flags.c_contiguous and pos.size == self.S * self.nmax * 3
+            assert n.dtype == np.int32 and e.dtype == np.float64 and sow.dtype == np.int32
         check(_lib.lib().regc_get_walkers(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(e, C.c_double),
                                           _p(sow, C.c_int32)), "regc_get_walkers")
         return pos, n, e, sow

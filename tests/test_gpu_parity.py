@@ -200,3 +200,31 @@ def test_torch_stream_is_used():
     ref.exchange()
     for x, y in zip(g.get_walkers(), ref.get_walkers()):
         assert np.array_equal(x, y)
+
+
+def test_walker_io_round_trip_and_checks():
+    """Walker state goes in and out bit for bit (entries beyond N are ignored on
+    the way in); a coordinate outside the region or N out of range is refused."""
+    p = W.fcc100_small(L=2, M=2)
+    pos, n = W.initial_walkers(p, np.array([0, 3, 17, 32]), seed=9)
+    pos = np.asarray(pos, np.float32).copy()
+    pos[0, :] = 123.0              # beyond N = 0: ignored
+    pos[1, 3:] = -5.0              # beyond N = 3: ignored
+    g = Regc(p)
+    g.set_walkers(pos, n, np.array([3, 2, 1, 0], np.int32))
+    pg, ng, eg, sg = g.get_walkers()
+    assert np.array_equal(ng, n) and np.array_equal(sg, [3, 2, 1, 0])
+    for w in range(p.S):
+        assert np.array_equal(pg[w, :n[w]], pos[w, :n[w]])
+    o = O.Oracle(p, pos=pos, n=n)
+    assert np.all(np.abs(eg - o.energy) <= 1e-5 * np.maximum(1.0, np.abs(o.energy)))
+    bad = pos.copy()
+    bad[2, 5, 2] = p.z_lo - 0.5    # below the region
+    with pytest.raises(Exception):
+        g.set_walkers(bad, n)
+    assert np.all(g.get_walkers()[1] == 0)       # left empty
+    with pytest.raises(Exception):
+        g.set_walkers(pos, np.array([0, 3, 17, p.nmax + 1], np.int32))
+    g.set_walkers(pos, n)
+    assert np.array_equal(g.get_walkers()[1], n)
+    assert g.check_energy() == 0.0
