@@ -362,6 +362,63 @@ REGC_API regc_status regc_surrogate_train(regc_handle *h, int steps, int batch, 
 REGC_API regc_status regc_surrogate_gradient(int n, const float *theta, const float *X, const float *y,
                                              float *loss, float *grad, void *cuda_stream);
 
+/* ---------------------------------------------------------------- batch
+ *
+ * Many systems of uneven size stepped together (the paper runs one system at
+ * a time; this is the GPU's way of filling itself with small ones).  A batch
+ * groups existing handles -- each its own surface, box, (T, mu) grid and
+ * Nmax -- without copying their state.  One batch step is, for every member,
+ * exactly what regc_sweep(h, sweeps_per_step) followed by regc_exchange(h)
+ * does, with the same Philox streams, so the results are bit-identical to
+ * stepping the members one by one; only the schedule differs:
+ *   - walkers are grouped into size classes by Nmax; each class runs as one
+ *     persistent kernel whose warps take (system, walker) items from a queue,
+ *     largest systems first, each warp one walker with its own shared memory;
+ *   - the classes run as parallel branches of one captured CUDA graph,
+ *     followed by one exchange attempt on every member's grid; the members'
+ *     Philox counters advance on the device, so steps replay the graph;
+ *   - the shape of each class's kernel (walkers per CTA, number of CTAs) is
+ *     chosen by regc_batch_autotune from timed steps.
+ * Members must be in plain mode (regc_set_mode 0), must outlive the batch,
+ * and must not be used concurrently with it: call regc_batch_sync before
+ * reading a member, and synchronise a member's own stream before running the
+ * batch after stepping that member on its own (its counters are picked up). */
+typedef struct regc_batch regc_batch;
+
+/* Create a batch over handles [count] (distinct, plain mode), stepping
+ * sweeps_per_step sweeps + one exchange attempt per step, on cuda_stream (a
+ * cudaStream_t; NULL: a stream the batch creates, which orders with work on
+ * the legacy default stream -- the legacy stream itself cannot be captured).
+ * Errors: REGC_EINVAL (bad arguments, a member in delayed-acceptance mode, a
+ * walker that does not fit one CTA's shared memory), REGC_ENOMEM, REGC_ECUDA,
+ * or a member's sticky status.  On error *out is NULL. */
+REGC_API regc_status regc_batch_create(regc_handle *const *handles, int count, int sweeps_per_step,
+                                       void *cuda_stream, regc_batch **out);
+
+/* Run n_steps steps (graph replays; the graph is captured on first use).
+ * Asynchronous on the batch's stream. */
+REGC_API regc_status regc_batch_run(regc_batch *b, int n_steps);
+
+/* Time `rounds` x (number of candidate shapes) real batch steps -- each
+ * class's kernel with walkers per CTA in 1, 2, 4, ... 16 (while its shared
+ * memory fits), CTAs = SMs x resident CTAs per SM (at most one per walker
+ * group) -- and keep each class's fastest shape.  The steps count as sampling
+ * steps (the chains advance).  Synchronous. */
+REGC_API regc_status regc_batch_autotune(regc_batch *b, int rounds);
+
+/* The current plan: *n_classes size classes; for the first max_classes of
+ * them nmax, walkers, walkers per CTA, CTAs and the last measured kernel time
+ * in ms (-1 before tuning).  Output arrays may be NULL. */
+REGC_API regc_status regc_batch_plan(const regc_batch *b, int max_classes, int *n_classes, int32_t *nmax,
+                                     int32_t *walkers, int32_t *walkers_per_cta, int32_t *ctas, double *ms);
+
+/* Wait for the batch's work and fold every member's device error word into
+ * its sticky status; returns the first error. */
+REGC_API regc_status regc_batch_sync(regc_batch *b);
+
+/* Release the batch (not its members).  NULL is accepted. */
+REGC_API void regc_batch_free(regc_batch *b);
+
 /* ----------------------------------------------------------- measurement */
 
 /* FP32 peak of the current GPU, measured: an FFMA-loop kernel (8 independent

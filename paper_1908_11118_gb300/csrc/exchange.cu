@@ -11,7 +11,8 @@
 namespace regc {
 namespace {
 
-__global__ void __launch_bounds__(1024) exchange_kernel(const __grid_constant__ ExchangeParams X, uint32_t e) {
+// One exchange attempt e of one (T, mu) grid, by the threads of one CTA.
+__device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t e) {
     const U4 C = philox(e, 0u, 0u, 2u, X.key0, X.key1);
     const int type = (int)(((unsigned long long)C.x * 4ull) >> 32);
     const int parity = (int)(C.y >> 31);
@@ -43,7 +44,35 @@ __global__ void __launch_bounds__(1024) exchange_kernel(const __grid_constant__ 
     }
 }
 
+__global__ void __launch_bounds__(1024) exchange_kernel(const __grid_constant__ ExchangeParams X, uint32_t e) {
+    exchange_grid(X, e);
+}
+
+// One exchange attempt of every grid of a batch (CTA m: grid m, attempt
+// number e_ctr[m]); afterwards each grid's exchange counter advances by one
+// and its sweep counter t0 by the sweeps just run, on the device, so that a
+// captured step can be replayed.
+__global__ void __launch_bounds__(256) batch_exchange_kernel(const ExchangeParams* xs, uint32_t* e_ctr,
+                                                             SweepParams* sys, int n_sweeps) {
+    const int m = blockIdx.x;
+    const ExchangeParams X = xs[m];
+    const uint32_t e = e_ctr[m];
+    exchange_grid(X, e);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        e_ctr[m] = e + 1u;
+        sys[m].t0 += (uint32_t)n_sweeps;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_exchange(const ExchangeParams* xs, uint32_t* e_ctr, SweepParams* sys, int n_systems,
+                                  int n_sweeps, cudaStream_t s) {
+    if (n_systems <= 0) return cudaSuccess;
+    batch_exchange_kernel<<<n_systems, 256, 0, s>>>(xs, e_ctr, sys, n_sweeps);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s) {
     exchange_kernel<<<1, 1024, 0, s>>>(X, e);

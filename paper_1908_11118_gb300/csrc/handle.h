@@ -1,0 +1,48 @@
+// handle.h -- the state behind a regc_handle (internal to the library).
+#pragma once
+
+#include <vector>
+
+#include "launch.h"
+
+using regc::ExchangeParams;
+using regc::SurrogateStore;
+using regc::SweepParams;
+
+struct regc_handle {
+    cudaStream_t stream = nullptr;
+    int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0;
+    double lambda0 = 1.0, e_lo = 0.0, e_bin = 1.0;
+    float Lx = 0, Ly = 0, Lz = 0, z_lo = 0, z_hi = 0;
+    int periodic_z = 0;
+    std::vector<double> kT_state, mu_state;   // per state
+    double* d_kT_state = nullptr;
+    double* d_mu_state = nullptr;
+    SweepParams P{};
+    ExchangeParams X{};
+    uint32_t t = 0, e = 0;
+    regc_status sticky = REGC_OK;
+    std::vector<void*> allocs;
+    int* d_error = nullptr;
+    long long* d_fix = nullptr;               // scratch [S] for energy recomputes
+    float* d_xyz = nullptr;                   // staging [S][nmax][3] for walker I/O
+    size_t smem_per_walker = 0;
+    // learned surrogate (delayed acceptance)
+    bool has_sur = false;
+    float* d_theta = nullptr;                 // [5313] binary32 master parameters
+    float* d_adam_m = nullptr;
+    float* d_adam_v = nullptr;
+    int adam_t = 0;
+    SurrogateStore sur{};
+    float* d_X = nullptr;                     // data set ring [cap][16]
+    float* d_y = nullptr;                     // [cap]
+    int ds_cap = 0, ds_count = 0, ds_next = 0;
+    uint32_t harvest_round = 0;
+};
+
+// Synchronise the handle's stream and fold its device error word into the
+// sticky status.
+regc_status handle_sync_check(regc_handle* h);
+
+// Record a CUDA error as the handle's sticky status; returns the status.
+regc_status handle_cuda_fail(regc_handle* h, cudaError_t e);

@@ -11,41 +11,12 @@
 #include <new>
 #include <vector>
 
+#include "handle.h"
 #include "launch.h"
 #include "mbar.h"
 
 using namespace regc;
 
-struct regc_handle {
-    cudaStream_t stream = nullptr;
-    int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0;
-    double lambda0 = 1.0, e_lo = 0.0, e_bin = 1.0;
-    float Lx = 0, Ly = 0, Lz = 0, z_lo = 0, z_hi = 0;
-    int periodic_z = 0;
-    std::vector<double> kT_state, mu_state;   // per state
-    double* d_kT_state = nullptr;
-    double* d_mu_state = nullptr;
-    SweepParams P{};
-    ExchangeParams X{};
-    uint32_t t = 0, e = 0;
-    regc_status sticky = REGC_OK;
-    std::vector<void*> allocs;
-    int* d_error = nullptr;
-    long long* d_fix = nullptr;               // scratch [S] for energy recomputes
-    float* d_xyz = nullptr;                   // staging [S][nmax][3] for walker I/O
-    size_t smem_per_walker = 0;
-    // learned surrogate (delayed acceptance)
-    bool has_sur = false;
-    float* d_theta = nullptr;                 // [5313] binary32 master parameters
-    float* d_adam_m = nullptr;
-    float* d_adam_v = nullptr;
-    int adam_t = 0;
-    SurrogateStore sur{};
-    float* d_X = nullptr;                     // data set ring [cap][16]
-    float* d_y = nullptr;                     // [cap]
-    int ds_cap = 0, ds_count = 0, ds_next = 0;
-    uint32_t harvest_round = 0;
-};
 
 namespace {
 
@@ -113,6 +84,10 @@ float hard_core_r2(double eps, double sigma, double T) {
 }
 
 }  // namespace
+
+regc_status handle_sync_check(regc_handle* h) { return sync_check(h); }
+
+regc_status handle_cuda_fail(regc_handle* h, cudaError_t e) { return cuda_fail(h, e); }
 
 extern "C" {
 

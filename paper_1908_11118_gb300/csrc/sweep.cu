@@ -165,6 +165,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
@@ -678,12 +682,11 @@ __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay,
     return r2_of(dx, dy, dz);
 }
 
+// n_sweeps sweeps of walker w by a group of K warps (tid: thread index in the
+// group, smem: the group's shared-memory region).
 template <int K, bool TRACE, bool DA>
-__global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
-    extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = blockIdx.x;
-    if (w >= P.S) return;
+__device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* smem, int tid) {
+    const int lane = tid & 31, warp = tid >> 5;
     const WalkerSmem S = carve<K>(smem, P);
 
     int N = P.n[w];
@@ -694,22 +697,27 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
 
     // 1. stage positions with a bulk copy
     if (N > 0) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             mbar_init(S.bar);
+            // the region may have been read and written by ordinary accesses
+            // (a previous walker): order those before the asynchronous copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bulk_load(S.pos, gpos, uint32_t(N) * 16u, S.bar);
         }
         group_sync<K>();
         const bool ok = mbar_wait_bounded(S.bar);
         const bool all_ok = (K == 1) ? (__all_sync(FULL, ok) != 0) : (__syncthreads_and(ok) != 0);
         if (!all_ok) {
-            if (threadIdx.x == 0) atomicOr(P.error, ERR_TIMEOUT);
+            if (tid == 0) atomicOr(P.error, ERR_TIMEOUT);
             mbar_wait_bounded(S.bar);  // one more bounded chance for the copy in flight
             return;
         }
+        group_sync<K>();
+        if (tid == 0) mbar_inval(S.bar);   // the barrier's memory is reused by the next walker
     }
     // 2. cell list
     if (warp == 0) build_cells(P, S, N, lane);
-    if (threadIdx.x == 0)
+    if (tid == 0)
         *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}};
     group_sync<K>();
 
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
     while (m0 < total_moves) {
         // 3a. Philox blocks of the next 32 moves, drawn by all lanes at once
         if (m0 + K > filled) {
-            for (int q = threadIdx.x; q < 64; q += 32 * K) {
+            for (int q = tid; q < 64; q += 32 * K) {
                 const int m = filled + (q >> 1);
                 if (m < total_moves) {
                     const int ts = m / P.mps;
@@ -740,7 +748,7 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
         group_sync<K>();
 
         // 4. commit in order (thread 0)
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             int committed = 0;
             bool any_acc = false, n_changed = false;
             float chx[2 * K], chy[2 * K], chz[2 * K];   // positions changed by accepted moves
@@ -900,11 +908,11 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
     }
 
     // 7. write back
-    for (int j = threadIdx.x; j < N; j += 32 * K) gpos[j] = S.pos[j];
+    for (int j = tid; j < N; j += 32 * K) gpos[j] = S.pos[j];
     // candidate distances evaluated (all evaluations, kept or not)
     const unsigned sum_cand = __reduce_add_sync(FULL, (unsigned)n_cand);
     if (lane == 0) atomicAdd(&P.pair_counts[1], (unsigned long long)sum_cand);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         const WalkerStats& st = *S.stats;
         atomicAdd(&P.pair_counts[0], st.pairs);
         atomicAdd(&P.pair_counts[2], st.rounds);
@@ -926,6 +934,14 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
             mc[2 * k + 1] += st.ac[k];
         }
     }
+}
+
+
+template <int K, bool TRACE, bool DA>
+__global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
+    extern __shared__ __align__(16) char smem[];
+    if (blockIdx.x >= (unsigned)P.S) return;
+    walker_sweep<K, TRACE, DA>(P, blockIdx.x, smem, threadIdx.x);
 }
 
 // Displacement q - p with the exact minimum image on periodic axes.
@@ -1005,7 +1021,62 @@ cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Persistent sweep of a batch of walkers from several systems.  Every warp of
+// the CTA is one walker at a time: lane 0 takes the next (system, walker) item
+// from the queue, the warp copies that system's parameters into its slot of
+// shared memory and runs the walker's sweeps in its own shared-memory region
+// of `region` bytes; items are listed largest first, so the queue balances
+// the uneven costs.
+constexpr int kBatchMaxWarps = 16;
+
+__global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_sweep_kernel(const SweepParams* __restrict__ sys,
+                                                                        const int2* __restrict__ items, int n_items,
+                                                                        int* counter, int region) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ SweepParams Psh[kBatchMaxWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    char* mine = smem + (size_t)warp * region;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= n_items) break;
+        const int2 mw = items[item];
+        const int* src = reinterpret_cast<const int*>(sys + mw.x);
+        int* dst = reinterpret_cast<int*>(&Psh[warp]);
+        for (int k = lane; k < (int)(sizeof(SweepParams) / sizeof(int)); k += 32) dst[k] = src[k];
+        __syncwarp();
+        walker_sweep<1, false, false>(Psh[warp], mw.y, mine, lane);
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+size_t batch_static_smem() { return sizeof(SweepParams) * kBatchMaxWarps; }
+
+int batch_max_warps() { return kBatchMaxWarps; }
+
+cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
+                               int warps_per_cta, int grid, int region, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (warps_per_cta < 1 || warps_per_cta > kBatchMaxWarps || grid < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)warps_per_cta * region;
+    batch_sweep_kernel<<<grid, 32 * warps_per_cta, smem, s>>>(sys, items, n_items, counter, region);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_prepare(int max_dynamic_smem) {
+    return cudaFuncSetAttribute(batch_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
+}
+
+int batch_occupancy(int warps_per_cta, int region) {
+    const size_t smem = (size_t)warps_per_cta * region;   // within the limit batch_prepare set
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_sweep_kernel, 32 * warps_per_cta, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
 
 size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker) {
     return smem_bytes(nmax, ncell, cap, warps_per_walker);

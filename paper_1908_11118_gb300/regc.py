@@ -225,6 +225,59 @@ class Regc:
         return nm, pN, f, it.value
 
 
+class Batch:
+    """Several Regc handles (systems of uneven size) stepped together: one
+    step = sweeps_per_step sweeps + one exchange attempt of every member,
+    bit-identical to stepping the members one by one."""
+
+    def __init__(self, members, sweeps_per_step: int = 10, stream=None):
+        self.members = list(members)          # the members must outlive the batch
+        arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        b = C.c_void_p()
+        check(_lib.lib().regc_batch_create(arr, len(self.members), int(sweeps_per_step), _stream_handle(stream),
+                                           C.byref(b)), "regc_batch_create")
+        self._b = b
+        self.sweeps_per_step = int(sweeps_per_step)
+
+    def run(self, n_steps: int = 1):
+        check(_lib.lib().regc_batch_run(self._b, int(n_steps)), "regc_batch_run")
+
+    def autotune(self, rounds: int = 1):
+        check(_lib.lib().regc_batch_autotune(self._b, int(rounds)), "regc_batch_autotune")
+
+    def sync(self):
+        check(_lib.lib().regc_batch_sync(self._b), "regc_batch_sync")
+
+    def plan(self):
+        n = C.c_int(0)
+        check(_lib.lib().regc_batch_plan(self._b, 0, C.byref(n), None, None, None, None, None), "regc_batch_plan")
+        k = n.value
+        nm, wk, wpc, ctas = (np.zeros(k, np.int32) for _ in range(4))
+        ms = np.zeros(k)
+        check(_lib.lib().regc_batch_plan(self._b, k, C.byref(n), _p(nm, C.c_int32), _p(wk, C.c_int32),
+                                         _p(wpc, C.c_int32), _p(ctas, C.c_int32), _p(ms, C.c_double)),
+              "regc_batch_plan")
+        return [{"nmax": int(nm[i]), "walkers": int(wk[i]), "walkers_per_cta": int(wpc[i]), "ctas": int(ctas[i]),
+                 "ms": float(ms[i])} for i in range(k)]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.lib().regc_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def surrogate_gradient(theta, X, y, stream=None):
     """Mean squared error of the surrogate with parameters theta on rows (X, y)
     and its gradient, from the library's training kernels."""

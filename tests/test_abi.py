@@ -99,3 +99,14 @@ def test_move_record_layout_matches_header(tmp_path):
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert out[0] == MOVE_DTYPE.itemsize
     assert out[1:] == [MOVE_DTYPE.fields[f][1] for f in fields]
+
+
+def test_batch_argument_checks_without_gpu(lib):
+    out = C.c_void_p(123)
+    arr = (C.c_void_p * 1)(None)
+    assert lib.regc_batch_create(arr, 0, 10, None, C.byref(out)) == -1 and not out.value
+    assert lib.regc_batch_create(arr, 1, 10, None, C.byref(out)) == -1 and not out.value
+    assert lib.regc_batch_create(None, 1, 10, None, C.byref(out)) == -1
+    assert lib.regc_batch_run(None, 1) == -1
+    assert lib.regc_batch_sync(None) == -1
+    lib.regc_batch_free(None)

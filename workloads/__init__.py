@@ -240,6 +240,55 @@ def initial_walkers(problem: Problem, n_init, seed: int, min_dist: float = 0.9):
     return pos, n
 
 
+def lattice_sites(problem: Problem, spacing: float = 1.1, clearance: float = 0.95) -> int:
+    """Number of sites lattice_walkers can fill in the problem's region."""
+    nx = int(problem.Lx // spacing)
+    ny = int(problem.Ly // spacing)
+    z0 = problem.z_lo + (0.0 if problem.periodic_z else clearance)
+    nz = int((problem.z_hi - 0.05 - z0) // spacing) + 1
+    z = z0 + 0.05 + np.arange(nz) * spacing
+    return nx * ny * int(np.sum(z <= problem.z_hi - 0.05))
+
+
+def uneven_batch(n_systems: int = 256, L: int = 4, M: int = 4, seed: int = 0, nmax_exp=(6, 11),
+                 side=(6, 16), height=(8.0, 16.0)):
+    """The batched uneven workload: n_systems independent systems, each an
+    L x M (kT, mu) grid (the grids of fcc100_small) over its own 3-layer
+    fcc(100) slab (spacing 1.5625) of nx x ny atoms, nx, ny ~ U{side}, with a
+    gas region of height ~ U[height] above the top layer and Nmax = 2^k,
+    k ~ U{nmax_exp}.  System i is keyed by seed * 100003 + i.  Returns a list
+    of Problems."""
+    rng = np.random.default_rng(seed)
+    eps, sig = _pair_tables(1.0, 1.0, 2.0, 1.0)
+    out = []
+    for i in range(n_systems):
+        nx, ny = (int(v) for v in rng.integers(side[0], side[1] + 1, size=2))
+        h = float(rng.uniform(*height))
+        nmax = int(2 ** int(rng.integers(nmax_exp[0], nmax_exp[1] + 1)))
+        xyz, lx, ly, ztop = fcc100_slab(nx, ny, 3, 1.5625)
+        zhi = float(f32(ztop + h))
+        e_bin = max(0.05, nmax / 256.0)
+        out.append(Problem(
+            n_types=2, eps=eps, sigma=sig, rc=2.5, Lx=lx, Ly=ly, Lz=zhi, periodic_z=0,
+            z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+            kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
+            max_disp=0.2, p_disp=1.0 / 3.0, seed=seed * 100003 + i,
+            e_lo=-float(nmax) * 14.0, e_bin=e_bin, n_e_bins=int(round(float(nmax) * 15.0 / e_bin)),
+            name="uneven_%d" % i))
+    return out
+
+
+def uneven_initial(problem: Problem, seed: int):
+    """Initial walkers of the batched uneven workload: N ~ U{0..Nmax/2} per
+    walker, capped at 90 % of the lattice sites that fit the region (a small
+    box cannot hold Nmax/2 particles without overlaps), on the jittered
+    lattice of lattice_walkers."""
+    rng = np.random.default_rng(seed)
+    cap = int(0.9 * lattice_sites(problem))
+    n0 = np.minimum(rng.integers(0, problem.nmax // 2 + 1, problem.S), cap)
+    return lattice_walkers(problem, n0, seed=seed)
+
+
 def lattice_walkers(problem: Problem, n_init, seed: int, spacing: float = 1.1,
                     clearance: float = 0.95):
     """Fast seeded initial configurations for large runs: walker w gets
