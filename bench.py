@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--da", type=int, default=1, help="1: add the plain vs delayed-acceptance comparison")
+    ap.add_argument("--batch", type=int, default=1, help="1: add the batched uneven workload")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
     ap.add_argument("--da-steps-large", type=int, default=60)
@@ -305,6 +307,86 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
     }
 
 
+# ------------------------------------------------------ batched uneven arm
+
+BATCH_WORKLOAD = ("256 systems x (4 kT x 4 mu) = 4096 replicas; 3-layer fcc(100) slabs of nx x ny atoms, "
+                  "nx, ny ~ U{6..16}; gas 8-16 high; Nmax = 2^k, k ~ U{6..11}; N0 ~ U{0..Nmax/2} capped at "
+                  "90% of a 1.1-spacing lattice; step = 10 sweeps + 1 exchange attempt per system")
+
+
+def batched_uneven_arm(torch, steps, seed=0):
+    """The batched uneven workload: every system's walkers in size-class
+    persistent kernels of one captured graph (autotuned), against the same
+    systems stepped one handle at a time."""
+    from paper_1908_11118_gb300 import Batch, Regc
+
+    ps = W.uneven_batch(256, seed=seed)
+    t0 = time.perf_counter()
+    hs = []
+    for i, p in enumerate(ps):
+        pos, n = W.uneven_initial(p, seed * 7919 + i)
+        h = Regc(p)
+        h.set_walkers(pos, n)
+        hs.append(h)
+    t_setup = time.perf_counter() - t0
+    S = sum(p.S for p in ps)
+    moves_per_step = S * SWEEPS_PER_STEP * 20
+    stream = torch.cuda.Stream()
+    bt = Batch(hs, sweeps_per_step=SWEEPS_PER_STEP, stream=stream)
+    plan_default = bt.plan()
+    t0 = time.perf_counter()
+    bt.autotune(1)
+    t_tune = time.perf_counter() - t0
+    bt.run(3)                                   # warm-up (captures the graph)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.run(1)
+        b.record(stream)
+        ev.append((a, b))
+    bt.sync()
+    batched_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    # the same systems, one handle after another on one stream (a fixed number of steps)
+    k1 = max(2, steps // 5)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(k1):
+        for h in hs:
+            h.sweep(SWEEPS_PER_STEP)
+            h.exchange()
+    b.record()
+    torch.cuda.synchronize()
+    single_s = a.elapsed_time(b) / 1e3
+    drift = max(h.check_energy() for h in hs)
+    acc = sum(int(h.counters()[0][:, :, 1].sum()) for h in hs)
+    trials = sum(int(h.counters()[0][:, :, 0].sum()) for h in hs)
+    out = {
+        "workload": BATCH_WORKLOAD,
+        "replicas": S,
+        "nmax_classes": sorted({p.nmax for p in ps}),
+        "trial_moves_per_s": moves_per_step * steps / batched_s,
+        "ms_per_step": batched_s / steps * 1e3,
+        "one_handle_at_a_time_moves_per_s": moves_per_step * k1 / single_s,
+        "acceptance": acc / max(trials, 1),
+        "plan_default": plan_default,
+        "plan_tuned": bt.plan(),
+        "setup_s": t_setup,
+        "autotune_s": t_tune,
+        "energy_drift_max": drift,
+        "timed_steps": steps,
+        "l2": "flushed (256 MB memset) before every timed step",
+    }
+    bt.close()
+    for h in hs:
+        h.close()
+    return out
+
+
 # ---------------------------------------------------------------- own arm
 
 def run_own(args):
@@ -391,6 +473,10 @@ def run_own(args):
     h2d = p.S * p.nmax * 12 + p.S * 4 * 2
     d2h = p.S * p.nmax * 12 + p.S * (4 + 8 + 4) + 4
 
+    batched = None
+    if args.batch and rank == 0:
+        batched = batched_uneven_arm(torch, args.batch_steps)
+
     da = None
     if args.da and rank == 0:
         da = [delayed_acceptance_arm(W.fcc100_small(seed=0), DA_SMALL, torch, stream, flush, 1_000_000,
@@ -433,6 +519,7 @@ def run_own(args):
             "clocks": clk,
             "cpu_baseline": cpu,
             "surrogate_da": da,
+            "batched_uneven": batched,
         }
         print(json.dumps(line), flush=True)
     g.close()
