@@ -61,6 +61,8 @@ class _System(C.Structure):
         ("mutation", C.c_int),
         ("da", C.c_int),
         ("sur_theta", C.POINTER(C.c_double)),
+        ("n_cluster", C.c_int),
+        ("cluster_type", C.c_int),
     ]
 
 
@@ -167,6 +169,8 @@ class Oracle:
         s.seed = int(problem.seed)
         s.e_lo, s.e_bin, s.n_e_bins = problem.e_lo, problem.e_bin, problem.n_e_bins
         s.mutation = int(mutation)
+        s.n_cluster = int(getattr(problem, "n_cluster", 0))
+        s.cluster_type = int(getattr(problem, "cluster_type", 0))
         self._theta = None
         if surrogate is not None:
             self._theta = np.ascontiguousarray(surrogate, np.float64)

@@ -31,6 +31,7 @@
  *   32  minimum image not applied along y
  *   64  removal: energy taken of particle i but particle (i+1) mod N removed
  *   128 delayed acceptance: stage 2 without the -dE~ correction
+ *   256 cluster: insertion/removal ratios with the total N instead of N_B
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -141,28 +142,38 @@ static void account(const oracle_system *sys, int ti, int tj, double r2, double 
     }
 }
 
+/* Potential type of mobile particle j: the cluster species for the first
+ * n_cluster particles, else the grand-canonical species 0. */
+static int species(const oracle_system *sys, int j)
+{
+    return j < sys->n_cluster ? sys->cluster_type : 0;
+}
+
 /* Interaction energy of a mobile particle at (x, y, z) with every surface atom
  * and every mobile particle j != skip (the moved particle's energy entering
- * E(R; N) in Eq. Ngrand). */
+ * E(R; N) in Eq. Ngrand).  The moved particle is particle `skip` (its species
+ * decides the pair types) or, for skip < 0, a new grand-canonical particle. */
 double oracle_particle_energy(const oracle_system *sys, const double *pos, int n,
                               double x, double y, double z, int skip,
                               double *sum_abs, double *band, int *n_pairs)
 {
+    const int ti = skip >= 0 ? species(sys, skip) : 0;
     double e = 0.0;
     for (int a = 0; a < sys->n_surf; ++a) {
         const double *ra = sys->surf_xyz + 3 * a;
         int ta = sys->surf_type[a];
         double r2 = pair_r2(sys, x, y, z, ra[0], ra[1], ra[2]);
-        double phi = oracle_phi(sys, 0, ta, r2);
-        account(sys, 0, ta, r2, phi, sum_abs, band, n_pairs);
+        double phi = oracle_phi(sys, ti, ta, r2);
+        account(sys, ti, ta, r2, phi, sum_abs, band, n_pairs);
         e += phi;
     }
     for (int j = 0; j < n; ++j) {
         if (j == skip) continue;
         const double *rj = pos + 3 * j;
+        const int tj = species(sys, j);
         double r2 = pair_r2(sys, x, y, z, rj[0], rj[1], rj[2]);
-        double phi = oracle_phi(sys, 0, 0, r2);
-        account(sys, 0, 0, r2, phi, sum_abs, band, n_pairs);
+        double phi = oracle_phi(sys, ti, tj, r2);
+        account(sys, ti, tj, r2, phi, sum_abs, band, n_pairs);
         e += phi;
     }
     return e;
@@ -175,14 +186,16 @@ double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
     double e = 0.0;
     for (int i = 0; i < n; ++i) {
         const double *ri = pos + 3 * i;
+        const int ti = species(sys, i);
         for (int a = 0; a < sys->n_surf; ++a) {
             const double *ra = sys->surf_xyz + 3 * a;
-            e += oracle_phi(sys, 0, sys->surf_type[a],
+            e += oracle_phi(sys, ti, sys->surf_type[a],
                             pair_r2(sys, ri[0], ri[1], ri[2], ra[0], ra[1], ra[2]));
         }
         for (int j = i + 1; j < n; ++j) {
             const double *rj = pos + 3 * j;
-            e += oracle_phi(sys, 0, 0, pair_r2(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2]));
+            e += oracle_phi(sys, ti, species(sys, j),
+                            pair_r2(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2]));
         }
     }
     return e;
@@ -204,6 +217,7 @@ double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int 
                                double x, double y, double z, int skip, double *feat)
 {
     const double rc = sys->rc, width = 1.7 / 15.0, eta = 1.0 / (2.0 * width * width);
+    const int ti = skip >= 0 ? species(sys, skip) : 0;   /* weights eps between the moved species and j */
     double G[SUR_NF];
     for (int k = 0; k < SUR_NF; ++k) G[k] = 0.0;
     for (int j = -sys->n_surf; j < n; ++j) {
@@ -215,11 +229,11 @@ double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int 
         } else {
             if (j == skip) continue;
             r = pos + 3 * j;
-            t = 0;
+            t = species(sys, j);
         }
         double d = sqrt(pair_r2(sys, x, y, z, r[0], r[1], r[2]));
         if (d >= rc) continue;
-        double fc = 0.5 * (cos(M_PI * d / rc) + 1.0) * sys->eps[0][t];
+        double fc = 0.5 * (cos(M_PI * d / rc) + 1.0) * sys->eps[ti][t];
         for (int k = 0; k < SUR_NF; ++k) {
             double c = 0.8 + 1.7 * k / 15.0;
             G[k] += exp(-eta * (d - c) * (d - c)) * fc;
@@ -327,6 +341,13 @@ static void observe(const oracle_system *sys, oracle_hist *h, int state, int n, 
     }
 }
 
+/* The particle count entering the grand-canonical ratios: N_B = N - n_cluster
+ * (mutation 256: the total N). */
+static int n_gc(const oracle_system *sys, int n)
+{
+    return (sys->mutation & 256) ? n : n - sys->n_cluster;
+}
+
 static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr,
                          double *e_ptr, int state, uint32_t t0, int n_sweeps,
                          oracle_hist *hist, oracle_move *trace, int64_t *counts)
@@ -398,16 +419,17 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
                 if (sys->periodic_z && nz >= lz) nz = f32(nz - lz);
                 mv.dE = oracle_particle_energy(sys, pos, n, nx, ny, nz, -1,
                                                &mv.sum_abs, &mv.band, &mv.n_pairs);
-                mv.log_alpha = oracle_log_alpha(sys, 1, state, n, mv.dE);
+                mv.log_alpha = oracle_log_alpha(sys, 1, state, n_gc(sys, n), mv.dE);
             } else {
-                /* removal of particle i, (i-1)/N <= y2 < i/N (Sec. II.A.1) */
-                if (n == 0) { mv.status = 1; goto decided; }
-                i = (int)(((uint64_t)B[0] * (uint64_t)n) >> 32);
+                /* removal of grand-canonical particle i, (i-1)/N <= y2 < i/N
+                 * (Sec. II.A.1), counted among the N_B of that species */
+                if (n == sys->n_cluster) { mv.status = 1; goto decided; }
+                i = sys->n_cluster + (int)(((uint64_t)B[0] * (uint64_t)(n - sys->n_cluster)) >> 32);
                 mv.index = i;
                 const double *ri = pos + 3 * i;
                 mv.dE = -oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
                                                 &mv.sum_abs, &mv.band, &mv.n_pairs);
-                mv.log_alpha = oracle_log_alpha(sys, 2, state, n, mv.dE);
+                mv.log_alpha = oracle_log_alpha(sys, 2, state, n_gc(sys, n), mv.dE);
             }
             if (sys->da) {
                 /* stage 1 with the surrogate energy change */
@@ -422,7 +444,7 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
                     mv.dE_sur = -oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
                 }
                 mv.ln_u1 = log(u32_open(B[3]));
-                mv.stage1 = mv.ln_u1 < oracle_log_alpha(sys, mv.type, state, n, mv.dE_sur);
+                mv.stage1 = mv.ln_u1 < oracle_log_alpha(sys, mv.type, state, n_gc(sys, n), mv.dE_sur);
                 /* stage 2: the exact correction */
                 double corr = (sys->mutation & 128) ? 0.0 : mv.dE_sur;
                 mv.accepted = mv.stage1 && mv.ln_u < -beta * (mv.dE - corr);
@@ -451,7 +473,7 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
             }
             if (trace) trace[((int64_t)ts * sys->moves_per_sweep + k)] = mv;
         }
-        observe(sys, hist, state, n, e);
+        observe(sys, hist, state, n - sys->n_cluster, e);
     }
     *n_ptr = n;
     *e_ptr = e;

@@ -64,6 +64,13 @@ typedef struct {
      * of the surrogate network (layout in oracle/surrogate.py) */
     int           da;
     const double *sur_theta;
+    /* a second mobile species (the cluster of configuration 5; not in the
+     * paper): particles 0..n_cluster-1 of every walker have potential type
+     * cluster_type and move only by displacement; insertion and removal act on
+     * the grand-canonical species (type 0), whose count N_B = N - n_cluster
+     * enters the acceptance ratios and the histograms */
+    int           n_cluster;
+    int           cluster_type;
 } oracle_system;
 
 /* One trial move as the oracle executed it. */
@@ -85,6 +92,7 @@ typedef struct {
 } oracle_move;
 
 /* Histograms filled once per sweep, at the walker's current state. */
+/* With a cluster, N below means N_B, the grand-canonical count. */
 typedef struct {
     int64_t *hN;        /* [S][nmax+1] occupation counts of N            */
     int64_t *hNE;       /* [nmax+1][n_e_bins] pooled (N, E-bin) counts   */

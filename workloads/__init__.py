@@ -62,6 +62,10 @@ class Problem:
     e_bin: float
     n_e_bins: int
     name: str = "custom"
+    # a second mobile species (configuration 5): particles 0..n_cluster-1 of
+    # every walker have potential type cluster_type and only displace
+    n_cluster: int = 0
+    cluster_type: int = 0
 
     def __post_init__(self):
         # the C ABI carries these as binary32: round them here, once, so that
@@ -276,6 +280,59 @@ def uneven_batch(n_systems: int = 256, L: int = 4, M: int = 4, seed: int = 0, nm
             e_lo=-float(nmax) * 14.0, e_bin=e_bin, n_e_bins=int(round(float(nmax) * 15.0 / e_bin)),
             name="uneven_%d" % i))
     return out
+
+
+def cluster_in_gas(L: int = 64, M: int = 64, nmax_b: int = 64, box: float = 15.0, seed: int = 0) -> Problem:
+    """The cluster-in-gas workload: a fully periodic cube of edge `box` with no
+    surface, a 4-atom cluster of species A (type 1: eps_AA = 4, sigma_AA = 1.1;
+    displacement only) in a gas of species B (type 0: eps_BB = 0.5, sigma_BB =
+    1; grand-canonical), eps_AB = 2, sigma_AB = 1, rc = 2.5 for every pair; the
+    (kT, mu) grids of fcc100_small with L x M states; Nmax_B = nmax_b."""
+    eps = np.zeros((4, 4))
+    sig = np.ones((4, 4))
+    eps[0, 0] = 0.5
+    eps[0, 1] = eps[1, 0] = 2.0
+    eps[1, 1] = 4.0
+    sig[1, 1] = 1.1
+    return Problem(
+        n_types=2, eps=eps, sigma=sig, rc=2.5, Lx=box, Ly=box, Lz=box, periodic_z=1,
+        z_lo=0.0, z_hi=box, surf_xyz=np.zeros((0, 3)), surf_type=np.zeros(0, np.int32),
+        kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax_b + 4, moves_per_sweep=20,
+        max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
+        e_lo=-float(nmax_b) * 16.0 - 40.0, e_bin=0.25, n_e_bins=int(round((float(nmax_b) * 17.0 + 40.0) / 0.25)),
+        name="cluster_in_gas", n_cluster=4, cluster_type=1)
+
+
+def cluster_initial(problem: Problem, n_b, seed: int, spacing: float = 1.25):
+    """Walkers of a cluster problem: the n_cluster atoms as a regular
+    tetrahedron (edge 2^(1/6) sigma_AA) at the box centre (first n_cluster
+    slots; a single atom sits at the centre), then n_b[w] B particles on
+    jittered lattice sites at least 1.2 from every cluster atom."""
+    rng = np.random.default_rng(seed)
+    S, nmax, nc = problem.S, problem.nmax, problem.n_cluster
+    c = np.array([problem.Lx, problem.Ly, problem.Lz]) / 2.0
+    a = 2.0 ** (1.0 / 6.0) * float(problem.sigma[problem.cluster_type, problem.cluster_type])
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float) * a / (2.0 * math.sqrt(2.0))
+    clus = f32(c + (tet[:nc] if nc > 1 else np.zeros((nc, 3))))
+    n1 = int(problem.Lx // spacing)
+    g = (np.arange(n1) + 0.5) * (problem.Lx / n1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    sites = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if nc:
+        d = np.min(np.linalg.norm(sites[:, None, :] - clus[None, :, :], axis=2), axis=1)
+        sites = sites[d > 1.2]
+    n_b = np.broadcast_to(np.asarray(n_b, np.int64), (S,))
+    if n_b.max() + nc > nmax or n_b.max() > len(sites):
+        raise ValueError("too many particles")
+    pos = np.zeros((S, nmax, 3))
+    for w in range(S):
+        pos[w, :nc] = clus
+        k = int(n_b[w])
+        pick = rng.choice(len(sites), size=k, replace=False)
+        p = f32((sites[pick] + rng.uniform(-0.05, 0.05, size=(k, 3))) % problem.Lx)
+        p = np.where(p >= problem.Lx, 0.0, p)
+        pos[w, nc:nc + k] = p
+    return pos, (n_b + nc).astype(np.int32)
 
 
 def uneven_initial(problem: Problem, seed: int):
