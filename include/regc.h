@@ -197,6 +197,23 @@ REGC_API void regc_free(regc_handle *h);
 REGC_API regc_status regc_set_walkers(regc_handle *h, const float *pos, const int32_t *n,
                              const int32_t *state_of_walker);
 
+/* A second mobile species, the "cluster" (not in the paper; the cluster-in-
+ * gas workload): particles 0..n_cluster-1 of every walker are of potential
+ * type cluster_type (1..n_types-1; pairs with the grand-canonical species use
+ * eps/sigma[0][cluster_type], with each other [cluster_type][cluster_type],
+ * with surface type t [cluster_type][t]) and move only by displacement;
+ * insertion and removal act on type 0, whose count N_B = N - n_cluster enters
+ * the acceptance ratios of Sec. II.A.1 and every histogram (hN, hNE, moments
+ * and the MBAR reweighting are over N_B).  Displacement picks uniformly among
+ * all N particles, removal among the N_B.  The exchange of Eq. Pacc is
+ * unchanged (both walkers hold the cluster, so N_a - N_b = N_B,a - N_B,b).
+ * n_cluster = 0 removes the species.  Every walker is emptied: regc_sweep
+ * refuses (REGC_EINVAL) until regc_set_walkers supplies walkers with
+ * n[w] >= n_cluster whose first n_cluster particles are the cluster atoms.
+ * Speculative warps are not used with a cluster (one warp per walker).
+ * Errors: REGC_EINVAL (n_cluster outside 0..nmax-1, bad type). */
+REGC_API regc_status regc_set_cluster(regc_handle *h, int n_cluster, int cluster_type);
+
 /* Read the walkers: pos [S][nmax][3] (entries beyond N undefined), n [S],
  * energy [S] (the running total E(R; N), all mobile-mobile and mobile-surface
  * pairs), state_of_walker [S].  Any may be NULL.  Synchronous. */

@@ -67,6 +67,7 @@ SIGNATURES = {
     "regc_reset_histograms": ([_h], C.c_int),
     "regc_free": ([_h], None),
     "regc_set_walkers": ([_h, _fp, _ip, _ip], C.c_int),
+    "regc_set_cluster": ([_h, C.c_int, C.c_int], C.c_int),
     "regc_get_walkers": ([_h, _fp, _ip, _dp, _ip], C.c_int),
     "regc_check_energy": ([_h, _dp], C.c_int),
     "regc_counters": ([_h, _lp, _lp, _lp], C.c_int),

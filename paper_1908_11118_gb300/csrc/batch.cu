@@ -178,7 +178,7 @@ regc_status check_members(regc_batch* b) {
     for (size_t m = 0; m < b->members.size(); ++m) {
         regc_handle* h = b->members[m];
         if (h->sticky != REGC_OK) return h->sticky;
-        if (h->P.delayed) return REGC_EINVAL;
+        if (h->P.delayed || h->need_walkers) return REGC_EINVAL;
         if (h->t != b->t_mirror[m] || h->e != b->e_mirror[m]) stale = true;
     }
     if (stale) return fail(b, upload_descriptors(b));
@@ -214,7 +214,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     *out = nullptr;
     if (!handles || count < 1 || sweeps_per_step < 1) return REGC_EINVAL;
     for (int i = 0; i < count; ++i) {
-        if (!handles[i] || handles[i]->P.delayed) return REGC_EINVAL;
+        if (!handles[i] || handles[i]->P.delayed || handles[i]->need_walkers) return REGC_EINVAL;
         if (handles[i]->sticky != REGC_OK) return handles[i]->sticky;
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return REGC_EINVAL;

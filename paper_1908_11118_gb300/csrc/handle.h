@@ -38,6 +38,11 @@ struct regc_handle {
     float* d_y = nullptr;                     // [cap]
     int ds_cap = 0, ds_count = 0, ds_next = 0;
     uint32_t harvest_round = 0;
+    // the potential as given (for the cluster species' pair tables)
+    int n_types = 0;
+    float eps[4][4] = {}, sigma[4][4] = {};
+    double hard_core_T = 0.0;
+    bool need_walkers = false;                // set_cluster emptied the walkers
 };
 
 // Synchronise the handle's stream and fold its device error word into the

@@ -316,6 +316,13 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         P.gs[t] = PairTab{4.0f * pot->eps[0][tt], pot->sigma[0][tt] * pot->sigma[0][tt],
                           hard_core_r2(pot->eps[0][tt], pot->sigma[0][tt], T), pot->eps[0][tt]};
     }
+    P.n_cluster = 0;
+    P.gA = P.gAB = P.gg;
+    for (int t = 0; t < 4; ++t) P.gsA[t] = P.gs[t];
+    h->n_types = nt;
+    memcpy(h->eps, pot->eps, sizeof(h->eps));
+    memcpy(h->sigma, pot->sigma, sizeof(h->sigma));
+    h->hard_core_T = T;
     P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 0.0f, 0.5f * surf->Lx, 0.5f * surf->Ly,
                    periodic_z ? 0.5f * surf->Lz : 0.0f, periodic_z, surf->z_lo, surf->z_hi,
                    surf->z_hi - surf->z_lo, (float)(rc * rc), (float)rc};
@@ -428,6 +435,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
 regc_status regc_sweep(regc_handle* h, int n_sweeps) {
     if (!h || n_sweeps < 0) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
+    if (h->need_walkers) return REGC_EINVAL;
     if (n_sweeps == 0) return REGC_OK;
     SweepParams P = h->P;
     P.t0 = h->t;
@@ -441,6 +449,7 @@ regc_status regc_sweep(regc_handle* h, int n_sweeps) {
 regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* trace) {
     if (!h || n_sweeps < 0 || (n_sweeps > 0 && !trace)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
+    if (h->need_walkers) return REGC_EINVAL;
     if (n_sweeps == 0) return REGC_OK;
     const size_t n = (size_t)h->S * n_sweeps * h->mps;
     regc_move_record* d_trace = nullptr;
@@ -511,7 +520,7 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
     for (int w = 0; w < S; ++w)
-        if (n[w] < 0 || n[w] > nmax) return REGC_EINVAL;
+        if (n[w] < h->P.n_cluster || n[w] > nmax) return REGC_EINVAL;
     std::vector<int> wos(S, -1);
     if (sow) {
         for (int w = 0; w < S; ++w) {
@@ -540,9 +549,33 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
         cudaMemsetAsync(h->P.efix, 0, S * sizeof(long long), h->stream);
         cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
         cudaStreamSynchronize(h->stream);
+        h->need_walkers = h->P.n_cluster > 0;
         return REGC_EINVAL;
     }
+    h->need_walkers = false;
     return REGC_OK;
+}
+
+regc_status regc_set_cluster(regc_handle* h, int n_cluster, int cluster_type) {
+    if (!h || n_cluster < 0 || n_cluster >= h->nmax) return REGC_EINVAL;
+    if (n_cluster > 0 && (cluster_type < 1 || cluster_type >= h->n_types)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    SweepParams& P = h->P;
+    const int ct = n_cluster > 0 ? cluster_type : 0;
+    auto tab = [&](int a, int b) {
+        return PairTab{4.0f * h->eps[a][b], h->sigma[a][b] * h->sigma[a][b],
+                       hard_core_r2(h->eps[a][b], h->sigma[a][b], h->hard_core_T), h->eps[a][b]};
+    };
+    P.n_cluster = n_cluster;
+    P.gA = tab(ct, ct);
+    P.gAB = tab(0, ct);
+    for (int t = 0; t < 4; ++t) P.gsA[t] = tab(ct, t < h->n_types ? t : 0);
+    // every walker must now hold the cluster: empty them until regc_set_walkers
+    cudaError_t e = cudaMemsetAsync(P.n, 0, h->S * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.efix, 0, h->S * sizeof(long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->need_walkers = n_cluster > 0;
+    return cuda_fail(h, e);
 }
 
 regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* energy, int32_t* sow) {

@@ -116,8 +116,11 @@ struct SweepParams {
     Geometry g;
     CellGrid cg;
     SurfaceTab st;
-    PairTab gg;            // mobile-mobile
+    PairTab gg;            // mobile-mobile (grand-canonical species)
     PairTab gs[4];         // mobile-surface by surface type
+    int n_cluster;         // particles 0..n_cluster-1 are the cluster species (0: none)
+    PairTab gA, gAB;       // cluster-cluster, cluster-grand-canonical
+    PairTab gsA[4];        // cluster-surface by surface type
     float max_disp;
     unsigned long long th_disp;   // displacement if A0 < th_disp (0 .. 2^32)
     int S, nmax, mps;

@@ -53,17 +53,19 @@ __device__ __forceinline__ float r2_exact(const Geometry& g, float qx, float qy,
 }
 
 // Features (per lane, before the warp sum) and exact binary32 interaction
-// energy (warp sum) of a position against every partner of walker w.
+// energy (warp sum) of a grand-canonical particle at q against every partner
+// of walker w (cluster partners with the cluster pair table).
 __device__ float features_all(const SweepParams& P, int w, int N, float qx, float qy, float qz, int skip,
                               float (&F)[kNF], int lane) {
     const float4* pos = P.pos + size_t(w) * P.nmax;
     float e = 0.f;
     for (int j = lane; j < N; j += 32) {
         if (j == skip) continue;
+        const PairTab& t = j < P.n_cluster ? P.gAB : P.gg;
         const float r2 = r2_exact(P.g, qx, qy, qz, pos[j]);
         if (r2 < P.g.rc2) {
-            add_features(F, r2, P.gg.eps, P.g.rc);
-            e += phi_of_r2(r2, P.gg);
+            add_features(F, r2, t.eps, P.g.rc);
+            e += phi_of_r2(r2, t);
         }
     }
     for (int a = lane; a < P.st.n_all; a += 32) {
@@ -113,8 +115,9 @@ __global__ void __launch_bounds__(128) harvest_kernel(const __grid_constant__ Sw
     const int N = P.n[w];
     float qx, qy, qz;
     int skip = -1;
-    if (slot < parts && N > 0) {
-        skip = (int)(((long long)slot * N) / parts);
+    const int nB = N - P.n_cluster;   // rows are grand-canonical particles
+    if (slot < parts && nB > 0) {
+        skip = P.n_cluster + (int)(((long long)slot * nB) / parts);
         const float4 p = P.pos[size_t(w) * P.nmax + skip];
         qx = p.x; qy = p.y; qz = p.z;
     } else {

@@ -65,6 +65,13 @@ struct MoveRes {
     int pad;
 };
 
+// Pair tables of the moving particle's species against a cluster partner (tA)
+// and a grand-canonical partner (tB); mA: the moving particle is a cluster atom.
+struct MoveTabs {
+    PairTab tA, tB;
+    bool mA;
+};
+
 // Constants of the walker's state for the binary32 pre-test of the acceptance.
 struct StateF {
     float beta, c_ins, c_del;
@@ -276,11 +283,11 @@ __device__ __forceinline__ StEntry stencil_entry(const SweepParams& P, Cell3 c, 
 // sgn0, query 1 with -1.  The candidate list is the concatenation of the
 // non-empty stencil entries; lane j of a batch of 32 finds its entry from the
 // OR-reduced mask of entry starts in the batch.
-template <int NQ>
+template <int NQ, bool CL>
 __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
                                             float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
                                             int sgn0, Fix3& acc, int& n_in, int& n_cand, int& overlap, int lane,
-                                            int warp) {
+                                            int warp, const MoveTabs& mt) {
     StEntry* st = S.stencil + warp * 32;
     StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
     const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
@@ -311,13 +318,14 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
                 const float4 p = S.pos[pj];
                 const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
                 n_cand += NQ;
+                const PairTab& tp = CL ? (pj < P.n_cluster ? mt.tA : mt.tB) : P.gg;
                 const float phi0 = pair_phi(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz),
-                                            P.g.rc2, P.gg, n_in, ov);
+                                            P.g.rc2, tp, n_in, ov);
                 fix_add(acc, phi0, sgn0);
                 if (NQ == 2) {
                     int ov1 = 0;
                     const float phi1 = pair_phi(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by),
-                                                __fsub_rn(e.az1, bz), P.g.rc2, P.gg, n_in, ov1);
+                                                __fsub_rn(e.az1, bz), P.g.rc2, tp, n_in, ov1);
                     fix_add(acc, phi1, -1);
                 }
             }
@@ -332,16 +340,16 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
 // images of frozen surface atoms listed for that column.  Each listed image
 // holds its coordinate already shifted by minus the period where that is
 // exact; flag bits ask for the query to be shifted by minus the period instead.
-template <int NQ>
+template <int NQ, bool CL>
 __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, float q0x, float q0y, float q0z,
                                              float q1x, float q1y, float q1z, int sgn0, Fix3& acc, int& n_in,
-                                             int& n_cand, int& overlap, int lane) {
+                                             int& n_cand, int& overlap, int lane, bool mA) {
     const int beg = col * P.st.stride, end = beg + P.st.stride;
     int ov = 0;
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
         const unsigned bits = __float_as_uint(a.w);
-        const PairTab& t = surf_tab(P, (int)(bits & 3u));
+        const PairTab& t = (CL && mA) ? P.gsA[bits & 3u] : surf_tab(P, (int)(bits & 3u));
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
         n_cand += NQ;
@@ -360,10 +368,11 @@ __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, floa
 
 // Surrogate features of NQ queries (sharing the stencil of cell c) from the
 // mobile particles of the stencil except `skip`, accumulated per lane.
-template <int NQ>
+template <int NQ, bool CL>
 __device__ __forceinline__ void feature_mobile(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
                                                float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
-                                               float (&F0)[kNF], float (&F1)[kNF], int lane, int warp) {
+                                               float (&F0)[kNF], float (&F1)[kNF], int lane, int warp,
+                                               const MoveTabs& mt) {
     StEntry* st = S.stencil + warp * 32;
     StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
     const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
@@ -394,10 +403,11 @@ __device__ __forceinline__ void feature_mobile(const SweepParams& P, const Walke
                 const float4 p = S.pos[pj];
                 const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
                 const float r20 = r2_of(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz));
-                if (r20 < P.g.rc2) add_features(F0, r20, P.gg.eps, P.g.rc);
+                const float wp = CL ? (pj < P.n_cluster ? mt.tA.eps : mt.tB.eps) : P.gg.eps;
+                if (r20 < P.g.rc2) add_features(F0, r20, wp, P.g.rc);
                 if (NQ == 2) {
                     const float r21 = r2_of(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by), __fsub_rn(e.az1, bz));
-                    if (r21 < P.g.rc2) add_features(F1, r21, P.gg.eps, P.g.rc);
+                    if (r21 < P.g.rc2) add_features(F1, r21, wp, P.g.rc);
                 }
             }
         }
@@ -408,15 +418,15 @@ __device__ __forceinline__ void feature_mobile(const SweepParams& P, const Walke
 
 // Surrogate features of NQ queries (sharing one surface column) from the
 // images of frozen surface atoms listed for that column.
-template <int NQ>
+template <int NQ, bool CL>
 __device__ __forceinline__ void feature_surface(const SweepParams& P, int col, float q0x, float q0y, float q0z,
                                                 float q1x, float q1y, float q1z, float (&F0)[kNF],
-                                                float (&F1)[kNF], int lane) {
+                                                float (&F1)[kNF], int lane, bool mA) {
     const int beg = col * P.st.stride, end = beg + P.st.stride;
     for (int j = beg + lane; j < end; j += 32) {
         const float4 a = __ldg(&P.st.atoms[j]);
         const unsigned bits = __float_as_uint(a.w);
-        const PairTab& t = surf_tab(P, (int)(bits & 3u));
+        const PairTab& t = (CL && mA) ? P.gsA[bits & 3u] : surf_tab(P, (int)(bits & 3u));
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
         const float r20 = r2_of(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
@@ -437,7 +447,7 @@ __device__ __forceinline__ int surface_col(const SweepParams& P, float x, float 
 }
 
 __device__ __forceinline__ bool near_surface(const SweepParams& P, float z) {
-    return P.g.periodic_z || z < P.st.z_reach;
+    return P.st.n_all > 0 && (P.g.periodic_z || z < P.st.z_reach);
 }
 
 __device__ __forceinline__ float4 packed(float x, float y, float z, int cell, int slot) {
@@ -496,9 +506,12 @@ __device__ void build_cells(const SweepParams& P, const WalkerSmem& S, int N, in
 // Evaluate trial move m of the launch (sweep m / mps, move m % mps) with one
 // warp against the current configuration with N particles; lane 0 stores the
 // result in *out.
-template <bool DA>
+template <bool DA, bool CL>
 __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int s, int m, int N,
                               int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
+    // with a cluster, particles 0..nA-1 are cluster atoms; insertion and
+    // removal act on the grand-canonical species, whose count is N - nA
+    const int nA = CL ? P.n_cluster : 0;
     const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
     const int type = (unsigned long long)A.x < P.th_disp ? 0 : ((B.z >> 31) == 0u ? 2 : 1);
     int status = 0, idx = -1, overlap = 0;
@@ -542,14 +555,21 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
             q0x = q1x = nx; q0y = q1y = ny; q0z = q1z = nz;
         }
     } else {
-        if (N == 0) {
+        if (N == nA) {
             status = 1;
         } else {
-            idx = (int)(((unsigned long long)B.x * (unsigned)N) >> 32);
+            idx = nA + (int)(((unsigned long long)B.x * (unsigned)(N - nA)) >> 32);
             const float4 old = S.pos[idx];
             q0x = q1x = old.x; q0y = q1y = old.y; q0z = q1z = old.z;
             sgn0 = -1;
         }
+    }
+    // pair tables of the moving species
+    MoveTabs mt;
+    mt.mA = CL && type == 0 && idx >= 0 && idx < nA;
+    if (CL) {
+        mt.tA = mt.mA ? P.gA : P.gAB;
+        mt.tB = mt.mA ? P.gAB : P.gg;
     }
 
     // delayed acceptance, stage 1: the surrogate energy change dE~
@@ -563,18 +583,19 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         const Cell3 c0 = cell3_of(P, q0x, q0y, q0z);
         const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
         if (nq == 2 && c0.x == c1.x && c0.y == c1.y && c0.z == c1.z) {
-            feature_mobile<2>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, F0, F1, lane, warp);
+            feature_mobile<2, CL>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, F0, F1, lane, warp, mt);
         } else {
-            feature_mobile<1>(P, S, c0, q0x, q0y, q0z, q0x, q0y, q0z, skip, F0, F1, lane, warp);
-            if (nq == 2) feature_mobile<1>(P, S, c1, q1x, q1y, q1z, q1x, q1y, q1z, skip, F1, F0, lane, warp);
+            feature_mobile<1, CL>(P, S, c0, q0x, q0y, q0z, q0x, q0y, q0z, skip, F0, F1, lane, warp, mt);
+            if (nq == 2)
+                feature_mobile<1, CL>(P, S, c1, q1x, q1y, q1z, q1x, q1y, q1z, skip, F1, F0, lane, warp, mt);
         }
         const bool s0 = near_surface(P, q0z), s1 = nq == 2 && near_surface(P, q1z);
         const int col0 = surface_col(P, q0x, q0y), col1 = nq == 2 ? surface_col(P, q1x, q1y) : col0;
         if (s0 && s1 && col0 == col1) {
-            feature_surface<2>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, F0, F1, lane);
+            feature_surface<2, CL>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, F0, F1, lane, mt.mA);
         } else {
-            if (s0) feature_surface<1>(P, col0, q0x, q0y, q0z, q0x, q0y, q0z, F0, F1, lane);
-            if (s1) feature_surface<1>(P, col1, q1x, q1y, q1z, q1x, q1y, q1z, F1, F0, lane);
+            if (s0) feature_surface<1, CL>(P, col0, q0x, q0y, q0z, q0x, q0y, q0z, F0, F1, lane, mt.mA);
+            if (s1) feature_surface<1, CL>(P, col1, q1x, q1y, q1z, q1x, q1y, q1z, F1, F0, lane, mt.mA);
         }
         float* scratch = S.scratch + warp * 64;
         const float e0 = mlp_forward(P.net, warp_reduce16(F0, lane), scratch, lane);
@@ -583,16 +604,16 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         dEs = type == 1 ? e0 : (type == 2 ? -e0 : e0 - e1);
         // ln u1 < ln alpha with dE~ in place of dE (u1 from B3)
         float c_f = 0.f;
-        if (type == 1) c_f = sf.c_ins - __logf((float)(N + 1));
-        else if (type == 2) c_f = sf.c_del + __logf((float)N);
+        if (type == 1) c_f = sf.c_ins - __logf((float)(N - nA + 1));
+        else if (type == 2) c_f = sf.c_del + __logf((float)(N - nA));
         const float la1 = c_f - sf.beta * dEs;
         const float lu1 = __logf(((float)B.w + 0.5f) * 2.3283064365386963e-10f);
         if (la1 >= 0.f || lu1 < la1 - 1e-3f) stage1 = 1;
         else if (lu1 > la1 + 1e-3f) stage1 = 0;
         else {
             double c = 0.0;
-            if (type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
-            else if (type == 2) c = P.c_del[s] + P.ln_tab[N];
+            if (type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
+            else if (type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
             stage1 = (log((double)B.w + 0.5) + kLn2m32) < c - P.beta[s] * (double)dEs;
         }
     }
@@ -604,15 +625,16 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
         const bool same = c0.x == c1.x && c0.y == c1.y && c0.z == c1.z;
         if (nq == 2 && same) {
-            mobile_pass<2>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, 1, acc, n_in, n_cand, overlap, lane, warp);
+            mobile_pass<2, CL>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, 1, acc, n_in, n_cand, overlap, lane, warp,
+                               mt);
         } else {
             // one pass per query: query 0 with its sign, then (a displacement
             // across cells) the old position with -1
             for (int pass = 0; pass < nq; ++pass) {
                 const float px = pass ? q1x : q0x, py = pass ? q1y : q0y, pz = pass ? q1z : q0z;
                 int ovp = 0;
-                mobile_pass<1>(P, S, pass ? c1 : c0, px, py, pz, px, py, pz, skip, pass ? -1 : sgn0, acc, n_in,
-                               n_cand, ovp, lane, warp);
+                mobile_pass<1, CL>(P, S, pass ? c1 : c0, px, py, pz, px, py, pz, skip, pass ? -1 : sgn0, acc, n_in,
+                                   n_cand, ovp, lane, warp, mt);
                 if (pass == 0) overlap |= ovp;
             }
         }
@@ -621,14 +643,14 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         const int col0 = surface_col(P, q0x, q0y);
         const int col1 = nq == 2 ? surface_col(P, q1x, q1y) : col0;
         if (s0 && s1 && col0 == col1) {
-            surface_pass<2>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, 1, acc, n_in, n_cand, overlap, lane);
+            surface_pass<2, CL>(P, col0, q0x, q0y, q0z, q1x, q1y, q1z, 1, acc, n_in, n_cand, overlap, lane, mt.mA);
         } else {
             for (int pass = 0; pass < nq; ++pass) {
                 if (!(pass ? s1 : s0)) continue;
                 const float px = pass ? q1x : q0x, py = pass ? q1y : q0y, pz = pass ? q1z : q0z;
                 int ovp = 0;
-                surface_pass<1>(P, pass ? col1 : col0, px, py, pz, px, py, pz, pass ? -1 : sgn0, acc, n_in, n_cand,
-                                ovp, lane);
+                surface_pass<1, CL>(P, pass ? col1 : col0, px, py, pz, px, py, pz, pass ? -1 : sgn0, acc, n_in, n_cand,
+                                ovp, lane, mt.mA);
                 if (pass == 0) overlap |= ovp;
             }
         }
@@ -654,7 +676,7 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         r.stage1 = stage1;
         r.dE_sur = dEs;
         if (!DA) {
-            r.dec = (status == 0 && !ovl) ? pretest(sf, type, N, big, hi, lo, B.y) : 0;
+            r.dec = (status == 0 && !ovl) ? pretest(sf, type, N - nA, big, hi, lo, B.y) : 0;
         } else if (status != 0 || ovl || !stage1) {
             r.dec = 0;
         } else {
@@ -684,9 +706,10 @@ __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay,
 
 // n_sweeps sweeps of walker w by a group of K warps (tid: thread index in the
 // group, smem: the group's shared-memory region).
-template <int K, bool TRACE, bool DA>
+template <int K, bool TRACE, bool DA, bool CL>
 __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* smem, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
+    const int nA = CL ? P.n_cluster : 0;   // cluster atoms: counted out of the grand-canonical N
     const WalkerSmem S = carve<K>(smem, P);
 
     int N = P.n[w];
@@ -744,7 +767,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         }
         // 3b. evaluate moves m0 .. m0 + K - 1 in parallel, one warp each
         const int mj = m0 + warp;
-        if (mj < total_moves) evaluate_move<DA>(P, S, sf, s, mj, N, n_in, n_cand, lane, warp, S.res + warp);
+        if (mj < total_moves) evaluate_move<DA, CL>(P, S, sf, s, mj, N, n_in, n_cand, lane, warp, S.res + warp);
         group_sync<K>();
 
         // 4. commit in order (thread 0)
@@ -802,17 +825,17 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     S.stats->passed += r.stage1;
                     if (TRACE) {
                         double c = 0.0;
-                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
-                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N];
+                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
+                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
                         la = r.stage1 ? c - P.beta[s] * ((double)dfix * kFixUnit) : (double)NAN;
                     }
                 } else if (status == 0 && !ovl) {
-                    const int dec = N == r.n_eval ? r.dec : pretest(sf, r.type, N, r.big, r.hi, r.lo, B.y);
+                    const int dec = N == r.n_eval ? r.dec : pretest(sf, r.type, N - nA, r.big, r.hi, r.lo, B.y);
                     accepted = dec == 1;
                     if (dec == 2 || TRACE) {
                         double c = 0.0;
-                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N + 1];
-                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N];
+                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
+                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
                         la = c - P.beta[s] * ((double)dfix * kFixUnit);
                         if (dec == 2) accepted = (log((double)B.y + 0.5) + kLn2m32) < la;
                     }
@@ -880,16 +903,17 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 }
                 // 6. observe once per sweep into the current state's histograms
                 if (k == P.mps - 1) {
-                    atomicAdd(&P.hN[size_t(s) * (P.nmax + 1) + N], 1ull);   // fire-and-forget reduction
+                    const int NB = N - nA;
+                    atomicAdd(&P.hN[size_t(s) * (P.nmax + 1) + NB], 1ull);   // fire-and-forget reduction
                     st.om += 1;
-                    st.mN += N;
-                    st.mN2 += (long long)N * N;
+                    st.mN += NB;
+                    st.mN2 += (long long)NB * NB;
                     st.mE += E;
                     const double e = (double)E * kFixUnit;
                     st.mE2 = fma(e, e, st.mE2);
                     const long long d = E - P.e_lo_fix;
                     const long long kb = d >= 0 ? d / P.e_bin_fix : -1;
-                    if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[size_t(N) * P.n_e_bins + (size_t)kb], 1ull);
+                    if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[size_t(NB) * P.n_e_bins + (size_t)kb], 1ull);
                     else st.eo += 1;
                 }
                 ++committed;
@@ -937,11 +961,11 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
 }
 
 
-template <int K, bool TRACE, bool DA>
+template <int K, bool TRACE, bool DA, bool CL>
 __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
     extern __shared__ __align__(16) char smem[];
     if (blockIdx.x >= (unsigned)P.S) return;
-    walker_sweep<K, TRACE, DA>(P, blockIdx.x, smem, threadIdx.x);
+    walker_sweep<K, TRACE, DA, CL>(P, blockIdx.x, smem, threadIdx.x);
 }
 
 // Displacement q - p with the exact minimum image on periodic axes.
@@ -974,14 +998,17 @@ __global__ void __launch_bounds__(32 * kEnergyWarps) energy_kernel(const __grid_
     for (int i = warp; i < N; i += kEnergyWarps) {
         Fix3 acc{0, 0, 0};
         const float4 pi = pos[i];
+        const bool iA = i < P.n_cluster;
         for (int j = i + 1 + lane; j < N; j += 32) {
+            const bool jA = j < P.n_cluster;
+            const PairTab& t = iA ? (jA ? P.gA : P.gAB) : (jA ? P.gAB : P.gg);
             disp_exact(P.g, pi, pos[j], dx, dy, dz);
-            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, P.gg, n_in, overlap), 1);
+            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, t, n_in, overlap), 1);
         }
         if (near_surface(P, pi.z)) {
             int n_cand = 0;
-            surface_pass<1>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, acc, n_in,
-                            n_cand, overlap, lane);
+            surface_pass<1, true>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, acc, n_in,
+                                  n_cand, overlap, lane, iA);
         }
         // fold into 64 bits per particle, so that the int32 parts cannot overflow
         total += fix_value(acc.big, acc.hi, acc.lo);
@@ -1005,18 +1032,20 @@ __global__ void __launch_bounds__(32 * kEnergyWarps) energy_kernel(const __grid_
     }
 }
 
-template <int K, bool DA>
+template <int K, bool DA, bool CL>
 cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
     const size_t smem = smem_bytes(P.nmax, P.cg.ncell, P.cg.cap, K);
     cudaError_t err;
     if (P.trace) {
-        err = cudaFuncSetAttribute(sweep_kernel<K, true, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, true, DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, true, DA><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, true, DA, CL><<<P.S, 32 * K, smem, s>>>(P);
     } else {
-        err = cudaFuncSetAttribute(sweep_kernel<K, false, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(sweep_kernel<K, false, DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, false, DA><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, false, DA, CL><<<P.S, 32 * K, smem, s>>>(P);
     }
     return cudaGetLastError();
 }
@@ -1046,7 +1075,8 @@ __global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_sweep_kernel(const 
         int* dst = reinterpret_cast<int*>(&Psh[warp]);
         for (int k = lane; k < (int)(sizeof(SweepParams) / sizeof(int)); k += 32) dst[k] = src[k];
         __syncwarp();
-        walker_sweep<1, false, false>(Psh[warp], mw.y, mine, lane);
+        if (Psh[warp].n_cluster > 0) walker_sweep<1, false, false, true>(Psh[warp], mw.y, mine, lane);
+        else walker_sweep<1, false, false, false>(Psh[warp], mw.y, mine, lane);
         __syncwarp();
     }
 }
@@ -1084,11 +1114,13 @@ size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker)
 
 cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
     if (P.n_sweeps <= 0) return cudaSuccess;
-    if (P.delayed) return launch_k<1, true>(P, s);   // delayed acceptance: one warp per walker
+    // delayed acceptance and the cluster species: one warp per walker
+    if (P.n_cluster > 0) return P.delayed ? launch_k<1, true, true>(P, s) : launch_k<1, false, true>(P, s);
+    if (P.delayed) return launch_k<1, true, false>(P, s);
     switch (P.warps_per_walker) {
-        case 1: return launch_k<1, false>(P, s);
-        case 2: return launch_k<2, false>(P, s);
-        case 4: return launch_k<4, false>(P, s);
+        case 1: return launch_k<1, false, false>(P, s);
+        case 2: return launch_k<2, false, false>(P, s);
+        case 4: return launch_k<4, false, false>(P, s);
     }
     return cudaErrorInvalidValue;
 }

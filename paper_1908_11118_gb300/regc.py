@@ -71,6 +71,9 @@ class Regc:
                                _stream_handle(stream), C.byref(h)), "regc_init_grid")
         self._h = h
         self.S = len(self._kT) * len(self._mu)
+        self.n_cluster = int(getattr(problem, "n_cluster", 0))
+        if self.n_cluster > 0:
+            check(L.regc_set_cluster(h, self.n_cluster, int(problem.cluster_type)), "regc_set_cluster")
         self.nmax = int(problem.nmax)
         self.mps = int(problem.moves_per_sweep)
         self.n_e_bins = int(problem.n_e_bins)
