@@ -60,6 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--da", type=int, default=1, help="1: add the plain vs delayed-acceptance comparison")
     ap.add_argument("--batch", type=int, default=1, help="1: add the batched uneven workload")
+    ap.add_argument("--cluster", type=int, default=1, help="1: add the cluster-in-gas workload")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
@@ -247,7 +248,10 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
     from paper_1908_11118_gb300 import Regc
 
     rng = np.random.default_rng(seed)
-    pos0, n0 = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=seed)
+    if p.n_cluster:
+        pos0, n0 = W.cluster_initial(p, rng.integers(0, (p.nmax - p.n_cluster) // 2 + 1, p.S), seed=seed)
+    else:
+        pos0, n0 = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=seed)
     g = Regc(p, stream=stream)
     g.set_walkers(pos0, n0)
     g.surrogate_init(seed=seed, scale=1.0)
@@ -309,6 +313,9 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
 
 # ------------------------------------------------------ batched uneven arm
 
+CLUSTER_WORKLOAD = ("15 sigma periodic cube, A4 cluster (eps_AA 4, sigma_AA 1.1; displacement only) in a B gas "
+                    "(eps_BB 0.5, eps_AB 2, sigma 1; grand-canonical), 64 kT x 64 mu = 4096 replicas, Nmax_B 64; "
+                    "step = 10 sweeps + 1 replica-exchange attempt")
 BATCH_WORKLOAD = ("256 systems x (4 kT x 4 mu) = 4096 replicas; 3-layer fcc(100) slabs of nx x ny atoms, "
                   "nx, ny ~ U{6..16}; gas 8-16 high; Nmax = 2^k, k ~ U{6..11}; N0 ~ U{0..Nmax/2} capped at "
                   "90% of a 1.1-spacing lattice; step = 10 sweeps + 1 exchange attempt per system")
@@ -483,6 +490,11 @@ def run_own(args):
                                      args.da_train_steps, args.da_steps_small),
               delayed_acceptance_arm(p, WORKLOAD, torch, stream, flush, 1_000_000, args.da_train_steps,
                                      args.da_steps_large)]
+    cluster = None
+    if args.cluster and rank == 0:
+        # the cluster-in-gas workload: plain and delayed acceptance, same protocol
+        cluster = delayed_acceptance_arm(W.cluster_in_gas(seed=0), CLUSTER_WORKLOAD, torch, stream, flush,
+                                         1_000_000, args.da_train_steps, args.da_steps_large)
 
     line = None
     if rank == 0:
@@ -520,6 +532,7 @@ def run_own(args):
             "cpu_baseline": cpu,
             "surrogate_da": da,
             "batched_uneven": batched,
+            "cluster_in_gas": cluster,
         }
         print(json.dumps(line), flush=True)
     g.close()
