@@ -40,6 +40,10 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 SWEEPS_PER_STEP = 10
+# DRAM bytes (read + write) of one sweep-kernel launch on the benchmark
+# workload, from the ncu capture of the current kernel
+# (dram__bytes_read.sum 4.3377e6 + dram__bytes_write.sum 512)
+SWEEP_TRAFFIC_BYTES = 4337664 + 512
 FLOPS_PER_PAIR = 20            # dx,dy,dz 3, xy minimum image 4, r^2 5, r^-2 1, s^6 3, 4eps s^6(s^6-1) 4
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 METRIC = "GCMC trial moves/s over all replicas"
@@ -518,7 +522,7 @@ def run_own(args):
             "pair_interactions_per_s": pairs * world / (total_max / 1e3),
             "candidate_pairs_per_s": cand * world / (total_max / 1e3),
             "roofline": {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": SWEEP_TRAFFIC_BYTES,
                          "peak_source": peak_src,
                          "work": "%d flop/pair x pairs within rc (%.3g per launch)" % (FLOPS_PER_PAIR, pairs / K),
                          "launch_ms": mean_sweep_s * 1e3},

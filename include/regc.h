@@ -226,6 +226,23 @@ REGC_API regc_status regc_get_walkers(regc_handle *h, float *pos, int32_t *n, do
  * not finite.  Synchronous. */
 REGC_API regc_status regc_check_energy(regc_handle *h, double *max_drift);
 
+/* Checkpoint of everything a run needs to continue exactly: walker
+ * configurations, N, running energies, state labels, the Philox counters of
+ * the sweeps and exchanges, histograms, moments and counters, and (if loaded)
+ * the surrogate's parameters, optimiser state and the sweep mode.  Not saved:
+ * the problem statement (restore into a handle created with the same one and
+ * the same seed) and the surrogate's training rows.  buf NULL: *length
+ * receives the size and nothing else happens; else buf (host, capacity bytes)
+ * receives the checkpoint.  Synchronous.  Errors: REGC_EINVAL (capacity too
+ * small). */
+REGC_API regc_status regc_checkpoint(regc_handle *h, void *buf, size_t capacity, size_t *length);
+
+/* Continue from a checkpoint: the handle's state becomes the saved one, so
+ * the following sweeps and exchanges are exactly those of the run that was
+ * saved.  Errors: REGC_EINVAL (not a checkpoint, corrupted (checksum), or of
+ * a handle with other sizes, cluster or seed); nothing is changed then. */
+REGC_API regc_status regc_restore(regc_handle *h, const void *buf, size_t length);
+
 /* Counters (host buffers, any may be NULL): moves [S walkers][3 types][trials,
  * accepts]; exchanges [S lower states][4 directions][attempts, accepts];
  * pairs [6]: pairs within rc of the committed moves, candidate pairs whose

@@ -68,6 +68,8 @@ SIGNATURES = {
     "regc_free": ([_h], None),
     "regc_set_walkers": ([_h, _fp, _ip, _ip], C.c_int),
     "regc_set_cluster": ([_h, C.c_int, C.c_int], C.c_int),
+    "regc_checkpoint": ([_h, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "regc_restore": ([_h, C.c_void_p, C.c_size_t], C.c_int),
     "regc_get_walkers": ([_h, _fp, _ip, _dp, _ip], C.c_int),
     "regc_check_energy": ([_h, _dp], C.c_int),
     "regc_counters": ([_h, _lp, _lp, _lp], C.c_int),

@@ -635,6 +635,146 @@ regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, in
     return sync_check(h);
 }
 
+// ------------------------------------------------------------ checkpoint
+
+namespace {
+
+// Byte layout of a checkpoint: this header, then the sections of
+// ckpt_sections() in order, raw.
+struct CkptHeader {
+    char magic[8];             // "REGCCKPT"
+    uint32_t version;          // 1
+    uint32_t flags;            // bit 0: surrogate present, bit 1: delayed-acceptance mode
+    int32_t S, nmax, n_e_bins, n_cluster;
+    uint32_t key0, key1, t, e;
+    int32_t adam_t;
+    uint32_t harvest_round;
+    uint64_t payload_bytes;
+    uint64_t checksum;         // FNV-1a 64 of the payload
+};
+
+struct Section {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<Section> ckpt_sections(regc_handle* h, bool with_sur) {
+    const size_t S = h->S, nb = h->nmax + 1;
+    std::vector<Section> v = {
+        {h->P.pos, S * h->nmax * sizeof(float4)},
+        {h->P.n, S * sizeof(int)},
+        {h->P.efix, S * sizeof(long long)},
+        {h->X.state_of_walker, S * sizeof(int)},
+        {h->X.walker_of_state, S * sizeof(int)},
+        {h->P.hN, S * nb * 8},
+        {h->P.hNE, nb * (size_t)h->n_e_bins * 8},
+        {h->P.omega, S * 8},
+        {h->P.moments, S * 4 * 8},
+        {h->P.e_out, S * 8},
+        {h->P.move_counts, S * 6 * 8},
+        {h->X.ex_counts, S * 8 * 8},
+        {h->P.pair_counts, 6 * 8},
+    };
+    if (with_sur) {
+        v.push_back({h->d_theta, REGC_SURROGATE_PARAMS * sizeof(float)});
+        v.push_back({h->d_adam_m, REGC_SURROGATE_PARAMS * sizeof(float)});
+        v.push_back({h->d_adam_v, REGC_SURROGATE_PARAMS * sizeof(float)});
+    }
+    return v;
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t x = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        x ^= p[i];
+        x *= 1099511628211ull;
+    }
+    return x;
+}
+
+regc_status surrogate_alloc(regc_handle* h);
+regc_status surrogate_loaded(regc_handle* h);
+
+}  // namespace
+
+regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* length) {
+    if (!h || !length) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const auto secs = ckpt_sections(h, h->has_sur);
+    size_t payload = 0;
+    for (const auto& x : secs) payload += x.bytes;
+    *length = sizeof(CkptHeader) + payload;
+    if (!buf) return REGC_OK;
+    if (capacity < *length) return REGC_EINVAL;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    unsigned char* q = out + sizeof(CkptHeader);
+    cudaError_t e = cudaSuccess;
+    for (const auto& x : secs) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(q, x.dev, x.bytes, cudaMemcpyDeviceToHost, h->stream);
+        q += x.bytes;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    const regc_status st = sync_check(h);
+    if (st != REGC_OK) return st;
+    CkptHeader hd{};
+    memcpy(hd.magic, "REGCCKPT", 8);
+    hd.version = 1;
+    hd.flags = (h->has_sur ? 1u : 0u) | (h->P.delayed ? 2u : 0u);
+    hd.S = h->S;
+    hd.nmax = h->nmax;
+    hd.n_e_bins = h->n_e_bins;
+    hd.n_cluster = h->P.n_cluster;
+    hd.key0 = h->P.key0;
+    hd.key1 = h->P.key1;
+    hd.t = h->t;
+    hd.e = h->e;
+    hd.adam_t = h->adam_t;
+    hd.harvest_round = h->harvest_round;
+    hd.payload_bytes = payload;
+    hd.checksum = fnv1a(out + sizeof(CkptHeader), payload);
+    memcpy(out, &hd, sizeof hd);
+    return REGC_OK;
+}
+
+regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
+    if (!h || !buf || length < sizeof(CkptHeader)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    CkptHeader hd;
+    memcpy(&hd, buf, sizeof hd);
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 1) return REGC_EINVAL;
+    if (hd.S != h->S || hd.nmax != h->nmax || hd.n_e_bins != h->n_e_bins || hd.n_cluster != h->P.n_cluster ||
+        hd.key0 != h->P.key0 || hd.key1 != h->P.key1)
+        return REGC_EINVAL;
+    const bool with_sur = (hd.flags & 1u) != 0;
+    if (with_sur) {
+        const regc_status st = surrogate_alloc(h);
+        if (st != REGC_OK) return st;
+    }
+    const auto secs = ckpt_sections(h, with_sur);
+    size_t payload = 0;
+    for (const auto& x : secs) payload += x.bytes;
+    if (hd.payload_bytes != payload || length != sizeof(CkptHeader) + payload) return REGC_EINVAL;
+    if (fnv1a(in + sizeof(CkptHeader), payload) != hd.checksum) return REGC_EINVAL;
+    const unsigned char* q = in + sizeof(CkptHeader);
+    cudaError_t e = cudaSuccess;
+    for (const auto& x : secs) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(x.dev, q, x.bytes, cudaMemcpyHostToDevice, h->stream);
+        q += x.bytes;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && with_sur) e = surrogate_pack(h->d_theta, h->sur, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->t = hd.t;
+    h->e = hd.e;
+    h->adam_t = hd.adam_t;
+    h->harvest_round = hd.harvest_round;
+    h->P.delayed = (with_sur && (hd.flags & 2u)) ? 1 : 0;
+    h->need_walkers = false;
+    return REGC_OK;
+}
+
 // ------------------------------------------------------------- surrogate
 
 namespace {

@@ -143,6 +143,18 @@ class Regc:
                                           _p(sow, C.c_int32)), "regc_get_walkers")
         return pos, n, e, sow
 
+    def checkpoint(self) -> bytes:
+        """The handle's full run state (see regc_checkpoint) as bytes."""
+        n = C.c_size_t(0)
+        check(_lib.lib().regc_checkpoint(self._h, None, 0, C.byref(n)), "regc_checkpoint")
+        buf = C.create_string_buffer(n.value)
+        check(_lib.lib().regc_checkpoint(self._h, buf, n.value, C.byref(n)), "regc_checkpoint")
+        return buf.raw[:n.value]
+
+    def restore(self, data: bytes):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        check(_lib.lib().regc_restore(self._h, buf, len(data)), "regc_restore")
+
     def check_energy(self) -> float:
         d = C.c_double(0)
         check(_lib.lib().regc_check_energy(self._h, C.byref(d)), "regc_check_energy")

@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_job_throughput_two_ranks():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     for r in range(2):
