@@ -67,6 +67,23 @@ struct MoveRes {
 
 // Pair tables of the moving particle's species against a cluster partner (tA)
 // and a grand-canonical partner (tB); mA: the moving particle is a cluster atom.
+// Binary32 pair energy without branches: 0 unless `use` and r < rc.  An
+// in-range term is computed with the same operations as pair_phi, hence is
+// bit-identical to it; the branch-free form lets the candidate loop be one
+// basic block, so independent loads and arithmetic overlap.
+__device__ __forceinline__ float pair_phi_sel(float dx, float dy, float dz, float rc2, const PairTab& t, bool use,
+                                              int& n_in, int& overlap) {
+    const float r2 = r2_of(dx, dy, dz);
+    const bool in = use && r2 < rc2;
+    const float rr = in ? r2 : 1.0f;
+    const float s2 = __fdividef(t.sig2, rr);
+    const float s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
+    const float phi = __fmul_rn(t.eps4, __fmaf_rn(s6, s6, -s6));
+    n_in += in;
+    overlap |= in && (r2 < t.rhc2);
+    return in ? phi : 0.0f;
+}
+
 struct MoveTabs {
     PairTab tA, tB;
     bool mA;
@@ -310,25 +327,26 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
         const unsigned bit = (cnt > 0 && excl >= base && excl < base + 32) ? (1u << (excl - base)) : 0u;
         const unsigned starts = __reduce_or_sync(FULL, bit);
         const int j = base + lane;
-        if (j < total) {
-            const int r = started + __popc(starts & lanemask_le(lane)) - 1;
-            const StEntry& e = st[r];
-            const int pj = S.slots[e.cell * P.cg.cap + (j - e.excl)];
-            if (pj != skip) {
-                const float4 p = S.pos[pj];
-                const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
-                n_cand += NQ;
-                const PairTab& tp = CL ? (pj < P.n_cluster ? mt.tA : mt.tB) : P.gg;
-                const float phi0 = pair_phi(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz),
-                                            P.g.rc2, tp, n_in, ov);
-                fix_add(acc, phi0, sgn0);
-                if (NQ == 2) {
-                    int ov1 = 0;
-                    const float phi1 = pair_phi(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by),
-                                                __fsub_rn(e.az1, bz), P.g.rc2, tp, n_in, ov1);
-                    fix_add(acc, phi1, -1);
-                }
-            }
+        const bool act = j < total;
+        // every lane finds a valid entry (some entry starts at or below it);
+        // lanes past the end read particle 0 and discard the term
+        const int r = started + __popc(starts & lanemask_le(lane)) - 1;
+        const StEntry& e = st[r];
+        int pj = -1;
+        if (act) pj = S.slots[e.cell * P.cg.cap + (j - e.excl)];
+        const bool use = act && pj != skip;
+        const float4 p = S.pos[use ? pj : 0];
+        const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
+        n_cand += use ? NQ : 0;
+        const PairTab& tp = CL ? (pj < P.n_cluster ? mt.tA : mt.tB) : P.gg;
+        const float phi0 = pair_phi_sel(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz),
+                                        P.g.rc2, tp, use, n_in, ov);
+        fix_add(acc, phi0, sgn0);
+        if (NQ == 2) {
+            int ov1 = 0;
+            const float phi1 = pair_phi_sel(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by), __fsub_rn(e.az1, bz),
+                                            P.g.rc2, tp, use, n_in, ov1);
+            fix_add(acc, phi1, -1);
         }
         started += __popc(starts);
     }
@@ -352,14 +370,14 @@ __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, floa
         const PairTab& t = (CL && mA) ? P.gsA[bits & 3u] : surf_tab(P, (int)(bits & 3u));
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
-        n_cand += NQ;
-        const float phi0 = pair_phi(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
-                                    __fsub_rn(__fsub_rn(q0z, sz), a.z), P.g.rc2, t, n_in, ov);
+        if (!(bits & 32u)) n_cand += NQ;   // padding slots are not candidates
+        const float phi0 = pair_phi_sel(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
+                                    __fsub_rn(__fsub_rn(q0z, sz), a.z), P.g.rc2, t, true, n_in, ov);
         fix_add(acc, phi0, sgn0);
         if (NQ == 2) {
             int ov1 = 0;
-            const float phi1 = pair_phi(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
-                                        __fsub_rn(__fsub_rn(q1z, sz), a.z), P.g.rc2, t, n_in, ov1);
+            const float phi1 = pair_phi_sel(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
+                                        __fsub_rn(__fsub_rn(q1z, sz), a.z), P.g.rc2, t, true, n_in, ov1);
             fix_add(acc, phi1, -1);
         }
     }
