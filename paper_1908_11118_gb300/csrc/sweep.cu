@@ -323,6 +323,7 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
     }
     __syncwarp();
     int ov = 0, started = 0;
+#pragma unroll 2   // two batches' independent chains may overlap
     for (int base = 0; base < total; base += 32) {
         const unsigned bit = (cnt > 0 && excl >= base && excl < base + 32) ? (1u << (excl - base)) : 0u;
         const unsigned starts = __reduce_or_sync(FULL, bit);
