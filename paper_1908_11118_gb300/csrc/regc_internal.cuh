@@ -38,7 +38,9 @@ struct U4 {
 
 __host__ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                               uint32_t k0, uint32_t k1) {
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int r = 0; r < 10; ++r) {
         if (r) {
             k0 += 0x9E3779B9u;
