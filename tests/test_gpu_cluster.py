@@ -110,3 +110,35 @@ def test_batch_with_cluster_members():
         for x, y in zip(a.get_walkers(), b.get_walkers()):
             assert np.array_equal(x, y)
         assert np.array_equal(a.histograms()["hN"], b.histograms()["hN"])
+
+
+def test_lockstep_cluster_on_a_slab():
+    """A cluster species of its own potential type (2) above the fcc(100)
+    slab: cluster-surface pairs use eps/sigma[2][1], cluster-gas [0][2],
+    cluster-cluster [2][2]."""
+    base = W.fcc100_small(L=2, M=2, nmax=40, seed=8)
+    eps, sig = base.eps.copy(), base.sigma.copy()
+    eps[2, 2], sig[2, 2] = 1.5, 1.05
+    eps[0, 2] = eps[2, 0] = 1.2
+    eps[1, 2] = eps[2, 1] = 1.8
+    p = base.replace(n_types=3, eps=eps, sigma=sig, n_cluster=3, cluster_type=2)
+    # cluster atoms close to the surface (within rc of the top layer), then gas
+    rng = np.random.default_rng(4)
+    pos = np.zeros((p.S, p.nmax, 3))
+    n = np.zeros(p.S, np.int32)
+    for w in range(p.S):
+        clus = np.array([[1.0, 1.0, p.z_lo + 1.0], [2.2, 1.0, p.z_lo + 1.1], [1.6, 2.1, p.z_lo + 1.0]])
+        pos[w, :3] = W.f32(clus)
+        k = 0
+        while k < 8 + 2 * w:
+            q = W.f32(rng.uniform([0, 0, p.z_lo + 0.5], [p.Lx, p.Ly, p.z_hi]))
+            d = q - pos[w, :3 + k]
+            d[:, :2] -= np.round(d[:, :2] / [p.Lx, p.Ly]) * [p.Lx, p.Ly]
+            if np.min(np.linalg.norm(d, axis=1)) > 0.95:
+                pos[w, 3 + k] = q
+                k += 1
+        n[w] = 3 + k
+    g, o, compared, diverged, observed = run_lockstep(p, pos, n, blocks=6, sweeps=10, min_moves=p.S * 20 * 6)
+    if not diverged:
+        assert_same_state(g, o, p, observed)
+    assert g.check_energy() == 0.0
