@@ -101,7 +101,20 @@ def test_lockstep_fcc100_16_replicas():
     assert g.check_energy() == 0.0
 
 
+def dense_slab_long_columns():
+    """4-layer fcc(100) slab of spacing 1.0 under a 5.5-high gas region: up to
+    80 surface images per column, so a column spans three 32-slot batches."""
+    xyz, lx, ly, ztop = W.fcc100_slab(6, 6, 4, 1.0)
+    eps, sig = W._pair_tables(1.0, 1.0, 1.5, 0.9)
+    return W.Problem(
+        n_types=2, eps=eps, sigma=sig, rc=2.5, Lx=lx, Ly=ly, Lz=ztop + 6.0, periodic_z=0,
+        z_lo=ztop + 0.5, z_hi=ztop + 6.0, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=np.array([0.9, 1.4]), mu=np.array([-4.0, -2.5]), lambda0=1.0, nmax=48, moves_per_sweep=20,
+        max_disp=0.25, p_disp=1.0 / 3.0, seed=5, e_lo=-700.0, e_bin=0.1, n_e_bins=8000, name="dense_slab")
+
+
 EDGE_CASES = {
+    "dense_slab_long_columns": lambda: (dense_slab_long_columns(), 10),
     "empty_walkers": lambda: (W.fcc100_small(), 0),
     "nmax_1": lambda: (W.fcc100_small(nmax=1), "half"),
     "ragged_nmax_37_full": lambda: (W.fcc100_small(L=1, M=1, nmax=37).replace(mu=np.array([-1.0])), "full"),

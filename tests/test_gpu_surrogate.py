@@ -252,6 +252,7 @@ def test_da_lockstep_fcc100_16_replicas():
 
 
 @pytest.mark.parametrize("case", ["empty_walkers", "ragged_nmax_37_full", "displacement_only", "gc_only",
+                                  "dense_slab_long_columns",
                                   "moves_45_p_disp_08", "periodic_cube_no_surface", "one_cell_per_axis"])
 def test_da_lockstep_edge_cases(case):
     p, n0 = EDGE_CASES[case]()
