@@ -113,6 +113,11 @@ def lib():
         _lib.oracle_surrogate_energy.argtypes = [sp, dp, C.c_int, C.c_double, C.c_double, C.c_double,
                                                  C.c_int, dp]
         _lib.oracle_surrogate_energy.restype = C.c_double
+        _lib.oracle_md.argtypes = [sp, C.c_int, dp, ip, dp, ip, C.c_uint32, C.c_int, C.c_double, C.c_double,
+                                   dp, C.c_int]
+        _lib.oracle_md.restype = C.c_int
+        _lib.oracle_forces.argtypes = [sp, dp, C.c_int, dp]
+        _lib.oracle_forces.restype = None
     return _lib
 
 
@@ -185,6 +190,7 @@ class Oracle:
         self.walker_of_state = np.arange(S, dtype=np.int32)
         self.t = 0
         self.e = 0
+        self.md_seg = 0
         self.reset_histograms()
         self.counts = np.zeros((S, 3, 2), np.int64)
         self.ex_counts = np.zeros((S, 4, 2), np.int64)
@@ -251,6 +257,29 @@ class Oracle:
             raise ValueError("oracle_sweeps rejected its arguments")
         self.t += n_sweeps
         return tr
+
+    def forces(self, w):
+        """MD forces [n, 3] on the particles of walker w."""
+        n = int(self.n[w])
+        pos = np.ascontiguousarray(self.pos[w])
+        f = np.zeros((max(n, 1), 3))
+        lib().oracle_forces(C.byref(self.sys), _ptr(pos, C.c_double), n, _ptr(f, C.c_double))
+        return f[:n]
+
+    def md(self, n_steps: int, dt: float, tau: float):
+        """One MD segment of every walker (see oracle_md); returns the kinetic
+        energies [S] after the last step."""
+        kin = np.zeros(self.p.S)
+        pos = np.ascontiguousarray(self.pos)
+        rc = lib().oracle_md(C.byref(self.sys), self.p.S, _ptr(pos, C.c_double), _ptr(self.n, C.c_int32),
+                             _ptr(self.energy, C.c_double), _ptr(self.state_of_walker, C.c_int32),
+                             C.c_uint32(self.md_seg), int(n_steps), float(dt), float(tau),
+                             _ptr(kin, C.c_double), self.n_threads)
+        if rc < 0:
+            raise ValueError("oracle_md rejected its arguments")
+        self.pos = pos
+        self.md_seg += 1
+        return kin
 
     def exchange(self):
         acc = lib().oracle_exchange(C.byref(self.sys), C.c_uint32(self.e), _ptr(self.n, C.c_int32),

@@ -32,6 +32,8 @@
  *   64  removal: energy taken of particle i but particle (i+1) mod N removed
  *   128 delayed acceptance: stage 2 without the -dE~ correction
  *   256 cluster: insertion/removal ratios with the total N instead of N_B
+ *   512 MD thermostat: the cross term 2 R1 sqrt(...) of the rescaled kinetic energy dropped
+ *   1024 MD: forces with the wrong sign
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -564,4 +566,166 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
         }
     }
     return accepted;
+}
+
+/* ------------------------------------------------------------------ MD */
+
+/* Molecular dynamics between grand-canonical moves (REGCMD, Sec. II.A.3: the
+ * canonical sampling step done by MD; Appendix: velocity Verlet with the
+ * stochastic velocity rescaling thermostat).  Reduced units, unit masses.
+ *
+ * One segment of n_steps steps of length dt for walker w at its state's kT:
+ *   - velocities are drawn from the Maxwell-Boltzmann distribution at kT
+ *     (particle i: Philox counter (i, seg, w, 8), Box-Muller on words 0-1 and
+ *     2-3, components x, y, z from the first three normals);
+ *   - each step: the stochastic velocity rescaling thermostat of Bussi,
+ *     Donadio & Parrinello (J. Chem. Phys. 126, 014101 (2007)) with time
+ *     constant tau over dt on all 3N degrees of freedom (normals from
+ *     counters (k, seg * n_steps + step, w, 9), k = 0, 1, ...: R1 is normal 0,
+ *     the chi-square variable the sum of the squares of normals 1..3N-1), then
+ *     one velocity-Verlet step: v += f dt/2, r += v dt, f = F(r), v += f dt/2;
+ *   - F_i = -grad_i E: truncated LJ forces from every other particle and
+ *     every surface atom within rc, nearest image;
+ *   - x and y wrap periodically (z too in a periodic box); otherwise the walls
+ *     at z_lo and z_hi reflect (z -> 2 z_wall - z, v_z -> -v_z);
+ *   - at the end coordinates are rounded to binary32 and E is recomputed.
+ * kin (if not NULL) receives the kinetic energy after the last step. */
+
+static void normals4(const oracle_system *sys, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double g[4])
+{
+    uint32_t u[4];
+    draw(sys, c0, c1, c2, c3, u);
+    for (int h = 0; h < 2; ++h) {
+        double r = sqrt(-2.0 * log(u32_open(u[2 * h])));
+        double a = 2.0 * M_PI * u32_open(u[2 * h + 1]);
+        g[2 * h] = r * cos(a);
+        g[2 * h + 1] = r * sin(a);
+    }
+}
+
+static void md_forces(const oracle_system *sys, const double *pos, int n, double *f)
+{
+    const double rc2 = sys->rc * sys->rc;
+    for (int i = 0; i < 3 * n; ++i) f[i] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *ri = pos + 3 * i;
+        const int ti = species(sys, i);
+        for (int j = -sys->n_surf; j < n; ++j) {
+            if (j == i) continue;
+            const double *rj;
+            int tj;
+            if (j < 0) {
+                rj = sys->surf_xyz + 3 * (j + sys->n_surf);
+                tj = sys->surf_type[j + sys->n_surf];
+            } else {
+                rj = pos + 3 * j;
+                tj = species(sys, j);
+            }
+            double d[3] = {min_image(ri[0] - rj[0], sys->Lx), min_image(ri[1] - rj[1], sys->Ly),
+                           sys->periodic_z ? min_image(ri[2] - rj[2], sys->Lz) : ri[2] - rj[2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rc2) continue;
+            double s2 = sys->sigma[ti][tj] * sys->sigma[ti][tj] / r2;
+            double s6 = s2 * s2 * s2;
+            /* -dphi/dr / r = 24 eps (2 s^12 - s^6) / r^2 */
+            double g = 24.0 * sys->eps[ti][tj] * (2.0 * s6 * s6 - s6) / r2;
+            if (sys->mutation & 1024) g = -g;
+            for (int c = 0; c < 3; ++c) f[3 * i + c] += g * d[c];
+        }
+    }
+}
+
+static void md_walker(const oracle_system *sys, int w, double *pos, int n, double *e_ptr, int state,
+                      uint32_t seg, int n_steps, double dt, double tau, double *kin)
+{
+    const double kT = kT_of(sys, state);
+    double *v = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double *f = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    const int nf = 3 * n;
+    for (int i = 0; i < n; ++i) {
+        double g[4];
+        normals4(sys, (uint32_t)i, seg, (uint32_t)w, 8u, g);
+        for (int c = 0; c < 3; ++c) v[3 * i + c] = sqrt(kT) * g[c];
+    }
+    md_forces(sys, pos, n, f);
+    const double c_tau = exp(-dt / tau);
+    for (int step = 0; step < n_steps && n > 0; ++step) {
+        /* thermostat: rescale every velocity by alpha (Bussi et al.) */
+        double K = 0.0;
+        for (int i = 0; i < nf; ++i) K += 0.5 * v[i] * v[i];
+        const double Kt = 0.5 * nf * kT;
+        double r1 = 0.0, chi = 0.0;
+        const uint32_t gstep = seg * (uint32_t)n_steps + (uint32_t)step;
+        for (int k = 0; 4 * k < nf; ++k) {
+            double g[4];
+            normals4(sys, (uint32_t)k, gstep, (uint32_t)w, 9u, g);
+            for (int h = 0; h < 4; ++h) {
+                int idx = 4 * k + h;
+                if (idx == 0) r1 = g[h];
+                else if (idx < nf) chi += g[h] * g[h];
+            }
+        }
+        if (K > 0.0) {
+            double cross = (sys->mutation & 512) ? 0.0 : 2.0 * r1 * sqrt(c_tau * (1.0 - c_tau) * K * Kt / nf);
+            double k_new = c_tau * K + (1.0 - c_tau) * Kt * (r1 * r1 + chi) / nf + cross;
+            double alpha = sqrt(k_new / K);
+            if (r1 + sqrt(c_tau * nf * K / ((1.0 - c_tau) * Kt)) < 0.0) alpha = -alpha;
+            for (int i = 0; i < nf; ++i) v[i] *= alpha;
+        }
+        /* velocity Verlet */
+        for (int i = 0; i < nf; ++i) v[i] += 0.5 * dt * f[i];
+        for (int i = 0; i < n; ++i) {
+            double *r = pos + 3 * i;
+            for (int c = 0; c < 3; ++c) r[c] += dt * v[3 * i + c];
+            r[0] -= sys->Lx * floor(r[0] / sys->Lx);
+            r[1] -= sys->Ly * floor(r[1] / sys->Ly);
+            if (sys->periodic_z) {
+                r[2] -= sys->Lz * floor(r[2] / sys->Lz);
+            } else {
+                if (r[2] < sys->z_lo) { r[2] = 2.0 * sys->z_lo - r[2]; v[3 * i + 2] = -v[3 * i + 2]; }
+                if (r[2] > sys->z_hi) { r[2] = 2.0 * sys->z_hi - r[2]; v[3 * i + 2] = -v[3 * i + 2]; }
+            }
+        }
+        md_forces(sys, pos, n, f);
+        for (int i = 0; i < nf; ++i) v[i] += 0.5 * dt * f[i];
+    }
+    if (kin) {
+        double K = 0.0;
+        for (int i = 0; i < nf; ++i) K += 0.5 * v[i] * v[i];
+        *kin = K;
+    }
+    for (int i = 0; i < 3 * n; ++i) pos[i] = f32(pos[i]);
+    for (int i = 0; i < n; ++i) {
+        /* binary32 rounding may put a coordinate on the upper boundary */
+        double *r = pos + 3 * i;
+        if (r[0] >= f32(sys->Lx)) r[0] = 0.0;
+        if (r[1] >= f32(sys->Ly)) r[1] = 0.0;
+        if (sys->periodic_z && r[2] >= f32(sys->Lz)) r[2] = 0.0;
+    }
+    *e_ptr = oracle_total_energy(sys, pos, n);
+    free(v);
+    free(f);
+}
+
+int oracle_md(const oracle_system *sys, int n_walkers, double *pos, const int32_t *n, double *energy,
+              const int32_t *state_of_walker, uint32_t seg, int n_steps, double dt, double tau, double *kin,
+              int n_threads)
+{
+    int S = sys->L * sys->M;
+    if (n_walkers != S || n_steps < 0 || !(dt > 0.0) || !(tau > 0.0)) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int w = 0; w < S; ++w)
+        md_walker(sys, w, pos + (int64_t)w * sys->nmax * 3, n[w], energy + w, state_of_walker[w], seg, n_steps, dt,
+                  tau, kin ? kin + w : NULL);
+    (void)n_threads;
+    return 0;
+}
+
+/* Forces F_i = -grad_i E on the n mobile particles (the MD forces), f [n][3]. */
+void oracle_forces(const oracle_system *sys, const double *pos, int n, double *f)
+{
+    md_forces(sys, pos, n, f);
 }
