@@ -161,6 +161,29 @@ REGC_API regc_status regc_sweep(regc_handle *h, int n_sweeps);
  * for move-by-move comparison with a reference implementation. */
 REGC_API regc_status regc_sweep_traced(regc_handle *h, int n_sweeps, regc_move_record *trace);
 
+/* REGCMD: one molecular-dynamics segment of every walker (Sec. II.A.3: the
+ * canonical sampling between grand-canonical and exchange moves done by MD;
+ * Appendix: velocity Verlet with the stochastic velocity rescaling thermostat
+ * of Bussi, Donadio & Parrinello 2007).  Reduced units, unit masses.  Each
+ * walker, at its state's kT:
+ *   - velocities are drawn from the Maxwell-Boltzmann distribution (particle
+ *     i: Philox counter (i, segment, walker, 8), Box-Muller);
+ *   - n_steps steps: the thermostat (time constant tau, all 3N degrees of
+ *     freedom, normals from counters (k, segment * n_steps + step, walker, 9)),
+ *     then v += f dt/2, r += v dt, f = F(r), v += f dt/2, with F the truncated
+ *     LJ forces of the other particles and the surface (binary32);
+ *   - x and y are periodic (z too in a periodic box); otherwise the walls at
+ *     z_lo and z_hi reflect;
+ *   - the exact energies are recomputed at the end.
+ * Use it in place of displacement moves (p_disp = 0) alternated with
+ * regc_sweep; velocities do not persist between segments.  kinetic [S] (host,
+ * may be NULL) receives each walker's kinetic energy after the last step
+ * (synchronous then; asynchronous otherwise).  Errors: REGC_EINVAL (n_steps < 0,
+ * dt or tau not positive, walkers missing after regc_set_cluster),
+ * REGC_ENUMERIC (a pair came inside the hard-core guard: the time step is far
+ * too long), REGC_ECAPACITY (a cell overflowed). */
+REGC_API regc_status regc_md(regc_handle *h, int n_steps, float dt, float tau, float *kinetic);
+
 /* One collective replica-exchange attempt (Sec. II.A.2, Eq. Pacc): a direction
  * (T, mu, diagonal, anti-diagonal) and a parity are drawn; every state of that
  * parity swaps with its neighbour in that direction with probability
@@ -228,7 +251,7 @@ REGC_API regc_status regc_check_energy(regc_handle *h, double *max_drift);
 
 /* Checkpoint of everything a run needs to continue exactly: walker
  * configurations, N, running energies, state labels, the Philox counters of
- * the sweeps and exchanges, histograms, moments and counters, and (if loaded)
+ * the sweeps, exchanges and MD segments, histograms, moments and counters, and (if loaded)
  * the surrogate's parameters, optimiser state and the sweep mode.  Not saved:
  * the problem statement (restore into a handle created with the same one and
  * the same seed) and the surrogate's training rows.  buf NULL: *length

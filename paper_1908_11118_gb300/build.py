@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libregc.so")
-SOURCES = ["sweep.cu", "exchange.cu", "mbar.cu", "regc_api.cu", "mbar_static.cu", "surrogate.cu", "probe.cu", "walkers.cu", "batch.cu"]
-HEADERS = ["regc_internal.cuh", "launch.h", "mbar.h", "surrogate.cuh", "handle.h"]
+SOURCES = ["sweep.cu", "exchange.cu", "mbar.cu", "regc_api.cu", "mbar_static.cu", "surrogate.cu", "probe.cu", "walkers.cu", "batch.cu", "md.cu"]
+HEADERS = ["regc_internal.cuh", "launch.h", "mbar.h", "surrogate.cuh", "handle.h", "cells.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--ptxas-options=-v" if os.environ.get("REGC_PTXAS_VERBOSE") else "-w"]

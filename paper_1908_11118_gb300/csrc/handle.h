@@ -43,6 +43,7 @@ struct regc_handle {
     float eps[4][4] = {}, sigma[4][4] = {};
     double hard_core_T = 0.0;
     bool need_walkers = false;                // set_cluster emptied the walkers
+    uint32_t md_seg = 0;                      // MD segments run (Philox counter of the MD streams)
 };
 
 // Synchronise the handle's stream and fold its device error word into the

@@ -14,8 +14,9 @@ size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker)
 // P.trace may be null.
 cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s);
 
-// From-scratch fixed-point energy of every walker into out[S]; overlap flags
-// go to P.error (ERR_OVERLAP) when check_overlap is set.
+// From-scratch fixed-point energy of every walker into out[S]; a pair inside
+// the hard-core guard sets ERR_OVERLAP (check_overlap 1) or ERR_NUMERIC
+// (check_overlap 2) in P.error.
 cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overlap,
                           cudaStream_t s);
 
@@ -50,6 +51,15 @@ int batch_occupancy(int warps_per_cta, int region);
 // e_ctr[m] += 1 and sys[m].t0 += n_sweeps on the device.
 cudaError_t launch_batch_exchange(const ExchangeParams* xs, uint32_t* e_ctr, SweepParams* sys, int n_systems,
                                   int n_sweeps, cudaStream_t s);
+
+// One MD segment of every walker (md.cu): n_steps velocity-Verlet steps of
+// length dt with the stochastic velocity rescaling thermostat (time constant
+// tau) from Maxwell-Boltzmann velocities (segment number seg); kinetic
+// energies after the last step into kin_out[S] if not null.  Positions are
+// written back; energies are not recomputed.
+cudaError_t launch_md(const SweepParams& P, int n_steps, float dt, float tau, uint32_t seg, float* kin_out,
+                      cudaStream_t s);
+size_t md_smem(int nmax, int ncell, int cap);
 
 // One collective exchange attempt number e.
 cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s);

@@ -470,6 +470,27 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
     return st != REGC_OK ? st : st2;
 }
 
+regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kinetic) {
+    if (!h || n_steps < 0 || !(dt > 0.0f) || !(tau > 0.0f) || !std::isfinite(dt) || !std::isfinite(tau))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (h->need_walkers) return REGC_EINVAL;
+    if (md_smem(h->nmax, h->P.cg.ncell, h->P.cg.cap) > kMaxSmem) return REGC_EINVAL;
+    float* d_kin = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_kin, h->S * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = launch_md(h->P, n_steps, dt, tau, h->md_seg, d_kin, h->stream);
+    // every particle moved: the exact energies from scratch (a pair inside the
+    // hard-core guard -- a time step far too long -- is a numeric error)
+    if (e == cudaSuccess) e = launch_energy(h->P, h->P.efix, 2, h->stream);
+    if (e == cudaSuccess && kinetic)
+        e = cudaMemcpyAsync(kinetic, d_kin, h->S * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (d_kin) cudaFreeAsync(d_kin, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->md_seg += 1;
+    if (kinetic) return sync_check(h);
+    return REGC_OK;
+}
+
 regc_status regc_exchange(regc_handle* h) {
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
@@ -643,12 +664,14 @@ namespace {
 // ckpt_sections() in order, raw.
 struct CkptHeader {
     char magic[8];             // "REGCCKPT"
-    uint32_t version;          // 1
+    uint32_t version;          // 2
     uint32_t flags;            // bit 0: surrogate present, bit 1: delayed-acceptance mode
     int32_t S, nmax, n_e_bins, n_cluster;
     uint32_t key0, key1, t, e;
     int32_t adam_t;
     uint32_t harvest_round;
+    uint32_t md_seg;
+    uint32_t reserved;
     uint64_t payload_bytes;
     uint64_t checksum;         // FNV-1a 64 of the payload
 };
@@ -718,7 +741,7 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
     if (st != REGC_OK) return st;
     CkptHeader hd{};
     memcpy(hd.magic, "REGCCKPT", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.flags = (h->has_sur ? 1u : 0u) | (h->P.delayed ? 2u : 0u);
     hd.S = h->S;
     hd.nmax = h->nmax;
@@ -730,6 +753,7 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
     hd.e = h->e;
     hd.adam_t = h->adam_t;
     hd.harvest_round = h->harvest_round;
+    hd.md_seg = h->md_seg;
     hd.payload_bytes = payload;
     hd.checksum = fnv1a(out + sizeof(CkptHeader), payload);
     memcpy(out, &hd, sizeof hd);
@@ -742,7 +766,7 @@ regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
     CkptHeader hd;
     memcpy(&hd, buf, sizeof hd);
     const unsigned char* in = static_cast<const unsigned char*>(buf);
-    if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 1) return REGC_EINVAL;
+    if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 2) return REGC_EINVAL;
     if (hd.S != h->S || hd.nmax != h->nmax || hd.n_e_bins != h->n_e_bins || hd.n_cluster != h->P.n_cluster ||
         hd.key0 != h->P.key0 || hd.key1 != h->P.key1)
         return REGC_EINVAL;
@@ -770,6 +794,7 @@ regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
     h->e = hd.e;
     h->adam_t = hd.adam_t;
     h->harvest_round = hd.harvest_round;
+    h->md_seg = hd.md_seg;
     h->P.delayed = (with_sur && (hd.flags & 2u)) ? 1 : 0;
     h->need_walkers = false;
     return REGC_OK;

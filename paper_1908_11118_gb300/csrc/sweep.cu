@@ -26,6 +26,7 @@
 //      FP64 otherwise, which gives the FP64 decision in every case;
 //   5. after each sweep the walker is observed into its state's histograms;
 //   6. positions, N and the running energy go back to HBM.
+#include "cells.cuh"
 #include "launch.h"
 #include "surrogate.cuh"
 
@@ -179,8 +180,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ unsigned lanemask_le(int lane) { return FULL >> (31 - lane); }
-__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
 // ---------------------------------------------------- bulk copy + mbarrier
 
@@ -229,29 +228,6 @@ template <int K>
 __device__ __forceinline__ void group_sync() {
     if (K == 1) __syncwarp();
     else __syncthreads();
-}
-
-// --------------------------------------------------------------- cells
-
-struct Cell3 {
-    int x, y, z;
-};
-
-__device__ __forceinline__ Cell3 cell3_of(const SweepParams& P, float x, float y, float z) {
-    Cell3 c;
-    c.x = min(P.cg.ncx - 1, (int)(x * P.cg.icx));
-    c.y = min(P.cg.ncy - 1, (int)(y * P.cg.icy));
-    const float zz = P.g.periodic_z ? z : (z - P.g.z_lo);
-    c.z = min(P.cg.ncz - 1, max(0, (int)(zz * P.cg.icz)));
-    return c;
-}
-
-__device__ __forceinline__ int cell_index(const SweepParams& P, Cell3 c) {
-    return (c.z * P.cg.ncy + c.y) * P.cg.ncx + c.x;
-}
-
-__device__ __forceinline__ int cell_of(const SweepParams& P, float x, float y, float z) {
-    return cell_index(P, cell3_of(P, x, y, z));
 }
 
 // Stencil entry handled by this lane (cell = -1 if none), for queries q0, q1
@@ -459,22 +435,6 @@ __device__ __forceinline__ void feature_surface(const SweepParams& P, int col, f
     }
 }
 
-__device__ __forceinline__ int surface_col(const SweepParams& P, float x, float y) {
-    const int sx = min(P.st.nsx - 1, (int)(x * P.st.isx));
-    const int sy = min(P.st.nsy - 1, (int)(y * P.st.isy));
-    return sy * P.st.nsx + sx;
-}
-
-__device__ __forceinline__ bool near_surface(const SweepParams& P, float z) {
-    return P.st.n_all > 0 && (P.g.periodic_z || z < P.st.z_reach);
-}
-
-__device__ __forceinline__ float4 packed(float x, float y, float z, int cell, int slot) {
-    return make_float4(x, y, z, __uint_as_float(((unsigned)cell << 16) | (unsigned)slot));
-}
-__device__ __forceinline__ int cell_bits(float w) { return (int)(__float_as_uint(w) >> 16); }
-__device__ __forceinline__ int slot_bits(float w) { return (int)(__float_as_uint(w) & 0xffffu); }
-
 // Remove a particle (whose packed w gives its cell and slot) from its cell.
 __device__ __forceinline__ void cell_remove(const SweepParams& P, const WalkerSmem& S, float wbits) {
     const int c = cell_bits(wbits), s = slot_bits(wbits);
@@ -490,36 +450,9 @@ __device__ __forceinline__ void cell_remove(const SweepParams& P, const WalkerSm
     S.cnt[c] = (uint16_t)last;
 }
 
-// Deterministic cell build by warp 0: particles in index order, ties inside a
-// batch of 32 resolved by lane order.
-__device__ void build_cells(const SweepParams& P, const WalkerSmem& S, int N, int lane) {
-    for (int c = lane; c < P.cg.ncell; c += 32) S.cnt[c] = 0;
-    __syncwarp();
-    for (int base = 0; base < N; base += 32) {
-        const int j = base + lane;
-        const bool act = j < N;
-        int c = -1;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act) {
-            p = S.pos[j];
-            c = cell_of(P, p.x, p.y, p.z);
-        }
-        const unsigned grp = __match_any_sync(FULL, c);
-        int before = 0;
-        if (act) {
-            before = S.cnt[c];
-            const int slot = before + __popc(grp & lanemask_lt(lane));
-            if (slot < P.cg.cap) {
-                S.slots[c * P.cg.cap + slot] = (uint16_t)j;
-                S.pos[j] = packed(p.x, p.y, p.z, c, slot);
-            } else {
-                atomicOr(P.error, ERR_CAPACITY);
-            }
-        }
-        __syncwarp();
-        if (act && lane == __ffs(grp) - 1) S.cnt[c] = (uint16_t)min(P.cg.cap, before + __popc(grp));
-        __syncwarp();
-    }
+// Deterministic cell build of the walker's staged positions by warp 0.
+__device__ __forceinline__ void build_cells(const SweepParams& P, const WalkerSmem& S, int N, int lane) {
+    build_cell_list(P, S.pos, N, S.cnt, S.slots, lane);
 }
 
 // Evaluate trial move m of the launch (sweep m / mps, move m % mps) with one
@@ -1047,7 +980,7 @@ __global__ void __launch_bounds__(32 * kEnergyWarps) energy_kernel(const __grid_
             o |= ovl[k];
         }
         out[w] = t;
-        if (o && check_overlap) atomicOr(P.error, ERR_OVERLAP);
+        if (o && check_overlap) atomicOr(P.error, check_overlap == 2 ? ERR_NUMERIC : ERR_OVERLAP);
     }
 }
 

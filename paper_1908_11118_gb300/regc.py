@@ -108,6 +108,13 @@ class Regc:
     def exchange(self):
         check(_lib.lib().regc_exchange(self._h), "regc_exchange")
 
+    def md(self, n_steps: int, dt: float, tau: float, kinetic: bool = True):
+        """One MD segment of every walker (regc_md); returns the kinetic
+        energies [S] after the last step (or None when kinetic is False)."""
+        k = np.zeros(self.S, np.float32) if kinetic else None
+        check(_lib.lib().regc_md(self._h, int(n_steps), float(dt), float(tau), _p(k, C.c_float)), "regc_md")
+        return k
+
     def run(self, n_sweeps: int, exchange_every: int = 10):
         """Blocks of exchange_every sweeps, each followed by one exchange attempt."""
         done = 0
