@@ -65,6 +65,8 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--da", type=int, default=1, help="1: add the plain vs delayed-acceptance comparison")
     ap.add_argument("--batch", type=int, default=1, help="1: add the batched uneven workload")
+    ap.add_argument("--md", type=int, default=1, help="1: add MD segments (REGCMD) of the main workload")
+    ap.add_argument("--md-segments", type=int, default=10)
     ap.add_argument("--cluster", type=int, default=1, help="1: add the cluster-in-gas workload")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--da-train-steps", type=int, default=3000)
@@ -399,6 +401,55 @@ def batched_uneven_arm(torch, steps, seed=0):
     return out
 
 
+# ---------------------------------------------------------------- REGCMD
+
+def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0.1):
+    """MD segments of every walker of the benchmark workload (regc_md) from its
+    current state, device-timed per segment with the L2 flushed before each;
+    and REGCMD cycles (one GC-only sweep of the same handle would need
+    p_disp = 0: here the cycle is a 1-sweep regc_sweep + one MD segment +
+    one exchange, as a user alternating them runs it)."""
+    n_mean = float(np.mean(g.get_walkers()[1]))
+    for _ in range(2):
+        g.md(n_steps, dt, tau, kinetic=False)
+    ev = []
+    for _ in range(segments):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.md(n_steps, dt, tau, kinetic=False)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    seg_ms = sum(a.elapsed_time(b) for a, b in ev) / segments
+    ev = []
+    for _ in range(segments):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.sweep(1)
+        g.md(n_steps, dt, tau, kinetic=False)
+        g.exchange()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    cyc_ms = sum(a.elapsed_time(b) for a, b in ev) / segments
+    drift = g.check_energy()
+    return {
+        "workload": WORKLOAD,
+        "segment": {"steps": n_steps, "dt": dt, "tau": tau},
+        "mean_N": n_mean,
+        "ms_per_segment": seg_ms,
+        "particle_steps_per_s": p.S * n_mean * n_steps / (seg_ms / 1e3),
+        "ms_per_cycle": cyc_ms,
+        "cycle": "1 sweep of 20 trial moves + 1 MD segment + 1 exchange attempt, every replica",
+        "energy_drift": drift,
+        "timed_segments": segments,
+    }
+
+
 # ---------------------------------------------------------------- own arm
 
 def run_own(args):
@@ -485,6 +536,10 @@ def run_own(args):
     h2d = p.S * p.nmax * 12 + p.S * 4 * 2
     d2h = p.S * p.nmax * 12 + p.S * (4 + 8 + 4) + 4
 
+    regcmd = None
+    if args.md and rank == 0:
+        regcmd = regcmd_arm(g, p, torch, stream, flush, args.md_segments)
+
     batched = None
     if args.batch and rank == 0:
         batched = batched_uneven_arm(torch, args.batch_steps)
@@ -537,6 +592,7 @@ def run_own(args):
             "cpu_baseline": cpu,
             "surrogate_da": da,
             "batched_uneven": batched,
+            "regcmd": regcmd,
             "cluster_in_gas": cluster,
         }
         print(json.dumps(line), flush=True)
