@@ -116,6 +116,9 @@ def lib():
         _lib.oracle_md.argtypes = [sp, C.c_int, dp, ip, dp, ip, C.c_uint32, C.c_int, C.c_double, C.c_double,
                                    dp, C.c_int]
         _lib.oracle_md.restype = C.c_int
+        _lib.oracle_cycle.argtypes = [sp, C.c_int, dp, ip, dp, ip, ip, C.c_uint32, C.c_uint32, C.c_int,
+                                      C.c_double, C.c_int, C.c_void_p, C.c_void_p, i64p, i64p]
+        _lib.oracle_cycle.restype = C.c_int
         _lib.oracle_forces.argtypes = [sp, dp, C.c_int, dp]
         _lib.oracle_forces.restype = None
     return _lib
@@ -257,6 +260,32 @@ class Oracle:
             raise ValueError("oracle_sweeps rejected its arguments")
         self.t += n_sweeps
         return tr
+
+    def cycle(self, n_steps: int, x0: float, n_canonical: int, hist: bool = True, trace: bool = False):
+        """n_steps steps of the REGC cycle (see oracle_cycle): with probability
+        x0 one particle-exchange attempt per replica, else one replica-exchange
+        attempt; then n_canonical displacement moves per replica.  Returns
+        (trace [S, n_steps, n_canonical + 1] or None, replica-exchange steps)."""
+        p = self.p
+        S = p.S
+        tr = np.zeros((S, n_steps, n_canonical + 1), MOVE_DTYPE) if trace else None
+        h = None
+        if hist:
+            h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
+                      _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
+                      _ptr(self.e_out, C.c_int64))
+        n_ex = lib().oracle_cycle(C.byref(self.sys), S, _ptr(self.pos, C.c_double), _ptr(self.n, C.c_int32),
+                                  _ptr(self.energy, C.c_double), _ptr(self.state_of_walker, C.c_int32),
+                                  _ptr(self.walker_of_state, C.c_int32), C.c_uint32(self.t), C.c_uint32(self.e),
+                                  int(n_steps), float(x0), int(n_canonical),
+                                  C.cast(C.byref(h), C.c_void_p) if h is not None else None,
+                                  tr.ctypes.data if tr is not None else None,
+                                  _ptr(self.counts, C.c_int64), _ptr(self.ex_counts, C.c_int64))
+        if n_ex < 0:
+            raise ValueError("oracle_cycle rejected its arguments")
+        self.t += n_steps
+        self.e += n_ex
+        return tr, n_ex
 
     def forces(self, w):
         """MD forces [n, 3] on the particles of walker w."""

@@ -20,6 +20,8 @@
  *   stream 2: exchange type and parity, counter (e, 0, 0, 2)
  *   stream 3: exchange uniform of the pair whose lower state index is a,
  *             counter (e, a, 0, 3)
+ *   stream 10: REGC cycle, particle or replica exchange at step t,
+ *             counter (t, 0, 0, 10)
  *
  * Planted-mistake switches (oracle_system.mutation, zero in real use) exist so
  * that the tests can show each pin detects the mistake it is meant to catch:
@@ -34,6 +36,8 @@
  *   256 cluster: insertion/removal ratios with the total N instead of N_B
  *   512 MD thermostat: the cross term 2 R1 sqrt(...) of the rescaled kinetic energy dropped
  *   1024 MD: forces with the wrong sign
+ *   2048 REGC cycle: the two branches of the x0 choice swapped
+ *   4096 REGC cycle: canonical moves drawn from the mixed move set
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -350,9 +354,18 @@ static int n_gc(const oracle_system *sys, int n)
     return (sys->mutation & 256) ? n : n - sys->n_cluster;
 }
 
-static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr,
-                         double *e_ptr, int state, uint32_t t0, int n_sweeps,
-                         oracle_hist *hist, oracle_move *trace, int64_t *counts)
+/* How a trial move picks its kind: MOVE_MIXED draws displacement or
+ * particle exchange from A0 and p_disp (the sweeps); the REGC cycle fixes it,
+ * MOVE_GC for its particle-exchange attempt, MOVE_DISPLACE for the canonical
+ * diffusion that follows. */
+enum { MOVE_MIXED = 0, MOVE_GC = 1, MOVE_DISPLACE = 2 };
+
+/* Trial move k of sweep (or REGC step) t of walker w at the walker's state:
+ * draws A = Philox((k, t, w, 0)) and B = Philox((k, t, w, 1)), evaluates the
+ * move and applies it if accepted (positions, *n_io, *e_io).  mv receives its
+ * record. */
+static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, double *e_io,
+                       int state, uint32_t k, uint32_t t, int kind, oracle_move *out)
 {
     const double lx = sys->Lx, ly = sys->Ly, lz = sys->Lz;
     const double delta = f32(sys->max_disp);
@@ -360,119 +373,135 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
     double p = sys->p_disp < 0.0 ? 0.0 : (sys->p_disp > 1.0 ? 1.0 : sys->p_disp);
     const uint64_t th_disp = (uint64_t)floor(p * 4294967296.0);
     const double beta = 1.0 / kT_of(sys, state);
+    int n = *n_io;
+    double e = *e_io;
+    uint32_t A[4], B[4];
+    draw(sys, k, t, (uint32_t)w, 0u, A);
+    draw(sys, k, t, (uint32_t)w, 1u, B);
+    oracle_move mv;
+    memset(&mv, 0, sizeof mv);
+    mv.ln_u = log(u32_open(B[1]));
+    if (kind == MOVE_DISPLACE || (kind == MOVE_MIXED && (uint64_t)A[0] < th_disp)) {
+        mv.type = 0;
+    } else {
+        /* removal if y1 < 0.5, else insertion (Sec. II.A.1) */
+        mv.type = (B[2] >> 31) == 0u ? 2 : 1;
+    }
+    double nx = 0, ny = 0, nz = 0;  /* new position (displace/insert) */
+    int i = -1;
+    if (mv.type == 0) {
+        /* Metropolis displacement (Sec. II.A.3): random atom, uniform
+         * displacement in a cube of half-edge max_disp */
+        if (n == 0) { mv.status = 1; goto decided; }
+        i = (int)(((uint64_t)B[0] * (uint64_t)n) >> 32);
+        mv.index = i;
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = f32(delta * f32(2.0 * u24(A[1 + c]) - 1.0));
+        const double *ri = pos + 3 * i;
+        nx = f32(ri[0] + d[0]);
+        ny = f32(ri[1] + d[1]);
+        nz = f32(ri[2] + d[2]);
+        if (nx < 0.0) nx = f32(nx + lx);
+        if (nx >= lx) nx = f32(nx - lx);
+        if (ny < 0.0) ny = f32(ny + ly);
+        if (ny >= ly) ny = f32(ny - ly);
+        if (sys->periodic_z) {
+            if (nz < 0.0) nz = f32(nz + lz);
+            if (nz >= lz) nz = f32(nz - lz);
+        } else if (nz < sys->z_lo || nz > sys->z_hi) {
+            mv.status = 2;
+            goto decided;
+        }
+        double e_new = oracle_particle_energy(sys, pos, n, nx, ny, nz, i,
+                                              &mv.sum_abs, &mv.band, &mv.n_pairs);
+        double e_old = oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
+                                              &mv.sum_abs, &mv.band, &mv.n_pairs);
+        mv.dE = e_new - e_old;
+        mv.log_alpha = -beta * mv.dE;
+    } else if (mv.type == 1) {
+        /* insertion at a uniform point of the region (Sec. II.A.1) */
+        if (n == sys->nmax) { mv.status = 1; goto decided; }
+        mv.index = n;
+        nx = f32(lx * u24(A[1]));
+        ny = f32(ly * u24(A[2]));
+        nz = f32(sys->z_lo + f32(height * u24(A[3])));
+        if (nx >= lx) nx = f32(nx - lx);
+        if (ny >= ly) ny = f32(ny - ly);
+        if (sys->periodic_z && nz >= lz) nz = f32(nz - lz);
+        mv.dE = oracle_particle_energy(sys, pos, n, nx, ny, nz, -1,
+                                       &mv.sum_abs, &mv.band, &mv.n_pairs);
+        mv.log_alpha = oracle_log_alpha(sys, 1, state, n_gc(sys, n), mv.dE);
+    } else {
+        /* removal of grand-canonical particle i, (i-1)/N <= y2 < i/N
+         * (Sec. II.A.1), counted among the N_B of that species */
+        if (n == sys->n_cluster) { mv.status = 1; goto decided; }
+        i = sys->n_cluster + (int)(((uint64_t)B[0] * (uint64_t)(n - sys->n_cluster)) >> 32);
+        mv.index = i;
+        const double *ri = pos + 3 * i;
+        mv.dE = -oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
+                                        &mv.sum_abs, &mv.band, &mv.n_pairs);
+        mv.log_alpha = oracle_log_alpha(sys, 2, state, n_gc(sys, n), mv.dE);
+    }
+    if (sys->da) {
+        /* stage 1 with the surrogate energy change */
+        if (mv.type == 0) {
+            const double *ri = pos + 3 * i;
+            mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, i, NULL) -
+                        oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
+        } else if (mv.type == 1) {
+            mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, -1, NULL);
+        } else {
+            const double *ri = pos + 3 * i;
+            mv.dE_sur = -oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
+        }
+        mv.ln_u1 = log(u32_open(B[3]));
+        mv.stage1 = mv.ln_u1 < oracle_log_alpha(sys, mv.type, state, n_gc(sys, n), mv.dE_sur);
+        /* stage 2: the exact correction */
+        double corr = (sys->mutation & 128) ? 0.0 : mv.dE_sur;
+        mv.accepted = mv.stage1 && mv.ln_u < -beta * (mv.dE - corr);
+    } else {
+        mv.accepted = mv.ln_u < mv.log_alpha;
+    }
+    if (mv.accepted) {
+        if (mv.type == 0) {
+            double *ri = pos + 3 * i;
+            ri[0] = nx; ri[1] = ny; ri[2] = nz;
+        } else if (mv.type == 1) {
+            double *rn = pos + 3 * n;
+            rn[0] = nx; rn[1] = ny; rn[2] = nz;
+            n += 1;
+        } else {
+            int gone = (sys->mutation & 64) ? (i + 1) % n : i;
+            memcpy(pos + 3 * gone, pos + 3 * (n - 1), 3 * sizeof(double));
+            n -= 1;
+        }
+        e += mv.dE;
+    }
+decided:
+    *n_io = n;
+    *e_io = e;
+    *out = mv;
+}
+
+static void count_move(int64_t *counts, int w, const oracle_move *mv)
+{
+    if (!counts) return;
+    counts[6 * (int64_t)w + 2 * mv->type] += 1;
+    counts[6 * (int64_t)w + 2 * mv->type + 1] += mv->accepted;
+}
+
+static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr,
+                         double *e_ptr, int state, uint32_t t0, int n_sweeps,
+                         oracle_hist *hist, oracle_move *trace, int64_t *counts)
+{
     int n = *n_ptr;
     double e = *e_ptr;
-
     for (int ts = 0; ts < n_sweeps; ++ts) {
         uint32_t t = t0 + (uint32_t)ts;
         for (int k = 0; k < sys->moves_per_sweep; ++k) {
-            uint32_t A[4], B[4];
-            draw(sys, (uint32_t)k, t, (uint32_t)w, 0u, A);
-            draw(sys, (uint32_t)k, t, (uint32_t)w, 1u, B);
             oracle_move mv;
-            memset(&mv, 0, sizeof mv);
-            mv.ln_u = log(u32_open(B[1]));
-            if ((uint64_t)A[0] < th_disp) {
-                mv.type = 0;
-            } else {
-                /* removal if y1 < 0.5, else insertion (Sec. II.A.1) */
-                mv.type = (B[2] >> 31) == 0u ? 2 : 1;
-            }
-            double nx = 0, ny = 0, nz = 0;  /* new position (displace/insert) */
-            int i = -1;
-            if (mv.type == 0) {
-                /* Metropolis displacement (Sec. II.A.3): random atom, uniform
-                 * displacement in a cube of half-edge max_disp */
-                if (n == 0) { mv.status = 1; goto decided; }
-                i = (int)(((uint64_t)B[0] * (uint64_t)n) >> 32);
-                mv.index = i;
-                double d[3];
-                for (int c = 0; c < 3; ++c) d[c] = f32(delta * f32(2.0 * u24(A[1 + c]) - 1.0));
-                const double *ri = pos + 3 * i;
-                nx = f32(ri[0] + d[0]);
-                ny = f32(ri[1] + d[1]);
-                nz = f32(ri[2] + d[2]);
-                if (nx < 0.0) nx = f32(nx + lx);
-                if (nx >= lx) nx = f32(nx - lx);
-                if (ny < 0.0) ny = f32(ny + ly);
-                if (ny >= ly) ny = f32(ny - ly);
-                if (sys->periodic_z) {
-                    if (nz < 0.0) nz = f32(nz + lz);
-                    if (nz >= lz) nz = f32(nz - lz);
-                } else if (nz < sys->z_lo || nz > sys->z_hi) {
-                    mv.status = 2;
-                    goto decided;
-                }
-                double e_new = oracle_particle_energy(sys, pos, n, nx, ny, nz, i,
-                                                      &mv.sum_abs, &mv.band, &mv.n_pairs);
-                double e_old = oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
-                                                      &mv.sum_abs, &mv.band, &mv.n_pairs);
-                mv.dE = e_new - e_old;
-                mv.log_alpha = -beta * mv.dE;
-            } else if (mv.type == 1) {
-                /* insertion at a uniform point of the region (Sec. II.A.1) */
-                if (n == sys->nmax) { mv.status = 1; goto decided; }
-                mv.index = n;
-                nx = f32(lx * u24(A[1]));
-                ny = f32(ly * u24(A[2]));
-                nz = f32(sys->z_lo + f32(height * u24(A[3])));
-                if (nx >= lx) nx = f32(nx - lx);
-                if (ny >= ly) ny = f32(ny - ly);
-                if (sys->periodic_z && nz >= lz) nz = f32(nz - lz);
-                mv.dE = oracle_particle_energy(sys, pos, n, nx, ny, nz, -1,
-                                               &mv.sum_abs, &mv.band, &mv.n_pairs);
-                mv.log_alpha = oracle_log_alpha(sys, 1, state, n_gc(sys, n), mv.dE);
-            } else {
-                /* removal of grand-canonical particle i, (i-1)/N <= y2 < i/N
-                 * (Sec. II.A.1), counted among the N_B of that species */
-                if (n == sys->n_cluster) { mv.status = 1; goto decided; }
-                i = sys->n_cluster + (int)(((uint64_t)B[0] * (uint64_t)(n - sys->n_cluster)) >> 32);
-                mv.index = i;
-                const double *ri = pos + 3 * i;
-                mv.dE = -oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
-                                                &mv.sum_abs, &mv.band, &mv.n_pairs);
-                mv.log_alpha = oracle_log_alpha(sys, 2, state, n_gc(sys, n), mv.dE);
-            }
-            if (sys->da) {
-                /* stage 1 with the surrogate energy change */
-                if (mv.type == 0) {
-                    const double *ri = pos + 3 * i;
-                    mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, i, NULL) -
-                                oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
-                } else if (mv.type == 1) {
-                    mv.dE_sur = oracle_surrogate_energy(sys, pos, n, nx, ny, nz, -1, NULL);
-                } else {
-                    const double *ri = pos + 3 * i;
-                    mv.dE_sur = -oracle_surrogate_energy(sys, pos, n, ri[0], ri[1], ri[2], i, NULL);
-                }
-                mv.ln_u1 = log(u32_open(B[3]));
-                mv.stage1 = mv.ln_u1 < oracle_log_alpha(sys, mv.type, state, n_gc(sys, n), mv.dE_sur);
-                /* stage 2: the exact correction */
-                double corr = (sys->mutation & 128) ? 0.0 : mv.dE_sur;
-                mv.accepted = mv.stage1 && mv.ln_u < -beta * (mv.dE - corr);
-            } else {
-                mv.accepted = mv.ln_u < mv.log_alpha;
-            }
-            if (mv.accepted) {
-                if (mv.type == 0) {
-                    double *ri = pos + 3 * i;
-                    ri[0] = nx; ri[1] = ny; ri[2] = nz;
-                } else if (mv.type == 1) {
-                    double *rn = pos + 3 * n;
-                    rn[0] = nx; rn[1] = ny; rn[2] = nz;
-                    n += 1;
-                } else {
-                    int gone = (sys->mutation & 64) ? (i + 1) % n : i;
-                    memcpy(pos + 3 * gone, pos + 3 * (n - 1), 3 * sizeof(double));
-                    n -= 1;
-                }
-                e += mv.dE;
-            }
-        decided:
-            if (counts) {
-                counts[6 * (int64_t)w + 2 * mv.type] += 1;
-                counts[6 * (int64_t)w + 2 * mv.type + 1] += mv.accepted;
-            }
+            trial_move(sys, w, pos, &n, &e, state, (uint32_t)k, t, MOVE_MIXED, &mv);
+            count_move(counts, w, &mv);
             if (trace) trace[((int64_t)ts * sys->moves_per_sweep + k)] = mv;
         }
         observe(sys, hist, state, n - sys->n_cluster, e);
@@ -566,6 +595,84 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
         }
     }
     return accepted;
+}
+
+/* ----------------------------------------------------------- REGC cycle */
+
+/* The REGC cycle of Sec. II.A (Fig. 1), with the settings of Sec. III.A:
+ * n_steps steps numbered t0, t0 + 1, ...  Step t draws G = Philox((t, 0, 0,
+ * 10)).  If G0 < floor(x0 2^32) -- probability x0 -- every replica attempts
+ * one particle exchange with the reservoir: move k = 0 of step t, an
+ * insertion or a removal with equal probability (B2, as in the sweeps).
+ * Otherwise one collective replica-exchange attempt is made (exchange numbers
+ * e0, e0 + 1, ... in order).  Then every replica diffuses at fixed N with
+ * moves k = 1 .. n_canonical of step t, all Metropolis displacements, and is
+ * observed once.
+ * trace, if given, is [n_walkers][n_steps][n_canonical + 1]; slot k = 0 of a
+ * replica-exchange step holds type -1 and status 4 (not attempted).
+ * counts and ex_counts as in oracle_sweeps and oracle_exchange.
+ * Planted mistakes: 2048 swaps the two branches of the x0 choice; 4096 draws
+ * the canonical moves from the mixed move set of the sweeps.
+ * Returns the number of replica-exchange steps, or -1 on invalid arguments. */
+int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, double *energy,
+                 int32_t *state_of_walker, int32_t *walker_of_state, uint32_t t0, uint32_t e0,
+                 int n_steps, double x0, int n_canonical, oracle_hist *hist, oracle_move *trace,
+                 int64_t *counts, int64_t *ex_counts)
+{
+    int S = sys->L * sys->M;
+    if (n_walkers != S || n_steps < 0 || n_canonical < 1 || !(x0 >= 0.0 && x0 <= 1.0)) return -1;
+    for (int w = 0; w < S; ++w)
+        if (n[w] < 0 || n[w] > sys->nmax || state_of_walker[w] < 0 || state_of_walker[w] >= S) return -1;
+    const uint64_t th_gc = x0 >= 1.0 ? (uint64_t)1 << 32 : (uint64_t)floor(x0 * 4294967296.0);
+    const int per_step = n_canonical + 1;
+    const int canonical_kind = (sys->mutation & 4096) ? MOVE_MIXED : MOVE_DISPLACE;
+    uint32_t e = e0;
+    int n_exchange = 0;
+    for (int ts = 0; ts < n_steps; ++ts) {
+        const uint32_t t = t0 + (uint32_t)ts;
+        uint32_t G[4];
+        draw(sys, t, 0u, 0u, 10u, G);
+        int gc = (uint64_t)G[0] < th_gc;
+        if (sys->mutation & 2048) gc = !gc;
+        if (gc) {
+            for (int w = 0; w < S; ++w) {
+                int nw = n[w];
+                oracle_move mv;
+                trial_move(sys, w, pos + (int64_t)w * sys->nmax * 3, &nw, energy + w, state_of_walker[w],
+                           0u, t, MOVE_GC, &mv);
+                n[w] = nw;
+                count_move(counts, w, &mv);
+                if (trace) trace[((int64_t)w * n_steps + ts) * per_step] = mv;
+            }
+        } else {
+            if (oracle_exchange(sys, e, n, energy, state_of_walker, walker_of_state, ex_counts) < 0) return -1;
+            e += 1;
+            n_exchange += 1;
+            if (trace) {
+                for (int w = 0; w < S; ++w) {
+                    oracle_move mv;
+                    memset(&mv, 0, sizeof mv);
+                    mv.type = -1;
+                    mv.status = 4;
+                    trace[((int64_t)w * n_steps + ts) * per_step] = mv;
+                }
+            }
+        }
+        for (int w = 0; w < S; ++w) {
+            int nw = n[w];
+            const int state = state_of_walker[w];
+            double *pw = pos + (int64_t)w * sys->nmax * 3;
+            for (int k = 1; k <= n_canonical; ++k) {
+                oracle_move mv;
+                trial_move(sys, w, pw, &nw, energy + w, state, (uint32_t)k, t, canonical_kind, &mv);
+                count_move(counts, w, &mv);
+                if (trace) trace[((int64_t)w * n_steps + ts) * per_step + k] = mv;
+            }
+            n[w] = nw;
+            observe(sys, hist, state, nw - sys->n_cluster, energy[w]);
+        }
+    }
+    return n_exchange;
 }
 
 /* ------------------------------------------------------------------ MD */

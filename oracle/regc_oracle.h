@@ -119,6 +119,10 @@ int    oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32
                      double *energy, const int32_t *state_of_walker, uint32_t t0,
                      int n_sweeps, oracle_hist *hist, oracle_move *trace,
                      int64_t *counts, int n_threads);
+int    oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, double *energy,
+                    int32_t *state_of_walker, int32_t *walker_of_state, uint32_t t0, uint32_t e0,
+                    int n_steps, double x0, int n_canonical, oracle_hist *hist, oracle_move *trace,
+                    int64_t *counts, int64_t *ex_counts);
 void   oracle_forces(const oracle_system *sys, const double *pos, int n, double *f);
 int    oracle_md(const oracle_system *sys, int n_walkers, double *pos, const int32_t *n, double *energy,
                  const int32_t *state_of_walker, uint32_t seg, int n_steps, double dt, double tau,
