@@ -41,10 +41,10 @@ import workloads as W  # noqa: E402
 
 SWEEPS_PER_STEP = 10
 # DRAM bytes (read + write) of one sweep-kernel launch on the benchmark
-# workload from an ncu capture of the current kernel
-# (dram__bytes_read.sum 4.331264e6 + dram__bytes_write.sum 256); None whenever
-# the kernel has changed since its last capture
-SWEEP_TRAFFIC_BYTES = 4331264 + 256
+# workload from an ncu capture of the current kernel; None whenever the
+# kernel has changed since its last capture (it has: the REGC cycle's move
+# schedule)
+SWEEP_TRAFFIC_BYTES = None
 FLOPS_PER_PAIR = 20            # dx,dy,dz 3, xy minimum image 4, r^2 5, r^-2 1, s^6 3, 4eps s^6(s^6-1) 4
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 METRIC = "GCMC trial moves/s over all replicas"
@@ -68,6 +68,9 @@ def parse_args(argv=None):
     ap.add_argument("--md", type=int, default=1, help="1: add MD segments (REGCMD) of the main workload")
     ap.add_argument("--md-segments", type=int, default=10)
     ap.add_argument("--cluster", type=int, default=1, help="1: add the cluster-in-gas workload")
+    ap.add_argument("--paper-cycle", type=int, default=1,
+                    help="1: add the paper's LJ run through the REGC cycle (x0 = 0.99)")
+    ap.add_argument("--paper-steps", type=int, default=120000, help="REGC steps of that run")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
@@ -450,6 +453,90 @@ def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0
     }
 
 
+# ---------------------------------------------------------------- the paper's LJ run
+
+PAPER_CYCLE = ("the paper's LJ surface system (Sec. III.A) in eV and Angstrom: two-layer fcc(111) A slab "
+               "(two 3x3 A18 cells, 36 A) under B gas in a 48 A zone, 10 T (200-650 K) x 16 mu "
+               "(-2.4..-0.9 eV) = 160 replicas, Nmax 256; REGC cycle x0 = 0.99, 10 displacements per step")
+
+
+def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, cpu_seconds=8.0, seed=0):
+    """The paper's whole LJ sampling run through regc_cycle: n_steps REGC steps
+    of the 160 replicas from the pristine slab (N_B = 0 everywhere),
+    device-timed in chunks of `chunk` steps with the L2 flushed before each.
+    Reports the rate, the wall time of the run, the replica-exchange
+    acceptance (about 25 % in the paper) and, from the second half of the
+    run, the mean and modal N_B per state counted per A18 cell."""
+    from paper_1908_11118_gb300 import Regc
+    p = W.lj_a18_slab(seed=seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(np.zeros((p.S, p.nmax, 3)), np.zeros(p.S, np.int32))
+    g.cycle(200, x0, n_c)                       # warm-up: launches and first insertions
+    g.reset_histograms()
+    mv0, ex0, _ = g.counters()
+    ev, n_ex = [], 0
+    h_half = None
+    done = 0
+    torch.cuda.synchronize()
+    while done < n_steps:
+        k = min(chunk, n_steps - done)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n_ex += g.cycle(k, x0, n_c)
+        b.record(stream)
+        ev.append((a, b))
+        done += k
+        if h_half is None and done >= n_steps // 2:
+            h_half = g.histograms()["hN"]
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    mv1, ex1, _ = g.counters()
+    h = g.histograms()["hN"] - h_half
+    ex = (ex1 - ex0).sum(axis=(0, 1))
+    trials = int((mv1[:, :, 0] - mv0[:, :, 0]).sum())
+    nv = np.arange(p.nmax + 1)
+    mean_nb = (h @ nv) / np.maximum(h.sum(axis=1), 1)
+    mode_nb = np.argmax(h, axis=1)
+    modes, counts = np.unique(mode_nb, return_counts=True)
+    drift = g.check_energy()
+    g.close()
+    # the oracle on the same run for a bounded number of steps, on the host cores
+    from oracle import oracle as O
+    O.build()
+    o = O.Oracle(p)
+    o.cycle(200, x0, n_c, hist=False)
+    chunks_cpu, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < cpu_seconds and chunks_cpu < len(ev):
+        o.cycle(chunk, x0, n_c, hist=True)
+        chunks_cpu += 1
+    el = time.perf_counter() - t0
+    steps_cpu = chunks_cpu * chunk
+    # the GPU on the same leading chunks of the same run (both from the
+    # pristine slab, same seed), for a like-for-like ratio
+    ms_same = sum(a.elapsed_time(b) for a, b in ev[:chunks_cpu])
+    return {
+        "workload": PAPER_CYCLE,
+        "steps": n_steps,
+        "ms": ms,
+        "regc_steps_per_s": n_steps / (ms / 1e3),
+        "trial_moves_per_s": trials / (ms / 1e3),
+        "paper_run_seconds": 1.2e5 * ms / 1e3 / n_steps,
+        "replica_exchange_steps": n_ex,
+        "replica_exchange_acceptance": float(ex[1] / max(ex[0], 1)),
+        "mean_nb_per_a18": np.round(mean_nb.reshape(p.L, p.M) / 2.0, 1).tolist(),
+        "modal_nb_per_a18": {str(int(m) / 2.0): int(c) for m, c in zip(modes, counts)},
+        "energy_drift": drift,
+        "l2": "flushed (256 MB memset) before every chunk of %d steps" % chunk,
+        "cpu_baseline": {"value": steps_cpu / el, "unit": "REGC steps/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": "the first %d steps of the same run from the pristine slab, after the "
+                                   "same 200 warm-up steps (%.1f s)" % (steps_cpu, el),
+                         "gpu_same_steps_per_s": steps_cpu / max(ms_same / 1e3, 1e-9)},
+    }
+
+
 # ---------------------------------------------------------------- own arm
 
 def run_own(args):
@@ -556,6 +643,10 @@ def run_own(args):
         cluster = delayed_acceptance_arm(W.cluster_in_gas(seed=0), CLUSTER_WORKLOAD, torch, stream, flush,
                                          1_000_000, args.da_train_steps, args.da_steps_large)
 
+    paper = None
+    if args.paper_cycle and rank == 0:
+        paper = paper_cycle_arm(torch, stream, flush, args.paper_steps)
+
     line = None
     if rank == 0:
         cpu = None
@@ -594,6 +685,7 @@ def run_own(args):
             "batched_uneven": batched,
             "regcmd": regcmd,
             "cluster_in_gas": cluster,
+            "paper_lj_cycle": paper,
         }
         print(json.dumps(line), flush=True)
     g.close()

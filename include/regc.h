@@ -41,6 +41,8 @@
  *   Exchange number e draws C = Philox((e, 0, 0, 2)) (direction (C0 * 4) >> 32,
  *   parity C1 >> 31) and, for the pair whose lower state index is a,
  *   D = Philox((e, a, 0, 3)), u = (D0 + 0.5) 2^-32.
+ *   Step t of the REGC cycle (regc_cycle) chooses particle or replica
+ *   exchange from Philox((t, 0, 0, 10)).
  */
 #ifndef REGC_H
 #define REGC_H
@@ -116,11 +118,12 @@ typedef struct {
 
 /* One trial move, as recorded by regc_sweep_traced. */
 typedef struct {
-    int32_t type;        /* 0 displacement, 1 insertion, 2 removal                 */
+    int32_t type;        /* 0 displacement, 1 insertion, 2 removal (-1: none)      */
     int32_t index;       /* particle moved or removed; insertion: the new slot N  */
     int32_t accepted;    /* 1 if accepted                                          */
     int32_t status;      /* 0 energy evaluated, 1 rejected at N = 0 or N = nmax,
-                            2 displacement left [z_lo, z_hi]                       */
+                            2 displacement left [z_lo, z_hi], 4 not attempted
+                            (regc_cycle_traced; type is then -1)                   */
     double  dE;          /* energy change of the move (status 0); NaN when delayed
                             acceptance rejected the move at stage 1 (dE is then
                             never computed)                                        */
@@ -192,6 +195,32 @@ REGC_API regc_status regc_md(regc_handle *h, int n_steps, float dt, float tau, f
  * where state a holds (N_a, E_a).  A swap exchanges the walkers' state labels.
  * Asynchronous.  The exchange counter advances by one per call. */
 REGC_API regc_status regc_exchange(regc_handle *h);
+
+/* n_steps steps of the REGC cycle (Sec. II.A and its flow chart, Fig. 1;
+ * Sec. III.A uses x0 = 0.99 and ten MC moves per step).  Step t (the sweep
+ * counter: steps and sweeps share it) draws G = Philox((t, 0, 0, 10)):
+ *   - G0 < floor(x0 2^32) (probability x0): every walker attempts one
+ *     particle exchange with the reservoir, trial move k = 0 of sweep t, an
+ *     insertion or a removal with equal probability (B2 as in a sweep; A0 is
+ *     not used);
+ *   - otherwise one collective replica-exchange attempt, as regc_exchange
+ *     (the exchange counter advances by one);
+ * then every walker makes n_canonical Metropolis displacements at fixed N,
+ * trial moves k = 1 .. n_canonical of sweep t (A0 not used), and is observed
+ * once into its state's histograms, as after a sweep.  moves_per_sweep and
+ * p_disp of the grid spec play no part.  Runs between two replica exchanges
+ * go to the device as one launch.  n_exchanges (host, may be NULL) receives
+ * the number of replica-exchange steps.  Asynchronous.  Errors: REGC_EINVAL
+ * (n_steps < 0, n_canonical outside 1..1023, x0 outside [0, 1] or NaN,
+ * walkers missing after regc_set_cluster), the handle's sticky status. */
+REGC_API regc_status regc_cycle(regc_handle *h, int n_steps, double x0, int n_canonical, int *n_exchanges);
+
+/* As regc_cycle, and write one record per trial move to host memory: trace is
+ * [S walkers][n_steps][n_canonical + 1], slot k of step t holding move k of
+ * that step; slot 0 of a replica-exchange step is not attempted and holds
+ * type -1, status 4, all else 0.  Synchronous. */
+REGC_API regc_status regc_cycle_traced(regc_handle *h, int n_steps, double x0, int n_canonical,
+                                       regc_move_record *trace, int *n_exchanges);
 
 /* Copy the histograms to caller-owned host buffers (any may be NULL):
  * hN [S][nmax+1], hNE [nmax+1][n_e_bins], omega [S], moments [S][4]

@@ -611,6 +611,8 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
  * trace, if given, is [n_walkers][n_steps][n_canonical + 1]; slot k = 0 of a
  * replica-exchange step holds type -1 and status 4 (not attempted).
  * counts and ex_counts as in oracle_sweeps and oracle_exchange.
+ * Walkers are independent within a step: the loops over them are OpenMP
+ * loops, as in oracle_sweeps.
  * Planted mistakes: 2048 swaps the two branches of the x0 choice; 4096 draws
  * the canonical moves from the mixed move set of the sweeps.
  * Returns the number of replica-exchange steps, or -1 on invalid arguments. */
@@ -635,6 +637,9 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
         int gc = (uint64_t)G[0] < th_gc;
         if (sys->mutation & 2048) gc = !gc;
         if (gc) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
             for (int w = 0; w < S; ++w) {
                 int nw = n[w];
                 oracle_move mv;
@@ -658,6 +663,9 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
                 }
             }
         }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
         for (int w = 0; w < S; ++w) {
             int nw = n[w];
             const int state = state_of_walker[w];

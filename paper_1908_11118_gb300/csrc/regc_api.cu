@@ -425,6 +425,9 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     P.move_counts = d_mc;
     P.error = h->d_error;
     P.trace = nullptr;
+    P.trace_steps = 0;
+    P.cycle = 0;
+    P.m_first = 0;
     h->X = ExchangeParams{grid->L, grid->M, P.key0, P.key1, d_beta, d_bmu, d_lnbeta, d_n, d_efix, d_sow, d_wos, d_exc};
     TRY(cuda_fail(h, cudaStreamSynchronize(h->stream)));
 #undef TRY
@@ -459,6 +462,7 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
     P.t0 = h->t;
     P.n_sweeps = n_sweeps;
     P.trace = d_trace;
+    P.trace_steps = n_sweeps;
     st = cuda_fail(h, launch_sweep(P, h->stream));
     if (st == REGC_OK) {
         h->t += (uint32_t)n_sweeps;
@@ -468,6 +472,94 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
     cudaFreeAsync(d_trace, h->stream);
     const regc_status st2 = sync_check(h);
     return st != REGC_OK ? st : st2;
+}
+
+// The REGC cycle.  The choice of step t (particle or replica exchange) is a
+// function of t alone, so the host reads the whole schedule from the Philox
+// stream first and launches each run of steps between two replica exchanges
+// as one sweep launch: mps = n_canonical + 1 moves per step, move 0 the
+// particle exchange, skipped (m_first = 1) in a step that began with a
+// replica exchange.
+static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, regc_move_record* trace,
+                             int* n_exchanges) {
+    if (!h || n_steps < 0 || n_canonical < 1 || n_canonical > 1023 || !(x0 >= 0.0 && x0 <= 1.0))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (h->need_walkers) return REGC_EINVAL;
+    if (n_exchanges) *n_exchanges = 0;
+    if (n_steps == 0) return REGC_OK;
+    const unsigned long long th_gc =
+        x0 >= 1.0 ? (1ull << 32) : (unsigned long long)floor(x0 * 4294967296.0);
+    const int mps = n_canonical + 1;
+    const size_t n_rec = (size_t)h->S * n_steps * mps;
+    regc_move_record* d_trace = nullptr;
+    if (trace) {
+        const regc_status st = cuda_fail(h, cudaMallocAsync(&d_trace, n_rec * sizeof(regc_move_record), h->stream));
+        if (st != REGC_OK) return st;
+    }
+    SweepParams P = h->P;
+    P.cycle = 1;
+    P.mps = mps;
+    P.trace_steps = n_steps;
+    std::vector<char> re_step(n_steps, 0);
+    cudaError_t e = cudaSuccess;
+    int n_ex = 0;
+    auto segment = [&](int a, int len, bool skip) {
+        if (e != cudaSuccess || len <= 0) return;
+        P.t0 = h->t + (uint32_t)a;
+        P.n_sweeps = len;
+        P.m_first = skip ? 1 : 0;
+        P.trace = d_trace ? d_trace + (size_t)a * mps : nullptr;
+        e = launch_sweep(P, h->stream);
+    };
+    int seg = 0;
+    bool seg_skip = false;
+    for (int ts = 0; ts < n_steps && e == cudaSuccess; ++ts) {
+        const U4 G = philox(h->t + (uint32_t)ts, 0u, 0u, 10u, P.key0, P.key1);
+        if ((unsigned long long)G.x < th_gc) continue;
+        re_step[ts] = 1;
+        segment(seg, ts - seg, seg_skip);
+        if (e == cudaSuccess) e = launch_exchange(h->X, h->e + (uint32_t)n_ex, h->stream);
+        n_ex += 1;
+        seg = ts;
+        seg_skip = true;
+    }
+    segment(seg, n_steps - seg, seg_skip);
+    regc_status st = cuda_fail(h, e);
+    if (st == REGC_OK) {
+        h->t += (uint32_t)n_steps;
+        h->e += (uint32_t)n_ex;
+        if (n_exchanges) *n_exchanges = n_ex;
+    }
+    if (d_trace) {
+        if (st == REGC_OK)
+            st = cuda_fail(h, cudaMemcpyAsync(trace, d_trace, n_rec * sizeof(regc_move_record),
+                                              cudaMemcpyDeviceToHost, h->stream));
+        cudaFreeAsync(d_trace, h->stream);
+        const regc_status st2 = sync_check(h);
+        if (st == REGC_OK) st = st2;
+        if (st == REGC_OK) {
+            // the particle exchange of a replica-exchange step is not attempted
+            regc_move_record none;
+            memset(&none, 0, sizeof none);
+            none.type = -1;
+            none.status = 4;
+            for (int w = 0; w < h->S; ++w)
+                for (int ts = 0; ts < n_steps; ++ts)
+                    if (re_step[ts]) trace[((size_t)w * n_steps + ts) * mps] = none;
+        }
+    }
+    return st;
+}
+
+regc_status regc_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, int* n_exchanges) {
+    return run_cycle(h, n_steps, x0, n_canonical, nullptr, n_exchanges);
+}
+
+regc_status regc_cycle_traced(regc_handle* h, int n_steps, double x0, int n_canonical, regc_move_record* trace,
+                              int* n_exchanges) {
+    if (!trace && n_steps > 0) return REGC_EINVAL;
+    return run_cycle(h, n_steps, x0, n_canonical, trace, n_exchanges);
 }
 
 regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kinetic) {

@@ -151,9 +151,14 @@ struct SweepParams {
     unsigned long long* pair_counts;  // [6] pairs in rc, candidates, rounds, evaluations,
                                       //     surrogate-screened moves, stage-1 passes
     int* error;
-    regc_move_record* trace;      // device [S][n_sweeps][mps] or null
+    regc_move_record* trace;      // device [S][trace_steps][mps] or null, at this launch's first sweep
+    int trace_steps;              // sweeps (steps) per walker in the trace buffer
     uint32_t t0;
     int n_sweeps;
+    int cycle;                    // 1: REGC cycle steps -- move 0 of a step is a particle exchange
+                                  //    (insertion or removal), moves 1 .. mps-1 are displacements
+    int m_first;                  // first move of the launch (1: its first step began with a
+                                  //    replica exchange, so its particle exchange is not attempted)
     int smem_per_walker;          // bytes
     int warps_per_walker;         // 1, 2 or 4
     int delayed;                  // 1: two-stage delayed acceptance with the surrogate

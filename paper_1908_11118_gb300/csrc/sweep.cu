@@ -465,7 +465,9 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
     // removal act on the grand-canonical species, whose count is N - nA
     const int nA = CL ? P.n_cluster : 0;
     const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
-    const int type = (unsigned long long)A.x < P.th_disp ? 0 : ((B.z >> 31) == 0u ? 2 : 1);
+    // the kind of move: drawn from A0 in a sweep, fixed by its place in a REGC cycle step
+    const int gc_type = (B.z >> 31) == 0u ? 2 : 1;
+    const int type = P.cycle ? (m % P.mps == 0 ? gc_type : 0) : ((unsigned long long)A.x < P.th_disp ? 0 : gc_type);
     int status = 0, idx = -1, overlap = 0;
     const int n_in0 = n_in;
     float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
@@ -700,7 +702,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
     const int total_moves = P.n_sweeps * P.mps;
     const float rc_guard = P.g.rc2 * 1.0004f + 1e-6f;   // a little beyond rc, conservatively
     int filled = 0;   // moves whose Philox blocks are in the ring
-    int m0 = 0;       // first move of the round
+    int m0 = P.m_first;   // first move of the round
 
     while (m0 < total_moves) {
         // 3a. Philox blocks of the next 32 moves, drawn by all lanes at once
@@ -851,7 +853,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     t.stage1 = DA ? r.stage1 : 1;
                     t.dE_sur = DA ? (double)r.dE_sur : 0.0;
                     t.ln_u1 = log((double)B.w + 0.5) + kLn2m32;
-                    P.trace[(size_t(w) * P.n_sweeps + ts) * P.mps + k] = t;
+                    P.trace[(size_t(w) * P.trace_steps + ts) * P.mps + k] = t;
                 }
                 // 6. observe once per sweep into the current state's histograms
                 if (k == P.mps - 1) {

@@ -108,6 +108,23 @@ class Regc:
     def exchange(self):
         check(_lib.lib().regc_exchange(self._h), "regc_exchange")
 
+    def cycle(self, n_steps: int, x0: float, n_canonical: int) -> int:
+        """n_steps steps of the REGC cycle (regc_cycle); returns the number of
+        replica-exchange steps."""
+        n_ex = C.c_int(0)
+        check(_lib.lib().regc_cycle(self._h, int(n_steps), float(x0), int(n_canonical), C.byref(n_ex)),
+              "regc_cycle")
+        return n_ex.value
+
+    def cycle_traced(self, n_steps: int, x0: float, n_canonical: int):
+        """As cycle, with the trace [S, n_steps, n_canonical + 1]; returns
+        (trace, replica-exchange steps)."""
+        tr = np.zeros((self.S, n_steps, n_canonical + 1), MOVE_DTYPE)
+        n_ex = C.c_int(0)
+        check(_lib.lib().regc_cycle_traced(self._h, int(n_steps), float(x0), int(n_canonical), tr.ctypes.data,
+                                           C.byref(n_ex)), "regc_cycle_traced")
+        return tr, n_ex.value
+
     def md(self, n_steps: int, dt: float, tau: float, kinetic: bool = True):
         """One MD segment of every walker (regc_md); returns the kinetic
         energies [S] after the last step (or None when kinetic is False)."""

@@ -16,6 +16,9 @@ Workloads (reduced Lennard-Jones units, k_B = eps_gg = sigma_gg = m = 1):
   ABC stacking), 18.75 x 16.238 box, gas region 12 high above the top layer,
   eps_sg in {1, 2, 3}, 32 x 32 (kT, mu) states, Nmax 512.  This stands in for
   the paper's LJ A18 slab in a B gas (Sec. III.A) in reduced units.
+* ``lj_a18_slab`` -- the paper's LJ surface system (Sec. III.A) in eV and
+  Angstrom: two-layer fcc(111) A slab, B gas in a 48 A zone, 10 T x 16 mu
+  replicas, in a rectangular cell holding two of the paper's 3 x 3 cells.
 * ``tiny_box`` -- a few surface atoms in a small box, Nmax <= 2, for
   brute-force partition-function checks.
 """
@@ -187,6 +190,108 @@ def fcc111_paper_scale(L: int = 32, M: int = 32, nmax: int = 512, eps_sg: float 
         max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
         e_lo=-float(nmax) * 14.0, e_bin=0.5,
         n_e_bins=int(round(float(nmax) * 15.0 / 0.5)), name="fcc111_paper_scale")
+
+
+# Physical constants (CODATA 2018) for the workload in physical units.
+K_B_EV = 8.617333262e-5          # Boltzmann constant, eV / K
+PLANCK_J_S = 6.62607015e-34
+AMU_KG = 1.66053906660e-27
+EV_J = 1.602176634e-19
+
+
+def thermal_lambda0(mass_amu: float) -> float:
+    """lambda0 in Angstrom eV^(1/2) such that Lambda(kT) = h / sqrt(2 pi m kT)
+    = lambda0 / sqrt(kT) with kT in eV (Sec. II.A.1, the thermal wavelength)."""
+    return PLANCK_J_S / math.sqrt(2.0 * math.pi * mass_amu * AMU_KG * EV_J) * 1e10
+
+
+def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = 39.948,
+                rc_over_sigma_ab: float = 2.5, zone: float = 48.0, seed: int = 0) -> Problem:
+    """The paper's Lennard-Jones surface system (Sec. III.A, Appendix) in
+    physical units: energies in eV, lengths in Angstrom, kT = k_B T in eV.
+
+    A frozen two-layer fcc(111) slab of species A (type 1) with hexagonal
+    lattice vectors of 11.489 A for its 3 x 3 cell (nearest-neighbour distance
+    11.489 / 3), under a gas of species B (type 0): eps_AB = 0.66 eV,
+    eps_BB = 0.01 eV, sigma_AB = 1.91 A, sigma_BB = 1.2 A.  The periodic cell
+    here is rectangular, 3 x 6 rows (11.489 x 19.899 A), and holds two of the
+    paper's hexagonal 3 x 3 cells: 36 A atoms, so that N_B here corresponds to
+    2 N_B of the paper's A18.  B lives in a zone of height `zone` above the
+    topmost A layer (hard walls at both ends).  The (T, mu) grid: L
+    temperatures from 200 K in steps of 50 K, M chemical potentials from
+    -2.4 eV in steps of 0.1 eV (10 x 16 = 160 replicas in the paper).
+    The paper gives neither the cutoff nor the mass of B: rc = 2.5 sigma_AB
+    and an argon mass are this workload's choices."""
+    s = 11.489 / 3.0
+    xyz, lx, ly, ztop = fcc111_slab(3, 6, 2, s)
+    eps = np.zeros((4, 4))
+    sig = np.ones((4, 4))
+    eps[0, 0], sig[0, 0] = 0.01, 1.2
+    eps[0, 1] = eps[1, 0] = 0.66
+    sig[0, 1] = sig[1, 0] = 1.91
+    sig[1, 1] = 2.5
+    zhi = float(f32(ztop + zone))
+    return Problem(
+        n_types=2, eps=f32(eps), sigma=f32(sig), rc=rc_over_sigma_ab * 1.91, Lx=lx, Ly=ly, Lz=zhi,
+        periodic_z=0, z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=K_B_EV * (200.0 + 50.0 * np.arange(L)), mu=-2.4 + 0.1 * np.arange(M),
+        lambda0=thermal_lambda0(mass_amu), nmax=nmax, moves_per_sweep=11, max_disp=0.2,
+        p_disp=1.0 / 3.0, seed=seed, e_lo=-1.8 * nmax, e_bin=0.01,
+        n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_slab")
+
+
+def lj_a18_initial(problem: Problem, n_b, seed: int, min_dist: float = 1.9):
+    """Seeded walkers of ``lj_a18_slab``: walker w gets n_b[w] B particles,
+    the first up to 36 on a random subset of the hollow sites of the top A
+    layer (both kinds, 36 in the cell) just above the zone's floor with a small
+    random offset, the rest at uniform points of the zone at least min_dist
+    from every particle and surface atom.  Binary32 coordinates.
+    Returns (pos [S, nmax, 3], n [S])."""
+    rng = np.random.default_rng(seed)
+    S, nmax = problem.S, problem.nmax
+    n_b = np.broadcast_to(np.asarray(n_b, dtype=np.int64), (S,))
+    s = 11.489 / 3.0
+    h = s * math.sqrt(3.0) / 2.0
+    sites = []
+    for sx, sy in ((0.0, 0.0), (s, 2.0 * h / 3.0)):      # the two hollow sites of a B-stacked top layer
+        for j in range(6):
+            for i in range(3):
+                sites.append((((i * s + (0.5 * s if j % 2 else 0.0) + sx) % problem.Lx), (j * h + sy) % problem.Ly))
+    sites = np.array(sites)
+    box = np.array([problem.Lx, problem.Ly, problem.Lz])
+    per = np.array([True, True, False])
+    pos = np.zeros((S, nmax, 3))
+    n = np.zeros(S, np.int32)
+    for w in range(S):
+        k = int(min(n_b[w], len(sites)))
+        pick = rng.permutation(len(sites))[:k]
+        pts = []
+        for a in pick:
+            x = (sites[a, 0] + rng.uniform(-0.1, 0.1)) % problem.Lx
+            y = (sites[a, 1] + rng.uniform(-0.1, 0.1)) % problem.Ly
+            q = f32([x, y, problem.z_lo + rng.uniform(0.0, 0.3)])
+            q[0] = 0.0 if q[0] >= problem.Lx else q[0]
+            q[1] = 0.0 if q[1] >= problem.Ly else q[1]
+            pts.append(list(q))
+        tries = 0
+        while len(pts) < n_b[w] and tries < 200000:
+            tries += 1
+            q = f32([rng.uniform(0, problem.Lx), rng.uniform(0, problem.Ly),
+                     rng.uniform(problem.z_lo + 2.0, problem.z_hi)])
+            if q[0] >= problem.Lx or q[1] >= problem.Ly or q[2] > problem.z_hi:
+                continue
+            others = np.array(pts + [list(a) for a in problem.surf_xyz]).reshape(-1, 3)
+            d = q - others
+            d = np.where(per, d - box * np.round(d / box), d)
+            if np.min(np.sum(d * d, axis=1)) < min_dist * min_dist:
+                continue
+            pts.append(list(q))
+        if len(pts) < n_b[w]:
+            raise ValueError("could not place the requested particles")
+        if pts:
+            pos[w, :len(pts)] = np.array(pts)
+        n[w] = len(pts)
+    return pos, n
 
 
 def tiny_box(nmax: int = 2, rc: float = 1.5, eps_sg: float = 1.0, eps_gg: float = 1.0,
