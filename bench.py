@@ -501,6 +501,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     mode_nb = np.argmax(h, axis=1)
     modes, counts = np.unique(mode_nb, return_counts=True)
     drift = g.check_energy()
+    wpw = g.warps_per_walker()
     g.close()
     # the oracle on the same run for a bounded number of steps, on the host cores
     from oracle import oracle as O
@@ -523,6 +524,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
         "regc_steps_per_s": n_steps / (ms / 1e3),
         "trial_moves_per_s": trials / (ms / 1e3),
         "paper_run_seconds": 1.2e5 * ms / 1e3 / n_steps,
+        "warps_per_walker": wpw,
         "replica_exchange_steps": n_ex,
         "replica_exchange_acceptance": float(ex[1] / max(ex[0], 1)),
         "mean_nb_per_a18": np.round(mean_nb.reshape(p.L, p.M) / 2.0, 1).tolist(),
@@ -675,7 +677,7 @@ def run_own(args):
                          "launch_ms": mean_sweep_s * 1e3},
             "e2e": {"value": p.S * SWEEPS_PER_STEP * p.moves_per_sweep * world / e2e_s, "unit": "moves/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "speculation": {"warps_per_walker": int(os.environ.get("REGC_WARPS_PER_WALKER", "1")),
+            "speculation": {"warps_per_walker": g.warps_per_walker(),
                             "moves_per_round": moves / max(rounds, 1),
                             "kept_fraction": moves / max(evals, 1)},
             "gpu_launches": 2 * K,

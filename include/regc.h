@@ -304,6 +304,14 @@ REGC_API regc_status regc_restore(regc_handle *h, const void *buf, size_t length
  * walkers since the last reset.  Synchronous. */
 REGC_API regc_status regc_counters(regc_handle *h, int64_t *moves, int64_t *exchanges, int64_t *pairs);
 
+/* Warps that evaluate a walker's moves in the plain sweep (1, 2 or 4; moves
+ * evaluated speculatively per round and committed in order, so the chain does
+ * not depend on it).  Chosen at creation from the replicas per SM (4 up to two
+ * per SM, 2 up to four, else 1) unless the environment variable
+ * REGC_WARPS_PER_WALKER sets it; halved while one walker's shared memory
+ * would not fit.  Delayed acceptance and the cluster species use one. */
+REGC_API regc_status regc_warps_per_walker(const regc_handle *h, int *warps);
+
 /* MBAR reweighting of the handle's pooled histogram (Sec. II.B).  Solves the
  * self-consistent equations of Eq. normlizationconstant over the occupied
  * (N, E) bins with the reduced potential

@@ -76,6 +76,7 @@ SIGNATURES = {
     "regc_get_walkers": ([_h, _fp, _ip, _dp, _ip], C.c_int),
     "regc_check_energy": ([_h, _dp], C.c_int),
     "regc_counters": ([_h, _lp, _lp, _lp], C.c_int),
+    "regc_warps_per_walker": ([_h, C.POINTER(C.c_int)], C.c_int),
     "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
     "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
                          C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),

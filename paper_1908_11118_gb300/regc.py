@@ -184,6 +184,11 @@ class Regc:
         check(_lib.lib().regc_check_energy(self._h, C.byref(d)), "regc_check_energy")
         return d.value
 
+    def warps_per_walker(self) -> int:
+        w = C.c_int(0)
+        check(_lib.lib().regc_warps_per_walker(self._h, C.byref(w)), "regc_warps_per_walker")
+        return w.value
+
     def counters(self):
         mv = np.zeros((self.S, 3, 2), np.int64)
         ex = np.zeros((self.S, 4, 2), np.int64)
