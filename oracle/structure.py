@@ -1,0 +1,160 @@
+"""FP64 oracle of the structural observables of Sec. III.A ("Structural
+properties") and of their MBAR averages per phase (Sec. II.B, Eq. avegr).
+
+TEST INFRASTRUCTURE ONLY: used by the tests and the benchmark's CPU baseline,
+never by the library.
+
+Per sample (one walker's configuration, grand-canonical species only):
+
+* axial distribution: particles counted in slabs of width dz parallel to the
+  surface, slab k of a particle at height z being floor((z - z_lo) * (1/dz));
+* lateral RDF of a layer l (particles with layer_lo[l] <= z < layer_hi[l]):
+  unordered pairs of the layer counted by their distance in the xy plane
+  (nearest image in x and y), bin k = floor(r * (1/dr)).
+
+The bin of a value is an integer decided by floating point, so it is taken
+in binary32, with the operations of the GPU path in the same order (the
+paper fixes no precision): d = z - z_lo, k = floor(d * inv_dz); the
+nearest-image difference e = q - p, or (q - L) - p when e > L/2, or
+q - (p - L) when e < -L/2; r2 = dx dx + dy dy, r = sqrt(r2),
+k = floor(r * inv_dr); inv_dz and inv_dr are 1/dz and 1/dr rounded once to
+binary32.  Everything after the counts is FP64.
+
+Per configuration the functions of Sec. III.A are
+  rho(z_k) = c_k / (A dz)                                (number density)
+  g_xy(r_k) = 2 A P_k / (M (M - 1) pi (r_{k+1}^2 - r_k^2))   (M >= 2, else 0)
+with A = Lx Ly, c_k the slab count, P_k the pair count of the layer and M its
+population (the normalisation that gives g_xy = 1 for uniformly placed points).
+
+MBAR average per phase (Eq. avegr, the phase i being N_B = i): every sample
+is a bin of its own, (N_n, E_n), count 1; the MBAR free energies of the
+sampled states follow from the solve of oracle/mbar.py, and the weight of
+sample n at the query state q is
+  W_n(q) = exp(-u_q(N_n, E_n) - D_n + f_q),  sum over all n of W_n(q) = 1.
+Eq. avegr as printed sums W_n(q) g(r; R_n) over the samples of phase i, the
+joint average of [N = i] g.  The average of g within phase i divides that by
+p_i(q) = sum over the samples of phase i of W_n(q); both are returned.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mbar as MB
+
+F = np.float32
+
+
+def _min_image_f32(q, p, L, hL):
+    e = F(q - p)
+    if e > hL:
+        return F(F(q - L) - p)
+    if e < -hL:
+        return F(q - F(p - L))
+    return e
+
+
+def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
+    """Counts of one configuration: (slab counts [n_z], pair counts
+    [n_layers, n_r], layer populations [n_layers]).
+
+    spec: dict with n_z, dz, layers [(lo, hi), ...], n_r, dr.
+    mutation 1: slab index one too high; 2: ordered pairs counted twice."""
+    n_z, n_r = int(spec["n_z"]), int(spec["n_r"])
+    layers = list(spec["layers"])
+    inv_dz, inv_dr = F(1.0 / spec["dz"]), F(1.0 / spec["dr"])
+    z_lo = F(problem.z_lo)
+    Lx, Ly = F(problem.Lx), F(problem.Ly)
+    hLx, hLy = F(0.5 * problem.Lx), F(0.5 * problem.Ly)
+    first = int(getattr(problem, "n_cluster", 0))
+    pts = [tuple(F(c) for c in pos_w[j]) for j in range(first, int(n_w))]
+    rho = np.zeros(n_z, np.int64)
+    for (_, _, z) in pts:
+        k = int(math.floor(F(F(z - z_lo) * inv_dz)))
+        if mutation & 1:
+            k += 1
+        if 0 <= k < n_z:
+            rho[k] += 1
+    pairs = np.zeros((len(layers), n_r), np.int64)
+    pop = np.zeros(len(layers), np.int64)
+    for l, (lo, hi) in enumerate(layers):
+        lo, hi = F(lo), F(hi)
+        mem = [q for q in pts if lo <= q[2] < hi]
+        pop[l] = len(mem)
+        for a in range(len(mem)):
+            for b in range(a + 1, len(mem)):
+                dx = _min_image_f32(mem[a][0], mem[b][0], Lx, hLx)
+                dy = _min_image_f32(mem[a][1], mem[b][1], Ly, hLy)
+                r2 = F(F(dx * dx) + F(dy * dy))
+                k = int(math.floor(F(np.sqrt(r2) * inv_dr)))
+                if k < n_r:
+                    pairs[l, k] += 2 if mutation & 2 else 1
+    return rho, pairs, pop
+
+
+def structure_of_walkers(problem, pos, n, state_of_walker, energy, spec):
+    """One sample per walker: dict of arrays state [S], N [S] (grand-canonical
+    count), E [S], rho [S, n_z], pairs [S, n_layers, n_r], pop [S, n_layers]."""
+    S = len(n)
+    first = int(getattr(problem, "n_cluster", 0))
+    out = {"state": np.array(state_of_walker, np.int64), "N": np.array(n, np.int64) - first,
+           "E": np.array(energy, np.float64),
+           "rho": np.zeros((S, spec["n_z"]), np.int64),
+           "pairs": np.zeros((S, len(spec["layers"]), spec["n_r"]), np.int64),
+           "pop": np.zeros((S, len(spec["layers"])), np.int64)}
+    for w in range(S):
+        r, p, m = sample_counts(problem, pos[w], n[w], spec)
+        out["rho"][w], out["pairs"][w], out["pop"][w] = r, p, m
+    return out
+
+
+def concat(samples):
+    return {k: np.concatenate([s[k] for s in samples]) for k in samples[0]}
+
+
+def reweight(problem, samples, spec, kT_q, mu_q, n_lo, n_hi, tol=1e-10, max_iter=200000, mutation: int = 0):
+    """MBAR averages per phase N_B = n_lo..n_hi at the query states.
+
+    Returns dict: f [S] (sampled states, f_0 = 0), p [Q, phases] (probability
+    of each phase), rho [Q, phases, n_z] and gxy [Q, phases, n_layers, n_r]
+    (averages within each phase; zero where p = 0), joint_rho and joint_gxy
+    (Eq. avegr as printed: the same sums without the division by p).
+    mutation 4: the 3 N ln Lambda term left out of the query's reduced potential."""
+    kT_s = np.asarray(problem.kT)[np.arange(problem.S) // problem.M]
+    mu_s = np.asarray(problem.mu)[np.arange(problem.S) % problem.M]
+    st, N, E = samples["state"], samples["N"].astype(np.float64), samples["E"]
+    omega = np.bincount(st, minlength=problem.S).astype(np.float64)
+    lam0 = problem.lambda0
+    f, D, _, _ = MB.solve(kT_s, mu_s, lam0, omega, N, E, np.ones(len(N)), tol=tol, max_iter=max_iter)
+    u = MB.reduced_potential(kT_q, mu_q, lam0, N, E)             # [Q, n]
+    if mutation & 4:
+        kq = np.atleast_1d(np.asarray(kT_q, np.float64))[:, None]
+        u = u - 3.0 * N[None, :] * (math.log(lam0) - 0.5 * np.log(kq))
+    ln_w = -u - D[None, :]
+    f_q = -MB.lse(ln_w, axis=1)
+    W = np.exp(ln_w + f_q[:, None])                                # [Q, n], rows sum to 1
+    A = problem.Lx * problem.Ly
+    dz, dr = float(spec["dz"]), float(spec["dr"])
+    n_r = int(spec["n_r"])
+    shell = math.pi * dr * dr * ((np.arange(n_r) + 1.0) ** 2 - np.arange(n_r) ** 2)
+    pop = samples["pop"].astype(np.float64)
+    norm = np.where(pop >= 2, 2.0 * A / np.maximum(pop * (pop - 1.0), 1.0), 0.0)       # [n, layers]
+    g_n = samples["pairs"] * norm[:, :, None] / shell[None, None, :]                      # [n, layers, n_r]
+    rho_n = samples["rho"] / (A * dz)                                                     # [n, n_z]
+    Q, P = W.shape[0], n_hi - n_lo + 1
+    out = {"f": f, "p": np.zeros((Q, P)), "rho": np.zeros((Q, P, rho_n.shape[1])),
+           "gxy": np.zeros((Q, P) + g_n.shape[1:]), "joint_rho": np.zeros((Q, P, rho_n.shape[1])),
+           "joint_gxy": np.zeros((Q, P) + g_n.shape[1:])}
+    for i in range(P):
+        sel = samples["N"] == n_lo + i
+        if not np.any(sel):
+            continue
+        w = W[:, sel]
+        out["p"][:, i] = w.sum(axis=1)
+        out["joint_rho"][:, i] = w @ rho_n[sel]
+        out["joint_gxy"][:, i] = np.tensordot(w, g_n[sel], axes=(1, 0))
+        ok = out["p"][:, i] > 0
+        out["rho"][ok, i] = out["joint_rho"][ok, i] / out["p"][ok, i][:, None]
+        out["gxy"][ok, i] = out["joint_gxy"][ok, i] / out["p"][ok, i][:, None, None]
+    return out
