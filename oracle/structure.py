@@ -17,8 +17,9 @@ in binary32, with the operations of the GPU path in the same order (the
 paper fixes no precision): d = z - z_lo, k = floor(d * inv_dz); the
 nearest-image difference e = q - p, or (q - L) - p when e > L/2, or
 q - (p - L) when e < -L/2; r2 = dx dx + dy dy, r = sqrt(r2),
-k = floor(r * inv_dr); inv_dz and inv_dr are 1/dz and 1/dr rounded once to
-binary32.  Everything after the counts is FP64.
+k = floor(r * inv_dr).  Like every geometric input, dz and dr are binary32
+values; inv_dz and inv_dr are 1/dz and 1/dr rounded once to binary32.
+Everything after the counts is FP64.
 
 Per configuration the functions of Sec. III.A are
   rho(z_k) = c_k / (A dz)                                (number density)
@@ -63,7 +64,7 @@ def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
     mutation 1: slab index one too high; 2: ordered pairs counted twice."""
     n_z, n_r = int(spec["n_z"]), int(spec["n_r"])
     layers = list(spec["layers"])
-    inv_dz, inv_dr = F(1.0 / spec["dz"]), F(1.0 / spec["dr"])
+    inv_dz, inv_dr = F(1.0 / float(F(spec["dz"]))), F(1.0 / float(F(spec["dr"])))
     z_lo = F(problem.z_lo)
     Lx, Ly = F(problem.Lx), F(problem.Ly)
     hLx, hLy = F(0.5 * problem.Lx), F(0.5 * problem.Ly)
@@ -135,7 +136,7 @@ def reweight(problem, samples, spec, kT_q, mu_q, n_lo, n_hi, tol=1e-10, max_iter
     f_q = -MB.lse(ln_w, axis=1)
     W = np.exp(ln_w + f_q[:, None])                                # [Q, n], rows sum to 1
     A = problem.Lx * problem.Ly
-    dz, dr = float(spec["dz"]), float(spec["dr"])
+    dz, dr = float(F(spec["dz"])), float(F(spec["dr"]))
     n_r = int(spec["n_r"])
     shell = math.pi * dr * dr * ((np.arange(n_r) + 1.0) ** 2 - np.arange(n_r) ** 2)
     pop = samples["pop"].astype(np.float64)

@@ -43,7 +43,11 @@ def hollow_sites(p):
         for j in range(6):
             for i in range(3):
                 pts.append(((i * a + (0.5 * a if j % 2 else 0.0) + sx) % p.Lx, (j * h + sy) % p.Ly))
-    return np.array(pts), a
+    xy = W.f32(np.array(pts))
+    # a coordinate that rounds up onto the period is the image at 0
+    xy[:, 0] = np.where(xy[:, 0] >= p.Lx, 0.0, xy[:, 0])
+    xy[:, 1] = np.where(xy[:, 1] >= p.Ly, 0.0, xy[:, 1])
+    return xy, a
 
 
 def test_honeycomb_pair_shells_and_one_slab():
@@ -123,7 +127,8 @@ def test_one_state_average_is_the_plain_average():
         sel = smp["N"] == nb
         assert out["p"][0, i] == pytest.approx(sel.mean(), rel=1e-12)
         if sel.any():
-            np.testing.assert_allclose(out["rho"][0, i], smp["rho"][sel].mean(axis=0) / (A * 0.12), rtol=1e-11)
+            dz = float(np.float32(0.12))                # widths are binary32 values
+            np.testing.assert_allclose(out["rho"][0, i], smp["rho"][sel].mean(axis=0) / (A * dz), rtol=1e-11)
 
 
 def ideal_gas_run(seed=0, blocks=300):
@@ -173,7 +178,7 @@ def test_ideal_gas_reweighted_to_an_unsampled_state(ideal):
     ok = out["p"][0] > 1e-3
     # the 75 slabs of 0.12 cover the whole region (H = 8.895): rho integrates
     # to N in every phase
-    integral = out["rho"][0].sum(axis=1) * A * spec["dz"]
+    integral = out["rho"][0].sum(axis=1) * A * float(np.float32(spec["dz"]))
     np.testing.assert_allclose(integral[ok], nb[ok], rtol=1e-12)
     # and is flat at N / (A H) over the 74 slabs inside the region
     flat = nb[ok] / (A * H)
