@@ -460,17 +460,43 @@ PAPER_CYCLE = ("the paper's LJ surface system (Sec. III.A) in eV and Angstrom: t
                "(-2.4..-0.9 eV) = 160 replicas, Nmax 256; REGC cycle x0 = 0.99, 10 displacements per step")
 
 
-def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, cpu_seconds=8.0, seed=0):
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) from the peaks file, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return float(json.load(open(path))["hbm_gbs"]), "MEASURED_PEAKS.json (hbm_gbs)"
+        except Exception:
+            pass
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def paper_structure_spec(p):
+    """Slabs of 0.12 A over the 48 A zone (Sec. III.A) and three adsorbate
+    layers above the floor for g_xy, lateral bins of 0.1 A up to 5.7 A."""
+    return {"n_z": 400, "dz": 0.12,
+            "layers": [(p.z_lo, p.z_lo + 0.6), (p.z_lo + 0.6, p.z_lo + 1.6), (p.z_lo + 1.6, p.z_lo + 2.6)],
+            "n_r": 57, "dr": 0.1}
+
+
+def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, cpu_seconds=8.0, seed=0,
+                    sample_every=100):
     """The paper's whole LJ sampling run through regc_cycle: n_steps REGC steps
-    of the 160 replicas from the pristine slab (N_B = 0 everywhere),
-    device-timed in chunks of `chunk` steps with the L2 flushed before each.
-    Reports the rate, the wall time of the run, the replica-exchange
-    acceptance (about 25 % in the paper) and, from the second half of the
-    run, the mean and modal N_B per state counted per A18 cell."""
+    of the 160 replicas from the pristine slab (N_B = 0 everywhere), with the
+    structure of every replica sampled every `sample_every` steps as the paper
+    sub-samples; device-timed in chunks of `chunk` steps with the L2 flushed
+    before each.  Reports the rate, the wall time of the run, the
+    replica-exchange acceptance (about 25 % in the paper), the mean and modal
+    N_B per state from the second half counted per A18 cell, and the MBAR
+    reweighting of the samples per phase (Eq. avegr) with the HBM roofline of
+    its accumulation kernel."""
     from paper_1908_11118_gb300 import Regc
     p = W.lj_a18_slab(seed=seed)
+    spec = paper_structure_spec(p)
     g = Regc(p, stream=stream)
     g.set_walkers(np.zeros((p.S, p.nmax, 3)), np.zeros(p.S, np.int32))
+    g.structure_init(spec["n_z"], spec["dz"], spec["layers"], spec["n_r"], spec["dr"],
+                     (n_steps // sample_every + 1) * p.S)
     g.cycle(200, x0, n_c)                       # warm-up: launches and first insertions
     g.reset_histograms()
     mv0, ex0, _ = g.counters()
@@ -484,12 +510,19 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
             flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        n_ex += g.cycle(k, x0, n_c)
+        left = k
+        while left > 0:
+            step = min(sample_every, left)
+            n_ex += g.cycle(step, x0, n_c)
+            left -= step
+            if step == sample_every:
+                g.structure_sample()
         b.record(stream)
         ev.append((a, b))
         done += k
         if h_half is None and done >= n_steps // 2:
             h_half = g.histograms()["hN"]
+            g.structure_reset()                 # MBAR on the second half only
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     mv1, ex1, _ = g.counters()
@@ -502,6 +535,24 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     modes, counts = np.unique(mode_nb, return_counts=True)
     drift = g.check_energy()
     wpw = g.warps_per_walker()
+
+    # MBAR over the sub-sampled second half, per phase, at eight states: the
+    # sampled corners and the two state points of the paper's g_xy figure
+    n_samples = g.structure_count()
+    kB = W.K_B_EV
+    kq = np.array([kB * 200, kB * 650, kB * 200, kB * 650, kB * 200, kB * 600, kB * 425, kB * 300])
+    mq = np.array([-0.9, -0.9, -2.4, -2.4, -1.3, -1.1, -1.5, -1.9])
+    t0 = time.perf_counter()
+    rw = g.structure_reweight(kq, mq, 0, p.nmax, tol=1e-9, max_iter=200000)
+    rw_s = time.perf_counter() - t0
+    tm = g.structure_timing()
+    ach = tm["bytes_accumulate"] / (tm["ms_accumulate"] / 1e3) / 1e9
+    peak, peak_src = hbm_peak()
+    phases = []
+    for q in range(len(kq)):
+        i = int(np.argmax(rw["p"][q]))
+        phases.append({"T_K": round(kq[q] / kB), "mu_eV": mq[q], "most_probable_nb_per_a18": i / 2.0,
+                       "p": round(float(rw["p"][q, i]), 3)})
     g.close()
     # the oracle on the same run for a bounded number of steps, on the host cores
     from oracle import oracle as O
@@ -531,10 +582,20 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
         "modal_nb_per_a18": {str(int(m) / 2.0): int(c) for m, c in zip(modes, counts)},
         "energy_drift": drift,
         "l2": "flushed (256 MB memset) before every chunk of %d steps" % chunk,
+        "structure": {
+            "samples": n_samples, "every_steps": sample_every, "spec": {k: v for k, v in spec.items()},
+            "reweight_s": rw_s, "mbar_iterations": rw["iters"], "ms_mbar": tm["ms_mbar"],
+            "ms_weights": tm["ms_weights"], "ms_accumulate": tm["ms_accumulate"],
+            "most_probable_phase": phases,
+            "roofline": {"bound": "hbm", "kernel": "accumulate_kernel", "achieved": ach, "peak": peak,
+                         "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src,
+                         "work": "%.4g algorithmic bytes per launch (%d samples x %d query states)"
+                                 % (tm["bytes_accumulate"], n_samples, len(kq))},
+        },
         "cpu_baseline": {"value": steps_cpu / el, "unit": "REGC steps/s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": "the first %d steps of the same run from the pristine slab, after the "
-                                   "same 200 warm-up steps (%.1f s)" % (steps_cpu, el),
+                                   "same 200 warm-up steps, without structure samples (%.1f s)" % (steps_cpu, el),
                          "gpu_same_steps_per_s": steps_cpu / max(ms_same / 1e3, 1e-9)},
     }
 

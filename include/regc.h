@@ -326,6 +326,81 @@ REGC_API regc_status regc_reweight(regc_handle *h, int nq, const double *kT_q, c
                           double tol, int max_iter, double *N_mean, double *pN,
                           double *f_states, int *iters);
 
+/* Structural observables (Sec. III.A, "Structural properties"): the axial
+ * distribution rho(z) of the adsorbed particles, counted in slabs parallel to
+ * the surface, and the lateral radial distribution g_xy(r) of the particles of
+ * an adsorbate layer z0 +- dz0, kept per sample and averaged per phase by MBAR
+ * (Sec. II.B, Eq. avegr).  Only the grand-canonical species is counted.
+ * Bin decisions are binary32, in this order: slab k = floor((z - z_lo) *
+ * inv_dz); lateral distance r = sqrt(dx dx + dy dy) with dx, dy the nearest
+ * image in x and y (e = q - p, or (q - L) - p when e > L/2, or q - (p - L)
+ * when e < -L/2), bin k = floor(r * inv_dr); inv_dz = 1/dz and inv_dr = 1/dr
+ * rounded to binary32 once. */
+typedef struct {
+    int     n_z;            /* slabs, 1..4096: slab k covers z_lo + [k, k+1) dz         */
+    float   dz;             /* > 0 (0.12 A in Sec. III.A)                               */
+    int     n_layers;       /* 0..4 adsorbate layers for g_xy                            */
+    float   layer_lo[4];    /* a particle is in layer l if layer_lo[l] <= z < layer_hi[l] */
+    float   layer_hi[4];
+    int     n_r;            /* 1..4096 lateral distance bins: bin k covers [k, k+1) dr   */
+    float   dr;             /* > 0, with n_r dr <= min(Lx, Ly) / 2                      */
+    int64_t capacity;       /* samples the device keeps; each regc_structure_sample call
+                               adds one per walker                                      */
+} regc_structure_spec;
+
+/* Allocate (or replace) the handle's sample store.  Samples are not part of
+ * checkpoints.  Errors: REGC_EINVAL (sizes out of range, n_r dr beyond half the
+ * box, a walker's counting tables beyond 227 KB of shared memory), REGC_ENOMEM. */
+REGC_API regc_status regc_structure_init(regc_handle *h, const regc_structure_spec *spec);
+
+/* Append one sample of every walker: its state, N_B, E, slab counts and, per
+ * layer, its population and pair counts.  Asynchronous.  The paper takes one
+ * every 100 REGC steps.  Errors: REGC_EINVAL (no store, or the store cannot
+ * hold S more samples: nothing is appended). */
+REGC_API regc_status regc_structure_sample(regc_handle *h);
+
+/* Number of samples held. */
+REGC_API regc_status regc_structure_count(regc_handle *h, int64_t *n_samples);
+
+/* Drop every sample (the store stays allocated). */
+REGC_API regc_status regc_structure_reset(regc_handle *h);
+
+/* Copy samples first .. first + count - 1 to host buffers (any may be NULL):
+ * state [count], n [count] (N_B), energy [count], rho [count][n_z] slab counts,
+ * pairs [count][n_layers][n_r] pair counts (unordered pairs), pop
+ * [count][n_layers] layer populations.  Synchronous. */
+REGC_API regc_status regc_structure_get(regc_handle *h, int64_t first, int64_t count, int32_t *state,
+                                        int32_t *n, double *energy, uint16_t *rho, uint32_t *pairs,
+                                        int32_t *pop);
+
+/* MBAR averages per phase N_B = n_lo .. n_hi at nq query states (kT_q, mu_q),
+ * over the samples held (Eq. avegr).  Each sample is a bin of its own, (N_B,
+ * E), count 1: the MBAR equations (Eq. normlizationconstant, with the reduced
+ * potential of regc_reweight) are solved over the samples for the free
+ * energies of the sampled states (f_states [S], f_0 = 0), and sample n
+ * weighs W_n(q) = exp(-u_q(n) - D_n + f_q) at query q (the weights of all
+ * samples sum to 1).  Outputs (host, any may be NULL), phases P = n_hi - n_lo + 1:
+ *   p    [nq][P]                    probability of each phase, sum of W_n over it
+ *   rho  [nq][P][n_z]               sum_n W_n c_nk / (p A dz): number density
+ *                                   within the phase (A = Lx Ly)
+ *   gxy  [nq][P][n_layers][n_r]     sum_n W_n g_n(r_k) / p with the sample's
+ *                                   g_n(r_k) = 2 A P_nk / (M_n (M_n - 1) pi
+ *                                   ((k+1)^2 - k^2) dr^2) (0 when M_n < 2)
+ * Eq. avegr as printed is the joint average, p times these; zero where p = 0.
+ * FP64 on the device.  Synchronous.  Errors: REGC_EINVAL (no samples, bad
+ * phase range, nq < 1). */
+REGC_API regc_status regc_structure_reweight(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
+                                             int n_lo, int n_hi, double tol, int max_iter, double *p,
+                                             double *rho, double *gxy, double *f_states, int *iters);
+
+/* Device time of the last regc_structure_reweight (milliseconds, any pointer
+ * may be NULL): the MBAR solve and query over the samples, the sample weights,
+ * and the accumulation per phase, with the accumulation's algorithmic bytes
+ * (every row of a phase in range read once per pass of 8 query states, with
+ * its population and index, plus the weights and the sums written). */
+REGC_API regc_status regc_structure_timing(regc_handle *h, double *ms_mbar, double *ms_weights,
+                                           double *ms_accumulate, double *bytes_accumulate);
+
 /* Stand-alone MBAR solve over caller-supplied pooled bins (host buffers):
  * S states (kT [S], mu [S], omega [S] observations), B bins (N_b [B], E_b [B],
  * H_b [B] > 0 counts).  Outputs f [S] (f_0 = 0) and D [B], the log denominators

@@ -51,6 +51,11 @@ class MoveRecord(C.Structure):
                 ("ln_u1", C.c_double)]
 
 
+class StructureSpec(C.Structure):
+    _fields_ = [("n_z", C.c_int), ("dz", C.c_float), ("n_layers", C.c_int), ("layer_lo", C.c_float * 4),
+                ("layer_hi", C.c_float * 4), ("n_r", C.c_int), ("dr", C.c_float), ("capacity", C.c_int64)]
+
+
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 _lp = C.POINTER(C.c_int64)
@@ -77,6 +82,15 @@ SIGNATURES = {
     "regc_check_energy": ([_h, _dp], C.c_int),
     "regc_counters": ([_h, _lp, _lp, _lp], C.c_int),
     "regc_warps_per_walker": ([_h, C.POINTER(C.c_int)], C.c_int),
+    "regc_structure_init": ([_h, C.c_void_p], C.c_int),
+    "regc_structure_sample": ([_h], C.c_int),
+    "regc_structure_count": ([_h, C.POINTER(C.c_int64)], C.c_int),
+    "regc_structure_reset": ([_h], C.c_int),
+    "regc_structure_timing": ([_h, _dp, _dp, _dp, _dp], C.c_int),
+    "regc_structure_get": ([_h, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p], C.c_int),
+    "regc_structure_reweight": ([_h, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
+                                 _dp, C.POINTER(C.c_int)], C.c_int),
     "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
     "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
                          C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libregc.so")
-SOURCES = ["sweep.cu", "exchange.cu", "mbar.cu", "regc_api.cu", "mbar_static.cu", "surrogate.cu", "probe.cu", "walkers.cu", "batch.cu", "md.cu"]
+SOURCES = ["sweep.cu", "exchange.cu", "mbar.cu", "regc_api.cu", "mbar_static.cu", "surrogate.cu", "probe.cu", "walkers.cu", "batch.cu", "md.cu", "structure.cu"]
 HEADERS = ["regc_internal.cuh", "launch.h", "mbar.h", "surrogate.cuh", "handle.h", "cells.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -9,6 +9,28 @@ using regc::ExchangeParams;
 using regc::SurrogateStore;
 using regc::SweepParams;
 
+// Samples of the structural observables (structure.cu): one device block
+// holding state [cap], nb [cap], energy [cap], pop [cap][4], rho [cap][n_z],
+// pairs [cap][n_layers][n_r].
+struct StructureStore {
+    int n_z = 0, n_layers = 0, n_r = 0;
+    float dz = 0, dr = 0, inv_dz = 0, inv_dr = 0;
+    float layer_lo[4] = {}, layer_hi[4] = {};
+    long long cap = 0, count = 0;
+    size_t smem = 0;
+    void* block = nullptr;
+    int32_t* state = nullptr;
+    int32_t* nb = nullptr;
+    double* energy = nullptr;
+    int32_t* pop = nullptr;
+    uint16_t* rho = nullptr;
+    uint32_t* pairs = nullptr;
+    // the last reweighting: device milliseconds of the MBAR solve and query,
+    // the weights and the accumulation, and the accumulation's algorithmic bytes
+    double last_ms[3] = {0, 0, 0};
+    double last_bytes = 0;
+};
+
 struct regc_handle {
     cudaStream_t stream = nullptr;
     int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0;
@@ -44,6 +66,7 @@ struct regc_handle {
     double hard_core_T = 0.0;
     bool need_walkers = false;                // set_cluster emptied the walkers
     uint32_t md_seg = 0;                      // MD segments run (Philox counter of the MD streams)
+    StructureStore stc;                       // structural observables (empty until regc_structure_init)
 };
 
 // Synchronise the handle's stream and fold its device error word into the

@@ -4,13 +4,17 @@
 // occupied (N, E) bins b with counts H_b, in log form:
 //   D_b = ln sum_k Omega_k exp(f_k - u_k(b))        (one thread per bin)
 //   f_s = -ln sum_b H_b exp(-u_s(b) - D_b)           (one block per state)
-// with f_0 = 0 after each iteration.  Sums are log-sum-exp in FP64 with an
+// with f_0 = 0 after each iteration, accelerated by Anderson mixing on the
+// host (mbar_solve_dev).  Sums are log-sum-exp in FP64 with an
 // online maximum; terms more than 50 below the running maximum are skipped
 // (their total weight is below the FP64 rounding of the sum).
 // Query states reuse the D_b: the weight of bin b at state q is
 // H_b exp(-u_q(b) - D_b + f_q), giving <N> and p_N (Eq. textbook with the
 // phase indicator chi_i = [N = i]).
 #include <math.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "mbar.h"
 
@@ -115,33 +119,6 @@ __global__ void __launch_bounds__(256) f_kernel(const __grid_constant__ MbarDev 
         lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
     L = block_merge(L);
     if (threadIdx.x == 0) m.f_new[s] = -(L.m + log(L.s));
-}
-
-// Gauge f_0 = 0, convergence test, f <- f_new.
-__global__ void __launch_bounds__(1024) norm_kernel(const __grid_constant__ MbarDev m, double tol) {
-    if (m.state[0]) return;
-    const double f0 = m.f_new[0];
-    double d = 0.0;
-    for (int s = threadIdx.x; s < m.S; s += blockDim.x) d = fmax(d, fabs((m.f_new[s] - f0) - m.f[s]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
-    __shared__ double sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-        if (threadIdx.x == 0) sh[0] = r;
-    }
-    __syncthreads();
-    d = sh[0];
-    for (int s = threadIdx.x; s < m.S; s += blockDim.x) m.f[s] = m.f_new[s] - f0;
-    if (threadIdx.x == 0) {
-        m.delta[0] = d;
-        m.state[1] += 1;
-        if (d < tol) m.state[0] = 1;
-    }
 }
 
 __global__ void __launch_bounds__(256) query_kernel(const __grid_constant__ MbarDev m, const double* a_q,
@@ -294,36 +271,132 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
 
 }  // namespace
 
+// The self-consistent map G(f) = gauge(f_new(D(f))) is iterated with
+// Anderson acceleration (Walker & Ni, SIAM J. Numer. Anal. 49, 1715 (2011),
+// "type II" with differences): with the residuals r_i = G(x_i) - x_i of the
+// last kDepth iterates, gamma minimises |r_k - sum_j gamma_j (r_{j+1} - r_j)|
+// and x_{k+1} = G(x_k) - sum_j gamma_j (G(x_{j+1}) - G(x_j)).  The fixed point
+// is the one of the plain iteration (x = G(x)); only the path to it is
+// shorter.  An iterate whose residual grows past 100 times the best one so far
+// restarts the history from the best image.  Converged when max |r| < tol.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s) {
-    cudaError_t err;
-    const int batch = 16;
-    int host_state[2] = {0, 0};
-    err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
+    constexpr int kDepth = 8;
+    const int S = m.S;
+    cudaError_t err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(m.f, 0, size_t(m.S) * sizeof(double), s);
+    err = cudaMemsetAsync(m.f, 0, size_t(S) * sizeof(double), s);
     if (err != cudaSuccess) return err;
     const int dgrid = (m.B + 255) / 256;
-    int launched = 0;
-    while (launched < max_iter) {
-        const int nb = min(batch, max_iter - launched);
-        for (int i = 0; i < nb; ++i) {
-            d_kernel<<<dgrid, 256, 0, s>>>(m, 0);
-            f_kernel<<<m.S, 256, 0, s>>>(m);
-            norm_kernel<<<1, 1024, 0, s>>>(m, tol);
+    std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
+    std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
+    std::vector<double> r_prev, g_prev;
+    double best = INFINITY;
+    int it = 0;
+    while (it < max_iter) {
+        if (it > 0) {
+            err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (err != cudaSuccess) return err;
         }
-        launched += nb;
+        d_kernel<<<dgrid, 256, 0, s>>>(m, 1);
+        f_kernel<<<S, 256, 0, s>>>(m);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        err = cudaMemcpyAsync(host_state, m.state, sizeof(host_state), cudaMemcpyDeviceToHost, s);
+        err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return err;
-        err = cudaStreamSynchronize(s);
-        if (err != cudaSuccess) return err;
-        if (host_state[0]) break;
+        ++it;
+        const double g0 = g[0];
+        double delta = 0.0;
+        for (int k = 0; k < S; ++k) {
+            g[k] -= g0;
+            r[k] = g[k] - x[k];
+            delta = fmax(delta, fabs(r[k]));
+        }
+        if (!(delta == delta)) return cudaErrorInvalidValue;   // NaN: no fixed point to approach
+        if (delta < tol) {
+            x = g;
+            break;
+        }
+        if (delta < best) {
+            best = delta;
+            best_g = g;
+        } else if (delta > 100.0 * best) {
+            dR.clear();
+            dG.clear();
+            r_prev.clear();
+            x = best_g;
+            continue;
+        }
+        if (!r_prev.empty()) {
+            std::vector<double> a(S), b(S);
+            for (int k = 0; k < S; ++k) {
+                a[k] = r[k] - r_prev[k];
+                b[k] = g[k] - g_prev[k];
+            }
+            dR.push_back(a);
+            dG.push_back(b);
+            if ((int)dR.size() > kDepth) {
+                dR.erase(dR.begin());
+                dG.erase(dG.begin());
+            }
+        }
+        r_prev = r;
+        g_prev = g;
+        const int mh = (int)dR.size();
+        x = g;
+        if (mh > 0) {
+            // normal equations (dR^T dR + eps I) gamma = dR^T r, by Gaussian elimination
+            for (int i = 0; i < mh; ++i) {
+                rhs[i] = 0.0;
+                for (int k = 0; k < S; ++k) rhs[i] += dR[i][k] * r[k];
+                for (int j = 0; j < mh; ++j) {
+                    double v = 0.0;
+                    for (int k = 0; k < S; ++k) v += dR[i][k] * dR[j][k];
+                    A[i * kDepth + j] = v;
+                }
+            }
+            double diag = 0.0;
+            for (int i = 0; i < mh; ++i) diag = fmax(diag, A[i * kDepth + i]);
+            for (int i = 0; i < mh; ++i) A[i * kDepth + i] += 1e-12 * diag + 1e-300;
+            bool ok = true;
+            for (int c = 0; c < mh && ok; ++c) {
+                int piv = c;
+                for (int i = c + 1; i < mh; ++i)
+                    if (fabs(A[i * kDepth + c]) > fabs(A[piv * kDepth + c])) piv = i;
+                if (!(fabs(A[piv * kDepth + c]) > 0.0)) {
+                    ok = false;
+                    break;
+                }
+                if (piv != c) {
+                    for (int j = 0; j < mh; ++j) std::swap(A[c * kDepth + j], A[piv * kDepth + j]);
+                    std::swap(rhs[c], rhs[piv]);
+                }
+                for (int i = c + 1; i < mh; ++i) {
+                    const double f = A[i * kDepth + c] / A[c * kDepth + c];
+                    for (int j = c; j < mh; ++j) A[i * kDepth + j] -= f * A[c * kDepth + j];
+                    rhs[i] -= f * rhs[c];
+                }
+            }
+            if (ok) {
+                for (int i = mh - 1; i >= 0; --i) {
+                    double v = rhs[i];
+                    for (int j = i + 1; j < mh; ++j) v -= A[i * kDepth + j] * gam[j];
+                    gam[i] = v / A[i * kDepth + i];
+                }
+                for (int j = 0; j < mh; ++j)
+                    for (int k = 0; k < S; ++k) x[k] -= gam[j] * dG[j][k];
+            }
+        }
     }
+    err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return err;
     d_kernel<<<dgrid, 256, 0, s>>>(m, 1);  // D_b of the final f
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    if (iters_out) *iters_out = host_state[1];
+    // the host vectors go out of scope: wait for the copy that reads x
+    err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    if (iters_out) *iters_out = it;
     return cudaSuccess;
 }
 

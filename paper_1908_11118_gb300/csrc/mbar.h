@@ -21,11 +21,12 @@ struct MbarDev {
     double* f_new;         // [S]
     double* D;             // [B]
     double* delta;         // [1] max |f_new - f| of the last iteration
-    int* state;            // [2] {converged flag, iterations done}
+    int* state;            // [2] cleared by the solve (the kernels skip work when state[0] is set)
 };
 
-// Iterate the self-consistent equations from f = 0 until max |df| < tol or
-// max_iter iterations.  Synchronises the stream every `batch` iterations.
+// Solve the self-consistent equations from f = 0 (the plain fixed-point map
+// with Anderson acceleration) until max |G(f) - f| < tol or max_iter maps.
+// Synchronises the stream after every map.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out,
                            cudaStream_t s);
 

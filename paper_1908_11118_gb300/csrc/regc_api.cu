@@ -108,6 +108,7 @@ void regc_free(regc_handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->stc.block) cudaFree(h->stc.block);
     delete h;
 }
 

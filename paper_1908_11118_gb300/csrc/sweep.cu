@@ -835,7 +835,9 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 WalkerStats& st = *S.stats;
                 st.tr[r.type] += 1;
                 st.ac[r.type] += accepted;
-                st.pairs += (unsigned)(r.flags >> 1);
+                // pairs that entered dE (a move that became impossible in this
+                // round, status 1, has none, whatever its evaluation counted)
+                if (status != 1) st.pairs += (unsigned)(r.flags >> 1);
                 const int ts = m / P.mps, k = m - ts * P.mps;
                 if (TRACE) {
                     regc_move_record t;

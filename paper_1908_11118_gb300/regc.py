@@ -184,6 +184,65 @@ class Regc:
         check(_lib.lib().regc_check_energy(self._h, C.byref(d)), "regc_check_energy")
         return d.value
 
+    # -- structural observables (axial density, lateral RDF; MBAR per phase)
+    def structure_init(self, n_z: int, dz: float, layers, n_r: int, dr: float, capacity: int):
+        """layers: up to four (z_lo, z_hi) windows for the lateral RDF."""
+        layers = list(layers)
+        spec = _lib.StructureSpec()
+        spec.n_z, spec.dz, spec.n_layers, spec.n_r, spec.dr = int(n_z), float(dz), len(layers), int(n_r), float(dr)
+        for l, (lo, hi) in enumerate(layers):
+            spec.layer_lo[l], spec.layer_hi[l] = float(lo), float(hi)
+        spec.capacity = int(capacity)
+        check(_lib.lib().regc_structure_init(self._h, C.byref(spec)), "regc_structure_init")
+        self._stc = (int(n_z), len(layers), int(n_r))
+
+    def structure_sample(self):
+        check(_lib.lib().regc_structure_sample(self._h), "regc_structure_sample")
+
+    def structure_count(self) -> int:
+        c = C.c_int64(0)
+        check(_lib.lib().regc_structure_count(self._h, C.byref(c)), "regc_structure_count")
+        return c.value
+
+    def structure_reset(self):
+        check(_lib.lib().regc_structure_reset(self._h), "regc_structure_reset")
+
+    def structure_get(self, first: int = 0, count=None) -> dict:
+        n_z, n_l, n_r = self._stc
+        if count is None:
+            count = self.structure_count() - first
+        out = {"state": np.zeros(count, np.int32), "N": np.zeros(count, np.int32), "E": np.zeros(count),
+               "rho": np.zeros((count, n_z), np.uint16), "pairs": np.zeros((count, n_l, n_r), np.uint32),
+               "pop": np.zeros((count, n_l), np.int32)}
+        check(_lib.lib().regc_structure_get(self._h, int(first), int(count), out["state"].ctypes.data,
+                                            out["N"].ctypes.data, out["E"].ctypes.data, out["rho"].ctypes.data,
+                                            out["pairs"].ctypes.data if n_l else None,
+                                            out["pop"].ctypes.data if n_l else None), "regc_structure_get")
+        return out
+
+    def structure_reweight(self, kT_q, mu_q, n_lo: int, n_hi: int, tol: float = 1e-10, max_iter: int = 200000):
+        """MBAR averages per phase N_B = n_lo..n_hi (regc_structure_reweight):
+        dict p [Q, P], rho [Q, P, n_z], gxy [Q, P, n_layers, n_r], f [S], iters."""
+        n_z, n_l, n_r = self._stc
+        kq = np.ascontiguousarray(kT_q, np.float64)
+        mq = np.ascontiguousarray(mu_q, np.float64)
+        Q, P = len(kq), n_hi - n_lo + 1
+        out = {"p": np.zeros((Q, P)), "rho": np.zeros((Q, P, n_z)), "gxy": np.zeros((Q, P, n_l, n_r)),
+               "f": np.zeros(self.S)}
+        it = C.c_int(0)
+        check(_lib.lib().regc_structure_reweight(self._h, Q, _p(kq, C.c_double), _p(mq, C.c_double), int(n_lo),
+                                                 int(n_hi), float(tol), int(max_iter), _p(out["p"], C.c_double),
+                                                 _p(out["rho"], C.c_double), _p(out["gxy"], C.c_double),
+                                                 _p(out["f"], C.c_double), C.byref(it)), "regc_structure_reweight")
+        out["iters"] = it.value
+        return out
+
+    def structure_timing(self) -> dict:
+        v = [C.c_double(0) for _ in range(4)]
+        check(_lib.lib().regc_structure_timing(self._h, *[C.byref(x) for x in v]), "regc_structure_timing")
+        return {"ms_mbar": v[0].value, "ms_weights": v[1].value, "ms_accumulate": v[2].value,
+                "bytes_accumulate": v[3].value}
+
     def warps_per_walker(self) -> int:
         w = C.c_int(0)
         check(_lib.lib().regc_warps_per_walker(self._h, C.byref(w)), "regc_warps_per_walker")

@@ -55,8 +55,12 @@ def assert_same(a, b):
     ha, hb = a.histograms(), b.histograms()
     for k in ha:
         assert np.array_equal(ha[k], hb[k]), k
-    for x, y in zip(a.counters(), b.counters()):
-        assert np.array_equal(x, y)
+    (ma, ea, pa), (mb, eb, pb) = a.counters(), b.counters()
+    assert np.array_equal(ma, mb) and np.array_equal(ea, eb)
+    # pairs within rc of the committed moves and the surrogate counts do not
+    # depend on the launch shape; candidates, rounds and evaluations do (the
+    # batch runs one warp per walker, a handle alone may speculate with more)
+    assert pa[0] == pb[0] and np.array_equal(pa[4:], pb[4:])
     assert a.check_energy() == 0.0
 
 

@@ -132,7 +132,7 @@ def test_mbar_solve_and_query_match_oracle():
     f_g, D_g, it_g = mbar_solve(kT, mu, 1.0, omega, N, E, H, tol=1e-11)
     np.testing.assert_allclose(f_g, f_o, atol=1e-9)
     np.testing.assert_allclose(D_g, D_o, atol=1e-9)
-    assert abs(it_g - it_o) <= 2
+    assert it_g <= it_o           # the same fixed point, reached by an accelerated iteration
     kq = np.array([0.75, 1.0, 1.2, 1.55])
     mq = np.array([-4.5, -3.3, -2.7, -2.2])
     n_o, p_o, fq_o = OM.query(kq, mq, 1.0, N, E, H, D_o, nmax)
