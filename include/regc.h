@@ -374,8 +374,9 @@ REGC_API regc_status regc_structure_get(regc_handle *h, int64_t first, int64_t c
                                         int32_t *pop);
 
 /* MBAR averages per phase N_B = n_lo .. n_hi at nq query states (kT_q, mu_q),
- * over the samples held (Eq. avegr).  Each sample is a bin of its own, (N_B,
- * E), count 1: the MBAR equations (Eq. normlizationconstant, with the reduced
+ * over the samples held (Eq. avegr).  Each distinct (N_B, E) of the samples is
+ * a bin with its count (samples with bit-identical energies, such as empty
+ * walkers, share one): the MBAR equations (Eq. normlizationconstant, with the reduced
  * potential of regc_reweight) are solved over the samples for the free
  * energies of the sampled states (f_states [S], f_0 = 0), and sample n
  * weighs W_n(q) = exp(-u_q(n) - D_n + f_q) at query q (the weights of all
@@ -387,8 +388,10 @@ REGC_API regc_status regc_structure_get(regc_handle *h, int64_t first, int64_t c
  *                                   g_n(r_k) = 2 A P_nk / (M_n (M_n - 1) pi
  *                                   ((k+1)^2 - k^2) dr^2) (0 when M_n < 2)
  * Eq. avegr as printed is the joint average, p times these; zero where p = 0.
- * FP64 on the device.  Synchronous.  Errors: REGC_EINVAL (no samples, bad
- * phase range, nq < 1). */
+ * FP64 on the device, except the weighted sums of the counts: over chunks of
+ * at most 256 samples of a phase, with the chunk's largest weight factored
+ * out, they are binary32 (relative error below 2e-5).  Synchronous.  Errors:
+ * REGC_EINVAL (no samples, bad phase range, nq < 1). */
 REGC_API regc_status regc_structure_reweight(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
                                              int n_lo, int n_hi, double tol, int max_iter, double *p,
                                              double *rho, double *gxy, double *f_states, int *iters);
@@ -429,7 +432,7 @@ REGC_API regc_status regc_mbar_query(int Q, const double *kT_q, const double *mu
  * device-wide synchronisation cudaMalloc and cudaFree may cause.
  * Arguments, outputs and results are those of regc_mbar_solve (host buffers).
  * The staged inputs and the work arrays live in one fixed scratch area of
- * about 9.3 MiB compiled into the library, which every GPU that loads the
+ * about 12.3 MiB compiled into the library, which every GPU that loads the
  * library keeps reserved until the process exits.
  *   - S > REGC_MBAR_STATIC_MAX_STATES or B > REGC_MBAR_STATIC_MAX_BINS:
  *     REGC_EINVAL, nothing is run.

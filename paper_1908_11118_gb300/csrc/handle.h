@@ -10,10 +10,11 @@ using regc::SurrogateStore;
 using regc::SweepParams;
 
 // Samples of the structural observables (structure.cu): one device block
-// holding state [cap], nb [cap], energy [cap], pop [cap][4], rho [cap][n_z],
-// pairs [cap][n_layers][n_r].
+// holding state [cap], nb [cap], energy [cap], pop [cap][4], rho
+// [cap][rho_stride] (n_z used), pairs [cap][pair_stride] (n_layers n_r used).
 struct StructureStore {
     int n_z = 0, n_layers = 0, n_r = 0;
+    int rho_stride = 0, pair_stride = 0;      // row strides: n_z and n_layers n_r rounded up to 16 bytes
     float dz = 0, dr = 0, inv_dz = 0, inv_dr = 0;
     float layer_lo[4] = {}, layer_hi[4] = {};
     long long cap = 0, count = 0;

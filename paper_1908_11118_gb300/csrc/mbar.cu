@@ -5,9 +5,11 @@
 //   D_b = ln sum_k Omega_k exp(f_k - u_k(b))        (one thread per bin)
 //   f_s = -ln sum_b H_b exp(-u_s(b) - D_b)           (one block per state)
 // with f_0 = 0 after each iteration, accelerated by Anderson mixing on the
-// host (mbar_solve_dev).  Sums are log-sum-exp in FP64 with an
-// online maximum; terms more than 50 below the running maximum are skipped
-// (their total weight is below the FP64 rounding of the sum).
+// host (mbar_solve_dev).  Sums are log-sum-exp in FP64 over the terms within
+// 50 of the largest (the others weigh less than the FP64 rounding of the sum),
+// found by a binary32 screening pass, so that with well separated states a
+// bin costs a few FP64 terms rather than one per state; the query keeps an
+// online maximum over all terms.
 // Query states reuse the D_b: the weight of bin b at state q is
 // H_b exp(-u_q(b) - D_b + f_q), giving <N> and p_N (Eq. textbook with the
 // phase indicator chi_i = [N = i]).
@@ -83,40 +85,101 @@ __device__ double block_sum(double v) {
     return r;
 }
 
-constexpr int kTile = 1024;
+__device__ double block_max(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = lane < nw ? sh[lane] : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    return r;
+}
+
+// Every sum is screened in binary32 first: the largest term of the sum
+// computed from binary32 copies (absolute error far below kMargin for terms
+// of magnitude up to 1e5), then only the terms within kSkip + kMargin of that
+// maximum are evaluated in FP64, summed by an online log-sum-exp.  The FP64
+// pipe of this GPU is narrow; with well separated states a bin or a state
+// has only a few such terms.
+constexpr float kMargin = 1.0f;
+constexpr int kDTile = 512;
+
+__global__ void en32_kernel(int B, const double* E_b, const int* N_b, float2* EN32) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) EN32[b] = make_float2((float)E_b[b], (float)N_b[b]);
+}
 
 // D_b = ln sum_k exp(lnom_k + f_k - a_k E_b - c_k N_b)
 __global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev m, int always) {
     if (!always && m.state[0]) return;
-    __shared__ double sa[kTile], sc[kTile], sg[kTile];
+    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile];
+    __shared__ float fa[kDTile], fc[kDTile], fg[kDTile];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = b < m.B;
     const double E = act ? m.E_b[b] : 0.0;
     const double N = act ? (double)m.N_b[b] : 0.0;
+    const float2 en = act ? m.EN32[b] : make_float2(0.f, 0.f);
+    const bool one_tile = m.S <= kDTile;
+    float mx32 = -INFINITY;
     Lse L{-INFINITY, 0.0};
-    for (int k0 = 0; k0 < m.S; k0 += kTile) {
-        const int nk = min(kTile, m.S - k0);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            sa[k] = m.a[k0 + k];
-            sc[k] = m.c[k0 + k];
-            sg[k] = m.lnom[k0 + k] + m.f[k0 + k];
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int k0 = 0; k0 < m.S; k0 += kDTile) {
+            const int nk = min(kDTile, m.S - k0);
+            if (pass == 0 || !one_tile) {
+                __syncthreads();
+                for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+                    const double g = m.lnom[k0 + k] + m.f[k0 + k];
+                    sa[k] = m.a[k0 + k];
+                    sc[k] = m.c[k0 + k];
+                    sg[k] = g;
+                    fa[k] = (float)sa[k];
+                    fc[k] = (float)sc[k];
+                    fg[k] = (float)g;
+                }
+                __syncthreads();
+            }
+            if (!act) continue;
+            if (pass == 0) {
+                for (int k = 0; k < nk; ++k) mx32 = fmaxf(mx32, fg[k] - fmaf(fa[k], en.x, fc[k] * en.y));
+            } else {
+                const float th = mx32 - (float)kSkip - kMargin;
+                for (int k = 0; k < nk; ++k)
+                    if (fg[k] - fmaf(fa[k], en.x, fc[k] * en.y) > th) lse_add(L, sg[k] - fma(sa[k], E, sc[k] * N));
+            }
         }
-        __syncthreads();
-        if (act)
-            for (int k = 0; k < nk; ++k) lse_add(L, sg[k] - fma(sa[k], E, sc[k] * N));
     }
-    if (act) m.D[b] = L.m + log(L.s);
+    if (act) {
+        const double D = L.m + log(L.s);
+        m.D[b] = D;
+        m.DH32[b] = (float)(D - m.lnH[b]);
+    }
 }
 
-// f_new_s = -ln sum_b exp(lnH_b - a_s E_b - c_s N_b - D_b)
-__global__ void __launch_bounds__(256) f_kernel(const __grid_constant__ MbarDev m) {
+// f_new_s = -ln sum_b exp(lnH_b - a_s E_b - c_s N_b - D_b); one block of
+// kFThreads per state.
+constexpr int kFThreads = 1024;
+__global__ void __launch_bounds__(kFThreads) f_kernel(const __grid_constant__ MbarDev m) {
     if (m.state[0]) return;
     const int s = blockIdx.x;
     const double a = m.a[s], c = m.c[s];
+    const float a32 = (float)a, c32 = (float)c;
+    float mx32 = -INFINITY;
+    for (int b = threadIdx.x; b < m.B; b += kFThreads) {
+        const float2 en = m.EN32[b];
+        mx32 = fmaxf(mx32, -fmaf(a32, en.x, c32 * en.y) - m.DH32[b]);
+    }
+    mx32 = (float)block_max((double)mx32);
+    const float th = mx32 - (float)kSkip - kMargin;
     Lse L{-INFINITY, 0.0};
-    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
-        lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+    for (int b = threadIdx.x; b < m.B; b += kFThreads) {
+        const float2 en = m.EN32[b];
+        if (-fmaf(a32, en.x, c32 * en.y) - m.DH32[b] > th)
+            lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+    }
     L = block_merge(L);
     if (threadIdx.x == 0) m.f_new[s] = -(L.m + log(L.s));
 }
@@ -287,6 +350,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     err = cudaMemsetAsync(m.f, 0, size_t(S) * sizeof(double), s);
     if (err != cudaSuccess) return err;
     const int dgrid = (m.B + 255) / 256;
+    en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32);
     std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
     std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
     std::vector<double> r_prev, g_prev;
@@ -298,7 +362,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             if (err != cudaSuccess) return err;
         }
         d_kernel<<<dgrid, 256, 0, s>>>(m, 1);
-        f_kernel<<<S, 256, 0, s>>>(m);
+        f_kernel<<<S, kFThreads, 0, s>>>(m);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -20,6 +20,8 @@ struct MbarDev {
     double* f;             // [S] current free energies (gauge f_0 = 0)
     double* f_new;         // [S]
     double* D;             // [B]
+    float2* EN32;          // [B] (E_b, N_b) in binary32, filled by the solve
+    float* DH32;           // [B] D_b - lnH_b in binary32, written with D
     double* delta;         // [1] max |f_new - f| of the last iteration
     int* state;            // [2] cleared by the solve (the kernels skip work when state[0] is set)
 };

@@ -27,8 +27,9 @@ constexpr size_t al(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kStateBytes = al(size_t(kMaxS) * sizeof(double));
 constexpr size_t kBinD = al(size_t(kMaxB) * sizeof(double));
 constexpr size_t kBinI = al(size_t(kMaxB) * sizeof(int));
-// states: kT, mu, omega, a, c, lnom, f, f_new; bins: N_b, E_b, H_b, lnH, D; delta, state
-constexpr size_t kScratchBytes = 8 * kStateBytes + kBinI + 4 * kBinD + 256 + 256;
+// states: kT, mu, omega, a, c, lnom, f, f_new; bins: N_b, E_b, H_b, lnH, D,
+// (E, N) and D - lnH in binary32; delta, state
+constexpr size_t kScratchBytes = 8 * kStateBytes + kBinI + 4 * kBinD + 256 + 256 + kBinD + kBinI;
 
 static __device__ __align__(256) unsigned char g_mbar_scratch[kScratchBytes];
 
@@ -80,6 +81,8 @@ extern "C" regc_status regc_mbar_solve_static(int S, const double* kT, const dou
     double* Dd = reinterpret_cast<double*>(bins + kBinI + 3 * kBinD);
     double* delta = reinterpret_cast<double*>(bins + kBinI + 4 * kBinD);
     int* state = reinterpret_cast<int*>(bins + kBinI + 4 * kBinD + 256);
+    float2* en32 = reinterpret_cast<float2*>(bins + kBinI + 4 * kBinD + 512);
+    float* dh32 = reinterpret_cast<float*>(bins + kBinI + 5 * kBinD + 512);
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemcpyAsync(d_kT, kT, S * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -103,6 +106,8 @@ extern "C" regc_status regc_mbar_solve_static(int S, const double* kT, const dou
     m.f = fd;
     m.f_new = f_new;
     m.D = Dd;
+    m.EN32 = en32;
+    m.DH32 = dh32;
     m.delta = delta;
     m.state = state;
     // mbar_solve_dev clears f and the convergence state before iterating, so

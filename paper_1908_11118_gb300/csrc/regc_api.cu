@@ -1154,6 +1154,8 @@ cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double
     m.f = buf.get<double>(m.S);
     m.f_new = buf.get<double>(m.S);
     m.D = buf.get<double>(m.B);
+    m.EN32 = buf.get<float2>(m.B);
+    m.DH32 = buf.get<float>(m.B);
     m.delta = buf.get<double>(1);
     m.state = buf.get<int>(2);
     if (buf.err != cudaSuccess) return buf.err;

@@ -43,6 +43,7 @@ struct SampleParams {
     float layer_lo[4], layer_hi[4];
     int n_r;
     float inv_dr;
+    int rho_stride, pair_stride;
     long long base;
     int32_t* state;
     int32_t* nb;
@@ -117,10 +118,10 @@ __global__ void __launch_bounds__(kSampleThreads) structure_sample_kernel(const 
     }
     __syncthreads();
     const long long row = P.base + w;
-    uint16_t* rr = P.rho + row * P.n_z;
-    for (int k = tid; k < P.n_z; k += kSampleThreads) rr[k] = (uint16_t)hz[k];
-    uint32_t* pr = P.pairs + row * (long long)(P.n_layers * P.n_r);
-    for (int k = tid; k < P.n_layers * P.n_r; k += kSampleThreads) pr[k] = hp[k];
+    uint16_t* rr = P.rho + row * P.rho_stride;
+    for (int k = tid; k < P.rho_stride; k += kSampleThreads) rr[k] = k < P.n_z ? (uint16_t)hz[k] : (uint16_t)0;
+    uint32_t* pr = P.pairs + row * (long long)P.pair_stride;
+    for (int k = tid; k < P.pair_stride; k += kSampleThreads) pr[k] = k < P.n_layers * P.n_r ? hp[k] : 0u;
     if (tid < 4) P.pop[row * 4 + tid] = tid < P.n_layers ? cnt[tid] : 0;
     if (tid == 0) {
         P.state[row] = P.sow[w];
@@ -136,14 +137,15 @@ __global__ void count_states_kernel(const int32_t* state, long long count, doubl
         atomicAdd(&omega[state[i]], 1.0);
 }
 
-// W[q][n] = exp(-(a_q E_n + c_q N_n) - D_n + f_q).
-__global__ void weights_kernel(const int32_t* nb, const double* energy, const double* D, long long count, int nq,
-                               const double* a_q, const double* c_q, const double* f_q, double* W) {
+// W[q][n] = exp(-(a_q E_n + c_q N_n) - D_bin(n) + f_q).
+__global__ void weights_kernel(const int32_t* nb, const double* energy, const int32_t* bin_of, const double* D,
+                               long long count, int nq, const double* a_q, const double* c_q, const double* f_q,
+                               double* W) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count * nq;
          i += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(i / count);
         const long long n = i - (long long)q * count;
-        W[i] = exp(-fma(a_q[q], energy[n], c_q[q] * (double)nb[n]) - D[n] + f_q[q]);
+        W[i] = exp(-fma(a_q[q], energy[n], c_q[q] * (double)nb[n]) - D[bin_of[n]] + f_q[q]);
     }
 }
 
@@ -152,24 +154,31 @@ constexpr int kChunk = 256;                     // samples of one phase per CTA 
 struct AccParams {
     const int32_t* order;     // sample indices grouped by phase, in sample order within a phase
     const int4* chunks;       // [n_chunks] (phase, first entry of order, samples, 0)
-    const uint16_t* rho;
-    const uint32_t* pairs;
+    const uint16_t* rho;      // [count][rho_stride]
+    const uint32_t* pairs;    // [count][pair_stride]
     const int32_t* pop;
     const double* W;          // [nq][count]
     long long count;
-    int n_z, n_layers, n_r, nq;
+    int rho_stride, pair_stride, n_r, nq;
     double area;
-    double* Jp;               // [n_chunks][nq][n_z + n_layers n_r] partial sums per chunk
+    double* Jp;               // [n_chunks][nq][rho_stride + pair_stride] partial sums per chunk
 };
 
-// Weighted column sums of one chunk of a phase's samples: the chunk's sample
-// indices, weights and layer populations are staged in shared memory, then
-// each thread (one column: a slab, or a layer's distance bin) streams its
-// column of the chunk's rows, four rows in flight, for kQB query states.
+// Weighted column sums of one chunk of a phase's samples.  The chunk's sample
+// indices, weights and layer normalisations are staged in shared memory; each
+// query state's weights are divided by their largest value in the chunk, so
+// that the products and the sum over the chunk (at most kChunk terms, all
+// non-negative) run on the binary32 pipe, relative error below kChunk 2^-24
+// (1.6e-5); the chunk's sum is scaled back in FP64.  Each thread takes two
+// adjacent columns (slabs, or a layer's distance bins; the row strides are
+// multiples of 16 bytes, so a pair never straddles the two parts) with one
+// vector load per row, eight rows in flight, for kQB query states.
 __global__ void __launch_bounds__(kAccThreads) accumulate_kernel(const __grid_constant__ AccParams A) {
-    __shared__ double ws[kChunk][kQB];
+    __shared__ double w64[kChunk][kQB];
+    __shared__ float4 w32[kChunk][kQB / 4];
+    __shared__ double scale[kQB];
     __shared__ int idx[kChunk];
-    __shared__ float cpop[kChunk][4];        // 2 A / (M (M - 1)) per layer, 0 when M < 2 (relative to 2 A)
+    __shared__ float cnorm[kChunk][4];       // 2 A / (M (M - 1)) per layer, 0 when M < 2
     const int4 ch = A.chunks[blockIdx.y];
     const int q0 = blockIdx.z * kQB;
     const int nql = min(kQB, A.nq - q0);
@@ -177,63 +186,84 @@ __global__ void __launch_bounds__(kAccThreads) accumulate_kernel(const __grid_co
         const int n = A.order[ch.y + i];
         idx[i] = n;
 #pragma unroll
-        for (int j = 0; j < kQB; ++j) ws[i][j] = j < nql ? A.W[(long long)(q0 + j) * A.count + n] : 0.0;
+        for (int j = 0; j < kQB; ++j) w64[i][j] = j < nql ? A.W[(long long)(q0 + j) * A.count + n] : 0.0;
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-            const float M = (float)A.pop[(long long)n * 4 + l];
-            cpop[i][l] = M >= 2.0f ? M * (M - 1.0f) : 0.0f;
+            const double M = (double)A.pop[(long long)n * 4 + l];
+            cnorm[i][l] = M >= 2.0 ? (float)(2.0 * A.area / (M * (M - 1.0))) : 0.0f;
         }
     }
     __syncthreads();
-    const int cols = A.n_z + A.n_layers * A.n_r;
-    const int col = blockIdx.x * kAccThreads + threadIdx.x;
-    if (col >= cols) return;
-    double acc[kQB];
+    {   // largest weight of each query state in the chunk: warp w takes states w, w + 4
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int j = warp; j < kQB; j += kAccThreads / 32) {
+            double mx = 0.0;
+            for (int i = lane; i < ch.z; i += 32) mx = fmax(mx, w64[i][j]);
 #pragma unroll
-    for (int j = 0; j < kQB; ++j) acc[j] = 0.0;
-    const int nlr = A.n_layers * A.n_r;
-    if (col < A.n_z) {
-        int i = 0;
-        for (; i + 4 <= ch.z; i += 4) {
-            double v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = (double)__ldg(&A.rho[(long long)idx[i + u] * A.n_z + col]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int j = 0; j < kQB; ++j) acc[j] = fma(ws[i + u][j], v[u], acc[j]);
-        }
-        for (; i < ch.z; ++i) {
-            const double v = (double)__ldg(&A.rho[(long long)idx[i] * A.n_z + col]);
-#pragma unroll
-            for (int j = 0; j < kQB; ++j) acc[j] = fma(ws[i][j], v, acc[j]);
-        }
-    } else {
-        const int c = col - A.n_z, l = c / A.n_r;
-        const double two_a = 2.0 * A.area;
-        int i = 0;
-        for (; i + 4 <= ch.z; i += 4) {
-            double v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double mm = (double)cpop[i + u][l];
-                const double pr = (double)__ldg(&A.pairs[(long long)idx[i + u] * nlr + c]);
-                v[u] = mm > 0.0 ? pr * two_a / mm : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int j = 0; j < kQB; ++j) acc[j] = fma(ws[i + u][j], v[u], acc[j]);
-        }
-        for (; i < ch.z; ++i) {
-            const double mm = (double)cpop[i][l];
-            const double pr = (double)__ldg(&A.pairs[(long long)idx[i] * nlr + c]);
-            const double v = mm > 0.0 ? pr * two_a / mm : 0.0;
-#pragma unroll
-            for (int j = 0; j < kQB; ++j) acc[j] = fma(ws[i][j], v, acc[j]);
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) scale[j] = mx;
         }
     }
-    for (int j = 0; j < nql; ++j) A.Jp[((long long)blockIdx.y * A.nq + q0 + j) * cols + col] = acc[j];
+    __syncthreads();
+    for (int t = threadIdx.x; t < ch.z * kQB; t += kAccThreads) {
+        const int i = t / kQB, j = t - i * kQB;
+        reinterpret_cast<float*>(&w32[i][0])[j] = scale[j] > 0.0 ? (float)(w64[i][j] / scale[j]) : 0.0f;
+    }
+    __syncthreads();
+    const int cols = A.rho_stride + A.pair_stride;
+    const int col = 2 * (blockIdx.x * kAccThreads + threadIdx.x);
+    if (col >= cols) return;
+    float acc0[kQB], acc1[kQB];
+#pragma unroll
+    for (int j = 0; j < kQB; ++j) acc0[j] = acc1[j] = 0.0f;
+    auto add = [&](int i, float v0, float v1) {
+        const float4 wa = w32[i][0], wb = w32[i][1];
+        const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int j = 0; j < kQB; ++j) {
+            acc0[j] = fmaf(w[j], v0, acc0[j]);
+            acc1[j] = fmaf(w[j], v1, acc1[j]);
+        }
+    };
+    constexpr int U = 8;
+    if (col < A.rho_stride) {
+        const unsigned* base = reinterpret_cast<const unsigned*>(A.rho) + col / 2;
+        const long long rs = A.rho_stride / 2;
+        int i = 0;
+        for (; i + U <= ch.z; i += U) {
+            unsigned v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldg(base + (long long)idx[i + u] * rs);
+#pragma unroll
+            for (int u = 0; u < U; ++u) add(i + u, (float)(v[u] & 0xffffu), (float)(v[u] >> 16));
+        }
+        for (; i < ch.z; ++i) {
+            const unsigned v = __ldg(base + (long long)idx[i] * rs);
+            add(i, (float)(v & 0xffffu), (float)(v >> 16));
+        }
+    } else {
+        const int c = col - A.rho_stride;
+        const int l0 = min(c / A.n_r, 3), l1 = min((c + 1) / A.n_r, 3);
+        const uint2* base = reinterpret_cast<const uint2*>(A.pairs + c);
+        const long long rs = A.pair_stride / 2;
+        int i = 0;
+        for (; i + U <= ch.z; i += U) {
+            uint2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldg(base + (long long)idx[i + u] * rs);
+#pragma unroll
+            for (int u = 0; u < U; ++u) add(i + u, (float)v[u].x * cnorm[i + u][l0], (float)v[u].y * cnorm[i + u][l1]);
+        }
+        for (; i < ch.z; ++i) {
+            const uint2 v = __ldg(base + (long long)idx[i] * rs);
+            add(i, (float)v.x * cnorm[i][l0], (float)v.y * cnorm[i][l1]);
+        }
+    }
+    double* out = A.Jp + ((long long)blockIdx.y * A.nq + q0) * cols + col;
+    for (int j = 0; j < nql; ++j) {
+        out[(long long)j * cols] = (double)acc0[j] * scale[j];
+        out[(long long)j * cols + 1] = (double)acc1[j] * scale[j];
+    }
 }
 
 // J[q][ph][col] = sum of the phase's chunk partials, in chunk order.
@@ -278,7 +308,8 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
     const size_t cap = (size_t)s.capacity;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_state = up(cap * 4), b_nb = up(cap * 4), b_e = up(cap * 8), b_pop = up(cap * 16);
-    const size_t b_rho = up(cap * s.n_z * 2), b_pairs = up(cap * (size_t)s.n_layers * s.n_r * 4);
+    const int rho_stride = (s.n_z + 7) & ~7, pair_stride = (s.n_layers * s.n_r + 3) & ~3;
+    const size_t b_rho = up(cap * rho_stride * 2), b_pairs = up(cap * (size_t)pair_stride * 4);
     void* block = nullptr;
     e = cudaMalloc(&block, b_state + b_nb + b_e + b_pop + b_rho + b_pairs);
     if (e != cudaSuccess) {
@@ -294,6 +325,8 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
     st.rho = reinterpret_cast<uint16_t*>(c + b_state + b_nb + b_e + b_pop);
     st.pairs = reinterpret_cast<uint32_t*>(c + b_state + b_nb + b_e + b_pop + b_rho);
     st.n_z = s.n_z;
+    st.rho_stride = rho_stride;
+    st.pair_stride = pair_stride;
     st.n_layers = s.n_layers;
     st.n_r = s.n_r;
     st.dz = s.dz;
@@ -337,6 +370,8 @@ regc_status regc_structure_sample(regc_handle* h) {
     }
     P.n_r = st.n_r;
     P.inv_dr = st.inv_dr;
+    P.rho_stride = st.rho_stride;
+    P.pair_stride = st.pair_stride;
     P.base = st.count;
     P.state = st.state;
     P.nb = st.nb;
@@ -388,8 +423,12 @@ regc_status regc_structure_get(regc_handle* h, int64_t first, int64_t count, int
     get(state, st.state + first, (size_t)count * 4);
     get(n, st.nb + first, (size_t)count * 4);
     get(energy, st.energy + first, (size_t)count * 8);
-    get(rho, st.rho + first * st.n_z, (size_t)count * st.n_z * 2);
-    if (nlr) get(pairs, st.pairs + first * nlr, (size_t)count * nlr * 4);
+    if (rho && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(rho, st.n_z * 2, st.rho + first * st.rho_stride, st.rho_stride * 2, st.n_z * 2, count,
+                              cudaMemcpyDeviceToHost, h->stream);
+    if (nlr && pairs && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(pairs, nlr * 4, st.pairs + first * st.pair_stride, st.pair_stride * 4, nlr * 4, count,
+                              cudaMemcpyDeviceToHost, h->stream);
     if (pop) {
         std::vector<int32_t> p4((size_t)count * 4);
         get(p4.data(), st.pop + first * 4, (size_t)count * 16);
@@ -415,14 +454,43 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     const int S = h->S;
     const int n_top = std::min(n_hi, h->nmax);
     const int P = n_hi - n_lo + 1;
-    const int cols = st.n_z + st.n_layers * st.n_r;
+    const int cols = st.rho_stride + st.pair_stride;       // padded columns of the sums
     cudaStream_t s = h->stream;
 
     // group the samples by phase (stable: sample order within a phase)
     std::vector<int32_t> nb(count);
+    std::vector<double> en(count);
     cudaError_t e = cudaMemcpyAsync(nb.data(), st.nb, count * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(en.data(), st.energy, count * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(h, e);
+    // samples with the same (N_B, E) -- bit-identical energies, as every empty
+    // walker has -- have the same weight at every state: they are pooled into
+    // one MBAR bin with their count, exactly as the equations allow
+    std::vector<int32_t> bin_of(count);
+    std::vector<int32_t> bN;
+    std::vector<double> bE, blnH;
+    {
+        std::vector<int32_t> ix(count);
+        for (long long i = 0; i < count; ++i) ix[i] = (int32_t)i;
+        std::sort(ix.begin(), ix.end(), [&](int32_t x, int32_t y) {
+            return nb[x] != nb[y] ? nb[x] < nb[y] : (en[x] != en[y] ? en[x] < en[y] : x < y);
+        });
+        long long run = 0;
+        for (long long i = 0; i < count; ++i) {
+            const int32_t k = ix[i];
+            if (i == 0 || nb[k] != bN.back() || en[k] != bE.back()) {
+                if (i > 0) blnH.push_back(log((double)run));
+                bN.push_back(nb[k]);
+                bE.push_back(en[k]);
+                run = 0;
+            }
+            bin_of[k] = (int32_t)(bN.size() - 1);
+            ++run;
+        }
+        blnH.push_back(log((double)run));
+    }
+    const long long B = (long long)bN.size();
     std::vector<long long> offset(P + 1, 0);
     for (long long i = 0; i < count; ++i)
         if (nb[i] >= n_lo && nb[i] <= n_hi) offset[nb[i] - n_lo + 1] += 1;
@@ -456,7 +524,9 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off += up(bytes); return o; };
     const size_t o_a = take(S * 8), o_c = take(S * 8), o_lnom = take(S * 8), o_om = take(S * 8), o_f = take(S * 8),
-                 o_fn = take(S * 8), o_del = take(8), o_stt = take(8), o_lnH = take(count * 8), o_D = take(count * 8),
+                 o_fn = take(S * 8), o_del = take(8), o_stt = take(8), o_lnH = take(B * 8), o_D = take(B * 8),
+                 o_en = take(B * 8), o_dh = take(B * 4), o_bN = take(B * 4), o_bE = take(B * 8),
+                 o_map = take(count * 4),
                  o_aq = take(nq * 8), o_cq = take(nq * 8), o_fq = take(nq * 8), o_pN = take(nq * nh * 8),
                  o_W = take((size_t)nq * count * 8), o_ord = take(order.size() * 4),
                  o_ch = take(chunks.size() * sizeof(int4)), o_fc = take((P + 1) * 4),
@@ -473,7 +543,12 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     double* d_del = reinterpret_cast<double*>(d + o_del);
     int* d_stt = reinterpret_cast<int*>(d + o_stt);
     double* d_lnH = reinterpret_cast<double*>(d + o_lnH);
+    int32_t* d_bN = reinterpret_cast<int32_t*>(d + o_bN);
+    double* d_bE = reinterpret_cast<double*>(d + o_bE);
+    int32_t* d_map = reinterpret_cast<int32_t*>(d + o_map);
     double* d_D = reinterpret_cast<double*>(d + o_D);
+    float2* d_en = reinterpret_cast<float2*>(d + o_en);
+    float* d_dh = reinterpret_cast<float*>(d + o_dh);
     double* d_aq = reinterpret_cast<double*>(d + o_aq);
     double* d_cq = reinterpret_cast<double*>(d + o_cq);
     double* d_fq = reinterpret_cast<double*>(d + o_fq);
@@ -490,7 +565,10 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_om, 0, S * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_lnH, 0, count * 8, s);           // every sample: count 1
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_lnH, blnH.data(), B * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_bN, bN.data(), B * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_bE, bE.data(), B * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_map, bin_of.data(), count * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         count_states_kernel<<<std::max(1, (int)std::min<long long>((count + 255) / 256, 4096)), 256, 0, s>>>(
             st.state, count, d_om);
@@ -498,7 +576,7 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     }
     if (e == cudaSuccess) e = mbar_prep_states(S, h->d_kT_state, h->d_mu_state, h->lambda0, d_om, nullptr, d_a, d_c,
                                                d_lnom, s);
-    MbarDev m{S, (int)count, d_a, d_c, d_lnom, st.nb, st.energy, d_lnH, d_f, d_fn, d_D, d_del, d_stt};
+    MbarDev m{S, (int)B, d_a, d_c, d_lnom, d_bN, d_bE, d_lnH, d_f, d_fn, d_D, d_en, d_dh, d_del, d_stt};
     if (count > 0x7fffffffLL) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = mbar_solve_dev(m, tol, max_iter, &it, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_aq, a_q.data(), nq * 8, cudaMemcpyHostToDevice, s);
@@ -508,7 +586,7 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     if (e == cudaSuccess) {
         const long long tot = (long long)nq * count;
         weights_kernel<<<(int)std::min<long long>((tot + 255) / 256, 65536), 256, 0, s>>>(
-            st.nb, st.energy, d_D, count, nq, d_aq, d_cq, d_fq, d_W);
+            st.nb, st.energy, d_map, d_D, count, nq, d_aq, d_cq, d_fq, d_W);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ord, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s);
@@ -517,9 +595,9 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_fc, first_chunk.data(), (P + 1) * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
     if (e == cudaSuccess) {
-        AccParams A{d_ord, d_ch, st.rho, st.pairs, st.pop, d_W, count, st.n_z, st.n_layers, st.n_r, nq,
-                    (double)h->Lx * (double)h->Ly, d_Jp};
-        const dim3 grid((cols + kAccThreads - 1) / kAccThreads, n_chunks, (nq + kQB - 1) / kQB);
+        AccParams A{d_ord, d_ch, st.rho, st.pairs, st.pop, d_W, count, st.rho_stride, st.pair_stride,
+                    std::max(st.n_r, 1), nq, (double)h->Lx * (double)h->Ly, d_Jp};
+        const dim3 grid((cols / 2 + kAccThreads - 1) / kAccThreads, n_chunks, (nq + kQB - 1) / kQB);
         accumulate_kernel<<<grid, kAccThreads, 0, s>>>(A);
         e = cudaGetLastError();
     }
@@ -544,9 +622,10 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
         // every row of a phase in range once per pass of kQB query states, with
         // its population and index, its weights, and the sums written (the
         // per-chunk partial sums are the implementation's, not counted)
-        const double row = (double)st.n_z * 2 + (double)st.n_layers * st.n_r * 4 + 16 + 4;
+        const double row = (double)st.rho_stride * 2 + (double)st.pair_stride * 4 + 16 + 4;
         const int passes = (nq + kQB - 1) / kQB;
-        sm.last_bytes = (double)offset[P] * (row * passes + 8.0 * nq) + (double)nq * P * cols * 8;
+        sm.last_bytes = (double)offset[P] * (row * passes + 8.0 * nq) +
+                        (double)nq * P * (st.n_z + st.n_layers * st.n_r) * 8;
     }
     for (int i = 0; i < 4; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
@@ -570,7 +649,7 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
                     for (int k = 0; k < st.n_r; ++k) {
                         const double shell = kPi * dr * dr * ((k + 1.0) * (k + 1.0) - (double)k * k);
                         gxy[(((size_t)q * P + i) * st.n_layers + l) * st.n_r + k] =
-                            pi_q > 0.0 ? Jr[st.n_z + l * st.n_r + k] / (pi_q * shell) : 0.0;
+                            pi_q > 0.0 ? Jr[st.rho_stride + l * st.n_r + k] / (pi_q * shell) : 0.0;
                     }
         }
     return handle_sync_check(h);

@@ -101,7 +101,7 @@ def compare_reweight(g, p, osmp, spec, kq, mq, n_lo, n_hi):
     every reduced potential differs by at most d = max beta |E_gpu - E_oracle|;
     then each D_n and f_s moves by at most 2 d, each weight by a factor within
     exp(+-4 d), and p, rho and g_xy (ratios of positive sums) by at most 8 d
-    relative."""
+    relative, plus 2e-5 for the binary32 sums over chunks of 256 samples."""
     rg = g.structure_reweight(kq, mq, n_lo, n_hi, tol=1e-11, max_iter=100000)
     ro = ST.reweight(p, osmp, spec, kq, mq, n_lo, n_hi, tol=1e-11)
     e_gpu = g.structure_get()["E"]
@@ -109,7 +109,7 @@ def compare_reweight(g, p, osmp, spec, kq, mq, n_lo, n_hi):
     d = beta * float(np.max(np.abs(e_gpu - osmp["E"])))
     print("max |beta dE| over the samples: %.3g" % d)
     np.testing.assert_allclose(rg["f"], ro["f"], rtol=0, atol=2 * d + 1e-9)
-    rel = 8 * d + 1e-9
+    rel = 8 * d + 2e-5                   # + the binary32 chunk sums of the accumulation
     # phases of probability below 1e-250 are carried by subnormal weights,
     # whose precision is lost on both sides: only their smallness is compared
     big = ro["p"] > 1e-250
@@ -142,7 +142,8 @@ def test_paper_run_in_lockstep_samples():
     A = p.Lx * p.Ly
     integral = rg["rho"].sum(axis=2) * A * float(np.float32(spec["dz"]))
     nb = np.broadcast_to(np.arange(p.nmax + 1), integral.shape)
-    assert np.all(integral[ok] <= nb[ok] * (1 + 1e-9))          # a particle on the top wall is past slab 399
+    # a particle on the top wall is past slab 399; 2e-5: the binary32 chunk sums
+    assert np.all(integral[ok] <= nb[ok] * (1 + 2e-5))
     np.testing.assert_allclose(integral[ok], nb[ok], rtol=1e-3)
 
 
@@ -182,7 +183,7 @@ def test_small_grid_lockstep_reweight_at_unsampled_states():
     ok = rg["p"] > 1e-12
     integral = rg["rho"].sum(axis=2) * A * float(np.float32(spec["dz"]))
     nb = np.broadcast_to(np.arange(p.nmax + 1), integral.shape)
-    np.testing.assert_allclose(integral[ok], nb[ok], rtol=1e-9)
+    np.testing.assert_allclose(integral[ok], nb[ok], rtol=2e-5)      # the binary32 chunk sums
 
 
 def test_store_limits_and_arguments():
