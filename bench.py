@@ -546,6 +546,18 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     rw = g.structure_reweight(kq, mq, 0, p.nmax, tol=1e-9, max_iter=200000)
     rw_s = time.perf_counter() - t0
     tm = g.structure_timing()
+    # MBAR@REGC against aiAT@REGC (Sec. III.A.1) on a (T, mu) grid: the most
+    # probable N_B against the composition of lowest formation free energy
+    Tg, mg = np.meshgrid(200.0 + 50.0 * np.arange(10), -2.4 + 0.05 * np.arange(31), indexing="ij")
+    rg = g.structure_reweight(kB * Tg.ravel(), mg.ravel(), 0, p.nmax, tol=1e-9, max_iter=200000)
+    mbar_phase = np.argmax(rg["p"], axis=1)
+    _, _, ai_phase = g.aiat(mg.ravel())
+    low = ai_phase <= 36                      # up to the first monolayer (18 per A18 cell)
+    agree = {"all": float(np.mean(mbar_phase == ai_phase)),
+             "aiat_nb_per_a18_le_18": float(np.mean((mbar_phase == ai_phase)[low])) if low.any() else None,
+             "aiat_nb_per_a18_gt_18": float(np.mean((mbar_phase == ai_phase)[~low])) if (~low).any() else None,
+             "mbar_minus_aiat_nb_per_a18_mean": float(np.mean(mbar_phase - ai_phase) / 2.0),
+             "grid": "10 T (200-650 K) x 31 mu (-2.4..-0.9 eV, 0.05 eV)"}
     ach = tm["bytes_accumulate"] / (tm["ms_accumulate"] / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     phases = []
@@ -587,6 +599,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
             "reweight_s": rw_s, "mbar_iterations": rw["iters"], "ms_mbar": tm["ms_mbar"],
             "ms_weights": tm["ms_weights"], "ms_accumulate": tm["ms_accumulate"],
             "most_probable_phase": phases,
+            "mbar_vs_aiat": agree,
             "roofline": {"bound": "hbm", "kernel": "accumulate_kernel", "achieved": ach, "peak": peak,
                          "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src,
                          "work": "%.4g algorithmic bytes per launch (%d samples x %d query states)"

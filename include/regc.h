@@ -362,7 +362,8 @@ REGC_API regc_status regc_structure_sample(regc_handle *h);
 /* Number of samples held. */
 REGC_API regc_status regc_structure_count(regc_handle *h, int64_t *n_samples);
 
-/* Drop every sample (the store stays allocated). */
+/* Drop every sample and the lowest-energy configurations (the store stays
+ * allocated). */
 REGC_API regc_status regc_structure_reset(regc_handle *h);
 
 /* Copy samples first .. first + count - 1 to host buffers (any may be NULL):
@@ -395,6 +396,25 @@ REGC_API regc_status regc_structure_get(regc_handle *h, int64_t first, int64_t c
 REGC_API regc_status regc_structure_reweight(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
                                              int n_lo, int n_hi, double tol, int max_iter, double *p,
                                              double *rho, double *gxy, double *f_states, int *iters);
+
+/* aiAT@REGC (Sec. III.A.1, Eq. aiTherm) over the samples of the structure
+ * store (since its last reset): per composition N_B the lowest sampled energy
+ * e_min [nmax+1] (NaN where N_B was never sampled; samples with |E| beyond
+ * 65536 energy units are not tracked), and at nq chemical potentials mu_q the
+ * formation free energy with every F approximated by that energy and F of
+ * the pristine slab taken as 0 (the frozen slab's own energy is not part of
+ * E): dG [nq][nmax+1] = e_min[n] - n mu_q (+inf where unsampled), and the
+ * stable composition phase [nq] (lowest dG; ties: smaller n).  The
+ * temperature enters only through mu(T, p).  Any output may be NULL.
+ * Synchronous.  Errors: REGC_EINVAL (no store, mu not finite). */
+REGC_API regc_status regc_aiat(regc_handle *h, int nq, const double *mu_q, double *e_min, double *dG,
+                               int32_t *phase);
+
+/* The configuration of a lowest-energy sample with N_B = n_b (among equal
+ * energies, the one of the lowest walker index): xyz [n][3] (host, room for
+ * nmax rows), *n its particle count (cluster atoms included).  Synchronous.
+ * Errors: REGC_EINVAL (no store, n_b out of range or never sampled). */
+REGC_API regc_status regc_aiat_config(regc_handle *h, int n_b, float *xyz, int32_t *n);
 
 /* Device time of the last regc_structure_reweight (milliseconds, any pointer
  * may be NULL): the MBAR solve and query over the samples, the sample weights,

@@ -26,6 +26,11 @@ struct StructureStore {
     int32_t* pop = nullptr;
     uint16_t* rho = nullptr;
     uint32_t* pairs = nullptr;
+    // aiAT: per N_B the lowest sampled energy packed with the walker index
+    // (E in 2^-30 units << 16 | walker), and that sample's configuration
+    long long* best_key = nullptr;            // [nmax + 1]
+    float* best_xyz = nullptr;                // [nmax + 1][nmax][3]
+    int32_t* best_n = nullptr;                // [nmax + 1] particles of the configuration
     // the last reweighting: device milliseconds of the MBAR solve and query,
     // the weights and the accumulation, and the accumulation's algorithmic bytes
     double last_ms[3] = {0, 0, 0};

@@ -29,6 +29,11 @@ constexpr int kSampleThreads = 256;
 constexpr int kAccThreads = 128;
 constexpr int kQB = 8;                          // query states per pass of the accumulation
 constexpr double kPi = 3.14159265358979323846;
+// aiAT keys: energy (2^-30 units) << 16 | walker; energies beyond +-2^46
+// units (65536 energy units) are not tracked.  An empty slot holds the byte
+// pattern 0x7f.. (larger than every key).
+constexpr long long kKeyEmpty = 0x7f7f7f7f7f7f7f7fLL;
+constexpr long long kKeyEnergyLimit = 1LL << 46;
 
 struct SampleParams {
     const float4* pos;
@@ -51,6 +56,7 @@ struct SampleParams {
     int32_t* pop;
     uint16_t* rho;
     uint32_t* pairs;
+    long long* best_key;
 };
 
 size_t sample_smem(int nmax, int n_z, int n_layers, int n_r) {
@@ -124,10 +130,34 @@ __global__ void __launch_bounds__(kSampleThreads) structure_sample_kernel(const 
     for (int k = tid; k < P.pair_stride; k += kSampleThreads) pr[k] = k < P.n_layers * P.n_r ? hp[k] : 0u;
     if (tid < 4) P.pop[row * 4 + tid] = tid < P.n_layers ? cnt[tid] : 0;
     if (tid == 0) {
+        const long long E = P.efix[w];
         P.state[row] = P.sow[w];
         P.nb[row] = m;
-        P.energy[row] = (double)P.efix[w] * kFixUnit;
+        P.energy[row] = (double)E * kFixUnit;
+        if (E > -kKeyEnergyLimit && E < kKeyEnergyLimit)
+            atomicMin(&P.best_key[m], (long long)(((unsigned long long)E << 16) | (unsigned long long)w));
     }
+}
+
+// The walker whose key is the lowest of its N_B copies its configuration
+// (keys are unique: one walker at most matches).
+__global__ void best_config_kernel(const float4* pos, const int* n, const long long* efix, int nmax, int n_cluster,
+                                   const long long* best_key, float* best_xyz, int32_t* best_n) {
+    const int w = blockIdx.x;
+    const int N = n[w], m = max(0, N - n_cluster);
+    const long long E = efix[w];
+    if (!(E > -kKeyEnergyLimit && E < kKeyEnergyLimit)) return;
+    const long long key = (long long)(((unsigned long long)E << 16) | (unsigned long long)w);
+    if (best_key[m] != key) return;
+    const float4* gp = pos + (size_t)w * nmax;
+    float* out = best_xyz + (size_t)m * nmax * 3;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const float4 q = gp[j];
+        out[3 * j] = q.x;
+        out[3 * j + 1] = q.y;
+        out[3 * j + 2] = q.z;
+    }
+    if (threadIdx.x == 0) best_n[m] = N;
 }
 
 // omega[s] = number of samples of state s (exact in double).
@@ -310,8 +340,10 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
     const size_t b_state = up(cap * 4), b_nb = up(cap * 4), b_e = up(cap * 8), b_pop = up(cap * 16);
     const int rho_stride = (s.n_z + 7) & ~7, pair_stride = (s.n_layers * s.n_r + 3) & ~3;
     const size_t b_rho = up(cap * rho_stride * 2), b_pairs = up(cap * (size_t)pair_stride * 4);
+    const size_t nh = (size_t)h->nmax + 1;
+    const size_t b_key = up(nh * 8), b_bn = up(nh * 4), b_bx = up(nh * (size_t)h->nmax * 12);
     void* block = nullptr;
-    e = cudaMalloc(&block, b_state + b_nb + b_e + b_pop + b_rho + b_pairs);
+    e = cudaMalloc(&block, b_state + b_nb + b_e + b_pop + b_rho + b_pairs + b_key + b_bn + b_bx);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return REGC_ENOMEM;
@@ -324,6 +356,13 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
     st.pop = reinterpret_cast<int32_t*>(c + b_state + b_nb + b_e);
     st.rho = reinterpret_cast<uint16_t*>(c + b_state + b_nb + b_e + b_pop);
     st.pairs = reinterpret_cast<uint32_t*>(c + b_state + b_nb + b_e + b_pop + b_rho);
+    char* c2 = c + b_state + b_nb + b_e + b_pop + b_rho + b_pairs;
+    st.best_key = reinterpret_cast<long long*>(c2);
+    st.best_n = reinterpret_cast<int32_t*>(c2 + b_key);
+    st.best_xyz = reinterpret_cast<float*>(c2 + b_key + b_bn);
+    e = cudaMemsetAsync(st.best_key, 0x7f, nh * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.best_n, 0, nh * 4, h->stream);
+    if (e != cudaSuccess) return fail(h, e);
     st.n_z = s.n_z;
     st.rho_stride = rho_stride;
     st.pair_stride = pair_stride;
@@ -379,8 +418,14 @@ regc_status regc_structure_sample(regc_handle* h) {
     P.pop = st.pop;
     P.rho = st.rho;
     P.pairs = st.pairs;
+    P.best_key = st.best_key;
     structure_sample_kernel<<<h->S, kSampleThreads, st.smem, h->stream>>>(P);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        best_config_kernel<<<h->S, 128, 0, h->stream>>>(h->P.pos, h->P.n, h->P.efix, h->nmax, h->P.n_cluster,
+                                                         st.best_key, st.best_xyz, st.best_n);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return fail(h, e);
     st.count += h->S;
     return REGC_OK;
@@ -404,7 +449,68 @@ regc_status regc_structure_count(regc_handle* h, int64_t* n_samples) {
 
 regc_status regc_structure_reset(regc_handle* h) {
     if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
     h->stc.count = 0;
+    if (h->stc.block) {
+        const cudaError_t e = cudaMemsetAsync(h->stc.best_key, 0x7f, ((size_t)h->nmax + 1) * 8, h->stream);
+        if (e != cudaSuccess) return fail(h, e);
+    }
+    return REGC_OK;
+}
+
+regc_status regc_aiat(regc_handle* h, int nq, const double* mu_q, double* e_min, double* dG, int32_t* phase) {
+    if (!h || nq < 0 || (nq > 0 && !mu_q)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const StructureStore& st = h->stc;
+    if (!st.block) return REGC_EINVAL;
+    for (int q = 0; q < nq; ++q)
+        if (!std::isfinite(mu_q[q])) return REGC_EINVAL;
+    const int nh = h->nmax + 1;
+    std::vector<long long> key(nh);
+    cudaError_t e = cudaMemcpyAsync(key.data(), st.best_key, nh * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, e);
+    std::vector<double> em(nh);
+    for (int n = 0; n < nh; ++n)
+        em[n] = key[n] == kKeyEmpty ? NAN : (double)(key[n] >> 16) * kFixUnit;   // arithmetic shift: floor
+    if (e_min) std::copy(em.begin(), em.end(), e_min);
+    // Eq. aiTherm with F ~ the lowest sampled energy and F of the pristine
+    // slab 0 (the frozen slab's own energy is not part of E)
+    for (int q = 0; q < nq; ++q) {
+        int best = -1;
+        double bv = INFINITY;
+        for (int n = 0; n < nh; ++n) {
+            const double v = std::isnan(em[n]) ? INFINITY : em[n] - (double)n * mu_q[q];
+            if (dG) dG[(size_t)q * nh + n] = v;
+            if (v < bv) {
+                bv = v;
+                best = n;
+            }
+        }
+        if (phase) phase[q] = best;
+    }
+    return REGC_OK;
+}
+
+regc_status regc_aiat_config(regc_handle* h, int n_b, float* xyz, int32_t* n) {
+    if (!h || !xyz || !n) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const StructureStore& st = h->stc;
+    if (!st.block || n_b < 0 || n_b > h->nmax) return REGC_EINVAL;
+    long long key = 0;
+    int32_t cnt = 0;
+    cudaError_t e = cudaMemcpyAsync(&key, st.best_key + n_b, 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, st.best_n + n_b, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, e);
+    if (key == kKeyEmpty) return REGC_EINVAL;
+    *n = cnt;
+    if (cnt > 0) {
+        e = cudaMemcpyAsync(xyz, st.best_xyz + (size_t)n_b * h->nmax * 3, (size_t)cnt * 12, cudaMemcpyDeviceToHost,
+                            h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return fail(h, e);
+    }
     return REGC_OK;
 }
 

@@ -237,6 +237,23 @@ class Regc:
         out["iters"] = it.value
         return out
 
+    def aiat(self, mu_q):
+        """aiAT@REGC (regc_aiat): (e_min [nmax+1], dG [Q, nmax+1], phase [Q])."""
+        mq = np.ascontiguousarray(np.atleast_1d(mu_q), np.float64)
+        e_min = np.zeros(self.nmax + 1)
+        dG = np.zeros((len(mq), self.nmax + 1))
+        ph = np.zeros(len(mq), np.int32)
+        check(_lib.lib().regc_aiat(self._h, len(mq), _p(mq, C.c_double), _p(e_min, C.c_double), _p(dG, C.c_double),
+                                   ph.ctypes.data), "regc_aiat")
+        return e_min, dG, ph
+
+    def aiat_config(self, n_b: int) -> np.ndarray:
+        """The lowest-energy sampled configuration with N_B = n_b: [n, 3]."""
+        xyz = np.zeros((self.nmax, 3), np.float32)
+        n = C.c_int32(0)
+        check(_lib.lib().regc_aiat_config(self._h, int(n_b), _p(xyz, C.c_float), C.byref(n)), "regc_aiat_config")
+        return xyz[:n.value].copy()
+
     def structure_timing(self) -> dict:
         v = [C.c_double(0) for _ in range(4)]
         check(_lib.lib().regc_structure_timing(self._h, *[C.byref(x) for x in v]), "regc_structure_timing")

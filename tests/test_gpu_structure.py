@@ -11,6 +11,9 @@ averages per phase) against the FP64 oracle.
   sampled and unsampled states within FP64 tolerance of the oracle's.
 * Properties of the reweighted averages at any size: p sums to 1 over the
   phases, rho integrates to N_B when the slabs cover the zone.
+* aiAT@REGC (Eq. aiTherm): the lowest sampled energy per composition and the
+  stable composition per chemical potential against the oracle's, and the
+  configuration kept for a composition.
 * Store limits and argument checks.
 """
 import math
@@ -19,6 +22,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import aiat as AI
 from oracle import oracle as O
 from oracle import structure as ST
 from paper_1908_11118_gb300 import Regc
@@ -211,3 +215,48 @@ def test_store_limits_and_arguments():
     assert g.structure_count() == 0
     g.structure_sample()
     assert g.structure_count() == p.S
+
+
+def test_aiat_matches_oracle():
+    """aiAT@REGC (Eq. aiTherm) over the lock-step samples of the LJ A18
+    narrow grid: the lowest energy per composition equals the oracle's within
+    the energy tolerance, the stable composition agrees wherever the two
+    lowest dG are further apart than that tolerance, and the configuration
+    kept for a composition has that composition and that energy."""
+    base = W.lj_a18_slab(nmax=128, seed=13)
+    p = base.replace(kT=W.K_B_EV * np.array([400.0, 450.0, 500.0, 550.0]), mu=np.array([-1.6, -1.5, -1.4, -1.3]))
+    rng = np.random.default_rng(5)
+    pos, n = W.lj_a18_initial(p, rng.integers(40, 100, p.S), seed=6)
+    spec = spec_of(p)
+    g, o, osmp = run_lockstep_with_samples(p, pos, n, blocks=10, steps=40, x0=0.9, n_c=10, spec=spec)
+    if osmp is None:
+        pytest.skip("the chains parted at a near tie before the samples were complete")
+    mu_q = np.linspace(-2.4, -0.9, 31)
+    e_g, dG_g, ph_g = g.aiat(mu_q)
+    e_o, first = AI.lowest_energy(osmp["N"], osmp["E"], p.nmax)
+    dG_o, ph_o = AI.formation_free_energy(e_o, mu_q)
+    assert np.array_equal(np.isnan(e_g), np.isnan(e_o))
+    seen = ~np.isnan(e_o)
+    tol = 1e-4 * np.maximum(1.0, np.abs(e_o[seen]))
+    assert np.all(np.abs(e_g[seen] - e_o[seen]) <= tol)
+    for q in range(len(mu_q)):
+        srt = np.sort(dG_o[q][np.isfinite(dG_o[q])])
+        if len(srt) > 1 and srt[1] - srt[0] > 2e-4 * max(1.0, abs(srt[0])):
+            assert ph_g[q] == ph_o[q], (mu_q[q], ph_g[q], ph_o[q])
+    # the kept configurations: composition and energy
+    for nb in np.nonzero(seen)[0][:: max(1, int(seen.sum()) // 6)]:
+        xyz = g.aiat_config(int(nb))
+        assert len(xyz) == nb
+        h = Regc(p)
+        one = np.zeros((p.S, p.nmax, 3), np.float32)
+        one[0, :nb] = xyz
+        cnt = np.zeros(p.S, np.int32)
+        cnt[0] = nb
+        h.set_walkers(one, cnt)
+        assert h.get_walkers()[2][0] == e_g[nb]                # the exact fixed-point energy
+        h.close()
+    g.structure_reset()
+    e_r, _, _ = g.aiat([0.0])
+    assert np.all(np.isnan(e_r))
+    with pytest.raises(Exception):
+        g.aiat_config(int(np.nonzero(seen)[0][0]))
