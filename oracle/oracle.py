@@ -287,6 +287,15 @@ class Oracle:
         self.e += n_ex
         return tr, n_ex
 
+    def cycle_md(self, n_steps: int, x0: float, md_steps: int, dt: float, tau: float):
+        """REGCMD: each step one REGC cycle step without canonical MC moves,
+        then one MD segment.  Returns the replica-exchange steps."""
+        n_ex = 0
+        for _ in range(n_steps):
+            n_ex += self.cycle(1, x0, 0)[1]
+            self.md(md_steps, dt, tau)
+        return n_ex
+
     def forces(self, w):
         """MD forces [n, 3] on the particles of walker w."""
         n = int(self.n[w])

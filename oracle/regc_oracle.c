@@ -607,7 +607,9 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
  * Otherwise one collective replica-exchange attempt is made (exchange numbers
  * e0, e0 + 1, ... in order).  Then every replica diffuses at fixed N with
  * moves k = 1 .. n_canonical of step t, all Metropolis displacements, and is
- * observed once.
+ * observed once after its last move of the step (n_canonical = 0 leaves a
+ * replica-exchange step without moves and without an observation: REGCMD
+ * runs its canonical diffusion as MD after the step).
  * trace, if given, is [n_walkers][n_steps][n_canonical + 1]; slot k = 0 of a
  * replica-exchange step holds type -1 and status 4 (not attempted).
  * counts and ex_counts as in oracle_sweeps and oracle_exchange.
@@ -622,7 +624,7 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
                  int64_t *counts, int64_t *ex_counts)
 {
     int S = sys->L * sys->M;
-    if (n_walkers != S || n_steps < 0 || n_canonical < 1 || !(x0 >= 0.0 && x0 <= 1.0)) return -1;
+    if (n_walkers != S || n_steps < 0 || n_canonical < 0 || !(x0 >= 0.0 && x0 <= 1.0)) return -1;
     for (int w = 0; w < S; ++w)
         if (n[w] < 0 || n[w] > sys->nmax || state_of_walker[w] < 0 || state_of_walker[w] >= S) return -1;
     const uint64_t th_gc = x0 >= 1.0 ? (uint64_t)1 << 32 : (uint64_t)floor(x0 * 4294967296.0);
@@ -677,7 +679,7 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
                 if (trace) trace[((int64_t)w * n_steps + ts) * per_step + k] = mv;
             }
             n[w] = nw;
-            observe(sys, hist, state, nw - sys->n_cluster, energy[w]);
+            if (gc || n_canonical > 0) observe(sys, hist, state, nw - sys->n_cluster, energy[w]);
         }
     }
     return n_exchange;

@@ -87,7 +87,20 @@ def test_x0_one_and_zero():
     with pytest.raises(ValueError):
         o.cycle(5, 1.5, 2)
     with pytest.raises(ValueError):
-        o.cycle(5, 0.5, 0)
+        o.cycle(5, 0.5, -1)
+
+
+def test_no_canonical_moves_observes_particle_exchange_steps_only():
+    """n_canonical = 0 (REGCMD: the canonical diffusion is MD): a replica is
+    observed after its particle-exchange attempt; a replica-exchange step has
+    no move and no observation."""
+    p = W.fcc100_small(L=2, M=2, seed=7)
+    o = O.Oracle(p)
+    tr, n_ex = o.cycle(400, 0.7, 0, trace=True)
+    assert tr.shape == (p.S, 400, 1)
+    assert o.omega.sum() == p.S * (400 - n_ex)
+    assert o.counts[:, 0, 0].sum() == 0                    # no displacement
+    assert o.counts[:, 1:, 0].sum() == p.S * (400 - n_ex)
 
 
 def small_box_cycle_pin(mutation=0, n_batches=16, steps=6000, x0=0.9, n_c=4):

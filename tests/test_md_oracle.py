@@ -16,6 +16,9 @@ rescaling thermostat).
   brute-force <N> and <E> of the small box.
 * Velocity Verlet conserves the total energy over short segments of a dilute
   system without the thermostat.
+* The REGCMD cycle (the x0 choice of Sec. II.A, then an MD segment) keeps the
+  small box's brute-force <N> and <E>; a dropped 1/(N+1) and wrong-sign
+  forces (planted) are caught.
 """
 import math
 
@@ -170,3 +173,40 @@ def test_velocity_verlet_conserves_energy_without_thermostat():
     k1 = b.md(400, 0.001, 1e12)[0]
     d = (b.energy[0] + k1) - (a.energy[0] + k0)
     assert abs(d) < 2e-3 * max(1.0, abs(a.energy[0] + k0)), d
+
+
+def regcmd_cycle_small_box(mutation=0, steps=6000, x0=0.9):
+    """<N>, <E> of the small box under the REGCMD cycle: per step the x0
+    choice (particle exchange or replica exchange), then one MD segment."""
+    p = small_box_problem().replace(p_disp=0.0)
+    o = O.Oracle(p, mutation=mutation)
+    nb, eb = [], []
+    nv = np.arange(p.nmax + 1)
+    for b in range(16):
+        h0, m0, om0 = o.hN.copy(), o.moments.copy(), o.omega.copy()
+        o.cycle_md(steps // 16, x0, 10, 0.005, 0.1)
+        dh = o.hN - h0
+        nb.append((dh @ nv) / np.maximum(dh.sum(axis=1), 1))
+        eb.append((o.moments[:, 2] - m0[:, 2]) / np.maximum(o.omega - om0, 1))
+    return p, np.array(nb), np.array(eb)
+
+
+def test_regcmd_cycle_small_box_brute_force():
+    p, nb, eb = regcmd_cycle_small_box()
+    exp_n, exp_e, sd_n = expected_small_box(p)
+    zn = (nb.mean(axis=0) - exp_n) / (nb.std(axis=0, ddof=1) / 4.0)
+    ze = (eb.mean(axis=0) - exp_e) / (eb.std(axis=0, ddof=1) / 4.0)
+    assert max(np.max(np.abs(zn)), np.max(np.abs(ze))) < 4.5, (zn, ze)
+
+
+@pytest.mark.parametrize("bit", [8, 1024])
+def test_planted_mistakes_under_the_regcmd_cycle(bit):
+    """The dropped 1/(N+1) of the insertion rule (8) and wrong-sign forces
+    (1024) both break the small-box pin under the REGCMD cycle (the latter
+    drives particles together until the energies are no longer finite)."""
+    p, nb, eb = regcmd_cycle_small_box(mutation=bit)
+    exp_n, exp_e, sd_n = expected_small_box(p)
+    zn = (nb.mean(axis=0) - exp_n) / (nb.std(axis=0, ddof=1) / 4.0)
+    ze = (eb.mean(axis=0) - exp_e) / (eb.std(axis=0, ddof=1) / 4.0)
+    worst = np.max(np.abs(np.concatenate([zn, ze])))        # NaN (non-finite energies) counts as caught
+    assert not worst < 6.0, worst
