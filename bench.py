@@ -409,9 +409,8 @@ def batched_uneven_arm(torch, steps, seed=0):
 def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0.1):
     """MD segments of every walker of the benchmark workload (regc_md) from its
     current state, device-timed per segment with the L2 flushed before each;
-    and REGCMD cycles (one GC-only sweep of the same handle would need
-    p_disp = 0: here the cycle is a 1-sweep regc_sweep + one MD segment +
-    one exchange, as a user alternating them runs it)."""
+    and REGCMD steps (regc_cycle_md: the x0 choice of Sec. II.A, then one MD
+    segment)."""
     n_mean = float(np.mean(g.get_walkers()[1]))
     for _ in range(2):
         g.md(n_steps, dt, tau, kinetic=False)
@@ -432,9 +431,7 @@ def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0
             flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        g.sweep(1)
-        g.md(n_steps, dt, tau, kinetic=False)
-        g.exchange()
+        g.cycle_md(1, 0.99, n_steps, dt, tau)
         b.record(stream)
         ev.append((a, b))
     torch.cuda.synchronize()
@@ -447,7 +444,8 @@ def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0
         "ms_per_segment": seg_ms,
         "particle_steps_per_s": p.S * n_mean * n_steps / (seg_ms / 1e3),
         "ms_per_cycle": cyc_ms,
-        "cycle": "1 sweep of 20 trial moves + 1 MD segment + 1 exchange attempt, every replica",
+        "cycle": "one REGCMD step (regc_cycle_md, x0 = 0.99): a particle-exchange attempt per replica or a "
+                 "replica-exchange attempt, then one MD segment",
         "energy_drift": drift,
         "timed_segments": segments,
     }

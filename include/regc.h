@@ -207,13 +207,26 @@ REGC_API regc_status regc_exchange(regc_handle *h);
  *     (the exchange counter advances by one);
  * then every walker makes n_canonical Metropolis displacements at fixed N,
  * trial moves k = 1 .. n_canonical of sweep t (A0 not used), and is observed
- * once into its state's histograms, as after a sweep.  moves_per_sweep and
+ * once into its state's histograms after its last move of the step, as after
+ * a sweep (with n_canonical = 0 a replica-exchange step has no move and no
+ * observation).  moves_per_sweep and
  * p_disp of the grid spec play no part.  Runs between two replica exchanges
  * go to the device as one launch.  n_exchanges (host, may be NULL) receives
  * the number of replica-exchange steps.  Asynchronous.  Errors: REGC_EINVAL
- * (n_steps < 0, n_canonical outside 1..1023, x0 outside [0, 1] or NaN,
+ * (n_steps < 0, n_canonical outside 0..1023, x0 outside [0, 1] or NaN,
  * walkers missing after regc_set_cluster), the handle's sticky status. */
 REGC_API regc_status regc_cycle(regc_handle *h, int n_steps, double x0, int n_canonical, int *n_exchanges);
+
+/* REGCMD (Sec. II.A, Fig. 1, with MD as the canonical sampler; Appendix):
+ * n_steps steps, each one step of regc_cycle with n_canonical = 0 (the x0
+ * choice, then a particle-exchange attempt per walker or a collective
+ * replica-exchange attempt) followed by one MD segment of md_steps steps of
+ * length dt with thermostat time constant tau, as regc_md.  Walkers are
+ * observed after their particle-exchange attempts.  n_exchanges (host, may
+ * be NULL) receives the replica-exchange steps.  Asynchronous.  Errors: those
+ * of regc_cycle and regc_md. */
+REGC_API regc_status regc_cycle_md(regc_handle *h, int n_steps, double x0, int md_steps, float dt, float tau,
+                                   int *n_exchanges);
 
 /* As regc_cycle, and write one record per trial move to host memory: trace is
  * [S walkers][n_steps][n_canonical + 1], slot k of step t holding move k of

@@ -70,6 +70,7 @@ SIGNATURES = {
     "regc_exchange": ([_h], C.c_int),
     "regc_cycle": ([_h, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "regc_cycle_traced": ([_h, C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "regc_cycle_md": ([_h, C.c_int, C.c_double, C.c_int, C.c_float, C.c_float, C.POINTER(C.c_int)], C.c_int),
     "regc_md": ([_h, C.c_int, C.c_float, C.c_float, _fp], C.c_int),
     "regc_histograms": ([_h, _lp, _lp, _lp, _dp, _lp], C.c_int),
     "regc_reset_histograms": ([_h], C.c_int),

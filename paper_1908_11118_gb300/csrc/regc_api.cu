@@ -494,7 +494,7 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
 // replica exchange.
 static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, regc_move_record* trace,
                              int* n_exchanges) {
-    if (!h || n_steps < 0 || n_canonical < 1 || n_canonical > 1023 || !(x0 >= 0.0 && x0 <= 1.0))
+    if (!h || n_steps < 0 || n_canonical < 0 || n_canonical > 1023 || !(x0 >= 0.0 && x0 <= 1.0))
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
@@ -517,7 +517,7 @@ static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canon
     cudaError_t e = cudaSuccess;
     int n_ex = 0;
     auto segment = [&](int a, int len, bool skip) {
-        if (e != cudaSuccess || len <= 0) return;
+        if (e != cudaSuccess || len <= 0 || len * mps <= (skip ? 1 : 0)) return;   // no move to make
         P.t0 = h->t + (uint32_t)a;
         P.n_sweeps = len;
         P.m_first = skip ? 1 : 0;
@@ -572,6 +572,27 @@ regc_status regc_cycle_traced(regc_handle* h, int n_steps, double x0, int n_cano
                               int* n_exchanges) {
     if (!trace && n_steps > 0) return REGC_EINVAL;
     return run_cycle(h, n_steps, x0, n_canonical, trace, n_exchanges);
+}
+
+regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, float dt, float tau,
+                          int* n_exchanges) {
+    if (!h || n_steps < 0 || md_steps < 0 || !(x0 >= 0.0 && x0 <= 1.0) || !(dt > 0.0f) || !(tau > 0.0f) ||
+        !std::isfinite(dt) || !std::isfinite(tau))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (h->need_walkers) return REGC_EINVAL;
+    if (md_smem(h->nmax, h->P.cg.ncell, h->P.cg.cap) > kMaxSmem) return REGC_EINVAL;
+    if (n_exchanges) *n_exchanges = 0;
+    int total = 0;
+    for (int t = 0; t < n_steps; ++t) {
+        int ex = 0;
+        regc_status st = run_cycle(h, 1, x0, 0, nullptr, &ex);
+        if (st == REGC_OK) st = regc_md(h, md_steps, dt, tau, nullptr);
+        if (st != REGC_OK) return st;
+        total += ex;
+    }
+    if (n_exchanges) *n_exchanges = total;
+    return REGC_OK;
 }
 
 regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kinetic) {

@@ -116,6 +116,13 @@ class Regc:
               "regc_cycle")
         return n_ex.value
 
+    def cycle_md(self, n_steps: int, x0: float, md_steps: int, dt: float, tau: float) -> int:
+        """REGCMD steps (regc_cycle_md); returns the replica-exchange steps."""
+        n_ex = C.c_int(0)
+        check(_lib.lib().regc_cycle_md(self._h, int(n_steps), float(x0), int(md_steps), float(dt), float(tau),
+                                       C.byref(n_ex)), "regc_cycle_md")
+        return n_ex.value
+
     def cycle_traced(self, n_steps: int, x0: float, n_canonical: int):
         """As cycle, with the trace [S, n_steps, n_canonical + 1]; returns
         (trace, replica-exchange steps)."""

@@ -69,6 +69,18 @@ def test_lockstep_fcc100_16_replicas(x0):
     assert g.check_energy() == 0.0
 
 
+def test_lockstep_without_canonical_moves():
+    """n_canonical = 0 (the REGCMD step): only the particle exchanges, each
+    observed; replica-exchange steps make no move and no observation."""
+    p = W.fcc100_small(seed=14)
+    pos, n = W.initial_walkers(p, 9, seed=5)
+    g, o, compared, diverged, observed, n_ex = run_cycle_lockstep(p, pos, n, blocks=4, steps=60, x0=0.7, n_c=0)
+    assert n_ex > 0
+    if not diverged:
+        assert_same_state(g, o, p, observed)
+    assert g.histograms()["omega"].sum() == p.S * (4 * 60 - n_ex)
+
+
 def test_paper_lj_slab_160_replicas():
     """The LJ A18 system (two cells) at the benchmark's settings: x0 = 0.99,
     ten displacements per step, walkers from empty to a full first layer of
@@ -152,7 +164,7 @@ def test_x0_limits_and_arguments():
     mv, ex, _ = g.counters()
     assert mv[:, 1:, 0].sum() == 20 * p.S                # one GC trial per walker and x0 = 1 step
     assert mv[:, 0, 0].sum() == 40 * 3 * p.S
-    for bad in ((-1, 0.5, 3), (5, 1.5, 3), (5, -0.1, 3), (5, float("nan"), 3), (5, 0.5, 0), (5, 0.5, 1024)):
+    for bad in ((-1, 0.5, 3), (5, 1.5, 3), (5, -0.1, 3), (5, float("nan"), 3), (5, 0.5, -1), (5, 0.5, 1024)):
         with pytest.raises(Exception):
             g.cycle(*bad)
     assert g.cycle(0, 0.5, 3) == 0

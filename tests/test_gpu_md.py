@@ -11,7 +11,10 @@ is checked statistically against values the oracle's pins fix:
     mean and variance;
   * grand-canonical sweeps alternated with MD segments reproduce the
     brute-force <N> and <E> of the small box;
-and for the cluster species a short segment matches the oracle too.
+and for the cluster species a short segment matches the oracle too.  The
+REGCMD cycle (the x0 choice of Sec. II.A, then an MD segment) makes the same
+exchanges as the oracle's over a few steps and reproduces the small box's
+brute-force averages.
 """
 import math
 
@@ -149,3 +152,51 @@ def test_md_arguments_and_checkpoint():
     h.md(5, 0.002, 0.05)
     for x, y in zip(h.get_walkers(), want):
         assert np.array_equal(x, y)      # the MD streams continue exactly
+
+
+def test_regcmd_cycle_short_parity():
+    """A few REGCMD steps (the x0 choice, then five MD steps) from identical
+    walkers: the same particle and replica exchanges as the oracle, positions
+    within the MD tolerance."""
+    p = W.fcc100_small(seed=5)
+    rng = np.random.default_rng(8)
+    pos, n = W.initial_walkers(p, rng.integers(2, 20, p.S), seed=4)
+    g = Regc(p)
+    g.set_walkers(pos, n)
+    o = O.Oracle(p, pos=pos, n=n)
+    for _ in range(3):
+        assert g.cycle_md(2, 0.7, 5, 0.002, 0.05) == o.cycle_md(2, 0.7, 5, 0.002, 0.05)
+    pg, ng, eg, sg = g.get_walkers()
+    assert np.array_equal(ng, o.n) and np.array_equal(sg, o.state_of_walker)
+    L = np.array([p.Lx, p.Ly])
+    for w in range(p.S):
+        d = pg[w, :ng[w]] - o.pos[w, :ng[w]]
+        d[:, :2] -= np.round(d[:, :2] / L) * L
+        assert np.max(np.abs(d), initial=0.0) < 1e-4, w
+    np.testing.assert_allclose(eg, o.energy, rtol=1e-4, atol=2e-3)
+    mv, ex, _ = g.counters()
+    assert np.array_equal(mv, o.counts) and np.array_equal(ex, o.ex_counts)
+    assert mv[:, 0, 0].sum() == 0                          # no displacement moves: MD does the diffusion
+
+
+def test_regcmd_cycle_small_box_brute_force():
+    p = small_box_problem().replace(p_disp=0.0)
+    g = Regc(p)
+    nb, eb = [], []
+    nv = np.arange(p.nmax + 1)
+    prev = g.histograms()
+    for b in range(16):
+        g.cycle_md(375, 0.9, 10, 0.005, 0.1)
+        h = g.histograms()
+        dh = h["hN"] - prev["hN"]
+        nb.append((dh @ nv) / np.maximum(dh.sum(axis=1), 1))
+        eb.append((h["moments"][:, 2] - prev["moments"][:, 2]) / np.maximum(h["omega"] - prev["omega"], 1))
+        prev = h
+    nb, eb = np.array(nb), np.array(eb)
+    exp_n, exp_e, _ = expected_small_box(p)
+    zn = (nb.mean(axis=0) - exp_n) / (nb.std(axis=0, ddof=1) / 4.0)
+    ze = (eb.mean(axis=0) - exp_e) / (eb.std(axis=0, ddof=1) / 4.0)
+    assert max(np.max(np.abs(zn)), np.max(np.abs(ze))) < 4.5, (zn, ze)
+    for bad in ((5, 1.5, 10, 0.005, 0.1), (5, 0.5, -1, 0.005, 0.1), (5, 0.5, 10, 0.0, 0.1)):
+        with pytest.raises(Exception):
+            g.cycle_md(*bad)
