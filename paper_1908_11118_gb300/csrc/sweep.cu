@@ -460,14 +460,15 @@ __device__ __forceinline__ void build_cells(const SweepParams& P, const WalkerSm
 // result in *out.
 template <bool DA, bool CL>
 __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int s, int m, int N,
-                              int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
+                              int slot, int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
     // with a cluster, particles 0..nA-1 are cluster atoms; insertion and
     // removal act on the grand-canonical species, whose count is N - nA
     const int nA = CL ? P.n_cluster : 0;
     const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
-    // the kind of move: drawn from A0 in a sweep, fixed by its place in a REGC cycle step
+    // the kind of move: drawn from A0 in a sweep (slot -1), fixed by its place
+    // in a REGC cycle step (slot 1: the particle exchange, 0: a displacement)
     const int gc_type = (B.z >> 31) == 0u ? 2 : 1;
-    const int type = P.cycle ? (m % P.mps == 0 ? gc_type : 0) : ((unsigned long long)A.x < P.th_disp ? 0 : gc_type);
+    const int type = slot < 0 ? ((unsigned long long)A.x < P.th_disp ? 0 : gc_type) : (slot ? gc_type : 0);
     int status = 0, idx = -1, overlap = 0;
     const int n_in0 = n_in;
     float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
@@ -721,7 +722,11 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         }
         // 3b. evaluate moves m0 .. m0 + K - 1 in parallel, one warp each
         const int mj = m0 + warp;
-        if (mj < total_moves) evaluate_move<DA, CL>(P, S, sf, s, mj, N, n_in, n_cand, lane, warp, S.res + warp);
+        if (mj < total_moves) {
+            int slot = -1;
+            if (P.cycle) slot = (mj % P.mps) == 0;
+            evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, n_in, n_cand, lane, warp, S.res + warp);
+        }
         group_sync<K>();
 
         // 4. commit in order (thread 0)
