@@ -184,3 +184,14 @@ def test_checkpoint_between_cycles():
     h.cycle(60, 0.9, 10)
     for x, y in zip(h.get_walkers(), want):
         assert np.array_equal(x, y)
+
+
+def test_longest_step_and_single_replica():
+    """n_canonical = 1023 (the longest step a launch takes) and a grid of one
+    state, where a replica-exchange attempt has no pair: the same moves as
+    the oracle."""
+    base = W.fcc100_small(L=1, M=1, nmax=32, seed=16)
+    pos, n = W.initial_walkers(base, 12, seed=2)
+    g, o, compared, diverged, observed, n_ex = run_cycle_lockstep(base, pos, n, blocks=2, steps=3, x0=0.5, n_c=1023)
+    if not diverged:
+        assert_same_state(g, o, base, observed)

@@ -260,3 +260,30 @@ def test_aiat_matches_oracle():
     assert np.all(np.isnan(e_r))
     with pytest.raises(Exception):
         g.aiat_config(int(np.nonzero(seen)[0][0]))
+
+
+def test_structure_edge_cases():
+    """Walkers at N = 0 and at N = Nmax, a periodic box (the slab counts span
+    the whole cell), no layers at all, a single distance bin; every count
+    equal to the oracle's."""
+    p = W.ideal_gas(W.fcc100_small(L=2, M=2, nmax=24, seed=15)).replace(
+        periodic_z=1, z_lo=0.0, z_hi=10.0, Lz=10.0, surf_xyz=np.zeros((0, 3)), surf_type=np.zeros(0, np.int32))
+    pos, n = W.initial_walkers(p, [0, 24, 1, 13], seed=9, min_dist=0.5)
+    g = Regc(p)
+    g.set_walkers(pos, n)
+    o = O.Oracle(p, pos=pos, n=n)
+    for spec in ({"n_z": 84, "dz": 0.12, "layers": [], "n_r": 1, "dr": 3.0},
+                 {"n_z": 1, "dz": 10.0, "layers": [(0.0, 10.0), (2.0, 2.5), (9.5, 10.0), (0.0, 0.1)], "n_r": 31,
+                  "dr": 0.1}):
+        init_store(g, spec, p.S)
+        g.structure_sample()
+        gs = g.structure_get()
+        os_ = ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec)
+        assert_same_samples(gs, os_)
+        assert gs["rho"].sum() == n.sum() if spec["n_z"] == 84 else True
+    # empty store: aiAT has no composition; reweighting is refused
+    g.structure_reset()
+    e_min, dG, ph = g.aiat([-1.0, 1.0])
+    assert np.all(np.isnan(e_min)) and np.all(np.isinf(dG)) and list(ph) == [-1, -1]
+    with pytest.raises(Exception):
+        g.structure_reweight([1.0], [-3.0], 0, 3)
