@@ -63,6 +63,7 @@ class _System(C.Structure):
         ("sur_theta", C.POINTER(C.c_double)),
         ("n_cluster", C.c_int),
         ("cluster_type", C.c_int),
+        ("shear", C.c_double),
     ]
 
 
@@ -179,6 +180,7 @@ class Oracle:
         s.mutation = int(mutation)
         s.n_cluster = int(getattr(problem, "n_cluster", 0))
         s.cluster_type = int(getattr(problem, "cluster_type", 0))
+        s.shear = float(getattr(problem, "shear", 0.0))
         self._theta = None
         if surrogate is not None:
             self._theta = np.ascontiguousarray(surrogate, np.float64)

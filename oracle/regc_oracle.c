@@ -118,13 +118,40 @@ static double min_image(double d, double box)
     return d - box * nearbyint(d / box);
 }
 
+/* Nearest-image displacement a - b, Cartesian.  Coordinates are in the cell
+ * frame (u, y, z): the lattice vectors of the cell are (Lx, 0) and
+ * (shear Ly, Ly), so the Cartesian x of a cell-frame point is u + shear y
+ * (shear = 0: a rectangular cell).  The nearest image is the shortest of the
+ * displacements to the images of b in the nine cells around the reduced
+ * difference. */
+static void pair_vec(const oracle_system *sys, double xa, double ya, double za,
+                     double xb, double yb, double zb, double d[3])
+{
+    double du = min_image(xa - xb, sys->Lx);
+    double dv = (sys->mutation & 32) ? (ya - yb) : min_image(ya - yb, sys->Ly);
+    double dz = sys->periodic_z ? min_image(za - zb, sys->Lz) : (za - zb);
+    int jr = (sys->mutation & 32) ? 0 : 1;
+    double best = INFINITY;
+    for (int j = -jr; j <= jr; ++j)
+        for (int i = -1; i <= 1; ++i) {
+            double v = dv + j * sys->Ly;
+            double x = du + i * sys->Lx + sys->shear * v;
+            double r2 = x * x + v * v + dz * dz;
+            if (r2 < best) {
+                best = r2;
+                d[0] = x;
+                d[1] = v;
+            }
+        }
+    d[2] = dz;
+}
+
 static double pair_r2(const oracle_system *sys, double xa, double ya, double za,
                       double xb, double yb, double zb)
 {
-    double dx = min_image(xa - xb, sys->Lx);
-    double dy = (sys->mutation & 32) ? (ya - yb) : min_image(ya - yb, sys->Ly);
-    double dz = sys->periodic_z ? min_image(za - zb, sys->Lz) : (za - zb);
-    return dx * dx + dy * dy + dz * dz;
+    double d[3];
+    pair_vec(sys, xa, ya, za, xb, yb, zb, d);
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
 }
 
 /* Error scale of a pair evaluated in binary32: 4 eps [(sigma/r)^12 + (sigma/r)^6],
@@ -738,8 +765,8 @@ static void md_forces(const oracle_system *sys, const double *pos, int n, double
                 rj = pos + 3 * j;
                 tj = species(sys, j);
             }
-            double d[3] = {min_image(ri[0] - rj[0], sys->Lx), min_image(ri[1] - rj[1], sys->Ly),
-                           sys->periodic_z ? min_image(ri[2] - rj[2], sys->Lz) : ri[2] - rj[2]};
+            double d[3];
+            pair_vec(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2], d);
             double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (r2 >= rc2) continue;
             double s2 = sys->sigma[ti][tj] * sys->sigma[ti][tj] / r2;
@@ -793,7 +820,10 @@ static void md_walker(const oracle_system *sys, int w, double *pos, int n, doubl
         for (int i = 0; i < nf; ++i) v[i] += 0.5 * dt * f[i];
         for (int i = 0; i < n; ++i) {
             double *r = pos + 3 * i;
-            for (int c = 0; c < 3; ++c) r[c] += dt * v[3 * i + c];
+            /* the cell-frame u moves by vx - shear vy */
+            r[0] += dt * (v[3 * i] - sys->shear * v[3 * i + 1]);
+            r[1] += dt * v[3 * i + 1];
+            r[2] += dt * v[3 * i + 2];
             r[0] -= sys->Lx * floor(r[0] / sys->Lx);
             r[1] -= sys->Ly * floor(r[1] / sys->Ly);
             if (sys->periodic_z) {

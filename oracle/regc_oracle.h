@@ -71,6 +71,9 @@ typedef struct {
      * enters the acceptance ratios and the histograms */
     int           n_cluster;
     int           cluster_type;
+    /* sheared cell: lattice vectors (Lx, 0) and (shear Ly, Ly); x coordinates
+     * are the cell-frame u = x - shear y (0: rectangular) */
+    double        shear;
 } oracle_system;
 
 /* One trial move as the oracle executed it. */

@@ -16,7 +16,8 @@ The bin of a value is an integer decided by floating point, so it is taken
 in binary32, with the operations of the GPU path in the same order (the
 paper fixes no precision): d = z - z_lo, k = floor(d * inv_dz); the
 nearest-image difference e = q - p, or (q - L) - p when e > L/2, or
-q - (p - L) when e < -L/2; r2 = dx dx + dy dy, r = sqrt(r2),
+q - (p - L) when e < -L/2, then in a sheared cell (cell-frame x) the
+Cartesian dx = du + shear dy; r2 = dx dx + dy dy, r = sqrt(r2),
 k = floor(r * inv_dr).  Like every geometric input, dz and dr are binary32
 values; inv_dz and inv_dr are 1/dz and 1/dr rounded once to binary32.
 Everything after the counts is FP64.
@@ -68,6 +69,7 @@ def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
     z_lo = F(problem.z_lo)
     Lx, Ly = F(problem.Lx), F(problem.Ly)
     hLx, hLy = F(0.5 * problem.Lx), F(0.5 * problem.Ly)
+    shear = F(getattr(problem, "shear", 0.0))
     first = int(getattr(problem, "n_cluster", 0))
     pts = [tuple(F(c) for c in pos_w[j]) for j in range(first, int(n_w))]
     rho = np.zeros(n_z, np.int64)
@@ -85,8 +87,8 @@ def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
         pop[l] = len(mem)
         for a in range(len(mem)):
             for b in range(a + 1, len(mem)):
-                dx = _min_image_f32(mem[a][0], mem[b][0], Lx, hLx)
                 dy = _min_image_f32(mem[a][1], mem[b][1], Ly, hLy)
+                dx = F(_min_image_f32(mem[a][0], mem[b][0], Lx, hLx) + F(shear * dy))
                 r2 = F(F(dx * dx) + F(dy * dy))
                 k = int(math.floor(F(np.sqrt(r2) * inv_dr)))
                 if k < n_r:

@@ -69,11 +69,14 @@ class Problem:
     # every walker have potential type cluster_type and only displace
     n_cluster: int = 0
     cluster_type: int = 0
+    # sheared (oblique) cell: lattice vectors (Lx, 0) and (shear Ly, Ly); every
+    # x coordinate is then the cell-frame u = x - shear y
+    shear: float = 0.0
 
     def __post_init__(self):
         # the C ABI carries these as binary32: round them here, once, so that
         # both implementations start from the same numbers
-        for k in ("rc", "Lx", "Ly", "Lz", "z_lo", "z_hi", "max_disp"):
+        for k in ("rc", "Lx", "Ly", "Lz", "z_lo", "z_hi", "max_disp", "shear"):
             setattr(self, k, float(f32(getattr(self, k))))
         self.eps = f32(self.eps)
         self.sigma = f32(self.sigma)
@@ -240,6 +243,55 @@ def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = 39.
         n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_slab")
 
 
+def lj_a18_hex_slab(L: int = 10, M: int = 16, nmax: int = 160, mass_amu: float = 39.948,
+                    rc_over_sigma_ab: float = 2.5, zone: float = 48.0, seed: int = 0) -> Problem:
+    """The paper's LJ surface system (Sec. III.A, Appendix) in its own cell:
+    the 3 x 3 hexagonal supercell of the fcc(111) layer (lattice vectors of
+    11.489 A at 60 degrees), two layers, 18 A atoms, as a sheared cell with
+    shear 1/sqrt(3) (x coordinates in the cell frame u = x - y / sqrt(3)).
+    Potential, zone, grid, mass and cutoff as in lj_a18_slab."""
+    a = 11.489 / 3.0
+    h = a * math.sqrt(3.0) / 2.0
+    dz = a * math.sqrt(2.0 / 3.0)
+    pts = []
+    for k, (su, sv) in enumerate(((0.0, 0.0), (a / 3.0, a / (2.0 * math.sqrt(3.0))))):
+        for j in range(3):
+            for i in range(3):
+                pts.append((i * a + su, j * h + sv, k * dz))
+    xyz = f32(np.array(pts))
+    ref = lj_a18_slab(L=L, M=M, nmax=nmax, mass_amu=mass_amu, rc_over_sigma_ab=rc_over_sigma_ab, zone=zone,
+                      seed=seed)
+    ztop = float(f32(dz))
+    zhi = float(f32(ztop + zone))
+    return ref.replace(Lx=3.0 * a, Ly=3.0 * h, Lz=zhi, z_lo=ztop, z_hi=zhi, surf_xyz=xyz,
+                       surf_type=np.ones(len(xyz), np.int32), shear=1.0 / math.sqrt(3.0),
+                       e_lo=-1.8 * nmax, e_bin=0.01, n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_hex")
+
+
+def hex_hollow_sites(problem: Problem):
+    """The 18 hollow sites (both kinds) of the top layer of lj_a18_hex_slab, in
+    the cell frame: above the bottom layer's atoms and above the third
+    stacking position."""
+    a = problem.Lx / 3.0
+    h = problem.Ly / 3.0
+    pts = []
+    for su, sv in ((0.0, 0.0), (2.0 * a / 3.0, a / math.sqrt(3.0))):
+        for j in range(3):
+            for i in range(3):
+                pts.append(((i * a + su) % problem.Lx, (j * h + sv) % problem.Ly))
+    xy = f32(np.array(pts))
+    xy[:, 0] = np.where(xy[:, 0] >= problem.Lx, 0.0, xy[:, 0])
+    xy[:, 1] = np.where(xy[:, 1] >= problem.Ly, 0.0, xy[:, 1])
+    return xy
+
+
+def cartesian(problem: Problem, pos):
+    """Cell-frame positions [..., 3] -> Cartesian (x = u + shear y)."""
+    out = np.array(pos, np.float64, copy=True)
+    out[..., 0] = out[..., 0] + float(getattr(problem, "shear", 0.0)) * out[..., 1]
+    return out
+
+
 def lj_a18_initial(problem: Problem, n_b, seed: int, min_dist: float = 1.9):
     """Seeded walkers of ``lj_a18_slab``: walker w gets n_b[w] B particles,
     the first up to 36 on a random subset of the hollow sites of the top A
@@ -250,14 +302,19 @@ def lj_a18_initial(problem: Problem, n_b, seed: int, min_dist: float = 1.9):
     rng = np.random.default_rng(seed)
     S, nmax = problem.S, problem.nmax
     n_b = np.broadcast_to(np.asarray(n_b, dtype=np.int64), (S,))
-    s = 11.489 / 3.0
-    h = s * math.sqrt(3.0) / 2.0
-    sites = []
-    for sx, sy in ((0.0, 0.0), (s, 2.0 * h / 3.0)):      # the two hollow sites of a B-stacked top layer
-        for j in range(6):
-            for i in range(3):
-                sites.append((((i * s + (0.5 * s if j % 2 else 0.0) + sx) % problem.Lx), (j * h + sy) % problem.Ly))
-    sites = np.array(sites)
+    shear = float(getattr(problem, "shear", 0.0))
+    if shear != 0.0:
+        sites = hex_hollow_sites(problem)
+    else:
+        s = 11.489 / 3.0
+        h = s * math.sqrt(3.0) / 2.0
+        sites = []
+        for sx, sy in ((0.0, 0.0), (s, 2.0 * h / 3.0)):      # the two hollow sites of a B-stacked top layer
+            for j in range(6):
+                for i in range(3):
+                    sites.append((((i * s + (0.5 * s if j % 2 else 0.0) + sx) % problem.Lx),
+                                  (j * h + sy) % problem.Ly))
+        sites = np.array(sites)
     box = np.array([problem.Lx, problem.Ly, problem.Lz])
     per = np.array([True, True, False])
     pos = np.zeros((S, nmax, 3))
@@ -283,6 +340,7 @@ def lj_a18_initial(problem: Problem, n_b, seed: int, min_dist: float = 1.9):
             others = np.array(pts + [list(a) for a in problem.surf_xyz]).reshape(-1, 3)
             d = q - others
             d = np.where(per, d - box * np.round(d / box), d)
+            d[:, 0] += shear * d[:, 1]          # Cartesian x (the reduced image is the nearest within rc)
             if np.min(np.sum(d * d, axis=1)) < min_dist * min_dist:
                 continue
             pts.append(list(q))
