@@ -99,6 +99,16 @@ typedef struct {
     float        Lx, Ly, Lz;
     int          periodic_z;
     float        z_lo, z_hi;
+    float        shear;     /* |shear| <= 1; 0 for a rectangular cell.  The
+                               cell's lattice vectors in the xy plane are
+                               (Lx, 0) and (shear Ly, Ly) -- 1/sqrt(3) for the
+                               hexagonal cell of an fcc(111) surface.  Every
+                               x coordinate of the ABI (surface atoms and
+                               walkers) is then the cell-frame u = x - shear y,
+                               in [0, Lx); the box needs
+                               rc sqrt(1 + shear^2) <= Lx / 2 and rc <= Ly / 2,
+                               and a displacement move is uniform in a cube
+                               of the cell frame (u, y, z). */
 } regc_surface;
 
 /* The (T, mu) grid of replicas (Sec. II.A.2: S = L x M states; state
@@ -356,7 +366,7 @@ typedef struct {
     float   layer_lo[4];    /* a particle is in layer l if layer_lo[l] <= z < layer_hi[l] */
     float   layer_hi[4];
     int     n_r;            /* 1..4096 lateral distance bins: bin k covers [k, k+1) dr   */
-    float   dr;             /* > 0, with n_r dr <= min(Lx, Ly) / 2                      */
+    float   dr;             /* > 0, with n_r dr <= min(Lx / sqrt(1 + shear^2), Ly) / 2  */
     int64_t capacity;       /* samples the device keeps; each regc_structure_sample call
                                adds one per walker                                      */
 } regc_structure_spec;

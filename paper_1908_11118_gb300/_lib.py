@@ -33,7 +33,7 @@ class Potential(C.Structure):
 class Surface(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("xyz", C.POINTER(C.c_float)), ("type", C.POINTER(C.c_int)),
                 ("Lx", C.c_float), ("Ly", C.c_float), ("Lz", C.c_float), ("periodic_z", C.c_int),
-                ("z_lo", C.c_float), ("z_hi", C.c_float)]
+                ("z_lo", C.c_float), ("z_hi", C.c_float), ("shear", C.c_float)]
 
 
 class GridSpec(C.Structure):

@@ -117,8 +117,8 @@ __device__ __forceinline__ float3 md_force(const SweepParams& P, const float4* p
                     const int j = slots[cell * P.cg.cap + s];
                     if (j == i) continue;
                     const float4 q = pos[j];
-                    const float dx = min_image_exact(p.x, q.x, P.g.Lx, P.g.hLx);
                     const float dy = min_image_exact(p.y, q.y, P.g.Ly, P.g.hLy);
+                    const float dx = cart_dx(P.g, min_image_exact(p.x, q.x, P.g.Lx, P.g.hLx), dy);
                     const float dz = P.g.periodic_z ? min_image_exact(p.z, q.z, P.g.Lz, P.g.hLz) : p.z - q.z;
                     const float r2 = r2_of(dx, dy, dz);
                     if (r2 < P.g.rc2) {
@@ -137,7 +137,8 @@ __device__ __forceinline__ float3 md_force(const SweepParams& P, const float4* p
             const PairTab& t = (CL && iA) ? P.gsA[bits & 3u] : P.gs[bits & 3u];
             const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
             const float sz = (bits & 16u) ? P.g.Lz : 0.f;
-            const float dx = (p.x - sx) - at.x, dy = (p.y - sy) - at.y, dz = (p.z - sz) - at.z;
+            const float dy = (p.y - sy) - at.y, dz = (p.z - sz) - at.z;
+            const float dx = cart_dx(P.g, (p.x - sx) - at.x, dy);
             const float r2 = r2_of(dx, dy, dz);
             if (r2 < P.g.rc2) lj_force_add(t, r2, dx, dy, dz, fx, fy, fz);
         }
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kMdThreads) md_kernel(const __grid_constant__ 
             v.y = fmaf(0.5f * dt, f.y, alpha * v.y);
             v.z = fmaf(0.5f * dt, f.z, alpha * v.z);
             float4 p = pos[i];
-            p.x = fmaf(dt, v.x, p.x);
+            p.x = fmaf(dt, fmaf(-P.g.shear, v.y, v.x), p.x);   // u = x - shear y
             p.y = fmaf(dt, v.y, p.y);
             p.z = fmaf(dt, v.z, p.z);
             if (p.x < 0.f) p.x += P.g.Lx;

@@ -128,7 +128,12 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
             eps_max = std::max(eps_max, (double)pot->eps[i][j]);
         }
     const double rc = pot->rc;
-    if (!(surf->Lx >= 2 * rc) || !(surf->Ly >= 2 * rc) || !(surf->z_hi > surf->z_lo)) return REGC_EINVAL;
+    // with a sheared cell, every partner within rc is the nearest image in the
+    // cell frame when rc sqrt(1 + shear^2) <= Lx / 2 and rc <= Ly / 2
+    const double shear = surf->shear;
+    if (!std::isfinite(shear) || !(fabs(shear) <= 1.0)) return REGC_EINVAL;
+    const double su = sqrt(1.0 + shear * shear);
+    if (!(surf->Lx >= 2 * rc * su) || !(surf->Ly >= 2 * rc) || !(surf->z_hi > surf->z_lo)) return REGC_EINVAL;
     if (surf->periodic_z && (!(surf->Lz >= 2 * rc) || surf->z_lo != 0.0f || surf->z_hi != surf->Lz))
         return REGC_EINVAL;
     if (surf->n_atoms < 0 || (surf->n_atoms > 0 && (!surf->xyz || !surf->type))) return REGC_EINVAL;
@@ -158,7 +163,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     const int periodic_z = surf->periodic_z ? 1 : 0;
     const double hz = periodic_z ? surf->Lz : (double)surf->z_hi - (double)surf->z_lo;
     CellGrid cg{};
-    cg.ncx = cells_along(surf->Lx, rc);
+    cg.ncx = cells_along(surf->Lx, rc * su);   // the cell frame's u-width reaches rc sqrt(1 + shear^2)
     cg.ncy = cells_along(surf->Ly, rc);
     cg.ncz = cells_along(hz, rc);
     if ((long long)cg.ncx * cg.ncy * cg.ncz > 65535) return REGC_EINVAL;
@@ -253,6 +258,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     st.isy = (float)(st.nsy / (double)surf->Ly);
     const double wx = (double)surf->Lx / st.nsx, wy = (double)surf->Ly / st.nsy;
     const double reach = rc * 1.0001 + 1e-4;
+    const double reach_u = reach * su;
     std::vector<float4> all(surf->n_atoms);
     double zmax = -INFINITY;
     std::vector<int> relevant;
@@ -285,7 +291,8 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
                             const double ay = (double)r[1] + sy * (double)surf->Ly;
                             const double ex = std::max(0.0, std::max(x0 - ax, ax - x1));
                             const double ey = std::max(0.0, std::max(y0 - ay, ay - y1));
-                            if (ex * ex + ey * ey >= reach * reach) continue;
+                            if (shear == 0.0 ? ex * ex + ey * ey >= reach * reach : (ex >= reach_u || ey >= reach))
+                                continue;
                             unsigned bits = (unsigned)surf->type[a];
                             float bx = r[0], by = r[1], bz = r[2];
                             if (sx < 0) bx = r[0] - surf->Lx;
@@ -337,7 +344,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     h->hard_core_T = T;
     P.g = Geometry{surf->Lx, surf->Ly, periodic_z ? surf->Lz : 0.0f, 0.5f * surf->Lx, 0.5f * surf->Ly,
                    periodic_z ? 0.5f * surf->Lz : 0.0f, periodic_z, surf->z_lo, surf->z_hi,
-                   surf->z_hi - surf->z_lo, (float)(rc * rc), (float)rc};
+                   surf->z_hi - surf->z_lo, (float)(rc * rc), (float)rc, surf->shear};
     P.cg = cg;
     P.max_disp = grid->max_disp;
     P.th_disp = (unsigned long long)floor(grid->p_disp * 4294967296.0);

@@ -94,6 +94,7 @@ struct Geometry {
     float height;          // binary32(z_hi - z_lo)
     float rc2;
     float rc;
+    float shear;           // the cell's second lattice vector is (shear Ly, Ly): x = u + shear v
 };
 
 struct CellGrid {
@@ -215,6 +216,11 @@ __device__ __forceinline__ float phi_of_r2(float r2, const PairTab& t) {
     const float s2 = __fdividef(t.sig2, r2);
     const float s6 = __fmul_rn(__fmul_rn(s2, s2), s2);
     return __fmul_rn(t.eps4, __fmaf_rn(s6, s6, -s6));
+}
+
+// Cartesian x component of a displacement (du, dv) in the cell frame.
+__device__ __forceinline__ float cart_dx(const Geometry& g, float du, float dv) {
+    return __fadd_rn(du, __fmul_rn(g.shear, dv));
 }
 
 __device__ __forceinline__ float r2_of(float dx, float dy, float dz) {

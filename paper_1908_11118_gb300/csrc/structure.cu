@@ -41,7 +41,7 @@ struct SampleParams {
     const long long* efix;
     const int* sow;
     int nmax, n_cluster;
-    float Lx, Ly, hLx, hLy, z_lo;
+    float Lx, Ly, hLx, hLy, z_lo, shear;
     int n_z;
     float inv_dz;
     int n_layers;
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kSampleThreads) structure_sample_kernel(const 
             const float xa = xs[ia], ya = ys[ia];
             for (int b = a + 1 + lane; b < ml; b += 32) {
                 const int ib = li[b];
-                const float dx = min_image_exact(xa, xs[ib], P.Lx, P.hLx);
                 const float dy = min_image_exact(ya, ys[ib], P.Ly, P.hLy);
+                const float dx = __fadd_rn(min_image_exact(xa, xs[ib], P.Lx, P.hLx), __fmul_rn(P.shear, dy));
                 const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
                 const float k = floorf(__fmul_rn(r, P.inv_dr));
                 if (k < (float)P.n_r) atomicAdd(&hl[(int)k], 1u);
@@ -323,7 +323,11 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
     if (s.n_z < 1 || s.n_z > 4096 || !(s.dz > 0.0f) || !std::isfinite(s.dz) || s.n_layers < 0 || s.n_layers > 4 ||
         s.n_r < 1 || s.n_r > 4096 || !(s.dr > 0.0f) || !std::isfinite(s.dr) || s.capacity < 1)
         return REGC_EINVAL;
-    if (!((double)s.n_r * s.dr <= 0.5 * std::min(h->Lx, h->Ly))) return REGC_EINVAL;
+    // lateral distances up to the inscribed radius of the cell, where the
+    // nearest image in the cell frame is the nearest image
+    const double sh = h->P.g.shear;
+    if (!((double)s.n_r * s.dr <= 0.5 * std::min((double)h->Lx / sqrt(1.0 + sh * sh), (double)h->Ly)))
+        return REGC_EINVAL;
     for (int l = 0; l < s.n_layers; ++l)
         if (!(s.layer_lo[l] < s.layer_hi[l])) return REGC_EINVAL;
     const size_t smem = sample_smem(h->nmax, s.n_z, s.n_layers, s.n_r);
@@ -400,6 +404,7 @@ regc_status regc_structure_sample(regc_handle* h) {
     P.hLx = h->P.g.hLx;
     P.hLy = h->P.g.hLy;
     P.z_lo = h->P.g.z_lo;
+    P.shear = h->P.g.shear;
     P.n_z = st.n_z;
     P.inv_dz = st.inv_dz;
     P.n_layers = st.n_layers;

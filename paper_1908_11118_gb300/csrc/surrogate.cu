@@ -46,8 +46,8 @@ __global__ void pack_kernel(const float* theta, __nv_bfloat16* w1, float* b1, __
 
 // Displacement q - p with the exact minimum image on periodic axes.
 __device__ __forceinline__ float r2_exact(const Geometry& g, float qx, float qy, float qz, float4 p) {
-    const float dx = min_image_exact(qx, p.x, g.Lx, g.hLx);
     const float dy = min_image_exact(qy, p.y, g.Ly, g.hLy);
+    const float dx = cart_dx(g, min_image_exact(qx, p.x, g.Lx, g.hLx), dy);
     const float dz = g.periodic_z ? min_image_exact(qz, p.z, g.Lz, g.hLz) : __fsub_rn(qz, p.z);
     return r2_of(dx, dy, dz);
 }

@@ -316,12 +316,14 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
         const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
         n_cand += use ? NQ : 0;
         const PairTab& tp = CL ? (pj < P.n_cluster ? mt.tA : mt.tB) : P.gg;
-        const float phi0 = pair_phi_sel(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz),
+        const float dy0 = __fsub_rn(e.ay0, by);
+        const float phi0 = pair_phi_sel(cart_dx(P.g, __fsub_rn(e.ax0, bx), dy0), dy0, __fsub_rn(e.az0, bz),
                                         P.g.rc2, tp, use, n_in, ov);
         fix_add(acc, phi0, sgn0);
         if (NQ == 2) {
             int ov1 = 0;
-            const float phi1 = pair_phi_sel(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by), __fsub_rn(e.az1, bz),
+            const float dy1 = __fsub_rn(e.ay1, by);
+            const float phi1 = pair_phi_sel(cart_dx(P.g, __fsub_rn(e.ax1, bx), dy1), dy1, __fsub_rn(e.az1, bz),
                                             P.g.rc2, tp, use, n_in, ov1);
             fix_add(acc, phi1, -1);
         }
@@ -348,13 +350,15 @@ __device__ __forceinline__ void surface_pass(const SweepParams& P, int col, floa
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
         if (!(bits & 32u)) n_cand += NQ;   // padding slots are not candidates
-        const float phi0 = pair_phi_sel(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
-                                    __fsub_rn(__fsub_rn(q0z, sz), a.z), P.g.rc2, t, true, n_in, ov);
+        const float dy0 = __fsub_rn(__fsub_rn(q0y, sy), a.y);
+        const float phi0 = pair_phi_sel(cart_dx(P.g, __fsub_rn(__fsub_rn(q0x, sx), a.x), dy0), dy0,
+                                        __fsub_rn(__fsub_rn(q0z, sz), a.z), P.g.rc2, t, true, n_in, ov);
         fix_add(acc, phi0, sgn0);
         if (NQ == 2) {
             int ov1 = 0;
-            const float phi1 = pair_phi_sel(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
-                                        __fsub_rn(__fsub_rn(q1z, sz), a.z), P.g.rc2, t, true, n_in, ov1);
+            const float dy1 = __fsub_rn(__fsub_rn(q1y, sy), a.y);
+            const float phi1 = pair_phi_sel(cart_dx(P.g, __fsub_rn(__fsub_rn(q1x, sx), a.x), dy1), dy1,
+                                            __fsub_rn(__fsub_rn(q1z, sz), a.z), P.g.rc2, t, true, n_in, ov1);
             fix_add(acc, phi1, -1);
         }
     }
@@ -397,11 +401,13 @@ __device__ __forceinline__ void feature_mobile(const SweepParams& P, const Walke
             if (pj != skip) {
                 const float4 p = S.pos[pj];
                 const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
-                const float r20 = r2_of(__fsub_rn(e.ax0, bx), __fsub_rn(e.ay0, by), __fsub_rn(e.az0, bz));
+                const float dy0 = __fsub_rn(e.ay0, by);
+                const float r20 = r2_of(cart_dx(P.g, __fsub_rn(e.ax0, bx), dy0), dy0, __fsub_rn(e.az0, bz));
                 const float wp = CL ? (pj < P.n_cluster ? mt.tA.eps : mt.tB.eps) : P.gg.eps;
                 if (r20 < P.g.rc2) add_features(F0, r20, wp, P.g.rc);
                 if (NQ == 2) {
-                    const float r21 = r2_of(__fsub_rn(e.ax1, bx), __fsub_rn(e.ay1, by), __fsub_rn(e.az1, bz));
+                    const float dy1 = __fsub_rn(e.ay1, by);
+                    const float r21 = r2_of(cart_dx(P.g, __fsub_rn(e.ax1, bx), dy1), dy1, __fsub_rn(e.az1, bz));
                     if (r21 < P.g.rc2) add_features(F1, r21, wp, P.g.rc);
                 }
             }
@@ -424,11 +430,13 @@ __device__ __forceinline__ void feature_surface(const SweepParams& P, int col, f
         const PairTab& t = (CL && mA) ? P.gsA[bits & 3u] : surf_tab(P, (int)(bits & 3u));
         const float sx = (bits & 4u) ? P.g.Lx : 0.f, sy = (bits & 8u) ? P.g.Ly : 0.f;
         const float sz = (bits & 16u) ? P.g.Lz : 0.f;
-        const float r20 = r2_of(__fsub_rn(__fsub_rn(q0x, sx), a.x), __fsub_rn(__fsub_rn(q0y, sy), a.y),
+        const float dy0 = __fsub_rn(__fsub_rn(q0y, sy), a.y);
+        const float r20 = r2_of(cart_dx(P.g, __fsub_rn(__fsub_rn(q0x, sx), a.x), dy0), dy0,
                                 __fsub_rn(__fsub_rn(q0z, sz), a.z));
         if (r20 < P.g.rc2) add_features(F0, r20, t.eps, P.g.rc);
         if (NQ == 2) {
-            const float r21 = r2_of(__fsub_rn(__fsub_rn(q1x, sx), a.x), __fsub_rn(__fsub_rn(q1y, sy), a.y),
+            const float dy1 = __fsub_rn(__fsub_rn(q1y, sy), a.y);
+            const float r21 = r2_of(cart_dx(P.g, __fsub_rn(__fsub_rn(q1x, sx), a.x), dy1), dy1,
                                     __fsub_rn(__fsub_rn(q1z, sz), a.z));
             if (r21 < P.g.rc2) add_features(F1, r21, t.eps, P.g.rc);
         }
@@ -653,8 +661,8 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
 // Squared minimum-image distance in binary32 (periodic axes per geometry).
 __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay, float az, float bx, float by,
                                        float bz) {
-    const float dx = min_image_exact(ax, bx, P.g.Lx, P.g.hLx);
     const float dy = min_image_exact(ay, by, P.g.Ly, P.g.hLy);
+    const float dx = cart_dx(P.g, min_image_exact(ax, bx, P.g.Lx, P.g.hLx), dy);
     const float dz = P.g.periodic_z ? min_image_exact(az, bz, P.g.Lz, P.g.hLz) : __fsub_rn(az, bz);
     return r2_of(dx, dy, dz);
 }
@@ -929,10 +937,11 @@ __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __g
     walker_sweep<K, TRACE, DA, CL>(P, blockIdx.x, smem, threadIdx.x);
 }
 
-// Displacement q - p with the exact minimum image on periodic axes.
+// Displacement q - p with the exact minimum image on periodic axes (cell
+// frame), x made Cartesian.
 __device__ __forceinline__ void disp_exact(const Geometry& g, float4 q, float4 p, float& dx, float& dy, float& dz) {
-    dx = min_image_exact(q.x, p.x, g.Lx, g.hLx);
     dy = min_image_exact(q.y, p.y, g.Ly, g.hLy);
+    dx = cart_dx(g, min_image_exact(q.x, p.x, g.Lx, g.hLx), dy);
     dz = g.periodic_z ? min_image_exact(q.z, p.z, g.Lz, g.hLz) : __fsub_rn(q.z, p.z);
 }
 

@@ -58,7 +58,8 @@ class Regc:
         self._stype = np.ascontiguousarray(np.asarray(problem.surf_type, np.int32))
         surf = _lib.Surface(len(self._stype), _p(self._sxyz, C.c_float), _p(self._stype, C.c_int32),
                             float(problem.Lx), float(problem.Ly), float(problem.Lz),
-                            int(problem.periodic_z), float(problem.z_lo), float(problem.z_hi))
+                            int(problem.periodic_z), float(problem.z_lo), float(problem.z_hi),
+                            float(getattr(problem, "shear", 0.0)))
         self._kT = np.ascontiguousarray(problem.kT, np.float64)
         self._mu = np.ascontiguousarray(problem.mu, np.float64)
         grid = _lib.GridSpec(len(self._kT), len(self._mu), _p(self._kT, C.c_double),

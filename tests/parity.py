@@ -12,7 +12,8 @@ Energy tolerance (per move): |dE_gpu - dE_oracle| <= 1e-5 max(|dE|, T), where
 T = sum over the pairs entering dE of 4 eps [(sigma/r)^12 + (sigma/r)^6] (the
 two terms of the LJ pair energy cancel near r = sigma, so |phi| alone would
 understate the binary32 rounding), plus the step of phi at rc for every pair
-within 4e-6 rc^2 of the cutoff.
+within 4e-6 rc^2 of the cutoff, plus half a unit of the GPU's fixed-point
+energy grid (2^-30) per pair within rc.
 """
 import numpy as np
 
@@ -20,7 +21,10 @@ DE_REL = 1e-5
 
 
 def de_tolerance(o):
-    return DE_REL * np.maximum(np.abs(o["dE"]), o["sum_abs"]) + o["band"] + 1e-9
+    # + half a fixed-point unit (2^-30) per pair: the GPU rounds every pair
+    # energy onto that grid before summing (visible when energies are small in
+    # the problem's units, e.g. eV for weak gas-gas pairs)
+    return DE_REL * np.maximum(np.abs(o["dE"]), o["sum_abs"]) + o["band"] + o["n_pairs"] * 2.0 ** -31 + 1e-9
 
 
 def compare_traces(gt, ot, beta_max):
