@@ -453,9 +453,10 @@ def regcmd_arm(g, p, torch, stream, flush, segments, n_steps=10, dt=0.005, tau=0
 
 # ---------------------------------------------------------------- the paper's LJ run
 
-PAPER_CYCLE = ("the paper's LJ surface system (Sec. III.A) in eV and Angstrom: two-layer fcc(111) A slab "
-               "(two 3x3 A18 cells, 36 A) under B gas in a 48 A zone, 10 T (200-650 K) x 16 mu "
-               "(-2.4..-0.9 eV) = 160 replicas, Nmax 256; REGC cycle x0 = 0.99, 10 displacements per step")
+PAPER_CYCLE = ("the paper's LJ surface system (Sec. III.A) in eV and Angstrom, in its own cell: the 3x3 "
+               "hexagonal supercell of a two-layer fcc(111) A slab (A18, lattice vectors 11.489 A at 60 deg) "
+               "under B gas in a 48 A zone, 10 T (200-650 K) x 16 mu (-2.4..-0.9 eV) = 160 replicas, "
+               "Nmax 160; REGC cycle x0 = 0.99, 10 displacements per step")
 
 
 def hbm_peak():
@@ -471,10 +472,11 @@ def hbm_peak():
 
 def paper_structure_spec(p):
     """Slabs of 0.12 A over the 48 A zone (Sec. III.A) and three adsorbate
-    layers above the floor for g_xy, lateral bins of 0.1 A up to 5.7 A."""
+    layers above the floor for g_xy, lateral bins of 0.1 A up to 4.9 A (the
+    inscribed radius of the hexagonal cell is 4.97 A)."""
     return {"n_z": 400, "dz": 0.12,
             "layers": [(p.z_lo, p.z_lo + 0.6), (p.z_lo + 0.6, p.z_lo + 1.6), (p.z_lo + 1.6, p.z_lo + 2.6)],
-            "n_r": 57, "dr": 0.1}
+            "n_r": 49, "dr": 0.1}
 
 
 def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, cpu_seconds=8.0, seed=0,
@@ -489,7 +491,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     reweighting of the samples per phase (Eq. avegr) with the HBM roofline of
     its accumulation kernel."""
     from paper_1908_11118_gb300 import Regc
-    p = W.lj_a18_slab(seed=seed)
+    p = W.lj_a18_hex_slab(seed=seed)
     spec = paper_structure_spec(p)
     g = Regc(p, stream=stream)
     g.set_walkers(np.zeros((p.S, p.nmax, 3)), np.zeros(p.S, np.int32))
@@ -550,18 +552,18 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     rg = g.structure_reweight(kB * Tg.ravel(), mg.ravel(), 0, p.nmax, tol=1e-9, max_iter=200000)
     mbar_phase = np.argmax(rg["p"], axis=1)
     _, _, ai_phase = g.aiat(mg.ravel())
-    low = ai_phase <= 36                      # up to the first monolayer (18 per A18 cell)
+    low = ai_phase <= 18                      # up to the first monolayer of the A18 cell
     agree = {"all": float(np.mean(mbar_phase == ai_phase)),
-             "aiat_nb_per_a18_le_18": float(np.mean((mbar_phase == ai_phase)[low])) if low.any() else None,
-             "aiat_nb_per_a18_gt_18": float(np.mean((mbar_phase == ai_phase)[~low])) if (~low).any() else None,
-             "mbar_minus_aiat_nb_per_a18_mean": float(np.mean(mbar_phase - ai_phase) / 2.0),
+             "aiat_nb_le_18": float(np.mean((mbar_phase == ai_phase)[low])) if low.any() else None,
+             "aiat_nb_gt_18": float(np.mean((mbar_phase == ai_phase)[~low])) if (~low).any() else None,
+             "mbar_minus_aiat_nb_mean": float(np.mean(mbar_phase - ai_phase)),
              "grid": "10 T (200-650 K) x 31 mu (-2.4..-0.9 eV, 0.05 eV)"}
     ach = tm["bytes_accumulate"] / (tm["ms_accumulate"] / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     phases = []
     for q in range(len(kq)):
         i = int(np.argmax(rw["p"][q]))
-        phases.append({"T_K": round(kq[q] / kB), "mu_eV": mq[q], "most_probable_nb_per_a18": i / 2.0,
+        phases.append({"T_K": round(kq[q] / kB), "mu_eV": mq[q], "most_probable_nb": i,
                        "p": round(float(rw["p"][q, i]), 3)})
     g.close()
     # the oracle on the same run for a bounded number of steps, on the host cores
@@ -588,8 +590,8 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
         "warps_per_walker": wpw,
         "replica_exchange_steps": n_ex,
         "replica_exchange_acceptance": float(ex[1] / max(ex[0], 1)),
-        "mean_nb_per_a18": np.round(mean_nb.reshape(p.L, p.M) / 2.0, 1).tolist(),
-        "modal_nb_per_a18": {str(int(m) / 2.0): int(c) for m, c in zip(modes, counts)},
+        "mean_nb": np.round(mean_nb.reshape(p.L, p.M), 1).tolist(),
+        "modal_nb": {str(int(m)): int(c) for m, c in zip(modes, counts)},
         "energy_drift": drift,
         "l2": "flushed (256 MB memset) before every chunk of %d steps" % chunk,
         "structure": {
