@@ -479,6 +479,34 @@ def paper_structure_spec(p):
             "n_r": 49, "dr": 0.1}
 
 
+def rho_u_convergence(p, smp):
+    """The paper's convergence criterion (Sec. III.A: the density of
+    reduced-energy states rho(U), U = beta (E - mu N), no longer changes with
+    more steps) as a diagnostic: per state, the two-sample Kolmogorov-Smirnov
+    distance between the U samples of the first and second half of the
+    samples held, against its 1 % critical value 1.63 sqrt(2 / n)."""
+    st, N, E = smp["state"], smp["N"].astype(np.float64), smp["E"]
+    beta = 1.0 / np.asarray(p.kT)[st // p.M]
+    U = beta * (E - np.asarray(p.mu)[st % p.M] * N)
+    half = len(st) // 2
+    ks, ok = [], 0
+    for s in range(p.S):
+        a = np.sort(U[:half][st[:half] == s])
+        b = np.sort(U[half:][st[half:] == s])
+        if len(a) < 5 or len(b) < 5:
+            continue
+        grid = np.concatenate([a, b])
+        d = np.max(np.abs(np.searchsorted(a, grid, side="right") / len(a) -
+                          np.searchsorted(b, grid, side="right") / len(b)))
+        ks.append(d)
+        ok += d < 1.63 * np.sqrt((len(a) + len(b)) / (len(a) * len(b)))
+    ks = np.array(ks)
+    return {"states": int(len(ks)), "ks_median": float(np.median(ks)) if len(ks) else None,
+            "ks_max": float(np.max(ks)) if len(ks) else None,
+            "states_unchanged_at_1pct": int(ok),
+            "note": "samples are correlated (one per 100 steps), so the critical value is optimistic"}
+
+
 def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, cpu_seconds=8.0, seed=0,
                     sample_every=100):
     """The paper's whole LJ sampling run through regc_cycle: n_steps REGC steps
@@ -539,6 +567,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     # MBAR over the sub-sampled second half, per phase, at eight states: the
     # sampled corners and the two state points of the paper's g_xy figure
     n_samples = g.structure_count()
+    conv = rho_u_convergence(p, g.structure_get())
     kB = W.K_B_EV
     kq = np.array([kB * 200, kB * 650, kB * 200, kB * 650, kB * 200, kB * 600, kB * 425, kB * 300])
     mq = np.array([-0.9, -0.9, -2.4, -2.4, -1.3, -1.1, -1.5, -1.9])
@@ -600,6 +629,7 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
             "ms_weights": tm["ms_weights"], "ms_accumulate": tm["ms_accumulate"],
             "most_probable_phase": phases,
             "mbar_vs_aiat": agree,
+            "rho_u_convergence": conv,
             "roofline": {"bound": "hbm", "kernel": "accumulate_kernel", "achieved": ach, "peak": peak,
                          "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src,
                          "work": "%.4g algorithmic bytes per launch (%d samples x %d query states)"
