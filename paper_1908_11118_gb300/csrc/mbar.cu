@@ -343,7 +343,7 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
 // shorter.  An iterate whose residual grows past 100 times the best one so far
 // restarts the history from the best image.  Converged when max |r| < tol.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s) {
-    constexpr int kDepth = 8;
+    constexpr int kDepth = 16;
     const int S = m.S;
     cudaError_t err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
     if (err != cudaSuccess) return err;
