@@ -569,8 +569,12 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     n_samples = g.structure_count()
     conv = rho_u_convergence(p, g.structure_get())
     kB = W.K_B_EV
-    kq = np.array([kB * 200, kB * 650, kB * 200, kB * 650, kB * 200, kB * 600, kB * 425, kB * 300])
-    mq = np.array([-0.9, -0.9, -2.4, -2.4, -1.3, -1.1, -1.5, -1.9])
+    # the corner states, a few inside the grid, and the paper's two g_xy state
+    # points given as (T, p): (200 K, 2.03e-17 atm) and (600 K, 8.89e-2 atm)
+    from paper_1908_11118_gb300 import mu_of_pressure
+    kq = np.array([kB * 200, kB * 650, kB * 200, kB * 650, kB * 425, kB * 300, kB * 200, kB * 600])
+    mq = np.concatenate([[-0.9, -0.9, -2.4, -2.4, -1.5, -1.9],
+                         mu_of_pressure(kq[6:], np.array([2.03e-17, 8.89e-2]) * W.ATM_EV_PER_A3, p.lambda0)])
     t0 = time.perf_counter()
     rw = g.structure_reweight(kq, mq, 0, p.nmax, tol=1e-9, max_iter=200000)
     rw_s = time.perf_counter() - t0
@@ -592,8 +596,8 @@ def paper_cycle_arm(torch, stream, flush, n_steps, chunk=1000, x0=0.99, n_c=10, 
     phases = []
     for q in range(len(kq)):
         i = int(np.argmax(rw["p"][q]))
-        phases.append({"T_K": round(kq[q] / kB), "mu_eV": mq[q], "most_probable_nb": i,
-                       "p": round(float(rw["p"][q, i]), 3)})
+        phases.append({"T_K": round(kq[q] / kB), "mu_eV": round(float(mq[q]), 4), "most_probable_nb": i,
+                       "p": round(float(rw["p"][q, i]), 3), "p_nb_59": float(rw["p"][q, 59])})
     g.close()
     # the oracle on the same run for a bounded number of steps, on the host cores
     from oracle import oracle as O

@@ -345,6 +345,15 @@ REGC_API regc_status regc_warps_per_walker(const regc_handle *h, int *warps);
  * receives the state free energies (f_0 = 0).  Any output may be NULL.
  * Iterates until max |delta f| < tol or max_iter iterations; *iters, if not
  * NULL, receives the count.  FP64 log-sum-exp on the device.  Synchronous. */
+/* The ideal-gas reservoir of Sec. III.A: beta mu = beta mu0 + ln(beta p) with
+ * mu0 = kT ln Lambda^3, Lambda = lambda0 / sqrt(kT), i.e.
+ *   mu = kT (3 ln Lambda + ln(p / kT)),   p = (kT / Lambda^3) exp(mu / kT),
+ * p in the problem's units of energy per volume (eV / A^3 for eV and A; 1 atm
+ * = 6.3242e-7 eV / A^3).  n host values in, n out.  Errors: REGC_EINVAL (n < 0,
+ * a null pointer with n > 0, kT, p or lambda0 not positive, mu not finite). */
+REGC_API regc_status regc_mu_of_pressure(int n, const double *kT, const double *p, double lambda0, double *mu);
+REGC_API regc_status regc_pressure_of_mu(int n, const double *kT, const double *mu, double lambda0, double *p);
+
 REGC_API regc_status regc_reweight(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
                           double tol, int max_iter, double *N_mean, double *pN,
                           double *f_states, int *iters);

@@ -89,6 +89,8 @@ SIGNATURES = {
     "regc_structure_reset": ([_h], C.c_int),
     "regc_structure_timing": ([_h, _dp, _dp, _dp, _dp], C.c_int),
     "regc_aiat": ([_h, C.c_int, _dp, _dp, _dp, C.c_void_p], C.c_int),
+    "regc_mu_of_pressure": ([C.c_int, _dp, _dp, C.c_double, _dp], C.c_int),
+    "regc_pressure_of_mu": ([C.c_int, _dp, _dp, C.c_double, _dp], C.c_int),
     "regc_aiat_config": ([_h, C.c_int, _fp, C.POINTER(C.c_int32)], C.c_int),
     "regc_structure_get": ([_h, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p], C.c_int),

@@ -1218,6 +1218,23 @@ cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double
 
 extern "C" {
 
+regc_status regc_mu_of_pressure(int n, const double* kT, const double* p, double lambda0, double* mu) {
+    if (n < 0 || (n > 0 && (!kT || !p || !mu)) || !(lambda0 > 0.0) || !std::isfinite(lambda0)) return REGC_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!(kT[i] > 0.0) || !(p[i] > 0.0) || !std::isfinite(kT[i]) || !std::isfinite(p[i])) return REGC_EINVAL;
+    for (int i = 0; i < n; ++i) mu[i] = kT[i] * (3.0 * (log(lambda0) - 0.5 * log(kT[i])) + log(p[i] / kT[i]));
+    return REGC_OK;
+}
+
+regc_status regc_pressure_of_mu(int n, const double* kT, const double* mu, double lambda0, double* p) {
+    if (n < 0 || (n > 0 && (!kT || !mu || !p)) || !(lambda0 > 0.0) || !std::isfinite(lambda0)) return REGC_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!(kT[i] > 0.0) || !std::isfinite(kT[i]) || !std::isfinite(mu[i])) return REGC_EINVAL;
+    for (int i = 0; i < n; ++i)
+        p[i] = kT[i] * exp(mu[i] / kT[i] - 3.0 * (log(lambda0) - 0.5 * log(kT[i])));
+    return REGC_OK;
+}
+
 regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const double* mu_q, double tol, int max_iter,
                           double* N_mean, double* pN, double* f_states, int* iters) {
     if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;

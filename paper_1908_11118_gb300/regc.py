@@ -486,3 +486,23 @@ def mbar_solve_static(kT, mu, lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter
                                             _p(D, C.c_double), C.byref(it), _stream_handle(stream)),
           "regc_mbar_solve_static")
     return f, D, it.value
+
+
+def mu_of_pressure(kT, p, lambda0: float) -> np.ndarray:
+    """mu = kT (3 ln Lambda + ln(p / kT)) of the ideal-gas reservoir (regc_mu_of_pressure)."""
+    kT = np.ascontiguousarray(np.atleast_1d(kT), np.float64)
+    p = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(p), kT.shape), np.float64)
+    mu = np.zeros_like(kT)
+    check(_lib.lib().regc_mu_of_pressure(len(kT), _p(kT, C.c_double), _p(p, C.c_double), float(lambda0),
+                                         _p(mu, C.c_double)), "regc_mu_of_pressure")
+    return mu
+
+
+def pressure_of_mu(kT, mu, lambda0: float) -> np.ndarray:
+    """p = (kT / Lambda^3) exp(mu / kT) of the ideal-gas reservoir (regc_pressure_of_mu)."""
+    kT = np.ascontiguousarray(np.atleast_1d(kT), np.float64)
+    mu = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(mu), kT.shape), np.float64)
+    p = np.zeros_like(kT)
+    check(_lib.lib().regc_pressure_of_mu(len(kT), _p(kT, C.c_double), _p(mu, C.c_double), float(lambda0),
+                                         _p(p, C.c_double)), "regc_pressure_of_mu")
+    return p

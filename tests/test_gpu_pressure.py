@@ -1,0 +1,37 @@
+"""The ideal-gas reservoir relation of Sec. III.A in the library
+(regc_mu_of_pressure, regc_pressure_of_mu) against the oracle's, and the
+paper's own state point: with the B mass it implies, (200 K, 2.03e-17 atm)
+is the corner state (200 K, -0.9 eV)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mbar as OM
+from paper_1908_11118_gb300 import build as B
+from paper_1908_11118_gb300 import mu_of_pressure, pressure_of_mu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_pressure_relation_matches_oracle_and_round_trips():
+    rng = np.random.default_rng(0)
+    kT = rng.uniform(0.01, 2.0, 50)
+    p = 10.0 ** rng.uniform(-25, 0, 50)
+    for lam0 in (1.0, W.thermal_lambda0(W.PAPER_B_MASS_AMU)):
+        mu = mu_of_pressure(kT, p, lam0)
+        np.testing.assert_allclose(mu, OM.mu_from_pressure(kT, p, lam0), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(pressure_of_mu(kT, mu, lam0), p, rtol=1e-12)
+    with pytest.raises(Exception):
+        mu_of_pressure([1.0], [-1.0], 1.0)
+
+
+def test_paper_state_point():
+    lam0 = W.thermal_lambda0(W.PAPER_B_MASS_AMU)
+    mu = mu_of_pressure(W.K_B_EV * np.array([200.0, 600.0]), np.array([2.03e-17, 8.89e-2]) * W.ATM_EV_PER_A3, lam0)
+    assert abs(mu[0] + 0.9) < 1e-9
+    assert -1.0 < mu[1] < -0.95

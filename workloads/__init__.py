@@ -202,13 +202,31 @@ AMU_KG = 1.66053906660e-27
 EV_J = 1.602176634e-19
 
 
+ATM_EV_PER_A3 = 101325.0 / EV_J * 1e-30    # 1 atm in eV / A^3
+
+
+def mass_from_state_point(T_K: float, p_atm: float, mu_eV: float) -> float:
+    """The gas mass (u) for which the ideal-gas reservoir of Sec. III.A maps
+    (T, p) onto mu: mu = kT (3 ln Lambda + ln(p / kT)) fixes Lambda, and
+    Lambda = h / sqrt(2 pi m kT) fixes m."""
+    kT = K_B_EV * T_K
+    ln_lam = (mu_eV / kT - math.log(p_atm * ATM_EV_PER_A3 / kT)) / 3.0
+    lam_m = math.exp(ln_lam) * 1e-10
+    return PLANCK_J_S ** 2 / (2.0 * math.pi * kT * EV_J * lam_m ** 2) / AMU_KG
+
+
+# The paper does not give the mass of B, but states that (200 K, 2.03e-17 atm)
+# is exactly its corner state (200 K, -0.9 eV): that fixes m_B = 16.48 u.
+PAPER_B_MASS_AMU = mass_from_state_point(200.0, 2.03e-17, -0.9)
+
+
 def thermal_lambda0(mass_amu: float) -> float:
     """lambda0 in Angstrom eV^(1/2) such that Lambda(kT) = h / sqrt(2 pi m kT)
     = lambda0 / sqrt(kT) with kT in eV (Sec. II.A.1, the thermal wavelength)."""
     return PLANCK_J_S / math.sqrt(2.0 * math.pi * mass_amu * AMU_KG * EV_J) * 1e10
 
 
-def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = 39.948,
+def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = PAPER_B_MASS_AMU,
                 rc_over_sigma_ab: float = 2.5, zone: float = 48.0, seed: int = 0) -> Problem:
     """The paper's Lennard-Jones surface system (Sec. III.A, Appendix) in
     physical units: energies in eV, lengths in Angstrom, kT = k_B T in eV.
@@ -223,8 +241,9 @@ def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = 39.
     topmost A layer (hard walls at both ends).  The (T, mu) grid: L
     temperatures from 200 K in steps of 50 K, M chemical potentials from
     -2.4 eV in steps of 0.1 eV (10 x 16 = 160 replicas in the paper).
-    The paper gives neither the cutoff nor the mass of B: rc = 2.5 sigma_AB
-    and an argon mass are this workload's choices."""
+    The paper gives no cutoff: rc = 2.5 sigma_AB is this workload's choice.
+    The mass of B follows from the paper's own (T, p) <-> (T, mu) state point
+    (PAPER_B_MASS_AMU, 16.48 u)."""
     s = 11.489 / 3.0
     xyz, lx, ly, ztop = fcc111_slab(3, 6, 2, s)
     eps = np.zeros((4, 4))
@@ -243,7 +262,7 @@ def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = 39.
         n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_slab")
 
 
-def lj_a18_hex_slab(L: int = 10, M: int = 16, nmax: int = 160, mass_amu: float = 39.948,
+def lj_a18_hex_slab(L: int = 10, M: int = 16, nmax: int = 160, mass_amu: float = PAPER_B_MASS_AMU,
                     rc_over_sigma_ab: float = 2.5, zone: float = 48.0, seed: int = 0) -> Problem:
     """The paper's LJ surface system (Sec. III.A, Appendix) in its own cell:
     the 3 x 3 hexagonal supercell of the fcc(111) layer (lattice vectors of
