@@ -121,7 +121,8 @@ static double min_image(double d, double box)
 /* Nearest-image displacement a - b, Cartesian.  Coordinates are in the cell
  * frame (u, y, z): the lattice vectors of the cell are (Lx, 0) and
  * (shear Ly, Ly), so the Cartesian x of a cell-frame point is u + shear y
- * (shear = 0: a rectangular cell).  The nearest image is the shortest of the
+ * (shear = 0: a rectangular cell, where the reduced difference is the
+ * nearest image).  In a sheared cell the nearest image is the shortest of the
  * displacements to the images of b in the nine cells around the reduced
  * difference. */
 static void pair_vec(const oracle_system *sys, double xa, double ya, double za,
@@ -130,6 +131,13 @@ static void pair_vec(const oracle_system *sys, double xa, double ya, double za,
     double du = min_image(xa - xb, sys->Lx);
     double dv = (sys->mutation & 32) ? (ya - yb) : min_image(ya - yb, sys->Ly);
     double dz = sys->periodic_z ? min_image(za - zb, sys->Lz) : (za - zb);
+    if (sys->shear == 0.0) {
+        /* rectangular cell: the reduced difference is the nearest image */
+        d[0] = du;
+        d[1] = dv;
+        d[2] = dz;
+        return;
+    }
     int jr = (sys->mutation & 32) ? 0 : 1;
     double best = INFINITY;
     for (int j = -jr; j <= jr; ++j)
