@@ -15,10 +15,14 @@
 // phase indicator chi_i = [N = i]).
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <vector>
 
 #include "mbar.h"
+
+namespace cg = cooperative_groups;
 
 namespace regc {
 namespace {
@@ -159,29 +163,55 @@ __global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev 
     }
 }
 
-// f_new_s = -ln sum_b exp(lnH_b - a_s E_b - c_s N_b - D_b); one block of
-// kFThreads per state.
-constexpr int kFThreads = 1024;
-__global__ void __launch_bounds__(kFThreads) f_kernel(const __grid_constant__ MbarDev m) {
-    if (m.state[0]) return;
-    const int s = blockIdx.x;
-    const double a = m.a[s], c = m.c[s];
-    const float a32 = (float)a, c32 = (float)c;
-    float mx32 = -INFINITY;
-    for (int b = threadIdx.x; b < m.B; b += kFThreads) {
-        const float2 en = m.EN32[b];
-        mx32 = fmaxf(mx32, -fmaf(a32, en.x, c32 * en.y) - m.DH32[b]);
-    }
-    mx32 = (float)block_max((double)mx32);
-    const float th = mx32 - (float)kSkip - kMargin;
+// f_new_s = -ln sum_b exp(lnH_b - a_s E_b - c_s N_b - D_b).  A cluster of
+// kFSplit CTAs per state, each over a contiguous quarter of the bins (its own
+// binary32 screening: a term more than kSkip below the largest of its
+// quarter is also that far below the largest of all); the quarters' partial
+// sums meet in CTA rank 0 through distributed shared memory and are merged
+// in rank order (deterministic).
+constexpr int kFThreads = 256;
+constexpr int kFSplit = 4;
+__global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
+    f_kernel(const __grid_constant__ MbarDev m) {
+    __shared__ double part[2];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int s = blockIdx.x / kFSplit;
+    const bool live = !m.state[0];
     Lse L{-INFINITY, 0.0};
-    for (int b = threadIdx.x; b < m.B; b += kFThreads) {
-        const float2 en = m.EN32[b];
-        if (-fmaf(a32, en.x, c32 * en.y) - m.DH32[b] > th)
-            lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+    if (live) {
+        const int per = (m.B + kFSplit - 1) / kFSplit;
+        const int b0 = rank * per, b1 = min(m.B, b0 + per);
+        const double a = m.a[s], c = m.c[s];
+        const float a32 = (float)a, c32 = (float)c;
+        float mx32 = -INFINITY;
+        for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) {
+            const float2 en = m.EN32[b];
+            mx32 = fmaxf(mx32, -fmaf(a32, en.x, c32 * en.y) - m.DH32[b]);
+        }
+        mx32 = (float)block_max((double)mx32);
+        const float th = mx32 - (float)kSkip - kMargin;
+        for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) {
+            const float2 en = m.EN32[b];
+            if (-fmaf(a32, en.x, c32 * en.y) - m.DH32[b] > th)
+                lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+        }
+        L = block_merge(L);
     }
-    L = block_merge(L);
-    if (threadIdx.x == 0) m.f_new[s] = -(L.m + log(L.s));
+    if (threadIdx.x == 0) {
+        part[0] = L.m;
+        part[1] = L.s;
+    }
+    cluster.sync();
+    if (live && rank == 0 && threadIdx.x == 0) {
+        Lse T{-INFINITY, 0.0};
+        for (int r = 0; r < kFSplit; ++r) {
+            const double* pr = cluster.map_shared_rank(part, r);
+            T = lse_merge(T, Lse{pr[0], pr[1]});
+        }
+        m.f_new[s] = -(T.m + log(T.s));
+    }
+    cluster.sync();   // the partial sums stay readable until rank 0 has merged them
 }
 
 __global__ void __launch_bounds__(256) query_kernel(const __grid_constant__ MbarDev m, const double* a_q,
@@ -350,6 +380,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     err = cudaMemsetAsync(m.f, 0, size_t(S) * sizeof(double), s);
     if (err != cudaSuccess) return err;
     const int dgrid = (m.B + 255) / 256;
+    const int dgrid128 = (m.B + 127) / 128;   // a bin per thread, small blocks to spread over every SM
     en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32);
     std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
     std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
@@ -361,8 +392,8 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
             if (err != cudaSuccess) return err;
         }
-        d_kernel<<<dgrid, 256, 0, s>>>(m, 1);
-        f_kernel<<<S, kFThreads, 0, s>>>(m);
+        d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);
+        f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -454,7 +485,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     }
     err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return err;
-    d_kernel<<<dgrid, 256, 0, s>>>(m, 1);  // D_b of the final f
+    d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);  // D_b of the final f
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     // the host vectors go out of scope: wait for the copy that reads x
