@@ -54,6 +54,7 @@ struct regc_handle {
     int* d_error = nullptr;
     long long* d_fix = nullptr;               // scratch [S] for energy recomputes
     float* d_xyz = nullptr;                   // staging [S][nmax][3] for walker I/O
+    void* h_stage = nullptr;                  // pinned host staging: error word, [S] energies or labels
     size_t smem_per_walker = 0;
     // learned surrogate (delayed acceptance)
     bool has_sur = false;

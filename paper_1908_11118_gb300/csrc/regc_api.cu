@@ -50,10 +50,11 @@ regc_status upload(regc_handle* h, T* dst, const T* src, size_t count) {
 // Synchronise and fold the device error word into the sticky status.
 regc_status sync_check(regc_handle* h) {
     if (h->sticky != REGC_OK) return h->sticky;
-    int err = 0;
-    cudaError_t e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    int* flag = static_cast<int*>(h->h_stage);   // pinned: the copy stays asynchronous
+    cudaError_t e = cudaMemcpyAsync(flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
+    const int err = *flag;
     if (err & ERR_TIMEOUT) h->sticky = REGC_ETIMEOUT;
     else if (err & ERR_CAPACITY) h->sticky = REGC_ECAPACITY;
     else if (err & ERR_NUMERIC) h->sticky = REGC_ENUMERIC;
@@ -109,6 +110,7 @@ void regc_free(regc_handle* h) {
     cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) cudaFree(p);
     if (h->stc.block) cudaFree(h->stc.block);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
     delete h;
 }
 
@@ -433,6 +435,11 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &h->d_error, 1));
     TRY(dalloc(h, &h->d_fix, S));
     TRY(dalloc(h, &h->d_xyz, (size_t)S * grid->nmax * 3));
+    if (cudaHostAlloc(&h->h_stage, 64 + (size_t)S * 8, cudaHostAllocDefault) != cudaSuccess) {
+        h->h_stage = nullptr;
+        regc_free(h);
+        return REGC_ENOMEM;
+    }
     std::vector<int> ident(S);
     for (int s = 0; s < S; ++s) ident[s] = s;
     TRY(upload(h, d_sow, ident.data(), S));
@@ -674,8 +681,11 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
     const int S = h->S, nmax = h->nmax;
     for (int w = 0; w < S; ++w)
         if (n[w] < h->P.n_cluster || n[w] > nmax) return REGC_EINVAL;
-    std::vector<int> wos(S, -1);
+    // walker of each state, built in the pinned staging area (asynchronous copy)
+    int* flag = static_cast<int*>(h->h_stage);
+    int* wos = reinterpret_cast<int*>(static_cast<char*>(h->h_stage) + 64);
     if (sow) {
+        for (int k = 0; k < S; ++k) wos[k] = -1;
         for (int w = 0; w < S; ++w) {
             if (sow[w] < 0 || sow[w] >= S || wos[sow[w]] >= 0) return REGC_EINVAL;
             wos[sow[w]] = w;
@@ -688,15 +698,14 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
     if (e == cudaSuccess && sow)
         e = cudaMemcpyAsync(h->X.state_of_walker, sow, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && sow)
-        e = cudaMemcpyAsync(h->X.walker_of_state, wos.data(), S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(h->X.walker_of_state, wos, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = pack_walkers(h->d_xyz, h->P.n, S, nmax, h->P.g, h->P.pos, h->d_error, h->stream);
     if (e == cudaSuccess) e = launch_energy(h->P, h->P.efix, 1, h->stream);
-    int err = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
-    if (err & (ERR_OVERLAP | ERR_INPUT)) {
+    if (*flag & (ERR_OVERLAP | ERR_INPUT)) {
         // leave a consistent state behind: no walker holds particles
         cudaMemsetAsync(h->P.n, 0, S * sizeof(int), h->stream);
         cudaMemsetAsync(h->P.efix, 0, S * sizeof(long long), h->stream);
@@ -735,7 +744,7 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
-    std::vector<long long> ef;
+    long long* ef = reinterpret_cast<long long*>(static_cast<char*>(h->h_stage) + 64);   // pinned
     cudaError_t e = cudaSuccess;
     if (pos) {
         e = unpack_walkers(h->P.pos, (long long)S * nmax, h->d_xyz, h->stream);
@@ -744,10 +753,8 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
                                 h->stream);
     }
     if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, h->P.n, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (energy && e == cudaSuccess) {
-        ef.resize(S);
-        e = cudaMemcpyAsync(ef.data(), h->P.efix, S * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
-    }
+    if (energy && e == cudaSuccess)
+        e = cudaMemcpyAsync(ef, h->P.efix, S * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
     if (sow && e == cudaSuccess)
         e = cudaMemcpyAsync(sow, h->X.state_of_walker, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);

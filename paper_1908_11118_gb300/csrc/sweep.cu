@@ -945,59 +945,179 @@ __device__ __forceinline__ void disp_exact(const Geometry& g, float4 q, float4 p
     dz = g.periodic_z ? min_image_exact(q.z, p.z, g.Lz, g.hLz) : __fsub_rn(q.z, p.z);
 }
 
-// From-scratch energy of every walker: all pairs i < j and all particle-surface
-// pairs, with the nearest periodic image.  One CTA of kEnergyWarps warps per
-// walker, warp k taking particles i = k mod kEnergyWarps; the surface partners
-// of a particle come from its column of the surface table, exactly as in the
-// sweep.  Every pair within rc gets the same rounded displacement, hence the
-// same fixed-point term, as in the sweep, and fixed-point sums do not depend on
-// the order, so the result equals the sweep's running total exactly.
-constexpr int kEnergyWarps = 4;
+// From-scratch energy of every walker: every unordered pair of particles and
+// every particle-surface pair, with the nearest periodic image.  A walker gets
+// kEnergySplit CTAs of kEnergyThreads threads; its positions are staged in
+// shared memory.  Two enumerations of the mobile pairs:
+//
+// * cells (the cell grid of the sweep has at least three cells along every
+//   periodic axis, so the 27 cells around a cell are distinct): every CTA
+//   builds the walker's cell list (shared-memory atomics; the order inside a
+//   cell does not matter) and takes items (i, o) -- particle i against the
+//   o-th cell of the forward half of its stencil (o = 0: its own cell, partners
+//   j > i; o = 1..13: the 13 offsets after (0, 0, 0) in (z, y, x) order) --
+//   which lists every pair within rc once;
+// * all pairs (small periodic boxes, or a cell over capacity): the circulant
+//   order (i, i + d mod N), d = 1 .. floor(N / 2) (for even N the offset N / 2
+//   only from i < N / 2), which lists each unordered pair once and gives every
+//   particle the same number of partners.
+//
+// Consecutive threads take consecutive items.  The displacement is
+// antisymmetric under exchange of the pair (min_image_exact and cart_dx round
+// -x to -fl(x)), so r^2, hence every pair term, is the one the sweep computes
+// for that pair.  The surface partners of a particle come from its column of
+// the surface table, one warp per particle, exactly as in the sweep.  Partial
+// sums are folded to 64 bits before the int32 parts of a Fix3 can overflow and
+// added to the walker's total with a 64-bit integer atomic: fixed-point sums do
+// not depend on the order, so the result is deterministic and equals the
+// sweep's running total exactly.
+constexpr int kEnergyThreads = 256;
+constexpr int kEnergySplit = 4;
+constexpr int kEnergyTeam = kEnergySplit * kEnergyThreads;
+constexpr int kFoldEvery = 256;   // pair terms per thread between folds (|lo| < 2^21 per term)
 
-__global__ void __launch_bounds__(32 * kEnergyWarps) energy_kernel(const __grid_constant__ SweepParams P,
-                                                                   long long* out, int check_overlap) {
-    __shared__ long long part[kEnergyWarps];
-    __shared__ int ovl[kEnergyWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = blockIdx.x;
-    const int N = P.n[w];
-    const float4* pos = P.pos + size_t(w) * P.nmax;
-    long long total = 0;
-    int n_in = 0, overlap = 0;
+struct EnergyAcc {
+    Fix3 acc;
+    long long total;
+    int folds, n_in, overlap;
+    __device__ __forceinline__ void add(float phi) {
+        fix_add(acc, phi, 1);
+        if (++folds == kFoldEvery) fold();
+    }
+    __device__ __forceinline__ void fold() {
+        total += fix_value(acc.big, acc.hi, acc.lo);
+        acc = Fix3{0, 0, 0};
+        folds = 0;
+    }
+};
+
+__device__ __forceinline__ void energy_pair(const SweepParams& P, const float4* sp, int i, int j, EnergyAcc& a) {
+    const bool iA = i < P.n_cluster, jA = j < P.n_cluster;
+    const PairTab& tp = iA ? (jA ? P.gA : P.gAB) : (jA ? P.gAB : P.gg);
     float dx, dy, dz;
-    for (int i = warp; i < N; i += kEnergyWarps) {
-        Fix3 acc{0, 0, 0};
-        const float4 pi = pos[i];
-        const bool iA = i < P.n_cluster;
-        for (int j = i + 1 + lane; j < N; j += 32) {
-            const bool jA = j < P.n_cluster;
-            const PairTab& t = iA ? (jA ? P.gA : P.gAB) : (jA ? P.gAB : P.gg);
-            disp_exact(P.g, pi, pos[j], dx, dy, dz);
-            fix_add(acc, pair_phi(dx, dy, dz, P.g.rc2, t, n_in, overlap), 1);
+    disp_exact(P.g, sp[i], sp[j], dx, dy, dz);
+    a.add(pair_phi(dx, dy, dz, P.g.rc2, tp, a.n_in, a.overlap));
+}
+
+__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_constant__ SweepParams P,
+                                                                unsigned long long* out, int check_overlap,
+                                                                int use_cells) {
+    extern __shared__ float4 sp[];   // [nmax] positions (w: packed cell), then cnt [ncell], slots [ncell][cap]
+    __shared__ long long part[kEnergyThreads / 32];
+    __shared__ int ovl[kEnergyThreads / 32];
+    int* cnt = reinterpret_cast<int*>(sp + P.nmax);
+    uint16_t* slots = reinterpret_cast<uint16_t*>(cnt + ((P.cg.ncell + 3) & ~3));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = blockIdx.x / kEnergySplit, c = blockIdx.x % kEnergySplit;
+    const int N = P.n[w];
+    const int t = c * kEnergyThreads + threadIdx.x;
+    const float4* pos = P.pos + size_t(w) * P.nmax;
+    if (use_cells)
+        for (int k = threadIdx.x; k < P.cg.ncell; k += kEnergyThreads) cnt[k] = 0;
+    for (int i = threadIdx.x; i < N; i += kEnergyThreads) {
+        float4 q = pos[i];
+        if (use_cells) {
+            const Cell3 cc = cell3_of(P, q.x, q.y, q.z);
+            q.w = __uint_as_float((unsigned)cc.x | ((unsigned)cc.y << 10) | ((unsigned)cc.z << 20));
         }
+        sp[i] = q;
+    }
+    __syncthreads();
+    bool cells = false;
+    if (use_cells) {
+        int full = 0;
+        for (int i = threadIdx.x; i < N; i += kEnergyThreads) {
+            const unsigned b = __float_as_uint(sp[i].w);
+            const int cell = (int)(((b >> 20) * P.cg.ncy + ((b >> 10) & 1023u)) * P.cg.ncx + (b & 1023u));
+            const int k = atomicAdd(cnt + cell, 1);
+            if (k < P.cg.cap) slots[cell * P.cg.cap + k] = (uint16_t)i;
+            else full = 1;
+        }
+        cells = !__syncthreads_or(full);   // identical in every CTA of the walker (counts are)
+    }
+    EnergyAcc a{{0, 0, 0}, 0, 0, 0, 0};
+    if (cells) {
+        // item k = 14 i + o; this thread takes k = t, t + T, ... (one division)
+        int i = t / 14, o = t % 14;
+        constexpr int qT = kEnergyTeam / 14, rT = kEnergyTeam % 14;
+        while (i < N) {
+            const unsigned b = __float_as_uint(sp[i].w);
+            const int idx = 13 + o;   // offset (ox, oy, oz) = (idx % 3, idx / 3 % 3, idx / 9) - 1
+            int nx = (int)(b & 1023u) + idx % 3 - 1;
+            int ny = (int)((b >> 10) & 1023u) + (idx / 3) % 3 - 1;
+            int nz = (int)(b >> 20) + idx / 9 - 1;
+            if (nx < 0) nx += P.cg.ncx;
+            else if (nx >= P.cg.ncx) nx -= P.cg.ncx;
+            if (ny < 0) ny += P.cg.ncy;
+            else if (ny >= P.cg.ncy) ny -= P.cg.ncy;
+            bool ok = true;
+            if (nz >= P.cg.ncz) {
+                if (P.g.periodic_z) nz -= P.cg.ncz;
+                else ok = false;
+            }
+            if (ok) {
+                const int cell = (nz * P.cg.ncy + ny) * P.cg.ncx + nx;
+                const int n_c = cnt[cell];
+                const uint16_t* sl = slots + cell * P.cg.cap;
+                for (int m = 0; m < n_c; ++m) {
+                    const int j = sl[m];
+                    if (o == 0 && j <= i) continue;
+                    energy_pair(P, sp, i, j, a);
+                }
+            }
+            o += rT;
+            i += qT;
+            if (o >= 14) {
+                o -= 14;
+                i += 1;
+            }
+        }
+    } else if (N >= 2) {
+        // item k = (d - 1) N + i, d = 1 .. D
+        const int D = N >> 1;
+        int i = t % N, d = t / N + 1;
+        const int qT = kEnergyTeam / N, rT = kEnergyTeam % N;
+        const bool even = (N & 1) == 0;
+        while (d <= D) {
+            if (!(even && d == D && i >= D)) {
+                int j = i + d;
+                if (j >= N) j -= N;
+                energy_pair(P, sp, i, j, a);
+            }
+            i += rT;
+            d += qT;
+            if (i >= N) {
+                i -= N;
+                d += 1;
+            }
+        }
+    }
+    a.fold();
+    // surface partners: one warp per particle
+    for (int i = c * (kEnergyThreads / 32) + warp; i < N; i += kEnergyTeam / 32) {
+        const float4 pi = sp[i];
         if (near_surface(P, pi.z)) {
             int n_cand = 0;
-            surface_pass<1, true>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, acc, n_in,
-                                  n_cand, overlap, lane, iA);
+            surface_pass<1, true>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, a.acc,
+                                  a.n_in, n_cand, a.overlap, lane, i < P.n_cluster);
+            a.fold();
         }
-        // fold into 64 bits per particle, so that the int32 parts cannot overflow
-        total += fix_value(acc.big, acc.hi, acc.lo);
     }
-    total = warp_sum_ll(total);
-    overlap = __any_sync(FULL, overlap);
+    const long long total = warp_sum_ll(a.total);
+    const int overlap = __any_sync(FULL, a.overlap);
     if (lane == 0) {
         part[warp] = total;
         ovl[warp] = overlap;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long t = 0;
+        long long tsum = 0;
         int o = 0;
-        for (int k = 0; k < kEnergyWarps; ++k) {
-            t += part[k];
+        for (int k = 0; k < kEnergyThreads / 32; ++k) {
+            tsum += part[k];
             o |= ovl[k];
         }
-        out[w] = t;
+        if (tsum != 0) atomicAdd(out + w, (unsigned long long)tsum);   // two's complement: exact
         if (o && check_overlap) atomicOr(P.error, check_overlap == 2 ? ERR_NUMERIC : ERR_OVERLAP);
     }
 }
@@ -1096,7 +1216,20 @@ cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
 }
 
 cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overlap, cudaStream_t s) {
-    energy_kernel<<<P.S, 32 * kEnergyWarps, 0, s>>>(P, out, check_overlap);
+    constexpr size_t kMaxSmem = 232448;   // 227 KB per block
+    const size_t base = size_t(P.nmax) * sizeof(float4);
+    const size_t with_cells = base + size_t((P.cg.ncell + 3) & ~3) * 4 + size_t(P.cg.ncell) * P.cg.cap * 2;
+    // cells: 27 distinct stencil cells, cell coordinates packed in 10 bits each
+    const int use_cells = P.cg.ncx >= 3 && P.cg.ncy >= 3 && (!P.g.periodic_z || P.cg.ncz >= 3) &&
+                          P.cg.ncx < 1024 && P.cg.ncy < 1024 && P.cg.ncz < 1024 && with_cells + 1024 <= kMaxSmem;
+    const size_t smem = use_cells ? with_cells : base;
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024)
+        e = cudaFuncSetAttribute(energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, size_t(P.S) * sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    energy_kernel<<<P.S * kEnergySplit, kEnergyThreads, smem, s>>>(P, reinterpret_cast<unsigned long long*>(out),
+                                                                   check_overlap, use_cells);
     return cudaGetLastError();
 }
 
