@@ -362,6 +362,109 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
     if (b < B) lnH[b] = log(H[b]);
 }
 
+// ---- iterations on the kernel matrix
+// With every state sampled, the map can be iterated in linear space: for a
+// reference point f_ref (the iterate at the last build),
+//   K_sb = exp(t_sb - M_b),  t_sb = ln Omega_s + f_ref,s - u_s(b),  M_b = max_s t_sb,
+// so that with w_s = exp(f_s - f_ref,s)
+//   D_b = M_b + ln d_b,  d_b = sum_s K_sb w_s,
+//   f_new,s = ln Omega_s + f_ref,s - ln sum_b (H_b / d_b) K_sb.
+// Each map is then two FP64 matrix-vector products over a matrix built once
+// per reference point (one exponential per entry), instead of S B
+// exponentials.  The reference moves with the iterate: once some
+// |f_s - f_ref,s| exceeds kRebuild the matrix is rebuilt, so w stays within
+// e^(+-kRebuild) and d_b >= e^-kRebuild (the largest entry of a column is 1),
+// far from the FP64 range limits (e^-708 .. e^709); a sum of positive terms
+// keeps its relative accuracy whatever their spread.  Entries below e^-708
+// (subnormal or zero) weigh less than e^(-708 + 2 kRebuild) = e^-108 against
+// the sums they enter.  The build (one FP64 exponential per entry) costs
+// about ten maps, so the bound is set wide.
+constexpr double kRebuild = 300.0;
+constexpr size_t kMatBytes = size_t(2) << 30;
+
+struct MatDev {
+    double* K;      // [S][B]
+    double* M;      // [B]
+    double* V;      // [B] H_b / d_b of the last map
+    double* fref;   // [S]
+};
+
+// One thread per bin: t_sb over the states (tiled through shared memory),
+// M_b, then the column of K.  Block 0 records f_ref = f.
+__global__ void __launch_bounds__(256) mat_build_kernel(const __grid_constant__ MbarDev m, MatDev k) {
+    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = b < m.B;
+    if (blockIdx.x == 0)
+        for (int q = threadIdx.x; q < m.S; q += blockDim.x) k.fref[q] = m.f[q];
+    const double E = act ? m.E_b[b] : 0.0;
+    const double N = act ? (double)m.N_b[b] : 0.0;
+    double M = -INFINITY;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int k0 = 0; k0 < m.S; k0 += kDTile) {
+            const int nk = min(kDTile, m.S - k0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < nk; q += blockDim.x) {
+                sa[q] = m.a[k0 + q];
+                sc[q] = m.c[k0 + q];
+                sg[q] = m.lnom[k0 + q] + m.f[k0 + q];
+            }
+            __syncthreads();
+            if (!act) continue;
+            if (pass == 0) {
+                for (int q = 0; q < nk; ++q) M = fmax(M, sg[q] - fma(sa[q], E, sc[q] * N));
+            } else {
+                for (int q = 0; q < nk; ++q) k.K[size_t(k0 + q) * m.B + b] = exp(sg[q] - fma(sa[q], E, sc[q] * N) - M);
+            }
+        }
+    }
+    if (act) k.M[b] = M;
+}
+
+// One thread per bin: d_b = sum_s K_sb w_s, V_b = H_b / d_b.
+__global__ void __launch_bounds__(128) mat_d_kernel(const __grid_constant__ MbarDev m, MatDev k) {
+    __shared__ double sw[kDTile];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = b < m.B;
+    double d = 0.0;
+    for (int k0 = 0; k0 < m.S; k0 += kDTile) {
+        const int nk = min(kDTile, m.S - k0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nk; q += blockDim.x) sw[q] = exp(m.f[k0 + q] - k.fref[k0 + q]);
+        __syncthreads();
+        if (!act) continue;
+        const double* col = k.K + size_t(k0) * m.B + b;
+        for (int q = 0; q < nk; ++q) d = fma(col[size_t(q) * m.B], sw[q], d);
+    }
+    if (act) k.V[b] = exp(m.lnH[b]) / d;
+}
+
+// f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb: a cluster of kFSplit
+// CTAs per state, each over a contiguous quarter of the row; the quarters'
+// sums meet in CTA rank 0 through distributed shared memory, added in rank
+// order (deterministic).
+__global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
+    mat_f_kernel(const __grid_constant__ MbarDev m, MatDev k) {
+    __shared__ double part;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int s = blockIdx.x / kFSplit;
+    const int per = (m.B + kFSplit - 1) / kFSplit;
+    const int b0 = rank * per, b1 = min(m.B, b0 + per);
+    const double* row = k.K + size_t(s) * m.B;
+    double acc = 0.0;
+    for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) acc = fma(k.V[b], row[b], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part = acc;
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int r = 0; r < kFSplit; ++r) t += *cluster.map_shared_rank(&part, r);
+        m.f_new[s] = m.lnom[s] + k.fref[s] - log(t);
+    }
+    cluster.sync();   // the partial sums stay readable until rank 0 has added them
+}
+
 }  // namespace
 
 // The self-consistent map G(f) = gauge(f_new(D(f))) is iterated with
@@ -372,7 +475,8 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
 // is the one of the plain iteration (x = G(x)); only the path to it is
 // shorter.  An iterate whose residual grows past 100 times the best one so far
 // restarts the history from the best image.  Converged when max |r| < tol.
-cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s) {
+cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s,
+                           bool allow_matrix) {
     constexpr int kDepth = 16;
     const int S = m.S;
     cudaError_t err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
@@ -382,6 +486,36 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     const int dgrid = (m.B + 255) / 256;
     const int dgrid128 = (m.B + 127) / 128;   // a bin per thread, small blocks to spread over every SM
     en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32);
+    // the kernel matrix, when every state is sampled and it fits
+    MatDev mat{};
+    void* mat_block = nullptr;
+    const size_t mat_doubles = size_t(S) * m.B + 2 * size_t(m.B) + size_t(S);
+    if (allow_matrix && mat_doubles * sizeof(double) <= kMatBytes) {
+        std::vector<double> lnom_h(S);
+        err = cudaMemcpyAsync(lnom_h.data(), m.lnom, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) return err;
+        bool all_sampled = true;
+        for (int k = 0; k < S; ++k) all_sampled = all_sampled && std::isfinite(lnom_h[k]);
+        if (all_sampled) {
+            if (cudaMallocAsync(&mat_block, mat_doubles * sizeof(double), s) == cudaSuccess) {
+                double* p = static_cast<double*>(mat_block);
+                mat = MatDev{p, p + size_t(S) * m.B, p + size_t(S) * m.B + m.B, p + size_t(S) * m.B + 2 * size_t(m.B)};
+            } else {
+                mat_block = nullptr;
+                (void)cudaGetLastError();   // out of memory is not sticky: iterate on log-sum-exps
+            }
+        }
+    }
+    struct FreeOnExit {
+        void* p;
+        cudaStream_t s;
+        ~FreeOnExit() {
+            if (p) cudaFreeAsync(p, s);
+        }
+    } free_mat{mat_block, s};
+    std::vector<double> fref_h(S, 0.0);
+    bool build = true;
     std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
     std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
     std::vector<double> r_prev, g_prev;
@@ -392,8 +526,20 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
             if (err != cudaSuccess) return err;
         }
-        d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);
-        f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m);
+        if (mat.K) {
+            double drift = 0.0;
+            for (int k = 0; k < S; ++k) drift = fmax(drift, fabs(x[k] - fref_h[k]));
+            if (build || !(drift <= kRebuild)) {
+                mat_build_kernel<<<dgrid, 256, 0, s>>>(m, mat);
+                fref_h = x;
+                build = false;
+            }
+            mat_d_kernel<<<dgrid128, 128, 0, s>>>(m, mat);
+            mat_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, mat);
+        } else {
+            d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);
+            f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m);
+        }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -29,8 +29,12 @@ struct MbarDev {
 // Solve the self-consistent equations from f = 0 (the plain fixed-point map
 // with Anderson acceleration) until max |G(f) - f| < tol or max_iter maps.
 // Synchronises the stream after every map.
+// With allow_matrix (and every state sampled, and S B doubles within 2 GiB)
+// the iterations run on the kernel matrix K_sb = exp(-u_s(b) + ln Omega_s +
+// f_ref,s - max_k(...)), allocated on the stream for the duration of the call;
+// otherwise (or when the allocation fails) on log-sum-exps of the energies.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out,
-                           cudaStream_t s);
+                           cudaStream_t s, bool allow_matrix = true);
 
 // Reweight to Q query states given on the device as (a_q, c_q):
 // N_mean [Q], pN [Q][nmax+1], f_q [Q] (device, any may be null).

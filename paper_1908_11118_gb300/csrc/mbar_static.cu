@@ -112,7 +112,7 @@ extern "C" regc_status regc_mbar_solve_static(int S, const double* kT, const dou
     m.state = state;
     // mbar_solve_dev clears f and the convergence state before iterating, so
     // nothing left in the scratch area by an earlier call is read.
-    e = regc::mbar_solve_dev(m, tol, max_iter, iters, s);
+    e = regc::mbar_solve_dev(m, tol, max_iter, iters, s, false);   // no device allocation
     if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, fd, S * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && D) e = cudaMemcpyAsync(D, Dd, B * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
