@@ -387,6 +387,7 @@ struct MatDev {
     double* M;      // [B]
     double* V;      // [B] H_b / d_b of the last map
     double* fref;   // [S]
+    double* w;      // [S] exp(f_s - f_ref,s) of the current iterate (from the host)
 };
 
 // One thread per bin: t_sb over the states (tiled through shared memory),
@@ -421,22 +422,38 @@ __global__ void __launch_bounds__(256) mat_build_kernel(const __grid_constant__ 
     if (act) k.M[b] = M;
 }
 
-// One thread per bin: d_b = sum_s K_sb w_s, V_b = H_b / d_b.
-__global__ void __launch_bounds__(128) mat_d_kernel(const __grid_constant__ MbarDev m, MatDev k) {
+// d_b = sum_s K_sb w_s, V_b = H_b / d_b.  A block takes 32 bins; its
+// kDGroups warps take every kDGroups-th state (two independent FMA chains
+// each), and the partial sums of a bin are added in a fixed order.  Rows of
+// K are read 32 consecutive bins (256 bytes) at a time.
+constexpr int kDGroups = 4;
+__global__ void __launch_bounds__(32 * kDGroups) mat_d_kernel(const __grid_constant__ MbarDev m, MatDev k) {
     __shared__ double sw[kDTile];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double part[kDGroups][32];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
     const bool act = b < m.B;
-    double d = 0.0;
+    double d0 = 0.0, d1 = 0.0;
     for (int k0 = 0; k0 < m.S; k0 += kDTile) {
         const int nk = min(kDTile, m.S - k0);
         __syncthreads();
-        for (int q = threadIdx.x; q < nk; q += blockDim.x) sw[q] = exp(m.f[k0 + q] - k.fref[k0 + q]);
+        for (int q = threadIdx.x; q < nk; q += blockDim.x) sw[q] = k.w[k0 + q];
         __syncthreads();
         if (!act) continue;
         const double* col = k.K + size_t(k0) * m.B + b;
-        for (int q = 0; q < nk; ++q) d = fma(col[size_t(q) * m.B], sw[q], d);
+        int q = grp;
+        for (; q + kDGroups < nk; q += 2 * kDGroups) {
+            d0 = fma(col[size_t(q) * m.B], sw[q], d0);
+            d1 = fma(col[size_t(q + kDGroups) * m.B], sw[q + kDGroups], d1);
+        }
+        if (q < nk) d0 = fma(col[size_t(q) * m.B], sw[q], d0);
     }
-    if (act) k.V[b] = exp(m.lnH[b]) / d;
+    part[grp][lane] = d0 + d1;
+    __syncthreads();
+    if (grp == 0 && act) {
+        const double d = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+        k.V[b] = exp(m.lnH[b]) / d;
+    }
 }
 
 // f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb: a cluster of kFSplit
@@ -489,7 +506,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     // the kernel matrix, when every state is sampled and it fits
     MatDev mat{};
     void* mat_block = nullptr;
-    const size_t mat_doubles = size_t(S) * m.B + 2 * size_t(m.B) + size_t(S);
+    const size_t mat_doubles = size_t(S) * m.B + 2 * size_t(m.B) + 2 * size_t(S);
     if (allow_matrix && mat_doubles * sizeof(double) <= kMatBytes) {
         std::vector<double> lnom_h(S);
         err = cudaMemcpyAsync(lnom_h.data(), m.lnom, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -500,7 +517,8 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
         if (all_sampled) {
             if (cudaMallocAsync(&mat_block, mat_doubles * sizeof(double), s) == cudaSuccess) {
                 double* p = static_cast<double*>(mat_block);
-                mat = MatDev{p, p + size_t(S) * m.B, p + size_t(S) * m.B + m.B, p + size_t(S) * m.B + 2 * size_t(m.B)};
+                double* q = p + size_t(S) * m.B;
+                mat = MatDev{p, q, q + m.B, q + 2 * size_t(m.B), q + 2 * size_t(m.B) + S};
             } else {
                 mat_block = nullptr;
                 (void)cudaGetLastError();   // out of memory is not sticky: iterate on log-sum-exps
@@ -514,7 +532,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             if (p) cudaFreeAsync(p, s);
         }
     } free_mat{mat_block, s};
-    std::vector<double> fref_h(S, 0.0);
+    std::vector<double> fref_h(S, 0.0), w_h(S);
     bool build = true;
     std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
     std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
@@ -534,7 +552,10 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
                 fref_h = x;
                 build = false;
             }
-            mat_d_kernel<<<dgrid128, 128, 0, s>>>(m, mat);
+            for (int k = 0; k < S; ++k) w_h[k] = exp(x[k] - fref_h[k]);
+            err = cudaMemcpyAsync(mat.w, w_h.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (err != cudaSuccess) return err;
+            mat_d_kernel<<<(m.B + 31) / 32, 32 * kDGroups, 0, s>>>(m, mat);
             mat_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, mat);
         } else {
             d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);
