@@ -991,20 +991,20 @@ struct EnergyAcc {
     }
 };
 
+template <bool CL>
 __device__ __forceinline__ void energy_pair(const SweepParams& P, const float4* sp, int i, int j, EnergyAcc& a) {
-    const bool iA = i < P.n_cluster, jA = j < P.n_cluster;
+    const bool iA = CL && i < P.n_cluster, jA = CL && j < P.n_cluster;
     const PairTab& tp = iA ? (jA ? P.gA : P.gAB) : (jA ? P.gAB : P.gg);
     float dx, dy, dz;
     disp_exact(P.g, sp[i], sp[j], dx, dy, dz);
     a.add(pair_phi(dx, dy, dz, P.g.rc2, tp, a.n_in, a.overlap));
 }
 
+template <bool CL>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_constant__ SweepParams P,
                                                                 unsigned long long* out, int check_overlap,
                                                                 int use_cells) {
     extern __shared__ float4 sp[];   // [nmax] positions (w: packed cell), then cnt [ncell], slots [ncell][cap]
-    __shared__ long long part[kEnergyThreads / 32];
-    __shared__ int ovl[kEnergyThreads / 32];
     int* cnt = reinterpret_cast<int*>(sp + P.nmax);
     uint16_t* slots = reinterpret_cast<uint16_t*>(cnt + ((P.cg.ncell + 3) & ~3));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1062,7 +1062,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
                 for (int m = 0; m < n_c; ++m) {
                     const int j = sl[m];
                     if (o == 0 && j <= i) continue;
-                    energy_pair(P, sp, i, j, a);
+                    energy_pair<CL>(P, sp, i, j, a);
                 }
             }
             o += rT;
@@ -1082,7 +1082,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
             if (!(even && d == D && i >= D)) {
                 int j = i + d;
                 if (j >= N) j -= N;
-                energy_pair(P, sp, i, j, a);
+                energy_pair<CL>(P, sp, i, j, a);
             }
             i += rT;
             d += qT;
@@ -1098,27 +1098,18 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
         const float4 pi = sp[i];
         if (near_surface(P, pi.z)) {
             int n_cand = 0;
-            surface_pass<1, true>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, a.acc,
-                                  a.n_in, n_cand, a.overlap, lane, i < P.n_cluster);
+            surface_pass<1, CL>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, a.acc,
+                                a.n_in, n_cand, a.overlap, lane, CL && i < P.n_cluster);
             a.fold();
         }
     }
+    // each warp adds its share (two's complement: exact, in any order) and
+    // leaves; no barrier after the items, so a warp that finished early exits
     const long long total = warp_sum_ll(a.total);
     const int overlap = __any_sync(FULL, a.overlap);
     if (lane == 0) {
-        part[warp] = total;
-        ovl[warp] = overlap;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long tsum = 0;
-        int o = 0;
-        for (int k = 0; k < kEnergyThreads / 32; ++k) {
-            tsum += part[k];
-            o |= ovl[k];
-        }
-        if (tsum != 0) atomicAdd(out + w, (unsigned long long)tsum);   // two's complement: exact
-        if (o && check_overlap) atomicOr(P.error, check_overlap == 2 ? ERR_NUMERIC : ERR_OVERLAP);
+        if (total != 0) atomicAdd(out + w, (unsigned long long)total);
+        if (overlap && check_overlap) atomicOr(P.error, check_overlap == 2 ? ERR_NUMERIC : ERR_OVERLAP);
     }
 }
 
@@ -1223,13 +1214,14 @@ cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overla
     const int use_cells = P.cg.ncx >= 3 && P.cg.ncy >= 3 && (!P.g.periodic_z || P.cg.ncz >= 3) &&
                           P.cg.ncx < 1024 && P.cg.ncy < 1024 && P.cg.ncz < 1024 && with_cells + 1024 <= kMaxSmem;
     const size_t smem = use_cells ? with_cells : base;
+    // the pair tables of a second species only where the walkers hold a cluster
+    auto kernel = P.n_cluster > 0 ? energy_kernel<true> : energy_kernel<false>;
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024)
-        e = cudaFuncSetAttribute(energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, size_t(P.S) * sizeof(long long), s);
     if (e != cudaSuccess) return e;
-    energy_kernel<<<P.S * kEnergySplit, kEnergyThreads, smem, s>>>(P, reinterpret_cast<unsigned long long*>(out),
-                                                                   check_overlap, use_cells);
+    kernel<<<P.S * kEnergySplit, kEnergyThreads, smem, s>>>(P, reinterpret_cast<unsigned long long*>(out),
+                                                            check_overlap, use_cells);
     return cudaGetLastError();
 }
 
