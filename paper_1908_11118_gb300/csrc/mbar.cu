@@ -15,6 +15,8 @@
 // phase indicator chi_i = [N = i]).
 #include <math.h>
 
+#include <cmath>
+
 #include <cooperative_groups.h>
 
 #include <algorithm>
