@@ -5,11 +5,16 @@
 //   D_b = ln sum_k Omega_k exp(f_k - u_k(b))        (one thread per bin)
 //   f_s = -ln sum_b H_b exp(-u_s(b) - D_b)           (one block per state)
 // with f_0 = 0 after each iteration, accelerated by Anderson mixing on the
-// host (mbar_solve_dev).  Sums are log-sum-exp in FP64 over the terms within
-// 50 of the largest (the others weigh less than the FP64 rounding of the sum),
-// found by a binary32 screening pass, so that with well separated states a
-// bin costs a few FP64 terms rather than one per state; the query keeps an
-// online maximum over all terms.
+// host (mbar_solve_dev).  Two forms of the map:
+// * on a kernel matrix K_sb (every state sampled, the matrix within its
+//   memory bound): each map is two FP64 matrix-vector products, the matrix
+//   rebuilt when the iterate has moved far from the point it was built at;
+// * log-sum-exp in FP64 over the terms within 50 of the largest (the others
+//   weigh less than the FP64 rounding of the sum), found by a binary32
+//   screening pass, so that with well separated states a bin costs a few FP64
+//   terms rather than one per state (the allocation-free solve, and the final
+//   D_b of either form).
+// The query keeps an online maximum over all terms.
 // Query states reuse the D_b: the weight of bin b at state q is
 // H_b exp(-u_q(b) - D_b + f_q), giving <N> and p_N (Eq. textbook with the
 // phase indicator chi_i = [N = i]).
