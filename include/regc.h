@@ -459,7 +459,12 @@ REGC_API regc_status regc_structure_timing(regc_handle *h, double *ms_mbar, doub
 /* Stand-alone MBAR solve over caller-supplied pooled bins (host buffers):
  * S states (kT [S], mu [S], omega [S] observations), B bins (N_b [B], E_b [B],
  * H_b [B] > 0 counts).  Outputs f [S] (f_0 = 0) and D [B], the log denominators
- * D_b = ln sum_k omega_k exp(f_k - u_k(b)).  Runs on cuda_stream. */
+ * D_b = ln sum_k omega_k exp(f_k - u_k(b)).  Runs on cuda_stream.
+ * Device memory: besides O(S + B) buffers, when every omega_k > 0 and
+ * 8 (S B + 2 B + 2 S) bytes are at most 2 GiB, the iterations use a kernel
+ * matrix of S B doubles allocated on the stream for the duration of the call
+ * (if that allocation fails they run without it; the result is the same
+ * fixed point).  regc_reweight and regc_structure_reweight solve the same way. */
 REGC_API regc_status regc_mbar_solve(int S, const double *kT, const double *mu, double lambda0,
                             const double *omega, int B, const int32_t *N_b,
                             const double *E_b, const double *H_b, double tol,
