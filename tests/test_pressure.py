@@ -1,7 +1,8 @@
 """The ideal-gas reservoir relation of Sec. III.A in the library
 (regc_mu_of_pressure, regc_pressure_of_mu) against the oracle's, and the
 paper's own state point: with the B mass it implies, (200 K, 2.03e-17 atm)
-is the corner state (200 K, -0.9 eV)."""
+is the corner state (200 K, -0.9 eV).  Both entry points are host code of the
+library: no GPU is needed."""
 import numpy as np
 import pytest
 
@@ -9,8 +10,6 @@ import workloads as W
 from oracle import mbar as OM
 from paper_1908_11118_gb300 import build as B
 from paper_1908_11118_gb300 import mu_of_pressure, pressure_of_mu
-
-pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
