@@ -56,12 +56,15 @@ def mu_from_pressure(kT, p, lambda0):
     return kT * np.log(np.asarray(p, np.float64) * lam ** 3 / kT)
 
 
-def occupied_bins(hNE, e_lo, e_bin):
+def occupied_bins(hNE, e_lo, e_bin, centre: float = 0.5):
     """Pooled (N, E) histogram -> (N_b, E_b at the bin centre, H_b) of the
-    non-empty bins, in row-major (N, E-bin) order."""
+    non-empty bins, in row-major (N, E-bin) order.  Bin k covers
+    [e_lo + k e_bin, e_lo + (k + 1) e_bin); centre is the fraction of the bin
+    where its energy is taken (0.5: the midpoint; any other value is a planted
+    mistake used by the tests)."""
     hNE = np.asarray(hNE)
     n_idx, k_idx = np.nonzero(hNE)
-    return (n_idx.astype(np.float64), e_lo + (k_idx + 0.5) * e_bin,
+    return (n_idx.astype(np.float64), e_lo + (k_idx + centre) * e_bin,
             hNE[n_idx, k_idx].astype(np.float64))
 
 

@@ -38,6 +38,7 @@
  *   1024 MD: forces with the wrong sign
  *   2048 REGC cycle: the two branches of the x0 choice swapped
  *   4096 REGC cycle: canonical moves drawn from the mixed move set
+ *   8192 pooled (N, E) histogram: an observation counted one energy bin too high
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -370,6 +371,7 @@ static void observe(const oracle_system *sys, oracle_hist *h, int state, int n, 
     }
     if (h->hNE) {
         double k = floor((e - sys->e_lo) / sys->e_bin);
+        if (sys->mutation & 8192) k += 1.0;
         if (k >= 0.0 && k < (double)sys->n_e_bins) {
             int64_t idx = (int64_t)n * sys->n_e_bins + (int64_t)k;
 #ifdef _OPENMP

@@ -166,6 +166,14 @@ def mu_grid(M: int, lo: float = -6.0, hi: float = -2.0) -> np.ndarray:
     return lo + (hi - lo) * np.arange(M) / (M - 1)
 
 
+def centred_e_lo(lo: float, e_bin: float) -> float:
+    """Lower edge of an energy-histogram window at or below lo, placed so that
+    E = 0 -- the energy of every empty walker -- is the centre of a bin rather
+    than an edge: binned MBAR takes a bin's energy at its centre, and with 0 on
+    an edge every empty walker would carry e_bin / 2."""
+    return -(math.ceil(-lo / e_bin - 1e-9) + 0.5) * e_bin
+
+
 def fcc100_small(L: int = 4, M: int = 4, nmax: int = 32, eps_sg: float = 2.0,
                  seed: int = 0) -> Problem:
     """The 16-replica fcc(100) workload (4x4x2 slab, 6.25 x 6.25 x 10 box)."""
@@ -176,7 +184,7 @@ def fcc100_small(L: int = 4, M: int = 4, nmax: int = 32, eps_sg: float = 2.0,
         z_lo=ztop, z_hi=10.0, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
         kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
         max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
-        e_lo=-float(nmax) * 12.0, e_bin=0.05,
+        e_lo=centred_e_lo(-float(nmax) * 12.0, 0.05), e_bin=0.05,
         n_e_bins=int(round(float(nmax) * 13.0 / 0.05)), name="fcc100_small")
 
 
@@ -191,7 +199,7 @@ def fcc111_paper_scale(L: int = 32, M: int = 32, nmax: int = 512, eps_sg: float 
         z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
         kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
         max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
-        e_lo=-float(nmax) * 14.0, e_bin=0.5,
+        e_lo=centred_e_lo(-float(nmax) * 14.0, 0.5), e_bin=0.5,
         n_e_bins=int(round(float(nmax) * 15.0 / 0.5)), name="fcc111_paper_scale")
 
 
@@ -258,7 +266,7 @@ def lj_a18_slab(L: int = 10, M: int = 16, nmax: int = 256, mass_amu: float = PAP
         periodic_z=0, z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
         kT=K_B_EV * (200.0 + 50.0 * np.arange(L)), mu=-2.4 + 0.1 * np.arange(M),
         lambda0=thermal_lambda0(mass_amu), nmax=nmax, moves_per_sweep=11, max_disp=0.2,
-        p_disp=1.0 / 3.0, seed=seed, e_lo=-1.8 * nmax, e_bin=0.01,
+        p_disp=1.0 / 3.0, seed=seed, e_lo=centred_e_lo(-1.8 * nmax, 0.01), e_bin=0.01,
         n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_slab")
 
 
@@ -284,7 +292,8 @@ def lj_a18_hex_slab(L: int = 10, M: int = 16, nmax: int = 160, mass_amu: float =
     zhi = float(f32(ztop + zone))
     return ref.replace(Lx=3.0 * a, Ly=3.0 * h, Lz=zhi, z_lo=ztop, z_hi=zhi, surf_xyz=xyz,
                        surf_type=np.ones(len(xyz), np.int32), shear=1.0 / math.sqrt(3.0),
-                       e_lo=-1.8 * nmax, e_bin=0.01, n_e_bins=int(round(2.0 * nmax / 0.01)), name="lj_a18_hex")
+                       e_lo=centred_e_lo(-1.8 * nmax, 0.01), e_bin=0.01, n_e_bins=int(round(2.0 * nmax / 0.01)),
+                       name="lj_a18_hex")
 
 
 def hex_hollow_sites(problem: Problem):
@@ -382,7 +391,7 @@ def tiny_box(nmax: int = 2, rc: float = 1.5, eps_sg: float = 1.0, eps_gg: float 
         periodic_z=0, z_lo=1.0, z_hi=2.6, surf_xyz=xyz,
         surf_type=np.ones(2, np.int32), kT=np.asarray(kT, float), mu=np.asarray(mu, float),
         lambda0=1.0, nmax=nmax, moves_per_sweep=20, max_disp=0.3, p_disp=1.0 / 3.0,
-        seed=seed, e_lo=-40.0, e_bin=0.05, n_e_bins=1600, name="tiny_box")
+        seed=seed, e_lo=centred_e_lo(-40.0, 0.05), e_bin=0.05, n_e_bins=1600, name="tiny_box")
 
 
 def ideal_gas(problem: Problem) -> Problem:
@@ -459,7 +468,7 @@ def uneven_batch(n_systems: int = 256, L: int = 4, M: int = 4, seed: int = 0, nm
             z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
             kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
             max_disp=0.2, p_disp=1.0 / 3.0, seed=seed * 100003 + i,
-            e_lo=-float(nmax) * 14.0, e_bin=e_bin, n_e_bins=int(round(float(nmax) * 15.0 / e_bin)),
+            e_lo=centred_e_lo(-float(nmax) * 14.0, e_bin), e_bin=e_bin, n_e_bins=int(round(float(nmax) * 15.0 / e_bin)),
             name="uneven_%d" % i))
     return out
 
@@ -481,7 +490,7 @@ def cluster_in_gas(L: int = 64, M: int = 64, nmax_b: int = 64, box: float = 15.0
         z_lo=0.0, z_hi=box, surf_xyz=np.zeros((0, 3)), surf_type=np.zeros(0, np.int32),
         kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax_b + 4, moves_per_sweep=20,
         max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
-        e_lo=-float(nmax_b) * 16.0 - 40.0, e_bin=0.25, n_e_bins=int(round((float(nmax_b) * 17.0 + 40.0) / 0.25)),
+        e_lo=centred_e_lo(-float(nmax_b) * 16.0 - 40.0, 0.25), e_bin=0.25, n_e_bins=int(round((float(nmax_b) * 17.0 + 40.0) / 0.25)),
         name="cluster_in_gas", n_cluster=4, cluster_type=1)
 
 
