@@ -12,15 +12,17 @@ Per sample (one walker's configuration, grand-canonical species only):
   unordered pairs of the layer counted by their distance in the xy plane
   (nearest image in x and y), bin k = floor(r * (1/dr)).
 
-The bin of a value is an integer decided by floating point, so it is taken
-in binary32, with the operations of the GPU path in the same order (the
-paper fixes no precision): d = z - z_lo, k = floor(d * inv_dz); the
-nearest-image difference e = q - p, or (q - L) - p when e > L/2, or
-q - (p - L) when e < -L/2, then in a sheared cell (cell-frame x) the
-Cartesian dx = du + shear dy; r2 = dx dx + dy dy, r = sqrt(r2),
-k = floor(r * inv_dr).  Like every geometric input, dz and dr are binary32
-values; inv_dz and inv_dr are 1/dz and 1/dr rounded once to binary32.
-Everything after the counts is FP64.
+Like every geometric input of the C ABI, coordinates, z_lo, the periods, the
+shear, dz and dr are binary32 values.  The bins are decided from them in
+FP64 (the paper fixes no precision): slab k = floor((z - z_lo) / dz); the
+lateral distance r = sqrt(dx^2 + dy^2) with du, dy the nearest-image
+differences along the cell's axes and, in a sheared cell (cell-frame x), the
+Cartesian dx = du + shear dy; bin k = floor(r / dr).  An implementation that
+takes these decisions in binary32 can land on the other side of an edge only
+for a value within a few binary32 roundings of it: ``sample_counts`` lists
+every count whose value (in units of its bin width) lies within EDGE_REL of
+an edge, with the bin on the other side.  Everything after the counts is
+FP64.
 
 Per configuration the functions of Sec. III.A are
   rho(z_k) = c_k / (A dz)                                (number density)
@@ -47,34 +49,53 @@ from . import mbar as MB
 
 F = np.float32
 
-
-def _min_image_f32(q, p, L, hL):
-    e = F(q - p)
-    if e > hL:
-        return F(F(q - L) - p)
-    if e < -hL:
-        return F(q - F(p - L))
-    return e
+# relative distance to a bin edge within which a binary32 decision (a handful
+# of roundings of 2^-24 each) may differ from the FP64 one
+EDGE_REL = 1e-6
 
 
-def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
+def _bin_of(v, edges, kind, layer):
+    """floor(v), and the neighbouring bin if v lies within EDGE_REL of an edge
+    (appended to edges as (kind, layer, k, k_other))."""
+    k = math.floor(v)
+    tol = EDGE_REL * max(1.0, abs(v))
+    if edges is not None:
+        if v - k < tol:
+            edges.append((kind, layer, k, k - 1))
+        elif k + 1 - v < tol:
+            edges.append((kind, layer, k, k + 1))
+    return k
+
+
+def _min_image(d, L):
+    """Nearest-image difference along a periodic axis of period L (FP64)."""
+    if d > 0.5 * L:
+        return d - L
+    if d < -0.5 * L:
+        return d + L
+    return d
+
+
+def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0, edges=None):
     """Counts of one configuration: (slab counts [n_z], pair counts
     [n_layers, n_r], layer populations [n_layers]).
 
     spec: dict with n_z, dz, layers [(lo, hi), ...], n_r, dr.
+    edges: a list that receives (kind 'rho' or 'pairs', layer, k, k_other) for
+    every count whose bin decision lies within EDGE_REL of an edge (bins out
+    of range included, so a count may appear or vanish).
     mutation 1: slab index one too high; 2: ordered pairs counted twice."""
     n_z, n_r = int(spec["n_z"]), int(spec["n_r"])
     layers = list(spec["layers"])
-    inv_dz, inv_dr = F(1.0 / float(F(spec["dz"]))), F(1.0 / float(F(spec["dr"])))
-    z_lo = F(problem.z_lo)
-    Lx, Ly = F(problem.Lx), F(problem.Ly)
-    hLx, hLy = F(0.5 * problem.Lx), F(0.5 * problem.Ly)
-    shear = F(getattr(problem, "shear", 0.0))
+    dz, dr = float(F(spec["dz"])), float(F(spec["dr"]))
+    z_lo = float(F(problem.z_lo))
+    Lx, Ly = float(F(problem.Lx)), float(F(problem.Ly))
+    shear = float(F(getattr(problem, "shear", 0.0)))
     first = int(getattr(problem, "n_cluster", 0))
-    pts = [tuple(F(c) for c in pos_w[j]) for j in range(first, int(n_w))]
+    pts = [tuple(float(F(c)) for c in pos_w[j]) for j in range(first, int(n_w))]
     rho = np.zeros(n_z, np.int64)
     for (_, _, z) in pts:
-        k = int(math.floor(F(F(z - z_lo) * inv_dz)))
+        k = _bin_of((z - z_lo) / dz, edges, "rho", -1)
         if mutation & 1:
             k += 1
         if 0 <= k < n_z:
@@ -82,23 +103,23 @@ def sample_counts(problem, pos_w, n_w, spec, mutation: int = 0):
     pairs = np.zeros((len(layers), n_r), np.int64)
     pop = np.zeros(len(layers), np.int64)
     for l, (lo, hi) in enumerate(layers):
-        lo, hi = F(lo), F(hi)
+        lo, hi = float(F(lo)), float(F(hi))
         mem = [q for q in pts if lo <= q[2] < hi]
         pop[l] = len(mem)
         for a in range(len(mem)):
             for b in range(a + 1, len(mem)):
-                dy = _min_image_f32(mem[a][1], mem[b][1], Ly, hLy)
-                dx = F(_min_image_f32(mem[a][0], mem[b][0], Lx, hLx) + F(shear * dy))
-                r2 = F(F(dx * dx) + F(dy * dy))
-                k = int(math.floor(F(np.sqrt(r2) * inv_dr)))
+                dy = _min_image(mem[a][1] - mem[b][1], Ly)
+                dx = _min_image(mem[a][0] - mem[b][0], Lx) + shear * dy
+                k = _bin_of(math.sqrt(dx * dx + dy * dy) / dr, edges, "pairs", l)
                 if k < n_r:
                     pairs[l, k] += 2 if mutation & 2 else 1
     return rho, pairs, pop
 
 
-def structure_of_walkers(problem, pos, n, state_of_walker, energy, spec):
+def structure_of_walkers(problem, pos, n, state_of_walker, energy, spec, edges=None):
     """One sample per walker: dict of arrays state [S], N [S] (grand-canonical
-    count), E [S], rho [S, n_z], pairs [S, n_layers, n_r], pop [S, n_layers]."""
+    count), E [S], rho [S, n_z], pairs [S, n_layers, n_r], pop [S, n_layers].
+    edges: a list that receives one list per walker (see sample_counts)."""
     S = len(n)
     first = int(getattr(problem, "n_cluster", 0))
     out = {"state": np.array(state_of_walker, np.int64), "N": np.array(n, np.int64) - first,
@@ -107,13 +128,48 @@ def structure_of_walkers(problem, pos, n, state_of_walker, energy, spec):
            "pairs": np.zeros((S, len(spec["layers"]), spec["n_r"]), np.int64),
            "pop": np.zeros((S, len(spec["layers"])), np.int64)}
     for w in range(S):
-        r, p, m = sample_counts(problem, pos[w], n[w], spec)
+        ew = [] if edges is not None else None
+        r, p, m = sample_counts(problem, pos[w], n[w], spec, edges=ew)
         out["rho"][w], out["pairs"][w], out["pop"][w] = r, p, m
+        if edges is not None:
+            edges.append(ew)
     return out
+
+
+def edge_moves(counts, reference, edges):
+    """Reconcile another implementation's counts with the oracle's.
+
+    counts, reference: dicts with rho [n, n_z] and pairs [n, n_layers, n_r]
+    (the other implementation's, the oracle's); edges: per sample the list
+    from sample_counts.  A count may differ from the oracle's only by a
+    near-edge item that landed in the neighbouring bin.  Returns (unexplained,
+    moved): the counts that no such move explains, and the items moved."""
+    bad = moved = 0
+    n_layers = reference["pairs"].shape[1]
+    for w in range(reference["rho"].shape[0]):
+        res = {("rho", -1): np.asarray(counts["rho"][w], np.int64) - reference["rho"][w]}
+        for l in range(n_layers):
+            res[("pairs", l)] = np.asarray(counts["pairs"][w, l], np.int64) - reference["pairs"][w, l]
+        for kind, l, k, k2 in edges[w]:
+            r = res[(kind, l)]
+            src, dst = 0 <= k < len(r), 0 <= k2 < len(r)
+            if (src or dst) and (not src or r[k] < 0) and (not dst or r[k2] > 0):
+                if src:
+                    r[k] += 1
+                if dst:
+                    r[k2] -= 1
+                moved += 1
+        bad += sum(int(np.abs(r).sum()) for r in res.values())
+    return bad, moved
 
 
 def concat(samples):
     return {k: np.concatenate([s[k] for s in samples]) for k in samples[0]}
+
+
+def concat_edges(edge_lists):
+    """Concatenate the per-sample edge lists of several structure_of_walkers calls."""
+    return [e for lst in edge_lists for e in lst]
 
 
 def reweight(problem, samples, spec, kT_q, mu_q, n_lo, n_hi, tol=1e-10, max_iter=200000, mutation: int = 0):

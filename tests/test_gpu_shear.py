@@ -22,7 +22,7 @@ from paper_1908_11118_gb300 import build as B
 from parity import compare_da_traces
 from test_gpu_cycle import run_cycle_lockstep
 from test_gpu_parity import assert_same_state, beta_max, run_lockstep
-from test_gpu_structure import assert_same_samples
+from test_gpu_structure import assert_same_samples, oracle_samples
 from test_gpu_surrogate import sur_tol_of, theta_of
 
 pytestmark = pytest.mark.gpu
@@ -125,7 +125,7 @@ def test_structure_counts_and_hollow_shells():
     g.structure_sample()
     gs = g.structure_get()
     o = O.Oracle(p, pos=pos, n=n)
-    assert_same_samples(gs, ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec))
+    assert_same_samples(gs, *oracle_samples(p, o, spec))
     a = p.Lx / 3.0
     want = np.zeros(49, np.int64)
     for d, z in ((a / math.sqrt(3.0), 3), (a, 6), (2.0 * a / math.sqrt(3.0), 3)):

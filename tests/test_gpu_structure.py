@@ -3,11 +3,14 @@
 lateral RDF g_xy(r) of adsorbate layers; Sec. II.B, Eq. avegr, their MBAR
 averages per phase) against the FP64 oracle.
 
-* Per-sample counts (slabs, layer populations, pair counts) bit-identical to
-  the oracle's on seeded LJ A18 walkers, including the honeycomb of hollow
-  sites whose pair shells are known in closed form.
+* Per-sample counts (slabs, layer populations, pair counts) equal to the
+  oracle's on seeded LJ A18 walkers, including the honeycomb of hollow sites
+  whose pair shells are known in closed form.  The oracle decides bins in FP64,
+  the GPU in binary32: a count may differ only by an item within binary32
+  rounding of a bin edge landing in the neighbouring bin (the oracle lists
+  those items; their number is bounded).
 * The paper's run in lock-step with the oracle (160 replicas, x0 = 0.99, a
-  sample every 100 steps): identical samples, then MBAR averages per phase at
+  sample every 100 steps): the same samples, then MBAR averages per phase at
   sampled and unsampled states within FP64 tolerance of the oracle's.
 * Properties of the reweighted averages at any size: p sums to 1 over the
   phases, rho integrates to N_B when the slabs cover the zone.
@@ -48,13 +51,27 @@ def init_store(g, spec, capacity):
     g.structure_init(spec["n_z"], spec["dz"], spec["layers"], spec["n_r"], spec["dr"], capacity)
 
 
-def assert_same_samples(gs, os_, e_tol=1e-4):
+def assert_same_samples(gs, os_, edges, e_tol=1e-4):
+    """The GPU's samples against the oracle's: states, N_B and layer
+    populations equal; slab and pair counts equal except items within binary32
+    rounding of a bin edge (the oracle decides bins in FP64), which may sit in
+    the neighbouring bin; energies within e_tol."""
     assert np.array_equal(gs["state"], os_["state"])
     assert np.array_equal(gs["N"], os_["N"])
-    assert np.array_equal(gs["rho"].astype(np.int64), os_["rho"])
     assert np.array_equal(gs["pop"].astype(np.int64), os_["pop"])
-    assert np.array_equal(gs["pairs"].astype(np.int64), os_["pairs"])
+    bad, moved = ST.edge_moves(gs, os_, edges)
+    n_items = int(os_["rho"].sum() + os_["pairs"].sum())
+    n_edge = sum(len(e) for e in edges)
+    assert bad == 0, "%d counts differ beyond the near-edge items (%d near an edge, %d moved)" % (bad, n_edge, moved)
+    assert moved <= n_edge <= max(4, 1e-3 * n_items)
     assert np.all(np.abs(gs["E"] - os_["E"]) <= e_tol * np.maximum(1.0, np.abs(os_["E"])))
+    return moved
+
+
+def oracle_samples(p, o, spec):
+    """The oracle's samples of the walkers it holds, and their near-edge items."""
+    edges = []
+    return ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec, edges=edges), edges
 
 
 def test_sample_counts_match_oracle():
@@ -75,8 +92,8 @@ def test_sample_counts_match_oracle():
     g.structure_sample()
     gs = g.structure_get()
     o = O.Oracle(p, pos=pos, n=n)
-    os_ = ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec)
-    assert_same_samples(gs, os_)
+    os_, edges = oracle_samples(p, o, spec)
+    assert_same_samples(gs, os_, edges)
     assert gs["pairs"][0, 0].sum() == 54 + 108 + 54       # the honeycomb's three shells within 5.7 A
     assert gs["rho"][0, 0] == 36
 
@@ -86,15 +103,19 @@ def run_lockstep_with_samples(p, pos, n, blocks, steps, x0, n_c, spec):
     g.set_walkers(pos, n)
     init_store(g, spec, blocks * p.S)
     o = O.Oracle(p, pos=pos, n=n)
-    osamples = []
+    osamples, oedges = [], []
     for b in range(blocks):
         tg, _ = g.cycle_traced(steps, x0, n_c)
         to, _ = o.cycle(steps, x0, n_c, trace=True)
         if not np.array_equal(tg["accepted"], to["accepted"]):
             return g, o, None                   # a near tie: the chains part (checked elsewhere)
         g.structure_sample()
-        osamples.append(ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec))
-    return g, o, ST.concat(osamples)
+        smp, edges = oracle_samples(p, o, spec)
+        osamples.append(smp)
+        oedges.append(edges)
+    out = ST.concat(osamples)
+    out["edges"] = ST.concat_edges(oedges)
+    return g, o, out
 
 
 def compare_reweight(g, p, osmp, spec, kq, mq, n_lo, n_hi):
@@ -137,7 +158,7 @@ def test_paper_run_in_lockstep_samples():
     g, o, osmp = run_lockstep_with_samples(p, pos, n, blocks=4, steps=100, x0=0.99, n_c=10, spec=spec)
     if osmp is None:
         pytest.skip("the chains parted at a near tie before the samples were complete")
-    assert_same_samples(g.structure_get(), osmp)
+    assert_same_samples(g.structure_get(), osmp, osmp["edges"])
     kq = p.kT[[0, 5, 9]]
     mq = p.mu[[8, 12, 15]]
     rg = g.structure_reweight(kq, mq, 0, p.nmax, tol=1e-10, max_iter=100000)
@@ -163,7 +184,7 @@ def test_lj_slab_narrow_grid_reweighted():
     g, o, osmp = run_lockstep_with_samples(p, pos, n, blocks=16, steps=50, x0=0.9, n_c=10, spec=spec)
     if osmp is None:
         pytest.skip("the chains parted at a near tie before the samples were complete")
-    assert_same_samples(g.structure_get(), osmp)
+    assert_same_samples(g.structure_get(), osmp, osmp["edges"])
     kB = W.K_B_EV
     kq = np.array([p.kT[1], p.kT[2], kB * 475.0, kB * 520.0])
     mq = np.array([p.mu[1], p.mu[2], -1.45, -1.38])
@@ -178,7 +199,7 @@ def test_small_grid_lockstep_reweight_at_unsampled_states():
     g, o, osmp = run_lockstep_with_samples(p, pos, n, blocks=12, steps=20, x0=0.9, n_c=10, spec=spec)
     if osmp is None:
         pytest.skip("the chains parted at a near tie before the samples were complete")
-    assert_same_samples(g.structure_get(), osmp)
+    assert_same_samples(g.structure_get(), osmp, osmp["edges"])
     kq = np.array([0.7, 1.2, p.kT[2]])
     mq = np.array([-5.0, -2.5, p.mu[1]])
     rg, _ = compare_reweight(g, p, osmp, spec, kq, mq, 0, p.nmax)
@@ -278,8 +299,8 @@ def test_structure_edge_cases():
         init_store(g, spec, p.S)
         g.structure_sample()
         gs = g.structure_get()
-        os_ = ST.structure_of_walkers(p, o.pos, o.n, o.state_of_walker, o.energy, spec)
-        assert_same_samples(gs, os_)
+        os_, edges = oracle_samples(p, o, spec)
+        assert_same_samples(gs, os_, edges)
         assert gs["rho"].sum() == n.sum() if spec["n_z"] == 84 else True
     # empty store: aiAT has no composition; reweighting is refused
     g.structure_reset()

@@ -50,7 +50,7 @@ def theta_of(seed, scale=1.0):
     return SG.inference_params(th)
 
 
-# Tolerances of the binary32 surrogate against FP64 (derivation in the design doc):
+# Tolerances of the binary32 surrogate against FP64:
 # each feature term carries the error of the cosine cutoff (absolute, about
 # 2^-21 of the weight) and of exp2 and the distance (a few ulp, relative), so
 #   |dG_k| <= 4e-6 (sum of the weights within rc) + 1e-5 |G_k|;
