@@ -3,8 +3,10 @@
 * The GPU sampler in the ideal-gas limit reproduces the truncated Poisson
   distribution of Eq. Ngrand at every state, with replica exchange on.
 * On the 16-replica fcc(100) workload, per-state <N> and <E> of the GPU run
-  agree with those of an independent FP64 oracle run within 4 combined
-  standard errors (batch means), and the error of each is reported.
+  agree with those of an independent FP64 oracle run within 3 combined
+  standard errors (batch means over 50 batches of 2000 sweeps: shorter
+  batches of this system are correlated, lag-1 about 0.65 at 200 sweeps, and
+  would understate the errors), and the error of each is reported.
 * The device MBAR solve and query (FP64 log-sum-exp) agree with the numpy
   oracle on seeded pooled histograms to 1e-9, and the handle's reweighting
   (histogram compaction + solve + query) agrees with the stand-alone entry
@@ -72,7 +74,7 @@ def mean_se(x):
 def test_gpu_ideal_gas_with_exchange():
     p = W.ideal_gas(W.fcc100_small()).replace(moves_per_sweep=3, p_disp=0.0)
     g = Regc(p)
-    nb, _ = batches_gpu(g, 20, 400, exchange_every=1)
+    nb, _ = batches_gpu(g, 50, 400, exchange_every=1)
     m, se = mean_se(nb)
     nv = np.arange(p.nmax + 1)
     for s in range(p.S):
@@ -80,20 +82,21 @@ def test_gpu_ideal_gas_with_exchange():
         pr = trunc_poisson(p.volume * math.exp(mu / kT) * kT ** 1.5, p.nmax)
         mean = pr @ nv
         sd = math.sqrt(pr @ nv ** 2 - mean ** 2)
-        err = max(se[s], sd / math.sqrt(20 * 400))
-        assert abs(m[s] - mean) < 4.5 * err, (s, m[s], mean, err)
+        err = max(se[s], sd / math.sqrt(50 * 400))
+        assert abs(m[s] - mean) < 3.0 * err, (s, m[s], mean, err)
 
 
 def test_statistical_parity_with_oracle_fcc100():
-    """<N> and <E> per state: 16 replicas, 2000 sweeps of 20 moves, exchange
-    every 10 sweeps, GPU and oracle each from N = 0."""
+    """<N> and <E> per state: 16 replicas, 1000 + 50 x 2000 sweeps of 20 moves,
+    exchange every 10 sweeps, GPU and oracle each from N = 0 (their chains are
+    independent: the oracle's seed differs)."""
     p = W.fcc100_small()
     g = Regc(p)
-    o = O.Oracle(p)
-    g.run(200)
-    o.run(200, hist=False)
-    gn, ge = batches_gpu(g, 20, 90, 10)
-    on, oe = batches_oracle(o, 20, 90, 10)
+    o = O.Oracle(p.replace(seed=1))
+    g.run(1000)
+    o.run(1000, hist=False)
+    gn, ge = batches_gpu(g, 50, 2000, 10)
+    on, oe = batches_oracle(o, 50, 2000, 10)
     gm, gs = mean_se(gn)
     om, os_ = mean_se(on)
     gem, ges = mean_se(ge)
@@ -101,7 +104,10 @@ def test_statistical_parity_with_oracle_fcc100():
     zn = np.abs(gm - om) / np.maximum(np.hypot(gs, os_), 1e-3)
     ze = np.abs(gem - oem) / np.maximum(np.hypot(ges, oes), 1e-3)
     print("max z <N> %.2f, <E> %.2f; SE(<N>) gpu %.3g oracle %.3g" % (zn.max(), ze.max(), gs.max(), os_.max()))
-    assert zn.max() < 4.0 and ze.max() < 4.0
+    for s in range(p.S):
+        print("state %2d  <N> gpu %.4f oracle %.4f (SE %.4f, %.4f)  <E> gpu %.4f oracle %.4f (SE %.4f, %.4f)"
+              % (s, gm[s], om[s], gs[s], os_[s], gem[s], oem[s], ges[s], oes[s]))
+    assert zn.max() < 3.0 and ze.max() < 3.0
     assert g.check_energy() == 0.0
 
 
