@@ -34,12 +34,13 @@ def built():
 
 
 def crowded_walkers(p, n_crowd, spacing=0.6):
-    """Walker 0: n_crowd particles on a cubic lattice of the given spacing
-    inside the first cell of the sweep's cell grid (cells of the fcc(111)
-    workload are about 2.68 x 2.71 x 3.0); the other walkers a few particles."""
+    """Walker 0: n_crowd particles on a lattice of the given spacing (0.55 in
+    z) inside the first cell of the sweep's cell grid (cells of the fcc(111)
+    workload are about 2.68 x 2.71 x 3.0), at least 1.0 above the top surface
+    layer; the other walkers a few particles."""
     pos, n = W.initial_walkers(p, [0] + [5] * (p.S - 1), seed=3)
     g = np.arange(4) * spacing + 0.15
-    gz = np.arange(5) * spacing + 0.15
+    gz = np.arange(4) * 0.55 + 1.0
     sites = np.array([(x, y, p.z_lo + z) for z in gz for y in g for x in g])
     pos[0, :n_crowd] = W.f32(sites[:n_crowd])
     n[0] = n_crowd
