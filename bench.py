@@ -72,6 +72,8 @@ def parse_args(argv=None):
                     help="1: add the paper's LJ run through the REGC cycle (x0 = 0.99)")
     ap.add_argument("--paper-steps", type=int, default=120000, help="REGC steps of that run")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--production", type=int, default=100000,
+                    help="sweeps of the 1024-replica production run reweighted to <N>(T, p) (0: skip)")
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
     ap.add_argument("--da-steps-large", type=int, default=60)
@@ -174,13 +176,18 @@ def initial_state(p, seed):
 
 # ------------------------------------------------------------- CPU oracle
 
-def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0, threads=0):
+def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0, threads=0, equil=0, orc=None):
     """Run the FP64 oracle on the workload in steps of 10 sweeps + exchange
-    until `seconds` have passed.  Returns (moves/s, steps timed, seconds,
-    threads used)."""
+    until `seconds` have passed, after `equil` untimed equilibration sweeps
+    (the GPU arm's protocol) unless an equilibrated oracle `orc` is given.
+    Returns (moves/s, steps timed, seconds, threads used, oracle)."""
     from oracle import oracle as O
     O.build()
-    orc = O.Oracle(p, pos=pos, n=n, n_threads=threads)
+    if orc is None:
+        orc = O.Oracle(p, pos=pos, n=n, n_threads=threads)
+        if equil > 0:
+            orc.run(equil, exchange_every=SWEEPS_PER_STEP, hist=False)
+    orc.n_threads = threads
     for _ in range(warmup):
         orc.run(SWEEPS_PER_STEP, exchange_every=SWEEPS_PER_STEP, hist=True)
     steps, t0 = 0, time.perf_counter()
@@ -191,7 +198,7 @@ def time_oracle(p, pos, n, seconds, min_steps=1, max_steps=None, warmup=0, threa
         if (el >= seconds and steps >= min_steps) or (max_steps and steps >= max_steps):
             break
     moves = steps * p.S * SWEEPS_PER_STEP * p.moves_per_sweep
-    return moves / el, steps, el, (threads if threads > 0 else os.cpu_count())
+    return moves / el, steps, el, (threads if threads > 0 else os.cpu_count()), orc
 
 
 def run_reference(args):
@@ -200,13 +207,15 @@ def run_reference(args):
         return 0
     p = W.fcc111_paper_scale(seed=0)
     pos, n = initial_state(p, 0)
-    rate, steps, el, cores = time_oracle(p, pos, n, seconds=0.0, min_steps=args.steps,
-                                         max_steps=args.steps, warmup=args.warmup)
+    rate, steps, el, cores, _ = time_oracle(p, pos, n, seconds=0.0, min_steps=args.steps,
+                                            max_steps=args.steps, warmup=args.warmup,
+                                            equil=args.equil)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "moves/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "start": "seeded lattice state, no equilibration"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "equilibration_sweeps": args.equil,
+                                        "start": "seeded lattice state, equilibrated by the oracle itself"},
         "cpu_baseline": {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
                          "sample": "full 1024-replica workload, %d steps of 10 sweeps + exchange" % steps},
         "e2e": {"value": rate, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -468,6 +477,76 @@ def hbm_peak():
         except Exception:
             pass
     return 6800.0, "fallback 6.8 TB/s"
+
+
+def ks_halves(h1, h2):
+    """Per row: the two-sample Kolmogorov-Smirnov distance between the
+    histograms h1 and h2 (same bins), and its 1 % critical value."""
+    c1 = np.cumsum(h1, axis=1) / np.maximum(h1.sum(axis=1, keepdims=True), 1)
+    c2 = np.cumsum(h2, axis=1) / np.maximum(h2.sum(axis=1, keepdims=True), 1)
+    n1, n2 = np.maximum(h1.sum(axis=1), 1), np.maximum(h2.sum(axis=1), 1)
+    return np.max(np.abs(c1 - c2), axis=1), 1.63 * np.sqrt((n1 + n2) / (n1 * n2))
+
+
+def production_arm(torch, stream, sweeps, equil=2000, seed=0):
+    """Configuration 2's production run: the 1024-replica workload for
+    `sweeps` sweeps after `equil` equilibration sweeps, each state's energies
+    in a window of its own (centred on its mean after equilibration), then the
+    pooled (N, E) histogram reweighted in FP64 (Sec. II.B) to <N> and the most
+    probable N on a (T, p) grid (mu from p by the ideal-gas reservoir of
+    Sec. III.A).  The convergence check of Sec. III.A compares each state's
+    energy distribution between the two halves of the run."""
+    from paper_1908_11118_gb300 import Regc, mu_of_pressure
+
+    p = W.fcc111_paper_scale(seed=seed)
+    pos, n = initial_state(p, seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos, n)
+    g.run(equil, exchange_every=SWEEPS_PER_STEP)
+    g.set_state_windows(1024, 0.5, None)
+    g.reset_histograms()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    half = None
+    chunk = 1000
+    done = 0
+    while done < sweeps:
+        g.run(min(chunk, sweeps - done), exchange_every=SWEEPS_PER_STEP)
+        done += min(chunk, sweeps - done)
+        if half is None and done >= sweeps // 2:
+            half = g.state_histograms()[0]
+    full = g.state_histograms()[0]
+    torch.cuda.synchronize()
+    run_s = time.perf_counter() - t0
+    ks, crit = ks_halves(half, full - half)
+    h = g.histograms()
+    # (T, p) query grid: 12 temperatures over the grid's range, 12 pressures
+    # spanning mu -6 .. -2 at the middle temperature
+    kT_q = np.geomspace(0.6, 1.5, 12)
+    kT_mid = float(np.sqrt(0.6 * 1.5))
+    p_lo, p_hi = (kT_mid * np.exp(np.array([-6.0, -2.0]) / kT_mid) / (p.lambda0 / np.sqrt(kT_mid)) ** 3)
+    p_q = np.geomspace(p_lo, p_hi, 12)
+    T, P = np.meshgrid(kT_q, p_q, indexing="ij")
+    mu_q = mu_of_pressure(T.ravel(), P.ravel(), p.lambda0)
+    t1 = time.perf_counter()
+    nm, pN, f, iters = g.reweight(T.ravel(), mu_q, tol=1e-9, max_iter=200000)
+    rw_s = time.perf_counter() - t1
+    g.close()
+    return {"workload": WORKLOAD, "sweeps": sweeps, "equilibration_sweeps": equil,
+            "run_s": run_s, "trial_moves_per_s": p.S * sweeps * p.moves_per_sweep / run_s,
+            "observations": int(h["omega"].sum()), "pooled_bins_occupied": int(np.count_nonzero(h["hNE"])),
+            "e_out": int(h["e_out"].sum()),
+            "state_windows": {"bins": 1024, "e_bin": 0.5,
+                              "outside": int(full[:, 0].sum() + full[:, -1].sum())},
+            "convergence_ks_halves": {"median": float(np.median(ks)), "max": float(np.max(ks)),
+                                      "states_unchanged_at_1pct": int(np.sum(ks < crit)),
+                                      "note": "per-state energy histograms of the two halves; samples "
+                                              "one sweep apart are correlated, so the critical value "
+                                              "is optimistic"},
+            "reweight_s": rw_s, "mbar_iterations": iters,
+            "phase_map": {"kT": kT_q.tolist(), "p": p_q.tolist(),
+                          "N_mean": nm.reshape(12, 12).round(3).tolist(),
+                          "N_most_probable": np.argmax(pN, axis=1).reshape(12, 12).tolist()}}
 
 
 def paper_structure_spec(p):
@@ -757,15 +836,20 @@ def run_own(args):
     if args.paper_cycle and rank == 0:
         paper = paper_cycle_arm(torch, stream, flush, args.paper_steps)
 
+    production = None
+    if args.production > 0 and rank == 0:
+        production = production_arm(torch, stream, args.production)
+
     line = None
     if rank == 0:
         cpu = None
         if world == 1:
-            rate, steps, el, cores = time_oracle(p, pos0, n0, seconds=args.cpu_seconds)
-            rate1, steps1, el1, _ = time_oracle(p, pos0, n0, seconds=args.cpu_seconds / 4, threads=1)
+            rate, steps, el, cores, orc = time_oracle(p, pos0, n0, seconds=args.cpu_seconds, equil=args.equil)
+            rate1, steps1, el1, _, _ = time_oracle(p, pos0, n0, seconds=args.cpu_seconds / 4, threads=1, orc=orc)
             cpu = {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
-                   "sample": "full 1024-replica workload from the seeded lattice state, "
-                             "%d steps of 10 sweeps + exchange (%.1f s)" % (steps, el),
+                   "sample": "full 1024-replica workload from the seeded lattice state after %d "
+                             "equilibration sweeps of the oracle's own, %d steps of 10 sweeps + "
+                             "exchange (%.1f s)" % (args.equil, steps, el),
                    "value_1_thread": rate1,
                    "sample_1_thread": "%d steps on one thread (%.1f s)" % (steps1, el1)}
         line = {
@@ -796,6 +880,7 @@ def run_own(args):
             "regcmd": regcmd,
             "cluster_in_gas": cluster,
             "paper_lj_cycle": paper,
+            "production_phase_map": production,
         }
         print(json.dumps(line), flush=True)
     g.close()

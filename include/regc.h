@@ -255,6 +255,32 @@ REGC_API regc_status regc_histograms(regc_handle *h, int64_t *hN, int64_t *hNE, 
 /* Zero every histogram and counter (not the walkers). */
 REGC_API regc_status regc_reset_histograms(regc_handle *h);
 
+/* Per-state energy histograms (Sec. II.B: the observations Omega_{l,m} of
+ * each state; Sec. III.A judges convergence by each state's distribution of
+ * the reduced energy).  Every state s gets its own window of n_bins bins of
+ * width e_bin starting at e_lo[s], plus an underflow and an overflow bin:
+ * from now on each observation of a walker at state s (the same observations
+ * as hN) adds one count to
+ *   hE[s][0]           if E < e_lo[s],
+ *   hE[s][k + 1]       if e_lo[s] + k e_bin <= E < e_lo[s] + (k + 1) e_bin,
+ *   hE[s][n_bins + 1]  if E >= e_lo[s] + n_bins e_bin.
+ * e_lo: host [S], or NULL to centre each state's window on the mean energy
+ * observed at that state so far (moments E sum / omega; 0 for a state never
+ * observed), e_lo[s] = mean - n_bins e_bin / 2.  The origins and the width are
+ * rounded to the library's energy grid of 2^-30 (regc_state_histograms
+ * returns the values used).  Replaces earlier windows and zeroes the
+ * per-state histograms; n_bins = 0 switches them off.  regc_reset_histograms
+ * zeroes them too; checkpoints carry them (restore into a handle with windows
+ * of the same n_bins).  Set windows before creating a batch that holds the
+ * handle.  Synchronous.  Errors: REGC_EINVAL (n_bins outside 0..2^20, e_bin
+ * below 2^-30 or not finite, an origin not finite or beyond 2^32), REGC_ENOMEM. */
+REGC_API regc_status regc_set_state_windows(regc_handle *h, int n_bins, double e_bin, const double *e_lo);
+
+/* Copy the per-state energy histograms hE [S][n_bins + 2] (layout above), the
+ * window origins e_lo [S] and the bin width *e_bin as the library uses them
+ * (host; any may be NULL).  Synchronous.  Errors: REGC_EINVAL (no windows). */
+REGC_API regc_status regc_state_histograms(regc_handle *h, int64_t *hE, double *e_lo, double *e_bin);
+
 /* Release the handle and its device memory.  NULL is accepted. */
 REGC_API void regc_free(regc_handle *h);
 

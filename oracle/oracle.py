@@ -74,6 +74,10 @@ class _Hist(C.Structure):
         ("omega", C.POINTER(C.c_int64)),
         ("moments", C.POINTER(C.c_double)),
         ("e_out", C.POINTER(C.c_int64)),
+        ("hE", C.POINTER(C.c_int64)),
+        ("hE_lo", C.POINTER(C.c_double)),
+        ("hE_bin", C.c_double),
+        ("hE_bins", C.c_int),
     ]
 
 
@@ -207,6 +211,26 @@ class Oracle:
         self.omega = np.zeros(p.S, np.int64)
         self.moments = np.zeros((p.S, 4))
         self.e_out = np.zeros(p.S, np.int64)
+        if getattr(self, "hE_lo", None) is not None:
+            self.hE = np.zeros((p.S, self.hE.shape[1]), np.int64)
+
+    def set_state_windows(self, n_bins: int, e_bin: float, e_lo):
+        """Per-state energy windows: state s has n_bins bins of width e_bin
+        from e_lo[s], with an underflow bin first and an overflow bin last."""
+        self.hE_lo = np.ascontiguousarray(e_lo, np.float64)
+        self.hE_bin = float(e_bin)
+        self.hE = np.zeros((self.p.S, int(n_bins) + 2), np.int64)
+
+    def _hist(self):
+        h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
+                  _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
+                  _ptr(self.e_out, C.c_int64))
+        if getattr(self, "hE_lo", None) is not None:
+            h.hE = _ptr(self.hE, C.c_int64)
+            h.hE_lo = _ptr(self.hE_lo, C.c_double)
+            h.hE_bin = self.hE_bin
+            h.hE_bins = self.hE.shape[1] - 2
+        return h
 
     # -- single-function access for the pins
     def phi(self, ti, tj, r2):
@@ -249,9 +273,7 @@ class Oracle:
         tr = np.zeros((S, n_sweeps, p.moves_per_sweep), MOVE_DTYPE) if trace else None
         h = None
         if hist:
-            h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
-                      _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
-                      _ptr(self.e_out, C.c_int64))
+            h = self._hist()
         rc = lib().oracle_sweeps(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
                                  _ptr(self.n, C.c_int32), _ptr(self.energy, C.c_double),
                                  _ptr(self.state_of_walker, C.c_int32), C.c_uint32(self.t),
@@ -273,9 +295,7 @@ class Oracle:
         tr = np.zeros((S, n_steps, n_canonical + 1), MOVE_DTYPE) if trace else None
         h = None
         if hist:
-            h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
-                      _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
-                      _ptr(self.e_out, C.c_int64))
+            h = self._hist()
         n_ex = lib().oracle_cycle(C.byref(self.sys), S, _ptr(self.pos, C.c_double), _ptr(self.n, C.c_int32),
                                   _ptr(self.energy, C.c_double), _ptr(self.state_of_walker, C.c_int32),
                                   _ptr(self.walker_of_state, C.c_int32), C.c_uint32(self.t), C.c_uint32(self.e),

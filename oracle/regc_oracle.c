@@ -39,6 +39,8 @@
  *   2048 REGC cycle: the two branches of the x0 choice swapped
  *   4096 REGC cycle: canonical moves drawn from the mixed move set
  *   8192 pooled (N, E) histogram: an observation counted one energy bin too high
+ *   16384 per-state energy histograms: an observation counted in the row of the
+ *         walker instead of the row of the walker's state
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -356,9 +358,16 @@ double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
 
 /* ---------------------------------------------------------------- sweeps */
 
-static void observe(const oracle_system *sys, oracle_hist *h, int state, int n, double e)
+static void observe(const oracle_system *sys, oracle_hist *h, int state, int w, int n, double e)
 {
     if (!h) return;
+    if (h->hE) {
+        /* the state's own window (Sec. II.B: the observations of each state) */
+        const int row = (sys->mutation & 16384) ? w : state;
+        const double k = floor((e - h->hE_lo[row]) / h->hE_bin);
+        const int64_t idx = k < 0.0 ? 0 : (k >= (double)h->hE_bins ? h->hE_bins + 1 : (int64_t)k + 1);
+        h->hE[(int64_t)row * (h->hE_bins + 2) + idx] += 1;
+    }
     int nb = sys->nmax + 1;
     if (h->hN) h->hN[(int64_t)state * nb + n] += 1;
     if (h->omega) h->omega[state] += 1;
@@ -541,7 +550,7 @@ static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *
             count_move(counts, w, &mv);
             if (trace) trace[((int64_t)ts * sys->moves_per_sweep + k)] = mv;
         }
-        observe(sys, hist, state, n - sys->n_cluster, e);
+        observe(sys, hist, state, w, n - sys->n_cluster, e);
     }
     *n_ptr = n;
     *e_ptr = e;
@@ -716,7 +725,7 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
                 if (trace) trace[((int64_t)w * n_steps + ts) * per_step + k] = mv;
             }
             n[w] = nw;
-            if (gc || n_canonical > 0) observe(sys, hist, state, nw - sys->n_cluster, energy[w]);
+            if (gc || n_canonical > 0) observe(sys, hist, state, w, nw - sys->n_cluster, energy[w]);
         }
     }
     return n_exchange;

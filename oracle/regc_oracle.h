@@ -102,6 +102,13 @@ typedef struct {
     int64_t *omega;     /* [S] observations per state                    */
     double  *moments;   /* [S][4]: sum N, sum N^2, sum E, sum E^2        */
     int64_t *e_out;     /* [S] observations with E outside the E window  */
+    /* per-state energy histograms (NULL: none): state s has hE_bins bins of
+     * width hE_bin from hE_lo[s], bin 0 below the window, k + 1 for window bin
+     * k, hE_bins + 1 at or beyond its end */
+    int64_t      *hE;        /* [S][hE_bins + 2] */
+    const double *hE_lo;     /* [S] */
+    double        hE_bin;
+    int           hE_bins;
 } oracle_hist;
 
 #ifdef __cplusplus

@@ -74,6 +74,8 @@ SIGNATURES = {
     "regc_md": ([_h, C.c_int, C.c_float, C.c_float, _fp], C.c_int),
     "regc_histograms": ([_h, _lp, _lp, _lp, _dp, _lp], C.c_int),
     "regc_reset_histograms": ([_h], C.c_int),
+    "regc_set_state_windows": ([_h, C.c_int, C.c_double, _dp], C.c_int),
+    "regc_state_histograms": ([_h, _lp, _dp, _dp], C.c_int),
     "regc_free": ([_h], None),
     "regc_set_walkers": ([_h, _fp, _ip, _ip], C.c_int),
     "regc_set_cluster": ([_h, C.c_int, C.c_int], C.c_int),

@@ -74,6 +74,7 @@ struct regc_handle {
     bool need_walkers = false;                // set_cluster emptied the walkers
     uint32_t md_seg = 0;                      // MD segments run (Philox counter of the MD streams)
     StructureStore stc;                       // structural observables (empty until regc_structure_init)
+    void* hE_block = nullptr;                 // per-state energy histograms [S][bins + 2] and window origins [S]
 };
 
 // Synchronise the handle's stream and fold its device error word into the

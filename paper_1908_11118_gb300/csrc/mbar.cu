@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256) write_kernel(const unsigned long long* h,
         if (i < n && h[i] != 0ull) {
             const long long nn = i / nbins, kb = i - nn * nbins;
             N_b[out] = (int)nn;
-            E_b[out] = e_lo + ((double)kb + 0.5) * e_bin;
+            E_b[out] = __dadd_rn(e_lo, __dmul_rn((double)kb + 0.5, e_bin));   // as written: no contraction
             lnH[out] = log((double)h[i]);
             ++out;
         }

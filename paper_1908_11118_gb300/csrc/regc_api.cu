@@ -110,6 +110,7 @@ void regc_free(regc_handle* h) {
     cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) cudaFree(p);
     if (h->stc.block) cudaFree(h->stc.block);
+    if (h->hE_block) cudaFree(h->hE_block);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     delete h;
 }
@@ -672,7 +673,81 @@ regc_status regc_reset_histograms(regc_handle* h) {
     zero(h->P.move_counts, S * 6 * 8);
     zero(h->X.ex_counts, S * 8 * 8);
     zero(h->P.pair_counts, 6 * 8);
+    if (h->P.hE) zero(h->P.hE, S * (size_t)(h->P.hE_bins + 2) * 8);
     return cuda_fail(h, e);
+}
+
+regc_status regc_set_state_windows(regc_handle* h, int n_bins, double e_bin, const double* e_lo) {
+    if (!h || n_bins < 0 || n_bins > (1 << 20)) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (n_bins > 0 && !(e_bin * kFixPerUnit >= 1.0 && e_bin < 4294967296.0)) return REGC_EINVAL;
+    const size_t S = h->S;
+    std::vector<long long> lo_fix(S, 0);
+    long long bin_fix = 0;
+    if (n_bins > 0) {
+        bin_fix = llround(e_bin * kFixPerUnit);
+        std::vector<double> lo(S);
+        if (e_lo) {
+            for (size_t s = 0; s < S; ++s) lo[s] = e_lo[s];
+        } else {
+            // centred on each state's mean energy observed so far (0 if never observed)
+            std::vector<double> mom(S * 4);
+            std::vector<unsigned long long> om(S);
+            cudaError_t e = cudaMemcpyAsync(mom.data(), h->P.moments, S * 4 * 8, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(om.data(), h->P.omega, S * 8, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+            for (size_t s = 0; s < S; ++s)
+                lo[s] = (om[s] ? mom[4 * s + 2] / (double)om[s] : 0.0) - 0.5 * n_bins * ((double)bin_fix * kFixUnit);
+        }
+        for (size_t s = 0; s < S; ++s) {
+            if (!std::isfinite(lo[s]) || !(fabs(lo[s]) < 4294967296.0)) return REGC_EINVAL;
+            lo_fix[s] = llround(lo[s] * kFixPerUnit);
+        }
+    }
+    // (re)allocate: the old block may still be read by queued sweeps
+    if (h->hE_block) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaFree(h->hE_block);
+        h->hE_block = nullptr;
+        h->P.hE = nullptr;
+        h->P.hE_lo_fix = nullptr;
+        h->P.hE_bins = 0;
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    if (n_bins == 0) return REGC_OK;
+    const size_t hist_bytes = S * (size_t)(n_bins + 2) * 8;
+    void* block = nullptr;
+    cudaError_t e = cudaMalloc(&block, hist_bytes + S * 8);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->hE_block = block;
+    h->P.hE = static_cast<unsigned long long*>(block);
+    long long* d_lo = reinterpret_cast<long long*>(static_cast<char*>(block) + hist_bytes);
+    h->P.hE_lo_fix = d_lo;
+    h->P.hE_bin_fix = bin_fix;
+    h->P.hE_bins = n_bins;
+    e = cudaMemsetAsync(block, 0, hist_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_lo, lo_fix.data(), S * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // lo_fix is a host temporary
+    return cuda_fail(h, e);
+}
+
+regc_status regc_state_histograms(regc_handle* h, int64_t* hE, double* e_lo, double* e_bin) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (!h->P.hE) return REGC_EINVAL;
+    const size_t S = h->S;
+    std::vector<long long> lo(S);
+    cudaError_t e = cudaSuccess;
+    if (hE) e = cudaMemcpyAsync(hE, h->P.hE, S * (size_t)(h->P.hE_bins + 2) * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lo.data(), h->P.hE_lo_fix, S * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    const regc_status st = sync_check(h);
+    if (st != REGC_OK) return st;
+    if (e_lo)
+        for (size_t s = 0; s < S; ++s) e_lo[s] = (double)lo[s] * kFixUnit;
+    if (e_bin) *e_bin = (double)h->P.hE_bin_fix * kFixUnit;
+    return REGC_OK;
 }
 
 regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n, const int32_t* sow) {
@@ -809,14 +884,15 @@ namespace {
 // ckpt_sections() in order, raw.
 struct CkptHeader {
     char magic[8];             // "REGCCKPT"
-    uint32_t version;          // 2
+    uint32_t version;          // 3
     uint32_t flags;            // bit 0: surrogate present, bit 1: delayed-acceptance mode
     int32_t S, nmax, n_e_bins, n_cluster;
     uint32_t key0, key1, t, e;
     int32_t adam_t;
     uint32_t harvest_round;
     uint32_t md_seg;
-    uint32_t reserved;
+    int32_t hE_bins;           // per-state energy windows (0: none)
+    int64_t hE_bin_fix;
     uint64_t payload_bytes;
     uint64_t checksum;         // FNV-1a 64 of the payload
 };
@@ -843,6 +919,10 @@ std::vector<Section> ckpt_sections(regc_handle* h, bool with_sur) {
         {h->X.ex_counts, S * 8 * 8},
         {h->P.pair_counts, 6 * 8},
     };
+    if (h->P.hE) {
+        v.push_back({h->P.hE, S * (size_t)(h->P.hE_bins + 2) * 8});
+        v.push_back({const_cast<long long*>(h->P.hE_lo_fix), S * 8});
+    }
     if (with_sur) {
         v.push_back({h->d_theta, REGC_SURROGATE_PARAMS * sizeof(float)});
         v.push_back({h->d_adam_m, REGC_SURROGATE_PARAMS * sizeof(float)});
@@ -886,7 +966,7 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
     if (st != REGC_OK) return st;
     CkptHeader hd{};
     memcpy(hd.magic, "REGCCKPT", 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.flags = (h->has_sur ? 1u : 0u) | (h->P.delayed ? 2u : 0u);
     hd.S = h->S;
     hd.nmax = h->nmax;
@@ -899,6 +979,8 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
     hd.adam_t = h->adam_t;
     hd.harvest_round = h->harvest_round;
     hd.md_seg = h->md_seg;
+    hd.hE_bins = h->P.hE_bins;
+    hd.hE_bin_fix = h->P.hE_bin_fix;
     hd.payload_bytes = payload;
     hd.checksum = fnv1a(out + sizeof(CkptHeader), payload);
     memcpy(out, &hd, sizeof hd);
@@ -911,9 +993,9 @@ regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
     CkptHeader hd;
     memcpy(&hd, buf, sizeof hd);
     const unsigned char* in = static_cast<const unsigned char*>(buf);
-    if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 2) return REGC_EINVAL;
+    if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 3) return REGC_EINVAL;
     if (hd.S != h->S || hd.nmax != h->nmax || hd.n_e_bins != h->n_e_bins || hd.n_cluster != h->P.n_cluster ||
-        hd.key0 != h->P.key0 || hd.key1 != h->P.key1)
+        hd.key0 != h->P.key0 || hd.key1 != h->P.key1 || hd.hE_bins != h->P.hE_bins)
         return REGC_EINVAL;
     const bool with_sur = (hd.flags & 1u) != 0;
     if (with_sur) {
@@ -940,6 +1022,7 @@ regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
     h->adam_t = hd.adam_t;
     h->harvest_round = hd.harvest_round;
     h->md_seg = hd.md_seg;
+    h->P.hE_bin_fix = hd.hE_bin_fix;
     h->P.delayed = (with_sur && (hd.flags & 2u)) ? 1 : 0;
     h->need_walkers = false;
     return REGC_OK;

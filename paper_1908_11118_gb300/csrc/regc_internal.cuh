@@ -148,6 +148,11 @@ struct SweepParams {
     double e_lo, e_bin;
     long long e_lo_fix, e_bin_fix;  // E-histogram origin and bin width in units of 2^-30
     int n_e_bins;
+    unsigned long long* hE;       // [S][hE_bins + 2] per-state energy histograms, or null: bin 0
+                                  //     below the state's window, k + 1 window bin k, hE_bins + 1 beyond
+    const long long* hE_lo_fix;   // [S] window origins in units of 2^-30
+    long long hE_bin_fix;         // window bin width in units of 2^-30
+    int hE_bins;
     long long* move_counts;       // [S][6]
     unsigned long long* pair_counts;  // [6] pairs in rc, candidates, rounds, evaluations,
                                       //     surrogate-screened moves, stage-1 passes

@@ -658,6 +658,15 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
     }
 }
 
+// One observation of energy E (2^-30 units) into state s's own histogram:
+// bin 0 below the window, k + 1 for window bin k, hE_bins + 1 at or beyond its end.
+__device__ __forceinline__ void observe_state_energy(const SweepParams& P, int s, long long E) {
+    const long long d = E - P.hE_lo_fix[s];
+    const long long kb = d >= 0 ? d / P.hE_bin_fix : -1;
+    const int idx = kb < 0 ? 0 : (kb >= P.hE_bins ? P.hE_bins + 1 : (int)kb + 1);
+    atomicAdd(&P.hE[size_t(s) * (P.hE_bins + 2) + idx], 1ull);
+}
+
 // Squared minimum-image distance in binary32 (periodic axes per geometry).
 __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay, float az, float bx, float by,
                                        float bz) {
@@ -884,6 +893,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     const long long kb = d >= 0 ? d / P.e_bin_fix : -1;
                     if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[size_t(NB) * P.n_e_bins + (size_t)kb], 1ull);
                     else st.eo += 1;
+                    if (P.hE) observe_state_energy(P, s, E);
                 }
                 ++committed;
             }

@@ -78,6 +78,7 @@ class Regc:
         self.nmax = int(problem.nmax)
         self.mps = int(problem.moves_per_sweep)
         self.n_e_bins = int(problem.n_e_bins)
+        self.hE_bins = 0
 
     # -- lifetime
     def close(self):
@@ -338,6 +339,27 @@ class Regc:
 
     def reset_histograms(self):
         check(_lib.lib().regc_reset_histograms(self._h), "regc_reset_histograms")
+
+    def set_state_windows(self, n_bins: int, e_bin: float, e_lo=None):
+        """Per-state energy windows (regc_set_state_windows); e_lo None centres
+        each state's window on its mean observed energy."""
+        lo = None if e_lo is None else np.ascontiguousarray(e_lo, np.float64)
+        if lo is not None and lo.shape != (self.S,):
+            raise ValueError("e_lo must have one origin per state")
+        check(_lib.lib().regc_set_state_windows(self._h, int(n_bins), float(e_bin),
+                                                 None if lo is None else _p(lo, C.c_double)),
+              "regc_set_state_windows")
+        self.hE_bins = int(n_bins)
+
+    def state_histograms(self):
+        """(hE [S, n_bins + 2], e_lo [S], e_bin): bin 0 below each state's
+        window, k + 1 for window bin k, n_bins + 1 beyond it."""
+        hE = np.zeros((self.S, self.hE_bins + 2), np.int64)
+        lo = np.zeros(self.S)
+        eb = C.c_double(0.0)
+        check(_lib.lib().regc_state_histograms(self._h, _p(hE, C.c_int64), _p(lo, C.c_double), C.byref(eb)),
+              "regc_state_histograms")
+        return hE, lo, eb.value
 
     def reweight(self, kT_q, mu_q, tol: float = 1e-10, max_iter: int = 100000):
         kq = np.ascontiguousarray(kT_q, np.float64)

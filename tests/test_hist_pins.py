@@ -215,3 +215,62 @@ def test_cfg1_binned_against_unbinned_mbar():
     # bins taken at their lower edge shift f by (beta_s - beta_0) e_bin / 2
     f_edge, _, _ = binned(orc.hNE, centre=0.0)
     assert np.max(np.abs(f_edge - f_u)) > 0.8 * shift
+
+
+# ---------------------------------------------- per-state energy histograms
+
+def ideal_state_window_errors(mutation=0):
+    """Ideal gas (E = 0 always) with a different window per state: the bin of
+    E = 0 in each state's window is known in closed form, so every state's
+    observations must sit in that one bin (underflow and overflow included)."""
+    # neighbouring states close together, so that walkers often swap states
+    p = W.ideal_gas(W.fcc100_small(L=2, M=3, nmax=24)).replace(kT=np.array([1.0, 1.1]),
+                                                               mu=np.array([-3.0, -2.9, -2.8]))
+    orc = O.Oracle(p, mutation=mutation)
+    # 4 bins of 0.25 from e_lo: E = 0 lands in window bin floor(-e_lo / 0.25)
+    e_lo = np.array([-0.55, 0.1, -2.0, 0.0, -1.0, -0.3])
+    expect = np.array([3, 0, 5, 1, 5, 2])   # bin 2, below, beyond, bin 0, beyond (0 is the end), bin 1
+    orc.set_state_windows(4, 0.25, e_lo)
+    orc.run(300, exchange_every=10)
+    want = np.zeros_like(orc.hE)
+    want[np.arange(p.S), expect] = orc.omega
+    return int(np.abs(orc.hE - want).sum()), orc
+
+
+def test_ideal_gas_state_windows_exact():
+    err, orc = ideal_state_window_errors()
+    assert err == 0
+    assert orc.ex_counts[:, :, 1].sum() > 10        # walkers did change states
+
+
+def lj_state_window_z(mutation=0, n_bins=4096, e_bin=0.1):
+    """Per state: z of (mean bin energy - exact mean energy) over the same
+    observations, windows centred on each state's mean from an earlier run;
+    +inf where an observation fell outside its window.  (The ideal gas cannot
+    tell a walker's row from its state's row: every row then gets one
+    observation per sweep, all at E = 0; here the energy depends on the state.)"""
+    p = W.fcc100_small()
+    pos, n = W.initial_walkers(p, [8] * p.S, seed=6)
+    orc = O.Oracle(p, pos=pos, n=n, mutation=mutation)
+    orc.run(1500, exchange_every=10, hist=False)
+    orc.run(300, exchange_every=10)
+    mean = orc.moments[:, 2] / orc.omega
+    orc.set_state_windows(n_bins, e_bin, mean - 0.5 * n_bins * e_bin)
+    orc.reset_histograms()
+    orc.run(600, exchange_every=10)
+    inside = orc.hE[:, 1:-1]
+    n_s = inside.sum(axis=1)
+    if not np.array_equal(n_s, orc.omega):
+        return np.inf
+    centres = orc.hE_lo[:, None] + (np.arange(n_bins) + 0.5) * e_bin
+    e_binned = (inside * centres).sum(axis=1) / n_s
+    e_exact = orc.moments[:, 2] / orc.omega
+    return float(np.max(np.abs(e_binned - e_exact) / (e_bin / np.sqrt(12.0 * n_s))))
+
+
+def test_lj_state_windows_match_exact_moments():
+    assert lj_state_window_z() < 5.0
+
+
+def test_lj_state_windows_catch_walker_rows():
+    assert lj_state_window_z(mutation=16384) > 20.0
