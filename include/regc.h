@@ -597,6 +597,16 @@ REGC_API regc_status regc_surrogate_eval(regc_handle *h, int walker, int n_query
 REGC_API regc_status regc_surrogate_harvest(regc_handle *h, int particles, int probes, float e_clip,
                                             int capacity, int64_t *n_rows);
 
+/* Replace the data set by n_rows caller rows: X [n_rows][16] features and
+ * y [n_rows] targets (host, finite), stored as rows 0 .. n_rows - 1 of the
+ * ring (allocated with `capacity` rows on first use, as by
+ * regc_surrogate_harvest; later calls pass the same capacity, or 0); later
+ * harvests continue after them.  Lets a caller train on rows of its own.
+ * Synchronous.  Errors: REGC_EINVAL (n_rows beyond the capacity, a non-finite
+ * value, a NULL buffer with n_rows > 0). */
+REGC_API regc_status regc_surrogate_set_dataset(regc_handle *h, int64_t n_rows, const float *X, const float *y,
+                                                int capacity);
+
 /* Copy the data set (X [n][16], y [n], n = rows held, in ring order) to host
  * buffers of at least `max_rows` rows; *n_rows receives n.  Synchronous. */
 REGC_API regc_status regc_surrogate_dataset(regc_handle *h, int64_t max_rows, float *X, float *y,
@@ -604,18 +614,33 @@ REGC_API regc_status regc_surrogate_dataset(regc_handle *h, int64_t max_rows, fl
 
 /* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
  * the mean squared error of mini-batches of `batch` rows drawn uniformly from
- * the data set (Philox stream 6), on the device; then refresh the inference
- * copy.  loss [steps] (host, may be NULL) receives each step's mini-batch
+ * the data set, on the device; then refresh the inference copy.  Adam step
+ * number a (counted over the handle's life, from 1) takes row
+ * (P0 * rows held) >> 32 for its i-th row, P = Philox((i, a, 0, 6)).  The
+ * gradient is regc_surrogate_gradient_bf16's (tensor cores, BF16 operands,
+ * FP32 accumulation); masters and optimiser moments are binary32.  loss [steps] (host, may be NULL) receives each step's mini-batch
  * loss before its update.  Errors: REGC_EINVAL (empty data set, no
  * surrogate, batch < 1).  Synchronous. */
 REGC_API regc_status regc_surrogate_train(regc_handle *h, int steps, int batch, float lr, float *loss);
 
 /* Stateless: the mean squared error of the network with parameters theta
  * [REGC_SURROGATE_PARAMS] on n rows X [n][16], y [n] (host) and its gradient
- * grad [REGC_SURROGATE_PARAMS] (host), computed by the training kernels in
- * binary32.  Runs on cuda_stream.  Synchronous. */
+ * grad [REGC_SURROGATE_PARAMS] (host), everything in binary32 on the FP32
+ * pipe.  Runs on cuda_stream.  Synchronous. */
 REGC_API regc_status regc_surrogate_gradient(int n, const float *theta, const float *X, const float *y,
                                              float *loss, float *grad, void *cuda_stream);
+
+/* As regc_surrogate_gradient, computed as regc_surrogate_train computes it:
+ * every matrix product of the forward and backward passes on tensor cores
+ * with bfloat16 operands (nearest, ties to even) and FP32 accumulation --
+ *   z1 = bf(X) bf(W1) + b1, h1 = silu(z1), z2 = bf(h1) bf(W2) + b2,
+ *   h2 = silu(z2), e = h2 . W3 + b3,
+ *   dz2 = g W3 silu'(z2), dW2 = bf(h1)^T bf(dz2),
+ *   dz1 = (bf(dz2) bf(W2)^T) silu'(z1), dW1 = bf(X)^T bf(dz1),
+ * with g = 2 (e - y) / n and the rest (e, dW3, the bias gradients and the
+ * element-wise products) in binary32. */
+REGC_API regc_status regc_surrogate_gradient_bf16(int n, const float *theta, const float *X, const float *y,
+                                                  float *loss, float *grad, void *cuda_stream);
 
 /* ---------------------------------------------------------------- batch
  *

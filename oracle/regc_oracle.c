@@ -252,11 +252,26 @@ double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
 
 static double silu(double x) { return x / (1.0 + exp(-x)); }
 
+/* x rounded to binary32, then to the nearest bfloat16 (ties to even): the
+ * precision of every layer input of the sampler's network. */
+static double bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
 /* Surrogate energy e~ of a mobile particle at (x, y, z): 16 Gaussian radial
  * features over every surface atom and mobile particle j != skip within rc,
  * G_k = sum_j eps_0j exp(-eta (r_j - c_k)^2) (cos(pi r_j / rc) + 1) / 2 with
  * c_k = 0.8 + 1.7 k / 15 and eta = 1 / (2 (1.7/15)^2), then the network
- * 16 -> 64 -> 64 -> 1 with SiLU hidden layers.  feat, if given, receives G. */
+ * 16 -> 64 -> 64 -> 1 with SiLU hidden layers, each layer's inputs (G, then
+ * the hidden activations) rounded to bfloat16 as the sampler's network takes
+ * them (its weights are bfloat16 already: sur_theta holds the inference
+ * parameters).  feat, if given, receives G (not rounded). */
 double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int n,
                                double x, double y, double z, int skip, double *feat)
 {
@@ -287,16 +302,17 @@ double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int 
         for (int k = 0; k < SUR_NF; ++k) feat[k] = G[k];
     const double *W1 = sys->sur_theta, *b1 = W1 + SUR_NF * SUR_NH, *W2 = b1 + SUR_NH;
     const double *b2 = W2 + SUR_NH * SUR_NH, *W3 = b2 + SUR_NH, *b3 = W3 + SUR_NH;
-    double h1[SUR_NH], h2[SUR_NH];
+    double h1[SUR_NH], h2[SUR_NH], g16[SUR_NF];
+    for (int k = 0; k < SUR_NF; ++k) g16[k] = bf16(G[k]);
     for (int u = 0; u < SUR_NH; ++u) {
         double z1 = b1[u];
-        for (int k = 0; k < SUR_NF; ++k) z1 += W1[k * SUR_NH + u] * G[k];
-        h1[u] = silu(z1);
+        for (int k = 0; k < SUR_NF; ++k) z1 += W1[k * SUR_NH + u] * g16[k];
+        h1[u] = bf16(silu(z1));
     }
     for (int v = 0; v < SUR_NH; ++v) {
         double z2 = b2[v];
         for (int u = 0; u < SUR_NH; ++u) z2 += W2[u * SUR_NH + v] * h1[u];
-        h2[v] = silu(z2);
+        h2[v] = bf16(silu(z2));
     }
     double e = b3[0];
     for (int v = 0; v < SUR_NH; ++v) e += W3[v] * h2[v];

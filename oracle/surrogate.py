@@ -10,7 +10,8 @@ problem statement of the delayed-acceptance configuration:
   cutoff f_c(r) = (cos(pi r / rc) + 1) / 2, weight w_j = eps between the mobile
   species and the neighbour's species (element-weighted radial functions);
 * network: 16 -> 64 -> 64 -> 1, SiLU hidden activations, scalar output e~(r),
-  the predicted interaction energy of a particle at r;
+  the predicted interaction energy of a particle at r; the sampler's copy
+  rounds its weights and every layer's inputs to bfloat16;
 * loss: mean squared error against the exact interaction energy e(r),
   targets clipped from above at a fixed value;
 * optimiser: Adam.
@@ -56,7 +57,7 @@ def init_params(seed: int, scale: float = 1.0) -> np.ndarray:
 
 
 def to_bf16(theta) -> np.ndarray:
-    """Round each parameter to the nearest bfloat16 value (ties to even)."""
+    """Round each value to binary32, then to the nearest bfloat16 value (ties to even)."""
     f = np.asarray(theta, np.float32).view(np.uint32).astype(np.uint64)
     rounded = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16
     return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
@@ -105,14 +106,19 @@ def dsilu(x):
     return s * (1.0 + x * (1.0 - s))
 
 
-def forward(theta, X):
-    """Predicted energies for feature rows X [n, 16]; returns (e [n], cache)."""
+def forward(theta, X, bf16_inputs: bool = False):
+    """Predicted energies for feature rows X [n, 16]; returns (e [n], cache).
+
+    bf16_inputs: round every layer's inputs (the features, then the hidden
+    activations) to bfloat16, as the sampler's network takes them (training
+    keeps them in full precision)."""
     W1, b1, W2, b2, W3, b3 = unpack(theta)
     X = np.atleast_2d(np.asarray(X, np.float64))
-    z1 = X @ W1 + b1
-    h1 = silu(z1)
+    r = to_bf16 if bf16_inputs else (lambda a: a)
+    z1 = r(X) @ W1 + b1
+    h1 = r(silu(z1))
     z2 = h1 @ W2 + b2
-    h2 = silu(z2)
+    h2 = r(silu(z2))
     e = h2 @ W3 + b3[0]
     return e, (X, z1, h1, z2, h2)
 
@@ -135,6 +141,53 @@ def loss_and_grad(theta, X, y):
     dW1 = X.T @ dz1
     db1 = dz1.sum(axis=0)
     return loss, pack(dW1, db1, dW2, db2, dW3, db3)
+
+
+def loss_and_grad_bf16(theta, X, y):
+    """The mean squared error and its gradient as mixed-precision training
+    defines them: every matrix product takes bfloat16 operands (nearest, ties
+    to even) -- bf(X) bf(W1), bf(h1) bf(W2), bf(h1)^T bf(dz2), bf(dz2)
+    bf(W2)^T, bf(X)^T bf(dz1) -- and everything else (the output layer, the
+    biases, SiLU and its derivative, the products with them, the sums over
+    rows) is taken without rounding (FP64 here).  Products of bfloat16 values
+    and their sums are exact in FP64 to far below the accumulation error of
+    any FP32 implementation."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    bf = to_bf16
+    X = np.atleast_2d(np.asarray(X, np.float64))
+    n = X.shape[0]
+    xb, W1b, W2b = bf(X), bf(W1), bf(W2)
+    z1 = xb @ W1b + b1
+    h1 = silu(z1)
+    h1b = bf(h1)
+    z2 = h1b @ W2b + b2
+    h2 = silu(z2)
+    e = h2 @ W3 + b3[0]
+    r = e - np.asarray(y, np.float64)
+    loss = float(np.mean(r * r))
+    g = 2.0 * r / n
+    dW3 = h2.T @ g
+    db3 = np.array([g.sum()])
+    dz2 = np.outer(g, W3) * dsilu(z2)
+    dz2b = bf(dz2)
+    dW2 = h1b.T @ dz2b
+    db2 = dz2.sum(axis=0)
+    dz1 = (dz2b @ W2b.T) * dsilu(z1)
+    dW1 = xb.T @ bf(dz1)
+    db1 = dz1.sum(axis=0)
+    return loss, pack(dW1, db1, dW2, db2, dW3, db3)
+
+
+def batch_rows(step, batch, count, key):
+    """Row indices of Adam step number `step` (from 1) of a mini-batch of
+    `batch` rows drawn uniformly from `count` rows: row i is (P0 count) >> 32
+    with P = Philox4x32-10((i, step, 0, 6), key)."""
+    from . import oracle as O
+    out = np.zeros(batch, np.int64)
+    for i in range(batch):
+        p0 = O.philox4x32_10((i, step, 0, 6), key)[0]
+        out[i] = (int(p0) * int(count)) >> 32
+    return out
 
 
 class Adam:

@@ -94,9 +94,11 @@ size_t surrogate_partial_floats(int n);
 // Gradient of the mean squared error of n rows (idx[t] or t) at theta_in into
 // grad (may be null) and the sum of squared residuals into *loss; then, when
 // adam_t > 0, Adam step number adam_t with learning rate lr on theta, m, v.
+// tensor_cores: the matrix products in BF16 on mma.sync tiles (FP32
+// accumulation); else everything in binary32 on the FP32 pipe.
 cudaError_t surrogate_step(const float* theta_in, const float* X, const float* y, const int* idx, int n,
                            float* partial, float* grad, float* loss, float* theta, float* m, float* v, int adam_t,
-                           float lr, cudaStream_t s);
+                           float lr, bool tensor_cores, cudaStream_t s);
 
 // Seeded initial parameters (normal weights of standard deviation
 // scale / sqrt(fan-in), zero biases) into theta[5313].

@@ -1160,6 +1160,36 @@ regc_status regc_surrogate_harvest(regc_handle* h, int particles, int probes, fl
     return REGC_OK;
 }
 
+regc_status regc_surrogate_set_dataset(regc_handle* h, int64_t n_rows, const float* X, const float* y,
+                                       int capacity) {
+    if (!h || n_rows < 0 || capacity < 0 || (n_rows > 0 && (!X || !y))) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    for (int64_t i = 0; i < n_rows * 16; ++i)
+        if (!std::isfinite(X[i])) return REGC_EINVAL;
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (!std::isfinite(y[i])) return REGC_EINVAL;
+    if (h->ds_cap == 0) {
+        if (capacity < 1 || n_rows > capacity) return REGC_EINVAL;
+        regc_status st = dalloc(h, &h->d_X, (size_t)capacity * 16);
+        if (st == REGC_OK) st = dalloc(h, &h->d_y, (size_t)capacity);
+        if (st != REGC_OK) return st;
+        h->ds_cap = capacity;
+    } else if ((capacity != 0 && capacity != h->ds_cap) || n_rows > h->ds_cap) {
+        return REGC_EINVAL;
+    }
+    cudaError_t e = cudaSuccess;
+    if (n_rows > 0) {
+        e = cudaMemcpyAsync(h->d_X, X, (size_t)n_rows * 16 * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->d_y, y, (size_t)n_rows * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the host rows may go away
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->ds_count = (int)n_rows;
+    h->ds_next = (int)(n_rows % h->ds_cap);
+    return REGC_OK;
+}
+
 regc_status regc_surrogate_dataset(regc_handle* h, int64_t max_rows, float* X, float* y, int64_t* n_rows) {
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
@@ -1189,7 +1219,7 @@ regc_status regc_surrogate_train(regc_handle* h, int steps, int batch, float lr,
         e = surrogate_batch_index(d_idx, batch, h->ds_count, (uint32_t)h->adam_t, h->P.key0, h->P.key1, h->stream);
         if (e == cudaSuccess)
             e = surrogate_step(h->d_theta, h->d_X, h->d_y, d_idx, batch, d_part, nullptr, d_loss + k, h->d_theta,
-                               h->d_adam_m, h->d_adam_v, h->adam_t, lr, h->stream);
+                               h->d_adam_m, h->d_adam_v, h->adam_t, lr, true, h->stream);
     }
     if (e == cudaSuccess) e = surrogate_pack(h->d_theta, h->sur, h->stream);
     std::vector<float> lsum(steps);
@@ -1205,8 +1235,12 @@ regc_status regc_surrogate_train(regc_handle* h, int steps, int batch, float lr,
     return st;
 }
 
-regc_status regc_surrogate_gradient(int n, const float* theta, const float* X, const float* y, float* loss,
-                                    float* grad, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+regc_status surrogate_gradient_on(int n, const float* theta, const float* X, const float* y, float* loss,
+                                  float* grad, void* cuda_stream, bool tensor_cores) {
     if (n < 1 || !theta || !X || !y) return REGC_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     float *d_theta = nullptr, *d_X = nullptr, *d_y = nullptr, *d_part = nullptr, *d_grad = nullptr,
@@ -1223,7 +1257,7 @@ regc_status regc_surrogate_gradient(int n, const float* theta, const float* X, c
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, y, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = surrogate_step(d_theta, d_X, d_y, nullptr, n, d_part, d_grad, d_loss, nullptr, nullptr, nullptr, 0, 0.0f,
-                           s);
+                           tensor_cores, s);
     float l = 0.0f;
     if (e == cudaSuccess && grad)
         e = cudaMemcpyAsync(grad, d_grad, REGC_SURROGATE_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -1235,6 +1269,20 @@ regc_status regc_surrogate_gradient(int n, const float* theta, const float* X, c
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? REGC_ENOMEM : REGC_ECUDA;
     if (loss) *loss = l / (float)n;
     return REGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+regc_status regc_surrogate_gradient(int n, const float* theta, const float* X, const float* y, float* loss,
+                                    float* grad, void* cuda_stream) {
+    return surrogate_gradient_on(n, theta, X, y, loss, grad, cuda_stream, false);
+}
+
+regc_status regc_surrogate_gradient_bf16(int n, const float* theta, const float* X, const float* y, float* loss,
+                                         float* grad, void* cuda_stream) {
+    return surrogate_gradient_on(n, theta, X, y, loss, grad, cuda_stream, true);
 }
 
 }  // extern "C"

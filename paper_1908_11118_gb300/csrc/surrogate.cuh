@@ -9,7 +9,9 @@
 //
 // Parameters: FP32 master vector of 5313 values (W1 [16][64], b1 [64],
 // W2 [64][64], b2 [64], W3 [64], b3), and a BF16 inference copy packed so that
-// every hidden unit's weights are contiguous (unit-major).
+// every hidden unit's weights are contiguous (unit-major).  Inference runs the
+// layers on tensor cores: every layer's inputs (the features, then the hidden
+// activations) and weights are BF16, accumulation and biases FP32.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -53,57 +55,129 @@ __device__ __forceinline__ float warp_reduce16(float (&F)[kNF], int lane) {
 
 __device__ __forceinline__ float silu_f(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 
-// Network output for the features held as in warp_reduce16 (lane l holds
-// G[(l >> 1) & 15]).  scratch: 64 floats of shared memory for this warp.
-__device__ __forceinline__ float mlp_forward(const SurrogateDev& net, float g_lane, float* scratch, int lane) {
-    if ((lane & 1) == 0) scratch[lane >> 1] = g_lane;
-    __syncwarp();
-    float G[kNF];
+// ------------------------------------------------ the network on tensor cores
+//
+// Every layer is BF16 x BF16 with FP32 accumulation on mma.sync.m16n8k16
+// tiles: A (16 x 16, row-major) holds layer inputs, one row per trial
+// position; B (16 x 8) holds 16 inputs x 8 units of the layer's weights; C
+// (16 x 8, FP32) the pre-activations.  Only rows 0 and 1 of A are positions
+// (a move's new and old position); the other rows stay zero.  In the PTX
+// fragment layouts lane l, with g = l / 4 and t = l % 4, holds
+//   A: rows g and g + 8, columns 2t, 2t + 1, 2t + 8, 2t + 9,
+//   B: column (unit) g, rows (inputs) 2t, 2t + 1, 2t + 8, 2t + 9,
+//   C: rows g and g + 8, columns 2t, 2t + 1,
+// so a layer's C tiles for units 16 kk .. 16 kk + 15 are, after the bias,
+// SiLU and rounding to BF16, the next layer's A fragment for inputs
+// 16 kk .. 16 kk + 15 without leaving the registers.  The unit-major BF16
+// inference copy puts each B fragment pair in one 32-bit word.
+
+// This lane's B fragments of the three layers and the biases of its columns,
+// loaded once per launch.
+struct NetFrag {
+    uint32_t w1[8][2];       // layer 1, units 8j .. 8j + 7
+    uint32_t w2[8][4][2];    // layer 2, units 8j .. 8j + 7, inputs 16kk .. 16kk + 15
+    uint32_t w3[4][2];       // output unit (column 0 of the tile), inputs 16kk ..
+    const float2* b1;        // biases, read where used (L1-resident; registers are scarce)
+    const float2* b2;
+    const float* b3;
+};
+
+__device__ __forceinline__ uint32_t ld_bf16x2(const __nv_bfloat16* p) {
+    return __ldg(reinterpret_cast<const unsigned int*>(p));
+}
+
+__device__ __forceinline__ void load_net(const SurrogateDev& net, int lane, NetFrag& F) {
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int k = 0; k < kNF; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(scratch + k);
-        G[k] = v.x; G[k + 1] = v.y; G[k + 2] = v.z; G[k + 3] = v.w;
-    }
-    __syncwarp();
-    float h[2];
+    for (int j = 0; j < 8; ++j) {
+        const int u = 8 * j + g;
+        F.w1[j][0] = ld_bf16x2(net.w1 + u * kNF + 2 * t);
+        F.w1[j][1] = ld_bf16x2(net.w1 + u * kNF + 2 * t + 8);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int u = lane + 32 * t;
-        const __nv_bfloat162* wr = reinterpret_cast<const __nv_bfloat162*>(net.w1 + u * kNF);
-        float z = net.b1[u];
-#pragma unroll
-        for (int k = 0; k < kNF; k += 2) {
-            const float2 wf = __bfloat1622float2(wr[k / 2]);
-            z = fmaf(wf.x, G[k], z);
-            z = fmaf(wf.y, G[k + 1], z);
+        for (int kk = 0; kk < 4; ++kk) {
+            F.w2[j][kk][0] = ld_bf16x2(net.w2 + u * kNH + 16 * kk + 2 * t);
+            F.w2[j][kk][1] = ld_bf16x2(net.w2 + u * kNH + 16 * kk + 2 * t + 8);
         }
-        h[t] = silu_f(z);
     }
-    scratch[lane] = h[0];
-    scratch[lane + 32] = h[1];
-    __syncwarp();
-    float o = 0.0f;
+    F.b1 = reinterpret_cast<const float2*>(net.b1) + t;   // + 4 j: units 8j + 2t, 8j + 2t + 1
+    F.b2 = reinterpret_cast<const float2*>(net.b2) + t;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int v = lane + 32 * t;
-        const __nv_bfloat162* wr = reinterpret_cast<const __nv_bfloat162*>(net.w2 + v * kNH);
-        float z = net.b2[v];
-#pragma unroll 8
-        for (int u = 0; u < kNH; u += 4) {
-            const float4 hv = *reinterpret_cast<const float4*>(scratch + u);
-            const float2 a = __bfloat1622float2(wr[u / 2]);
-            const float2 b = __bfloat1622float2(wr[u / 2 + 1]);
-            z = fmaf(a.x, hv.x, z);
-            z = fmaf(a.y, hv.y, z);
-            z = fmaf(b.x, hv.z, z);
-            z = fmaf(b.y, hv.w, z);
-        }
-        o = fmaf(__bfloat162float(net.w3[v]), silu_f(z), o);
+    for (int kk = 0; kk < 4; ++kk) {
+        F.w3[kk][0] = g == 0 ? ld_bf16x2(net.w3 + 16 * kk + 2 * t) : 0u;
+        F.w3[kk][1] = g == 0 ? ld_bf16x2(net.w3 + 16 * kk + 2 * t + 8) : 0u;
     }
-    __syncwarp();
+    F.b3 = net.b3;
+}
+
+// Two binary32 values rounded to BF16 (nearest, ties to even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// c += A B on one m16n8k16 tile, BF16 operands, FP32 accumulation.
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Layer-1 A fragment from the features of two positions held as warp_reduce16
+// leaves them (feature k of position p in lanes 2k and 2k + 1 of r_p): lanes
+// 0..3 take position 0's, lanes 4..7 position 1's, the rest zero.
+__device__ __forceinline__ void features_to_frag(float r0, float r1, int lane, uint32_t (&a)[4]) {
+    const int g = lane >> 2, t = lane & 3;
+    const float x0 = __shfl_sync(0xffffffffu, r0, 4 * t), x1 = __shfl_sync(0xffffffffu, r0, 4 * t + 2);
+    const float x2 = __shfl_sync(0xffffffffu, r0, 4 * t + 16), x3 = __shfl_sync(0xffffffffu, r0, 4 * t + 18);
+    const float y0 = __shfl_sync(0xffffffffu, r1, 4 * t), y1 = __shfl_sync(0xffffffffu, r1, 4 * t + 2);
+    const float y2 = __shfl_sync(0xffffffffu, r1, 4 * t + 16), y3 = __shfl_sync(0xffffffffu, r1, 4 * t + 18);
+    a[0] = g == 0 ? pack_bf16(x0, x1) : (g == 1 ? pack_bf16(y0, y1) : 0u);
+    a[2] = g == 0 ? pack_bf16(x2, x3) : (g == 1 ? pack_bf16(y2, y3) : 0u);
+    a[1] = a[3] = 0u;   // rows 8..15
+}
+
+// A fragment for inputs 16kk .. 16kk + 15 of the next layer from the C tiles
+// 2kk, 2kk + 1 of this one: bias, SiLU, BF16 (rows 8..15 stay zero).
+__device__ __forceinline__ void silu_to_frag(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
+    a[0] = pack_bf16(silu_f(c0[0]), silu_f(c0[1]));
+    a[2] = pack_bf16(silu_f(c1[0]), silu_f(c1[1]));
+    a[1] = a[3] = 0u;
+}
+
+// e~ of the positions in rows 0 and 1 of the layer-1 fragment a: returns
+// row 0's in every lane and stores row 1's in *e1.
+__device__ __forceinline__ float net_mma(const NetFrag& W, const uint32_t (&a)[4], float* e1) {
+    float c[8][4];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
-    return o + __ldg(net.b3);
+    for (int j = 0; j < 8; ++j) {
+        const float2 b = __ldg(W.b1 + 4 * j);
+        c[j][0] = b.x;
+        c[j][1] = b.y;
+        c[j][2] = c[j][3] = 0.f;
+        mma_bf16(c[j], a, W.w1[j]);
+    }
+    uint32_t h[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) silu_to_frag(c[2 * kk], c[2 * kk + 1], h[kk]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2 b = __ldg(W.b2 + 4 * j);
+        c[j][0] = b.x;
+        c[j][1] = b.y;
+        c[j][2] = c[j][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(c[j], h[kk], W.w2[j][kk]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) silu_to_frag(c[2 * kk], c[2 * kk + 1], h[kk]);
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) mma_bf16(o, h[kk], W.w3[kk]);
+    // column 0 of row g sits in lane 4 g (t = 0)
+    const float b3 = __ldg(W.b3);
+    *e1 = __shfl_sync(0xffffffffu, o[0], 4) + b3;
+    return __shfl_sync(0xffffffffu, o[0], 0) + b3;
 }
 
 }  // namespace regc

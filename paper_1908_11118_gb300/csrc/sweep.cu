@@ -468,7 +468,8 @@ __device__ __forceinline__ void build_cells(const SweepParams& P, const WalkerSm
 // result in *out.
 template <bool DA, bool CL>
 __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int s, int m, int N,
-                              int slot, int& n_in, int& n_cand, int lane, int warp, MoveRes* out) {
+                              int slot, int& n_in, int& n_cand, int lane, int warp, const NetFrag* nf,
+                              MoveRes* out) {
     // with a cluster, particles 0..nA-1 are cluster atoms; insertion and
     // removal act on the grand-canonical species, whose count is N - nA
     const int nA = CL ? P.n_cluster : 0;
@@ -560,10 +561,13 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
             if (s0) feature_surface<1, CL>(P, col0, q0x, q0y, q0z, q0x, q0y, q0z, F0, F1, lane, mt.mA);
             if (s1) feature_surface<1, CL>(P, col1, q1x, q1y, q1z, q1x, q1y, q1z, F1, F0, lane, mt.mA);
         }
-        float* scratch = S.scratch + warp * 64;
-        const float e0 = mlp_forward(P.net, warp_reduce16(F0, lane), scratch, lane);
+        // both positions through the network at once: rows 0 and 1 of the tiles
+        const float r0 = warp_reduce16(F0, lane);
+        const float r1 = nq == 2 ? warp_reduce16(F1, lane) : 0.f;
+        uint32_t a[4];
+        features_to_frag(r0, r1, lane, a);
         float e1 = 0.f;
-        if (nq == 2) e1 = mlp_forward(P.net, warp_reduce16(F1, lane), scratch, lane);
+        const float e0 = net_mma(*nf, a, &e1);
         dEs = type == 1 ? e0 : (type == 2 ? -e0 : e0 - e1);
         // ln u1 < ln alpha with dE~ in place of dE (u1 from B3)
         float c_f = 0.f;
@@ -717,6 +721,8 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
     group_sync<K>();
 
     int n_in = 0, n_cand = 0;
+    NetFrag nf;                       // the surrogate's weights in this lane's fragments
+    if (DA) load_net(P.net, lane, nf);
     const int total_moves = P.n_sweeps * P.mps;
     const float rc_guard = P.g.rc2 * 1.0004f + 1e-6f;   // a little beyond rc, conservatively
     int filled = 0;   // moves whose Philox blocks are in the ring
@@ -742,7 +748,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         if (mj < total_moves) {
             int slot = -1;
             if (P.cycle) slot = (mj % P.mps) == 0;
-            evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, n_in, n_cand, lane, warp, S.res + warp);
+            evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, n_in, n_cand, lane, warp, &nf, S.res + warp);
         }
         group_sync<K>();
 

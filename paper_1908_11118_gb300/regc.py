@@ -312,6 +312,13 @@ class Regc:
                                                 int(capacity), C.byref(n)), "regc_surrogate_harvest")
         return n.value
 
+    def surrogate_set_dataset(self, X, y, capacity: int = 0):
+        """Replace the training rows by caller rows X [n, 16], y [n]."""
+        X = np.ascontiguousarray(np.asarray(X, np.float32).reshape(-1, 16))
+        y = np.ascontiguousarray(np.asarray(y, np.float32).reshape(-1))
+        check(_lib.lib().regc_surrogate_set_dataset(self._h, len(y), _p(X, C.c_float), _p(y, C.c_float),
+                                                    int(capacity)), "regc_surrogate_set_dataset")
+
     def surrogate_dataset(self):
         n = C.c_int64(0)
         check(_lib.lib().regc_surrogate_dataset(self._h, 0, None, None, C.byref(n)), "regc_surrogate_dataset")
@@ -428,17 +435,19 @@ class Batch:
         self.close()
 
 
-def surrogate_gradient(theta, X, y, stream=None):
+def surrogate_gradient(theta, X, y, stream=None, tensor_cores: bool = False):
     """Mean squared error of the surrogate with parameters theta on rows (X, y)
-    and its gradient, from the library's training kernels."""
+    and its gradient, from the library's training kernels: binary32 on the
+    FP32 pipe, or (tensor_cores) BF16 operands with FP32 accumulation as
+    training computes it."""
     th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(SURROGATE_PARAMS))
     X = np.ascontiguousarray(np.asarray(X, np.float32).reshape(-1, 16))
     y = np.ascontiguousarray(np.asarray(y, np.float32).reshape(-1))
     g = np.zeros(SURROGATE_PARAMS, np.float32)
     loss = C.c_float(0)
-    check(_lib.lib().regc_surrogate_gradient(len(y), _p(th, C.c_float), _p(X, C.c_float), _p(y, C.c_float),
-                                             C.byref(loss), _p(g, C.c_float), _stream_handle(stream)),
-          "regc_surrogate_gradient")
+    name = "regc_surrogate_gradient_bf16" if tensor_cores else "regc_surrogate_gradient"
+    check(getattr(_lib.lib(), name)(len(y), _p(th, C.c_float), _p(X, C.c_float), _p(y, C.c_float),
+                                    C.byref(loss), _p(g, C.c_float), _stream_handle(stream)), name)
     return float(loss.value), g
 
 

@@ -3,7 +3,8 @@
 Every test calls the library through its C ABI and compares with the FP64
 oracle on identical seeded inputs:
   * features and network output e~ of arbitrary positions, with the same
-    inference parameters (bfloat16 weights, binary32 biases) on both sides;
+    inference parameters (bfloat16 weights, binary32 biases) and bfloat16
+    layer inputs on both sides (the GPU runs the layers on tensor cores);
   * the training loss and its gradient (the library's forward and backward
     kernels) against the oracle's analytic backward pass, over several CTAs of
     rows and a ragged tail;
@@ -111,7 +112,8 @@ def test_eval_matches_oracle():
 
 def test_eval_empty_walker_and_far_from_surface():
     """With no neighbour within rc every feature is 0 and e~ is the network's
-    value at G = 0: b3 + W3 . silu(W2^T silu(b1) + b2)."""
+    value at G = 0: b3 + W3 . bf(silu(W2^T bf(silu(b1)) + b2)), bf the
+    bfloat16 rounding of the layer inputs."""
     p = W.fcc100_small(L=1, M=1)
     th = theta_of(6)
     g = Regc(p)
@@ -120,7 +122,8 @@ def test_eval_empty_walker_and_far_from_surface():
     e, f = g.surrogate_eval(0, q)
     assert np.all(f == 0.0)
     W1, b1, W2, b2, W3, b3 = SG.unpack(th)
-    e0 = float(SG.silu(SG.silu(b1) @ W2 + b2) @ W3 + b3[0])
+    bf = SG.to_bf16
+    e0 = float(bf(SG.silu(bf(SG.silu(b1)) @ W2 + b2)) @ W3 + b3[0])
     assert np.all(np.abs(e - e0) <= e_tol(e0))
 
 
@@ -147,6 +150,99 @@ def test_gradient_matches_oracle(n_rows):
     r = e_o - y64
     dr = 1e-5 * (1.0 + np.abs(e_o) + np.abs(y64))
     assert abs(loss - loss_o) <= float(np.mean(2 * np.abs(r) * dr + dr * dr)) + 1e-12
+
+
+def grad_scale(th64, X64, y64):
+    """Per parameter: the mean over rows of each row's |gradient contribution|."""
+    gabs = np.zeros(SG.N_PARAMS)
+    for i in range(len(y64)):
+        gabs += np.abs(SG.loss_and_grad(th64, X64[i:i + 1], y64[i:i + 1])[1]) / len(y64)
+    return gabs
+
+
+@pytest.mark.parametrize("n_rows", [1, 77, 128, 1000])
+def test_tensor_core_gradient_matches_oracle(n_rows):
+    """The training gradient (BF16 operands on tensor cores, FP32
+    accumulation) against the oracle's mixed-precision gradient with the same
+    rounding points: the two differ by FP32 accumulation and SiLU, and by the
+    rare operand that rounds to the neighbouring bfloat16 because its FP32 and
+    FP64 values straddle the rounding point (one bfloat16 step, 2^-8, of one
+    row's contribution).  Against the FP64 gradient: within a few bfloat16
+    roundings of the per-row magnitudes."""
+    rng = np.random.default_rng(n_rows + 11)
+    th = SG.init_params(7, scale=1.0).astype(np.float32)
+    th[~SG.weight_mask()] = (rng.normal(size=int((~SG.weight_mask()).sum())) * 0.2).astype(np.float32)
+    X = rng.uniform(0.0, 3.0, size=(n_rows, 16)).astype(np.float32)
+    y = rng.normal(0.0, 2.0, size=n_rows).astype(np.float32)
+    loss, grad = surrogate_gradient(th, X, y, tensor_cores=True)
+    th64, X64, y64 = th.astype(np.float64), X.astype(np.float64), y.astype(np.float64)
+    loss_b, grad_b = SG.loss_and_grad_bf16(th64, X64, y64)
+    loss_e, grad_e = SG.loss_and_grad(th64, X64, y64)
+    gabs = grad_scale(th64, X64, y64)
+    tol = 2e-4 * gabs + 2.0 ** -8 * gabs / np.sqrt(n_rows) + 1e-9
+    ratio = np.abs(grad - grad_b) / tol
+    print("worst |g - g_bf16 oracle| / tol %.3g; worst |g - g_fp64| / (sum |row g|) %.3g"
+          % (ratio.max(), (np.abs(grad - grad_e) / (gabs + 1e-12)).max()))
+    assert ratio.max() <= 1.0, np.flatnonzero(ratio > 1.0)[:10]
+    if n_rows >= 64:
+        # over many rows the BF16 roundings average out against the per-row
+        # magnitudes; one row's gradient can cancel inside a contraction, where
+        # no such relative bound holds
+        assert np.max(np.abs(grad - grad_e) / (gabs + 1e-12)) < 6 * 2.0 ** -8
+    assert abs(loss - loss_b) <= 1e-4 * (1.0 + loss_b)
+
+
+def test_adam_steps_match_oracle():
+    """Three Adam steps of regc_surrogate_train on caller rows against the
+    oracle's Adam (FP64) on the oracle's mixed-precision gradient of the same
+    mini-batches (Philox stream 6 draws the rows).  Adam's step
+    lr m^/sqrt(v^) is a smooth function of the gradients away from zero: where
+    every step's gradient of a parameter exceeds 20 times its tolerance
+    (relative tolerance rel < 1/20), the update may differ from the oracle's
+    by at most 3 rel lr per step; elsewhere the normalised step may point
+    either way and is only bounded (|update| <= 3.2 lr per step)."""
+    p = W.fcc100_small(L=2, M=2, seed=9)
+    pos, n = W.initial_walkers(p, [20, 12, 26, 8], seed=4)
+    o = O.Oracle(p, pos=pos, n=n, surrogate=theta_of(2))
+    rng = np.random.default_rng(5)
+    X, y = [], []
+    for _ in range(600):
+        w = int(rng.integers(p.S))
+        q = np.array([rng.uniform(0, p.Lx), rng.uniform(0, p.Ly), rng.uniform(p.z_lo, p.z_lo + 4.0)])
+        _, f = o.surrogate_energy(w, q)
+        e, _, _, _ = o.particle_energy(w, q)
+        X.append(f)
+        y.append(min(e, 8.0))
+    X = np.array(X, np.float32)
+    y = np.array(y, np.float32)
+    th = SG.init_params(3, scale=1.0).astype(np.float32)
+    steps, batch, lr = 3, 256, 1e-3
+    g = Regc(p)
+    g.surrogate_set(th)
+    g.surrogate_set_dataset(X, y, capacity=1024)
+    losses = g.surrogate_train(steps, batch, lr)
+    th_g = g.surrogate_get().astype(np.float64)
+    key = (int(p.seed) & 0xFFFFFFFF, int(p.seed) >> 32)
+    th_o = th.astype(np.float64)
+    adam = SG.Adam(SG.N_PARAMS, lr)
+    rel = np.zeros(SG.N_PARAMS)
+    X64, y64 = X.astype(np.float64), y.astype(np.float64)
+    for a in range(1, steps + 1):
+        rows = SG.batch_rows(a, batch, len(y), key)
+        loss_o, grad_o = SG.loss_and_grad_bf16(th_o, X64[rows], y64[rows])
+        assert abs(losses[a - 1] - loss_o) <= 1e-3 * (1.0 + loss_o)
+        gs = grad_scale(th_o, X64[rows], y64[rows])
+        gtol = 2e-4 * gs + 2.0 ** -8 * gs / np.sqrt(batch) + 1e-9
+        rel = np.maximum(rel, gtol / np.maximum(np.abs(grad_o), 1e-300))
+        th_o = adam.step(th_o, grad_o)
+    d = np.abs(th_g - th_o)
+    stable = rel < 0.05
+    bound = 3.0 * rel * steps * lr + 1e-6 * np.abs(th_o)
+    print("stable parameters %d of %d; worst |d theta| / bound (stable) %.3g; worst |d theta| / lr (other) %.3g"
+          % (stable.sum(), SG.N_PARAMS, (d[stable] / bound[stable]).max(), d[~stable].max() / lr))
+    assert stable.sum() > 0.5 * SG.N_PARAMS
+    assert np.all(d[stable] <= bound[stable])
+    assert np.all(d <= 3.2 * steps * lr)
 
 
 def test_harvest_rows_match_oracle():

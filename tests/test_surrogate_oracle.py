@@ -72,7 +72,8 @@ def test_c_oracle_features_and_network_agree_with_numpy():
         r = np.sqrt(np.sum(d * d, axis=1))
         ref = SG.features(r, w, p.rc)
         np.testing.assert_allclose(feat, ref, rtol=1e-12, atol=1e-14)
-        e_ref, _ = SG.forward(theta, ref[None, :])
+        # the sampler's network: bfloat16 weights and layer inputs
+        e_ref, _ = SG.forward(theta, ref[None, :], bf16_inputs=True)
         assert e == pytest.approx(e_ref[0], rel=1e-12, abs=1e-12)
 
 
@@ -155,3 +156,41 @@ def test_delayed_acceptance_small_box_brute_force():
     tr = orc.sweeps(20, trace=True)
     ev = tr["status"] == 0
     assert 0 < np.mean(tr["stage1"][ev]) < 1
+
+
+def test_bf16_training_gradient_within_bfloat16_of_the_exact_one():
+    """The mixed-precision gradient (bfloat16 operands of every matrix
+    product) against the FP64 analytic gradient, itself pinned by finite
+    differences: within a few bfloat16 roundings (2^-8) of the per-row
+    gradient magnitudes.  A transposed or dropped operand is far outside."""
+    rng = np.random.default_rng(3)
+    th = SG.init_params(7)
+    th[~SG.weight_mask()] = rng.normal(size=int((~SG.weight_mask()).sum())) * 0.2
+    X = rng.uniform(0.0, 3.0, size=(200, 16))
+    y = rng.normal(0.0, 2.0, size=200)
+    loss_b, g_b = SG.loss_and_grad_bf16(th, X, y)
+    loss_e, g_e = SG.loss_and_grad(th, X, y)
+    gabs = np.zeros(SG.N_PARAMS)
+    for i in range(len(y)):
+        gabs += np.abs(SG.loss_and_grad(th, X[i:i + 1], y[i:i + 1])[1]) / len(y)
+    rel = np.abs(g_b - g_e) / (gabs + 1e-12)
+    assert np.max(rel) < 6 * 2.0 ** -8
+    assert np.median(rel) < 2.0 ** -8
+    assert abs(loss_b - loss_e) < 0.05 * loss_e
+    # planted: W2 transposed in the backward product
+    W1, b1, W2, b2, W3, b3 = SG.unpack(th)
+    th_t = SG.pack(W1, b1, W2.T, b2, W3, b3)
+    _, g_t = SG.loss_and_grad_bf16(th_t, X, y)
+    _, g_te = SG.loss_and_grad(th, X, y)
+    assert np.max(np.abs(g_t - g_te) / (gabs + 1e-12)) > 0.1
+
+
+def test_batch_rows_are_uniform_multiply_shift():
+    key = (0x1234, 0x5678)
+    rows = SG.batch_rows(1, 4096, 1000, key)
+    assert rows.min() >= 0 and rows.max() < 1000
+    counts = np.bincount(rows, minlength=1000)
+    # 4096 draws over 1000 rows: chi-square with 999 degrees of freedom
+    chi2 = float(np.sum((counts - 4.096) ** 2 / 4.096))
+    assert abs(chi2 - 999) < 6 * np.sqrt(2 * 999)
+    assert not np.array_equal(rows, SG.batch_rows(2, 4096, 1000, key))
