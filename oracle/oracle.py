@@ -64,6 +64,10 @@ class _System(C.Structure):
         ("n_cluster", C.c_int),
         ("cluster_type", C.c_int),
         ("shear", C.c_double),
+        ("gc2_type", C.c_int),
+        ("K", C.c_int),
+        ("mu2", C.POINTER(C.c_double)),
+        ("lambda0_2", C.c_double),
     ]
 
 
@@ -78,6 +82,8 @@ class _Hist(C.Structure):
         ("hE_lo", C.POINTER(C.c_double)),
         ("hE_bin", C.c_double),
         ("hE_bins", C.c_int),
+        ("hN2", C.POINTER(C.c_int64)),
+        ("moments2", C.POINTER(C.c_double)),
     ]
 
 
@@ -115,6 +121,21 @@ def lib():
         _lib.oracle_sweeps.restype = C.c_int
         _lib.oracle_exchange.argtypes = [sp, C.c_uint32, ip, dp, ip, ip, i64p]
         _lib.oracle_exchange.restype = C.c_int
+        _lib.oracle_sweeps2.argtypes = [sp, C.c_int, dp, ip, ip, dp, ip, C.c_uint32, C.c_int,
+                                        C.POINTER(_Hist), C.c_void_p, i64p, C.c_int]
+        _lib.oracle_sweeps2.restype = C.c_int
+        _lib.oracle_exchange2.argtypes = [sp, C.c_uint32, ip, ip, dp, ip, ip, i64p]
+        _lib.oracle_exchange2.restype = C.c_int
+        _lib.oracle_total_energy2.argtypes = [sp, dp, C.c_int, C.c_int]
+        _lib.oracle_total_energy2.restype = C.c_double
+        _lib.oracle_particle_energy2.argtypes = [sp, dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                                 C.c_int, C.c_int, dp, dp, ip]
+        _lib.oracle_particle_energy2.restype = C.c_double
+        _lib.oracle_log_alpha2.argtypes = [sp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
+        _lib.oracle_log_alpha2.restype = C.c_double
+        _lib.oracle_exchange_log_alpha2.argtypes = [sp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                    C.c_double, C.c_double]
+        _lib.oracle_exchange_log_alpha2.restype = C.c_double
         _lib.oracle_surrogate_energy.argtypes = [sp, dp, C.c_int, C.c_double, C.c_double, C.c_double,
                                                  C.c_int, dp]
         _lib.oracle_surrogate_energy.restype = C.c_double
@@ -150,7 +171,7 @@ class Oracle:
     counter e, histograms and acceptance counters."""
 
     def __init__(self, problem, pos=None, n=None, mutation: int = 0, n_threads: int = 0,
-                 surrogate=None):
+                 surrogate=None, nb=None):
         self.p = problem
         S, nmax = problem.S, problem.nmax
         self._kT = np.ascontiguousarray(problem.kT, np.float64)
@@ -185,6 +206,12 @@ class Oracle:
         s.n_cluster = int(getattr(problem, "n_cluster", 0))
         s.cluster_type = int(getattr(problem, "cluster_type", 0))
         s.shear = float(getattr(problem, "shear", 0.0))
+        self.two = int(getattr(problem, "gc2_type", 0)) > 0
+        self._mu2 = np.ascontiguousarray(problem.mu2 if self.two else [0.0], np.float64)
+        s.gc2_type = int(getattr(problem, "gc2_type", 0))
+        s.K = int(problem.K)
+        s.mu2 = _ptr(self._mu2, C.c_double)
+        s.lambda0_2 = float(getattr(problem, "lambda0_2", 1.0))
         self._theta = None
         if surrogate is not None:
             self._theta = np.ascontiguousarray(surrogate, np.float64)
@@ -194,6 +221,8 @@ class Oracle:
         self.n_threads = int(n_threads)
         self.pos = np.zeros((S, nmax, 3)) if pos is None else np.array(pos, np.float64).reshape(S, nmax, 3)
         self.n = np.zeros(S, np.int32) if n is None else np.array(n, np.int32)
+        # with a second species: N_B per walker (particles [0, N_B) are B)
+        self.nb = np.array(self.n if nb is None else nb, np.int32)
         self.energy = np.array([self.total_energy(w) for w in range(S)])
         self.state_of_walker = np.arange(S, dtype=np.int32)
         self.walker_of_state = np.arange(S, dtype=np.int32)
@@ -202,12 +231,15 @@ class Oracle:
         self.md_seg = 0
         self.reset_histograms()
         self.counts = np.zeros((S, 3, 2), np.int64)
-        self.ex_counts = np.zeros((S, 4, 2), np.int64)
+        self.ex_counts = np.zeros((S, 5 if problem.K > 1 else 4, 2), np.int64)
 
     def reset_histograms(self):
         p = self.p
         self.hN = np.zeros((p.S, p.nmax + 1), np.int64)
-        self.hNE = np.zeros((p.nmax + 1, p.n_e_bins), np.int64)
+        rows = (p.nmax + 1) ** 2 if getattr(p, "gc2_type", 0) else p.nmax + 1
+        self.hNE = np.zeros((rows, p.n_e_bins), np.int64)
+        self.hN2 = np.zeros((p.S, p.nmax + 1), np.int64)
+        self.moments2 = np.zeros((p.S, 2))
         self.omega = np.zeros(p.S, np.int64)
         self.moments = np.zeros((p.S, 4))
         self.e_out = np.zeros(p.S, np.int64)
@@ -225,6 +257,9 @@ class Oracle:
         h = _Hist(_ptr(self.hN, C.c_int64), _ptr(self.hNE, C.c_int64),
                   _ptr(self.omega, C.c_int64), _ptr(self.moments, C.c_double),
                   _ptr(self.e_out, C.c_int64))
+        if self.two:
+            h.hN2 = _ptr(self.hN2, C.c_int64)
+            h.moments2 = _ptr(self.moments2, C.c_double)
         if getattr(self, "hE_lo", None) is not None:
             h.hE = _ptr(self.hE, C.c_int64)
             h.hE_lo = _ptr(self.hE_lo, C.c_double)
@@ -238,7 +273,25 @@ class Oracle:
 
     def total_energy(self, w):
         pos = np.ascontiguousarray(self.pos[w])
-        return lib().oracle_total_energy(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]))
+        nb = int(self.nb[w]) if self.two else int(self.n[w])
+        return lib().oracle_total_energy2(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]), nb)
+
+    def particle_energy2(self, w, xyz, skip=-1, species_new=0):
+        """Interaction energy of a particle at xyz in walker w (two species:
+        particles [0, N_B) are B); a new particle has potential type species_new."""
+        pos = np.ascontiguousarray(self.pos[w])
+        sa, band = C.c_double(0), C.c_double(0)
+        npairs = C.c_int32(0)
+        e = lib().oracle_particle_energy2(C.byref(self.sys), _ptr(pos, C.c_double), int(self.n[w]),
+                                          int(self.nb[w]), float(xyz[0]), float(xyz[1]), float(xyz[2]),
+                                          int(skip), int(species_new), C.byref(sa), C.byref(band), C.byref(npairs))
+        return e, sa.value, band.value, npairs.value
+
+    def log_alpha2(self, move_type, species, state, n_c, dE):
+        return lib().oracle_log_alpha2(C.byref(self.sys), move_type, species, state, n_c, dE)
+
+    def exchange_log_alpha2(self, sa, sb, nba, nca, nbb, ncb, ea, eb):
+        return lib().oracle_exchange_log_alpha2(C.byref(self.sys), sa, sb, nba, nca, nbb, ncb, ea, eb)
 
     def particle_energy(self, w, xyz, skip=-1):
         pos = np.ascontiguousarray(self.pos[w])
@@ -274,12 +327,13 @@ class Oracle:
         h = None
         if hist:
             h = self._hist()
-        rc = lib().oracle_sweeps(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
-                                 _ptr(self.n, C.c_int32), _ptr(self.energy, C.c_double),
-                                 _ptr(self.state_of_walker, C.c_int32), C.c_uint32(self.t),
-                                 n_sweeps, C.byref(h) if h is not None else None,
-                                 tr.ctypes.data if tr is not None else None,
-                                 _ptr(self.counts, C.c_int64), self.n_threads)
+        rc = lib().oracle_sweeps2(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
+                                  _ptr(self.n, C.c_int32), _ptr(self.nb, C.c_int32) if self.two else None,
+                                  _ptr(self.energy, C.c_double),
+                                  _ptr(self.state_of_walker, C.c_int32), C.c_uint32(self.t),
+                                  n_sweeps, C.byref(h) if h is not None else None,
+                                  tr.ctypes.data if tr is not None else None,
+                                  _ptr(self.counts, C.c_int64), self.n_threads)
         if rc != 0:
             raise ValueError("oracle_sweeps rejected its arguments")
         self.t += n_sweeps
@@ -342,8 +396,9 @@ class Oracle:
         return kin
 
     def exchange(self):
-        acc = lib().oracle_exchange(C.byref(self.sys), C.c_uint32(self.e), _ptr(self.n, C.c_int32),
-                                    _ptr(self.energy, C.c_double),
+        acc = lib().oracle_exchange2(C.byref(self.sys), C.c_uint32(self.e), _ptr(self.n, C.c_int32),
+                                     _ptr(self.nb, C.c_int32) if self.two else None,
+                                     _ptr(self.energy, C.c_double),
                                     _ptr(self.state_of_walker, C.c_int32),
                                     _ptr(self.walker_of_state, C.c_int32),
                                     _ptr(self.ex_counts, C.c_int64))

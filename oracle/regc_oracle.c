@@ -41,6 +41,8 @@
  *   8192 pooled (N, E) histogram: an observation counted one energy bin too high
  *   16384 per-state energy histograms: an observation counted in the row of the
  *         walker instead of the row of the walker's state
+ *   32768 second species: insertion and removal of C with species B's mu and Lambda
+ *   65536 second species: the exchange without the mu2 term
  *
  * Delayed acceptance (da != 0; not in the paper, Christen & Fox 2005): a move
  * is first screened with the surrogate energy change dE~ (stage 1: accept iff
@@ -186,12 +188,18 @@ static void account(const oracle_system *sys, int ti, int tj, double r2, double 
     }
 }
 
-/* Potential type of mobile particle j: the cluster species for the first
- * n_cluster particles, else the grand-canonical species 0. */
-static int species(const oracle_system *sys, int j)
+/* Potential type of mobile particle j of a walker with nb particles of
+ * species B: the cluster species for the first n_cluster particles; with a
+ * second grand-canonical species, type gc2_type from index nb on; else the
+ * grand-canonical species 0. */
+static int species_nb(const oracle_system *sys, int j, int nb)
 {
-    return j < sys->n_cluster ? sys->cluster_type : 0;
+    if (j < sys->n_cluster) return sys->cluster_type;
+    if (sys->gc2_type > 0 && j >= nb) return sys->gc2_type;
+    return 0;
 }
+
+static int species(const oracle_system *sys, int j) { return species_nb(sys, j, 1 << 30); }
 
 /* Interaction energy of a mobile particle at (x, y, z) with every surface atom
  * and every mobile particle j != skip (the moved particle's energy entering
@@ -201,7 +209,16 @@ double oracle_particle_energy(const oracle_system *sys, const double *pos, int n
                               double x, double y, double z, int skip,
                               double *sum_abs, double *band, int *n_pairs)
 {
-    const int ti = skip >= 0 ? species(sys, skip) : 0;
+    return oracle_particle_energy2(sys, pos, n, n, x, y, z, skip, 0, sum_abs, band, n_pairs);
+}
+
+/* As oracle_particle_energy for a walker with nb particles of species B; a
+ * new particle (skip < 0) has potential type species_new. */
+double oracle_particle_energy2(const oracle_system *sys, const double *pos, int n, int nb,
+                               double x, double y, double z, int skip, int species_new,
+                               double *sum_abs, double *band, int *n_pairs)
+{
+    const int ti = skip >= 0 ? species_nb(sys, skip, nb) : species_new;
     double e = 0.0;
     for (int a = 0; a < sys->n_surf; ++a) {
         const double *ra = sys->surf_xyz + 3 * a;
@@ -214,7 +231,7 @@ double oracle_particle_energy(const oracle_system *sys, const double *pos, int n
     for (int j = 0; j < n; ++j) {
         if (j == skip) continue;
         const double *rj = pos + 3 * j;
-        const int tj = species(sys, j);
+        const int tj = species_nb(sys, j, nb);
         double r2 = pair_r2(sys, x, y, z, rj[0], rj[1], rj[2]);
         double phi = oracle_phi(sys, ti, tj, r2);
         account(sys, ti, tj, r2, phi, sum_abs, band, n_pairs);
@@ -227,10 +244,15 @@ double oracle_particle_energy(const oracle_system *sys, const double *pos, int n
  * slab is frozen, so surface-surface pairs are constant and left out. */
 double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
 {
+    return oracle_total_energy2(sys, pos, n, n);
+}
+
+double oracle_total_energy2(const oracle_system *sys, const double *pos, int n, int nb)
+{
     double e = 0.0;
     for (int i = 0; i < n; ++i) {
         const double *ri = pos + 3 * i;
-        const int ti = species(sys, i);
+        const int ti = species_nb(sys, i, nb);
         for (int a = 0; a < sys->n_surf; ++a) {
             const double *ra = sys->surf_xyz + 3 * a;
             e += oracle_phi(sys, ti, sys->surf_type[a],
@@ -238,7 +260,7 @@ double oracle_total_energy(const oracle_system *sys, const double *pos, int n)
         }
         for (int j = i + 1; j < n; ++j) {
             const double *rj = pos + 3 * j;
-            e += oracle_phi(sys, ti, species(sys, j),
+            e += oracle_phi(sys, ti, species_nb(sys, j, nb),
                             pair_r2(sys, ri[0], ri[1], ri[2], rj[0], rj[1], rj[2]));
         }
     }
@@ -321,13 +343,22 @@ double oracle_surrogate_energy(const oracle_system *sys, const double *pos, int 
 
 /* ---------------------------------------------------------- acceptance */
 
-static double kT_of(const oracle_system *sys, int state) { return sys->kT[state / sys->M]; }
-static double mu_of(const oracle_system *sys, int state) { return sys->mu[state % sys->M]; }
+/* States s = (l M + m) K + k with K = 1 for one grand-canonical species. */
+static int axis_K(const oracle_system *sys) { return (sys->gc2_type > 0 && sys->K > 1) ? sys->K : 1; }
+static int n_states(const oracle_system *sys) { return sys->L * sys->M * axis_K(sys); }
+static double kT_of(const oracle_system *sys, int state) { return sys->kT[state / (sys->M * axis_K(sys))]; }
+static double mu_of(const oracle_system *sys, int state) { return sys->mu[(state / axis_K(sys)) % sys->M]; }
+static double mu2_of(const oracle_system *sys, int state) { return sys->mu2[state % axis_K(sys)]; }
 
 static double ln_lambda(const oracle_system *sys, double kT)
 {
     /* Lambda = h / sqrt(2 pi m kT) (Eq. Ngrand); in reduced units lambda0/sqrt(kT) */
     return log(sys->lambda0) - 0.5 * log(kT);
+}
+
+static double ln_lambda2(const oracle_system *sys, double kT)
+{
+    return log(sys->lambda0_2) - 0.5 * log(kT);
 }
 
 static double volume(const oracle_system *sys)
@@ -343,9 +374,17 @@ static double volume(const oracle_system *sys)
  * (the insertion exponent is read as beta[mu - (E_{N+1} - E_N)]). */
 double oracle_log_alpha(const oracle_system *sys, int type, int state, int n, double dE)
 {
-    double kT = kT_of(sys, state), beta = 1.0 / kT, mu = mu_of(sys, state);
+    return oracle_log_alpha2(sys, type, 0, state, n, dE);
+}
+
+/* As oracle_log_alpha for a grand-canonical move of species `species` (0: B,
+ * 1: C, with its own mu2 and Lambda) at a state holding n_c particles of it. */
+double oracle_log_alpha2(const oracle_system *sys, int type, int species2, int state, int n, double dE)
+{
+    const int c = species2 && !(sys->mutation & 32768);
+    double kT = kT_of(sys, state), beta = 1.0 / kT, mu = c ? mu2_of(sys, state) : mu_of(sys, state);
     double lam_pow = (sys->mutation & 4) ? 1.0 : 3.0;
-    double lnL = ln_lambda(sys, kT);
+    double lnL = c ? ln_lambda2(sys, kT) : ln_lambda(sys, kT);
     double lnV = log(volume(sys));
     if (type == 0) return -beta * dE;
     if (type == 1) {
@@ -360,6 +399,23 @@ double oracle_log_alpha(const oracle_system *sys, int type, int state, int n, do
  *   1.5 (na - nb) ln(beta_a / beta_b) - (beta_a - beta_b)(eb - ea)
  *     - (beta_a mu_a - beta_b mu_b)(na - nb)
  * (the leading minus of the printed exponent is read as covering both terms). */
+/* With a second species: state a holds (N_B,a, N_C,a, E_a); both thermal
+ * wavelengths scale as beta^(1/2), so the Lambda factor takes the total N:
+ *   1.5 (N_a - N_b) ln(beta_a / beta_b) - (beta_a - beta_b)(E_b - E_a)
+ *   - (beta_a mu_a - beta_b mu_b)(N_B,a - N_B,b)
+ *   - (beta_a mu2_a - beta_b mu2_b)(N_C,a - N_C,b). */
+double oracle_exchange_log_alpha2(const oracle_system *sys, int sa, int sb, int nba, int nca,
+                                  int nbb, int ncb, double ea, double eb)
+{
+    double ba = 1.0 / kT_of(sys, sa), bb = 1.0 / kT_of(sys, sb);
+    double dn = (double)((nba + nca) - (nbb + ncb));
+    double lam = 1.5 * dn * log(ba / bb);
+    double mu_term = (ba * mu_of(sys, sa) - bb * mu_of(sys, sb)) * (double)(nba - nbb);
+    if (!(sys->mutation & 65536))
+        mu_term += (ba * mu2_of(sys, sa) - bb * mu2_of(sys, sb)) * (double)(nca - ncb);
+    return lam - (ba - bb) * (eb - ea) - mu_term;
+}
+
 double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
                                  int na, int nb, double ea, double eb)
 {
@@ -374,9 +430,17 @@ double oracle_exchange_log_alpha(const oracle_system *sys, int sa, int sb,
 
 /* ---------------------------------------------------------------- sweeps */
 
-static void observe(const oracle_system *sys, oracle_hist *h, int state, int w, int n, double e)
+static void observe(const oracle_system *sys, oracle_hist *h, int state, int w, int n, int nc, double e)
 {
     if (!h) return;
+    if (sys->gc2_type > 0) {
+        /* the second species' count; n is N_B here */
+        if (h->hN2) h->hN2[(int64_t)state * (sys->nmax + 1) + nc] += 1;
+        if (h->moments2) {
+            h->moments2[2 * (int64_t)state] += nc;
+            h->moments2[2 * (int64_t)state + 1] += (double)nc * nc;
+        }
+    }
     if (h->hE) {
         /* the state's own window (Sec. II.B: the observations of each state) */
         const int row = (sys->mutation & 16384) ? w : state;
@@ -398,7 +462,8 @@ static void observe(const oracle_system *sys, oracle_hist *h, int state, int w, 
         double k = floor((e - sys->e_lo) / sys->e_bin);
         if (sys->mutation & 8192) k += 1.0;
         if (k >= 0.0 && k < (double)sys->n_e_bins) {
-            int64_t idx = (int64_t)n * sys->n_e_bins + (int64_t)k;
+            const int64_t row = sys->gc2_type > 0 ? (int64_t)n * (sys->nmax + 1) + nc : (int64_t)n;
+            int64_t idx = row * sys->n_e_bins + (int64_t)k;
 #ifdef _OPENMP
 #pragma omp atomic
 #endif
@@ -426,9 +491,11 @@ enum { MOVE_MIXED = 0, MOVE_GC = 1, MOVE_DISPLACE = 2 };
  * draws A = Philox((k, t, w, 0)) and B = Philox((k, t, w, 1)), evaluates the
  * move and applies it if accepted (positions, *n_io, *e_io).  mv receives its
  * record. */
-static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, double *e_io,
+static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, int *nb_io, double *e_io,
                        int state, uint32_t k, uint32_t t, int kind, oracle_move *out)
 {
+    const int two = sys->gc2_type > 0;
+    int nb = two ? *nb_io : *n_io;   /* species B occupies [0, nb) */
     const double lx = sys->Lx, ly = sys->Ly, lz = sys->Lz;
     const double delta = f32(sys->max_disp);
     const double height = f32(sys->z_hi - sys->z_lo);
@@ -449,6 +516,10 @@ static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, 
         /* removal if y1 < 0.5, else insertion (Sec. II.A.1) */
         mv.type = (B[2] >> 31) == 0u ? 2 : 1;
     }
+    /* with a second species, the next bit of B2 picks the species of a
+     * grand-canonical move: 0 B, 1 C */
+    const int gcs = (two && mv.type != 0) ? (int)((B[2] >> 30) & 1u) : 0;
+    const int nc = n - nb;
     double nx = 0, ny = 0, nz = 0;  /* new position (displace/insert) */
     int i = -1;
     if (mv.type == 0) {
@@ -474,35 +545,45 @@ static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, 
             mv.status = 2;
             goto decided;
         }
-        double e_new = oracle_particle_energy(sys, pos, n, nx, ny, nz, i,
-                                              &mv.sum_abs, &mv.band, &mv.n_pairs);
-        double e_old = oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
-                                              &mv.sum_abs, &mv.band, &mv.n_pairs);
+        double e_new = oracle_particle_energy2(sys, pos, n, nb, nx, ny, nz, i, 0,
+                                               &mv.sum_abs, &mv.band, &mv.n_pairs);
+        double e_old = oracle_particle_energy2(sys, pos, n, nb, ri[0], ri[1], ri[2], i, 0,
+                                               &mv.sum_abs, &mv.band, &mv.n_pairs);
         mv.dE = e_new - e_old;
         mv.log_alpha = -beta * mv.dE;
     } else if (mv.type == 1) {
         /* insertion at a uniform point of the region (Sec. II.A.1) */
         if (n == sys->nmax) { mv.status = 1; goto decided; }
-        mv.index = n;
+        /* a new B goes to index nb (the first C moves to the end), a new C to n */
+        mv.index = (two && gcs == 0) ? nb : n;
         nx = f32(lx * u24(A[1]));
         ny = f32(ly * u24(A[2]));
         nz = f32(sys->z_lo + f32(height * u24(A[3])));
         if (nx >= lx) nx = f32(nx - lx);
         if (ny >= ly) ny = f32(ny - ly);
         if (sys->periodic_z && nz >= lz) nz = f32(nz - lz);
-        mv.dE = oracle_particle_energy(sys, pos, n, nx, ny, nz, -1,
-                                       &mv.sum_abs, &mv.band, &mv.n_pairs);
-        mv.log_alpha = oracle_log_alpha(sys, 1, state, n_gc(sys, n), mv.dE);
+        mv.dE = oracle_particle_energy2(sys, pos, n, nb, nx, ny, nz, -1, gcs ? sys->gc2_type : 0,
+                                        &mv.sum_abs, &mv.band, &mv.n_pairs);
+        mv.log_alpha = two ? oracle_log_alpha2(sys, 1, gcs, state, gcs ? nc : nb, mv.dE)
+                           : oracle_log_alpha(sys, 1, state, n_gc(sys, n), mv.dE);
     } else {
         /* removal of grand-canonical particle i, (i-1)/N <= y2 < i/N
          * (Sec. II.A.1), counted among the N_B of that species */
-        if (n == sys->n_cluster) { mv.status = 1; goto decided; }
-        i = sys->n_cluster + (int)(((uint64_t)B[0] * (uint64_t)(n - sys->n_cluster)) >> 32);
+        if (two) {
+            /* uniformly among the particles of the chosen species */
+            const int cnt = gcs ? nc : nb, first = gcs ? nb : 0;
+            if (cnt == 0) { mv.status = 1; goto decided; }
+            i = first + (int)(((uint64_t)B[0] * (uint64_t)cnt) >> 32);
+        } else {
+            if (n == sys->n_cluster) { mv.status = 1; goto decided; }
+            i = sys->n_cluster + (int)(((uint64_t)B[0] * (uint64_t)(n - sys->n_cluster)) >> 32);
+        }
         mv.index = i;
         const double *ri = pos + 3 * i;
-        mv.dE = -oracle_particle_energy(sys, pos, n, ri[0], ri[1], ri[2], i,
-                                        &mv.sum_abs, &mv.band, &mv.n_pairs);
-        mv.log_alpha = oracle_log_alpha(sys, 2, state, n_gc(sys, n), mv.dE);
+        mv.dE = -oracle_particle_energy2(sys, pos, n, nb, ri[0], ri[1], ri[2], i, 0,
+                                         &mv.sum_abs, &mv.band, &mv.n_pairs);
+        mv.log_alpha = two ? oracle_log_alpha2(sys, 2, gcs, state, gcs ? nc : nb, mv.dE)
+                           : oracle_log_alpha(sys, 2, state, n_gc(sys, n), mv.dE);
     }
     if (sys->da) {
         /* stage 1 with the surrogate energy change */
@@ -529,9 +610,23 @@ static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, 
             double *ri = pos + 3 * i;
             ri[0] = nx; ri[1] = ny; ri[2] = nz;
         } else if (mv.type == 1) {
-            double *rn = pos + 3 * n;
-            rn[0] = nx; rn[1] = ny; rn[2] = nz;
+            if (two && gcs == 0) {
+                /* the first C (if any) moves to the end, the new B takes its index */
+                memmove(pos + 3 * n, pos + 3 * nb, 3 * sizeof(double));
+                double *rn = pos + 3 * nb;
+                rn[0] = nx; rn[1] = ny; rn[2] = nz;
+                nb += 1;
+            } else {
+                double *rn = pos + 3 * n;
+                rn[0] = nx; rn[1] = ny; rn[2] = nz;
+            }
             n += 1;
+        } else if (two && gcs == 0) {
+            /* the last B fills the gap, the last C fills the last B's index */
+            memmove(pos + 3 * i, pos + 3 * (nb - 1), 3 * sizeof(double));
+            memmove(pos + 3 * (nb - 1), pos + 3 * (n - 1), 3 * sizeof(double));
+            nb -= 1;
+            n -= 1;
         } else {
             int gone = (sys->mutation & 64) ? (i + 1) % n : i;
             memcpy(pos + 3 * gone, pos + 3 * (n - 1), 3 * sizeof(double));
@@ -541,6 +636,7 @@ static void trial_move(const oracle_system *sys, int w, double *pos, int *n_io, 
     }
 decided:
     *n_io = n;
+    if (two) *nb_io = nb;
     *e_io = e;
     *out = mv;
 }
@@ -552,23 +648,25 @@ static void count_move(int64_t *counts, int w, const oracle_move *mv)
     counts[6 * (int64_t)w + 2 * mv->type + 1] += mv->accepted;
 }
 
-static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr,
+static void sweep_walker(const oracle_system *sys, int w, double *pos, int32_t *n_ptr, int32_t *nb_ptr,
                          double *e_ptr, int state, uint32_t t0, int n_sweeps,
                          oracle_hist *hist, oracle_move *trace, int64_t *counts)
 {
     int n = *n_ptr;
+    int nb = nb_ptr ? *nb_ptr : n;
     double e = *e_ptr;
     for (int ts = 0; ts < n_sweeps; ++ts) {
         uint32_t t = t0 + (uint32_t)ts;
         for (int k = 0; k < sys->moves_per_sweep; ++k) {
             oracle_move mv;
-            trial_move(sys, w, pos, &n, &e, state, (uint32_t)k, t, MOVE_MIXED, &mv);
+            trial_move(sys, w, pos, &n, &nb, &e, state, (uint32_t)k, t, MOVE_MIXED, &mv);
             count_move(counts, w, &mv);
             if (trace) trace[((int64_t)ts * sys->moves_per_sweep + k)] = mv;
         }
-        observe(sys, hist, state, w, n - sys->n_cluster, e);
+        observe(sys, hist, state, w, sys->gc2_type > 0 ? nb : n - sys->n_cluster, n - nb, e);
     }
     *n_ptr = n;
+    if (nb_ptr) *nb_ptr = nb;
     *e_ptr = e;
 }
 
@@ -582,12 +680,27 @@ int oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32_t 
                   int n_sweeps, oracle_hist *hist, oracle_move *trace,
                   int64_t *counts, int n_threads)
 {
-    int S = sys->L * sys->M;
+    if (sys->gc2_type > 0) return -1;   /* two species: oracle_sweeps2 */
+    return oracle_sweeps2(sys, n_walkers, pos, n, NULL, energy, state_of_walker, t0, n_sweeps, hist, trace,
+                          counts, n_threads);
+}
+
+int oracle_sweeps2(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
+                   double *energy, const int32_t *state_of_walker, uint32_t t0,
+                   int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                   int64_t *counts, int n_threads)
+{
+    int S = n_states(sys);
     if (n_walkers != S || sys->nmax < 1 || sys->moves_per_sweep < 0 || n_sweeps < 0) return -1;
+    if (sys->gc2_type > 0 && (!nb || sys->n_cluster > 0 || sys->da)) return -1;
     char *seen = (char *)calloc((size_t)S, 1);
     for (int w = 0; w < S; ++w) {
         int s = state_of_walker[w];
-        if (s < 0 || s >= S || seen[s] || n[w] < 0 || n[w] > sys->nmax) { free(seen); return -1; }
+        if (s < 0 || s >= S || seen[s] || n[w] < 0 || n[w] > sys->nmax ||
+            (nb && (nb[w] < 0 || nb[w] > n[w]))) {
+            free(seen);
+            return -1;
+        }
         seen[s] = 1;
     }
     free(seen);
@@ -597,7 +710,7 @@ int oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32_t 
 #endif
     for (int w = 0; w < S; ++w) {
         oracle_move *tr = trace ? trace + (int64_t)w * n_sweeps * sys->moves_per_sweep : NULL;
-        sweep_walker(sys, w, pos + (int64_t)w * sys->nmax * 3, n + w, energy + w,
+        sweep_walker(sys, w, pos + (int64_t)w * sys->nmax * 3, n + w, nb ? nb + w : NULL, energy + w,
                      state_of_walker[w], t0, n_sweeps, hist, tr, counts);
     }
     (void)n_threads;
@@ -619,33 +732,51 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
                     const double *energy, int32_t *state_of_walker,
                     int32_t *walker_of_state, int64_t *ex_counts)
 {
-    static const int DL[4] = {1, 0, 1, 1};
-    static const int DM[4] = {0, 1, 1, -1};
-    int L = sys->L, M = sys->M, S = L * M;
+    if (sys->gc2_type > 0) return -1;   /* two species: oracle_exchange2 */
+    return oracle_exchange2(sys, e, n, NULL, energy, state_of_walker, walker_of_state, ex_counts);
+}
+
+/* With a second species on a third axis (K > 1) a fifth direction joins the
+ * four: type = (C0 * 5) >> 32, type 4 pairing (l, m, k) with (l, m, k + 1)
+ * for k of the drawn parity; the other directions act in every k-slice
+ * alike.  ex_counts is then [S][5][2]. */
+int oracle_exchange2(const oracle_system *sys, uint32_t e, const int32_t *n, const int32_t *nb,
+                     const double *energy, int32_t *state_of_walker,
+                     int32_t *walker_of_state, int64_t *ex_counts)
+{
+    static const int DL[5] = {1, 0, 1, 1, 0};
+    static const int DM[5] = {0, 1, 1, -1, 0};
+    static const int DK[5] = {0, 0, 0, 0, 1};
+    const int K = axis_K(sys), n_dir = K > 1 ? 5 : 4;
+    int L = sys->L, M = sys->M, S = L * M * K;
+    if (sys->gc2_type > 0 && !nb) return -1;
     for (int s = 0; s < S; ++s) {
         int w = walker_of_state[s];
         if (w < 0 || w >= S || state_of_walker[w] != s) return -1;
     }
     uint32_t C[4];
     draw(sys, e, 0u, 0u, 2u, C);
-    int type = (int)(((uint64_t)C[0] * 4u) >> 32);
+    int type = (int)(((uint64_t)C[0] * (uint64_t)n_dir) >> 32);
     int parity = (int)(C[1] >> 31);
     int accepted = 0;
     for (int l = 0; l < L; ++l) {
         for (int m = 0; m < M; ++m) {
-            int key = DL[type] ? l : m;
+          for (int k = 0; k < K; ++k) {
+            int key = DK[type] ? k : (DL[type] ? l : m);
             if ((key & 1) != parity) continue;
-            int l2 = l + DL[type], m2 = m + DM[type];
-            if (l2 < 0 || l2 >= L || m2 < 0 || m2 >= M) continue;
-            int a = l * M + m, b = l2 * M + m2;
+            int l2 = l + DL[type], m2 = m + DM[type], k2 = k + DK[type];
+            if (l2 < 0 || l2 >= L || m2 < 0 || m2 >= M || k2 >= K) continue;
+            int a = (l * M + m) * K + k, b = (l2 * M + m2) * K + k2;
             int wa = walker_of_state[a], wb = walker_of_state[b];
-            double la = oracle_exchange_log_alpha(sys, a, b, n[wa], n[wb], energy[wa], energy[wb]);
+            double la = nb ? oracle_exchange_log_alpha2(sys, a, b, nb[wa], n[wa] - nb[wa], nb[wb], n[wb] - nb[wb],
+                                                        energy[wa], energy[wb])
+                           : oracle_exchange_log_alpha(sys, a, b, n[wa], n[wb], energy[wa], energy[wb]);
             uint32_t D[4];
             draw(sys, e, (uint32_t)a, 0u, 3u, D);
             int acc = log(u32_open(D[0])) < la;
             if (ex_counts) {
-                ex_counts[8 * (int64_t)a + 2 * type] += 1;
-                ex_counts[8 * (int64_t)a + 2 * type + 1] += acc;
+                ex_counts[2 * n_dir * (int64_t)a + 2 * type] += 1;
+                ex_counts[2 * n_dir * (int64_t)a + 2 * type + 1] += acc;
             }
             if (acc) {
                 walker_of_state[a] = wb;
@@ -654,6 +785,7 @@ int oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
                 state_of_walker[wb] = a;
                 accepted += 1;
             }
+          }
         }
     }
     return accepted;
@@ -686,6 +818,7 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
                  int64_t *counts, int64_t *ex_counts)
 {
     int S = sys->L * sys->M;
+    if (sys->gc2_type > 0) return -1;   /* one grand-canonical species only */
     if (n_walkers != S || n_steps < 0 || n_canonical < 0 || !(x0 >= 0.0 && x0 <= 1.0)) return -1;
     for (int w = 0; w < S; ++w)
         if (n[w] < 0 || n[w] > sys->nmax || state_of_walker[w] < 0 || state_of_walker[w] >= S) return -1;
@@ -707,7 +840,7 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
             for (int w = 0; w < S; ++w) {
                 int nw = n[w];
                 oracle_move mv;
-                trial_move(sys, w, pos + (int64_t)w * sys->nmax * 3, &nw, energy + w, state_of_walker[w],
+                trial_move(sys, w, pos + (int64_t)w * sys->nmax * 3, &nw, &nw, energy + w, state_of_walker[w],
                            0u, t, MOVE_GC, &mv);
                 n[w] = nw;
                 count_move(counts, w, &mv);
@@ -736,12 +869,12 @@ int oracle_cycle(const oracle_system *sys, int n_walkers, double *pos, int32_t *
             double *pw = pos + (int64_t)w * sys->nmax * 3;
             for (int k = 1; k <= n_canonical; ++k) {
                 oracle_move mv;
-                trial_move(sys, w, pw, &nw, energy + w, state, (uint32_t)k, t, canonical_kind, &mv);
+                trial_move(sys, w, pw, &nw, &nw, energy + w, state, (uint32_t)k, t, canonical_kind, &mv);
                 count_move(counts, w, &mv);
                 if (trace) trace[((int64_t)w * n_steps + ts) * per_step + k] = mv;
             }
             n[w] = nw;
-            if (gc || n_canonical > 0) observe(sys, hist, state, w, nw - sys->n_cluster, energy[w]);
+            if (gc || n_canonical > 0) observe(sys, hist, state, w, nw - sys->n_cluster, 0, energy[w]);
         }
     }
     return n_exchange;
@@ -894,6 +1027,7 @@ int oracle_md(const oracle_system *sys, int n_walkers, double *pos, const int32_
               int n_threads)
 {
     int S = sys->L * sys->M;
+    if (sys->gc2_type > 0) return -1;   /* one grand-canonical species only */
     if (n_walkers != S || n_steps < 0 || !(dt > 0.0) || !(tau > 0.0)) return -1;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);

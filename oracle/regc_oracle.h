@@ -74,6 +74,16 @@ typedef struct {
     /* sheared cell: lattice vectors (Lx, 0) and (shear Ly, Ly); x coordinates
      * are the cell-frame u = x - shear y (0: rectangular) */
     double        shear;
+    /* a second grand-canonical species C (more than one reactive gas, the
+     * outlook of Sec. IV; gc2_type 0: none): potential type gc2_type
+     * (1..n_types-1), chemical potentials mu2[K] on a third axis of the grid
+     * (state s = (l M + m) K + k holds kT[l], mu[m], mu2[k]) and thermal
+     * wavelength lambda0_2 / sqrt(kT).  A walker's particles [0, N_B) are
+     * species B (type 0), [N_B, N) species C.  Not combined with a cluster. */
+    int           gc2_type;
+    int           K;
+    const double *mu2;
+    double        lambda0_2;
 } oracle_system;
 
 /* One trial move as the oracle executed it. */
@@ -109,6 +119,11 @@ typedef struct {
     const double *hE_lo;     /* [S] */
     double        hE_bin;
     int           hE_bins;
+    /* second species (gc2_type != 0): occupation counts of N_C and its
+     * moments; hN and moments then hold N_B, and the pooled histogram is
+     * [(nmax+1)^2][n_e_bins] with row N_B (nmax+1) + N_C */
+    int64_t      *hN2;       /* [S][nmax+1] */
+    double       *moments2;  /* [S][2]: sum N_C, sum N_C^2 */
 } oracle_hist;
 
 #ifdef __cplusplus
@@ -140,6 +155,23 @@ int    oracle_md(const oracle_system *sys, int n_walkers, double *pos, const int
 int    oracle_exchange(const oracle_system *sys, uint32_t e, const int32_t *n,
                        const double *energy, int32_t *state_of_walker,
                        int32_t *walker_of_state, int64_t *ex_counts);
+/* Two grand-canonical species: nb [walkers] holds each walker's N_B (its
+ * particles [0, N_B) are species B, the rest species C).  The exchange has a
+ * fifth direction, mu2 (ex_counts [S][5][2]) when K > 1. */
+double oracle_particle_energy2(const oracle_system *sys, const double *pos, int n, int nb,
+                               double x, double y, double z, int skip, int species_new,
+                               double *sum_abs, double *band, int *n_pairs);
+double oracle_total_energy2(const oracle_system *sys, const double *pos, int n, int nb);
+double oracle_log_alpha2(const oracle_system *sys, int type, int species, int state, int n_c, double dE);
+double oracle_exchange_log_alpha2(const oracle_system *sys, int sa, int sb, int nba, int nca,
+                                  int nbb, int ncb, double ea, double eb);
+int    oracle_sweeps2(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
+                      double *energy, const int32_t *state_of_walker, uint32_t t0,
+                      int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                      int64_t *counts, int n_threads);
+int    oracle_exchange2(const oracle_system *sys, uint32_t e, const int32_t *n, const int32_t *nb,
+                        const double *energy, int32_t *state_of_walker,
+                        int32_t *walker_of_state, int64_t *ex_counts);
 #ifdef __cplusplus
 }
 #endif

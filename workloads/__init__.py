@@ -72,6 +72,13 @@ class Problem:
     # sheared (oblique) cell: lattice vectors (Lx, 0) and (shear Ly, Ly); every
     # x coordinate is then the cell-frame u = x - shear y
     shear: float = 0.0
+    # a second grand-canonical species C of potential type gc2_type (0: none)
+    # with chemical potentials mu2 [K] on a third grid axis (state
+    # s = (l M + m) K + k) and thermal wavelength lambda0_2 / sqrt(kT); a
+    # walker's particles [0, N_B) are species B, [N_B, N) species C
+    gc2_type: int = 0
+    mu2: np.ndarray = None
+    lambda0_2: float = 1.0
 
     def __post_init__(self):
         # the C ABI carries these as binary32: round them here, once, so that
@@ -91,8 +98,20 @@ class Problem:
         return int(len(self.mu))
 
     @property
+    def K(self) -> int:
+        return int(len(self.mu2)) if self.gc2_type else 1
+
+    @property
     def S(self) -> int:
-        return self.L * self.M
+        return self.L * self.M * self.K
+
+    def state_params(self):
+        """Per state s: (kT, mu, mu2) with s = (l M + m) K + k."""
+        s = np.arange(self.S)
+        kT = np.asarray(self.kT)[s // (self.M * self.K)]
+        mu = np.asarray(self.mu)[(s // self.K) % self.M]
+        mu2 = np.asarray(self.mu2)[s % self.K] if self.gc2_type else np.zeros(self.S)
+        return kT, mu, mu2
 
     @property
     def n_surf(self) -> int:
@@ -392,6 +411,41 @@ def tiny_box(nmax: int = 2, rc: float = 1.5, eps_sg: float = 1.0, eps_gg: float 
         surf_type=np.ones(2, np.int32), kT=np.asarray(kT, float), mu=np.asarray(mu, float),
         lambda0=1.0, nmax=nmax, moves_per_sweep=20, max_disp=0.3, p_disp=1.0 / 3.0,
         seed=seed, e_lo=centred_e_lo(-40.0, 0.05), e_bin=0.05, n_e_bins=1600, name="tiny_box")
+
+
+def two_gas_small(L: int = 2, M: int = 3, K: int = 3, nmax: int = 32, seed: int = 0) -> Problem:
+    """Two reactive gases over configuration 1's fcc(100) slab (the outlook of
+    Sec. IV: more than one grand-canonical species): B (type 0: eps_BB 1,
+    sigma 1, eps_sB 2) and C (type 2: eps_CC 0.6, sigma_CC 0.9, eps_BC 0.8,
+    sigma_BC 0.95, eps_sC 1.2, sigma_sC 0.95, a thermal wavelength 0.7 of B's),
+    on an L x M x K grid of kT (0.6 .. 1.5), mu_B (-6 .. -2), mu_C (-6 .. -2)."""
+    xyz, lx, ly, ztop = fcc100_slab(4, 4, 2, 1.5625)
+    eps = np.zeros((4, 4))
+    sig = np.ones((4, 4))
+    eps[0, 0], eps[0, 1], eps[1, 0] = 1.0, 2.0, 2.0
+    eps[2, 2], sig[2, 2] = 0.6, 0.9
+    eps[0, 2] = eps[2, 0] = 0.8
+    sig[0, 2] = sig[2, 0] = 0.95
+    eps[1, 2] = eps[2, 1] = 1.2
+    sig[1, 2] = sig[2, 1] = 0.95
+    return Problem(
+        n_types=3, eps=f32(eps), sigma=f32(sig), rc=2.5, Lx=lx, Ly=ly, Lz=10.0, periodic_z=0,
+        z_lo=ztop, z_hi=10.0, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
+        max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
+        e_lo=centred_e_lo(-float(nmax) * 12.0, 0.25), e_bin=0.25,
+        n_e_bins=int(round(float(nmax) * 13.0 / 0.25)), name="two_gas_small",
+        gc2_type=2, mu2=mu_grid(K), lambda0_2=0.7)
+
+
+def two_gas_initial(problem: Problem, nb, nc, seed: int, min_dist: float = 0.9):
+    """Seeded walkers of a two-species problem: walker w holds nb[w]
+    particles of B then nc[w] of C at uniform positions of the gas region.
+    Returns (pos [S, nmax, 3], n [S], nb [S])."""
+    nb = np.broadcast_to(np.asarray(nb, np.int32), (problem.S,)).copy()
+    nc = np.broadcast_to(np.asarray(nc, np.int32), (problem.S,)).copy()
+    pos, n = initial_walkers(problem, nb + nc, seed=seed, min_dist=min_dist)
+    return pos, n, nb
 
 
 def ideal_gas(problem: Problem) -> Problem:
