@@ -160,6 +160,43 @@ REGC_API regc_status regc_init_grid(const regc_potential *pot, const regc_surfac
                            const regc_grid_spec *grid, uint64_t seed, void *cuda_stream,
                            regc_handle **out);
 
+/* A second grand-canonical species C: more than one reactive gas (the
+ * outlook of Sec. IV).  The grid gains a third axis: state
+ * s = (l M + m) K + k holds kT[l], mu[m] of species B (type 0) and mu[k] of
+ * species C, and S = L M K.  Species C is inserted and removed by the rules
+ * of Sec. II.A.1 with its own chemical potential and thermal wavelength
+ * Lambda_C(kT) = lambda0 / sqrt(kT); a grand-canonical move picks its species
+ * by bit 30 of Philox word B2 (0: B, 1: C), then removal or insertion by bit
+ * 31 as for one species; removal picks uniformly among the particles of that
+ * species.  Displacement picks among all N particles.  A walker keeps its B
+ * particles at indices [0, N_B) and its C particles at [N_B, N): a new B takes
+ * index N_B (the C there moves to the end), a removed B's index is filled by
+ * the last B and that one's by the last C; a new C is appended, a removed C
+ * replaced by the last particle.  The exchange of Eq. Pacc takes both
+ * species: ln alpha = 1.5 (N_a - N_b) ln(b_a / b_b) - (b_a - b_b)(E_b - E_a)
+ * - (b_a mu_a - b_b mu_b)(N_B,a - N_B,b) - (b_a mu2_a - b_b mu2_b)(N_C,a - N_C,b)
+ * (both wavelengths scale as b^(1/2)), and with K > 1 a fifth direction
+ * along mu2 joins the four, drawn as (C0 * 5) >> 32, pairing (l, m, k) with
+ * (l, m, k + 1) for k of the drawn parity (the others act within every
+ * k-slice).  Histograms: hN and the moments hold N_B, regc_histograms2 gives
+ * N_C's; the pooled histogram has (nmax + 1)^2 rows, row N_B (nmax + 1) + N_C.
+ * Not available with two species: the cluster, delayed acceptance, MD, the
+ * REGC cycle, structural samples, surrogate evaluation and harvesting, batches
+ * and regc_reweight (regc_reweight2 instead). */
+typedef struct {
+    int           type;      /* potential type of species C, 1..n_types-1 */
+    int           K;         /* >= 1; L M K <= 65536 */
+    const double *mu;        /* host [K], finite */
+    double        lambda0;   /* > 0 */
+} regc_species2;
+
+/* As regc_init_grid, with a second grand-canonical species.  Every walker
+ * starts empty.  Errors: those of regc_init_grid, and REGC_EINVAL for a bad
+ * species2 or (nmax + 1)^2 n_e_bins beyond 2^31. */
+REGC_API regc_status regc_init_grid2(const regc_potential *pot, const regc_surface *surf,
+                                     const regc_grid_spec *grid, const regc_species2 *species2,
+                                     uint64_t seed, void *cuda_stream, regc_handle **out);
+
 /* Run n_sweeps sweeps (n_sweeps x moves_per_sweep trial moves) on every walker
  * (Sec. II.A.1 insertion/removal, Sec. II.A.3 displacement) at the walkers'
  * current states, and observe each walker once per sweep into its state's
@@ -246,11 +283,17 @@ REGC_API regc_status regc_cycle_traced(regc_handle *h, int n_steps, double x0, i
                                        regc_move_record *trace, int *n_exchanges);
 
 /* Copy the histograms to caller-owned host buffers (any may be NULL):
- * hN [S][nmax+1], hNE [nmax+1][n_e_bins], omega [S], moments [S][4]
+ * hN [S][nmax+1], hNE [nmax+1][n_e_bins] (with a second species
+ * [(nmax+1)^2][n_e_bins], row N_B (nmax+1) + N_C), omega [S], moments [S][4]
  * (sum N, sum N^2, sum E, sum E^2), e_out [S] (observations with E outside
  * the E window).  Synchronous. */
 REGC_API regc_status regc_histograms(regc_handle *h, int64_t *hN, int64_t *hNE, int64_t *omega,
                             double *moments, int64_t *e_out);
+
+/* Second species: hN2 [S][nmax+1] occupation counts of N_C and moments2
+ * [S][2] (sum N_C, sum N_C^2) per state (host, either may be NULL).
+ * Synchronous.  Errors: REGC_EINVAL (one species). */
+REGC_API regc_status regc_histograms2(regc_handle *h, int64_t *hN2, double *moments2);
 
 /* Zero every histogram and counter (not the walkers). */
 REGC_API regc_status regc_reset_histograms(regc_handle *h);
@@ -297,6 +340,17 @@ REGC_API void regc_free(regc_handle *h);
  * hard-core guard radius (every walker is then left empty, N = 0). */
 REGC_API regc_status regc_set_walkers(regc_handle *h, const float *pos, const int32_t *n,
                              const int32_t *state_of_walker);
+
+/* As regc_set_walkers with species B's counts nb [S] (0 <= nb[w] <= n[w]:
+ * particles [0, nb[w]) of walker w are B, the rest C).  nb NULL (and
+ * regc_set_walkers) makes every particle B. */
+REGC_API regc_status regc_set_walkers2(regc_handle *h, const float *pos, const int32_t *n, const int32_t *nb,
+                                       const int32_t *state_of_walker);
+
+/* As regc_get_walkers, with species B's counts nb [S] (second species only;
+ * REGC_EINVAL otherwise). */
+REGC_API regc_status regc_get_walkers2(regc_handle *h, float *pos, int32_t *n, int32_t *nb, double *energy,
+                                       int32_t *state_of_walker);
 
 /* A second mobile species, the "cluster" (not in the paper; the cluster-in-
  * gas workload): particles 0..n_cluster-1 of every walker are of potential
@@ -345,7 +399,8 @@ REGC_API regc_status regc_checkpoint(regc_handle *h, void *buf, size_t capacity,
 REGC_API regc_status regc_restore(regc_handle *h, const void *buf, size_t length);
 
 /* Counters (host buffers, any may be NULL): moves [S walkers][3 types][trials,
- * accepts]; exchanges [S lower states][4 directions][attempts, accepts];
+ * accepts]; exchanges [S lower states][4 directions (5 with a second species
+ * on K > 1 chemical potentials)][attempts, accepts];
  * pairs [6]: pairs within rc of the committed moves, candidate pairs whose
  * distance was evaluated (including speculative evaluations that were
  * discarded), evaluation rounds, move evaluations, moves screened by the

@@ -36,6 +36,10 @@ class Surface(C.Structure):
                 ("z_lo", C.c_float), ("z_hi", C.c_float), ("shear", C.c_float)]
 
 
+class Species2(C.Structure):
+    _fields_ = [("type", C.c_int), ("K", C.c_int), ("mu", C.POINTER(C.c_double)), ("lambda0", C.c_double)]
+
+
 class GridSpec(C.Structure):
     _fields_ = [("L", C.c_int), ("M", C.c_int), ("kT", C.POINTER(C.c_double)),
                 ("mu", C.POINTER(C.c_double)), ("lambda0", C.c_double), ("nmax", C.c_int),
@@ -65,6 +69,11 @@ _h = C.c_void_p
 SIGNATURES = {
     "regc_init_grid": ([C.POINTER(Potential), C.POINTER(Surface), C.POINTER(GridSpec), C.c_uint64,
                         C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "regc_init_grid2": ([C.POINTER(Potential), C.POINTER(Surface), C.POINTER(GridSpec), C.POINTER(Species2),
+                         C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "regc_histograms2": ([_h, _lp, _dp], C.c_int),
+    "regc_set_walkers2": ([_h, _fp, _ip, _ip, _ip], C.c_int),
+    "regc_get_walkers2": ([_h, _fp, _ip, _ip, _dp, _ip], C.c_int),
     "regc_sweep": ([_h, C.c_int], C.c_int),
     "regc_sweep_traced": ([_h, C.c_int, C.c_void_p], C.c_int),
     "regc_exchange": ([_h], C.c_int),

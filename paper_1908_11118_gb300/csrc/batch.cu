@@ -214,7 +214,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     *out = nullptr;
     if (!handles || count < 1 || sweeps_per_step < 1) return REGC_EINVAL;
     for (int i = 0; i < count; ++i) {
-        if (!handles[i] || handles[i]->P.delayed || handles[i]->need_walkers) return REGC_EINVAL;
+        if (!handles[i] || handles[i]->P.delayed || handles[i]->need_walkers || handles[i]->P.gc2) return REGC_EINVAL;
         if (handles[i]->sticky != REGC_OK) return handles[i]->sticky;
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return REGC_EINVAL;

@@ -12,29 +12,47 @@ namespace regc {
 namespace {
 
 // One exchange attempt e of one (T, mu) grid, by the threads of one CTA.
+// With a second species on a third axis (K > 1) a fifth direction, along
+// mu2, joins the four: type = (C0 * 5) >> 32, pairing (l, m, k) with
+// (l, m, k + 1) for k of the drawn parity; the other directions act within
+// every k-slice.  With two species the swap rule takes both: the Lambda
+// factor the total N (both wavelengths scale as beta^(1/2)), the mu terms
+// each species' count.
 __device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t e) {
+    const int K = X.K;
+    const int n_dir = K > 1 ? 5 : 4;
     const U4 C = philox(e, 0u, 0u, 2u, X.key0, X.key1);
-    const int type = (int)(((unsigned long long)C.x * 4ull) >> 32);
+    const int type = (int)(((unsigned long long)C.x * (unsigned long long)n_dir) >> 32);
     const int parity = (int)(C.y >> 31);
-    const int dl = type == 1 ? 0 : 1;
-    const int dm = type == 0 ? 0 : (type == 3 ? -1 : 1);
-    const int S = X.L * X.M;
+    const int dk = type == 4 ? 1 : 0;
+    const int dl = (type == 1 || type == 4) ? 0 : 1;
+    const int dm = (type == 0 || type == 4) ? 0 : (type == 3 ? -1 : 1);
+    const int S = X.L * X.M * K;
     for (int a = threadIdx.x; a < S; a += blockDim.x) {
-        const int l = a / X.M, m = a - (a / X.M) * X.M;
-        const int key = dl ? l : m;
+        const int lm = a / K, k = a - lm * K;
+        const int l = lm / X.M, m = lm - l * X.M;
+        const int key = dk ? k : (dl ? l : m);
         if ((key & 1) != parity) continue;
-        const int l2 = l + dl, m2 = m + dm;
-        if (l2 >= X.L || m2 < 0 || m2 >= X.M) continue;
-        const int b = l2 * X.M + m2;
+        const int l2 = l + dl, m2 = m + dm, k2 = k + dk;
+        if (l2 >= X.L || m2 < 0 || m2 >= X.M || k2 >= K) continue;
+        const int b = (l2 * X.M + m2) * K + k2;
         const int wa = X.walker_of_state[a], wb = X.walker_of_state[b];
         const double dn = (double)(X.n[wa] - X.n[wb]);
         const double ea = (double)X.efix[wa] * kFixUnit, eb = (double)X.efix[wb] * kFixUnit;
-        const double la = 1.5 * dn * (X.lnbeta[a] - X.lnbeta[b]) - (X.beta[a] - X.beta[b]) * (eb - ea) -
-                          (X.bmu[a] - X.bmu[b]) * dn;
+        double la;
+        if (X.nb) {
+            const double dnb = (double)(X.nb[wa] - X.nb[wb]);
+            const double dnc = dn - dnb;
+            la = 1.5 * dn * (X.lnbeta[a] - X.lnbeta[b]) - (X.beta[a] - X.beta[b]) * (eb - ea) -
+                 (X.bmu[a] - X.bmu[b]) * dnb - (X.bmu2[a] - X.bmu2[b]) * dnc;
+        } else {
+            la = 1.5 * dn * (X.lnbeta[a] - X.lnbeta[b]) - (X.beta[a] - X.beta[b]) * (eb - ea) -
+                 (X.bmu[a] - X.bmu[b]) * dn;
+        }
         const U4 D = philox(e, (uint32_t)a, 0u, 3u, X.key0, X.key1);
         const bool acc = log(((double)D.x + 0.5) * 2.3283064365386963e-10) < la;
-        X.ex_counts[8 * a + 2 * type] += 1;
-        X.ex_counts[8 * a + 2 * type + 1] += acc;
+        X.ex_counts[2 * n_dir * a + 2 * type] += 1;
+        X.ex_counts[2 * n_dir * a + 2 * type + 1] += acc;
         if (acc) {
             X.walker_of_state[a] = wb;
             X.walker_of_state[b] = wa;

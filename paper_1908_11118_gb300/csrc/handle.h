@@ -75,6 +75,11 @@ struct regc_handle {
     uint32_t md_seg = 0;                      // MD segments run (Philox counter of the MD streams)
     StructureStore stc;                       // structural observables (empty until regc_structure_init)
     void* hE_block = nullptr;                 // per-state energy histograms [S][bins + 2] and window origins [S]
+    // a second grand-canonical species (P.gc2): a third grid axis of K
+    // chemical potentials; the pooled histogram then has (nmax+1)^2 rows
+    int K = 1;
+    int n_dir = 4;                            // exchange directions (5 with K > 1)
+    long long hist_rows = 0;                  // rows of the pooled (N, E) histogram
 };
 
 // Synchronise the handle's stream and fold its device error word into the

@@ -115,11 +115,22 @@ void regc_free(regc_handle* h) {
     delete h;
 }
 
-regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, const regc_grid_spec* grid,
-                           uint64_t seed, void* cuda_stream, regc_handle** out) {
+}  // extern "C"
+
+namespace {
+
+regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const regc_grid_spec* grid,
+                      const regc_species2* sp2, uint64_t seed, void* cuda_stream, regc_handle** out) {
     if (!out) return REGC_EINVAL;
     *out = nullptr;
     if (!pot || !surf || !grid) return REGC_EINVAL;
+    const int K = sp2 ? sp2->K : 1;
+    if (sp2) {
+        if (sp2->type < 1 || sp2->type >= pot->n_types || sp2->K < 1 || !sp2->mu || !(sp2->lambda0 > 0.0))
+            return REGC_EINVAL;
+        for (int k = 0; k < sp2->K; ++k)
+            if (!std::isfinite(sp2->mu[k])) return REGC_EINVAL;
+    }
     // ---- validation
     const int nt = pot->n_types;
     if (nt < 1 || nt > 4 || !(pot->rc > 0.0f)) return REGC_EINVAL;
@@ -146,7 +157,7 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         if (!(r[0] >= 0.0f && r[0] < surf->Lx && r[1] >= 0.0f && r[1] < surf->Ly) || !std::isfinite(r[2]))
             return REGC_EINVAL;
     }
-    if (grid->L < 1 || grid->M < 1 || (long long)grid->L * grid->M > 65536 || !grid->kT || !grid->mu)
+    if (grid->L < 1 || grid->M < 1 || (long long)grid->L * grid->M * K > 65536 || !grid->kT || !grid->mu)
         return REGC_EINVAL;
     double kT_max = 0.0;
     for (int l = 0; l < grid->L; ++l) {
@@ -160,7 +171,8 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     if (!(grid->max_disp >= 0.0f) || !(grid->p_disp >= 0.0 && grid->p_disp <= 1.0) || !(grid->lambda0 > 0.0))
         return REGC_EINVAL;
     if (!(grid->e_bin > 0.0) || grid->n_e_bins < 1 || !std::isfinite(grid->e_lo)) return REGC_EINVAL;
-    if ((long long)(grid->nmax + 1) * grid->n_e_bins > (1LL << 31)) return REGC_EINVAL;
+    const long long hist_rows = sp2 ? (long long)(grid->nmax + 1) * (grid->nmax + 1) : grid->nmax + 1;
+    if (hist_rows * grid->n_e_bins > (1LL << 31)) return REGC_EINVAL;
 
     // ---- geometry of the cell list
     const int periodic_z = surf->periodic_z ? 1 : 0;
@@ -209,7 +221,10 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->L = grid->L;
     h->M = grid->M;
-    h->S = grid->L * grid->M;
+    h->K = K;
+    h->n_dir = K > 1 ? 5 : 4;
+    h->hist_rows = hist_rows;
+    h->S = grid->L * grid->M * K;
     h->nmax = grid->nmax;
     h->mps = grid->moves_per_sweep;
     h->n_e_bins = grid->n_e_bins;
@@ -228,11 +243,12 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     // ---- per-state constants of the acceptance rules
     const double V = (double)surf->Lx * (double)surf->Ly * ((double)surf->z_hi - (double)surf->z_lo);
     const double lnV = log(V);
-    std::vector<double> beta(S), c_ins(S), c_del(S), bmu(S), lnbeta(S);
+    std::vector<double> beta(S), c_ins(S), c_del(S), bmu(S), lnbeta(S), c_ins2(S), c_del2(S), bmu2(S);
     h->kT_state.resize(S);
     h->mu_state.resize(S);
     for (int s = 0; s < S; ++s) {
-        const double kT = grid->kT[s / grid->M], mu = grid->mu[s % grid->M];
+        // state s = (l M + m) K + k: kT[l], mu[m], and mu2[k] of a second species
+        const double kT = grid->kT[s / (grid->M * K)], mu = grid->mu[(s / K) % grid->M];
         const double b = 1.0 / kT;
         const double lnL = log(grid->lambda0) - 0.5 * log(kT);
         beta[s] = b;
@@ -242,6 +258,13 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
         lnbeta[s] = log(b);
         h->kT_state[s] = kT;
         h->mu_state[s] = mu;
+        if (sp2) {
+            const double mu2 = sp2->mu[s % K];
+            const double lnL2 = log(sp2->lambda0) - 0.5 * log(kT);
+            c_ins2[s] = lnV - 3.0 * lnL2 + b * mu2;
+            c_del2[s] = 3.0 * lnL2 - lnV - b * mu2;
+            bmu2[s] = b * mu2;
+        }
     }
     std::vector<double> ln_tab(grid->nmax + 2, 0.0);
     for (int k = 1; k < grid->nmax + 2; ++k) ln_tab[k] = log((double)k);
@@ -341,6 +364,24 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     P.n_cluster = 0;
     P.gA = P.gAB = P.gg;
     for (int t = 0; t < 4; ++t) P.gsA[t] = P.gs[t];
+    P.gc2 = sp2 ? 1 : 0;
+    if (sp2) {
+        // species B = type 0 (particles [0, N_B)), C = sp2->type: the two-species
+        // tables hold B-B, B-C, C-C and the surface tables of each
+        const int c = sp2->type;
+        auto tab = [&](int a, int b) {
+            return PairTab{4.0f * pot->eps[a][b], pot->sigma[a][b] * pot->sigma[a][b],
+                           hard_core_r2(pot->eps[a][b], pot->sigma[a][b], T), pot->eps[a][b]};
+        };
+        P.gA = tab(0, 0);
+        P.gAB = tab(0, c);
+        P.gg = tab(c, c);
+        for (int t = 0; t < 4; ++t) {
+            const int tt = t < nt ? t : 0;
+            P.gsA[t] = tab(0, tt);
+            P.gs[t] = tab(c, tt);
+        }
+    }
     h->n_types = nt;
     memcpy(h->eps, pot->eps, sizeof(h->eps));
     memcpy(h->sigma, pot->sigma, sizeof(h->sigma));
@@ -426,11 +467,38 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     TRY(dalloc(h, &d_sow, S));
     TRY(dalloc(h, &d_wos, S));
     TRY(dalloc(h, &d_mc, (size_t)S * 6));
-    TRY(dalloc(h, &d_exc, (size_t)S * 8));
+    TRY(dalloc(h, &d_exc, (size_t)S * 2 * h->n_dir));
     TRY(dalloc(h, &P.hN, (size_t)S * (grid->nmax + 1)));
     TRY(dalloc(h, &P.omega, S));
     TRY(dalloc(h, &P.moments, (size_t)S * 4));
-    TRY(dalloc(h, &P.hNE, (size_t)(grid->nmax + 1) * grid->n_e_bins));
+    TRY(dalloc(h, &P.hNE, (size_t)hist_rows * grid->n_e_bins));
+    double *d_bmu2 = nullptr;
+    if (sp2) {
+        double *d_ci2, *d_cd2;
+        float *d_ci2f, *d_cd2f;
+        std::vector<float> ci2f(S), cd2f(S);
+        for (int q = 0; q < S; ++q) {
+            ci2f[q] = (float)c_ins2[q];
+            cd2f[q] = (float)c_del2[q];
+        }
+        TRY(dalloc(h, &d_ci2, S));
+        TRY(dalloc(h, &d_cd2, S));
+        TRY(dalloc(h, &d_ci2f, S));
+        TRY(dalloc(h, &d_cd2f, S));
+        TRY(dalloc(h, &d_bmu2, S));
+        TRY(upload(h, d_ci2, c_ins2.data(), S));
+        TRY(upload(h, d_cd2, c_del2.data(), S));
+        TRY(upload(h, d_ci2f, ci2f.data(), S));
+        TRY(upload(h, d_cd2f, cd2f.data(), S));
+        TRY(upload(h, d_bmu2, bmu2.data(), S));
+        TRY(dalloc(h, &P.nb, S));
+        TRY(dalloc(h, &P.hN2, (size_t)S * (grid->nmax + 1)));
+        TRY(dalloc(h, &P.moments2, (size_t)S * 2));
+        P.c_ins2 = d_ci2;
+        P.c_del2 = d_cd2;
+        P.c_ins2_f = d_ci2f;
+        P.c_del2_f = d_cd2f;
+    }
     TRY(dalloc(h, &P.e_out, S));
     TRY(dalloc(h, &P.pair_counts, 6));
     TRY(dalloc(h, &h->d_error, 1));
@@ -455,11 +523,30 @@ regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, 
     P.trace_steps = 0;
     P.cycle = 0;
     P.m_first = 0;
-    h->X = ExchangeParams{grid->L, grid->M, P.key0, P.key1, d_beta, d_bmu, d_lnbeta, d_n, d_efix, d_sow, d_wos, d_exc};
+    h->X = ExchangeParams{grid->L, grid->M, P.key0, P.key1, d_beta, d_bmu, d_lnbeta, d_n, d_efix, d_sow, d_wos, d_exc,
+                          K, sp2 ? P.nb : nullptr, d_bmu2};
     TRY(cuda_fail(h, cudaStreamSynchronize(h->stream)));
 #undef TRY
     *out = h;
     return REGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+regc_status regc_init_grid(const regc_potential* pot, const regc_surface* surf, const regc_grid_spec* grid,
+                           uint64_t seed, void* cuda_stream, regc_handle** out) {
+    return init_grid(pot, surf, grid, nullptr, seed, cuda_stream, out);
+}
+
+regc_status regc_init_grid2(const regc_potential* pot, const regc_surface* surf, const regc_grid_spec* grid,
+                            const regc_species2* species2, uint64_t seed, void* cuda_stream, regc_handle** out) {
+    if (!species2) {
+        if (out) *out = nullptr;
+        return REGC_EINVAL;
+    }
+    return init_grid(pot, surf, grid, species2, seed, cuda_stream, out);
 }
 
 regc_status regc_sweep(regc_handle* h, int n_sweeps) {
@@ -509,6 +596,7 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
 // replica exchange.
 static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, regc_move_record* trace,
                              int* n_exchanges) {
+    if (h && h->P.gc2) return REGC_EINVAL;   // the REGC cycle with one grand-canonical species only
     if (!h || n_steps < 0 || n_canonical < 0 || n_canonical > 1023 || !(x0 >= 0.0 && x0 <= 1.0))
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
@@ -592,7 +680,7 @@ regc_status regc_cycle_traced(regc_handle* h, int n_steps, double x0, int n_cano
 regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, float dt, float tau,
                           int* n_exchanges) {
     if (!h || n_steps < 0 || md_steps < 0 || !(x0 >= 0.0 && x0 <= 1.0) || !(dt > 0.0f) || !(tau > 0.0f) ||
-        !std::isfinite(dt) || !std::isfinite(tau))
+        !std::isfinite(dt) || !std::isfinite(tau) || h->P.gc2)
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
@@ -613,6 +701,7 @@ regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, 
 regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kinetic) {
     if (!h || n_steps < 0 || !(dt > 0.0f) || !(tau > 0.0f) || !std::isfinite(dt) || !std::isfinite(tau))
         return REGC_EINVAL;
+    if (h->P.gc2) return REGC_EINVAL;   // MD with one grand-canonical species only
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
     if (md_smem(h->nmax, h->P.cg.ncell, h->P.cg.cap) > kMaxSmem) return REGC_EINVAL;
@@ -649,10 +738,22 @@ regc_status regc_histograms(regc_handle* h, int64_t* hN, int64_t* hNE, int64_t* 
         if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
     };
     get(hN, h->P.hN, S * (h->nmax + 1) * 8);
-    get(hNE, h->P.hNE, (size_t)(h->nmax + 1) * h->n_e_bins * 8);
+    get(hNE, h->P.hNE, (size_t)h->hist_rows * h->n_e_bins * 8);
     get(omega, h->P.omega, S * 8);
     get(moments, h->P.moments, S * 4 * 8);
     get(e_out, h->P.e_out, S * 8);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_histograms2(regc_handle* h, int64_t* hN2, double* moments2) {
+    if (!h) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    if (!h->P.gc2) return REGC_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (hN2) e = cudaMemcpyAsync(hN2, h->P.hN2, (size_t)h->S * (h->nmax + 1) * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (moments2 && e == cudaSuccess)
+        e = cudaMemcpyAsync(moments2, h->P.moments2, (size_t)h->S * 2 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
     return sync_check(h);
 }
@@ -666,12 +767,16 @@ regc_status regc_reset_histograms(regc_handle* h) {
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, h->stream);
     };
     zero(h->P.hN, S * (h->nmax + 1) * 8);
-    zero(h->P.hNE, (size_t)(h->nmax + 1) * h->n_e_bins * 8);
+    zero(h->P.hNE, (size_t)h->hist_rows * h->n_e_bins * 8);
+    if (h->P.gc2) {
+        zero(h->P.hN2, S * (h->nmax + 1) * 8);
+        zero(h->P.moments2, S * 2 * 8);
+    }
     zero(h->P.omega, S * 8);
     zero(h->P.moments, S * 4 * 8);
     zero(h->P.e_out, S * 8);
     zero(h->P.move_counts, S * 6 * 8);
-    zero(h->X.ex_counts, S * 8 * 8);
+    zero(h->X.ex_counts, S * 2 * h->n_dir * 8);
     zero(h->P.pair_counts, 6 * 8);
     if (h->P.hE) zero(h->P.hE, S * (size_t)(h->P.hE_bins + 2) * 8);
     return cuda_fail(h, e);
@@ -751,11 +856,16 @@ regc_status regc_state_histograms(regc_handle* h, int64_t* hE, double* e_lo, dou
 }
 
 regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n, const int32_t* sow) {
+    return regc_set_walkers2(h, pos, n, nullptr, sow);
+}
+
+regc_status regc_set_walkers2(regc_handle* h, const float* pos, const int32_t* n, const int32_t* nb,
+                              const int32_t* sow) {
     if (!h || !pos || !n) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
     for (int w = 0; w < S; ++w)
-        if (n[w] < h->P.n_cluster || n[w] > nmax) return REGC_EINVAL;
+        if (n[w] < h->P.n_cluster || n[w] > nmax || (nb && (nb[w] < 0 || nb[w] > n[w]))) return REGC_EINVAL;
     // walker of each state, built in the pinned staging area (asynchronous copy)
     int* flag = static_cast<int*>(h->h_stage);
     int* wos = reinterpret_cast<int*>(static_cast<char*>(h->h_stage) + 64);
@@ -770,6 +880,9 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
     cudaError_t e = cudaMemcpyAsync(h->d_xyz, pos, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyHostToDevice,
                                     h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.n, n, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    // species B's counts (without them every particle is B)
+    if (e == cudaSuccess && h->P.gc2)
+        e = cudaMemcpyAsync(h->P.nb, nb ? nb : n, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && sow)
         e = cudaMemcpyAsync(h->X.state_of_walker, sow, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && sow)
@@ -794,7 +907,7 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
 }
 
 regc_status regc_set_cluster(regc_handle* h, int n_cluster, int cluster_type) {
-    if (!h || n_cluster < 0 || n_cluster >= h->nmax) return REGC_EINVAL;
+    if (!h || n_cluster < 0 || n_cluster >= h->nmax || h->P.gc2) return REGC_EINVAL;
     if (n_cluster > 0 && (cluster_type < 1 || cluster_type >= h->n_types)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     SweepParams& P = h->P;
@@ -816,8 +929,13 @@ regc_status regc_set_cluster(regc_handle* h, int n_cluster, int cluster_type) {
 }
 
 regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* energy, int32_t* sow) {
+    return regc_get_walkers2(h, pos, n, nullptr, energy, sow);
+}
+
+regc_status regc_get_walkers2(regc_handle* h, float* pos, int32_t* n, int32_t* nb, double* energy, int32_t* sow) {
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
+    if (nb && !h->P.gc2) return REGC_EINVAL;
     const int S = h->S, nmax = h->nmax;
     long long* ef = reinterpret_cast<long long*>(static_cast<char*>(h->h_stage) + 64);   // pinned
     cudaError_t e = cudaSuccess;
@@ -828,6 +946,7 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
                                 h->stream);
     }
     if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, h->P.n, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (nb && e == cudaSuccess) e = cudaMemcpyAsync(nb, h->P.nb, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (energy && e == cudaSuccess)
         e = cudaMemcpyAsync(ef, h->P.efix, S * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
     if (sow && e == cudaSuccess)
@@ -869,7 +988,8 @@ regc_status regc_counters(regc_handle* h, int64_t* moves, int64_t* exchanges, in
     cudaError_t e = cudaSuccess;
     if (moves) e = cudaMemcpyAsync(moves, h->P.move_counts, (size_t)h->S * 6 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (exchanges && e == cudaSuccess)
-        e = cudaMemcpyAsync(exchanges, h->X.ex_counts, (size_t)h->S * 8 * 8, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(exchanges, h->X.ex_counts, (size_t)h->S * 2 * h->n_dir * 8, cudaMemcpyDeviceToHost,
+                            h->stream);
     if (pairs && e == cudaSuccess)
         e = cudaMemcpyAsync(pairs, h->P.pair_counts, 6 * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e);
@@ -911,14 +1031,19 @@ std::vector<Section> ckpt_sections(regc_handle* h, bool with_sur) {
         {h->X.state_of_walker, S * sizeof(int)},
         {h->X.walker_of_state, S * sizeof(int)},
         {h->P.hN, S * nb * 8},
-        {h->P.hNE, nb * (size_t)h->n_e_bins * 8},
+        {h->P.hNE, (size_t)h->hist_rows * h->n_e_bins * 8},
         {h->P.omega, S * 8},
         {h->P.moments, S * 4 * 8},
         {h->P.e_out, S * 8},
         {h->P.move_counts, S * 6 * 8},
-        {h->X.ex_counts, S * 8 * 8},
+        {h->X.ex_counts, S * 2 * h->n_dir * 8},
         {h->P.pair_counts, 6 * 8},
     };
+    if (h->P.gc2) {
+        v.push_back({h->P.nb, S * sizeof(int)});
+        v.push_back({h->P.hN2, S * nb * 8});
+        v.push_back({h->P.moments2, S * 2 * 8});
+    }
     if (h->P.hE) {
         v.push_back({h->P.hE, S * (size_t)(h->P.hE_bins + 2) * 8});
         v.push_back({const_cast<long long*>(h->P.hE_lo_fix), S * 8});
@@ -967,7 +1092,7 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
     CkptHeader hd{};
     memcpy(hd.magic, "REGCCKPT", 8);
     hd.version = 3;
-    hd.flags = (h->has_sur ? 1u : 0u) | (h->P.delayed ? 2u : 0u);
+    hd.flags = (h->has_sur ? 1u : 0u) | (h->P.delayed ? 2u : 0u) | (h->P.gc2 ? 4u : 0u);
     hd.S = h->S;
     hd.nmax = h->nmax;
     hd.n_e_bins = h->n_e_bins;
@@ -995,6 +1120,7 @@ regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
     const unsigned char* in = static_cast<const unsigned char*>(buf);
     if (memcmp(hd.magic, "REGCCKPT", 8) != 0 || hd.version != 3) return REGC_EINVAL;
     if (hd.S != h->S || hd.nmax != h->nmax || hd.n_e_bins != h->n_e_bins || hd.n_cluster != h->P.n_cluster ||
+        ((hd.flags & 4u) != 0) != (h->P.gc2 != 0) ||
         hd.key0 != h->P.key0 || hd.key1 != h->P.key1 || hd.hE_bins != h->P.hE_bins)
         return REGC_EINVAL;
     const bool with_sur = (hd.flags & 1u) != 0;
@@ -1097,6 +1223,7 @@ regc_status regc_surrogate_get(regc_handle* h, float* theta) {
 
 regc_status regc_set_mode(regc_handle* h, int mode) {
     if (!h || (mode != 0 && mode != 1)) return REGC_EINVAL;
+    if (mode == 1 && h->P.gc2) return REGC_EINVAL;   // delayed acceptance with one species only
     if (mode == 1 && !h->has_sur) return REGC_EINVAL;
     h->P.delayed = mode;
     return REGC_OK;
@@ -1104,7 +1231,7 @@ regc_status regc_set_mode(regc_handle* h, int mode) {
 
 regc_status regc_surrogate_eval(regc_handle* h, int walker, int n_query, const float* xyz, float* e_out,
                                 float* features) {
-    if (!h || walker < 0 || walker >= h->S || n_query < 0 || (n_query > 0 && (!xyz || !e_out)))
+    if (!h || walker < 0 || walker >= h->S || n_query < 0 || (n_query > 0 && (!xyz || !e_out)) || h->P.gc2)
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (!h->has_sur) return REGC_EINVAL;
@@ -1137,7 +1264,7 @@ regc_status regc_surrogate_eval(regc_handle* h, int walker, int n_query, const f
 
 regc_status regc_surrogate_harvest(regc_handle* h, int particles, int probes, float e_clip, int capacity,
                                    int64_t* n_rows) {
-    if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip)) return REGC_EINVAL;
+    if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip) || h->P.gc2) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->ds_cap == 0) {
         if (capacity < 1) return REGC_EINVAL;
@@ -1376,6 +1503,7 @@ regc_status regc_pressure_of_mu(int n, const double* kT, const double* mu, doubl
 regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const double* mu_q, double tol, int max_iter,
                           double* N_mean, double* pN, double* f_states, int* iters) {
     if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;
+    if (h->P.gc2) return REGC_EINVAL;   // two species: regc_reweight2
     for (int q = 0; q < nq; ++q)
         if (!(kT_q[q] > 0.0) || !std::isfinite(mu_q[q])) return REGC_EINVAL;
     regc_status st = sync_check(h);

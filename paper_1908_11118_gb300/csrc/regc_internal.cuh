@@ -124,6 +124,20 @@ struct SweepParams {
     int n_cluster;         // particles 0..n_cluster-1 are the cluster species (0: none)
     PairTab gA, gAB;       // cluster-cluster, cluster-grand-canonical
     PairTab gsA[4];        // cluster-surface by surface type
+    // A second grand-canonical species (gc2 = 1): walker w's particles
+    // [0, nb[w]) are species B and [nb[w], N) species C; the two-species
+    // tables above then hold B-B (gA), B-C (gAB), C-C (gg), B-surface (gsA)
+    // and C-surface (gs), so the cluster's code paths serve with the split
+    // taken per walker.  A grand-canonical move picks its species by bit 30
+    // of Philox word B2 (0: B, 1: C).
+    int gc2;
+    int* nb;               // [S] species-B count of each walker
+    const double* c_ins2;  // [S] ln V - 3 ln Lambda_C,s + beta_s mu2_s
+    const double* c_del2;  // [S] 3 ln Lambda_C,s - ln V - beta_s mu2_s
+    const float* c_ins2_f;
+    const float* c_del2_f;
+    unsigned long long* hN2;      // [S][nmax+1] observations of N_C
+    double* moments2;             // [S][2] sum N_C, sum N_C^2
     float max_disp;
     unsigned long long th_disp;   // displacement if A0 < th_disp (0 .. 2^32)
     int S, nmax, mps;
@@ -181,7 +195,10 @@ struct ExchangeParams {
     const long long* efix;
     int* state_of_walker;
     int* walker_of_state;
-    long long* ex_counts;  // [S][8]
+    long long* ex_counts;  // [S][2 x directions]
+    int K;                 // a third grid axis (mu2 of a second species; 1: none)
+    const int* nb;         // [S] walkers' species-B counts, or null (one species)
+    const double* bmu2;    // [S] beta_s mu2_s (with nb)
 };
 
 // ----------------------------------------------------------- pair energy

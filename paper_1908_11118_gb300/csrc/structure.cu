@@ -317,6 +317,7 @@ regc_status fail(regc_handle* h, cudaError_t e) { return handle_cuda_fail(h, e);
 extern "C" {
 
 regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec) {
+    if (h && h->P.gc2) return REGC_EINVAL;   // structure samples with one grand-canonical species only
     if (!h || !spec) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const regc_structure_spec& s = *spec;

@@ -63,7 +63,8 @@ struct MoveRes {
     int dec;       // decision with N = n_eval: 0 reject, 1 accept, 2 near tie (FP64 needed)
     int stage1;    // delayed acceptance: 1 if the surrogate stage accepted
     float dE_sur;  // delayed acceptance: surrogate energy change
-    int pad;
+    int gy;        // two mobile species: 0 if the moved (inserted, removed) particle is
+                   // of the first (index < split), 1 of the second
 };
 
 // Pair tables of the moving particle's species against a cluster partner (tA)
@@ -93,6 +94,7 @@ struct MoveTabs {
 // Constants of the walker's state for the binary32 pre-test of the acceptance.
 struct StateF {
     float beta, c_ins, c_del;
+    float c_ins2, c_del2;   // a second grand-canonical species
 };
 
 // Binary32 pre-test of ln u < ln alpha with N particles before the move:
@@ -119,6 +121,7 @@ struct WalkerStats {
     unsigned long long rounds, evals;
     unsigned long long screened, passed;   // delayed acceptance: stage-1 screens and passes
     int tr[3], ac[3];
+    long long mC, mC2;                      // second grand-canonical species: sum N_C, N_C^2
 };
 
 // Round state broadcast by the committer.
@@ -126,6 +129,8 @@ struct RoundHdr {
     int N;
     int committed;
     long long E;
+    int split;   // two mobile species: the current boundary
+    int pad;
 };
 
 struct WalkerSmem {
@@ -280,7 +285,7 @@ template <int NQ, bool CL>
 __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
                                             float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
                                             int sgn0, Fix3& acc, int& n_in, int& n_cand, int& overlap, int lane,
-                                            int warp, const MoveTabs& mt) {
+                                            int warp, int split, const MoveTabs& mt) {
     StEntry* st = S.stencil + warp * 32;
     StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
     const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
@@ -315,7 +320,7 @@ __device__ __forceinline__ void mobile_pass(const SweepParams& P, const WalkerSm
         const float4 p = S.pos[use ? pj : 0];
         const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
         n_cand += use ? NQ : 0;
-        const PairTab& tp = CL ? (pj < P.n_cluster ? mt.tA : mt.tB) : P.gg;
+        const PairTab& tp = CL ? (pj < split ? mt.tA : mt.tB) : P.gg;
         const float dy0 = __fsub_rn(e.ay0, by);
         const float phi0 = pair_phi_sel(cart_dx(P.g, __fsub_rn(e.ax0, bx), dy0), dy0, __fsub_rn(e.az0, bz),
                                         P.g.rc2, tp, use, n_in, ov);
@@ -371,7 +376,7 @@ template <int NQ, bool CL>
 __device__ __forceinline__ void feature_mobile(const SweepParams& P, const WalkerSmem& S, Cell3 c, float q0x,
                                                float q0y, float q0z, float q1x, float q1y, float q1z, int skip,
                                                float (&F0)[kNF], float (&F1)[kNF], int lane, int warp,
-                                               const MoveTabs& mt) {
+                                               int split, const MoveTabs& mt) {
     StEntry* st = S.stencil + warp * 32;
     StEntry se = stencil_entry(P, c, lane, q0x, q0y, q0z, q1x, q1y, q1z);
     const int cnt = se.cell >= 0 ? (int)S.cnt[se.cell] : 0;
@@ -403,7 +408,7 @@ __device__ __forceinline__ void feature_mobile(const SweepParams& P, const Walke
                 const float bx = __fsub_rn(p.x, e.obx), by = __fsub_rn(p.y, e.oby), bz = __fsub_rn(p.z, e.obz);
                 const float dy0 = __fsub_rn(e.ay0, by);
                 const float r20 = r2_of(cart_dx(P.g, __fsub_rn(e.ax0, bx), dy0), dy0, __fsub_rn(e.az0, bz));
-                const float wp = CL ? (pj < P.n_cluster ? mt.tA.eps : mt.tB.eps) : P.gg.eps;
+                const float wp = CL ? (pj < split ? mt.tA.eps : mt.tB.eps) : P.gg.eps;
                 if (r20 < P.g.rc2) add_features(F0, r20, wp, P.g.rc);
                 if (NQ == 2) {
                     const float dy1 = __fsub_rn(e.ay1, by);
@@ -468,12 +473,20 @@ __device__ __forceinline__ void build_cells(const SweepParams& P, const WalkerSm
 // result in *out.
 template <bool DA, bool CL>
 __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const StateF& sf, int s, int m, int N,
-                              int slot, int& n_in, int& n_cand, int lane, int warp, const NetFrag* nf,
+                              int slot, int split_in, int& n_in, int& n_cand, int lane, int warp, const NetFrag* nf,
                               MoveRes* out) {
-    // with a cluster, particles 0..nA-1 are cluster atoms; insertion and
-    // removal act on the grand-canonical species, whose count is N - nA
-    const int nA = CL ? P.n_cluster : 0;
+    // Two mobile species (CL): particles [0, split) are of the first, the
+    // rest of the second -- a cluster (split = n_cluster, moved only by
+    // displacement; insertion and removal act on the gas after it) or two
+    // grand-canonical species B and C (split = N_B, gc2).
+    const int split = CL ? split_in : 0;
     const uint4 A = S.rng[2 * (m % kRing)], B = S.rng[2 * (m % kRing) + 1];
+    // the species of a grand-canonical move: the second (the gas after a
+    // cluster), or with two grand-canonical species the one bit 30 of B2 picks
+    const int gy = (CL && P.gc2) ? (int)((B.z >> 30) & 1u) : 1;
+    const int gcnt = gy ? N - split : split;          // its count before the move
+    const bool use2 = CL && P.gc2 && gy == 1;         // species C's constants
+    const float cins_f = use2 ? sf.c_ins2 : sf.c_ins, cdel_f = use2 ? sf.c_del2 : sf.c_del;
     // the kind of move: drawn from A0 in a sweep (slot -1), fixed by its place
     // in a REGC cycle step (slot 1: the particle exchange, 0: a displacement)
     const int gc_type = (B.z >> 31) == 0u ? 2 : 1;
@@ -519,10 +532,10 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
             q0x = q1x = nx; q0y = q1y = ny; q0z = q1z = nz;
         }
     } else {
-        if (N == nA) {
+        if (gcnt == 0) {
             status = 1;
         } else {
-            idx = nA + (int)(((unsigned long long)B.x * (unsigned)(N - nA)) >> 32);
+            idx = (gy ? split : 0) + (int)(((unsigned long long)B.x * (unsigned)gcnt) >> 32);
             const float4 old = S.pos[idx];
             q0x = q1x = old.x; q0y = q1y = old.y; q0z = q1z = old.z;
             sgn0 = -1;
@@ -530,7 +543,7 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
     }
     // pair tables of the moving species
     MoveTabs mt;
-    mt.mA = CL && type == 0 && idx >= 0 && idx < nA;
+    mt.mA = CL && ((type != 1 && idx >= 0 && idx < split) || (type == 1 && gy == 0));
     if (CL) {
         mt.tA = mt.mA ? P.gA : P.gAB;
         mt.tB = mt.mA ? P.gAB : P.gg;
@@ -547,11 +560,11 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         const Cell3 c0 = cell3_of(P, q0x, q0y, q0z);
         const Cell3 c1 = nq == 2 ? cell3_of(P, q1x, q1y, q1z) : c0;
         if (nq == 2 && c0.x == c1.x && c0.y == c1.y && c0.z == c1.z) {
-            feature_mobile<2, CL>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, F0, F1, lane, warp, mt);
+            feature_mobile<2, CL>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, F0, F1, lane, warp, split, mt);
         } else {
-            feature_mobile<1, CL>(P, S, c0, q0x, q0y, q0z, q0x, q0y, q0z, skip, F0, F1, lane, warp, mt);
+            feature_mobile<1, CL>(P, S, c0, q0x, q0y, q0z, q0x, q0y, q0z, skip, F0, F1, lane, warp, split, mt);
             if (nq == 2)
-                feature_mobile<1, CL>(P, S, c1, q1x, q1y, q1z, q1x, q1y, q1z, skip, F1, F0, lane, warp, mt);
+                feature_mobile<1, CL>(P, S, c1, q1x, q1y, q1z, q1x, q1y, q1z, skip, F1, F0, lane, warp, split, mt);
         }
         const bool s0 = near_surface(P, q0z), s1 = nq == 2 && near_surface(P, q1z);
         const int col0 = surface_col(P, q0x, q0y), col1 = nq == 2 ? surface_col(P, q1x, q1y) : col0;
@@ -571,16 +584,16 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         dEs = type == 1 ? e0 : (type == 2 ? -e0 : e0 - e1);
         // ln u1 < ln alpha with dE~ in place of dE (u1 from B3)
         float c_f = 0.f;
-        if (type == 1) c_f = sf.c_ins - __logf((float)(N - nA + 1));
-        else if (type == 2) c_f = sf.c_del + __logf((float)(N - nA));
+        if (type == 1) c_f = cins_f - __logf((float)(gcnt + 1));
+        else if (type == 2) c_f = cdel_f + __logf((float)gcnt);
         const float la1 = c_f - sf.beta * dEs;
         const float lu1 = __logf(((float)B.w + 0.5f) * 2.3283064365386963e-10f);
         if (la1 >= 0.f || lu1 < la1 - 1e-3f) stage1 = 1;
         else if (lu1 > la1 + 1e-3f) stage1 = 0;
         else {
             double c = 0.0;
-            if (type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
-            else if (type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
+            if (type == 1) c = (use2 ? P.c_ins2[s] : P.c_ins[s]) - P.ln_tab[gcnt + 1];
+            else if (type == 2) c = (use2 ? P.c_del2[s] : P.c_del[s]) + P.ln_tab[gcnt];
             stage1 = (log((double)B.w + 0.5) + kLn2m32) < c - P.beta[s] * (double)dEs;
         }
     }
@@ -593,7 +606,7 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         const bool same = c0.x == c1.x && c0.y == c1.y && c0.z == c1.z;
         if (nq == 2 && same) {
             mobile_pass<2, CL>(P, S, c0, q0x, q0y, q0z, q1x, q1y, q1z, skip, 1, acc, n_in, n_cand, overlap, lane, warp,
-                               mt);
+                               split, mt);
         } else {
             // one pass per query: query 0 with its sign, then (a displacement
             // across cells) the old position with -1
@@ -601,7 +614,7 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
                 const float px = pass ? q1x : q0x, py = pass ? q1y : q0y, pz = pass ? q1z : q0z;
                 int ovp = 0;
                 mobile_pass<1, CL>(P, S, pass ? c1 : c0, px, py, pz, px, py, pz, skip, pass ? -1 : sgn0, acc, n_in,
-                                   n_cand, ovp, lane, warp, mt);
+                                   n_cand, ovp, lane, warp, split, mt);
                 if (pass == 0) overlap |= ovp;
             }
         }
@@ -642,8 +655,11 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
         r.q1x = q1x; r.q1y = q1y; r.q1z = q1z;
         r.stage1 = stage1;
         r.dE_sur = dEs;
+        r.gy = gy;
         if (!DA) {
-            r.dec = (status == 0 && !ovl) ? pretest(sf, type, N - nA, big, hi, lo, B.y) : 0;
+            r.dec = (status == 0 && !ovl) ? pretest(StateF{sf.beta, cins_f, cdel_f, 0.f, 0.f}, type, gcnt, big, hi,
+                                                    lo, B.y)
+                                          : 0;
         } else if (status != 0 || ovl || !stage1) {
             r.dec = 0;
         } else {
@@ -685,13 +701,17 @@ __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay,
 template <int K, bool TRACE, bool DA, bool CL>
 __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* smem, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
-    const int nA = CL ? P.n_cluster : 0;   // cluster atoms: counted out of the grand-canonical N
     const WalkerSmem S = carve<K>(smem, P);
 
     int N = P.n[w];
     long long E = P.efix[w];
     const int s = P.state_of_walker[w];
-    const StateF sf{P.beta_f[s], P.c_ins_f[s], P.c_del_f[s]};
+    const bool two = CL && P.gc2;
+    // two mobile species: particles [0, split) are the cluster, or species B
+    // of two grand-canonical species (then split = N_B changes with the moves)
+    int split = CL ? (two ? P.nb[w] : P.n_cluster) : 0;
+    const StateF sf{P.beta_f[s], P.c_ins_f[s], P.c_del_f[s], two ? P.c_ins2_f[s] : 0.f,
+                    two ? P.c_del2_f[s] : 0.f};
     float4* gpos = P.pos + size_t(w) * P.nmax;
 
     // 1. stage positions with a bulk copy
@@ -717,7 +737,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
     // 2. cell list
     if (warp == 0) build_cells(P, S, N, lane);
     if (tid == 0)
-        *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}};
+        *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}, 0, 0};
     group_sync<K>();
 
     int n_in = 0, n_cand = 0;
@@ -748,7 +768,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         if (mj < total_moves) {
             int slot = -1;
             if (P.cycle) slot = (mj % P.mps) == 0;
-            evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, n_in, n_cand, lane, warp, &nf, S.res + warp);
+            evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, split, n_in, n_cand, lane, warp, &nf, S.res + warp);
         }
         group_sync<K>();
 
@@ -800,6 +820,11 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 int accepted = 0;
                 double la = 0.0;
                 const bool ovl = (r.flags & 1) != 0;
+                // the grand-canonical species of the move: its count and constants
+                const int gcnt = (CL && r.gy == 0) ? split : N - split;
+                const bool use2 = two && r.gy == 1;
+                const double* cins = use2 ? P.c_ins2 : P.c_ins;
+                const double* cdel = use2 ? P.c_del2 : P.c_del;
                 if (DA && status == 0) {
                     // both stages were decided by the evaluating warp (one warp per walker)
                     accepted = !ovl && r.dec == 1;
@@ -807,22 +832,25 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     S.stats->passed += r.stage1;
                     if (TRACE) {
                         double c = 0.0;
-                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
-                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
+                        if (r.type == 1) c = cins[s] - P.ln_tab[gcnt + 1];
+                        else if (r.type == 2) c = cdel[s] + P.ln_tab[gcnt];
                         la = r.stage1 ? c - P.beta[s] * ((double)dfix * kFixUnit) : (double)NAN;
                     }
                 } else if (status == 0 && !ovl) {
-                    const int dec = N == r.n_eval ? r.dec : pretest(sf, r.type, N - nA, r.big, r.hi, r.lo, B.y);
+                    const int dec = N == r.n_eval ? r.dec
+                                                  : pretest(StateF{sf.beta, use2 ? sf.c_ins2 : sf.c_ins,
+                                                                   use2 ? sf.c_del2 : sf.c_del, 0.f, 0.f},
+                                                            r.type, gcnt, r.big, r.hi, r.lo, B.y);
                     accepted = dec == 1;
                     if (dec == 2 || TRACE) {
                         double c = 0.0;
-                        if (r.type == 1) c = P.c_ins[s] - P.ln_tab[N - nA + 1];
-                        else if (r.type == 2) c = P.c_del[s] + P.ln_tab[N - nA];
+                        if (r.type == 1) c = cins[s] - P.ln_tab[gcnt + 1];
+                        else if (r.type == 2) c = cdel[s] + P.ln_tab[gcnt];
                         la = c - P.beta[s] * ((double)dfix * kFixUnit);
                         if (dec == 2) accepted = (log((double)B.y + 0.5) + kLn2m32) < la;
                     }
                 }
-                const int n_before = N;
+                const int n_before = N, split_before = split;
                 if (accepted) {
                     const int cap = P.cg.cap;
                     if (r.type == 0) {
@@ -839,20 +867,41 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                         chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
                         chx[nch] = r.q1x; chy[nch] = r.q1y; chz[nch] = r.q1z; ++nch;
                     } else if (r.type == 1) {
+                        // a new particle goes to the end, or (species B of two
+                        // grand-canonical species) to index split, whose C moves to the end
+                        int at = N;
+                        if (two && r.gy == 0) {
+                            at = split;
+                            if (split < N) {
+                                const float4 pc = S.pos[split];
+                                S.pos[N] = pc;
+                                S.slots[cell_bits(pc.w) * cap + slot_bits(pc.w)] = (uint16_t)N;
+                            }
+                            split += 1;
+                        }
                         const int sl = S.cnt[c_new];
-                        S.slots[c_new * cap + sl] = (uint16_t)N;
+                        S.slots[c_new * cap + sl] = (uint16_t)at;
                         S.cnt[c_new] = (uint16_t)(sl + 1);
-                        S.pos[N] = packed(r.q0x, r.q0y, r.q0z, c_new, sl);
+                        S.pos[at] = packed(r.q0x, r.q0y, r.q0z, c_new, sl);
                         chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
                         n_changed = true;
                     } else {
                         cell_remove(P, S, old.w);
                         const int last = N - 1;
-                        if (r.idx != last) {
-                            const float4 pl = S.pos[last];
+                        // the gap is filled from the end of the particle's block; a
+                        // removed B's block end is then filled by the last C
+                        const int fill = (two && r.gy == 0) ? split - 1 : last;
+                        if (r.idx != fill) {
+                            const float4 pl = S.pos[fill];
                             S.pos[r.idx] = pl;
                             S.slots[cell_bits(pl.w) * cap + slot_bits(pl.w)] = (uint16_t)r.idx;
                         }
+                        if (fill != last) {
+                            const float4 pc = S.pos[last];
+                            S.pos[fill] = pc;
+                            S.slots[cell_bits(pc.w) * cap + slot_bits(pc.w)] = (uint16_t)fill;
+                        }
+                        if (two && r.gy == 0) split -= 1;
                         chx[nch] = r.q0x; chy[nch] = r.q0y; chz[nch] = r.q0z; ++nch;
                         n_changed = true;
                     }
@@ -870,7 +919,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 if (TRACE) {
                     regc_move_record t;
                     t.type = r.type;
-                    t.index = status == 1 ? 0 : (r.type == 1 ? n_before : r.idx);
+                    t.index = status == 1 ? 0 : (r.type == 1 ? ((two && r.gy == 0) ? split_before : n_before) : r.idx);
                     t.accepted = accepted;
                     t.status = status == 3 ? 0 : status;
                     t.dE = (status == 0 || status == 3) ? (double)dfix * kFixUnit : 0.0;
@@ -887,8 +936,15 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 }
                 // 6. observe once per sweep into the current state's histograms
                 if (k == P.mps - 1) {
-                    const int NB = N - nA;
+                    // N_B: the grand-canonical count (with two species, species B's)
+                    const int NB = two ? split : N - split;
+                    const int NC = two ? N - split : 0;
                     atomicAdd(&P.hN[size_t(s) * (P.nmax + 1) + NB], 1ull);   // fire-and-forget reduction
+                    if (two) {
+                        atomicAdd(&P.hN2[size_t(s) * (P.nmax + 1) + NC], 1ull);
+                        st.mC += NC;
+                        st.mC2 += (long long)NC * NC;
+                    }
                     st.om += 1;
                     st.mN += NB;
                     st.mN2 += (long long)NB * NB;
@@ -897,7 +953,8 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     st.mE2 = fma(e, e, st.mE2);
                     const long long d = E - P.e_lo_fix;
                     const long long kb = d >= 0 ? d / P.e_bin_fix : -1;
-                    if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[size_t(NB) * P.n_e_bins + (size_t)kb], 1ull);
+                    const size_t row = two ? size_t(NB) * (P.nmax + 1) + NC : size_t(NB);
+                    if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[row * P.n_e_bins + (size_t)kb], 1ull);
                     else st.eo += 1;
                     if (P.hE) observe_state_energy(P, s, E);
                 }
@@ -905,6 +962,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             }
             S.hdr->N = N;
             S.hdr->E = E;
+            S.hdr->split = split;
             S.hdr->committed = committed;
             S.stats->rounds += 1;
             S.stats->evals += min(K, total_moves - m0);
@@ -912,6 +970,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         group_sync<K>();
         N = S.hdr->N;
         E = S.hdr->E;
+        split = S.hdr->split;
         m0 += S.hdr->committed;
         group_sync<K>();   // the header and results are rewritten by the next round
     }
@@ -929,6 +988,11 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         atomicAdd(&P.pair_counts[4], st.screened);
         atomicAdd(&P.pair_counts[5], st.passed);
         P.n[w] = N;
+        if (two) {
+            P.nb[w] = split;
+            P.moments2[size_t(s) * 2] += (double)st.mC;
+            P.moments2[size_t(s) * 2 + 1] += (double)st.mC2;
+        }
         P.efix[w] = E;
         P.omega[s] += st.om;
         P.e_out[s] += st.eo;
@@ -1008,8 +1072,9 @@ struct EnergyAcc {
 };
 
 template <bool CL>
-__device__ __forceinline__ void energy_pair(const SweepParams& P, const float4* sp, int i, int j, EnergyAcc& a) {
-    const bool iA = CL && i < P.n_cluster, jA = CL && j < P.n_cluster;
+__device__ __forceinline__ void energy_pair(const SweepParams& P, const float4* sp, int i, int j, int split,
+                                            EnergyAcc& a) {
+    const bool iA = CL && i < split, jA = CL && j < split;
     const PairTab& tp = iA ? (jA ? P.gA : P.gAB) : (jA ? P.gAB : P.gg);
     float dx, dy, dz;
     disp_exact(P.g, sp[i], sp[j], dx, dy, dz);
@@ -1026,6 +1091,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = blockIdx.x / kEnergySplit, c = blockIdx.x % kEnergySplit;
     const int N = P.n[w];
+    const int split = CL ? (P.gc2 ? P.nb[w] : P.n_cluster) : 0;   // two mobile species: the boundary
     const int t = c * kEnergyThreads + threadIdx.x;
     const float4* pos = P.pos + size_t(w) * P.nmax;
     if (use_cells)
@@ -1078,7 +1144,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
                 for (int m = 0; m < n_c; ++m) {
                     const int j = sl[m];
                     if (o == 0 && j <= i) continue;
-                    energy_pair<CL>(P, sp, i, j, a);
+                    energy_pair<CL>(P, sp, i, j, split, a);
                 }
             }
             o += rT;
@@ -1098,7 +1164,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
             if (!(even && d == D && i >= D)) {
                 int j = i + d;
                 if (j >= N) j -= N;
-                energy_pair<CL>(P, sp, i, j, a);
+                energy_pair<CL>(P, sp, i, j, split, a);
             }
             i += rT;
             d += qT;
@@ -1115,7 +1181,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
         if (near_surface(P, pi.z)) {
             int n_cand = 0;
             surface_pass<1, CL>(P, surface_col(P, pi.x, pi.y), pi.x, pi.y, pi.z, pi.x, pi.y, pi.z, 1, a.acc,
-                                a.n_in, n_cand, a.overlap, lane, CL && i < P.n_cluster);
+                                a.n_in, n_cand, a.overlap, lane, CL && i < split);
             a.fold();
         }
     }
@@ -1212,7 +1278,7 @@ size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker)
 cudaError_t launch_sweep(const SweepParams& P, cudaStream_t s) {
     if (P.n_sweeps <= 0) return cudaSuccess;
     // delayed acceptance and the cluster species: one warp per walker
-    if (P.n_cluster > 0) return P.delayed ? launch_k<1, true, true>(P, s) : launch_k<1, false, true>(P, s);
+    if (P.n_cluster > 0 || P.gc2) return P.delayed ? launch_k<1, true, true>(P, s) : launch_k<1, false, true>(P, s);
     if (P.delayed) return launch_k<1, true, false>(P, s);
     switch (P.warps_per_walker) {
         case 1: return launch_k<1, false, false>(P, s);
@@ -1231,7 +1297,7 @@ cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overla
                           P.cg.ncx < 1024 && P.cg.ncy < 1024 && P.cg.ncz < 1024 && with_cells + 1024 <= kMaxSmem;
     const size_t smem = use_cells ? with_cells : base;
     // the pair tables of a second species only where the walkers hold a cluster
-    auto kernel = P.n_cluster > 0 ? energy_kernel<true> : energy_kernel<false>;
+    auto kernel = (P.n_cluster > 0 || P.gc2) ? energy_kernel<true> : energy_kernel<false>;
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, size_t(P.S) * sizeof(long long), s);

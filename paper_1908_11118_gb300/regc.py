@@ -68,10 +68,20 @@ class Regc:
                              float(problem.p_disp), float(problem.e_lo), float(problem.e_bin),
                              int(problem.n_e_bins))
         h = C.c_void_p()
-        check(L.regc_init_grid(C.byref(pot), C.byref(surf), C.byref(grid), C.c_uint64(int(problem.seed)),
-                               _stream_handle(stream), C.byref(h)), "regc_init_grid")
+        self.two = int(getattr(problem, "gc2_type", 0)) > 0
+        if self.two:
+            self._mu2 = np.ascontiguousarray(problem.mu2, np.float64)
+            sp2 = _lib.Species2(int(problem.gc2_type), len(self._mu2), _p(self._mu2, C.c_double),
+                                float(problem.lambda0_2))
+            check(L.regc_init_grid2(C.byref(pot), C.byref(surf), C.byref(grid), C.byref(sp2),
+                                    C.c_uint64(int(problem.seed)), _stream_handle(stream), C.byref(h)),
+                  "regc_init_grid2")
+        else:
+            check(L.regc_init_grid(C.byref(pot), C.byref(surf), C.byref(grid), C.c_uint64(int(problem.seed)),
+                                   _stream_handle(stream), C.byref(h)), "regc_init_grid")
         self._h = h
-        self.S = len(self._kT) * len(self._mu)
+        self.K = len(self._mu2) if self.two else 1
+        self.S = len(self._kT) * len(self._mu) * self.K
         self.n_cluster = int(getattr(problem, "n_cluster", 0))
         if self.n_cluster > 0:
             check(L.regc_set_cluster(h, self.n_cluster, int(problem.cluster_type)), "regc_set_cluster")
@@ -152,12 +162,21 @@ class Regc:
                 self.exchange()
 
     # -- state
-    def set_walkers(self, pos, n, state_of_walker=None):
+    def set_walkers(self, pos, n, state_of_walker=None, nb=None):
+        """nb: with a second species, species B's count per walker (particles
+        [0, nb[w]) are B); None makes every particle B."""
         pos = np.ascontiguousarray(np.asarray(pos, np.float32).reshape(self.S, self.nmax, 3))
         n = np.ascontiguousarray(np.asarray(n, np.int32))
         sow = None if state_of_walker is None else np.ascontiguousarray(np.asarray(state_of_walker, np.int32))
-        check(_lib.lib().regc_set_walkers(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(sow, C.c_int32)),
-              "regc_set_walkers")
+        nb = None if nb is None else np.ascontiguousarray(np.asarray(nb, np.int32))
+        check(_lib.lib().regc_set_walkers2(self._h, _p(pos, C.c_float), _p(n, C.c_int32), _p(nb, C.c_int32),
+                                           _p(sow, C.c_int32)), "regc_set_walkers2")
+
+    def species_counts(self) -> np.ndarray:
+        """Species B's count N_B per walker (second species only)."""
+        nb = np.zeros(self.S, np.int32)
+        check(_lib.lib().regc_get_walkers2(self._h, None, None, _p(nb, C.c_int32), None, None), "regc_get_walkers2")
+        return nb
 
     def get_walkers(self, out=None):
         """(pos [S][nmax][3] float32, n [S] int32, energy [S] float64,
@@ -276,7 +295,7 @@ class Regc:
 
     def counters(self):
         mv = np.zeros((self.S, 3, 2), np.int64)
-        ex = np.zeros((self.S, 4, 2), np.int64)
+        ex = np.zeros((self.S, 5 if self.K > 1 else 4, 2), np.int64)
         pr = np.zeros(6, np.int64)
         check(_lib.lib().regc_counters(self._h, _p(mv, C.c_int64), _p(ex, C.c_int64), _p(pr, C.c_int64)),
               "regc_counters")
@@ -336,13 +355,20 @@ class Regc:
 
     def histograms(self):
         hN = np.zeros((self.S, self.nmax + 1), np.int64)
-        hNE = np.zeros((self.nmax + 1, self.n_e_bins), np.int64)
+        rows = (self.nmax + 1) ** 2 if self.two else self.nmax + 1
+        hNE = np.zeros((rows, self.n_e_bins), np.int64)
         om = np.zeros(self.S, np.int64)
         mo = np.zeros((self.S, 4))
         eo = np.zeros(self.S, np.int64)
         check(_lib.lib().regc_histograms(self._h, _p(hN, C.c_int64), _p(hNE, C.c_int64), _p(om, C.c_int64),
                                          _p(mo, C.c_double), _p(eo, C.c_int64)), "regc_histograms")
-        return {"hN": hN, "hNE": hNE, "omega": om, "moments": mo, "e_out": eo}
+        out = {"hN": hN, "hNE": hNE, "omega": om, "moments": mo, "e_out": eo}
+        if self.two:
+            hN2 = np.zeros((self.S, self.nmax + 1), np.int64)
+            mo2 = np.zeros((self.S, 2))
+            check(_lib.lib().regc_histograms2(self._h, _p(hN2, C.c_int64), _p(mo2, C.c_double)), "regc_histograms2")
+            out["hN2"], out["moments2"] = hN2, mo2
+        return out
 
     def reset_histograms(self):
         check(_lib.lib().regc_reset_histograms(self._h), "regc_reset_histograms")
