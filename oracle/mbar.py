@@ -48,6 +48,18 @@ def reduced_potential(kT, mu, lambda0, N, E):
     return (E - mu * N) / kT + 3.0 * N * ln_lambda
 
 
+def reduced_potential2(kT, mu, mu2, lambda0, lambda0_2, N, N2, E):
+    """u with a second grand-canonical species C (count N2, chemical potential
+    mu2, thermal wavelength lambda0_2 / sqrt(kT)): the product over species of
+    Eq. Ngrand's factors gives u = beta (E - mu N - mu2 N2) + 3 N ln Lambda
+    + 3 N2 ln Lambda_C."""
+    kT2 = np.atleast_1d(np.asarray(kT, np.float64))[:, None]
+    mu2 = np.atleast_1d(np.asarray(mu2, np.float64))[:, None]
+    N2 = np.asarray(N2, np.float64)[None, :]
+    ln_lambda2 = np.log(lambda0_2) - 0.5 * np.log(kT2)
+    return reduced_potential(kT, mu, lambda0, N, E) + (-mu2 / kT2 + 3.0 * ln_lambda2) * N2
+
+
 def mu_from_pressure(kT, p, lambda0):
     """mu = kT ln(p Lambda^3 / kT): the ideal-gas reservoir relation of Sec. III.A
     (beta mu = beta mu0 + ln(beta p), mu0 = kT ln Lambda^3)."""
@@ -68,11 +80,25 @@ def occupied_bins(hNE, e_lo, e_bin, centre: float = 0.5):
             hNE[n_idx, k_idx].astype(np.float64))
 
 
-def solve(kT_s, mu_s, lambda0, omega_s, N_b, E_b, H_b, tol=1e-10, max_iter=200000):
-    """Self-consistent MBAR free energies f_s (f_0 = 0).
+def occupied_bins2(hNE, nmax, e_lo, e_bin):
+    """Pooled (N_B, N_C, E) histogram of two species (row N_B (nmax+1) + N_C)
+    -> (N_B, N_C, E at the bin centre, H) of the non-empty bins."""
+    hNE = np.asarray(hNE)
+    r_idx, k_idx = np.nonzero(hNE)
+    return ((r_idx // (nmax + 1)).astype(np.float64), (r_idx % (nmax + 1)).astype(np.float64),
+            e_lo + (k_idx + 0.5) * e_bin, hNE[r_idx, k_idx].astype(np.float64))
+
+
+def solve(kT_s, mu_s, lambda0, omega_s, N_b, E_b, H_b, tol=1e-10, max_iter=200000, mu2_s=None, N2_b=None,
+          lambda0_2=1.0):
+    """Self-consistent MBAR free energies f_s (f_0 = 0); with mu2_s and N2_b
+    the reduced potential of two species (reduced_potential2).
 
     Returns (f [S], D [B], iterations, converged)."""
-    u = reduced_potential(kT_s, mu_s, lambda0, N_b, E_b)          # [S, B]
+    if N2_b is None:
+        u = reduced_potential(kT_s, mu_s, lambda0, N_b, E_b)      # [S, B]
+    else:
+        u = reduced_potential2(kT_s, mu_s, mu2_s, lambda0, lambda0_2, N_b, N2_b, E_b)
     omega = np.asarray(omega_s, np.float64)
     ln_omega = np.where(omega > 0, np.log(np.where(omega > 0, omega, 1.0)), -np.inf)
     ln_h = np.log(np.asarray(H_b, np.float64))
@@ -110,3 +136,20 @@ def query(kT_q, mu_q, lambda0, N_b, E_b, H_b, D_b, nmax):
         if np.any(sel):
             p_N[:, n] = np.sum(w[:, sel], axis=1)
     return n_mean, p_N, f_q
+
+
+def query2(kT_q, mu_q, mu2_q, lambda0, lambda0_2, N_b, N2_b, E_b, H_b, D_b, nmax):
+    """Two species: reweight to query states (kT_q, mu_q, mu2_q).
+
+    Returns (<N_B> [Q], <N_C> [Q], p_N_B [Q, nmax+1], p_N_C [Q, nmax+1], f_q [Q])."""
+    u = reduced_potential2(kT_q, mu_q, mu2_q, lambda0, lambda0_2, N_b, N2_b, E_b)
+    ln_w = np.log(np.asarray(H_b, np.float64))[None, :] - u - np.asarray(D_b)[None, :]
+    f_q = -lse(ln_w, axis=1)
+    w = np.exp(ln_w + f_q[:, None])
+    N_b, N2_b = np.asarray(N_b), np.asarray(N2_b)
+    pB = np.zeros((u.shape[0], nmax + 1))
+    pC = np.zeros((u.shape[0], nmax + 1))
+    for n in range(nmax + 1):
+        pB[:, n] = np.sum(w[:, N_b == n], axis=1)
+        pC[:, n] = np.sum(w[:, N2_b == n], axis=1)
+    return w @ N_b, w @ N2_b, pB, pC, f_q

@@ -100,3 +100,57 @@ def test_pressure_relation_ideal_gas():
     mu = mbar.mu_from_pressure(kT, p, 1.0)
     lam = 100.0 * np.exp(mu / kT) / (1.0 / np.sqrt(kT)) ** 3
     np.testing.assert_allclose(lam, p * 100.0 / kT, rtol=1e-12)
+
+
+def _ideal2_setup(nmax=20, V=50.0, lam0_2=0.7):
+    """Two ideal species (B: lambda0 1, C: lambda0_2) on six (kT, mu_B, mu_C)
+    states, histograms proportional to the exact probabilities of the product
+    of two Poisson laws truncated to N_B + N_C <= nmax."""
+    kT = np.array([0.7, 0.7, 1.1, 1.1, 1.6, 1.6])
+    mu = np.array([-4.0, -3.2, -3.6, -3.0, -4.2, -3.4])
+    mu2 = np.array([-3.6, -4.1, -3.2, -3.9, -3.5, -4.4])
+    omega = np.array([1000.0, 2000.0, 1500.0, 800.0, 1200.0, 900.0])
+    a = np.arange(nmax + 1)
+    NB, NC = np.meshgrid(a, a, indexing="ij")
+    keep = NB + NC <= nmax
+    NB, NC = NB[keep].astype(float), NC[keep].astype(float)
+    lg = np.array([math.lgamma(k + 1) for k in range(nmax + 1)])
+    H = np.zeros(len(NB))
+    lnxi = np.zeros(len(kT))
+    for s in range(len(kT)):
+        lb = math.log(V) + mu[s] / kT[s] + 1.5 * math.log(kT[s])
+        lc = math.log(V) + mu2[s] / kT[s] - 3 * math.log(lam0_2) + 1.5 * math.log(kT[s])
+        lp = NB * lb + NC * lc - lg[NB.astype(int)] - lg[NC.astype(int)]
+        lnxi[s] = mbar.lse(lp)
+        H += omega[s] * np.exp(lp - lnxi[s])
+    return kT, mu, mu2, omega, NB, NC, H, lnxi, V, lam0_2
+
+
+def test_two_species_ideal_gas_free_energies_and_reweighting():
+    """With two species the partition function is the truncated double sum
+    Xi_s = sum_{a + b <= nmax} lambda_B^a / a! lambda_C^b / b!: MBAR must give
+    f_s - f_0 = -ln(Xi_s / Xi_0), and reweighting to other (kT, mu_B, mu_C)
+    the exact truncated means of both counts."""
+    nmax = 20
+    kT, mu, mu2, omega, NB, NC, H, lnxi, V, l2 = _ideal2_setup(nmax)
+    E = np.zeros(len(NB))
+    lnV = math.log(V)
+    f, D, it, ok = mbar.solve(kT, mu + kT * lnV, 1.0, omega, NB, E, H, tol=1e-12,
+                              mu2_s=mu2 + kT * lnV, N2_b=NC, lambda0_2=l2)
+    assert ok
+    np.testing.assert_allclose(f, -(lnxi - lnxi[0]), atol=1e-9)
+    kq, mq, m2q = np.array([0.8, 1.3]), np.array([-3.5, -3.3]), np.array([-3.8, -3.6])
+    nb, nc, pB, pC, _ = mbar.query2(kq, mq + kq * lnV, m2q + kq * lnV, 1.0, l2, NB, NC, E, H, D, nmax)
+    lg = np.array([math.lgamma(k + 1) for k in range(nmax + 1)])
+    for q in range(len(kq)):
+        lb = lnV + mq[q] / kq[q] + 1.5 * math.log(kq[q])
+        lc = lnV + m2q[q] / kq[q] - 3 * math.log(l2) + 1.5 * math.log(kq[q])
+        lp = NB * lb + NC * lc - lg[NB.astype(int)] - lg[NC.astype(int)]
+        w = np.exp(lp - mbar.lse(lp))
+        assert nb[q] == pytest.approx(w @ NB, rel=1e-9)
+        assert nc[q] == pytest.approx(w @ NC, rel=1e-9)
+        assert pB[q].sum() == pytest.approx(1.0, abs=1e-12)
+    # planted: the second species' chemical potential left out
+    f_bad, _, _, _ = mbar.solve(kT, mu + kT * lnV, 1.0, omega, NB, E, H, tol=1e-12,
+                                mu2_s=np.zeros_like(mu2), N2_b=NC, lambda0_2=l2)
+    assert np.max(np.abs(f_bad + (lnxi - lnxi[0]))) > 1e-2
