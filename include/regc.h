@@ -439,6 +439,22 @@ REGC_API regc_status regc_reweight(regc_handle *h, int nq, const double *kT_q, c
                           double tol, int max_iter, double *N_mean, double *pN,
                           double *f_states, int *iters);
 
+/* MBAR (Sec. II.B) over a two-species run (regc_init_grid2): the pooled
+ * histogram's bins are (N_B, N_C, E) and the reduced potential of a state
+ * (kT, mu_B, mu_C) at a bin is
+ *   u = E / kT + N_B (3 ln Lambda_B - mu_B / kT) + N_C (3 ln Lambda_C - mu_C / kT),
+ * Lambda_X = lambda0_X / sqrt(kT), the two-species form of Eq. 4's weight.
+ * The sampled states' free energies are solved as in regc_reweight (f_states
+ * [S], f_0 = 0, state s = (l M + m) K + k), then reweighted to nq host
+ * queries (kT_q, mu_q, mu2_q): NB_mean, NC_mean [nq] and the marginal
+ * distributions pNB, pNC [nq][nmax+1] of the two counts.  Any output may be
+ * NULL.  Errors: REGC_EINVAL (a one-species handle, nq < 0, a null query
+ * array with nq > 0, kT_q not positive, a query not finite, tol <= 0,
+ * max_iter < 1, nothing observed yet), REGC_ENOMEM, REGC_ECUDA.  Synchronous. */
+REGC_API regc_status regc_reweight2(regc_handle *h, int nq, const double *kT_q, const double *mu_q,
+                                    const double *mu2_q, double tol, int max_iter, double *NB_mean,
+                                    double *NC_mean, double *pNB, double *pNC, double *f_states, int *iters);
+
 /* Structural observables (Sec. III.A, "Structural properties"): the axial
  * distribution rho(z) of the adsorbed particles, counted in slabs parallel to
  * the surface, and the lateral radial distribution g_xy(r) of the particles of

@@ -108,6 +108,7 @@ SIGNATURES = {
     "regc_structure_reweight": ([_h, C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp, _dp,
                                  _dp, C.POINTER(C.c_int)], C.c_int),
     "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
+    "regc_reweight2": ([_h, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _ip], C.c_int),
     "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
                          C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
     "regc_mbar_solve_static": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,

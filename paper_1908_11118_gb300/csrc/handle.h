@@ -80,6 +80,9 @@ struct regc_handle {
     int K = 1;
     int n_dir = 4;                            // exchange directions (5 with K > 1)
     long long hist_rows = 0;                  // rows of the pooled (N, E) histogram
+    std::vector<double> mu2_state;            // per state: mu of species C (two species)
+    double* d_mu2_state = nullptr;
+    double lambda0_2 = 1.0;                   // Lambda_C at kT = 1
 };
 
 // Synchronise the handle's stream and fold its device error word into the

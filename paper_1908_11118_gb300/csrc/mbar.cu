@@ -119,21 +119,39 @@ __device__ double block_max(double v) {
 constexpr float kMargin = 1.0f;
 constexpr int kDTile = 512;
 
-__global__ void en32_kernel(int B, const double* E_b, const int* N_b, float2* EN32) {
+__global__ void en32_kernel(int B, const double* E_b, const int* N_b, float2* EN32, const int* N2_b, float* N2f) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) EN32[b] = make_float2((float)E_b[b], (float)N_b[b]);
+    if (b < B) {
+        EN32[b] = make_float2((float)E_b[b], (float)N_b[b]);
+        if (N2_b) N2f[b] = (float)N2_b[b];
+    }
 }
 
-// D_b = ln sum_k exp(lnom_k + f_k - a_k E_b - c_k N_b)
+// The reduced potential of state (a, c, c2) at bin (E, N, N2): a E + c N,
+// plus c2 N2 with a second species (TWO); the same in binary32 for the
+// screening.
+template <bool TWO>
+__device__ __forceinline__ double u_of(double a, double c, double c2, double E, double N, double N2) {
+    return TWO ? fma(a, E, fma(c2, N2, c * N)) : fma(a, E, c * N);
+}
+template <bool TWO>
+__device__ __forceinline__ float u32_of(float a, float c, float c2, float E, float N, float N2) {
+    return TWO ? fmaf(a, E, fmaf(c2, N2, c * N)) : fmaf(a, E, c * N);
+}
+
+// D_b = ln sum_k exp(lnom_k + f_k - u_k(b))
+template <bool TWO>
 __global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev m, int always) {
     if (!always && m.state[0]) return;
-    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile];
-    __shared__ float fa[kDTile], fc[kDTile], fg[kDTile];
+    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile], sc2[TWO ? kDTile : 1];
+    __shared__ float fa[kDTile], fc[kDTile], fg[kDTile], fc2[TWO ? kDTile : 1];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = b < m.B;
     const double E = act ? m.E_b[b] : 0.0;
     const double N = act ? (double)m.N_b[b] : 0.0;
+    const double N2 = (TWO && act) ? (double)m.N2_b[b] : 0.0;
     const float2 en = act ? m.EN32[b] : make_float2(0.f, 0.f);
+    const float n2f = (TWO && act) ? m.N2f[b] : 0.f;
     const bool one_tile = m.S <= kDTile;
     float mx32 = -INFINITY;
     Lse L{-INFINITY, 0.0};
@@ -150,16 +168,22 @@ __global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev 
                     fa[k] = (float)sa[k];
                     fc[k] = (float)sc[k];
                     fg[k] = (float)g;
+                    if (TWO) {
+                        sc2[k] = m.c2[k0 + k];
+                        fc2[k] = (float)sc2[k];
+                    }
                 }
                 __syncthreads();
             }
             if (!act) continue;
             if (pass == 0) {
-                for (int k = 0; k < nk; ++k) mx32 = fmaxf(mx32, fg[k] - fmaf(fa[k], en.x, fc[k] * en.y));
+                for (int k = 0; k < nk; ++k)
+                    mx32 = fmaxf(mx32, fg[k] - u32_of<TWO>(fa[k], fc[k], fc2[TWO ? k : 0], en.x, en.y, n2f));
             } else {
                 const float th = mx32 - (float)kSkip - kMargin;
                 for (int k = 0; k < nk; ++k)
-                    if (fg[k] - fmaf(fa[k], en.x, fc[k] * en.y) > th) lse_add(L, sg[k] - fma(sa[k], E, sc[k] * N));
+                    if (fg[k] - u32_of<TWO>(fa[k], fc[k], fc2[TWO ? k : 0], en.x, en.y, n2f) > th)
+                        lse_add(L, sg[k] - u_of<TWO>(sa[k], sc[k], sc2[TWO ? k : 0], E, N, N2));
             }
         }
     }
@@ -178,6 +202,7 @@ __global__ void __launch_bounds__(256) d_kernel(const __grid_constant__ MbarDev 
 // in rank order (deterministic).
 constexpr int kFThreads = 256;
 constexpr int kFSplit = 4;
+template <bool TWO>
 __global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
     f_kernel(const __grid_constant__ MbarDev m) {
     __shared__ double part[2];
@@ -189,19 +214,20 @@ __global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
     if (live) {
         const int per = (m.B + kFSplit - 1) / kFSplit;
         const int b0 = rank * per, b1 = min(m.B, b0 + per);
-        const double a = m.a[s], c = m.c[s];
-        const float a32 = (float)a, c32 = (float)c;
+        const double a = m.a[s], c = m.c[s], c2 = TWO ? m.c2[s] : 0.0;
+        const float a32 = (float)a, c32 = (float)c, c232 = (float)c2;
         float mx32 = -INFINITY;
         for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) {
             const float2 en = m.EN32[b];
-            mx32 = fmaxf(mx32, -fmaf(a32, en.x, c32 * en.y) - m.DH32[b]);
+            mx32 = fmaxf(mx32, -u32_of<TWO>(a32, c32, c232, en.x, en.y, TWO ? m.N2f[b] : 0.f) - m.DH32[b]);
         }
         mx32 = (float)block_max((double)mx32);
         const float th = mx32 - (float)kSkip - kMargin;
         for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) {
             const float2 en = m.EN32[b];
-            if (-fmaf(a32, en.x, c32 * en.y) - m.DH32[b] > th)
-                lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+            if (-u32_of<TWO>(a32, c32, c232, en.x, en.y, TWO ? m.N2f[b] : 0.f) - m.DH32[b] > th)
+                lse_add(L, m.lnH[b] - u_of<TWO>(a, c, c2, m.E_b[b], (double)m.N_b[b],
+                                                 TWO ? (double)m.N2_b[b] : 0.0) - m.D[b]);
         }
         L = block_merge(L);
     }
@@ -315,7 +341,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(int* counts, int nblk, int* 
 
 __global__ void __launch_bounds__(256) write_kernel(const unsigned long long* h, long long n, int nbins,
                                                     double e_lo, double e_bin, const int* offsets,
-                                                    int* N_b, double* E_b, double* lnH) {
+                                                    int* N_b, double* E_b, double* lnH, int rows2, int* N2_b) {
     const long long base = (long long)blockIdx.x * kChunk;
     int c = 0;
     for (int k = 0; k < 4; ++k) {
@@ -340,7 +366,13 @@ __global__ void __launch_bounds__(256) write_kernel(const unsigned long long* h,
         const long long i = base + threadIdx.x * 4 + k;
         if (i < n && h[i] != 0ull) {
             const long long nn = i / nbins, kb = i - nn * nbins;
-            N_b[out] = (int)nn;
+            if (N2_b) {
+                // two species: the row is N (rows2) + N2
+                N_b[out] = (int)(nn / rows2);
+                N2_b[out] = (int)(nn % rows2);
+            } else {
+                N_b[out] = (int)nn;
+            }
             E_b[out] = __dadd_rn(e_lo, __dmul_rn((double)kb + 0.5, e_bin));   // as written: no contraction
             lnH[out] = log((double)h[i]);
             ++out;
@@ -361,6 +393,57 @@ __global__ void prep_states_kernel(int S, const double* kT, const double* mu, do
     if (lnom) {
         const double om = omega_d ? omega_d[s] : (omega_u ? (double)omega_u[s] : 0.0);
         lnom[s] = om > 0.0 ? log(om) : -INFINITY;
+    }
+}
+
+// c2 = 3 ln Lambda_C - beta mu2 of a second species.
+__global__ void prep_states2_kernel(int S, const double* kT, const double* mu2, double lambda0_2, double* c2) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    c2[s] = 3.0 * (log(lambda0_2) - 0.5 * log(kT[s])) - mu2[s] / kT[s];
+}
+
+// Two species: the query of query_kernel with u = a E + c N + c2 N2, and the
+// distributions of both counts.
+__global__ void __launch_bounds__(256) query2_kernel(const __grid_constant__ MbarDev m, const double* a_q,
+                                                     const double* c_q, const double* c2_q, int nmax,
+                                                     double* n_mean, double* n2_mean, double* pN, double* pN2,
+                                                     double* f_q) {
+    extern __shared__ double hist2[];   // [2][nmax + 1]
+    const int q = blockIdx.x;
+    const double a = a_q[q], c = c_q[q], c2 = c2_q[q];
+    for (int n = threadIdx.x; n < 2 * (nmax + 1); n += blockDim.x) hist2[n] = 0.0;
+    Lse L{-INFINITY, 0.0};
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
+        lse_add(L, m.lnH[b] - u_of<true>(a, c, c2, m.E_b[b], (double)m.N_b[b], (double)m.N2_b[b]) - m.D[b]);
+    L = block_merge(L);
+    const double fq = -(L.m + log(L.s));
+    double nsum = 0.0, n2sum = 0.0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x) {
+        const double x =
+            m.lnH[b] - u_of<true>(a, c, c2, m.E_b[b], (double)m.N_b[b], (double)m.N2_b[b]) - m.D[b] + fq;
+        if (x > -745.0) {
+            const double w = exp(x);
+            const int n = m.N_b[b], n2 = m.N2_b[b];
+            nsum += w * (double)n;
+            n2sum += w * (double)n2;
+            if (n <= nmax) atomicAdd(&hist2[n], w);
+            if (n2 <= nmax) atomicAdd(&hist2[nmax + 1 + n2], w);
+        }
+    }
+    nsum = block_sum(nsum);
+    __syncthreads();
+    n2sum = block_sum(n2sum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (n_mean) n_mean[q] = nsum;
+        if (n2_mean) n2_mean[q] = n2sum;
+        if (f_q) f_q[q] = fq;
+    }
+    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) {
+        if (pN) pN[size_t(q) * (nmax + 1) + n] = hist2[n];
+        if (pN2) pN2[size_t(q) * (nmax + 1) + n] = hist2[nmax + 1 + n];
     }
 }
 
@@ -399,14 +482,16 @@ struct MatDev {
 
 // One thread per bin: t_sb over the states (tiled through shared memory),
 // M_b, then the column of K.  Block 0 records f_ref = f.
+template <bool TWO>
 __global__ void __launch_bounds__(256) mat_build_kernel(const __grid_constant__ MbarDev m, MatDev k) {
-    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile];
+    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile], sc2[TWO ? kDTile : 1];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = b < m.B;
     if (blockIdx.x == 0)
         for (int q = threadIdx.x; q < m.S; q += blockDim.x) k.fref[q] = m.f[q];
     const double E = act ? m.E_b[b] : 0.0;
     const double N = act ? (double)m.N_b[b] : 0.0;
+    const double N2 = (TWO && act) ? (double)m.N2_b[b] : 0.0;
     double M = -INFINITY;
     for (int pass = 0; pass < 2; ++pass) {
         for (int k0 = 0; k0 < m.S; k0 += kDTile) {
@@ -416,13 +501,15 @@ __global__ void __launch_bounds__(256) mat_build_kernel(const __grid_constant__ 
                 sa[q] = m.a[k0 + q];
                 sc[q] = m.c[k0 + q];
                 sg[q] = m.lnom[k0 + q] + m.f[k0 + q];
+                if (TWO) sc2[q] = m.c2[k0 + q];
             }
             __syncthreads();
             if (!act) continue;
             if (pass == 0) {
-                for (int q = 0; q < nk; ++q) M = fmax(M, sg[q] - fma(sa[q], E, sc[q] * N));
+                for (int q = 0; q < nk; ++q) M = fmax(M, sg[q] - u_of<TWO>(sa[q], sc[q], sc2[TWO ? q : 0], E, N, N2));
             } else {
-                for (int q = 0; q < nk; ++q) k.K[size_t(k0 + q) * m.B + b] = exp(sg[q] - fma(sa[q], E, sc[q] * N) - M);
+                for (int q = 0; q < nk; ++q)
+                    k.K[size_t(k0 + q) * m.B + b] = exp(sg[q] - u_of<TWO>(sa[q], sc[q], sc2[TWO ? q : 0], E, N, N2) - M);
             }
         }
     }
@@ -509,7 +596,8 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     if (err != cudaSuccess) return err;
     const int dgrid = (m.B + 255) / 256;
     const int dgrid128 = (m.B + 127) / 128;   // a bin per thread, small blocks to spread over every SM
-    en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32);
+    en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32, m.N2_b, m.N2f);
+    const bool two = m.N2_b != nullptr;
     // the kernel matrix, when every state is sampled and it fits
     MatDev mat{};
     void* mat_block = nullptr;
@@ -555,7 +643,8 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             double drift = 0.0;
             for (int k = 0; k < S; ++k) drift = fmax(drift, fabs(x[k] - fref_h[k]));
             if (build || !(drift <= kRebuild)) {
-                mat_build_kernel<<<dgrid, 256, 0, s>>>(m, mat);
+                if (two) mat_build_kernel<true><<<dgrid, 256, 0, s>>>(m, mat);
+                else mat_build_kernel<false><<<dgrid, 256, 0, s>>>(m, mat);
                 fref_h = x;
                 build = false;
             }
@@ -565,8 +654,13 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             mat_d_kernel<<<(m.B + 31) / 32, 32 * kDGroups, 0, s>>>(m, mat);
             mat_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, mat);
         } else {
-            d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);
-            f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m);
+            if (two) {
+                d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);
+                f_kernel<true><<<S * kFSplit, kFThreads, 0, s>>>(m);
+            } else {
+                d_kernel<false><<<dgrid128, 128, 0, s>>>(m, 1);
+                f_kernel<false><<<S * kFSplit, kFThreads, 0, s>>>(m);
+            }
         }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -659,7 +753,8 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     }
     err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return err;
-    d_kernel<<<dgrid128, 128, 0, s>>>(m, 1);  // D_b of the final f
+    if (two) d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);  // D_b of the final f
+    else d_kernel<false><<<dgrid128, 128, 0, s>>>(m, 1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     // the host vectors go out of scope: wait for the copy that reads x
@@ -694,7 +789,34 @@ cudaError_t compact_write_dev(const unsigned long long* hist, long long n, int n
                               const int* scratch, int* N_b, double* E_b, double* lnH, cudaStream_t s) {
     const int nblk = (int)((n + kChunk - 1) / kChunk);
     if (nblk == 0) return cudaSuccess;
-    write_kernel<<<nblk, 256, 0, s>>>(hist, n, nbins, e_lo, e_bin, scratch, N_b, E_b, lnH);
+    write_kernel<<<nblk, 256, 0, s>>>(hist, n, nbins, e_lo, e_bin, scratch, N_b, E_b, lnH, 1, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t compact_write2_dev(const unsigned long long* hist, long long n, int nbins, int rows2, double e_lo,
+                               double e_bin, const int* scratch, int* N_b, int* N2_b, double* E_b, double* lnH,
+                               cudaStream_t s) {
+    const int nblk = (int)((n + kChunk - 1) / kChunk);
+    if (nblk == 0) return cudaSuccess;
+    write_kernel<<<nblk, 256, 0, s>>>(hist, n, nbins, e_lo, e_bin, scratch, N_b, E_b, lnH, rows2, N2_b);
+    return cudaGetLastError();
+}
+
+cudaError_t mbar_prep_states2(int S, const double* kT, const double* mu2, double lambda0_2, double* c2,
+                              cudaStream_t s) {
+    if (S <= 0) return cudaSuccess;
+    prep_states2_kernel<<<(S + 255) / 256, 256, 0, s>>>(S, kT, mu2, lambda0_2, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, const double* c2_q,
+                            int nmax, double* n_mean, double* n2_mean, double* pN, double* pN2, double* f_q,
+                            cudaStream_t s) {
+    if (Q <= 0) return cudaSuccess;
+    const size_t smem = 2 * size_t(nmax + 1) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(query2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    query2_kernel<<<Q, 256, smem, s>>>(m, a_q, c_q, c2_q, nmax, n_mean, n2_mean, pN, pN2, f_q);
     return cudaGetLastError();
 }
 

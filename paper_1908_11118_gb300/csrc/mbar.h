@@ -24,6 +24,10 @@ struct MbarDev {
     float* DH32;           // [B] D_b - lnH_b in binary32, written with D
     double* delta;         // [1] max |f_new - f| of the last iteration
     int* state;            // [2] cleared by the solve (the kernels skip work when state[0] is set)
+    // a second grand-canonical species: u_s(b) = a[s] E_b + c[s] N_b + c2[s] N2_b
+    const int* N2_b;       // [B] its counts, or null (one species)
+    const double* c2;      // [S] 3 ln Lambda_C - beta mu2
+    float* N2f;            // [B] N2_b in binary32, filled by the solve
 };
 
 // Solve the self-consistent equations from f = 0 (the plain fixed-point map
@@ -41,6 +45,17 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
 cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q,
                            int nmax, double* N_mean, double* pN, double* f_q, cudaStream_t s);
 
+// Two species: reweight to Q query states (a_q, c_q, c2_q): the means of both
+// counts N_mean, N2_mean [Q], their distributions pN, pN2 [Q][nmax+1] and
+// f_q [Q] (device, any may be null).
+cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, const double* c2_q,
+                            int nmax, double* N_mean, double* N2_mean, double* pN, double* pN2, double* f_q,
+                            cudaStream_t s);
+
+// c2 = 3 ln(lambda0_2 / sqrt(kT)) - mu2 / kT of a second species, per state (device).
+cudaError_t mbar_prep_states2(int S, const double* kT, const double* mu2, double lambda0_2, double* c2,
+                              cudaStream_t s);
+
 // Compact the non-empty bins of a pooled histogram hist[n] (row-major in
 // (N, E-bin), nbins E-bins per N) into N_b, E_b (bin centres), lnH (ln
 // counts), in row-major order.  compact_count_dev writes the per-block
@@ -52,6 +67,12 @@ cudaError_t compact_count_dev(const unsigned long long* hist, long long n, int* 
                               cudaStream_t s);
 cudaError_t compact_write_dev(const unsigned long long* hist, long long n, int nbins, double e_lo, double e_bin,
                               const int* scratch, int* N_b, double* E_b, double* lnH, cudaStream_t s);
+
+// As compact_write_dev for the two-species histogram, whose row is
+// N (rows2) + N2: fills N_b and N2_b.
+cudaError_t compact_write2_dev(const unsigned long long* hist, long long n, int nbins, int rows2, double e_lo,
+                               double e_bin, const int* scratch, int* N_b, int* N2_b, double* E_b, double* lnH,
+                               cudaStream_t s);
 
 // State constants on the device: a = 1/kT, c = 3 ln(lambda0/sqrt(kT)) - mu/kT,
 // lnom = ln Omega (-inf for Omega = 0; skipped when lnom is null).  kT, mu are

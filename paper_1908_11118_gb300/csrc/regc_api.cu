@@ -246,6 +246,7 @@ regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const
     std::vector<double> beta(S), c_ins(S), c_del(S), bmu(S), lnbeta(S), c_ins2(S), c_del2(S), bmu2(S);
     h->kT_state.resize(S);
     h->mu_state.resize(S);
+    h->mu2_state.clear();
     for (int s = 0; s < S; ++s) {
         // state s = (l M + m) K + k: kT[l], mu[m], and mu2[k] of a second species
         const double kT = grid->kT[s / (grid->M * K)], mu = grid->mu[(s / K) % grid->M];
@@ -264,8 +265,10 @@ regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const
             c_ins2[s] = lnV - 3.0 * lnL2 + b * mu2;
             c_del2[s] = 3.0 * lnL2 - lnV - b * mu2;
             bmu2[s] = b * mu2;
+            h->mu2_state.push_back(mu2);
         }
     }
+    if (sp2) h->lambda0_2 = sp2->lambda0;
     std::vector<double> ln_tab(grid->nmax + 2, 0.0);
     for (int k = 1; k < grid->nmax + 2; ++k) ln_tab[k] = log((double)k);
     std::vector<float> beta_f(S), cins_f(S), cdel_f(S), ln_f(grid->nmax + 2);
@@ -491,6 +494,8 @@ regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const
         TRY(upload(h, d_ci2f, ci2f.data(), S));
         TRY(upload(h, d_cd2f, cd2f.data(), S));
         TRY(upload(h, d_bmu2, bmu2.data(), S));
+        TRY(dalloc(h, &h->d_mu2_state, S));
+        TRY(upload(h, h->d_mu2_state, h->mu2_state.data(), S));
         TRY(dalloc(h, &P.nb, S));
         TRY(dalloc(h, &P.hN2, (size_t)S * (grid->nmax + 1)));
         TRY(dalloc(h, &P.moments2, (size_t)S * 2));
@@ -1543,6 +1548,94 @@ regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const doub
     e = solve_and_query(buf, m, h->lambda0, tol, max_iter, iters, f_states, nullptr, nq, kT_q, mu_q, h->nmax, N_mean,
                         pN, nullptr);
     return status_of(e);
+}
+
+regc_status regc_reweight2(regc_handle* h, int nq, const double* kT_q, const double* mu_q, const double* mu2_q,
+                           double tol, int max_iter, double* NB_mean, double* NC_mean, double* pNB, double* pNC,
+                           double* f_states, int* iters) {
+    if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q || !mu2_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;
+    if (!h->P.gc2) return REGC_EINVAL;   // one species: regc_reweight
+    for (int q = 0; q < nq; ++q)
+        if (!(kT_q[q] > 0.0) || !std::isfinite(kT_q[q]) || !std::isfinite(mu_q[q]) || !std::isfinite(mu2_q[q]))
+            return REGC_EINVAL;
+    regc_status st = sync_check(h);
+    if (st != REGC_OK) return st;
+    MbarBuffers buf;
+    buf.s = h->stream;
+    cudaStream_t s = h->stream;
+    const int rows2 = h->nmax + 1;
+    const long long n = h->hist_rows * h->n_e_bins;
+    int* scratch = buf.get<int>(compact_scratch_ints(n));
+    int* d_count = buf.get<int>(1);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    cudaError_t e = compact_count_dev(h->P.hNE, n, scratch, d_count, s);
+    int B = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&B, d_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_of(e);
+    if (B == 0) return REGC_EINVAL;   // nothing observed yet
+    MbarDev m{};
+    m.S = h->S;
+    m.B = B;
+    int* N_b = buf.get<int>(B);
+    int* N2_b = buf.get<int>(B);
+    double* E_b = buf.get<double>(B);
+    double* lnH = buf.get<double>(B);
+    double* a = buf.get<double>(h->S);
+    double* c = buf.get<double>(h->S);
+    double* c2 = buf.get<double>(h->S);
+    double* lnom = buf.get<double>(h->S);
+    m.f = buf.get<double>(m.S);
+    m.f_new = buf.get<double>(m.S);
+    m.D = buf.get<double>(B);
+    m.EN32 = buf.get<float2>(B);
+    m.DH32 = buf.get<float>(B);
+    m.N2f = buf.get<float>(B);
+    m.delta = buf.get<double>(1);
+    m.state = buf.get<int>(2);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    e = compact_write2_dev(h->P.hNE, n, h->n_e_bins, rows2, h->e_lo, h->e_bin, scratch, N_b, N2_b, E_b, lnH, s);
+    if (e == cudaSuccess)
+        e = mbar_prep_states(h->S, h->d_kT_state, h->d_mu_state, h->lambda0, nullptr, h->P.omega, a, c, lnom, s);
+    if (e == cudaSuccess) e = mbar_prep_states2(h->S, h->d_kT_state, h->d_mu2_state, h->lambda0_2, c2, s);
+    if (e != cudaSuccess) return status_of(e);
+    m.a = a;
+    m.c = c;
+    m.c2 = c2;
+    m.lnom = lnom;
+    m.N_b = N_b;
+    m.N2_b = N2_b;
+    m.E_b = E_b;
+    m.lnH = lnH;
+    e = mbar_solve_dev(m, tol, max_iter, iters, s);
+    if (e == cudaSuccess && f_states) e = cudaMemcpyAsync(f_states, m.f, m.S * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return status_of(e);
+    if (nq > 0) {
+        const size_t P = (size_t)nq * rows2;
+        double* d_kq = buf.get<double>(nq);
+        double* d_mq = buf.get<double>(nq);
+        double* d_m2q = buf.get<double>(nq);
+        double* a_q = buf.get<double>(nq);
+        double* c_q = buf.get<double>(nq);
+        double* c2_q = buf.get<double>(nq);
+        double* d_nb = buf.get<double>(nq);
+        double* d_nc = buf.get<double>(nq);
+        double* d_pb = buf.get<double>(P);
+        double* d_pc = buf.get<double>(P);
+        if (buf.err != cudaSuccess) return status_of(buf.err);
+        e = cudaMemcpyAsync(d_kq, kT_q, nq * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_mq, mu_q, nq * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_m2q, mu2_q, nq * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = mbar_prep_states(nq, d_kq, d_mq, h->lambda0, nullptr, nullptr, a_q, c_q, nullptr, s);
+        if (e == cudaSuccess) e = mbar_prep_states2(nq, d_kq, d_m2q, h->lambda0_2, c2_q, s);
+        if (e == cudaSuccess) e = mbar_query2_dev(m, nq, a_q, c_q, c2_q, h->nmax, d_nb, d_nc, d_pb, d_pc, nullptr, s);
+        if (e == cudaSuccess && NB_mean) e = cudaMemcpyAsync(NB_mean, d_nb, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && NC_mean) e = cudaMemcpyAsync(NC_mean, d_nc, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && pNB) e = cudaMemcpyAsync(pNB, d_pb, P * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && pNC) e = cudaMemcpyAsync(pNC, d_pc, P * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return status_of(e);
+    }
+    return status_of(cudaStreamSynchronize(s));
 }
 
 regc_status regc_mbar_solve(int S, const double* kT, const double* mu, double lambda0, const double* omega, int B,

@@ -407,6 +407,24 @@ class Regc:
                                        C.byref(it)), "regc_reweight")
         return nm, pN, f, it.value
 
+    def reweight2(self, kT_q, mu_q, mu2_q, tol: float = 1e-10, max_iter: int = 100000):
+        """Two species: (NB_mean, NC_mean, pNB, pNC, f_states, iterations) at
+        the query states (kT_q, mu_q, mu2_q)."""
+        kq = np.ascontiguousarray(kT_q, np.float64)
+        mq = np.ascontiguousarray(mu_q, np.float64)
+        m2 = np.ascontiguousarray(mu2_q, np.float64)
+        Q = len(kq)
+        if len(mq) != Q or len(m2) != Q:
+            raise ValueError("query arrays differ in length")
+        nb, nc = np.zeros(Q), np.zeros(Q)
+        pb, pc = np.zeros((Q, self.nmax + 1)), np.zeros((Q, self.nmax + 1))
+        f = np.zeros(self.S)
+        it = C.c_int32(0)
+        d = C.c_double
+        check(_lib.lib().regc_reweight2(self._h, Q, _p(kq, d), _p(mq, d), _p(m2, d), tol, max_iter, _p(nb, d),
+                                        _p(nc, d), _p(pb, d), _p(pc, d), _p(f, d), C.byref(it)), "regc_reweight2")
+        return nb, nc, pb, pc, f, it.value
+
 
 class Batch:
     """Several Regc handles (systems of uneven size) stepped together: one

@@ -11,6 +11,9 @@ against the FP64 oracle.
   two Poisson laws truncated to N_B + N_C <= Nmax, within 3 standard errors.
 * Walker upload with species counts, energies against the oracle's.
 * Checkpoint and resume; the paths that take one species only refuse.
+* MBAR over the (N_B, N_C, E) histogram (regc_reweight2): the sampled
+  states' free energies and the reweighted means and distributions of both
+  counts against oracle/mbar.py on the same bins.
 """
 import math
 
@@ -18,6 +21,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import mbar as OM
 from oracle import oracle as O
 from paper_1908_11118_gb300 import Batch, Regc
 from paper_1908_11118_gb300 import build as B
@@ -144,3 +148,35 @@ def test_checkpoint_and_refusals_two_species():
                  lambda: g.structure_init(10, 0.1, [], 5, 0.1, 100)):
         with pytest.raises(Exception):
             call()
+
+
+def test_reweight2_matches_oracle():
+    p = W.two_gas_small(seed=11)
+    g, _ = make(p, 6, 6, seed=3)
+    g.run(400, exchange_every=1)
+    h = g.histograms()
+    assert (h["omega"] > 0).all()
+    kT_s, mu_s, mu2_s = p.state_params()
+    N_b, N2_b, E_b, H_b = OM.occupied_bins2(h["hNE"], p.nmax, p.e_lo, p.e_bin)
+    assert len(np.unique(N2_b)) > 3 and len(np.unique(N_b)) > 3
+    f_o, D_o, _, ok = OM.solve(kT_s, mu_s, p.lambda0, h["omega"].astype(float), N_b, E_b, H_b, tol=1e-12,
+                               mu2_s=mu2_s, N2_b=N2_b, lambda0_2=p.lambda0_2)
+    assert ok
+    # queries: two sampled states and points between and beyond the grid
+    kq = np.array([kT_s[0], kT_s[-1], 0.5 * (p.kT[0] + p.kT[-1]), p.kT[0]])
+    mq = np.array([mu_s[0], mu_s[-1], 0.5 * (p.mu[0] + p.mu[-1]), p.mu[-1] + 0.1])
+    m2q = np.array([mu2_s[0], mu2_s[-1], 0.5 * (p.mu2[0] + p.mu2[-1]), p.mu2[0] - 0.1])
+    nb_o, nc_o, pb_o, pc_o, _ = OM.query2(kq, mq, m2q, p.lambda0, p.lambda0_2, N_b, N2_b, E_b, H_b, D_o, p.nmax)
+    nb_g, nc_g, pb_g, pc_g, f_g, it = g.reweight2(kq, mq, m2q, tol=1e-11)
+    assert it > 0
+    np.testing.assert_allclose(f_g, f_o, atol=1e-8)
+    np.testing.assert_allclose(nb_g, nb_o, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(nc_g, nc_o, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(pb_g, pb_o, atol=1e-9)
+    np.testing.assert_allclose(pc_g, pc_o, atol=1e-9)
+    np.testing.assert_allclose(pb_g.sum(1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(pc_g.sum(1), 1.0, atol=1e-12)
+    single = Regc(W.fcc100_small(L=2, M=3))
+    single.run(20)
+    with pytest.raises(Exception):
+        single.reweight2([1.0], [-3.0], [-3.0])
