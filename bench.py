@@ -74,6 +74,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--production", type=int, default=100000,
                     help="sweeps of the 1024-replica production run reweighted to <N>(T, p) (0: skip)")
+    ap.add_argument("--two-species", type=int, default=1, help="1: add the two-species workload")
+    ap.add_argument("--two-species-steps", type=int, default=20)
+    ap.add_argument("--two-species-sweeps", type=int, default=20000)
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
     ap.add_argument("--da-steps-large", type=int, default=60)
@@ -549,6 +552,95 @@ def production_arm(torch, stream, sweeps, equil=2000, seed=0):
                           "N_most_probable": np.argmax(pN, axis=1).reshape(12, 12).tolist()}}
 
 
+TWO_SPECIES = ("two LJ gases B, C over the fcc111 12x12x4 slab, 8 kT x 16 mu_B x 8 mu_C = 1024 replicas, "
+               "N_B + N_C <= 256, 20 moves/sweep; step = 10 sweeps + 1 replica-exchange attempt "
+               "(5 directions)")
+
+
+def two_species_arm(torch, stream, flush, steps, sweeps, equil=2000, seed=0):
+    """Two grand-canonical species (regc_init_grid2) at paper scale: device-
+    timed steps as in the main arm, then a production run with per-state
+    energy windows (convergence by the KS test of the two halves) and the
+    pooled (N_B, N_C, E) histogram reweighted (Sec. II.B) onto a mu_B x mu_C
+    map at three temperatures."""
+    from paper_1908_11118_gb300 import Regc
+
+    p = W.two_gas_paper_scale(seed=seed)
+    rng = np.random.default_rng(seed)
+    pos, n, nb = W.two_gas_initial(p, rng.integers(0, 40, p.S), rng.integers(0, 40, p.S), seed=seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos, n, nb=nb)
+    g.run(equil, exchange_every=SWEEPS_PER_STEP)
+    for _ in range(3):
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+    mv0, ex0, _ = g.counters()
+    ev = []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        g.sweep(SWEEPS_PER_STEP)
+        e[1].record(stream)
+        g.exchange()
+        e[2].record(stream)
+        ev.append(e)
+    torch.cuda.synchronize()
+    step_ms = sum(e[0].elapsed_time(e[2]) for e in ev) / steps
+    sweep_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    mv1, ex1, _ = g.counters()
+    dm = mv1 - mv0
+    dx = ex1 - ex0
+    timed = {"steps": steps, "ms_per_step": step_ms, "sweep_launch_ms": sweep_ms,
+             "trial_moves_per_s": p.S * SWEEPS_PER_STEP * p.moves_per_sweep / (step_ms / 1e3),
+             "acceptance": float(dm[:, :, 1].sum() / max(dm[:, :, 0].sum(), 1)),
+             "exchange_acceptance_per_direction": (dx[:, :, 1].sum(0) / np.maximum(dx[:, :, 0].sum(0), 1)).tolist(),
+             "l2": "flushed (256 MB memset) before every timed step"}
+    g.set_state_windows(1024, 0.5, None)
+    g.reset_histograms()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    half, done, chunk = None, 0, 1000
+    while done < sweeps:
+        k = min(chunk, sweeps - done)
+        g.run(k, exchange_every=SWEEPS_PER_STEP)
+        done += k
+        if half is None and done >= sweeps // 2:
+            half = g.state_histograms()[0]
+    full = g.state_histograms()[0]
+    torch.cuda.synchronize()
+    run_s = time.perf_counter() - t0
+    ks, crit = ks_halves(half, full - half)
+    h = g.histograms()
+    cnt = g.species_counts()
+    kT_q = np.array([p.kT[1], p.kT[len(p.kT) // 2], p.kT[-2]])
+    mb = np.linspace(-6.0, -2.0, 12)
+    mc = np.linspace(-6.0, -2.0, 12)
+    T, MB, MC = np.meshgrid(kT_q, mb, mc, indexing="ij")
+    t1 = time.perf_counter()
+    nbm, ncm, pb, pc, f, iters = g.reweight2(T.ravel(), MB.ravel(), MC.ravel(), tol=1e-9, max_iter=200000)
+    rw_s = time.perf_counter() - t1
+    g.close()
+    shape = (len(kT_q), len(mb), len(mc))
+    return {"workload": TWO_SPECIES, "equilibration_sweeps": equil, "timed": timed,
+            "production": {"sweeps": sweeps, "run_s": run_s,
+                           "trial_moves_per_s": p.S * sweeps * p.moves_per_sweep / run_s,
+                           "observations": int(h["omega"].sum()),
+                           "pooled_bins_occupied": int(np.count_nonzero(h["hNE"])),
+                           "e_out": int(h["e_out"].sum()),
+                           "walkers_N_B_mean": float(cnt.mean()),
+                           "convergence_ks_halves": {"median": float(np.median(ks)), "max": float(np.max(ks)),
+                                                     "states_unchanged_at_1pct": int(np.sum(ks < crit))}},
+            "reweight_s": rw_s, "mbar_iterations": iters,
+            "phase_map": {"kT": kT_q.tolist(), "mu_B": mb.tolist(), "mu_C": mc.tolist(),
+                          "N_B_mean": nbm.reshape(shape).round(2).tolist(),
+                          "N_C_mean": ncm.reshape(shape).round(2).tolist(),
+                          "N_B_most_probable": np.argmax(pb, axis=1).reshape(shape).tolist(),
+                          "N_C_most_probable": np.argmax(pc, axis=1).reshape(shape).tolist()}}
+
+
 def paper_structure_spec(p):
     """Slabs of 0.12 A over the 48 A zone (Sec. III.A) and three adsorbate
     layers above the floor for g_xy, lateral bins of 0.1 A up to 4.9 A (the
@@ -840,6 +932,10 @@ def run_own(args):
     if args.production > 0 and rank == 0:
         production = production_arm(torch, stream, args.production)
 
+    two = None
+    if args.two_species and rank == 0:
+        two = two_species_arm(torch, stream, flush, args.two_species_steps, args.two_species_sweeps)
+
     line = None
     if rank == 0:
         cpu = None
@@ -881,6 +977,7 @@ def run_own(args):
             "cluster_in_gas": cluster,
             "paper_lj_cycle": paper,
             "production_phase_map": production,
+            "two_species": two,
         }
         print(json.dumps(line), flush=True)
     g.close()

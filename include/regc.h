@@ -557,16 +557,43 @@ REGC_API regc_status regc_structure_timing(regc_handle *h, double *ms_mbar, doub
  * S states (kT [S], mu [S], omega [S] observations), B bins (N_b [B], E_b [B],
  * H_b [B] > 0 counts).  Outputs f [S] (f_0 = 0) and D [B], the log denominators
  * D_b = ln sum_k omega_k exp(f_k - u_k(b)).  Runs on cuda_stream.
- * Device memory: besides O(S + B) buffers, when every omega_k > 0 and
- * 8 (S B + 2 B + 2 S) bytes are at most 2 GiB, the iterations use a kernel
- * matrix of S B doubles allocated on the stream for the duration of the call
- * (if that allocation fails they run without it; the result is the same
- * fixed point).  regc_reweight and regc_structure_reweight solve the same way. */
+ * Device memory: besides O(S + B) buffers, when every omega_k > 0 the
+ * iterations use the kept entries of the kernel matrix (those within e^-70
+ * of the largest of their bin, stored by bin and by state: 24 bytes each),
+ * allocated on the stream for the duration of the call when they fit in half
+ * the free device memory (otherwise they run without it; the result is the
+ * same fixed point).  regc_reweight, regc_reweight2 and
+ * regc_structure_reweight solve the same way; regc_mbar_last_info reports
+ * what the last solve did. */
 REGC_API regc_status regc_mbar_solve(int S, const double *kT, const double *mu, double lambda0,
                             const double *omega, int B, const int32_t *N_b,
                             const double *E_b, const double *H_b, double tol,
                             int max_iter, double *f, double *D, int *iters,
                             void *cuda_stream);
+
+/* What the calling thread's last MBAR solve (regc_mbar_solve, regc_reweight,
+ * regc_reweight2, regc_structure_reweight) did: path 1 when it iterated on the
+ * sparse kernel matrix, 0 on log-sum-exps only; its iterations (maps of the
+ * self-consistent equations), matrix builds, maps taken on log-sum-exps (no
+ * matrix, or a state without a kept entry far from the fixed point), the kept
+ * entries of the last build, its S and B, the device milliseconds of the
+ * matrix builds and of the maps on the matrix (CUDA events on the solve's
+ * stream), and the number of those maps.  All zero before the first solve.
+ * Errors: REGC_EINVAL (out NULL). */
+typedef struct {
+    int32_t path;
+    int32_t iterations;
+    int32_t builds;
+    int32_t lse_maps;
+    int64_t nnz;
+    int64_t S;
+    int64_t B;
+    double ms_build;
+    double ms_maps;
+    int32_t sparse_maps;
+    int32_t reserved;
+} regc_mbar_info;
+REGC_API regc_status regc_mbar_last_info(regc_mbar_info *out);
 
 /* Stand-alone MBAR query: with D [B] from regc_mbar_solve, reweight to Q
  * states; outputs N_mean [Q], pN [Q][nmax+1], f_q [Q] (any may be NULL). */

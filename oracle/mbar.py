@@ -90,9 +90,11 @@ def occupied_bins2(hNE, nmax, e_lo, e_bin):
 
 
 def solve(kT_s, mu_s, lambda0, omega_s, N_b, E_b, H_b, tol=1e-10, max_iter=200000, mu2_s=None, N2_b=None,
-          lambda0_2=1.0):
+          lambda0_2=1.0, f0=None):
     """Self-consistent MBAR free energies f_s (f_0 = 0); with mu2_s and N2_b
-    the reduced potential of two species (reduced_potential2).
+    the reduced potential of two species (reduced_potential2).  The plain
+    iteration starts from f0 (default 0); with max_iter=1 it applies the map
+    once, so that a solution found elsewhere can be checked as a fixed point.
 
     Returns (f [S], D [B], iterations, converged)."""
     if N2_b is None:
@@ -102,7 +104,7 @@ def solve(kT_s, mu_s, lambda0, omega_s, N_b, E_b, H_b, tol=1e-10, max_iter=20000
     omega = np.asarray(omega_s, np.float64)
     ln_omega = np.where(omega > 0, np.log(np.where(omega > 0, omega, 1.0)), -np.inf)
     ln_h = np.log(np.asarray(H_b, np.float64))
-    f = np.zeros(u.shape[0])
+    f = np.zeros(u.shape[0]) if f0 is None else np.asarray(f0, np.float64) - float(f0[0])
     it, converged = 0, False
     D = None
     while it < max_iter:

@@ -40,6 +40,12 @@ class Species2(C.Structure):
     _fields_ = [("type", C.c_int), ("K", C.c_int), ("mu", C.POINTER(C.c_double)), ("lambda0", C.c_double)]
 
 
+class MbarInfo(C.Structure):
+    _fields_ = [("path", C.c_int32), ("iterations", C.c_int32), ("builds", C.c_int32), ("lse_maps", C.c_int32),
+                ("nnz", C.c_int64), ("S", C.c_int64), ("B", C.c_int64), ("ms_build", C.c_double),
+                ("ms_maps", C.c_double), ("sparse_maps", C.c_int32), ("reserved", C.c_int32)]
+
+
 class GridSpec(C.Structure):
     _fields_ = [("L", C.c_int), ("M", C.c_int), ("kT", C.POINTER(C.c_double)),
                 ("mu", C.POINTER(C.c_double)), ("lambda0", C.c_double), ("nmax", C.c_int),
@@ -109,6 +115,7 @@ SIGNATURES = {
                                  _dp, C.POINTER(C.c_int)], C.c_int),
     "regc_reweight": ([_h, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _ip], C.c_int),
     "regc_reweight2": ([_h, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _ip], C.c_int),
+    "regc_mbar_last_info": ([C.POINTER(MbarInfo)], C.c_int),
     "regc_mbar_solve": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,
                          C.c_int, _dp, _dp, _ip, C.c_void_p], C.c_int),
     "regc_mbar_solve_static": ([C.c_int, _dp, _dp, C.c_double, _dp, C.c_int, _ip, _dp, _dp, C.c_double,

@@ -6,9 +6,10 @@
 //   f_s = -ln sum_b H_b exp(-u_s(b) - D_b)           (one block per state)
 // with f_0 = 0 after each iteration, accelerated by Anderson mixing on the
 // host (mbar_solve_dev).  Two forms of the map:
-// * on a kernel matrix K_sb (every state sampled, the matrix within its
-//   memory bound): each map is two FP64 matrix-vector products, the matrix
-//   rebuilt when the iterate has moved far from the point it was built at;
+// * on the kept entries of a kernel matrix K_sb (every state sampled, the
+//   entries within their memory bound): each map is two FP64 sparse
+//   matrix-vector products, the matrix rebuilt when the iterate has moved
+//   far from the point it was built at;
 // * log-sum-exp in FP64 over the terms within 50 of the largest (the others
 //   weigh less than the FP64 rounding of the sum), found by a binary32
 //   screening pass, so that with well separated states a bin costs a few FP64
@@ -452,129 +453,462 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
     if (b < B) lnH[b] = log(H[b]);
 }
 
-// ---- iterations on the kernel matrix
+// ---- iterations on a sparse kernel matrix
 // With every state sampled, the map can be iterated in linear space: for a
 // reference point f_ref (the iterate at the last build),
 //   K_sb = exp(t_sb - M_b),  t_sb = ln Omega_s + f_ref,s - u_s(b),  M_b = max_s t_sb,
 // so that with w_s = exp(f_s - f_ref,s)
 //   D_b = M_b + ln d_b,  d_b = sum_s K_sb w_s,
-//   f_new,s = ln Omega_s + f_ref,s - ln sum_b (H_b / d_b) K_sb.
-// Each map is then two FP64 matrix-vector products over a matrix built once
-// per reference point (one exponential per entry), instead of S B
-// exponentials.  The reference moves with the iterate: once some
-// |f_s - f_ref,s| exceeds kRebuild the matrix is rebuilt, so w stays within
-// e^(+-kRebuild) and d_b >= e^-kRebuild (the largest entry of a column is 1),
-// far from the FP64 range limits (e^-708 .. e^709); a sum of positive terms
-// keeps its relative accuracy whatever their spread.  Entries below e^-708
-// (subnormal or zero) weigh less than e^(-708 + 2 kRebuild) = e^-108 against
-// the sums they enter.  The build (one FP64 exponential per entry) costs
-// about ten maps, so the bound is set wide.
-constexpr double kRebuild = 300.0;
-constexpr size_t kMatBytes = size_t(2) << 30;
+//   f_new,s = ln Omega_s + f_ref,s - ln sum_b (H_b / d_b) K_sb,
+// two FP64 sparse matrix-vector products per map and no exponentials.  Of
+// the S B entries only those whose binary32 screen value (t_sb in binary32)
+// is within kKeep + kMargin of the largest of their bin are kept: with
+// hundreds of states most of a bin's terms lie far below its largest.  The
+// matrix holds to e^-50 while the spread of the drift, max_s (f_s - f_ref,s)
+// - min_s (f_s - f_ref,s), is at most kSpreadAcc: a dropped entry then weighs
+// at most e^(-kKeep + kSpreadAcc) = e^-50 of the largest term of its bin (a
+// uniform shift of f changes nothing), so the (at most 65536) dropped terms
+// of d_b stay below 1e-17 of it, and those of a state's sum below 1e-17 of
+// it too while its observations Omega_s are not below N_obs / S e^-13.  Far
+// from the fixed point the iteration runs on the matrix until the spread
+// exceeds kSpreadMax (its map then errs by at most e^-10 relative, which
+// changes the path, not the end point); convergence is accepted only on a
+// map evaluated within kSpreadAcc, else the matrix is rebuilt there.
+// Each bin keeps its largest entry (K = 1), so d_b > 0; a state whose sum has
+// no kept entry (possible far from the fixed point) makes that map fall back
+// to the log-sum-exp form.
+// The entries are held twice: by bin (CSR, states ascending) for d_b and by
+// state (in kFSplit bin quarters, bins ascending) for f_new; both are summed
+// in a fixed order, so the iteration is deterministic.
+constexpr double kKeep = 70.0;
+constexpr double kSpreadAcc = 20.0;
+constexpr double kSpreadMax = 60.0;
 
-struct MatDev {
-    double* K;      // [S][B]
-    double* M;      // [B]
-    double* V;      // [B] H_b / d_b of the last map
-    double* fref;   // [S]
-    double* w;      // [S] exp(f_s - f_ref,s) of the current iterate (from the host)
+struct SpDev {
+    long long* rp;   // [B + 1] entries of bin b: rp[b] .. rp[b + 1] - 1
+    int* ci;         // [nnz] their states, ascending within a bin
+    double* cv;      // [nnz] K_sb
+    long long* cp;   // [kFSplit S + 1] entries of state s in bin quarter r: cp[kFSplit s + r] ..
+    int* bi;         // [nnz] their bins, ascending within a segment
+    double* bv;      // [nnz] K_sb
+    float* thr;      // [B] the bin's binary32 screening threshold
+    double* M;       // [B] M_b
+    double* H;       // [B] H_b
+    double* V;       // [B] H_b / d_b of the last map
+    double* fref;    // [S]
+    double* w;       // [S] exp(f_s - f_ref,s) of the current iterate (from the host)
+    int* flag;       // [2] entries of the state segments missing from their bin's row; empty state sums
 };
 
-// One thread per bin: t_sb over the states (tiled through shared memory),
-// M_b, then the column of K.  Block 0 records f_ref = f.
+// The binary32 screen value of state (g, a, c, c2) at bin (en, n2).  The row
+// and the state passes evaluate this same expression on the same binary32
+// operands, so they keep the same entries.
 template <bool TWO>
-__global__ void __launch_bounds__(256) mat_build_kernel(const __grid_constant__ MbarDev m, MatDev k) {
-    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile], sc2[TWO ? kDTile : 1];
+__device__ __forceinline__ float screen32(float g, float a, float c, float c2, float2 en, float n2) {
+    return g - u32_of<TWO>(a, c, c2, en.x, en.y, n2);
+}
+
+template <bool TWO>
+__device__ __forceinline__ void state32(const MbarDev& m, const double* fref, int k, float& g, float& a, float& c,
+                                        float& c2) {
+    g = (float)(m.lnom[k] + fref[k]);
+    a = (float)m.a[k];
+    c = (float)m.c[k];
+    c2 = TWO ? (float)m.c2[k] : 0.f;
+}
+
+// One thread per bin: the largest screen value over the states (tiled
+// through shared memory), the threshold, and the number of kept entries
+// (-> rp[b + 1], scanned afterwards).
+template <bool TWO>
+__global__ void __launch_bounds__(256) sp_screen_kernel(const __grid_constant__ MbarDev m, SpDev p) {
+    __shared__ float fa[kDTile], fc[kDTile], fg[kDTile], fc2[TWO ? kDTile : 1];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = b < m.B;
-    if (blockIdx.x == 0)
-        for (int q = threadIdx.x; q < m.S; q += blockDim.x) k.fref[q] = m.f[q];
+    const float2 en = act ? m.EN32[b] : make_float2(0.f, 0.f);
+    const float n2f = (TWO && act) ? m.N2f[b] : 0.f;
+    const bool one_tile = m.S <= kDTile;
+    float mx = -INFINITY, th = -INFINITY;
+    long long cnt = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) th = mx - (float)kKeep - kMargin;
+        for (int k0 = 0; k0 < m.S; k0 += kDTile) {
+            const int nk = min(kDTile, m.S - k0);
+            if (pass == 0 || !one_tile) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < nk; q += blockDim.x) {
+                    float c2;
+                    state32<TWO>(m, p.fref, k0 + q, fg[q], fa[q], fc[q], c2);
+                    if (TWO) fc2[q] = c2;
+                }
+                __syncthreads();
+            }
+            if (!act) continue;
+            if (pass == 0) {
+                for (int q = 0; q < nk; ++q)
+                    mx = fmaxf(mx, screen32<TWO>(fg[q], fa[q], fc[q], fc2[TWO ? q : 0], en, n2f));
+            } else {
+                for (int q = 0; q < nk; ++q)
+                    cnt += screen32<TWO>(fg[q], fa[q], fc[q], fc2[TWO ? q : 0], en, n2f) > th;
+            }
+        }
+    }
+    if (act) {
+        p.thr[b] = th;
+        p.rp[b + 1] = cnt;
+    }
+}
+
+// One thread per bin: M_b over the kept states in FP64, then the row
+// (states ascending, K_sb = exp(t_sb - M_b)).
+template <bool TWO>
+__global__ void __launch_bounds__(256) sp_rows_kernel(const __grid_constant__ MbarDev m, SpDev p) {
+    __shared__ double sa[kDTile], sc[kDTile], sg[kDTile], sc2[TWO ? kDTile : 1];
+    __shared__ float fa[kDTile], fc[kDTile], fg[kDTile], fc2[TWO ? kDTile : 1];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = b < m.B;
     const double E = act ? m.E_b[b] : 0.0;
     const double N = act ? (double)m.N_b[b] : 0.0;
     const double N2 = (TWO && act) ? (double)m.N2_b[b] : 0.0;
+    const float2 en = act ? m.EN32[b] : make_float2(0.f, 0.f);
+    const float n2f = (TWO && act) ? m.N2f[b] : 0.f;
+    const float th = act ? p.thr[b] : 0.f;
+    const bool one_tile = m.S <= kDTile;
     double M = -INFINITY;
+    long long e = act ? p.rp[b] : 0;
     for (int pass = 0; pass < 2; ++pass) {
         for (int k0 = 0; k0 < m.S; k0 += kDTile) {
             const int nk = min(kDTile, m.S - k0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < nk; q += blockDim.x) {
-                sa[q] = m.a[k0 + q];
-                sc[q] = m.c[k0 + q];
-                sg[q] = m.lnom[k0 + q] + m.f[k0 + q];
-                if (TWO) sc2[q] = m.c2[k0 + q];
+            if (pass == 0 || !one_tile) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < nk; q += blockDim.x) {
+                    float c2;
+                    state32<TWO>(m, p.fref, k0 + q, fg[q], fa[q], fc[q], c2);
+                    sa[q] = m.a[k0 + q];
+                    sc[q] = m.c[k0 + q];
+                    sg[q] = m.lnom[k0 + q] + p.fref[k0 + q];
+                    if (TWO) {
+                        fc2[q] = c2;
+                        sc2[q] = m.c2[k0 + q];
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
             if (!act) continue;
-            if (pass == 0) {
-                for (int q = 0; q < nk; ++q) M = fmax(M, sg[q] - u_of<TWO>(sa[q], sc[q], sc2[TWO ? q : 0], E, N, N2));
-            } else {
-                for (int q = 0; q < nk; ++q)
-                    k.K[size_t(k0 + q) * m.B + b] = exp(sg[q] - u_of<TWO>(sa[q], sc[q], sc2[TWO ? q : 0], E, N, N2) - M);
+            for (int q = 0; q < nk; ++q) {
+                if (!(screen32<TWO>(fg[q], fa[q], fc[q], fc2[TWO ? q : 0], en, n2f) > th)) continue;
+                const double t = sg[q] - u_of<TWO>(sa[q], sc[q], sc2[TWO ? q : 0], E, N, N2);
+                if (pass == 0) {
+                    M = fmax(M, t);
+                } else {
+                    p.ci[e] = k0 + q;
+                    p.cv[e] = exp(t - M);
+                    ++e;
+                }
             }
         }
     }
-    if (act) k.M[b] = M;
+    if (act) {
+        p.M[b] = M;
+        p.H[b] = exp(m.lnH[b]);
+    }
 }
 
-// d_b = sum_s K_sb w_s, V_b = H_b / d_b.  A block takes 32 bins; its
-// kDGroups warps take every kDGroups-th state (two independent FMA chains
-// each), and the partial sums of a bin are added in a fixed order.  Rows of
-// K are read 32 consecutive bins (256 bytes) at a time.
-constexpr int kDGroups = 4;
-__global__ void __launch_bounds__(32 * kDGroups) mat_d_kernel(const __grid_constant__ MbarDev m, MatDev k) {
-    __shared__ double sw[kDTile];
-    __shared__ double part[kDGroups][32];
-    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    const int b = blockIdx.x * 32 + lane;
-    const bool act = b < m.B;
-    double d0 = 0.0, d1 = 0.0;
-    for (int k0 = 0; k0 < m.S; k0 += kDTile) {
-        const int nk = min(kDTile, m.S - k0);
+// The entries by state: kFSplit CTAs per state, CTA r over bin quarter r.
+// COUNT: the number of kept entries -> cp[kFSplit s + r + 1] (scanned
+// afterwards).  Otherwise the segment is written in bin order (a block-wide
+// ordered compaction), each value taken from the bin's row (binary search
+// over its ascending states).
+template <bool TWO, bool COUNT>
+__global__ void __launch_bounds__(kFThreads) sp_cols_kernel(const __grid_constant__ MbarDev m, SpDev p) {
+    constexpr int kWarps = kFThreads / 32;
+    __shared__ int wcnt[kWarps];
+    const int s = blockIdx.x / kFSplit, r = blockIdx.x % kFSplit;
+    const int per = (m.B + kFSplit - 1) / kFSplit;
+    const int b0 = r * per, b1 = min(m.B, b0 + per);
+    float g, a, c, c2;
+    state32<TWO>(m, p.fref, s, g, a, c, c2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (COUNT) {
+        long long cnt = 0;
+        for (int b = b0 + threadIdx.x; b < b1; b += kFThreads)
+            cnt += screen32<TWO>(g, a, c, c2, m.EN32[b], TWO ? m.N2f[b] : 0.f) > p.thr[b];
+        const double tot = block_sum((double)cnt);   // exact: counts below 2^53
+        if (threadIdx.x == 0) p.cp[blockIdx.x + 1] = (long long)tot;
+        return;
+    }
+    long long base = p.cp[blockIdx.x];
+    for (int bb = b0; bb < b1; bb += kFThreads) {
+        const int b = bb + threadIdx.x;
+        const bool keep = b < b1 && screen32<TWO>(g, a, c, c2, m.EN32[b], TWO ? m.N2f[b] : 0.f) > p.thr[b];
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
-        for (int q = threadIdx.x; q < nk; q += blockDim.x) sw[q] = k.w[k0 + q];
-        __syncthreads();
-        if (!act) continue;
-        const double* col = k.K + size_t(k0) * m.B + b;
-        int q = grp;
-        for (; q + kDGroups < nk; q += 2 * kDGroups) {
-            d0 = fma(col[size_t(q) * m.B], sw[q], d0);
-            d1 = fma(col[size_t(q + kDGroups) * m.B], sw[q + kDGroups], d1);
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            off += w < warp ? wcnt[w] : 0;
+            tot += wcnt[w];
         }
-        if (q < nk) d0 = fma(col[size_t(q) * m.B], sw[q], d0);
-    }
-    part[grp][lane] = d0 + d1;
-    __syncthreads();
-    if (grp == 0 && act) {
-        const double d = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
-        k.V[b] = exp(m.lnH[b]) / d;
+        if (keep) {
+            const long long e = base + off + __popc(bal & ((1u << lane) - 1u));
+            long long lo = p.rp[b], hi = p.rp[b + 1];
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (p.ci[mid] < s) lo = mid + 1;
+                else hi = mid;
+            }
+            p.bi[e] = b;
+            if (lo < p.rp[b + 1] && p.ci[lo] == s) {
+                p.bv[e] = p.cv[lo];
+            } else {
+                p.bv[e] = 0.0;
+                atomicAdd(&p.flag[0], 1);
+            }
+        }
+        base += tot;
+        __syncthreads();   // wcnt is rewritten by the next round
     }
 }
 
-// f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb: a cluster of kFSplit
-// CTAs per state, each over a contiguous quarter of the row; the quarters'
-// sums meet in CTA rank 0 through distributed shared memory, added in rank
-// order (deterministic).
+// d_b = sum_s K_sb w_s over the bin's row (a warp per bin, a fixed
+// reduction tree), then V_b = H_b / d_b; FINAL: D_b = M_b + ln d_b instead.
+template <bool FINAL>
+__global__ void __launch_bounds__(256) sp_d_kernel(const __grid_constant__ MbarDev m, SpDev p) {
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= m.B) return;   // the whole warp
+    const long long e1 = p.rp[b + 1];
+    double d = 0.0;
+    for (long long e = p.rp[b] + lane; e < e1; e += 32) d = fma(p.cv[e], __ldg(p.w + p.ci[e]), d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) {
+        if (FINAL) {
+            const double D = p.M[b] + log(d);
+            m.D[b] = D;
+            m.DH32[b] = (float)(D - m.lnH[b]);
+        } else {
+            p.V[b] = p.H[b] / d;
+        }
+    }
+}
+
+// f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb over the state's
+// segments: CTA r of the cluster over quarter r, the quarters' sums added in
+// rank order by CTA 0 (deterministic).  An empty sum raises flag[1].
 __global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
-    mat_f_kernel(const __grid_constant__ MbarDev m, MatDev k) {
+    sp_f_kernel(const __grid_constant__ MbarDev m, SpDev p) {
     __shared__ double part;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int s = blockIdx.x / kFSplit;
-    const int per = (m.B + kFSplit - 1) / kFSplit;
-    const int b0 = rank * per, b1 = min(m.B, b0 + per);
-    const double* row = k.K + size_t(s) * m.B;
+    const long long e1 = p.cp[blockIdx.x + 1];
     double acc = 0.0;
-    for (int b = b0 + threadIdx.x; b < b1; b += kFThreads) acc = fma(k.V[b], row[b], acc);
+    for (long long e = p.cp[blockIdx.x] + threadIdx.x; e < e1; e += kFThreads)
+        acc = fma(p.bv[e], p.V[p.bi[e]], acc);
     acc = block_sum(acc);
     if (threadIdx.x == 0) part = acc;
     cluster.sync();
     if (rank == 0 && threadIdx.x == 0) {
         double t = 0.0;
-        for (int r = 0; r < kFSplit; ++r) t += *cluster.map_shared_rank(&part, r);
-        m.f_new[s] = m.lnom[s] + k.fref[s] - log(t);
+        for (int q = 0; q < kFSplit; ++q) t += *cluster.map_shared_rank(&part, q);
+        if (t > 0.0) {
+            m.f_new[s] = m.lnom[s] + p.fref[s] - log(t);
+        } else {
+            m.f_new[s] = 0.0;
+            atomicAdd(&p.flag[1], 1);
+        }
     }
     cluster.sync();   // the partial sums stay readable until rank 0 has added them
 }
+
+// ---- inclusive scan of long long x[n] in place: chunk totals, one block
+// over the totals (exclusive), then every chunk with its offset.
+constexpr int kScanChunk = 1024;   // 256 threads x 4
+
+__device__ __forceinline__ long long block_scan_incl(long long v, long long* wsum, long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long y = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        wsum[lane] = y;
+    }
+    __syncthreads();
+    const long long r = v + (warp > 0 ? wsum[warp - 1] : 0);
+    if (total) *total = wsum[nw - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) lchunk_sum_kernel(const long long* x, long long n, long long* tot) {
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    long long v = 0;
+    for (int k = 0; k < 4; ++k) {
+        const long long i = base + threadIdx.x * 4 + k;
+        if (i < n) v += x[i];
+    }
+    const double t = block_sum((double)v);   // exact: totals below 2^53
+    if (threadIdx.x == 0) tot[blockIdx.x] = (long long)t;
+}
+
+__global__ void __launch_bounds__(1024) ltot_scan_kernel(long long* tot, long long nblk) {
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b0 = 0; b0 < nblk; b0 += blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        const long long v = i < nblk ? tot[i] : 0;
+        long long all;
+        const long long incl = block_scan_incl(v, wsum, &all);
+        if (i < nblk) tot[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += all;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) lchunk_scan_kernel(long long* x, long long n, const long long* tot) {
+    __shared__ long long wsum[32];
+    const long long i0 = (long long)blockIdx.x * kScanChunk + threadIdx.x * 4;
+    long long v[4], run = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = i0 + k < n ? x[i0 + k] : 0;
+        run += v[k];
+        v[k] = run;
+    }
+    const long long excl = block_scan_incl(run, wsum, nullptr) - run + tot[blockIdx.x];
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < n) x[i0 + k] = v[k] + excl;
+}
+
+}  // namespace
+
+namespace {
+
+double spread_of(const std::vector<double>& x, const std::vector<double>& ref) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (size_t k = 0; k < x.size(); ++k) {
+        lo = fmin(lo, x[k] - ref[k]);
+        hi = fmax(hi, x[k] - ref[k]);
+    }
+    return x.empty() ? 0.0 : hi - lo;
+}
+
+cudaError_t lscan(long long* x, long long n, long long* tmp, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long nblk = (n + kScanChunk - 1) / kScanChunk;
+    lchunk_sum_kernel<<<(unsigned)nblk, 256, 0, s>>>(x, n, tmp);
+    ltot_scan_kernel<<<1, 1024, 0, s>>>(tmp, nblk);
+    lchunk_scan_kernel<<<(unsigned)nblk, 256, 0, s>>>(x, n, tmp);
+    return cudaGetLastError();
+}
+
+// The sparse kernel matrix on the device (allocated on the stream, freed
+// with it) and its build at the iterate held in m.f.
+struct SparseMat {
+    cudaStream_t s = nullptr;
+    void* fixed = nullptr;     // the bin- and state-sized arrays
+    void* entries = nullptr;   // cap entries: cv, bv (double), ci, bi (int)
+    long long cap = 0, nnz = 0;
+    long long* tmp = nullptr;  // scan scratch
+    SpDev p{};
+
+    ~SparseMat() {
+        if (entries) cudaFreeAsync(entries, s);
+        if (fixed) cudaFreeAsync(fixed, s);
+    }
+
+    cudaError_t init(const MbarDev& m) {
+        const size_t B = size_t(m.B), S = size_t(m.S), SF = size_t(kFSplit) * S;
+        const size_t nt = std::max((B + kScanChunk - 1) / kScanChunk, (SF + kScanChunk - 1) / kScanChunk) + 1;
+        const size_t n8 = (B + 1) + (SF + 1) + 3 * B + 2 * S + nt;
+        cudaError_t e = cudaMallocAsync(&fixed, n8 * 8 + B * 4 + 16, s);
+        if (e != cudaSuccess) {
+            fixed = nullptr;
+            return e;
+        }
+        long long* q = static_cast<long long*>(fixed);
+        p.rp = q;
+        p.cp = p.rp + (B + 1);
+        double* d = reinterpret_cast<double*>(p.cp + (SF + 1));
+        p.M = d;
+        p.H = d + B;
+        p.V = d + 2 * B;
+        p.fref = d + 3 * B;
+        p.w = p.fref + S;
+        tmp = reinterpret_cast<long long*>(p.w + S);
+        p.thr = reinterpret_cast<float*>(tmp + nt);
+        p.flag = reinterpret_cast<int*>(p.thr + B);
+        e = cudaMemsetAsync(p.rp, 0, sizeof(long long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.cp, 0, sizeof(long long), s);
+        return e;
+    }
+
+    // *ok is false when the entries do not fit (half the free device memory)
+    // or the two orders disagree; the caller then iterates on log-sum-exps.
+    template <bool TWO>
+    cudaError_t build(const MbarDev& m, bool* ok) {
+        *ok = false;
+        const int S = m.S, B = m.B;
+        cudaError_t e = cudaMemcpyAsync(p.fref, m.f, size_t(S) * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        sp_screen_kernel<TWO><<<(B + 255) / 256, 256, 0, s>>>(m, p);
+        e = lscan(p.rp + 1, B, tmp, s);
+        long long n_h = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&n_h, p.rp + B, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (n_h > cap) {
+            if (entries) cudaFreeAsync(entries, s);
+            entries = nullptr;
+            cap = 0;
+            size_t fr = 0, tot = 0;
+            e = cudaMemGetInfo(&fr, &tot);
+            if (e != cudaSuccess) return e;
+            const size_t need = size_t(n_h) * 24;
+            if (need > fr / 2) return cudaSuccess;
+            if (cudaMallocAsync(&entries, need, s) != cudaSuccess) {
+                entries = nullptr;
+                (void)cudaGetLastError();   // out of memory is not sticky
+                return cudaSuccess;
+            }
+            cap = n_h;
+            p.cv = static_cast<double*>(entries);
+            p.bv = p.cv + cap;
+            p.ci = reinterpret_cast<int*>(p.bv + cap);
+            p.bi = p.ci + cap;
+        }
+        nnz = n_h;
+        sp_rows_kernel<TWO><<<(B + 255) / 256, 256, 0, s>>>(m, p);
+        sp_cols_kernel<TWO, true><<<S * kFSplit, kFThreads, 0, s>>>(m, p);
+        e = lscan(p.cp + 1, (long long)S * kFSplit, tmp, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.flag, 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        sp_cols_kernel<TWO, false><<<S * kFSplit, kFThreads, 0, s>>>(m, p);
+        int flag_h = 0;
+        long long n_cols = 0;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag_h, p.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&n_cols, p.cp + size_t(S) * kFSplit, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        *ok = flag_h == 0 && n_cols == nnz;
+        return cudaSuccess;
+    }
+};
 
 }  // namespace
 
@@ -586,10 +920,43 @@ __global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
 // is the one of the plain iteration (x = G(x)); only the path to it is
 // shorter.  An iterate whose residual grows past 100 times the best one so far
 // restarts the history from the best image.  Converged when max |r| < tol.
+namespace {
+thread_local MbarInfo g_last_info{};
+}
+
+MbarInfo mbar_last_info() { return g_last_info; }
+
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s,
                            bool allow_matrix) {
     constexpr int kDepth = 16;
     const int S = m.S;
+    MbarInfo& info = g_last_info;
+    info = MbarInfo{0, 0, 0, 0, 0, S, m.B, 0.0, 0.0, 0};
+    // device time of the builds and of the maps on the matrix
+    struct Timer {
+        cudaEvent_t a = nullptr, b = nullptr;
+        Timer() {
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+                (void)cudaGetLastError();
+                a = b = nullptr;
+            }
+        }
+        ~Timer() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+        void start(cudaStream_t s) {
+            if (a) cudaEventRecord(a, s);
+        }
+        void stop(cudaStream_t s) {
+            if (b) cudaEventRecord(b, s);
+        }
+        // once the stream has been synchronised past the stop event
+        double ms() const {
+            float t = 0.f;
+            return (a && b && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ? (double)t : 0.0;
+        }
+    } tb, tm;
     cudaError_t err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(m.f, 0, size_t(S) * sizeof(double), s);
@@ -598,11 +965,11 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     const int dgrid128 = (m.B + 127) / 128;   // a bin per thread, small blocks to spread over every SM
     en32_kernel<<<dgrid, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.EN32, m.N2_b, m.N2f);
     const bool two = m.N2_b != nullptr;
-    // the kernel matrix, when every state is sampled and it fits
-    MatDev mat{};
-    void* mat_block = nullptr;
-    const size_t mat_doubles = size_t(S) * m.B + 2 * size_t(m.B) + 2 * size_t(S);
-    if (allow_matrix && mat_doubles * sizeof(double) <= kMatBytes) {
+    // the sparse kernel matrix, when every state is sampled and it fits
+    SparseMat sp;
+    sp.s = s;
+    bool use_sp = false;
+    if (allow_matrix) {
         std::vector<double> lnom_h(S);
         err = cudaMemcpyAsync(lnom_h.data(), m.lnom, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
@@ -610,23 +977,10 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
         bool all_sampled = true;
         for (int k = 0; k < S; ++k) all_sampled = all_sampled && std::isfinite(lnom_h[k]);
         if (all_sampled) {
-            if (cudaMallocAsync(&mat_block, mat_doubles * sizeof(double), s) == cudaSuccess) {
-                double* p = static_cast<double*>(mat_block);
-                double* q = p + size_t(S) * m.B;
-                mat = MatDev{p, q, q + m.B, q + 2 * size_t(m.B), q + 2 * size_t(m.B) + S};
-            } else {
-                mat_block = nullptr;
-                (void)cudaGetLastError();   // out of memory is not sticky: iterate on log-sum-exps
-            }
+            use_sp = sp.init(m) == cudaSuccess;
+            if (!use_sp) (void)cudaGetLastError();   // out of memory is not sticky: iterate on log-sum-exps
         }
     }
-    struct FreeOnExit {
-        void* p;
-        cudaStream_t s;
-        ~FreeOnExit() {
-            if (p) cudaFreeAsync(p, s);
-        }
-    } free_mat{mat_block, s};
     std::vector<double> fref_h(S, 0.0), w_h(S);
     bool build = true;
     std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
@@ -639,21 +993,55 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
             if (err != cudaSuccess) return err;
         }
-        if (mat.K) {
-            double drift = 0.0;
-            for (int k = 0; k < S; ++k) drift = fmax(drift, fabs(x[k] - fref_h[k]));
-            if (build || !(drift <= kRebuild)) {
-                if (two) mat_build_kernel<true><<<dgrid, 256, 0, s>>>(m, mat);
-                else mat_build_kernel<false><<<dgrid, 256, 0, s>>>(m, mat);
+        double spread = 0.0;
+        if (use_sp) {
+            spread = spread_of(x, fref_h);
+            if (build || !(spread <= kSpreadMax)) {
+                bool ok = false;
+                tb.start(s);
+                err = two ? sp.build<true>(m, &ok) : sp.build<false>(m, &ok);
+                if (err != cudaSuccess) return err;
+                tb.stop(s);
+                err = cudaStreamSynchronize(s);
+                if (err != cudaSuccess) return err;
+                info.ms_build += tb.ms();
+                use_sp = ok;   // too large or inconsistent: log-sum-exps from here on
+                info.path = ok ? 1 : 0;
+                info.builds += ok ? 1 : 0;
+                info.nnz = ok ? sp.nnz : 0;
                 fref_h = x;
+                spread = 0.0;
                 build = false;
+                // the map has changed: the Anderson history starts again
+                dR.clear();
+                dG.clear();
+                r_prev.clear();
+                best = INFINITY;
             }
+        }
+        bool mapped = false;
+        if (use_sp) {
             for (int k = 0; k < S; ++k) w_h[k] = exp(x[k] - fref_h[k]);
-            err = cudaMemcpyAsync(mat.w, w_h.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+            int empty = 0;
+            err = cudaMemcpyAsync(sp.p.w, w_h.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (err == cudaSuccess) err = cudaMemsetAsync(sp.p.flag + 1, 0, sizeof(int), s);
             if (err != cudaSuccess) return err;
-            mat_d_kernel<<<(m.B + 31) / 32, 32 * kDGroups, 0, s>>>(m, mat);
-            mat_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, mat);
-        } else {
+            tm.start(s);
+            sp_d_kernel<false><<<(m.B + 7) / 8, 256, 0, s>>>(m, sp.p);
+            sp_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, sp.p);
+            tm.stop(s);
+            err = cudaGetLastError();
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess) err = cudaMemcpyAsync(&empty, sp.p.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+            if (err != cudaSuccess) return err;
+            info.ms_maps += tm.ms();
+            ++info.sparse_maps;
+            mapped = empty == 0;   // else a state had no kept entry: this map on log-sum-exps
+        }
+        if (!mapped) {
+            ++info.lse_maps;
             if (two) {
                 d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);
                 f_kernel<true><<<S * kFSplit, kFThreads, 0, s>>>(m);
@@ -661,12 +1049,12 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
                 d_kernel<false><<<dgrid128, 128, 0, s>>>(m, 1);
                 f_kernel<false><<<S * kFSplit, kFThreads, 0, s>>>(m);
             }
+            err = cudaGetLastError();
+            if (err != cudaSuccess) return err;
+            err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+            if (err != cudaSuccess) return err;
         }
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-        err = cudaMemcpyAsync(g.data(), m.f_new, size_t(S) * sizeof(double), cudaMemcpyDeviceToHost, s);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-        if (err != cudaSuccess) return err;
         ++it;
         const double g0 = g[0];
         double delta = 0.0;
@@ -678,6 +1066,12 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
         if (!(delta == delta)) return cudaErrorInvalidValue;   // NaN: no fixed point to approach
         if (delta < tol) {
             x = g;
+            // converged on a matrix that no longer holds to e^-50 at x: rebuild
+            // there and go on
+            if (mapped && !(spread <= kSpreadAcc)) {
+                build = true;
+                continue;
+            }
             break;
         }
         if (delta < best) {
@@ -753,14 +1147,24 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     }
     err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return err;
-    if (two) d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);  // D_b of the final f
-    else d_kernel<false><<<dgrid128, 128, 0, s>>>(m, 1);
+    // D_b of the final f: on the matrix while it holds for f, else log-sum-exps
+    if (use_sp && spread_of(x, fref_h) <= kSpreadAcc) {
+        for (int k = 0; k < S; ++k) w_h[k] = exp(x[k] - fref_h[k]);
+        err = cudaMemcpyAsync(sp.p.w, w_h.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (err != cudaSuccess) return err;
+        sp_d_kernel<true><<<(m.B + 7) / 8, 256, 0, s>>>(m, sp.p);
+    } else if (two) {
+        d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);
+    } else {
+        d_kernel<false><<<dgrid128, 128, 0, s>>>(m, 1);
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     // the host vectors go out of scope: wait for the copy that reads x
     err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return err;
     if (iters_out) *iters_out = it;
+    info.iterations = it;
     return cudaSuccess;
 }
 

@@ -30,13 +30,28 @@ struct MbarDev {
     float* N2f;            // [B] N2_b in binary32, filled by the solve
 };
 
+// What the last mbar_solve_dev of the calling thread did: path 1 when it
+// iterated on the sparse kernel matrix (0: log-sum-exps only), its
+// iterations, matrix builds, maps taken on log-sum-exps, the kept entries of
+// the last build, S, B, the device time of the builds and of the maps on the
+// matrix, and the number of those maps.
+struct MbarInfo {
+    int path, iterations, builds, lse_maps;
+    long long nnz;
+    long long S, B;
+    double ms_build, ms_maps;   // device time of the matrix builds and of the maps on it
+    int sparse_maps;            // maps on the matrix
+};
+MbarInfo mbar_last_info();
+
 // Solve the self-consistent equations from f = 0 (the plain fixed-point map
 // with Anderson acceleration) until max |G(f) - f| < tol or max_iter maps.
 // Synchronises the stream after every map.
-// With allow_matrix (and every state sampled, and S B doubles within 2 GiB)
-// the iterations run on the kernel matrix K_sb = exp(-u_s(b) + ln Omega_s +
-// f_ref,s - max_k(...)), allocated on the stream for the duration of the call;
-// otherwise (or when the allocation fails) on log-sum-exps of the energies.
+// With allow_matrix (and every state sampled) the iterations run on the
+// kept entries of the kernel matrix K_sb = exp(-u_s(b) + ln Omega_s + f_ref,s
+// - max_k(...)) (those within e^-70 of their bin's largest), allocated on the
+// stream for the duration of the call when they fit in half the free device
+// memory; otherwise on log-sum-exps of the energies.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out,
                            cudaStream_t s, bool allow_matrix = true);
 

@@ -1638,6 +1638,14 @@ regc_status regc_reweight2(regc_handle* h, int nq, const double* kT_q, const dou
     return status_of(cudaStreamSynchronize(s));
 }
 
+regc_status regc_mbar_last_info(regc_mbar_info* out) {
+    if (!out) return REGC_EINVAL;
+    const MbarInfo i = mbar_last_info();
+    *out = regc_mbar_info{i.path, i.iterations, i.builds, i.lse_maps, i.nnz, i.S, i.B,
+                          i.ms_build, i.ms_maps, i.sparse_maps, 0};
+    return REGC_OK;
+}
+
 regc_status regc_mbar_solve(int S, const double* kT, const double* mu, double lambda0, const double* omega, int B,
                             const int32_t* N_b, const double* E_b, const double* H_b, double tol, int max_iter,
                             double* f, double* D, int* iters, void* cuda_stream) {

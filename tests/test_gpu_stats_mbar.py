@@ -20,7 +20,8 @@ import pytest
 import workloads as W
 from oracle import mbar as OM
 from oracle import oracle as O
-from paper_1908_11118_gb300 import Regc, mbar_query, mbar_solve
+from paper_1908_11118_gb300 import Regc, mbar_last_info, mbar_query, mbar_solve
+from paper_1908_11118_gb300.regc import mbar_solve_static
 from paper_1908_11118_gb300 import build as B
 
 pytestmark = pytest.mark.gpu
@@ -111,12 +112,12 @@ def test_statistical_parity_with_oracle_fcc100():
     assert g.check_energy() == 0.0
 
 
-def synthetic_bins(seed=0, S_side=5, nmax=30):
+def synthetic_bins(seed=0, S_side=5, nmax=30, kT_range=(0.7, 1.6), mu_range=(-5.0, -2.0), per_n=40):
     """Seeded pooled (N, E) histogram drawn from a model density of states."""
     rng = np.random.default_rng(seed)
-    kT = np.repeat(np.geomspace(0.7, 1.6, S_side), S_side)
-    mu = np.tile(np.linspace(-5.0, -2.0, S_side), S_side)
-    N = np.repeat(np.arange(nmax + 1), 40)
+    kT = np.repeat(np.geomspace(*kT_range, S_side), S_side)
+    mu = np.tile(np.linspace(*mu_range, S_side), S_side)
+    N = np.repeat(np.arange(nmax + 1), per_n)
     E = -2.5 * N + rng.normal(size=N.size) * (1.0 + 0.3 * np.sqrt(N))
     E = np.round(E * 20.0) / 20.0
     lnw_s = (-(E[None, :] - mu[:, None] * N[None, :]) / kT[:, None]
@@ -146,6 +147,65 @@ def test_mbar_solve_and_query_match_oracle():
     np.testing.assert_allclose(n_g, n_o, rtol=1e-9)
     np.testing.assert_allclose(p_g, p_o, atol=1e-10)
     np.testing.assert_allclose(fq_g, fq_o, atol=1e-9)
+
+
+def test_sparse_kernel_matrix_solves_the_oracle_equations():
+    """64 well separated states over N <= 300: most of the kernel matrix lies
+    more than e^-70 below its bin's largest term and is dropped.  The device
+    solution is a fixed point of the oracle's own map (one FP64 map from it
+    moves f by < 1e-9, and gives the same D_b), and it agrees with the
+    log-sum-exp solve of the allocation-free entry point."""
+    kT, mu, omega, N, E, H, nmax = synthetic_bins(seed=5, S_side=8, nmax=300, kT_range=(0.5, 1.6),
+                                                  mu_range=(-6.0, -1.0), per_n=12)
+    f_g, D_g, it_g = mbar_solve(kT, mu, 1.0, omega, N, E, H, tol=1e-12)
+    info = mbar_last_info()
+    S, B = len(kT), len(N)
+    assert info["path"] == 1 and info["builds"] >= 1 and (info["S"], info["B"]) == (S, B)
+    assert 0 < info["nnz"] < 0.5 * S * B, info
+    f1, D1, _, _ = OM.solve(kT, mu, 1.0, omega, N, E, H, max_iter=1, f0=f_g)
+    np.testing.assert_allclose(f1, f_g, atol=1e-9)
+    np.testing.assert_allclose(D_g, D1, atol=1e-9)
+    f_s, D_s, _ = mbar_solve_static(kT, mu, 1.0, omega, N, E, H, tol=1e-12)
+    assert mbar_last_info()["path"] == 0
+    np.testing.assert_allclose(f_g, f_s, atol=1e-8)
+    np.testing.assert_allclose(D_g, D_s, atol=1e-8)
+
+
+def test_full_size_solve_satisfies_sampled_equations():
+    """The 1024-replica fcc(111) workload (Nmax 512) after 2000 + 20000
+    sweeps: the device solve over its pooled bins (about 1e6 of them, on the
+    sparse kernel matrix) satisfies, checked one by one in FP64 by the
+    oracle's reduced potential, the D equation
+        D_b = ln sum_k Omega_k exp(f_k - u_k(b))
+    at 200 sampled bins and the f equation
+        f_s - f_0 = -ln sum_b H_b exp(-u_s(b) - D_b) + ln sum_b H_b exp(-u_0(b) - D_b)
+    at 24 sampled states."""
+    p = W.fcc111_paper_scale(seed=0)
+    rng = np.random.default_rng(0)
+    pos, n = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=0)
+    g = Regc(p)
+    g.set_walkers(pos, n)
+    g.run(2000)
+    g.reset_histograms()
+    g.run(20000)
+    h = g.histograms()
+    g.close()
+    N_b, E_b, H_b = OM.occupied_bins(h["hNE"], p.e_lo, p.e_bin)
+    kT_s, mu_s = np.repeat(p.kT, p.M), np.tile(p.mu, p.L)
+    omega = h["omega"].astype(float)
+    f, D, it = mbar_solve(kT_s, mu_s, p.lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter=200000)
+    info = mbar_last_info()
+    S, B = p.S, len(N_b)
+    assert info["path"] == 1 and info["nnz"] < 0.5 * S * B, info
+    assert B > 200000
+    sb = np.sort(rng.choice(B, 200, replace=False))
+    u = OM.reduced_potential(kT_s, mu_s, p.lambda0, N_b[sb], E_b[sb])           # [S, 200]
+    D_o = OM.lse(np.log(omega)[:, None] + f[:, None] - u, axis=0)
+    np.testing.assert_allclose(D[sb], D_o, rtol=0, atol=1e-9)
+    ss = np.concatenate([[0], np.sort(rng.choice(np.arange(1, S), 23, replace=False))])
+    u = OM.reduced_potential(kT_s[ss], mu_s[ss], p.lambda0, N_b, E_b)          # [24, B]
+    f_o = -OM.lse(np.log(H_b)[None, :] - u - D[None, :], axis=1)
+    np.testing.assert_allclose(f_o - f_o[0], f[ss], rtol=0, atol=1e-8)
 
 
 def test_handle_reweight_matches_standalone_entry_points():

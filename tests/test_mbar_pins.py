@@ -62,6 +62,23 @@ def test_ideal_gas_free_energies_exact():
     np.testing.assert_allclose(f, -(lnxi - lnxi[0]), atol=1e-9)
 
 
+def test_exact_free_energies_are_the_fixed_point_of_one_map():
+    """Started at the closed-form f, one map of the plain iteration stays
+    there; started elsewhere, the iteration returns to it."""
+    nmax = 40
+    kT, mu, lam, omega, H, lnxi, V = _ideal_setup(nmax)
+    N_b = np.arange(nmax + 1, dtype=float)
+    E_b = np.zeros(nmax + 1)
+    exact = -(lnxi - lnxi[0])
+    f1, _, it, _ = mbar.solve(kT, mu + kT * math.log(V), 1.0, omega, N_b, E_b, H, max_iter=1, f0=exact)
+    assert it == 1
+    np.testing.assert_allclose(f1, exact, atol=1e-12)
+    start = exact + np.linspace(-3.0, 3.0, len(exact))
+    f2, _, _, ok = mbar.solve(kT, mu + kT * math.log(V), 1.0, omega, N_b, E_b, H, tol=1e-13, f0=start)
+    assert ok
+    np.testing.assert_allclose(f2, exact, atol=1e-9)
+
+
 def test_ideal_gas_reweighting_off_grid():
     nmax = 40
     kT, mu, lam, omega, H, lnxi, V = _ideal_setup(nmax)

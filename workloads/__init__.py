@@ -438,6 +438,33 @@ def two_gas_small(L: int = 2, M: int = 3, K: int = 3, nmax: int = 32, seed: int 
         gc2_type=2, mu2=mu_grid(K), lambda0_2=0.7)
 
 
+def two_gas_paper_scale(L: int = 8, M: int = 16, K: int = 8, nmax: int = 256, seed: int = 0) -> Problem:
+    """Two reactive gases over the 1024-replica workload's fcc(111) slab
+    (12x12x4, gas 12 high): B and C with two_gas_small's pair parameters,
+    eps_sB 2 as in the one-species workload, on an 8 x 16 x 8 grid of kT
+    (0.6 .. 1.5), mu_B (-6 .. -2), mu_C (-6 .. -2), N_B + N_C <= 256.  The
+    pooled (N_B, N_C, E) histogram (257^2 rows x 3840 bins of 1.0) holds
+    2 GB."""
+    xyz, lx, ly, ztop = fcc111_slab(12, 12, 4, 1.5625)
+    eps = np.zeros((4, 4))
+    sig = np.ones((4, 4))
+    eps[0, 0], eps[0, 1], eps[1, 0] = 1.0, 2.0, 2.0
+    eps[2, 2], sig[2, 2] = 0.6, 0.9
+    eps[0, 2] = eps[2, 0] = 0.8
+    sig[0, 2] = sig[2, 0] = 0.95
+    eps[1, 2] = eps[2, 1] = 1.2
+    sig[1, 2] = sig[2, 1] = 0.95
+    zhi = float(f32(ztop + 12.0))
+    return Problem(
+        n_types=3, eps=f32(eps), sigma=f32(sig), rc=2.5, Lx=lx, Ly=ly, Lz=zhi, periodic_z=0,
+        z_lo=ztop, z_hi=zhi, surf_xyz=xyz, surf_type=np.ones(len(xyz), np.int32),
+        kT=kT_grid(L), mu=mu_grid(M), lambda0=1.0, nmax=nmax, moves_per_sweep=20,
+        max_disp=0.2, p_disp=1.0 / 3.0, seed=seed,
+        e_lo=centred_e_lo(-float(nmax) * 14.0, 1.0), e_bin=1.0,
+        n_e_bins=int(round(float(nmax) * 15.0 / 1.0)), name="two_gas_paper_scale",
+        gc2_type=2, mu2=mu_grid(K), lambda0_2=0.7)
+
+
 def two_gas_initial(problem: Problem, nb, nc, seed: int, min_dist: float = 0.9):
     """Seeded walkers of a two-species problem: walker w holds nb[w]
     particles of B then nc[w] of C at uniform positions of the gas region.
