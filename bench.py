@@ -76,7 +76,7 @@ def parse_args(argv=None):
                     help="sweeps of the 1024-replica production run reweighted to <N>(T, p) (0: skip)")
     ap.add_argument("--two-species", type=int, default=1, help="1: add the two-species workload")
     ap.add_argument("--two-species-steps", type=int, default=20)
-    ap.add_argument("--two-species-sweeps", type=int, default=20000)
+    ap.add_argument("--two-species-sweeps", type=int, default=100000)
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
     ap.add_argument("--da-steps-large", type=int, default=60)
@@ -534,6 +534,7 @@ def production_arm(torch, stream, sweeps, equil=2000, seed=0):
     t1 = time.perf_counter()
     nm, pN, f, iters = g.reweight(T.ravel(), mu_q, tol=1e-9, max_iter=200000)
     rw_s = time.perf_counter() - t1
+    mbar = mbar_summary()
     g.close()
     return {"workload": WORKLOAD, "sweeps": sweeps, "equilibration_sweeps": equil,
             "run_s": run_s, "trial_moves_per_s": p.S * sweeps * p.moves_per_sweep / run_s,
@@ -546,7 +547,7 @@ def production_arm(torch, stream, sweeps, equil=2000, seed=0):
                                       "note": "per-state energy histograms of the two halves; samples "
                                               "one sweep apart are correlated, so the critical value "
                                               "is optimistic"},
-            "reweight_s": rw_s, "mbar_iterations": iters,
+            "reweight_s": rw_s, "mbar_iterations": iters, "mbar": mbar,
             "phase_map": {"kT": kT_q.tolist(), "p": p_q.tolist(),
                           "N_mean": nm.reshape(12, 12).round(3).tolist(),
                           "N_most_probable": np.argmax(pN, axis=1).reshape(12, 12).tolist()}}
@@ -622,6 +623,7 @@ def two_species_arm(torch, stream, flush, steps, sweeps, equil=2000, seed=0):
     t1 = time.perf_counter()
     nbm, ncm, pb, pc, f, iters = g.reweight2(T.ravel(), MB.ravel(), MC.ravel(), tol=1e-9, max_iter=200000)
     rw_s = time.perf_counter() - t1
+    mbar = mbar_summary()
     g.close()
     shape = (len(kT_q), len(mb), len(mc))
     return {"workload": TWO_SPECIES, "equilibration_sweeps": equil, "timed": timed,
@@ -633,12 +635,26 @@ def two_species_arm(torch, stream, flush, steps, sweeps, equil=2000, seed=0):
                            "walkers_N_B_mean": float(cnt.mean()),
                            "convergence_ks_halves": {"median": float(np.median(ks)), "max": float(np.max(ks)),
                                                      "states_unchanged_at_1pct": int(np.sum(ks < crit))}},
-            "reweight_s": rw_s, "mbar_iterations": iters,
+            "reweight_s": rw_s, "mbar_iterations": iters, "mbar": mbar,
             "phase_map": {"kT": kT_q.tolist(), "mu_B": mb.tolist(), "mu_C": mc.tolist(),
                           "N_B_mean": nbm.reshape(shape).round(2).tolist(),
                           "N_C_mean": ncm.reshape(shape).round(2).tolist(),
                           "N_B_most_probable": np.argmax(pb, axis=1).reshape(shape).tolist(),
                           "N_C_most_probable": np.argmax(pc, axis=1).reshape(shape).tolist()}}
+
+
+def mbar_summary():
+    """The last MBAR solve (regc_mbar_last_info) with the sparse maps' rate:
+    algorithmic bytes per map = 24 per kept entry (index + FP64 value, by bin
+    and by state) + 32 per bin (row pointer, H_b, V_b written and read)."""
+    from paper_1908_11118_gb300 import mbar_last_info
+    i = mbar_last_info()
+    per_map = 24.0 * i["nnz"] + 32.0 * i["B"]
+    gbs = per_map * i["sparse_maps"] / (i["ms_maps"] / 1e3) / 1e9 if i["ms_maps"] > 0 else None
+    peak, src = hbm_peak()
+    return dict(i, bytes_per_map=per_map, sparse_map_gbs=gbs,
+                sparse_map_frac_of_hbm=(gbs / peak if gbs else None), hbm_peak_source=src,
+                kept_fraction=i["nnz"] / max(1, i["S"] * i["B"]))
 
 
 def paper_structure_spec(p):

@@ -578,7 +578,12 @@ REGC_API regc_status regc_mbar_solve(int S, const double *kT, const double *mu, 
  * matrix, or a state without a kept entry far from the fixed point), the kept
  * entries of the last build, its S and B, the device milliseconds of the
  * matrix builds and of the maps on the matrix (CUDA events on the solve's
- * stream), and the number of those maps.  All zero before the first solve.
+ * stream), and the number of those maps.  regc_reweight and regc_reweight2
+ * start a problem of at least 65536 bins from the solution of the same
+ * problem with 16 energy bins merged into one (solved to 1e-6; same fixed
+ * point, fewer matrix builds): coarse_iterations, coarse_B, coarse_builds
+ * and coarse_maps describe that solve (zero without one) and its device time
+ * is included in ms_build and ms_maps.  All zero before the first solve.
  * Errors: REGC_EINVAL (out NULL). */
 typedef struct {
     int32_t path;
@@ -591,7 +596,10 @@ typedef struct {
     double ms_build;
     double ms_maps;
     int32_t sparse_maps;
-    int32_t reserved;
+    int32_t coarse_iterations;
+    int64_t coarse_B;
+    int32_t coarse_builds;
+    int32_t coarse_maps;
 } regc_mbar_info;
 REGC_API regc_status regc_mbar_last_info(regc_mbar_info *out);
 

@@ -43,7 +43,8 @@ class Species2(C.Structure):
 class MbarInfo(C.Structure):
     _fields_ = [("path", C.c_int32), ("iterations", C.c_int32), ("builds", C.c_int32), ("lse_maps", C.c_int32),
                 ("nnz", C.c_int64), ("S", C.c_int64), ("B", C.c_int64), ("ms_build", C.c_double),
-                ("ms_maps", C.c_double), ("sparse_maps", C.c_int32), ("reserved", C.c_int32)]
+                ("ms_maps", C.c_double), ("sparse_maps", C.c_int32), ("coarse_iterations", C.c_int32),
+                ("coarse_B", C.c_int64), ("coarse_builds", C.c_int32), ("coarse_maps", C.c_int32)]
 
 
 class GridSpec(C.Structure):

@@ -480,6 +480,7 @@ __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
 // The entries are held twice: by bin (CSR, states ascending) for d_b and by
 // state (in kFSplit bin quarters, bins ascending) for f_new; both are summed
 // in a fixed order, so the iteration is deterministic.
+constexpr long long kWarmMinBins = 65536;   // smaller problems solve from f = 0
 constexpr double kKeep = 70.0;
 constexpr double kSpreadAcc = 20.0;
 constexpr double kSpreadMax = 60.0;
@@ -498,6 +499,10 @@ struct SpDev {
     double* fref;    // [S]
     double* w;       // [S] exp(f_s - f_ref,s) of the current iterate (from the host)
     int* flag;       // [2] entries of the state segments missing from their bin's row; empty state sums
+    // the by-state sums in pieces (sp_fp_kernel, sp_fs_kernel)
+    long long* pc_begin;   // [n_pieces + 1] first entry of each piece
+    int* pc_first;         // [S + 1] first piece of each state
+    double* pc_sum;        // [n_pieces]
 };
 
 // The binary32 screen value of state (g, a, c, c2) at bin (en, n2).  The row
@@ -671,18 +676,33 @@ __global__ void __launch_bounds__(kFThreads) sp_cols_kernel(const __grid_constan
     }
 }
 
-// d_b = sum_s K_sb w_s over the bin's row (a warp per bin, a fixed
-// reduction tree), then V_b = H_b / d_b; FINAL: D_b = M_b + ln d_b instead.
+// d_b = sum_s K_sb w_s over the bin's row, then V_b = H_b / d_b; FINAL:
+// D_b = M_b + ln d_b instead.  kDLanes lanes per bin (8 bins per warp): a
+// warp-wide FP64 instruction costs the narrow FP64 pipe the same whatever its
+// active lanes, so the reduction and the division are shared by 8 bins, while
+// a lane group still reads 32 consecutive bytes of its row per step.  Two
+// FMA chains per lane, combined in a fixed order (deterministic).
+constexpr int kDLanes = 4;
 template <bool FINAL>
 __global__ void __launch_bounds__(256) sp_d_kernel(const __grid_constant__ MbarDev m, SpDev p) {
-    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (b >= m.B) return;   // the whole warp
-    const long long e1 = p.rp[b + 1];
-    double d = 0.0;
-    for (long long e = p.rp[b] + lane; e < e1; e += 32) d = fma(p.cv[e], __ldg(p.w + p.ci[e]), d);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long b = gt / kDLanes;
+    const int sub = (int)(gt % kDLanes);
+    const bool act = b < m.B;
+    double d0 = 0.0, d1 = 0.0;
+    if (act) {
+        const long long e1 = p.rp[b + 1];
+        long long e = p.rp[b] + sub;
+        for (; e + kDLanes < e1; e += 2 * kDLanes) {
+            d0 = fma(p.cv[e], __ldg(p.w + p.ci[e]), d0);
+            d1 = fma(p.cv[e + kDLanes], __ldg(p.w + p.ci[e + kDLanes]), d1);
+        }
+        if (e < e1) d0 = fma(p.cv[e], __ldg(p.w + p.ci[e]), d0);
+    }
+    double d = d0 + d1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (lane == 0) {
+    for (int o = 1; o < kDLanes; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (act && sub == 0) {
         if (FINAL) {
             const double D = p.M[b] + log(d);
             m.D[b] = D;
@@ -693,33 +713,76 @@ __global__ void __launch_bounds__(256) sp_d_kernel(const __grid_constant__ MbarD
     }
 }
 
-// f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb over the state's
-// segments: CTA r of the cluster over quarter r, the quarters' sums added in
-// rank order by CTA 0 (deterministic).  An empty sum raises flag[1].
-__global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
-    sp_f_kernel(const __grid_constant__ MbarDev m, SpDev p) {
-    __shared__ double part;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const int s = blockIdx.x / kFSplit;
-    const long long e1 = p.cp[blockIdx.x + 1];
-    double acc = 0.0;
-    for (long long e = p.cp[blockIdx.x] + threadIdx.x; e < e1; e += kFThreads)
-        acc = fma(p.bv[e], p.V[p.bi[e]], acc);
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part = acc;
-    cluster.sync();
-    if (rank == 0 && threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kFSplit; ++q) t += *cluster.map_shared_rank(&part, q);
-        if (t > 0.0) {
-            m.f_new[s] = m.lnom[s] + p.fref[s] - log(t);
-        } else {
-            m.f_new[s] = 0.0;
-            atomicAdd(&p.flag[1], 1);
-        }
+// The by-state sums in balanced pieces: a state's entries (its kFSplit
+// segments, contiguous) are cut into pieces of at most kPiece entries, one
+// CTA per piece, so that a state with many entries does not hold back the
+// map; sp_fs_kernel then adds each state's piece sums in piece order
+// (deterministic) into f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb.
+constexpr long long kPiece = 32768;
+__global__ void __launch_bounds__(kFThreads) sp_fp_kernel(const __grid_constant__ SpDev p) {
+    const long long e0 = p.pc_begin[blockIdx.x], e1 = p.pc_begin[blockIdx.x + 1];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    long long e = e0 + threadIdx.x;
+    for (; e + 3 * kFThreads < e1; e += 4 * kFThreads) {
+        const int b0 = p.bi[e], b1 = p.bi[e + kFThreads], b2 = p.bi[e + 2 * kFThreads], b3 = p.bi[e + 3 * kFThreads];
+        const double k0 = p.bv[e], k1 = p.bv[e + kFThreads], k2 = p.bv[e + 2 * kFThreads], k3 = p.bv[e + 3 * kFThreads];
+        a0 = fma(k0, p.V[b0], a0);
+        a1 = fma(k1, p.V[b1], a1);
+        a2 = fma(k2, p.V[b2], a2);
+        a3 = fma(k3, p.V[b3], a3);
     }
-    cluster.sync();   // the partial sums stay readable until rank 0 has added them
+    for (; e < e1; e += kFThreads) a0 = fma(p.bv[e], p.V[p.bi[e]], a0);
+    const double acc = block_sum((a0 + a1) + (a2 + a3));
+    if (threadIdx.x == 0) p.pc_sum[blockIdx.x] = acc;
+}
+
+// One thread per state: its pieces are pc_first[s] .. pc_first[s + 1] - 1.
+// An empty sum raises flag[1].
+__global__ void __launch_bounds__(256) sp_fs_kernel(const __grid_constant__ MbarDev m, SpDev p) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m.S) return;
+    double t = 0.0;
+    for (int q = p.pc_first[s]; q < p.pc_first[s + 1]; ++q) t += p.pc_sum[q];
+    if (t > 0.0) {
+        m.f_new[s] = m.lnom[s] + p.fref[s] - log(t);
+    } else {
+        m.f_new[s] = 0.0;
+        atomicAdd(&p.flag[1], 1);
+    }
+}
+
+// ---- warm start: the problem coarsened in energy.  Bins adjacent in the
+// bin order with equal N (and N2) and equal floor(E / width) are merged: the
+// counts added, the energy their count-weighted mean.
+__device__ __forceinline__ bool same_coarse(const MbarDev& m, long long b, long long c, double width) {
+    return m.N_b[b] == m.N_b[c] && (m.N2_b == nullptr || m.N2_b[b] == m.N2_b[c]) &&
+           floor(m.E_b[b] / width) == floor(m.E_b[c] / width);
+}
+
+__global__ void __launch_bounds__(256) coarse_flag_kernel(const __grid_constant__ MbarDev m, double width,
+                                                          long long* cnt) {
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m.B) return;
+    cnt[b + 1] = (b == 0 || !same_coarse(m, b, b - 1, width)) ? 1 : 0;
+}
+
+// after the inclusive scan of cnt[1 .. B]: the run starting at b is coarse bin cnt[b + 1] - 1
+__global__ void __launch_bounds__(256) coarse_fill_kernel(const __grid_constant__ MbarDev m, double width,
+                                                          const long long* cnt, int* Nc, int* N2c, double* Ec,
+                                                          double* lnHc) {
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m.B || !(b == 0 || !same_coarse(m, b, b - 1, width))) return;
+    double h = 0.0, he = 0.0;
+    for (long long c = b; c < m.B && same_coarse(m, c, b, width); ++c) {
+        const double hc = exp(m.lnH[c]);
+        h += hc;
+        he = fma(hc, m.E_b[c], he);
+    }
+    const long long o = cnt[b + 1] - 1;
+    Nc[o] = m.N_b[b];
+    if (N2c) N2c[o] = m.N2_b[b];
+    Ec[o] = he / h;
+    lnHc[o] = log(h);
 }
 
 // ---- inclusive scan of long long x[n] in place: chunk totals, one block
@@ -821,11 +884,13 @@ struct SparseMat {
     cudaStream_t s = nullptr;
     void* fixed = nullptr;     // the bin- and state-sized arrays
     void* entries = nullptr;   // cap entries: cv, bv (double), ci, bi (int)
-    long long cap = 0, nnz = 0;
+    void* pieces = nullptr;    // pc_begin, pc_sum, pc_first for up to pc_cap pieces
+    long long cap = 0, nnz = 0, pc_cap = 0, n_pieces = 0;
     long long* tmp = nullptr;  // scan scratch
     SpDev p{};
 
     ~SparseMat() {
+        if (pieces) cudaFreeAsync(pieces, s);
         if (entries) cudaFreeAsync(entries, s);
         if (fixed) cudaFreeAsync(fixed, s);
     }
@@ -898,14 +963,49 @@ struct SparseMat {
         if (e != cudaSuccess) return e;
         sp_cols_kernel<TWO, false><<<S * kFSplit, kFThreads, 0, s>>>(m, p);
         int flag_h = 0;
-        long long n_cols = 0;
+        std::vector<long long> cp_h(size_t(S) * kFSplit + 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&flag_h, p.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&n_cols, p.cp + size_t(S) * kFSplit, sizeof(long long), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(cp_h.data(), p.cp, cp_h.size() * sizeof(long long), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        *ok = flag_h == 0 && n_cols == nnz;
+        if (flag_h != 0 || cp_h.back() != nnz) return cudaSuccess;
+        // pieces of at most kPiece entries, at least one per state
+        std::vector<long long> begin;
+        std::vector<int> first(size_t(S) + 1);
+        for (int k = 0; k < S; ++k) {
+            first[k] = (int)begin.size();
+            const long long a = cp_h[size_t(k) * kFSplit], b = cp_h[size_t(k + 1) * kFSplit];
+            const long long np = std::max(1LL, (b - a + kPiece - 1) / kPiece);
+            for (long long q = 0; q < np; ++q) begin.push_back(a + (b - a) * q / np);
+        }
+        first[S] = (int)begin.size();
+        n_pieces = (long long)begin.size();
+        begin.push_back(nnz);
+        if (n_pieces > pc_cap) {
+            if (pieces) cudaFreeAsync(pieces, s);
+            pieces = nullptr;
+            pc_cap = 0;
+            const long long want = n_pieces + n_pieces / 4 + 16;
+            e = cudaMallocAsync(&pieces, size_t(want + 1) * 16 + size_t(S + 1) * 4, s);
+            if (e != cudaSuccess) {
+                pieces = nullptr;
+                (void)cudaGetLastError();   // out of memory is not sticky
+                return cudaSuccess;
+            }
+            pc_cap = want;
+            p.pc_begin = static_cast<long long*>(pieces);
+            p.pc_sum = reinterpret_cast<double*>(p.pc_begin + (want + 1));
+            p.pc_first = reinterpret_cast<int*>(p.pc_sum + want);
+        }
+        e = cudaMemcpyAsync(p.pc_begin, begin.data(), begin.size() * sizeof(long long), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p.pc_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        // the host vectors go out of scope: wait for the copies
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        *ok = true;
         return cudaSuccess;
     }
 };
@@ -927,11 +1027,11 @@ thread_local MbarInfo g_last_info{};
 MbarInfo mbar_last_info() { return g_last_info; }
 
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out, cudaStream_t s,
-                           bool allow_matrix) {
+                           bool allow_matrix, const double* x0) {
     constexpr int kDepth = 16;
     const int S = m.S;
     MbarInfo& info = g_last_info;
-    info = MbarInfo{0, 0, 0, 0, 0, S, m.B, 0.0, 0.0, 0};
+    info = MbarInfo{0, 0, 0, 0, 0, S, m.B, 0.0, 0.0, 0, 0, 0, 0, 0};
     // device time of the builds and of the maps on the matrix
     struct Timer {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -959,7 +1059,10 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     } tb, tm;
     cudaError_t err = cudaMemsetAsync(m.state, 0, 2 * sizeof(int), s);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(m.f, 0, size_t(S) * sizeof(double), s);
+    std::vector<double> x(S, 0.0);
+    if (x0)
+        for (int k = 0; k < S; ++k) x[k] = x0[k] - x0[0];
+    err = cudaMemcpyAsync(m.f, x.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return err;
     const int dgrid = (m.B + 255) / 256;
     const int dgrid128 = (m.B + 127) / 128;   // a bin per thread, small blocks to spread over every SM
@@ -981,9 +1084,9 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             if (!use_sp) (void)cudaGetLastError();   // out of memory is not sticky: iterate on log-sum-exps
         }
     }
-    std::vector<double> fref_h(S, 0.0), w_h(S);
+    std::vector<double> fref_h(x), w_h(S);
     bool build = true;
-    std::vector<double> x(S, 0.0), g(S), r(S), best_g(S, 0.0), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
+    std::vector<double> g(S), r(S), best_g(x), rhs(kDepth), A(kDepth * kDepth), gam(kDepth);
     std::vector<std::vector<double>> dR, dG;       // differences of residuals and images, oldest first
     std::vector<double> r_prev, g_prev;
     double best = INFINITY;
@@ -1027,8 +1130,9 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
             if (err == cudaSuccess) err = cudaMemsetAsync(sp.p.flag + 1, 0, sizeof(int), s);
             if (err != cudaSuccess) return err;
             tm.start(s);
-            sp_d_kernel<false><<<(m.B + 7) / 8, 256, 0, s>>>(m, sp.p);
-            sp_f_kernel<<<S * kFSplit, kFThreads, 0, s>>>(m, sp.p);
+            sp_d_kernel<false><<<(unsigned)((m.B * (long long)kDLanes + 255) / 256), 256, 0, s>>>(m, sp.p);
+            sp_fp_kernel<<<(unsigned)sp.n_pieces, kFThreads, 0, s>>>(sp.p);
+            sp_fs_kernel<<<(S + 255) / 256, 256, 0, s>>>(m, sp.p);
             tm.stop(s);
             err = cudaGetLastError();
             if (err == cudaSuccess)
@@ -1152,7 +1256,7 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
         for (int k = 0; k < S; ++k) w_h[k] = exp(x[k] - fref_h[k]);
         err = cudaMemcpyAsync(sp.p.w, w_h.data(), size_t(S) * sizeof(double), cudaMemcpyHostToDevice, s);
         if (err != cudaSuccess) return err;
-        sp_d_kernel<true><<<(m.B + 7) / 8, 256, 0, s>>>(m, sp.p);
+        sp_d_kernel<true><<<(unsigned)((m.B * (long long)kDLanes + 255) / 256), 256, 0, s>>>(m, sp.p);
     } else if (two) {
         d_kernel<true><<<dgrid128, 128, 0, s>>>(m, 1);
     } else {
@@ -1166,6 +1270,94 @@ cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iter
     if (iters_out) *iters_out = it;
     info.iterations = it;
     return cudaSuccess;
+}
+
+cudaError_t mbar_solve_warm_dev(const MbarDev& m, double width, double tol, int max_iter, int* iters_out,
+                                cudaStream_t s) {
+    std::vector<double> x0;
+    long long Bc = 0;
+    int it_c = 0;
+    if (width > 0.0 && m.B >= kWarmMinBins) {
+        std::vector<void*> blocks;
+        struct Free {
+            std::vector<void*>& v;
+            cudaStream_t s;
+            ~Free() {
+                for (void* q : v) cudaFreeAsync(q, s);
+            }
+        } free_all{blocks, s};
+        auto get = [&](size_t bytes) -> void* {
+            void* q = nullptr;
+            if (cudaMallocAsync(&q, std::max<size_t>(bytes, 16), s) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return nullptr;
+            }
+            blocks.push_back(q);
+            return q;
+        };
+        const long long B = m.B;
+        long long* cnt = static_cast<long long*>(get(size_t(B + 1) * 8));
+        long long* tmp = static_cast<long long*>(get(size_t((B + kScanChunk - 1) / kScanChunk + 1) * 8));
+        bool ok = cnt && tmp;
+        cudaError_t e = cudaSuccess;
+        if (ok) {
+            e = cudaMemsetAsync(cnt, 0, 8, s);
+            if (e == cudaSuccess) {
+                coarse_flag_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(m, width, cnt);
+                e = lscan(cnt + 1, B, tmp, s);
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&Bc, cnt + B, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+        }
+        // worth it only when the merge shrinks the problem well
+        if (ok && Bc > 0 && Bc * 4 <= B) {
+            MbarDev c = m;
+            const size_t Sz = size_t(m.S);
+            c.B = (int)Bc;
+            int* Nc = static_cast<int*>(get(size_t(Bc) * 4));
+            int* N2c = m.N2_b ? static_cast<int*>(get(size_t(Bc) * 4)) : nullptr;
+            double* Ec = static_cast<double*>(get(size_t(Bc) * 8));
+            double* lnHc = static_cast<double*>(get(size_t(Bc) * 8));
+            c.f = static_cast<double*>(get(Sz * 8));
+            c.f_new = static_cast<double*>(get(Sz * 8));
+            c.D = static_cast<double*>(get(size_t(Bc) * 8));
+            c.EN32 = static_cast<float2*>(get(size_t(Bc) * 8));
+            c.DH32 = static_cast<float*>(get(size_t(Bc) * 4));
+            c.N2f = m.N2_b ? static_cast<float*>(get(size_t(Bc) * 4)) : nullptr;
+            c.delta = static_cast<double*>(get(8));
+            c.state = static_cast<int*>(get(8));
+            ok = Nc && Ec && lnHc && c.f && c.f_new && c.D && c.EN32 && c.DH32 && c.delta && c.state &&
+                 (!m.N2_b || (N2c && c.N2f));
+            if (ok) {
+                coarse_fill_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(m, width, cnt, Nc, N2c, Ec, lnHc);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                c.N_b = Nc;
+                c.N2_b = N2c;
+                c.E_b = Ec;
+                c.lnH = lnHc;
+                // a loose solve: it only has to land near the fine fixed point
+                e = mbar_solve_dev(c, std::max(tol, 1e-6), max_iter, &it_c, s, true, nullptr);
+                if (e != cudaSuccess) return e;
+                x0.resize(Sz);
+                e = cudaMemcpyAsync(x0.data(), c.f, Sz * 8, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    const MbarInfo coarse = g_last_info;
+    cudaError_t e = mbar_solve_dev(m, tol, max_iter, iters_out, s, true, x0.empty() ? nullptr : x0.data());
+    if (!x0.empty()) {
+        g_last_info.coarse_B = Bc;
+        g_last_info.coarse_iterations = it_c;
+        g_last_info.ms_build += coarse.ms_build;
+        g_last_info.ms_maps += coarse.ms_maps;
+        g_last_info.coarse_builds = coarse.builds;
+        g_last_info.coarse_maps = coarse.sparse_maps;
+    }
+    return e;
 }
 
 cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, int nmax,

@@ -41,6 +41,10 @@ struct MbarInfo {
     long long S, B;
     double ms_build, ms_maps;   // device time of the matrix builds and of the maps on it
     int sparse_maps;            // maps on the matrix
+    // the warm start of mbar_solve_warm_dev (zero without one): bins, iterations,
+    // builds and maps of the coarse solve (its times are included above)
+    long long coarse_B;
+    int coarse_iterations, coarse_builds, coarse_maps;
 };
 MbarInfo mbar_last_info();
 
@@ -52,8 +56,17 @@ MbarInfo mbar_last_info();
 // - max_k(...)) (those within e^-70 of their bin's largest), allocated on the
 // stream for the duration of the call when they fit in half the free device
 // memory; otherwise on log-sum-exps of the energies.
+// x0 (host, S values, optional) is the starting point instead of f = 0.
 cudaError_t mbar_solve_dev(const MbarDev& m, double tol, int max_iter, int* iters_out,
-                           cudaStream_t s, bool allow_matrix = true);
+                           cudaStream_t s, bool allow_matrix = true, const double* x0 = nullptr);
+
+// mbar_solve_dev started from the solution of the same problem coarsened in
+// energy (width > 0, at least 65536 bins): bins adjacent in the bin order
+// with equal N (and N2) and equal floor(E / width) merged into one at their
+// count-weighted mean energy, solved to 1e-6.  The fixed point is the fine
+// problem's; only the path to it is shorter (far fewer matrix builds).
+cudaError_t mbar_solve_warm_dev(const MbarDev& m, double width, double tol, int max_iter, int* iters_out,
+                                cudaStream_t s);
 
 // Reweight to Q query states given on the device as (a_q, c_q):
 // N_mean [Q], pN [Q][nmax+1], f_q [Q] (device, any may be null).

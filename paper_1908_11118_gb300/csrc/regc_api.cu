@@ -1440,14 +1440,18 @@ struct MbarBuffers {
     }
 };
 
+// energy bins merged for the warm start of the handle's reweighting
+constexpr double kWarmBins = 16.0;
+
 regc_status status_of(cudaError_t e) {
     return e == cudaSuccess ? REGC_OK : (e == cudaErrorMemoryAllocation ? REGC_ENOMEM : REGC_ECUDA);
 }
 
 // Solve over bins already on the device, then answer Q host queries.
+// warm_width > 0: started from the solve coarsened to energy bins of that width.
 cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double tol, int max_iter, int* iters,
                             double* f_host, double* D_host, int Q, const double* kT_q, const double* mu_q,
-                            int nmax, double* N_mean, double* pN, double* f_q) {
+                            int nmax, double* N_mean, double* pN, double* f_q, double warm_width = 0.0) {
     cudaStream_t s = buf.s;
     m.f = buf.get<double>(m.S);
     m.f_new = buf.get<double>(m.S);
@@ -1457,7 +1461,7 @@ cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double
     m.delta = buf.get<double>(1);
     m.state = buf.get<int>(2);
     if (buf.err != cudaSuccess) return buf.err;
-    cudaError_t e = mbar_solve_dev(m, tol, max_iter, iters, s);
+    cudaError_t e = mbar_solve_warm_dev(m, warm_width, tol, max_iter, iters, s);
     if (e != cudaSuccess) return e;
     if (f_host) e = cudaMemcpyAsync(f_host, m.f, m.S * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && D_host) e = cudaMemcpyAsync(D_host, m.D, m.B * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1546,7 +1550,7 @@ regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const doub
     m.E_b = E_b;
     m.lnH = lnH;
     e = solve_and_query(buf, m, h->lambda0, tol, max_iter, iters, f_states, nullptr, nq, kT_q, mu_q, h->nmax, N_mean,
-                        pN, nullptr);
+                        pN, nullptr, kWarmBins * h->e_bin);
     return status_of(e);
 }
 
@@ -1607,7 +1611,7 @@ regc_status regc_reweight2(regc_handle* h, int nq, const double* kT_q, const dou
     m.N2_b = N2_b;
     m.E_b = E_b;
     m.lnH = lnH;
-    e = mbar_solve_dev(m, tol, max_iter, iters, s);
+    e = mbar_solve_warm_dev(m, kWarmBins * h->e_bin, tol, max_iter, iters, s);
     if (e == cudaSuccess && f_states) e = cudaMemcpyAsync(f_states, m.f, m.S * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return status_of(e);
     if (nq > 0) {
@@ -1642,7 +1646,8 @@ regc_status regc_mbar_last_info(regc_mbar_info* out) {
     if (!out) return REGC_EINVAL;
     const MbarInfo i = mbar_last_info();
     *out = regc_mbar_info{i.path, i.iterations, i.builds, i.lse_maps, i.nnz, i.S, i.B,
-                          i.ms_build, i.ms_maps, i.sparse_maps, 0};
+                          i.ms_build, i.ms_maps, i.sparse_maps, i.coarse_iterations, i.coarse_B,
+                          i.coarse_builds, i.coarse_maps};
     return REGC_OK;
 }
 

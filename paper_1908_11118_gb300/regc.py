@@ -526,10 +526,11 @@ def mbar_last_info() -> dict:
     """What this thread's last MBAR solve did (regc_mbar_last_info): path 1
     on the sparse kernel matrix, 0 on log-sum-exps only; iterations, matrix
     builds, maps on log-sum-exps, kept entries, S, B, device milliseconds of
-    the builds and of the maps on the matrix, and the number of those maps."""
+    the builds and of the maps on the matrix, the number of those maps, and
+    the coarse warm-start solve's iterations, bins, builds and maps."""
     i = _lib.MbarInfo()
     check(_lib.lib().regc_mbar_last_info(C.byref(i)), "regc_mbar_last_info")
-    return {k: getattr(i, k) for k, _ in _lib.MbarInfo._fields_ if k != "reserved"}
+    return {k: getattr(i, k) for k, _ in _lib.MbarInfo._fields_}
 
 
 def mbar_query(kT_q, mu_q, lambda0, N_b, E_b, H_b, D, nmax, stream=None):

@@ -171,15 +171,9 @@ def test_sparse_kernel_matrix_solves_the_oracle_equations():
     np.testing.assert_allclose(D_g, D_s, atol=1e-8)
 
 
-def test_full_size_solve_satisfies_sampled_equations():
-    """The 1024-replica fcc(111) workload (Nmax 512) after 2000 + 20000
-    sweeps: the device solve over its pooled bins (about 1e6 of them, on the
-    sparse kernel matrix) satisfies, checked one by one in FP64 by the
-    oracle's reduced potential, the D equation
-        D_b = ln sum_k Omega_k exp(f_k - u_k(b))
-    at 200 sampled bins and the f equation
-        f_s - f_0 = -ln sum_b H_b exp(-u_s(b) - D_b) + ln sum_b H_b exp(-u_0(b) - D_b)
-    at 24 sampled states."""
+@pytest.fixture(scope="module")
+def fcc111_run():
+    """The 1024-replica fcc(111) workload (Nmax 512) after 2000 + 20000 sweeps."""
     p = W.fcc111_paper_scale(seed=0)
     rng = np.random.default_rng(0)
     pos, n = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=0)
@@ -188,8 +182,20 @@ def test_full_size_solve_satisfies_sampled_equations():
     g.run(2000)
     g.reset_histograms()
     g.run(20000)
-    h = g.histograms()
+    yield p, g, g.histograms()
     g.close()
+
+
+def test_full_size_solve_satisfies_sampled_equations(fcc111_run):
+    """The device solve over the full-size run's pooled bins (about 1e6 of
+    them, on the sparse kernel matrix) satisfies, checked one by one in FP64
+    by the oracle's reduced potential, the D equation
+        D_b = ln sum_k Omega_k exp(f_k - u_k(b))
+    at 200 sampled bins and the f equation
+        f_s - f_0 = -ln sum_b H_b exp(-u_s(b) - D_b) + ln sum_b H_b exp(-u_0(b) - D_b)
+    at 24 sampled states."""
+    p, _, h = fcc111_run
+    rng = np.random.default_rng(1)
     N_b, E_b, H_b = OM.occupied_bins(h["hNE"], p.e_lo, p.e_bin)
     kT_s, mu_s = np.repeat(p.kT, p.M), np.tile(p.mu, p.L)
     omega = h["omega"].astype(float)
@@ -206,6 +212,24 @@ def test_full_size_solve_satisfies_sampled_equations():
     u = OM.reduced_potential(kT_s[ss], mu_s[ss], p.lambda0, N_b, E_b)          # [24, B]
     f_o = -OM.lse(np.log(H_b)[None, :] - u - D[None, :], axis=1)
     np.testing.assert_allclose(f_o - f_o[0], f[ss], rtol=0, atol=1e-8)
+
+
+def test_warm_started_handle_reweight_reaches_the_same_fixed_point(fcc111_run):
+    """The handle's reweighting starts the full-size problem from the solve
+    with 16 energy bins merged; it reaches the fixed point the cold solve of
+    the same bins reaches, with fewer matrix builds."""
+    p, g, h = fcc111_run
+    N_b, E_b, H_b = OM.occupied_bins(h["hNE"], p.e_lo, p.e_bin)
+    kT_s, mu_s = np.repeat(p.kT, p.M), np.tile(p.mu, p.L)
+    f_c, _, _ = mbar_solve(kT_s, mu_s, p.lambda0, h["omega"].astype(float), N_b, E_b, H_b, tol=1e-11,
+                           max_iter=200000)
+    cold = mbar_last_info()
+    kq, mq = np.array([0.8, 1.2]), np.array([-4.0, -3.0])
+    _, _, f_w, _ = g.reweight(kq, mq, tol=1e-11, max_iter=200000)
+    warm = mbar_last_info()
+    assert warm["coarse_B"] > 0 and warm["coarse_B"] * 4 <= warm["B"] and warm["coarse_iterations"] > 0
+    assert cold["coarse_B"] == 0 and warm["builds"] < cold["builds"], (warm, cold)
+    np.testing.assert_allclose(f_w, f_c, rtol=0, atol=1e-7)
 
 
 def test_handle_reweight_matches_standalone_entry_points():
