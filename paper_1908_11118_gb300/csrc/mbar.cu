@@ -248,37 +248,103 @@ __global__ void __cluster_dims__(kFSplit, 1, 1) __launch_bounds__(kFThreads)
     cluster.sync();   // the partial sums stay readable until rank 0 has merged them
 }
 
-__global__ void __launch_bounds__(256) query_kernel(const __grid_constant__ MbarDev m, const double* a_q,
-                                                    const double* c_q, int nmax, double* n_mean,
-                                                    double* pN, double* f_q) {
-    extern __shared__ double hist[];   // [nmax + 1]
+// Reweighting to query state q = (a, c, c2): bin b weighs
+// H_b exp(-u_q(b) - D_b + f_q), f_q = -ln sum_b H_b exp(-u_q(b) - D_b), giving
+// <N>, p_N (Eq. textbook with the phase indicator chi_i = [N = i]) and, with
+// a second species (TWO), <N2> and p_N2.  Screened as the maps are, but per
+// phase: a binary32 pass finds the largest term of every N (and every N2),
+// and only the terms within kSkip + kMargin of the largest of their N (or of
+// their N2) are taken in FP64.  Each dropped term weighs below e^-50 of the
+// largest term of its own phase, so every p_N keeps its relative accuracy,
+// however small it is (the per-phase averages of the structure divide by
+// it).
+constexpr int kQThreads = 256;
+
+// atomic maximum of a binary32 value in shared memory (any sign, -inf start)
+__device__ __forceinline__ void atomic_max_f32(float* addr, float v) {
+    if (v >= 0.f) atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(kQThreads)
+    query_kernel(const __grid_constant__ MbarDev m, const double* a_q, const double* c_q, const double* c2_q,
+                 int nmax, double* n_mean, double* n2_mean, double* pN, double* pN2, double* f_q) {
+    // [nmax + 1] doubles of p_N (then of p_N2), [nmax + 1] floats of the
+    // largest screen value per N (then per N2)
+    extern __shared__ double hist[];
+    const int rows = nmax + 1, nh = (TWO ? 2 : 1) * rows;
+    float* rmax = reinterpret_cast<float*>(hist + nh);
     const int q = blockIdx.x;
-    const double a = a_q[q], c = c_q[q];
-    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) hist[n] = 0.0;
+    const double a = a_q[q], c = c_q[q], c2 = TWO ? c2_q[q] : 0.0;
+    const float a32 = (float)a, c32 = (float)c, c232 = (float)c2;
+    for (int n = threadIdx.x; n < nh; n += blockDim.x) {
+        hist[n] = 0.0;
+        rmax[n] = -INFINITY;
+    }
+    __syncthreads();
+    auto screen = [&](int b) {
+        const float2 en = m.EN32[b];
+        return -u32_of<TWO>(a32, c32, c232, en.x, en.y, TWO ? m.N2f[b] : 0.f) - m.DH32[b];
+    };
+    auto term = [&](int b) {
+        return m.lnH[b] - u_of<TWO>(a, c, c2, m.E_b[b], (double)m.N_b[b], TWO ? (double)m.N2_b[b] : 0.0) - m.D[b];
+    };
+    // a count beyond nmax (a caller's bins) shares the last row's threshold slot
+    auto row = [&](int n) { return min(max(n, 0), nmax); };
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x) {
+        const float x = screen(b);
+        atomic_max_f32(&rmax[row(m.N_b[b])], x);
+        if (TWO) atomic_max_f32(&rmax[rows + row(m.N2_b[b])], x);
+    }
+    __syncthreads();
+    constexpr float kCut = (float)kSkip + kMargin;
+    auto keep = [&](int b) {
+        const float x = screen(b);
+        return x > rmax[row(m.N_b[b])] - kCut || (TWO && x > rmax[rows + row(m.N2_b[b])] - kCut);
+    };
     Lse L{-INFINITY, 0.0};
     for (int b = threadIdx.x; b < m.B; b += blockDim.x)
-        lse_add(L, m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b]);
+        if (keep(b)) lse_add(L, term(b));
     L = block_merge(L);
     const double fq = -(L.m + log(L.s));
-    double nsum = 0.0;
+    double nsum = 0.0, n2sum = 0.0;
     __syncthreads();
     for (int b = threadIdx.x; b < m.B; b += blockDim.x) {
-        const double x = m.lnH[b] - fma(a, m.E_b[b], c * (double)m.N_b[b]) - m.D[b] + fq;
-        if (x > -745.0) {
-            const double w = exp(x);
-            const int n = m.N_b[b];
-            nsum += w * (double)n;
-            if (pN && n <= nmax) atomicAdd(&hist[n], w);
+        if (!keep(b)) continue;
+        const double w = exp(term(b) + fq);
+        const int n = m.N_b[b];
+        nsum = fma(w, (double)n, nsum);
+        if (pN && n <= nmax) atomicAdd(&hist[n], w);
+        if (TWO) {
+            const int n2 = m.N2_b[b];
+            n2sum = fma(w, (double)n2, n2sum);
+            if (pN2 && n2 <= nmax) atomicAdd(&hist[rows + n2], w);
         }
     }
     nsum = block_sum(nsum);
     __syncthreads();
+    if (TWO) n2sum = block_sum(n2sum);
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (n_mean) n_mean[q] = nsum;
+        if (TWO && n2_mean) n2_mean[q] = n2sum;
         if (f_q) f_q[q] = fq;
     }
-    if (pN)
-        for (int n = threadIdx.x; n <= nmax; n += blockDim.x) pN[size_t(q) * (nmax + 1) + n] = hist[n];
+    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) {
+        if (pN) pN[size_t(q) * rows + n] = hist[n];
+        if (TWO && pN2) pN2[size_t(q) * rows + n] = hist[rows + n];
+    }
+}
+
+// binary32 copies of the bins for the screening: (E, N), N2, D - lnH
+__global__ void prep32_kernel(int B, const double* E_b, const int* N_b, const int* N2_b, const double* D,
+                              const double* lnH, float2* EN32, float* N2f, float* DH32) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    EN32[b] = make_float2((float)E_b[b], (float)N_b[b]);
+    if (N2_b) N2f[b] = (float)N2_b[b];
+    DH32[b] = (float)(D[b] - lnH[b]);
 }
 
 // ------------------------------------------------------------- compaction
@@ -402,50 +468,6 @@ __global__ void prep_states2_kernel(int S, const double* kT, const double* mu2, 
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     c2[s] = 3.0 * (log(lambda0_2) - 0.5 * log(kT[s])) - mu2[s] / kT[s];
-}
-
-// Two species: the query of query_kernel with u = a E + c N + c2 N2, and the
-// distributions of both counts.
-__global__ void __launch_bounds__(256) query2_kernel(const __grid_constant__ MbarDev m, const double* a_q,
-                                                     const double* c_q, const double* c2_q, int nmax,
-                                                     double* n_mean, double* n2_mean, double* pN, double* pN2,
-                                                     double* f_q) {
-    extern __shared__ double hist2[];   // [2][nmax + 1]
-    const int q = blockIdx.x;
-    const double a = a_q[q], c = c_q[q], c2 = c2_q[q];
-    for (int n = threadIdx.x; n < 2 * (nmax + 1); n += blockDim.x) hist2[n] = 0.0;
-    Lse L{-INFINITY, 0.0};
-    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
-        lse_add(L, m.lnH[b] - u_of<true>(a, c, c2, m.E_b[b], (double)m.N_b[b], (double)m.N2_b[b]) - m.D[b]);
-    L = block_merge(L);
-    const double fq = -(L.m + log(L.s));
-    double nsum = 0.0, n2sum = 0.0;
-    __syncthreads();
-    for (int b = threadIdx.x; b < m.B; b += blockDim.x) {
-        const double x =
-            m.lnH[b] - u_of<true>(a, c, c2, m.E_b[b], (double)m.N_b[b], (double)m.N2_b[b]) - m.D[b] + fq;
-        if (x > -745.0) {
-            const double w = exp(x);
-            const int n = m.N_b[b], n2 = m.N2_b[b];
-            nsum += w * (double)n;
-            n2sum += w * (double)n2;
-            if (n <= nmax) atomicAdd(&hist2[n], w);
-            if (n2 <= nmax) atomicAdd(&hist2[nmax + 1 + n2], w);
-        }
-    }
-    nsum = block_sum(nsum);
-    __syncthreads();
-    n2sum = block_sum(n2sum);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (n_mean) n_mean[q] = nsum;
-        if (n2_mean) n2_mean[q] = n2sum;
-        if (f_q) f_q[q] = fq;
-    }
-    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) {
-        if (pN) pN[size_t(q) * (nmax + 1) + n] = hist2[n];
-        if (pN2) pN2[size_t(q) * (nmax + 1) + n] = hist2[nmax + 1 + n];
-    }
 }
 
 __global__ void prep_bins_kernel(int B, const double* H, double* lnH) {
@@ -1363,10 +1385,16 @@ cudaError_t mbar_solve_warm_dev(const MbarDev& m, double width, double tol, int 
 cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, int nmax,
                            double* n_mean, double* pN, double* f_q, cudaStream_t s) {
     if (Q <= 0) return cudaSuccess;
-    const size_t smem = size_t(nmax + 1) * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = size_t(nmax + 1) * (sizeof(double) + sizeof(float));
+    cudaError_t err = cudaFuncSetAttribute(query_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    query_kernel<<<Q, 256, smem, s>>>(m, a_q, c_q, nmax, n_mean, pN, f_q);
+    query_kernel<false><<<Q, kQThreads, smem, s>>>(m, a_q, c_q, nullptr, nmax, n_mean, nullptr, pN, nullptr, f_q);
+    return cudaGetLastError();
+}
+
+cudaError_t mbar_prep32_dev(const MbarDev& m, cudaStream_t s) {
+    if (m.B <= 0) return cudaSuccess;
+    prep32_kernel<<<(m.B + 255) / 256, 256, 0, s>>>(m.B, m.E_b, m.N_b, m.N2_b, m.D, m.lnH, m.EN32, m.N2f, m.DH32);
     return cudaGetLastError();
 }
 
@@ -1409,10 +1437,10 @@ cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const do
                             int nmax, double* n_mean, double* n2_mean, double* pN, double* pN2, double* f_q,
                             cudaStream_t s) {
     if (Q <= 0) return cudaSuccess;
-    const size_t smem = 2 * size_t(nmax + 1) * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(query2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = 2 * size_t(nmax + 1) * (sizeof(double) + sizeof(float));
+    cudaError_t err = cudaFuncSetAttribute(query_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    query2_kernel<<<Q, 256, smem, s>>>(m, a_q, c_q, c2_q, nmax, n_mean, n2_mean, pN, pN2, f_q);
+    query_kernel<true><<<Q, kQThreads, smem, s>>>(m, a_q, c_q, c2_q, nmax, n_mean, n2_mean, pN, pN2, f_q);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,9 @@ cudaError_t mbar_solve_warm_dev(const MbarDev& m, double width, double tol, int 
                                 cudaStream_t s);
 
 // Reweight to Q query states given on the device as (a_q, c_q):
-// N_mean [Q], pN [Q][nmax+1], f_q [Q] (device, any may be null).
+// N_mean [Q], pN [Q][nmax+1], f_q [Q] (device, any may be null).  Reads the
+// binary32 copies EN32, DH32 (and N2f) that a solve leaves, or that
+// mbar_prep32_dev writes from the FP64 bins and D.
 cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q,
                            int nmax, double* N_mean, double* pN, double* f_q, cudaStream_t s);
 
@@ -79,6 +81,10 @@ cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const dou
 cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, const double* c2_q,
                             int nmax, double* N_mean, double* N2_mean, double* pN, double* pN2, double* f_q,
                             cudaStream_t s);
+
+// The binary32 copies of the bins the query screens with: EN32, N2f (when
+// N2_b is set) and DH32 = D - lnH, from E_b, N_b, N2_b, D and lnH.
+cudaError_t mbar_prep32_dev(const MbarDev& m, cudaStream_t s);
 
 // c2 = 3 ln(lambda0_2 / sqrt(kT)) - mu2 / kT of a second species, per state (device).
 cudaError_t mbar_prep_states2(int S, const double* kT, const double* mu2, double lambda0_2, double* c2,

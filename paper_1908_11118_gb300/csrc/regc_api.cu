@@ -1737,7 +1737,11 @@ regc_status regc_mbar_query(int Q, const double* kT_q, const double* mu_q, doubl
     m.E_b = d_E;
     m.lnH = lnH;
     m.D = d_D;
-    e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
+    m.EN32 = buf.get<float2>(B);
+    m.DH32 = buf.get<float>(B);
+    if (buf.err != cudaSuccess) return status_of(buf.err);
+    e = mbar_prep32_dev(m, s);
+    if (e == cudaSuccess) e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
     if (e == cudaSuccess && N_mean) e = cudaMemcpyAsync(N_mean, d_nm, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && pN)
         e = cudaMemcpyAsync(pN, d_pn, (size_t)Q * (nmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, s);
