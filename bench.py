@@ -42,9 +42,9 @@ import workloads as W  # noqa: E402
 SWEEPS_PER_STEP = 10
 # DRAM bytes (read + write) of one sweep-kernel launch on the benchmark
 # workload from an ncu capture of the current kernel
-# (dram__bytes_read.sum 4343040 + dram__bytes_write.sum 0); None whenever the
+# (dram__bytes_read.sum 4342016 + dram__bytes_write.sum 256); None whenever the
 # kernel has changed since its last capture
-SWEEP_TRAFFIC_BYTES = 4343040 + 0
+SWEEP_TRAFFIC_BYTES = 4342016 + 256
 FLOPS_PER_PAIR = 20            # dx,dy,dz 3, xy minimum image 4, r^2 5, r^-2 1, s^6 3, 4eps s^6(s^6-1) 4
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 METRIC = "GCMC trial moves/s over all replicas"
@@ -77,6 +77,8 @@ def parse_args(argv=None):
     ap.add_argument("--two-species", type=int, default=1, help="1: add the two-species workload")
     ap.add_argument("--two-species-steps", type=int, default=20)
     ap.add_argument("--two-species-sweeps", type=int, default=100000)
+    ap.add_argument("--cluster-production", type=int, default=20000,
+                    help="sweeps of configuration 5 with the surrogate in a batch (0: skip; 1e6 is the full run)")
     ap.add_argument("--da-train-steps", type=int, default=3000)
     ap.add_argument("--da-steps-small", type=int, default=1000)
     ap.add_argument("--da-steps-large", type=int, default=60)
@@ -264,18 +266,10 @@ def timed_run(g, torch, stream, flush, steps, n_batches):
     return secs, int(mv[:, :, 0].sum()), int(mv[:, :, 1].sum()), pr, np.array(nb)
 
 
-def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_steps, timed_steps, seed=0):
-    """Train the surrogate on rows the plain sampler generates, then time the
-    plain and the delayed-acceptance sweep from the same state."""
-    from paper_1908_11118_gb300 import Regc
-
-    rng = np.random.default_rng(seed)
-    if p.n_cluster:
-        pos0, n0 = W.cluster_initial(p, rng.integers(0, (p.nmax - p.n_cluster) // 2 + 1, p.S), seed=seed)
-    else:
-        pos0, n0 = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=seed)
-    g = Regc(p, stream=stream)
-    g.set_walkers(pos0, n0)
+def harvest_and_train(g, p, torch, rows_target, train_steps, seed=0):
+    """The surrogate of a handle: initialised from the seed, 200 plain sweeps,
+    then rows harvested every 10 sweeps until rows_target, then train_steps
+    Adam steps on 1024-row mini-batches."""
     g.surrogate_init(seed=seed, scale=1.0)
     g.run(200, exchange_every=SWEEPS_PER_STEP)
     per = p.S * sum(DA_ROWS_PER_WALKER)
@@ -291,6 +285,25 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
     t0 = time.perf_counter()
     loss = g.surrogate_train(train_steps, 1024, 1e-3)
     t_train = time.perf_counter() - t0
+    return {"rows": rows, "harvests": harvests, "rows_per_walker_per_harvest": list(DA_ROWS_PER_WALKER),
+            "target_clip": DA_CLIP, "steps": train_steps, "batch": 1024, "lr": 1e-3,
+            "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-100:])),
+            "harvest_s": t_harvest, "train_s": t_train}
+
+
+def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_steps, timed_steps, seed=0):
+    """Train the surrogate on rows the plain sampler generates, then time the
+    plain and the delayed-acceptance sweep from the same state."""
+    from paper_1908_11118_gb300 import Regc
+
+    rng = np.random.default_rng(seed)
+    if p.n_cluster:
+        pos0, n0 = W.cluster_initial(p, rng.integers(0, (p.nmax - p.n_cluster) // 2 + 1, p.S), seed=seed)
+    else:
+        pos0, n0 = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos0, n0)
+    training = harvest_and_train(g, p, torch, rows_target, train_steps, seed)
     state = g.get_walkers()
     res, se_of, mean_of = {}, {}, {}
     for mode in ("plain", "delayed"):
@@ -319,10 +332,7 @@ def delayed_acceptance_arm(p, name, torch, stream, flush, rows_target, train_ste
         res[mode]["seconds_to_stderr_2pct_all_states"] = float(res[mode]["seconds"] * np.max((se / tgt) ** 2))
     return {
         "workload": name,
-        "training": {"rows": rows, "harvests": harvests, "rows_per_walker_per_harvest": list(DA_ROWS_PER_WALKER),
-                     "target_clip": DA_CLIP, "steps": train_steps, "batch": 1024, "lr": 1e-3,
-                     "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-100:])),
-                     "harvest_s": t_harvest, "train_s": t_train},
+        "training": training,
         "plain": pl, "delayed": da,
         "trial_moves_ratio": da["trial_moves_per_s"] / pl["trial_moves_per_s"],
         "accepted_moves_ratio": da["accepted_moves_per_s"] / pl["accepted_moves_per_s"],
@@ -341,6 +351,79 @@ CLUSTER_WORKLOAD = ("15 sigma periodic cube, A4 cluster (eps_AA 4, sigma_AA 1.1;
 BATCH_WORKLOAD = ("256 systems x (4 kT x 4 mu) = 4096 replicas; 3-layer fcc(100) slabs of nx x ny atoms, "
                   "nx, ny ~ U{6..16}; gas 8-16 high; Nmax = 2^k, k ~ U{6..11}; N0 ~ U{0..Nmax/2} capped at "
                   "90% of a 1.1-spacing lattice; step = 10 sweeps + 1 exchange attempt per system")
+
+
+def cluster_production_arm(torch, stream, sweeps, rows_target, train_steps, equil=500, seed=0):
+    """Configuration 5's production: the 4096-replica cluster-in-gas grid
+    sampled with the trained surrogate (delayed acceptance) through a batch
+    (the persistent delayed-acceptance kernel in a captured graph, shape
+    autotuned), `sweeps` sweeps with per-state energy windows (KS check of
+    the two halves, Sec. III.A), then the pooled (N_B, E) histogram reweighted
+    in FP64 (Sec. II.B) to <N_B> on a (T, p) grid (mu from p by the ideal-gas
+    reservoir of Sec. III.A)."""
+    from paper_1908_11118_gb300 import Batch, Regc, mu_of_pressure
+
+    p = W.cluster_in_gas(seed=seed)
+    rng = np.random.default_rng(seed)
+    pos0, n0 = W.cluster_initial(p, rng.integers(0, (p.nmax - p.n_cluster) // 2 + 1, p.S), seed=seed)
+    g = Regc(p, stream=stream)
+    g.set_walkers(pos0, n0)
+    training = harvest_and_train(g, p, torch, rows_target, train_steps, seed)
+    g.set_mode(True)
+    g.run(equil, exchange_every=SWEEPS_PER_STEP)
+    bt = Batch([g], sweeps_per_step=SWEEPS_PER_STEP, stream=stream)
+    bt.autotune(1)
+    plan = bt.plan()
+    g.set_state_windows(1024, 0.25, None)
+    g.reset_histograms()
+    mv0 = g.counters()
+    torch.cuda.synchronize()
+    steps = max(2, sweeps // SWEEPS_PER_STEP)
+    chunk = 100
+    half = None
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        k = min(chunk, steps - done)
+        bt.run(k)
+        done += k
+        if half is None and done >= steps // 2:
+            bt.sync()
+            half = g.state_histograms()[0]
+    bt.sync()
+    run_s = time.perf_counter() - t0
+    full = g.state_histograms()[0]
+    bt.close()
+    mv1 = g.counters()
+    ks, crit = ks_halves(half, full - half)
+    h = g.histograms()
+    kT_q = np.geomspace(0.6, 1.5, 12)
+    kT_mid = float(np.sqrt(0.6 * 1.5))
+    p_lo, p_hi = (kT_mid * np.exp(np.array([-6.0, -2.0]) / kT_mid) / (p.lambda0 / np.sqrt(kT_mid)) ** 3)
+    p_q = np.geomspace(p_lo, p_hi, 12)
+    T, P = np.meshgrid(kT_q, p_q, indexing="ij")
+    mu_q = mu_of_pressure(T.ravel(), P.ravel(), p.lambda0)
+    t1 = time.perf_counter()
+    nm, pN, f, iters = g.reweight(T.ravel(), mu_q, tol=1e-9, max_iter=200000)
+    rw_s = time.perf_counter() - t1
+    mbar = mbar_summary()
+    trials = int((mv1[0][:, :, 0] - mv0[0][:, :, 0]).sum())
+    screened = int(mv1[2][4] - mv0[2][4])
+    passed = int(mv1[2][5] - mv0[2][5])
+    g.set_mode(False)
+    g.close()
+    return {"workload": CLUSTER_WORKLOAD, "sampler": "delayed acceptance (trained surrogate) in a batch",
+            "training": training, "equilibration_sweeps": equil, "sweeps": steps * SWEEPS_PER_STEP,
+            "batch_plan": plan, "run_s": run_s, "trial_moves_per_s": trials / run_s,
+            "screen_pass_fraction": passed / max(screened, 1),
+            "observations": int(h["omega"].sum()), "pooled_bins_occupied": int(np.count_nonzero(h["hNE"])),
+            "e_out": int(h["e_out"].sum()),
+            "convergence_ks_halves": {"median": float(np.median(ks)), "max": float(np.max(ks)),
+                                      "states_unchanged_at_1pct": int(np.sum(ks < crit))},
+            "reweight_s": rw_s, "mbar_iterations": iters, "mbar": mbar,
+            "phase_map": {"kT": kT_q.tolist(), "p": p_q.tolist(),
+                          "N_B_mean": nm.reshape(12, 12).round(3).tolist(),
+                          "N_B_most_probable": np.argmax(pN, axis=1).reshape(12, 12).tolist()}}
 
 
 def batched_uneven_arm(torch, steps, seed=0):
@@ -948,6 +1031,11 @@ def run_own(args):
     if args.production > 0 and rank == 0:
         production = production_arm(torch, stream, args.production)
 
+    cluster_prod = None
+    if args.cluster_production > 0 and rank == 0:
+        cluster_prod = cluster_production_arm(torch, stream, args.cluster_production, 1_000_000,
+                                              args.da_train_steps)
+
     two = None
     if args.two_species and rank == 0:
         two = two_species_arm(torch, stream, flush, args.two_species_steps, args.two_species_sweeps)
@@ -994,6 +1082,7 @@ def run_own(args):
             "paper_lj_cycle": paper,
             "production_phase_map": production,
             "two_species": two,
+            "cluster_production": cluster_prod,
         }
         print(json.dumps(line), flush=True)
     g.close()

@@ -206,6 +206,16 @@ REGC_API regc_status regc_init_grid2(const regc_potential *pot, const regc_surfa
  * the handle's sticky status. */
 REGC_API regc_status regc_sweep(regc_handle *h, int n_sweeps);
 
+/* Failure-detection test hook (no paper counterpart): the next regc_sweep
+ * on h launches with its walkers issuing no bulk copy of their positions, so
+ * each walker's bounded wait on that copy (about 1 s of clock cycles, taken
+ * twice) expires, the walker stops without touching its state, and the
+ * handle's status becomes REGC_ETIMEOUT (sticky), reported by the next call
+ * that synchronises.  No GPU fault, trap or hang is involved: the wait ends
+ * by its own budget and the CUDA context stays usable.  Errors: REGC_EINVAL
+ * (h NULL). */
+REGC_API regc_status regc_test_expire_waits(regc_handle *h);
+
 /* As regc_sweep, and write one record per trial move to host memory:
  * trace is [S walkers][n_sweeps][moves_per_sweep].  Synchronous.  Intended
  * for move-by-move comparison with a reference implementation. */

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -26,6 +27,8 @@ constexpr size_t kMaxSmem = 232448;  // 227 KB per block on sm_103a
 
 struct Bucket {
     int nmax = 0;
+    bool da = false;                // its systems sample with delayed acceptance
+    bool cl = false;                // its systems carry a cluster species
     int region = 0;                 // dynamic shared memory per walker (bytes)
     std::vector<int2> items;        // (system, walker), largest systems first
     int2* d_items = nullptr;
@@ -39,6 +42,7 @@ struct Bucket {
 struct regc_batch {
     cudaStream_t stream = nullptr;
     std::vector<regc_handle*> members;
+    std::vector<char> member_da;    // a member's sampling mode at creation (1: delayed acceptance)
     int sweeps_per_step = 1;
     int sms = 1;
     SweepParams* d_sys = nullptr;
@@ -46,6 +50,7 @@ struct regc_batch {
     uint32_t* d_ectr = nullptr;
     int* d_counters = nullptr;
     std::vector<uint32_t> t_mirror, e_mirror;   // counters as held on the device
+    std::vector<SweepParams> sys_host;          // the parameters as uploaded (t0 as at the upload)
     std::vector<Bucket> buckets;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
@@ -72,6 +77,16 @@ void drop_graph(regc_batch* b) {
     b->graph = nullptr;
 }
 
+// A member's sweep parameters as the batch runs them.
+SweepParams batch_params(const regc_batch* b, const regc_handle* h) {
+    SweepParams P = h->P;
+    P.t0 = h->t;
+    P.n_sweeps = b->sweeps_per_step;
+    P.trace = nullptr;
+    P.expire_waits = 0;
+    return P;
+}
+
 // Upload every member's sweep and exchange parameters with its current
 // Philox counters (the members may have been stepped on their own since).
 cudaError_t upload_descriptors(regc_batch* b) {
@@ -80,14 +95,12 @@ cudaError_t upload_descriptors(regc_batch* b) {
     std::vector<ExchangeParams> xp(n);
     for (size_t m = 0; m < n; ++m) {
         regc_handle* h = b->members[m];
-        sys[m] = h->P;
-        sys[m].t0 = h->t;
-        sys[m].n_sweeps = b->sweeps_per_step;
-        sys[m].trace = nullptr;
+        sys[m] = batch_params(b, h);
         xp[m] = h->X;
         b->t_mirror[m] = h->t;
         b->e_mirror[m] = h->e;
     }
+    b->sys_host = sys;
     cudaError_t e = cudaMemcpyAsync(b->d_sys, sys.data(), n * sizeof(SweepParams), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_xp, xp.data(), n * sizeof(ExchangeParams), cudaMemcpyHostToDevice, b->stream);
@@ -122,7 +135,7 @@ cudaError_t record_step(regc_batch* b, std::vector<double>* ms_out) {
         for (int k = 0; k < nb && e == cudaSuccess; ++k) {
             const Bucket& q = b->buckets[k];
             e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.grid,
-                                   q.region, b->stream);
+                                   q.region, q.da, q.cl, b->stream);
             if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], b->stream);
         }
         if (e == cudaSuccess)
@@ -145,7 +158,7 @@ cudaError_t record_step(regc_batch* b, std::vector<double>* ms_out) {
         if (k > 0) e = cudaStreamWaitEvent(s, b->fork, 0);
         if (e == cudaSuccess)
             e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.grid,
-                                   q.region, s);
+                                   q.region, q.da, q.cl, s);
         if (e == cudaSuccess && k > 0) e = cudaEventRecord(b->join[k], s);
     }
     for (int k = 1; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->stream, b->join[k], 0);
@@ -171,15 +184,23 @@ cudaError_t build_graph(regc_batch* b) {
     return cudaGraphInstantiate(&b->exec, g, 0);
 }
 
-// Members must still be plain-mode handles without errors; re-upload the
-// descriptors if any member was stepped on its own since the last batch step.
+// Members must keep the sampling mode, Nmax and species they had at
+// creation and have no errors; re-upload the descriptors if any member was
+// stepped on its own since the last batch step or its parameters changed
+// (per-state energy windows set, say; a retrained network is read in place).
 regc_status check_members(regc_batch* b) {
     bool stale = false;
     for (size_t m = 0; m < b->members.size(); ++m) {
         regc_handle* h = b->members[m];
         if (h->sticky != REGC_OK) return h->sticky;
-        if (h->P.delayed || h->need_walkers) return REGC_EINVAL;
+        if ((h->P.delayed != 0) != (b->member_da[m] != 0) || h->need_walkers) return REGC_EINVAL;
+        if (h->nmax != b->sys_host[m].nmax || (h->P.n_cluster > 0) != (b->sys_host[m].n_cluster > 0) ||
+            h->P.gc2)
+            return REGC_EINVAL;
         if (h->t != b->t_mirror[m] || h->e != b->e_mirror[m]) stale = true;
+        SweepParams now = batch_params(b, h);
+        now.t0 = b->sys_host[m].t0;   // the device advances t0 itself
+        if (memcmp(&now, &b->sys_host[m], sizeof(SweepParams)) != 0) stale = true;
     }
     if (stale) return fail(b, upload_descriptors(b));
     return REGC_OK;
@@ -214,7 +235,8 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     *out = nullptr;
     if (!handles || count < 1 || sweeps_per_step < 1) return REGC_EINVAL;
     for (int i = 0; i < count; ++i) {
-        if (!handles[i] || handles[i]->P.delayed || handles[i]->need_walkers || handles[i]->P.gc2) return REGC_EINVAL;
+        if (!handles[i] || handles[i]->need_walkers || handles[i]->P.gc2) return REGC_EINVAL;
+        if (handles[i]->P.delayed && !handles[i]->has_sur) return REGC_EINVAL;
         if (handles[i]->sticky != REGC_OK) return handles[i]->sticky;
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return REGC_EINVAL;
@@ -223,6 +245,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     if (!b) return REGC_ENOMEM;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->members.assign(handles, handles + count);
+    for (int i = 0; i < count; ++i) b->member_da.push_back(handles[i]->P.delayed ? 1 : 0);
     cudaError_t e = cudaSuccess;
     if (!b->stream) {
         // the legacy default stream cannot be captured: use a stream of our own
@@ -236,13 +259,15 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    // size classes by Nmax; within a class the largest systems first
-    std::map<int, std::vector<int>> by_nmax;
-    for (int m = 0; m < count; ++m) by_nmax[handles[m]->nmax].push_back(m);
-    const size_t stat = batch_static_smem();
+    // size classes by (Nmax, sampling mode, cluster); within a class the largest systems first
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_nmax;
+    for (int m = 0; m < count; ++m)
+        by_nmax[{handles[m]->nmax, b->member_da[m], handles[m]->P.n_cluster > 0 ? 1 : 0}].push_back(m);
     for (auto it = by_nmax.rbegin(); it != by_nmax.rend(); ++it) {
         Bucket q;
-        q.nmax = it->first;
+        q.nmax = std::get<0>(it->first);
+        q.da = std::get<1>(it->first) != 0;
+        q.cl = std::get<2>(it->first) != 0;
         std::vector<int> ms = it->second;
         size_t region = 0;
         for (int m : ms) region = std::max(region, handles[m]->smem_per_walker);
@@ -254,13 +279,14 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
             for (int w = 0; w < handles[m]->S; ++w) q.items.push_back(make_int2(m, w));
         b->buckets.push_back(q);
     }
-    if (e == cudaSuccess) e = batch_prepare((int)(kMaxSmem - stat));
+    if (e == cudaSuccess) e = batch_prepare((int)kMaxSmem);
     // feasible shapes, and the default: the most resident walkers per SM
     for (auto& q : b->buckets) {
         int best = 0;
-        for (int wpc = 1; wpc <= batch_max_warps() && e == cudaSuccess; wpc *= 2) {
+        const size_t stat = batch_static_smem(q.da);
+        for (int wpc = 1; wpc <= batch_max_warps(q.da) && e == cudaSuccess; wpc *= 2) {
             if ((size_t)wpc * q.region + stat > kMaxSmem) break;
-            const int occ = batch_occupancy(wpc, q.region);
+            const int occ = batch_occupancy(wpc, q.region, q.da, q.cl);
             if (occ < 1) break;
             q.cand_wpc.push_back(wpc);
             if (wpc * occ > best) {
@@ -269,7 +295,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
             }
         }
         if (q.cand_wpc.empty()) e = cudaErrorInvalidValue;   // one walker does not fit
-        const int occ = batch_occupancy(q.wpc, q.region);
+        const int occ = batch_occupancy(q.wpc, q.region, q.da, q.cl);
         const int need = (int)((q.items.size() + q.wpc - 1) / q.wpc);
         q.grid = std::max(1, std::min(need, b->sms * std::max(occ, 1)));
     }
@@ -349,7 +375,7 @@ regc_status regc_batch_autotune(regc_batch* b, int rounds) {
         for (size_t c = 0; c < n_cand; ++c) {
             for (auto& q : b->buckets) {
                 const int wpc = q.cand_wpc[std::min(c, q.cand_wpc.size() - 1)];
-                const int occ = batch_occupancy(wpc, q.region);
+                const int occ = batch_occupancy(wpc, q.region, q.da, q.cl);
                 const int need = (int)((q.items.size() + wpc - 1) / wpc);
                 q.wpc = wpc;
                 q.grid = std::max(1, std::min(need, b->sms * std::max(occ, 1)));

@@ -83,6 +83,7 @@ struct regc_handle {
     std::vector<double> mu2_state;            // per state: mu of species C (two species)
     double* d_mu2_state = nullptr;
     double lambda0_2 = 1.0;                   // Lambda_C at kT = 1
+    bool expire_next = false;                 // regc_test_expire_waits: the next regc_sweep
 };
 
 // Synchronise the handle's stream and fold its device error word into the

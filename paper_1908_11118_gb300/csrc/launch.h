@@ -29,23 +29,26 @@ cudaError_t pack_walkers(const float* xyz, const int* n, int S, int nmax, const 
 cudaError_t unpack_walkers(const float4* pos, long long count, float* xyz, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch
-// Static shared memory of the batch sweep kernel and its warp limit per CTA.
-size_t batch_static_smem();
-int batch_max_warps();
+// Static shared memory of the batch sweep kernel and its warp limit per CTA
+// (da: the delayed-acceptance instantiation).
+size_t batch_static_smem(bool da);
+int batch_max_warps(bool da);
 
 // Persistent sweep of items (system, walker) of the systems sys[] (device
 // table; every system's n_sweeps and t0 are read from it), taken in order from
 // the queue *counter (zero before the launch); warps_per_cta walkers per CTA,
-// each with `region` bytes of dynamic shared memory.
+// each with `region` bytes of dynamic shared memory.  da: every system of the
+// items samples with delayed acceptance; cl: every system carries a cluster
+// species.
 cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
-                               int warps_per_cta, int grid, int region, cudaStream_t s);
+                               int warps_per_cta, int grid, int region, bool da, bool cl, cudaStream_t s);
 
-// Allow the batch sweep kernel up to max_dynamic_smem bytes of dynamic shared
-// memory (before any launch or capture that needs more than 48 KB).
-cudaError_t batch_prepare(int max_dynamic_smem);
+// Allow every batch sweep kernel up to max_smem bytes of shared memory in all
+// (before any launch or capture that needs more than 48 KB).
+cudaError_t batch_prepare(int max_smem);
 
 // Resident CTAs per SM of the batch sweep kernel for this shape (0 if none fit).
-int batch_occupancy(int warps_per_cta, int region);
+int batch_occupancy(int warps_per_cta, int region, bool da, bool cl);
 
 // One exchange attempt of every system's grid (attempt numbers e_ctr[]), then
 // e_ctr[m] += 1 and sys[m].t0 += n_sweeps on the device.

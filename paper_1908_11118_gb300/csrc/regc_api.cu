@@ -563,9 +563,17 @@ regc_status regc_sweep(regc_handle* h, int n_sweeps) {
     P.t0 = h->t;
     P.n_sweeps = n_sweeps;
     P.trace = nullptr;
+    P.expire_waits = h->expire_next ? 1 : 0;
+    h->expire_next = false;
     const regc_status st = cuda_fail(h, launch_sweep(P, h->stream));
     if (st == REGC_OK) h->t += (uint32_t)n_sweeps;
     return st;
+}
+
+regc_status regc_test_expire_waits(regc_handle* h) {
+    if (!h) return REGC_EINVAL;
+    h->expire_next = true;
+    return REGC_OK;
 }
 
 regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* trace) {

@@ -131,6 +131,9 @@ struct SweepParams {
     // taken per walker.  A grand-canonical move picks its species by bit 30
     // of Philox word B2 (0: B, 1: C).
     int gc2;
+    // failure-detection test hook: the walkers issue no bulk copy of their
+    // positions, so their bounded waits on it expire (ERR_TIMEOUT)
+    int expire_waits;
     int* nb;               // [S] species-B count of each walker
     const double* c_ins2;  // [S] ln V - 3 ln Lambda_C,s + beta_s mu2_s
     const double* c_del2;  // [S] 3 ln Lambda_C,s - ln V - beta_s mu2_s

@@ -721,7 +721,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             // the region may have been read and written by ordinary accesses
             // (a previous walker): order those before the asynchronous copy
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_load(S.pos, gpos, uint32_t(N) * 16u, S.bar);
+            if (!P.expire_waits) bulk_load(S.pos, gpos, uint32_t(N) * 16u, S.bar);
         }
         group_sync<K>();
         const bool ok = mbar_wait_bounded(S.bar);
@@ -1218,14 +1218,19 @@ cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
 // from the queue, the warp copies that system's parameters into its slot of
 // shared memory and runs the walker's sweeps in its own shared-memory region
 // of `region` bytes; items are listed largest first, so the queue balances
-// the uneven costs.
+// the uneven costs.  DA: the systems of the launch sample with delayed
+// acceptance (their networks' fragments take ~240 registers per thread, so
+// at most kBatchMaxWarpsDA walkers per CTA); CL: every system of the launch
+// carries a cluster species.
 constexpr int kBatchMaxWarps = 16;
+constexpr int kBatchMaxWarpsDA = 4;
 
-__global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_sweep_kernel(const SweepParams* __restrict__ sys,
-                                                                        const int2* __restrict__ items, int n_items,
-                                                                        int* counter, int region) {
+template <bool DA, bool CL>
+__global__ void __launch_bounds__(32 * (DA ? kBatchMaxWarpsDA : kBatchMaxWarps))
+    batch_sweep_kernel(const SweepParams* __restrict__ sys, const int2* __restrict__ items, int n_items,
+                       int* counter, int region) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ SweepParams Psh[kBatchMaxWarps];
+    __shared__ SweepParams Psh[DA ? kBatchMaxWarpsDA : kBatchMaxWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* mine = smem + (size_t)warp * region;
     for (;;) {
@@ -1238,37 +1243,68 @@ __global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_sweep_kernel(const 
         int* dst = reinterpret_cast<int*>(&Psh[warp]);
         for (int k = lane; k < (int)(sizeof(SweepParams) / sizeof(int)); k += 32) dst[k] = src[k];
         __syncwarp();
-        if (Psh[warp].n_cluster > 0) walker_sweep<1, false, false, true>(Psh[warp], mw.y, mine, lane);
-        else walker_sweep<1, false, false, false>(Psh[warp], mw.y, mine, lane);
+        walker_sweep<1, false, DA, CL>(Psh[warp], mw.y, mine, lane);
         __syncwarp();
     }
 }
 
 }  // namespace
 
-size_t batch_static_smem() { return sizeof(SweepParams) * kBatchMaxWarps; }
+size_t batch_static_smem(bool da) { return sizeof(SweepParams) * (da ? kBatchMaxWarpsDA : kBatchMaxWarps); }
 
-int batch_max_warps() { return kBatchMaxWarps; }
+int batch_max_warps(bool da) { return da ? kBatchMaxWarpsDA : kBatchMaxWarps; }
 
-cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
-                               int warps_per_cta, int grid, int region, cudaStream_t s) {
-    if (n_items <= 0) return cudaSuccess;
-    if (warps_per_cta < 1 || warps_per_cta > kBatchMaxWarps || grid < 1) return cudaErrorInvalidValue;
+namespace {
+
+template <bool DA, bool CL>
+cudaError_t launch_batch_k(const SweepParams* sys, const int2* items, int n_items, int* counter, int warps_per_cta,
+                           int grid, int region, cudaStream_t s) {
     const size_t smem = (size_t)warps_per_cta * region;
-    batch_sweep_kernel<<<grid, 32 * warps_per_cta, smem, s>>>(sys, items, n_items, counter, region);
+    batch_sweep_kernel<DA, CL><<<grid, 32 * warps_per_cta, smem, s>>>(sys, items, n_items, counter, region);
     return cudaGetLastError();
 }
 
-cudaError_t batch_prepare(int max_dynamic_smem) {
-    return cudaFuncSetAttribute(batch_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
+template <bool DA, bool CL>
+cudaError_t prepare_k(int max_smem) {
+    return cudaFuncSetAttribute(batch_sweep_kernel<DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem - (int)batch_static_smem(DA));
 }
 
-int batch_occupancy(int warps_per_cta, int region) {
-    const size_t smem = (size_t)warps_per_cta * region;   // within the limit batch_prepare set
+template <bool DA, bool CL>
+int occupancy_k(int warps_per_cta, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_sweep_kernel, 32 * warps_per_cta, smem) != cudaSuccess)
-        return 0;
-    return n;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_sweep_kernel<DA, CL>, 32 * warps_per_cta, smem) ==
+                   cudaSuccess
+               ? n
+               : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
+                               int warps_per_cta, int grid, int region, bool da, bool cl, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (warps_per_cta < 1 || warps_per_cta > batch_max_warps(da) || grid < 1) return cudaErrorInvalidValue;
+    if (da) {
+        return cl ? launch_batch_k<true, true>(sys, items, n_items, counter, warps_per_cta, grid, region, s)
+                  : launch_batch_k<true, false>(sys, items, n_items, counter, warps_per_cta, grid, region, s);
+    }
+    return cl ? launch_batch_k<false, true>(sys, items, n_items, counter, warps_per_cta, grid, region, s)
+              : launch_batch_k<false, false>(sys, items, n_items, counter, warps_per_cta, grid, region, s);
+}
+
+cudaError_t batch_prepare(int max_smem) {
+    cudaError_t e = prepare_k<false, false>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<false, true>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<true, false>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<true, true>(max_smem);
+    return e;
+}
+
+int batch_occupancy(int warps_per_cta, int region, bool da, bool cl) {
+    const size_t smem = (size_t)warps_per_cta * region;   // within the limit batch_prepare set
+    if (da) return cl ? occupancy_k<true, true>(warps_per_cta, smem) : occupancy_k<true, false>(warps_per_cta, smem);
+    return cl ? occupancy_k<false, true>(warps_per_cta, smem) : occupancy_k<false, false>(warps_per_cta, smem);
 }
 
 size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker) {

@@ -407,6 +407,11 @@ class Regc:
                                        C.byref(it)), "regc_reweight")
         return nm, pN, f, it.value
 
+    def test_expire_waits(self):
+        """Failure-detection test hook (regc_test_expire_waits): the next sweep's
+        bounded waits expire and the handle reports REGC_ETIMEOUT."""
+        check(_lib.lib().regc_test_expire_waits(self._h), "regc_test_expire_waits")
+
     def reweight2(self, kT_q, mu_q, mu2_q, tol: float = 1e-10, max_iter: int = 100000):
         """Two species: (NB_mean, NC_mean, pNB, pNC, f_states, iterations) at
         the query states (kT_q, mu_q, mu2_q)."""

@@ -7,7 +7,10 @@ on every member with the same Philox streams, so:
     histograms, moments and counters -- to stepping the members one by one;
   * every member's final state equals the FP64 oracle's for the same steps;
   * stepping a member on its own between batch steps is picked up;
-  * a member in delayed-acceptance mode is refused.
+  * members in delayed-acceptance mode run in classes of their own, with the
+    same bit-for-bit equality; a member whose mode changed after the batch
+    was made is refused; parameters changed on a member after the batch was
+    made (per-state windows) are picked up.
 """
 import numpy as np
 import pytest
@@ -131,14 +134,75 @@ def test_member_stepped_alone_between_batch_steps():
         assert_same(a, b)
 
 
-def test_batch_refuses_delayed_acceptance_member():
-    ps = small_uneven(2)
+def test_batch_with_delayed_acceptance_members_equals_one_by_one():
+    """Members sampling with delayed acceptance (each with its own network)
+    run in size classes of their own (the delayed-acceptance instantiation of
+    the persistent kernel) next to plain members, and every member ends
+    bit-identical to stepping it alone, surrogate counters included."""
+    ps = small_uneven(4)
     A, _ = members(ps, 41)
+    Bs, _ = members(ps, 41)
+    for hs in (A, Bs):
+        for i in (0, 2):
+            hs[i].surrogate_init(seed=1 + i)
+            hs[i].set_mode(True)
+    with Batch(A, sweeps_per_step=SPS) as bt:
+        plan = bt.plan()
+        assert len(plan) >= 3
+        bt.autotune(1)
+        bt.run(3)
+        bt.sync()
+    k = steps_done(A[0])
+    for h in Bs:
+        for _ in range(k):
+            h.sweep(SPS)
+            h.exchange()
+    for a, b in zip(A, Bs):
+        assert_same(a, b)
+    assert A[0].counters()[2][4] > 0              # stage-1 evaluations happened
+
+
+def test_batch_refuses_a_member_whose_mode_changed():
+    ps = small_uneven(2)
+    A, _ = members(ps, 43)
     A[0].surrogate_init(seed=1)
     A[0].set_mode(True)
-    with pytest.raises(Exception):
-        Batch(A, sweeps_per_step=SPS)
-    A[0].set_mode(False)
     with Batch(A, sweeps_per_step=SPS) as bt:
         bt.run(1)
         bt.sync()
+        A[0].set_mode(False)
+        with pytest.raises(Exception):
+            bt.run(1)
+        A[0].set_mode(True)
+        bt.run(1)
+        bt.sync()
+
+
+def test_batch_picks_up_state_windows_set_after_it_was_made():
+    """Parameters changed on a member after the batch was made (here its
+    per-state energy windows) are uploaded before the next batch step."""
+    ps = small_uneven(3)
+    A, _ = members(ps, 51)
+    Bs, _ = members(ps, 51)
+    with Batch(A, sweeps_per_step=SPS) as bt:
+        bt.run(1)
+        bt.sync()
+        for h in A:
+            h.set_state_windows(64, 0.5, None)
+            h.reset_histograms()
+        bt.run(2)
+        bt.sync()
+    for h in Bs:
+        h.sweep(SPS)
+        h.exchange()
+        h.set_state_windows(64, 0.5, None)
+        h.reset_histograms()
+        for _ in range(2):
+            h.sweep(SPS)
+            h.exchange()
+    for a, b in zip(A, Bs):
+        ha, hb = a.state_histograms(), b.state_histograms()
+        assert ha[0].sum() > 0
+        for x, y in zip(ha, hb):
+            assert np.array_equal(x, y)
+        assert_same(a, b)

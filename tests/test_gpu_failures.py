@@ -11,9 +11,15 @@ make the device code take its own error paths (no GPU fault, trap or hang).
   pairs inside the hard-core guard; the energy recompute at the end of the
   segment reports it as REGC_ENUMERIC (positions are kept inside the box by
   construction, so nothing is read or written out of range).
-* The bounded mbarrier wait of the sweep (REGC_ETIMEOUT) is not forced: that
-  would need a bulk copy that never completes.
+* Timeout: the sweep's bounded mbarrier wait on the bulk copy of a walker's
+  positions is made to run out by the test hook regc_test_expire_waits (the
+  next sweep's walkers issue no copy, so the barrier phase they wait for never
+  completes and each wait ends by its own budget of about 1 s of clock
+  cycles).  The handle reports REGC_ETIMEOUT, sticky; the context stays
+  usable and a fresh handle matches the oracle.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -24,7 +30,7 @@ from paper_1908_11118_gb300 import build as B
 
 pytestmark = pytest.mark.gpu
 
-ECAPACITY, ENUMERIC = -5, -6
+ETIMEOUT, ECAPACITY, ENUMERIC = -4, -5, -6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -90,3 +96,33 @@ def test_md_with_a_runaway_time_step_reports_numeric():
         g.sweep(1)
     assert err.value.status == ENUMERIC
     g.close()
+
+
+def test_expired_wait_reports_timeout_and_the_context_stays_usable():
+    p = W.fcc100_small()
+    pos, n = W.initial_walkers(p, [6] * p.S, seed=4)
+    g = Regc(p)
+    g.set_walkers(pos, n)
+    g.test_expire_waits()
+    t0 = time.perf_counter()
+    g.sweep(1)
+    with pytest.raises(RegcError) as err:
+        g.histograms()
+    waited = time.perf_counter() - t0
+    assert err.value.status == ETIMEOUT
+    assert 0.3 < waited < 30.0, waited             # the waits ended by their own budget
+    for call in (lambda: g.sweep(1), g.exchange, g.check_energy):
+        with pytest.raises(RegcError) as err:
+            call()
+        assert err.value.status == ETIMEOUT
+    g.close()
+    # the hook is one-shot and per handle: a fresh handle samples as the oracle does
+    h = Regc(p)
+    h.set_walkers(pos, n)
+    tr = h.sweep_traced(2)
+    o = O.Oracle(p, pos=pos, n=n)
+    to = o.sweeps(2, trace=True)
+    assert np.array_equal(tr["accepted"], to["accepted"]) and np.array_equal(tr["index"], to["index"])
+    h.sweep(3)
+    assert h.check_energy() == 0.0
+    h.close()
