@@ -796,17 +796,20 @@ REGC_API regc_status regc_batch_create(regc_handle *const *handles, int count, i
 REGC_API regc_status regc_batch_run(regc_batch *b, int n_steps);
 
 /* Time `rounds` x (number of candidate shapes) real batch steps -- each
- * class's kernel with walkers per CTA in 1, 2, 4, ... 16 (while its shared
- * memory fits), CTAs = SMs x resident CTAs per SM (at most one per walker
- * group) -- and keep each class's fastest shape.  The steps count as sampling
- * steps (the chains advance).  Synchronous. */
+ * class's kernel with warps per walker in 1, 2, 4 (more than one -- the
+ * speculative walker -- for plain one-species classes only) times walkers per
+ * CTA in 1, 2, 4, ... (CTAs of 32 ... 512 threads, while the shared memory
+ * fits), CTAs = SMs x resident CTAs per SM (at most one per walker group) --
+ * and keep each class's fastest shape.  The steps count as sampling steps
+ * (the chains advance); every shape gives the same chains.  Synchronous. */
 REGC_API regc_status regc_batch_autotune(regc_batch *b, int rounds);
 
 /* The current plan: *n_classes size classes; for the first max_classes of
- * them nmax, walkers, walkers per CTA, CTAs and the last measured kernel time
- * in ms (-1 before tuning).  Output arrays may be NULL. */
+ * them nmax, walkers, walkers per CTA, warps per walker, CTAs and the last
+ * measured kernel time in ms (-1 before tuning).  Output arrays may be NULL. */
 REGC_API regc_status regc_batch_plan(const regc_batch *b, int max_classes, int *n_classes, int32_t *nmax,
-                                     int32_t *walkers, int32_t *walkers_per_cta, int32_t *ctas, double *ms);
+                                     int32_t *walkers, int32_t *walkers_per_cta, int32_t *warps_per_walker,
+                                     int32_t *ctas, double *ms);
 
 /* Wait for the batch's work and fold every member's device error word into
  * its sticky status; returns the first error. */

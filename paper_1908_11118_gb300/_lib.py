@@ -139,7 +139,7 @@ SIGNATURES = {
     "regc_batch_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "regc_batch_run": ([_h, C.c_int], C.c_int),
     "regc_batch_autotune": ([_h, C.c_int], C.c_int),
-    "regc_batch_plan": ([_h, C.c_int, C.POINTER(C.c_int), _ip, _ip, _ip, _ip, _dp], C.c_int),
+    "regc_batch_plan": ([_h, C.c_int, C.POINTER(C.c_int), _ip, _ip, _ip, _ip, _ip, _dp], C.c_int),
     "regc_batch_sync": ([_h], C.c_int),
     "regc_batch_free": ([_h], None),
     "regc_status_string": ([C.c_int], C.c_char_p),

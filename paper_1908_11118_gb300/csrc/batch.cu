@@ -29,12 +29,17 @@ struct Bucket {
     int nmax = 0;
     bool da = false;                // its systems sample with delayed acceptance
     bool cl = false;                // its systems carry a cluster species
-    int region = 0;                 // dynamic shared memory per walker (bytes)
+    int region = 0;                 // dynamic shared memory per walker (bytes) at k warps per walker
+    int k = 1;                      // warps per walker
     std::vector<int2> items;        // (system, walker), largest systems first
+    std::vector<int> members;       // the members in the class
     int2* d_items = nullptr;
     int wpc = 1, grid = 1;          // walkers per CTA, CTAs
     double ms = -1.0;               // last measured kernel time
-    std::vector<int> cand_wpc;      // feasible walkers-per-CTA choices
+    struct Shape {
+        int k, wpc, region;
+    };
+    std::vector<Shape> cand;        // feasible (warps per walker, walkers per CTA) choices
 };
 
 }  // namespace
@@ -134,8 +139,8 @@ cudaError_t record_step(regc_batch* b, std::vector<double>* ms_out) {
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], b->stream);
         for (int k = 0; k < nb && e == cudaSuccess; ++k) {
             const Bucket& q = b->buckets[k];
-            e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.grid,
-                                   q.region, q.da, q.cl, b->stream);
+            e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.k,
+                                   q.grid, q.region, q.da, q.cl, b->stream);
             if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], b->stream);
         }
         if (e == cudaSuccess)
@@ -157,8 +162,8 @@ cudaError_t record_step(regc_batch* b, std::vector<double>* ms_out) {
         cudaStream_t s = k == 0 ? b->stream : b->side[k];
         if (k > 0) e = cudaStreamWaitEvent(s, b->fork, 0);
         if (e == cudaSuccess)
-            e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.grid,
-                                   q.region, q.da, q.cl, s);
+            e = launch_batch_sweep(b->d_sys, q.d_items, (int)q.items.size(), b->d_counters + k, q.wpc, q.k,
+                                   q.grid, q.region, q.da, q.cl, s);
         if (e == cudaSuccess && k > 0) e = cudaEventRecord(b->join[k], s);
     }
     for (int k = 1; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->stream, b->join[k], 0);
@@ -269,9 +274,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
         q.da = std::get<1>(it->first) != 0;
         q.cl = std::get<2>(it->first) != 0;
         std::vector<int> ms = it->second;
-        size_t region = 0;
-        for (int m : ms) region = std::max(region, handles[m]->smem_per_walker);
-        q.region = (int)((region + 15) / 16 * 16);
+        q.members = ms;
         std::stable_sort(ms.begin(), ms.end(), [&](int a, int c) {
             return handles[a]->P.cg.ncell * handles[a]->P.cg.cap > handles[c]->P.cg.ncell * handles[c]->P.cg.cap;
         });
@@ -280,22 +283,36 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
         b->buckets.push_back(q);
     }
     if (e == cudaSuccess) e = batch_prepare((int)kMaxSmem);
-    // feasible shapes, and the default: the most resident walkers per SM
+    // feasible shapes (warps per walker 1, 2, 4 -- more than one only for
+    // plain one-species classes -- times walkers per CTA, CTAs of at most 16
+    // warps), and the default: one warp per walker, the most resident walkers
+    // per SM
     for (auto& q : b->buckets) {
         int best = 0;
         const size_t stat = batch_static_smem(q.da);
-        for (int wpc = 1; wpc <= batch_max_warps(q.da) && e == cudaSuccess; wpc *= 2) {
-            if ((size_t)wpc * q.region + stat > kMaxSmem) break;
-            const int occ = batch_occupancy(wpc, q.region, q.da, q.cl);
-            if (occ < 1) break;
-            q.cand_wpc.push_back(wpc);
-            if (wpc * occ > best) {
-                best = wpc * occ;
-                q.wpc = wpc;
+        for (int k = 1; k <= 4 && e == cudaSuccess; k *= 2) {
+            if (k > 1 && (q.da || q.cl)) break;
+            size_t region = 0;
+            for (int m : q.members) {
+                const regc_handle* h = handles[m];
+                region = std::max(region, sweep_smem_per_walker(h->nmax, h->P.cg.ncell, h->P.cg.cap, k));
+            }
+            region = (region + 15) / 16 * 16;
+            for (int wpc = 1; k * wpc <= batch_max_warps(q.da) && e == cudaSuccess; wpc *= 2) {
+                if ((size_t)wpc * region + stat > kMaxSmem) break;
+                const int occ = batch_occupancy(wpc, k, (int)region, q.da, q.cl);
+                if (occ < 1) break;
+                q.cand.push_back({k, wpc, (int)region});
+                if (k == 1 && wpc * occ > best) {
+                    best = wpc * occ;
+                    q.k = 1;
+                    q.wpc = wpc;
+                    q.region = (int)region;
+                }
             }
         }
-        if (q.cand_wpc.empty()) e = cudaErrorInvalidValue;   // one walker does not fit
-        const int occ = batch_occupancy(q.wpc, q.region, q.da, q.cl);
+        if (q.cand.empty()) e = cudaErrorInvalidValue;   // one walker does not fit
+        const int occ = batch_occupancy(q.wpc, q.k, q.region, q.da, q.cl);
         const int need = (int)((q.items.size() + q.wpc - 1) / q.wpc);
         q.grid = std::max(1, std::min(need, b->sms * std::max(occ, 1)));
     }
@@ -366,18 +383,21 @@ regc_status regc_batch_autotune(regc_batch* b, int rounds) {
     if (st != REGC_OK) return st;
     const int nb = (int)b->buckets.size();
     size_t n_cand = 0;
-    for (const auto& q : b->buckets) n_cand = std::max(n_cand, q.cand_wpc.size());
+    for (const auto& q : b->buckets) n_cand = std::max(n_cand, q.cand.size());
     std::vector<double> best(nb, 1e300);
-    std::vector<int> best_wpc(nb), best_grid(nb);
+    std::vector<Bucket::Shape> best_shape(nb);
+    std::vector<int> best_grid(nb);
     std::vector<double> ms;
     // candidate c of every class in the same timed step; every step is a real step
     for (int r = 0; r < rounds; ++r) {
         for (size_t c = 0; c < n_cand; ++c) {
             for (auto& q : b->buckets) {
-                const int wpc = q.cand_wpc[std::min(c, q.cand_wpc.size() - 1)];
-                const int occ = batch_occupancy(wpc, q.region, q.da, q.cl);
-                const int need = (int)((q.items.size() + wpc - 1) / wpc);
-                q.wpc = wpc;
+                const Bucket::Shape sh = q.cand[std::min(c, q.cand.size() - 1)];
+                const int occ = batch_occupancy(sh.wpc, sh.k, sh.region, q.da, q.cl);
+                const int need = (int)((q.items.size() + sh.wpc - 1) / sh.wpc);
+                q.k = sh.k;
+                q.wpc = sh.wpc;
+                q.region = sh.region;
                 q.grid = std::max(1, std::min(need, b->sms * std::max(occ, 1)));
             }
             st = fail(b, record_step(b, &ms));
@@ -386,13 +406,15 @@ regc_status regc_batch_autotune(regc_batch* b, int rounds) {
             for (int k = 0; k < nb; ++k)
                 if (ms[k] < best[k]) {
                     best[k] = ms[k];
-                    best_wpc[k] = b->buckets[k].wpc;
+                    best_shape[k] = {b->buckets[k].k, b->buckets[k].wpc, b->buckets[k].region};
                     best_grid[k] = b->buckets[k].grid;
                 }
         }
     }
     for (int k = 0; k < nb; ++k) {
-        b->buckets[k].wpc = best_wpc[k];
+        b->buckets[k].k = best_shape[k].k;
+        b->buckets[k].wpc = best_shape[k].wpc;
+        b->buckets[k].region = best_shape[k].region;
         b->buckets[k].grid = best_grid[k];
         b->buckets[k].ms = best[k];
     }
@@ -401,7 +423,7 @@ regc_status regc_batch_autotune(regc_batch* b, int rounds) {
 }
 
 regc_status regc_batch_plan(const regc_batch* b, int max_classes, int* n_classes, int32_t* nmax, int32_t* walkers,
-                            int32_t* walkers_per_cta, int32_t* ctas, double* ms) {
+                            int32_t* walkers_per_cta, int32_t* warps_per_walker, int32_t* ctas, double* ms) {
     if (!b || !n_classes) return REGC_EINVAL;
     const int nb = (int)b->buckets.size();
     *n_classes = nb;
@@ -410,6 +432,7 @@ regc_status regc_batch_plan(const regc_batch* b, int max_classes, int* n_classes
         if (nmax) nmax[k] = q.nmax;
         if (walkers) walkers[k] = (int32_t)q.items.size();
         if (walkers_per_cta) walkers_per_cta[k] = q.wpc;
+        if (warps_per_walker) warps_per_walker[k] = q.k;
         if (ctas) ctas[k] = q.grid;
         if (ms) ms[k] = q.ms;
     }

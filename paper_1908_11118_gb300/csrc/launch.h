@@ -36,19 +36,21 @@ int batch_max_warps(bool da);
 
 // Persistent sweep of items (system, walker) of the systems sys[] (device
 // table; every system's n_sweeps and t0 are read from it), taken in order from
-// the queue *counter (zero before the launch); warps_per_cta walkers per CTA,
-// each with `region` bytes of dynamic shared memory.  da: every system of the
-// items samples with delayed acceptance; cl: every system carries a cluster
-// species.
+// the queue *counter (zero before the launch); walkers_per_cta walkers of
+// warps_per_walker warps each per CTA (1, 2 or 4; more than one for plain
+// one-species systems only), each with `region` bytes of dynamic shared
+// memory.  da: every system of the items samples with delayed acceptance; cl:
+// every system carries a cluster species.
 cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
-                               int warps_per_cta, int grid, int region, bool da, bool cl, cudaStream_t s);
+                               int walkers_per_cta, int warps_per_walker, int grid, int region, bool da, bool cl,
+                               cudaStream_t s);
 
 // Allow every batch sweep kernel up to max_smem bytes of shared memory in all
 // (before any launch or capture that needs more than 48 KB).
 cudaError_t batch_prepare(int max_smem);
 
 // Resident CTAs per SM of the batch sweep kernel for this shape (0 if none fit).
-int batch_occupancy(int warps_per_cta, int region, bool da, bool cl);
+int batch_occupancy(int walkers_per_cta, int warps_per_walker, int region, bool da, bool cl);
 
 // One exchange attempt of every system's grid (attempt numbers e_ctr[]), then
 // e_ctr[m] += 1 and sys[m].t0 += n_sweeps on the device.

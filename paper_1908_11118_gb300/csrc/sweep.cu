@@ -229,10 +229,29 @@ __device__ bool mbar_wait_bounded(uint64_t* bar) {
     return true;
 }
 
+// Synchronise the K warps of a walker group: a warp barrier for one warp,
+// else named barrier bar over the group's 32 K threads (bar 0 with the whole
+// CTA in the one-walker-per-CTA kernel, where it is __syncthreads()).
 template <int K>
-__device__ __forceinline__ void group_sync() {
+__device__ __forceinline__ void group_sync(int bar) {
     if (K == 1) __syncwarp();
-    else __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * K) : "memory");
+}
+
+// True in every thread of the group iff p holds in all of them (a barrier).
+template <int K>
+__device__ __forceinline__ bool group_all(int bar, bool p) {
+    if (K == 1) return __all_sync(0xffffffffu, p) != 0;
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred q, a;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred a, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, a;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(bar), "r"(32 * K)
+        : "memory");
+    return r != 0;
 }
 
 // Stencil entry handled by this lane (cell = -1 if none), for queries q0, q1
@@ -697,9 +716,10 @@ __device__ __forceinline__ float dist2(const SweepParams& P, float ax, float ay,
 }
 
 // n_sweeps sweeps of walker w by a group of K warps (tid: thread index in the
-// group, smem: the group's shared-memory region).
+// group, smem: the group's shared-memory region, bar: the group's named
+// barrier when K > 1).
 template <int K, bool TRACE, bool DA, bool CL>
-__device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* smem, int tid) {
+__device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* smem, int tid, int bar) {
     const int lane = tid & 31, warp = tid >> 5;
     const WalkerSmem S = carve<K>(smem, P);
 
@@ -723,22 +743,22 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (!P.expire_waits) bulk_load(S.pos, gpos, uint32_t(N) * 16u, S.bar);
         }
-        group_sync<K>();
+        group_sync<K>(bar);
         const bool ok = mbar_wait_bounded(S.bar);
-        const bool all_ok = (K == 1) ? (__all_sync(FULL, ok) != 0) : (__syncthreads_and(ok) != 0);
+        const bool all_ok = group_all<K>(bar, ok);
         if (!all_ok) {
             if (tid == 0) atomicOr(P.error, ERR_TIMEOUT);
             mbar_wait_bounded(S.bar);  // one more bounded chance for the copy in flight
             return;
         }
-        group_sync<K>();
+        group_sync<K>(bar);
         if (tid == 0) mbar_inval(S.bar);   // the barrier's memory is reused by the next walker
     }
     // 2. cell list
     if (warp == 0) build_cells(P, S, N, lane);
     if (tid == 0)
         *S.stats = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}, 0, 0};
-    group_sync<K>();
+    group_sync<K>(bar);
 
     int n_in = 0, n_cand = 0;
     NetFrag nf;                       // the surrogate's weights in this lane's fragments
@@ -761,7 +781,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 }
             }
             filled += 32;
-            group_sync<K>();
+            group_sync<K>(bar);
         }
         // 3b. evaluate moves m0 .. m0 + K - 1 in parallel, one warp each
         const int mj = m0 + warp;
@@ -770,7 +790,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             if (P.cycle) slot = (mj % P.mps) == 0;
             evaluate_move<DA, CL>(P, S, sf, s, mj, N, slot, split, n_in, n_cand, lane, warp, &nf, S.res + warp);
         }
-        group_sync<K>();
+        group_sync<K>(bar);
 
         // 4. commit in order (thread 0)
         if (tid == 0) {
@@ -967,12 +987,12 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             S.stats->rounds += 1;
             S.stats->evals += min(K, total_moves - m0);
         }
-        group_sync<K>();
+        group_sync<K>(bar);
         N = S.hdr->N;
         E = S.hdr->E;
         split = S.hdr->split;
         m0 += S.hdr->committed;
-        group_sync<K>();   // the header and results are rewritten by the next round
+        group_sync<K>(bar);   // the header and results are rewritten by the next round
     }
 
     // 7. write back
@@ -1014,7 +1034,7 @@ template <int K, bool TRACE, bool DA, bool CL>
 __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
     extern __shared__ __align__(16) char smem[];
     if (blockIdx.x >= (unsigned)P.S) return;
-    walker_sweep<K, TRACE, DA, CL>(P, blockIdx.x, smem, threadIdx.x);
+    walker_sweep<K, TRACE, DA, CL>(P, blockIdx.x, smem, threadIdx.x, 0);
 }
 
 // Displacement q - p with the exact minimum image on periodic axes (cell
@@ -1213,68 +1233,80 @@ cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Persistent sweep of a batch of walkers from several systems.  Every warp of
-// the CTA is one walker at a time: lane 0 takes the next (system, walker) item
-// from the queue, the warp copies that system's parameters into its slot of
-// shared memory and runs the walker's sweeps in its own shared-memory region
-// of `region` bytes; items are listed largest first, so the queue balances
-// the uneven costs.  DA: the systems of the launch sample with delayed
-// acceptance (their networks' fragments take ~240 registers per thread, so
-// at most kBatchMaxWarpsDA walkers per CTA); CL: every system of the launch
-// carries a cluster species.
+// Persistent sweep of a batch of walkers from several systems.  Every group
+// of K warps of the CTA is one walker at a time: its first thread takes the
+// next (system, walker) item from the queue, the group copies that system's
+// parameters into its slot of shared memory and runs the walker's sweeps in
+// its own shared-memory region of `region` bytes (K > 1: the speculative
+// walker, synchronised by the group's named barrier 1 + group); items are
+// listed largest first, so the queue balances the uneven costs.  DA: the
+// systems of the launch sample with delayed acceptance (their networks'
+// fragments take ~240 registers per thread, so at most kBatchMaxWarpsDA
+// walkers per CTA); CL: every system of the launch carries a cluster species.
 constexpr int kBatchMaxWarps = 16;
 constexpr int kBatchMaxWarpsDA = 4;
 
-template <bool DA, bool CL>
+template <bool DA, bool CL, int K>
 __global__ void __launch_bounds__(32 * (DA ? kBatchMaxWarpsDA : kBatchMaxWarps))
     batch_sweep_kernel(const SweepParams* __restrict__ sys, const int2* __restrict__ items, int n_items,
                        int* counter, int region) {
+    constexpr int kGroups = (DA ? kBatchMaxWarpsDA : kBatchMaxWarps) / K;
     extern __shared__ __align__(16) char smem[];
-    __shared__ SweepParams Psh[DA ? kBatchMaxWarpsDA : kBatchMaxWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    char* mine = smem + (size_t)warp * region;
+    __shared__ SweepParams Psh[kGroups];
+    __shared__ int item_sh[kGroups];
+    const int tid = threadIdx.x % (32 * K), grp = threadIdx.x / (32 * K);
+    const int bar = K == 1 ? 0 : 1 + grp;
+    char* mine = smem + (size_t)grp * region;
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(counter, 1);
-        item = __shfl_sync(FULL, item, 0);
+        if (K == 1) {
+            if (tid == 0) item = atomicAdd(counter, 1);
+            item = __shfl_sync(FULL, item, 0);
+        } else {
+            if (tid == 0) item_sh[grp] = atomicAdd(counter, 1);
+            group_sync<K>(bar);
+            item = item_sh[grp];
+        }
         if (item >= n_items) break;
         const int2 mw = items[item];
         const int* src = reinterpret_cast<const int*>(sys + mw.x);
-        int* dst = reinterpret_cast<int*>(&Psh[warp]);
-        for (int k = lane; k < (int)(sizeof(SweepParams) / sizeof(int)); k += 32) dst[k] = src[k];
-        __syncwarp();
-        walker_sweep<1, false, DA, CL>(Psh[warp], mw.y, mine, lane);
-        __syncwarp();
+        int* dst = reinterpret_cast<int*>(&Psh[grp]);
+        for (int k = tid; k < (int)(sizeof(SweepParams) / sizeof(int)); k += 32 * K) dst[k] = src[k];
+        group_sync<K>(bar);
+        walker_sweep<K, false, DA, CL>(Psh[grp], mw.y, mine, tid, bar);
+        group_sync<K>(bar);   // the slot and the item are rewritten for the next walker
     }
 }
 
 }  // namespace
 
-size_t batch_static_smem(bool da) { return sizeof(SweepParams) * (da ? kBatchMaxWarpsDA : kBatchMaxWarps); }
+size_t batch_static_smem(bool da) {
+    return (sizeof(SweepParams) + sizeof(int)) * (da ? kBatchMaxWarpsDA : kBatchMaxWarps);
+}
 
 int batch_max_warps(bool da) { return da ? kBatchMaxWarpsDA : kBatchMaxWarps; }
 
 namespace {
 
-template <bool DA, bool CL>
-cudaError_t launch_batch_k(const SweepParams* sys, const int2* items, int n_items, int* counter, int warps_per_cta,
-                           int grid, int region, cudaStream_t s) {
-    const size_t smem = (size_t)warps_per_cta * region;
-    batch_sweep_kernel<DA, CL><<<grid, 32 * warps_per_cta, smem, s>>>(sys, items, n_items, counter, region);
+template <bool DA, bool CL, int K>
+cudaError_t launch_batch_k(const SweepParams* sys, const int2* items, int n_items, int* counter,
+                           int walkers_per_cta, int grid, int region, cudaStream_t s) {
+    const size_t smem = (size_t)walkers_per_cta * region;
+    batch_sweep_kernel<DA, CL, K><<<grid, 32 * K * walkers_per_cta, smem, s>>>(sys, items, n_items, counter, region);
     return cudaGetLastError();
 }
 
-template <bool DA, bool CL>
+template <bool DA, bool CL, int K>
 cudaError_t prepare_k(int max_smem) {
-    return cudaFuncSetAttribute(batch_sweep_kernel<DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(batch_sweep_kernel<DA, CL, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 max_smem - (int)batch_static_smem(DA));
 }
 
-template <bool DA, bool CL>
-int occupancy_k(int warps_per_cta, size_t smem) {
+template <bool DA, bool CL, int K>
+int occupancy_k(int walkers_per_cta, size_t smem) {
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_sweep_kernel<DA, CL>, 32 * warps_per_cta, smem) ==
-                   cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_sweep_kernel<DA, CL, K>, 32 * K * walkers_per_cta,
+                                                         smem) == cudaSuccess
                ? n
                : 0;
 }
@@ -1282,29 +1314,45 @@ int occupancy_k(int warps_per_cta, size_t smem) {
 }  // namespace
 
 cudaError_t launch_batch_sweep(const SweepParams* sys, const int2* items, int n_items, int* counter,
-                               int warps_per_cta, int grid, int region, bool da, bool cl, cudaStream_t s) {
+                               int walkers_per_cta, int warps_per_walker, int grid, int region, bool da, bool cl,
+                               cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    if (warps_per_cta < 1 || warps_per_cta > batch_max_warps(da) || grid < 1) return cudaErrorInvalidValue;
+    const int K = warps_per_walker;
+    if (walkers_per_cta < 1 || K * walkers_per_cta > batch_max_warps(da) || grid < 1) return cudaErrorInvalidValue;
+    if (K != 1 && (da || cl)) return cudaErrorInvalidValue;   // speculation: plain one-species walkers only
     if (da) {
-        return cl ? launch_batch_k<true, true>(sys, items, n_items, counter, warps_per_cta, grid, region, s)
-                  : launch_batch_k<true, false>(sys, items, n_items, counter, warps_per_cta, grid, region, s);
+        return cl ? launch_batch_k<true, true, 1>(sys, items, n_items, counter, walkers_per_cta, grid, region, s)
+                  : launch_batch_k<true, false, 1>(sys, items, n_items, counter, walkers_per_cta, grid, region, s);
     }
-    return cl ? launch_batch_k<false, true>(sys, items, n_items, counter, warps_per_cta, grid, region, s)
-              : launch_batch_k<false, false>(sys, items, n_items, counter, warps_per_cta, grid, region, s);
+    if (cl) return launch_batch_k<false, true, 1>(sys, items, n_items, counter, walkers_per_cta, grid, region, s);
+    switch (K) {
+        case 1: return launch_batch_k<false, false, 1>(sys, items, n_items, counter, walkers_per_cta, grid, region, s);
+        case 2: return launch_batch_k<false, false, 2>(sys, items, n_items, counter, walkers_per_cta, grid, region, s);
+        case 4: return launch_batch_k<false, false, 4>(sys, items, n_items, counter, walkers_per_cta, grid, region, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t batch_prepare(int max_smem) {
-    cudaError_t e = prepare_k<false, false>(max_smem);
-    if (e == cudaSuccess) e = prepare_k<false, true>(max_smem);
-    if (e == cudaSuccess) e = prepare_k<true, false>(max_smem);
-    if (e == cudaSuccess) e = prepare_k<true, true>(max_smem);
+    cudaError_t e = prepare_k<false, false, 1>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<false, false, 2>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<false, false, 4>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<false, true, 1>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<true, false, 1>(max_smem);
+    if (e == cudaSuccess) e = prepare_k<true, true, 1>(max_smem);
     return e;
 }
 
-int batch_occupancy(int warps_per_cta, int region, bool da, bool cl) {
-    const size_t smem = (size_t)warps_per_cta * region;   // within the limit batch_prepare set
-    if (da) return cl ? occupancy_k<true, true>(warps_per_cta, smem) : occupancy_k<true, false>(warps_per_cta, smem);
-    return cl ? occupancy_k<false, true>(warps_per_cta, smem) : occupancy_k<false, false>(warps_per_cta, smem);
+int batch_occupancy(int walkers_per_cta, int warps_per_walker, int region, bool da, bool cl) {
+    const size_t smem = (size_t)walkers_per_cta * region;   // within the limit batch_prepare set
+    if (da) return cl ? occupancy_k<true, true, 1>(walkers_per_cta, smem) : occupancy_k<true, false, 1>(walkers_per_cta, smem);
+    if (cl) return occupancy_k<false, true, 1>(walkers_per_cta, smem);
+    switch (warps_per_walker) {
+        case 1: return occupancy_k<false, false, 1>(walkers_per_cta, smem);
+        case 2: return occupancy_k<false, false, 2>(walkers_per_cta, smem);
+        case 4: return occupancy_k<false, false, 4>(walkers_per_cta, smem);
+    }
+    return 0;
 }
 
 size_t sweep_smem_per_walker(int nmax, int ncell, int cap, int warps_per_walker) {

@@ -456,15 +456,17 @@ class Batch:
 
     def plan(self):
         n = C.c_int(0)
-        check(_lib.lib().regc_batch_plan(self._b, 0, C.byref(n), None, None, None, None, None), "regc_batch_plan")
+        check(_lib.lib().regc_batch_plan(self._b, 0, C.byref(n), None, None, None, None, None, None),
+              "regc_batch_plan")
         k = n.value
-        nm, wk, wpc, ctas = (np.zeros(k, np.int32) for _ in range(4))
+        nm, wk, wpc, wpw, ctas = (np.zeros(k, np.int32) for _ in range(5))
         ms = np.zeros(k)
         check(_lib.lib().regc_batch_plan(self._b, k, C.byref(n), _p(nm, C.c_int32), _p(wk, C.c_int32),
-                                         _p(wpc, C.c_int32), _p(ctas, C.c_int32), _p(ms, C.c_double)),
+                                         _p(wpc, C.c_int32), _p(wpw, C.c_int32), _p(ctas, C.c_int32),
+                                         _p(ms, C.c_double)),
               "regc_batch_plan")
-        return [{"nmax": int(nm[i]), "walkers": int(wk[i]), "walkers_per_cta": int(wpc[i]), "ctas": int(ctas[i]),
-                 "ms": float(ms[i])} for i in range(k)]
+        return [{"nmax": int(nm[i]), "walkers": int(wk[i]), "walkers_per_cta": int(wpc[i]),
+                 "warps_per_walker": int(wpw[i]), "ctas": int(ctas[i]), "ms": float(ms[i])} for i in range(k)]
 
     def close(self):
         if getattr(self, "_b", None):
