@@ -337,6 +337,109 @@ __global__ void __launch_bounds__(kQThreads)
     }
 }
 
+// The query over runs of bins with equal (N, N2) in the bin order (the
+// handle's compacted histogram is row-major, so a run is a whole row).  A
+// binary32 pass over all bins finds the query's largest screen value M_q;
+// then a warp takes whole runs: the run's largest screen value, and the sum
+// of exp(t_b - M_q) in FP64 over the run's terms within kSkip + kMargin of
+// that largest one (one exponential per kept term), added to the warp's own
+// sums per N (and per N2), N- and N2-weighted and in total.  The warps' sums
+// are added in warp order at the end, so the query is deterministic:
+//   f_q = -(M_q + ln total),  p_N = sum_N / total,  <N> = sum_{N-weighted} / total.
+// Each dropped term weighs below e^-50 of the largest term of its own run,
+// so every run sum -- hence every p_N -- keeps its relative accuracy down to
+// the FP64 range (a phase below e^-708 of the largest term is 0, as the
+// oracle's weights are).
+constexpr int kRunWarps = 8;
+
+template <bool TWO>
+__global__ void __launch_bounds__(32 * kRunWarps)
+    query_runs_kernel(const __grid_constant__ MbarDev m, const double* a_q, const double* c_q, const double* c2_q,
+                      int nmax, const int* run_start, int n_runs, int warps, double* n_mean, double* n2_mean,
+                      double* pN, double* pN2, double* f_q) {
+    // per warp: [nmax + 1] sums per N (then per N2), then total, N-, N2-weighted
+    extern __shared__ double acc[];
+    const int rows = nmax + 1, per_warp = (TWO ? 2 : 1) * rows + 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* mine = acc + (size_t)warp * per_warp;   // used only by the first `warps` warps
+    if (warp < warps)
+        for (int i = lane; i < per_warp; i += 32) mine[i] = 0.0;
+    const int q = blockIdx.x;
+    const double a = a_q[q], c = c_q[q], c2 = TWO ? c2_q[q] : 0.0;
+    const float a32 = (float)a, c32 = (float)c, c232 = (float)c2;
+    auto screen = [&](int b, float n32, float n232) {
+        return -u32_of<TWO>(a32, c32, c232, m.EN32[b].x, n32, n232) - m.DH32[b];
+    };
+    float mall = -INFINITY;
+    for (int b = threadIdx.x; b < m.B; b += blockDim.x)
+        mall = fmaxf(mall, screen(b, m.EN32[b].y, TWO ? m.N2f[b] : 0.f));
+    const double Mq = block_max((double)mall);
+    __syncthreads();
+    double* tot = mine + (TWO ? 2 : 1) * rows;
+    if (warp < warps) {
+        for (int r = warp; r < n_runs; r += warps) {
+            const int b0 = run_start[r], b1 = run_start[r + 1];
+            const float n32 = m.EN32[b0].y, n232 = TWO ? m.N2f[b0] : 0.f;
+            float mx = -INFINITY;
+            for (int b = b0 + lane; b < b1; b += 32) mx = fmaxf(mx, screen(b, n32, n232));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const float th = mx - (float)kSkip - kMargin;
+            const double nd = (double)m.N_b[b0], n2d = TWO ? (double)m.N2_b[b0] : 0.0;
+            double sum = 0.0;
+            for (int b = b0 + lane; b < b1; b += 32)
+                if (screen(b, n32, n232) > th)
+                    sum += exp(m.lnH[b] - u_of<TWO>(a, c, c2, m.E_b[b], nd, n2d) - m.D[b] - Mq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0 && sum > 0.0) {
+                const int n = m.N_b[b0];
+                if (n >= 0 && n <= nmax) mine[n] += sum;
+                tot[0] += sum;
+                tot[1] = fma(nd, sum, tot[1]);
+                if (TWO) {
+                    const int n2 = m.N2_b[b0];
+                    if (n2 >= 0 && n2 <= nmax) mine[rows + n2] += sum;
+                    tot[2] = fma(n2d, sum, tot[2]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // add the warps' sums in warp order into warp 0's
+    for (int i = threadIdx.x; i < per_warp; i += blockDim.x) {
+        double x = acc[i];
+        for (int w = 1; w < warps; ++w) x += acc[(size_t)w * per_warp + i];
+        acc[i] = x;
+    }
+    __syncthreads();
+    const double total = acc[(TWO ? 2 : 1) * rows];
+    if (threadIdx.x == 0) {
+        if (n_mean) n_mean[q] = acc[(TWO ? 2 : 1) * rows + 1] / total;
+        if (TWO && n2_mean) n2_mean[q] = acc[(TWO ? 2 : 1) * rows + 2] / total;
+        if (f_q) f_q[q] = -(Mq + log(total));
+    }
+    for (int n = threadIdx.x; n < rows; n += blockDim.x) {
+        if (pN) pN[size_t(q) * rows + n] = acc[n] / total;
+        if (TWO && pN2) pN2[size_t(q) * rows + n] = acc[rows + n] / total;
+    }
+}
+
+// Runs of equal (N, N2): cnt[b + 1] = 1 where a run starts, then (after the
+// inclusive scan) run_start[cnt[b + 1] - 1] = b, and run_start[n_runs] = B.
+__global__ void run_flag_kernel(int B, const int* N_b, const int* N2_b, long long* cnt) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    cnt[b + 1] = (b == 0 || N_b[b] != N_b[b - 1] || (N2_b && N2_b[b] != N2_b[b - 1])) ? 1 : 0;
+}
+
+__global__ void run_start_kernel(int B, const int* N_b, const int* N2_b, const long long* cnt, int* run_start) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) run_start[cnt[B]] = B;
+    if (b >= B) return;
+    if (b == 0 || N_b[b] != N_b[b - 1] || (N2_b && N2_b[b] != N2_b[b - 1])) run_start[cnt[b + 1] - 1] = b;
+}
+
 // binary32 copies of the bins for the screening: (E, N), N2, D - lnH
 __global__ void prep32_kernel(int B, const double* E_b, const int* N_b, const int* N2_b, const double* D,
                               const double* lnH, float2* EN32, float* N2f, float* DH32) {
@@ -1382,9 +1485,57 @@ cudaError_t mbar_solve_warm_dev(const MbarDev& m, double width, double tol, int 
     return e;
 }
 
+size_t mbar_runs_scratch(int B) {
+    return size_t(B) + 1 + size_t((B + kScanChunk - 1) / kScanChunk) + 1;
+}
+
+cudaError_t mbar_runs_dev(const MbarDev& m, long long* scratch, int* run_start, int* n_runs, cudaStream_t s) {
+    const int B = m.B;
+    long long* cnt = scratch;
+    long long* tmp = scratch + B + 1;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    run_flag_kernel<<<(B + 255) / 256, 256, 0, s>>>(B, m.N_b, m.N2_b, cnt);
+    e = lscan(cnt + 1, B, tmp, s);
+    if (e == cudaSuccess) {
+        run_start_kernel<<<(B + 255) / 256, 256, 0, s>>>(B, m.N_b, m.N2_b, cnt, run_start);
+        e = cudaGetLastError();
+    }
+    long long n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, cnt + B, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) *n_runs = (int)n;
+    return e;
+}
+
+namespace {
+
+// The query over runs when the per-warp accumulators fit in shared memory.
+template <bool TWO>
+bool query_runs(const MbarDev& m, int Q, const double* a_q, const double* c_q, const double* c2_q, int nmax,
+                double* n_mean, double* n2_mean, double* pN, double* pN2, double* f_q, cudaStream_t s,
+                cudaError_t* err) {
+    if (!m.run_start || m.n_runs <= 0) return false;
+    const size_t per_warp = ((TWO ? 2 : 1) * size_t(nmax + 1) + 3) * sizeof(double);
+    const int warps = (int)std::min<size_t>(kRunWarps, size_t(200 * 1024) / per_warp);
+    if (warps < 1) return false;
+    const size_t smem = per_warp * warps;
+    *err = cudaFuncSetAttribute(query_runs_kernel<TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (*err == cudaSuccess) {
+        query_runs_kernel<TWO><<<Q, 32 * kRunWarps, smem, s>>>(m, a_q, c_q, c2_q, nmax, m.run_start, m.n_runs, warps,
+                                                               n_mean, n2_mean, pN, pN2, f_q);
+        *err = cudaGetLastError();
+    }
+    return true;
+}
+
+}  // namespace
+
 cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, int nmax,
                            double* n_mean, double* pN, double* f_q, cudaStream_t s) {
     if (Q <= 0) return cudaSuccess;
+    cudaError_t rerr = cudaSuccess;
+    if (query_runs<false>(m, Q, a_q, c_q, nullptr, nmax, n_mean, nullptr, pN, nullptr, f_q, s, &rerr)) return rerr;
     const size_t smem = size_t(nmax + 1) * (sizeof(double) + sizeof(float));
     cudaError_t err = cudaFuncSetAttribute(query_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -1437,6 +1588,8 @@ cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const do
                             int nmax, double* n_mean, double* n2_mean, double* pN, double* pN2, double* f_q,
                             cudaStream_t s) {
     if (Q <= 0) return cudaSuccess;
+    cudaError_t rerr = cudaSuccess;
+    if (query_runs<true>(m, Q, a_q, c_q, c2_q, nmax, n_mean, n2_mean, pN, pN2, f_q, s, &rerr)) return rerr;
     const size_t smem = 2 * size_t(nmax + 1) * (sizeof(double) + sizeof(float));
     cudaError_t err = cudaFuncSetAttribute(query_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

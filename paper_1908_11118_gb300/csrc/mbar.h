@@ -28,6 +28,10 @@ struct MbarDev {
     const int* N2_b;       // [B] its counts, or null (one species)
     const double* c2;      // [S] 3 ln Lambda_C - beta mu2
     float* N2f;            // [B] N2_b in binary32, filled by the solve
+    // runs of bins with equal (N, N2) in the bin order (mbar_runs_dev), for
+    // the query; without them the query screens bin by bin
+    const int* run_start;  // [n_runs + 1], run_start[n_runs] = B
+    int n_runs;
 };
 
 // What the last mbar_solve_dev of the calling thread did: path 1 when it
@@ -81,6 +85,12 @@ cudaError_t mbar_query_dev(const MbarDev& m, int Q, const double* a_q, const dou
 cudaError_t mbar_query2_dev(const MbarDev& m, int Q, const double* a_q, const double* c_q, const double* c2_q,
                             int nmax, double* N_mean, double* N2_mean, double* pN, double* pN2, double* f_q,
                             cudaStream_t s);
+
+// Runs of bins with equal (N, N2) in the bin order: run_start [n_runs + 1]
+// (device, at most B + 1 ints), *n_runs (host; synchronises the stream).
+// scratch: mbar_runs_scratch(B) long longs (device).
+size_t mbar_runs_scratch(int B);
+cudaError_t mbar_runs_dev(const MbarDev& m, long long* scratch, int* run_start, int* n_runs, cudaStream_t s);
 
 // The binary32 copies of the bins the query screens with: EN32, N2f (when
 // N2_b is set) and DH32 = D - lnH, from E_b, N_b, N2_b, D and lnH.

@@ -1456,6 +1456,20 @@ regc_status status_of(cudaError_t e) {
 }
 
 // Solve over bins already on the device, then answer Q host queries.
+// The runs of equal (N, N2) of m's bins, for the query (m.run_start, m.n_runs).
+cudaError_t with_runs(MbarBuffers& buf, MbarDev& m, cudaStream_t s) {
+    long long* scratch = buf.get<long long>(mbar_runs_scratch(m.B));
+    int* run_start = buf.get<int>(size_t(m.B) + 1);
+    if (buf.err != cudaSuccess) return buf.err;
+    int n_runs = 0;
+    const cudaError_t e = mbar_runs_dev(m, scratch, run_start, &n_runs, s);
+    if (e == cudaSuccess) {
+        m.run_start = run_start;
+        m.n_runs = n_runs;
+    }
+    return e;
+}
+
 // warm_width > 0: started from the solve coarsened to energy bins of that width.
 cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double tol, int max_iter, int* iters,
                             double* f_host, double* D_host, int Q, const double* kT_q, const double* mu_q,
@@ -1486,6 +1500,7 @@ cudaError_t solve_and_query(MbarBuffers& buf, MbarDev& m, double lambda0, double
         e = cudaMemcpyAsync(d_kq, kT_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_mq, mu_q, Q * sizeof(double), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = mbar_prep_states(Q, d_kq, d_mq, lambda0, nullptr, nullptr, a_q, c_q, nullptr, s);
+        if (e == cudaSuccess) e = with_runs(buf, m, s);
         if (e == cudaSuccess) e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
         if (e == cudaSuccess && N_mean) e = cudaMemcpyAsync(N_mean, d_nm, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && pN)
@@ -1640,6 +1655,7 @@ regc_status regc_reweight2(regc_handle* h, int nq, const double* kT_q, const dou
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_m2q, mu2_q, nq * sizeof(double), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = mbar_prep_states(nq, d_kq, d_mq, h->lambda0, nullptr, nullptr, a_q, c_q, nullptr, s);
         if (e == cudaSuccess) e = mbar_prep_states2(nq, d_kq, d_m2q, h->lambda0_2, c2_q, s);
+        if (e == cudaSuccess) e = with_runs(buf, m, s);
         if (e == cudaSuccess) e = mbar_query2_dev(m, nq, a_q, c_q, c2_q, h->nmax, d_nb, d_nc, d_pb, d_pc, nullptr, s);
         if (e == cudaSuccess && NB_mean) e = cudaMemcpyAsync(NB_mean, d_nb, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && NC_mean) e = cudaMemcpyAsync(NC_mean, d_nc, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1749,6 +1765,7 @@ regc_status regc_mbar_query(int Q, const double* kT_q, const double* mu_q, doubl
     m.DH32 = buf.get<float>(B);
     if (buf.err != cudaSuccess) return status_of(buf.err);
     e = mbar_prep32_dev(m, s);
+    if (e == cudaSuccess) e = with_runs(buf, m, s);
     if (e == cudaSuccess) e = mbar_query_dev(m, Q, a_q, c_q, nmax, d_nm, d_pn, d_fq, s);
     if (e == cudaSuccess && N_mean) e = cudaMemcpyAsync(N_mean, d_nm, Q * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && pN)
