@@ -839,7 +839,8 @@ __global__ void __launch_bounds__(256) sp_d_kernel(const __grid_constant__ MbarD
 }
 
 // The by-state sums in balanced pieces: a state's entries (its kFSplit
-// segments, contiguous) are cut into pieces of at most kPiece entries, one
+// segments, contiguous) are cut into pieces of at most kPiece entries (fewer
+// for a small matrix), one
 // CTA per piece, so that a state with many entries does not hold back the
 // map; sp_fs_kernel then adds each state's piece sums in piece order
 // (deterministic) into f_new,s = ln Omega_s + f_ref,s - ln sum_b V_b K_sb.
@@ -1096,13 +1097,22 @@ struct SparseMat {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         if (flag_h != 0 || cp_h.back() != nnz) return cudaSuccess;
-        // pieces of at most kPiece entries, at least one per state
+        // pieces of at most kPiece entries (fewer for a small matrix, so that
+        // there are about eight per SM), at least one per state
+        int sms = 152;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            sms = 152;
+        }
+        const long long piece = std::max(2048LL, std::min(kPiece, nnz / (8LL * sms) + 1));
         std::vector<long long> begin;
         std::vector<int> first(size_t(S) + 1);
         for (int k = 0; k < S; ++k) {
             first[k] = (int)begin.size();
             const long long a = cp_h[size_t(k) * kFSplit], b = cp_h[size_t(k + 1) * kFSplit];
-            const long long np = std::max(1LL, (b - a + kPiece - 1) / kPiece);
+            const long long np = std::max(1LL, (b - a + piece - 1) / piece);
             for (long long q = 0; q < np; ++q) begin.push_back(a + (b - a) * q / np);
         }
         first[S] = (int)begin.size();

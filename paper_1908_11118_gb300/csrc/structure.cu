@@ -642,7 +642,8 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
                  o_aq = take(nq * 8), o_cq = take(nq * 8), o_fq = take(nq * 8), o_pN = take(nq * nh * 8),
                  o_W = take((size_t)nq * count * 8), o_ord = take(order.size() * 4),
                  o_ch = take(chunks.size() * sizeof(int4)), o_fc = take((P + 1) * 4),
-                 o_Jp = take((size_t)n_chunks * nq * cols * 8), o_J = take((size_t)nq * P * cols * 8);
+                 o_Jp = take((size_t)n_chunks * nq * cols * 8), o_J = take((size_t)nq * P * cols * 8),
+                 o_rs = take((B + 1) * 4), o_rsc = take(mbar_runs_scratch((int)B) * 8);
     char* d = nullptr;
     e = cudaMallocAsync(reinterpret_cast<void**>(&d), off, s);
     if (e != cudaSuccess) return fail(h, e);
@@ -693,7 +694,14 @@ regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, 
     if (e == cudaSuccess) e = mbar_solve_dev(m, tol, max_iter, &it, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_aq, a_q.data(), nq * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cq, c_q.data(), nq * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = mbar_query_dev(m, nq, d_aq, d_cq, h->nmax, nullptr, d_pN, d_fq, s);
+    int n_runs = 0;   // the bins are sorted by (N_B, E): a run is a row of one N_B
+    if (e == cudaSuccess)
+        e = mbar_runs_dev(m, reinterpret_cast<long long*>(d + o_rsc), reinterpret_cast<int*>(d + o_rs), &n_runs, s);
+    if (e == cudaSuccess) {
+        m.run_start = reinterpret_cast<int*>(d + o_rs);
+        m.n_runs = n_runs;
+        e = mbar_query_dev(m, nq, d_aq, d_cq, h->nmax, nullptr, d_pN, d_fq, s);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) {
         const long long tot = (long long)nq * count;
