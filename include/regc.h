@@ -342,9 +342,12 @@ REGC_API void regc_free(regc_handle *h);
 /* Replace the walkers' configurations: pos [S][nmax][3] (binary32, x in
  * [0, Lx), y in [0, Ly), z in [z_lo, z_hi]; entries beyond n[w] ignored),
  * n [S] in 0..nmax, and optionally state_of_walker [S] (a permutation of
- * 0..S-1; NULL keeps the current labels).  Host buffers (pinned memory makes
- * the copy asynchronous and fast).  The positions are copied once and checked
- * and repacked on the device; energies are recomputed on the device.
+ * 0..S-1; NULL keeps the current labels).  Host buffers.  A page-locked
+ * position buffer (cudaHostAlloc, cudaHostRegister, or PyTorch's pinned
+ * memory) is read in place by the repacking kernel (on a Grace-Blackwell node
+ * over NVLink-C2C, and only the first n[w] entries of each walker); any other
+ * is copied to the device once.  The positions are checked and repacked on
+ * the device; energies are recomputed on the device.
  * Synchronous.  Errors: REGC_EINVAL -- N out of range or not a permutation
  * (nothing changed), or a coordinate outside the region or a pair inside the
  * hard-core guard radius (every walker is then left empty, N = 0). */

@@ -25,8 +25,9 @@ cudaError_t launch_energy(const SweepParams& P, long long* out, int check_overla
 cudaError_t pack_walkers(const float* xyz, const int* n, int S, int nmax, const Geometry& g, float4* pos, int* error,
                          cudaStream_t s);
 
-// pos [count] -> xyz [count][3].
-cudaError_t unpack_walkers(const float4* pos, long long count, float* xyz, cudaStream_t s);
+// pos [count] -> xyz [count][3] (count = S nmax); with n [S], only the first
+// n[w] entries of each walker are written.
+cudaError_t unpack_walkers(const float4* pos, long long count, int nmax, const int* n, float* xyz, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch
 // Static shared memory of the batch sweep kernel and its warp limit per CTA

@@ -868,6 +868,24 @@ regc_status regc_state_histograms(regc_handle* h, int64_t* hE, double* e_lo, dou
     return REGC_OK;
 }
 
+namespace {
+
+// The device address of a host buffer the GPU can read and write directly
+// (page-locked memory, which unified addressing maps into the device's
+// address space; on a Grace-Blackwell node the accesses run over NVLink-C2C),
+// else null: the caller's positions are then read or written by the pack and
+// unpack kernels themselves instead of through a staged copy.
+void* device_view(const void* host) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
 regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n, const int32_t* sow) {
     return regc_set_walkers2(h, pos, n, nullptr, sow);
 }
@@ -889,9 +907,14 @@ regc_status regc_set_walkers2(regc_handle* h, const float* pos, const int32_t* n
             wos[sow[w]] = w;
         }
     }
-    // one copy of the caller's buffer; repacking and the coordinate checks run on the device
-    cudaError_t e = cudaMemcpyAsync(h->d_xyz, pos, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyHostToDevice,
-                                    h->stream);
+    // repacking and the coordinate checks run on the device, reading a
+    // page-locked caller buffer in place, else one copy of it
+    const float* src = static_cast<const float*>(device_view(pos));
+    cudaError_t e = cudaSuccess;
+    if (!src) {
+        e = cudaMemcpyAsync(h->d_xyz, pos, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        src = h->d_xyz;
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->P.n, n, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     // species B's counts (without them every particle is B)
     if (e == cudaSuccess && h->P.gc2)
@@ -901,7 +924,7 @@ regc_status regc_set_walkers2(regc_handle* h, const float* pos, const int32_t* n
     if (e == cudaSuccess && sow)
         e = cudaMemcpyAsync(h->X.walker_of_state, wos, S * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) e = pack_walkers(h->d_xyz, h->P.n, S, nmax, h->P.g, h->P.pos, h->d_error, h->stream);
+    if (e == cudaSuccess) e = pack_walkers(src, h->P.n, S, nmax, h->P.g, h->P.pos, h->d_error, h->stream);
     if (e == cudaSuccess) e = launch_energy(h->P, h->P.efix, 1, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(flag, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -953,8 +976,11 @@ regc_status regc_get_walkers2(regc_handle* h, float* pos, int32_t* n, int32_t* n
     long long* ef = reinterpret_cast<long long*>(static_cast<char*>(h->h_stage) + 64);   // pinned
     cudaError_t e = cudaSuccess;
     if (pos) {
-        e = unpack_walkers(h->P.pos, (long long)S * nmax, h->d_xyz, h->stream);
-        if (e == cudaSuccess)
+        // a page-locked caller buffer is written in place by the unpacking kernel
+        float* dst = static_cast<float*>(device_view(pos));
+        e = unpack_walkers(h->P.pos, (long long)S * nmax, nmax, dst ? h->P.n : nullptr, dst ? dst : h->d_xyz,
+                           h->stream);
+        if (e == cudaSuccess && !dst)
             e = cudaMemcpyAsync(pos, h->d_xyz, (size_t)S * nmax * 3 * sizeof(float), cudaMemcpyDeviceToHost,
                                 h->stream);
     }

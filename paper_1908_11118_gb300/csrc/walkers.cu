@@ -25,9 +25,10 @@ __global__ void pack_walkers_kernel(const float* xyz, const int* n, int S, int n
     pos[k] = v;
 }
 
-__global__ void unpack_walkers_kernel(const float4* pos, long long count, float* xyz) {
+__global__ void unpack_walkers_kernel(const float4* pos, long long count, int nmax, const int* n, float* xyz) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
+    if (n && (int)(k % nmax) >= n[k / nmax]) return;   // beyond N: left as it was
     const float4 v = pos[k];
     xyz[3 * k] = v.x;
     xyz[3 * k + 1] = v.y;
@@ -44,9 +45,9 @@ cudaError_t pack_walkers(const float* xyz, const int* n, int S, int nmax, const 
     return cudaGetLastError();
 }
 
-cudaError_t unpack_walkers(const float4* pos, long long count, float* xyz, cudaStream_t s) {
+cudaError_t unpack_walkers(const float4* pos, long long count, int nmax, const int* n, float* xyz, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    unpack_walkers_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pos, count, xyz);
+    unpack_walkers_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pos, count, nmax, n, xyz);
     return cudaGetLastError();
 }
 

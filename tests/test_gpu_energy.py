@@ -70,3 +70,33 @@ def test_crowded_cell_falls_back_to_all_pairs():
     n[0] = 64
     pos[2, :64] = W.f32(cube + np.array([0.0, 0.0, -3.0]))               # the same in cell (2, 2, 1)
     energies_match(p, pos, n)
+
+
+def test_page_locked_walker_buffers_are_read_and_written_in_place():
+    """A page-locked position buffer is read by the repacking kernel itself
+    and a page-locked output buffer written by the unpacking kernel (no staged
+    copy): the walkers, energies and the run that follows are those of the
+    copied path, and entries beyond N of the output are left as they were."""
+    torch = pytest.importorskip("torch")
+    p = W.fcc111_paper_scale(L=4, M=4, nmax=64)
+    rng = np.random.default_rng(3)
+    pos, n = W.lattice_walkers(p, rng.integers(0, 33, p.S), seed=3)
+    pinned_in = torch.empty(pos.shape, dtype=torch.float32, pin_memory=True).numpy()
+    pinned_in[:] = pos
+    a, b = Regc(p), Regc(p)
+    a.set_walkers(pos.astype(np.float32), n)
+    b.set_walkers(pinned_in, n)
+    for h in (a, b):
+        h.sweep(4)
+        h.exchange()
+    pa, na, ea, sa = a.get_walkers()
+    out = (torch.full(pos.shape, -7.0, dtype=torch.float32, pin_memory=True).numpy(),
+           torch.empty(p.S, dtype=torch.int32, pin_memory=True).numpy(),
+           torch.empty(p.S, dtype=torch.float64, pin_memory=True).numpy(),
+           torch.empty(p.S, dtype=torch.int32, pin_memory=True).numpy())
+    pb, nb_, eb, sb = b.get_walkers(out=out)
+    assert np.array_equal(na, nb_) and np.array_equal(ea, eb) and np.array_equal(sa, sb)
+    for w in range(p.S):
+        assert np.array_equal(pa[w, :na[w]], pb[w, :nb_[w]])
+        assert np.all(pb[w, nb_[w]:] == -7.0)
+    assert b.check_energy() == 0.0
