@@ -347,6 +347,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
 }
 
 regc_status regc_batch_run(regc_batch* b, int n_steps) {
+    NvtxRange nvtx_("regc_batch_run");
     if (!b || n_steps < 0) return REGC_EINVAL;
     if (b->sticky != REGC_OK) return b->sticky;
     regc_status st = check_members(b);

@@ -555,6 +555,7 @@ regc_status regc_init_grid2(const regc_potential* pot, const regc_surface* surf,
 }
 
 regc_status regc_sweep(regc_handle* h, int n_sweeps) {
+    NvtxRange nvtx_("regc_sweep");
     if (!h || n_sweeps < 0) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
@@ -577,6 +578,7 @@ regc_status regc_test_expire_waits(regc_handle* h) {
 }
 
 regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* trace) {
+    NvtxRange nvtx_("regc_sweep_traced");
     if (!h || n_sweeps < 0 || (n_sweeps > 0 && !trace)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
@@ -681,6 +683,7 @@ static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canon
 }
 
 regc_status regc_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, int* n_exchanges) {
+    NvtxRange nvtx_("regc_cycle");
     return run_cycle(h, n_steps, x0, n_canonical, nullptr, n_exchanges);
 }
 
@@ -692,6 +695,7 @@ regc_status regc_cycle_traced(regc_handle* h, int n_steps, double x0, int n_cano
 
 regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, float dt, float tau,
                           int* n_exchanges) {
+    NvtxRange nvtx_("regc_cycle_md");
     if (!h || n_steps < 0 || md_steps < 0 || !(x0 >= 0.0 && x0 <= 1.0) || !(dt > 0.0f) || !(tau > 0.0f) ||
         !std::isfinite(dt) || !std::isfinite(tau) || h->P.gc2)
         return REGC_EINVAL;
@@ -712,6 +716,7 @@ regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, 
 }
 
 regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kinetic) {
+    NvtxRange nvtx_("regc_md");
     if (!h || n_steps < 0 || !(dt > 0.0f) || !(tau > 0.0f) || !std::isfinite(dt) || !std::isfinite(tau))
         return REGC_EINVAL;
     if (h->P.gc2) return REGC_EINVAL;   // MD with one grand-canonical species only
@@ -734,6 +739,7 @@ regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kin
 }
 
 regc_status regc_exchange(regc_handle* h) {
+    NvtxRange nvtx_("regc_exchange");
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const regc_status st = cuda_fail(h, launch_exchange(h->X, h->e, h->stream));
@@ -743,6 +749,7 @@ regc_status regc_exchange(regc_handle* h) {
 
 regc_status regc_histograms(regc_handle* h, int64_t* hN, int64_t* hNE, int64_t* omega, double* moments,
                             int64_t* e_out) {
+    NvtxRange nvtx_("regc_histograms");
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const size_t S = h->S;
@@ -892,6 +899,7 @@ regc_status regc_set_walkers(regc_handle* h, const float* pos, const int32_t* n,
 
 regc_status regc_set_walkers2(regc_handle* h, const float* pos, const int32_t* n, const int32_t* nb,
                               const int32_t* sow) {
+    NvtxRange nvtx_("regc_set_walkers2");
     if (!h || !pos || !n) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const int S = h->S, nmax = h->nmax;
@@ -969,6 +977,7 @@ regc_status regc_get_walkers(regc_handle* h, float* pos, int32_t* n, double* ene
 }
 
 regc_status regc_get_walkers2(regc_handle* h, float* pos, int32_t* n, int32_t* nb, double* energy, int32_t* sow) {
+    NvtxRange nvtx_("regc_get_walkers2");
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (nb && !h->P.gc2) return REGC_EINVAL;
@@ -1110,6 +1119,7 @@ regc_status surrogate_loaded(regc_handle* h);
 }  // namespace
 
 regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* length) {
+    NvtxRange nvtx_("regc_checkpoint");
     if (!h || !length) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const auto secs = ckpt_sections(h, h->has_sur);
@@ -1152,6 +1162,7 @@ regc_status regc_checkpoint(regc_handle* h, void* buf, size_t capacity, size_t* 
 }
 
 regc_status regc_restore(regc_handle* h, const void* buf, size_t length) {
+    NvtxRange nvtx_("regc_restore");
     if (!h || !buf || length < sizeof(CkptHeader)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     CkptHeader hd;
@@ -1303,6 +1314,7 @@ regc_status regc_surrogate_eval(regc_handle* h, int walker, int n_query, const f
 
 regc_status regc_surrogate_harvest(regc_handle* h, int particles, int probes, float e_clip, int capacity,
                                    int64_t* n_rows) {
+    NvtxRange nvtx_("regc_surrogate_harvest");
     if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip) || h->P.gc2) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->ds_cap == 0) {
@@ -1371,6 +1383,7 @@ regc_status regc_surrogate_dataset(regc_handle* h, int64_t max_rows, float* X, f
 }
 
 regc_status regc_surrogate_train(regc_handle* h, int steps, int batch, float lr, float* loss) {
+    NvtxRange nvtx_("regc_surrogate_train");
     if (!h || steps < 0 || batch < 1 || !(lr >= 0.0f) || !std::isfinite(lr)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (!h->has_sur || h->ds_count == 0) return REGC_EINVAL;
@@ -1560,6 +1573,7 @@ regc_status regc_pressure_of_mu(int n, const double* kT, const double* mu, doubl
 
 regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const double* mu_q, double tol, int max_iter,
                           double* N_mean, double* pN, double* f_states, int* iters) {
+    NvtxRange nvtx_("regc_reweight");
     if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;
     if (h->P.gc2) return REGC_EINVAL;   // two species: regc_reweight2
     for (int q = 0; q < nq; ++q)
@@ -1606,6 +1620,7 @@ regc_status regc_reweight(regc_handle* h, int nq, const double* kT_q, const doub
 regc_status regc_reweight2(regc_handle* h, int nq, const double* kT_q, const double* mu_q, const double* mu2_q,
                            double tol, int max_iter, double* NB_mean, double* NC_mean, double* pNB, double* pNC,
                            double* f_states, int* iters) {
+    NvtxRange nvtx_("regc_reweight2");
     if (!h || nq < 0 || (nq > 0 && (!kT_q || !mu_q || !mu2_q)) || !(tol > 0.0) || max_iter < 1) return REGC_EINVAL;
     if (!h->P.gc2) return REGC_EINVAL;   // one species: regc_reweight
     for (int q = 0; q < nq; ++q)
@@ -1704,6 +1719,7 @@ regc_status regc_mbar_last_info(regc_mbar_info* out) {
 regc_status regc_mbar_solve(int S, const double* kT, const double* mu, double lambda0, const double* omega, int B,
                             const int32_t* N_b, const double* E_b, const double* H_b, double tol, int max_iter,
                             double* f, double* D, int* iters, void* cuda_stream) {
+    NvtxRange nvtx_("regc_mbar_solve");
     if (S < 1 || B < 1 || !kT || !mu || !omega || !N_b || !E_b || !H_b || !(tol > 0.0) || max_iter < 1 ||
         !(lambda0 > 0.0))
         return REGC_EINVAL;
@@ -1749,6 +1765,7 @@ regc_status regc_mbar_solve(int S, const double* kT, const double* mu, double la
 regc_status regc_mbar_query(int Q, const double* kT_q, const double* mu_q, double lambda0, int B,
                             const int32_t* N_b, const double* E_b, const double* H_b, const double* D, int nmax,
                             double* N_mean, double* pN, double* f_q, void* cuda_stream) {
+    NvtxRange nvtx_("regc_mbar_query");
     if (Q < 1 || B < 1 || !kT_q || !mu_q || !N_b || !E_b || !H_b || !D || nmax < 0 || !(lambda0 > 0.0))
         return REGC_EINVAL;
     for (int q = 0; q < Q; ++q)

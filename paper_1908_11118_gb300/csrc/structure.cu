@@ -389,6 +389,7 @@ regc_status regc_structure_init(regc_handle* h, const regc_structure_spec* spec)
 }
 
 regc_status regc_structure_sample(regc_handle* h) {
+    NvtxRange nvtx_("regc_structure_sample");
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     StructureStore& st = h->stc;
@@ -556,6 +557,7 @@ regc_status regc_structure_get(regc_handle* h, int64_t first, int64_t count, int
 regc_status regc_structure_reweight(regc_handle* h, int nq, const double* kT_q, const double* mu_q, int n_lo,
                                     int n_hi, double tol, int max_iter, double* p, double* rho, double* gxy,
                                     double* f_states, int* iters) {
+    NvtxRange nvtx_("regc_structure_reweight");
     if (!h || nq < 1 || !kT_q || !mu_q || n_lo < 0 || n_hi < n_lo || max_iter < 1 || !(tol > 0.0)) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     const StructureStore& st = h->stc;
