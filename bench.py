@@ -54,6 +54,14 @@ WORKLOAD = ("fcc111 12x12x4 slab + LJ gas, 32 kT x 32 mu = 1024 replicas, Nmax 5
             "20 moves/sweep; step = 10 sweeps + 1 replica-exchange attempt")
 
 
+def bench_config(args):
+    """The `config` of the headline line, identical in both arms: the same
+    workload, the same seeded start and the same equilibration protocol."""
+    return {"workload": WORKLOAD, "equilibration_sweeps": args.equil,
+            "start": "seeded lattice state (seed 0), then the equilibration sweeps untimed",
+            "l2": "GPU arm: flushed (256 MB memset) before every timed step; host arm: n/a"}
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,8 +227,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "moves/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "equilibration_sweeps": args.equil,
-                                        "start": "seeded lattice state, equilibrated by the oracle itself"},
+        "data": "synthetic", "config": bench_config(args),
         "cpu_baseline": {"value": rate, "unit": "moves/s", "cores": cores, "kind": "oracle",
                          "sample": "full 1024-replica workload, %d steps of 10 sweeps + exchange" % steps},
         "e2e": {"value": rate, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1056,9 +1063,8 @@ def run_own(args):
             "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "equilibration_sweeps": args.equil,
-                       "l2": "flushed (256 MB memset) before every timed step",
-                       "precision": "pair energies f32, totals exact 64-bit fixed point, acceptance f64"},
+            "config": bench_config(args),
+            "precision": "pair energies f32, totals exact 64-bit fixed point, acceptance f64",
             "accepted_moves_per_s": accepted * world / (total_max / 1e3),
             "pair_interactions_per_s": pairs * world / (total_max / 1e3),
             "candidate_pairs_per_s": cand * world / (total_max / 1e3),

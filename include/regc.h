@@ -641,6 +641,9 @@ REGC_API regc_status regc_mbar_query(int Q, const double *kT_q, const double *mu
  *   - The first call on a device, with that device current, looks up the
  *     device address of the scratch area; make that first call before any
  *     stream capture.
+ *   - Like regc_mbar_solve, the call waits for its stream after every map of
+ *     the iteration (the Anderson step runs on the host) and returns when the
+ *     results are in the host buffers.
  *   - Every call on a device shares that one scratch area, and it keeps the
  *     last call's contents (the solver clears what it needs cleared).  Calls
  *     that overlap on the GPU -- on different streams or from different host
