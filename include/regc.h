@@ -253,6 +253,47 @@ REGC_API regc_status regc_md(regc_handle *h, int n_steps, float dt, float tau, f
  * Asynchronous.  The exchange counter advances by one per call. */
 REGC_API regc_status regc_exchange(regc_handle *h);
 
+/* ------------------------------------------------- one grid over several GPUs
+ *
+ * The paper runs its S replicas on S groups of cores that meet only at the
+ * replica exchange (Sec. II.A.4); the grid splits the same way over GPUs.
+ * Every process creates the same grid (same problem, seed and walkers), and
+ * process r steps only its own range of walkers.  Between two exchanges the
+ * walkers are independent; an exchange attempt (Sec. II.A.2, Eq. Pacc) reads
+ * only every walker's N and E and moves only state labels, so before each
+ * attempt the processes all-gather (N, E) of their ranges, write the other
+ * ranges into their handles with regc_set_walker_ne, and call regc_exchange.
+ * The exchange draws its direction, parity and uniforms from the shared Philox
+ * stream, so every process takes the same decisions and keeps the same state
+ * labels; configurations never move between processes.  Each process's
+ * histograms count only its own walkers' observations: their sum over the
+ * processes is the grid's.  With the same Philox key, sweep and exchange
+ * counters, a sharded run is the single-process run walker for walker. */
+
+/* Step only walkers [w_begin, w_end) in regc_sweep from now on (default
+ * [0, S)).  Calls that need every walker's configuration refuse a handle with
+ * a proper shard (REGC_EINVAL): regc_sweep_traced, regc_cycle*, regc_md,
+ * regc_surrogate_harvest, regc_structure_sample and batches; regc_check_energy
+ * checks the shard's walkers only.  Errors: REGC_EINVAL (0 <= w_begin <
+ * w_end <= S violated). */
+REGC_API regc_status regc_set_shard(regc_handle *h, int w_begin, int w_end);
+
+/* Particle counts and exact running energies of walkers [w_begin, w_end) into
+ * host buffers: n and nb [w_end - w_begin] (nb: species B, two-species handles
+ * only, else may be NULL), efix [w_end - w_begin] in units of 2^-30 of the
+ * energy unit (the library's exact fixed-point totals; E = efix * 2^-30).
+ * Synchronous.  Errors: REGC_EINVAL (range outside [0, S], a NULL buffer). */
+REGC_API regc_status regc_get_walker_ne(regc_handle *h, int w_begin, int w_end, int32_t *n, int32_t *nb,
+                                        int64_t *efix);
+
+/* Overwrite N (and N_B) and the running energies of walkers [w_begin, w_end)
+ * with the values another process owns (layout as regc_get_walker_ne); their
+ * positions here are left as they are, so only regc_exchange should read those
+ * walkers until they are owned again.  Synchronous.  Errors: REGC_EINVAL (range
+ * outside [0, S], a NULL buffer, N outside [0, nmax] or N_B outside [0, N]). */
+REGC_API regc_status regc_set_walker_ne(regc_handle *h, int w_begin, int w_end, const int32_t *n,
+                                        const int32_t *nb, const int64_t *efix);
+
 /* n_steps steps of the REGC cycle (Sec. II.A and its flow chart, Fig. 1;
  * Sec. III.A uses x0 = 0.99 and ten MC moves per step).  Step t (the sweep
  * counter: steps and sweeps share it) draws G = Philox((t, 0, 0, 10)):

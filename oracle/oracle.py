@@ -124,6 +124,9 @@ def lib():
         _lib.oracle_sweeps2.argtypes = [sp, C.c_int, dp, ip, ip, dp, ip, C.c_uint32, C.c_int,
                                         C.POINTER(_Hist), C.c_void_p, i64p, C.c_int]
         _lib.oracle_sweeps2.restype = C.c_int
+        _lib.oracle_sweeps_range.argtypes = [sp, C.c_int, dp, ip, ip, dp, ip, C.c_uint32, C.c_int,
+                                             C.POINTER(_Hist), C.c_void_p, i64p, C.c_int, C.c_int, C.c_int]
+        _lib.oracle_sweeps_range.restype = C.c_int
         _lib.oracle_exchange2.argtypes = [sp, C.c_uint32, ip, ip, dp, ip, ip, i64p]
         _lib.oracle_exchange2.restype = C.c_int
         _lib.oracle_total_energy2.argtypes = [sp, dp, C.c_int, C.c_int]
@@ -320,20 +323,23 @@ class Oracle:
         return lib().oracle_exchange_log_alpha(C.byref(self.sys), sa, sb, na, nb, ea, eb)
 
     # -- the sampler
-    def sweeps(self, n_sweeps: int, hist: bool = True, trace: bool = False):
+    def sweeps(self, n_sweeps: int, hist: bool = True, trace: bool = False, walkers=None):
+        """n_sweeps sweeps of every walker, or of walkers [b, e) given as
+        walkers=(b, e) (the others are left as they are)."""
         p = self.p
         S = p.S
+        b, e = (0, S) if walkers is None else (int(walkers[0]), int(walkers[1]))
         tr = np.zeros((S, n_sweeps, p.moves_per_sweep), MOVE_DTYPE) if trace else None
         h = None
         if hist:
             h = self._hist()
-        rc = lib().oracle_sweeps2(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
+        rc = lib().oracle_sweeps_range(C.byref(self.sys), S, _ptr(self.pos, C.c_double),
                                   _ptr(self.n, C.c_int32), _ptr(self.nb, C.c_int32) if self.two else None,
                                   _ptr(self.energy, C.c_double),
                                   _ptr(self.state_of_walker, C.c_int32), C.c_uint32(self.t),
                                   n_sweeps, C.byref(h) if h is not None else None,
                                   tr.ctypes.data if tr is not None else None,
-                                  _ptr(self.counts, C.c_int64), self.n_threads)
+                                  _ptr(self.counts, C.c_int64), self.n_threads, b, e)
         if rc != 0:
             raise ValueError("oracle_sweeps rejected its arguments")
         self.t += n_sweeps

@@ -685,12 +685,29 @@ int oracle_sweeps(const oracle_system *sys, int n_walkers, double *pos, int32_t 
                           counts, n_threads);
 }
 
+int oracle_sweeps_range(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
+                        double *energy, const int32_t *state_of_walker, uint32_t t0,
+                        int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                        int64_t *counts, int n_threads, int w_begin, int w_end);
+
 int oracle_sweeps2(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
                    double *energy, const int32_t *state_of_walker, uint32_t t0,
                    int n_sweeps, oracle_hist *hist, oracle_move *trace,
                    int64_t *counts, int n_threads)
 {
+    return oracle_sweeps_range(sys, n_walkers, pos, n, nb, energy, state_of_walker, t0, n_sweeps, hist, trace,
+                               counts, n_threads, 0, n_walkers);
+}
+
+/* The sweeps of walkers [w_begin, w_end) only (the others are left as they
+ * are): a process's share of a grid split over several processes. */
+int oracle_sweeps_range(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
+                        double *energy, const int32_t *state_of_walker, uint32_t t0,
+                        int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                        int64_t *counts, int n_threads, int w_begin, int w_end)
+{
     int S = n_states(sys);
+    if (w_begin < 0 || w_end > n_walkers || w_begin > w_end) return -1;
     if (n_walkers != S || sys->nmax < 1 || sys->moves_per_sweep < 0 || n_sweeps < 0) return -1;
     if (sys->gc2_type > 0 && (!nb || sys->n_cluster > 0 || sys->da)) return -1;
     char *seen = (char *)calloc((size_t)S, 1);
@@ -708,7 +725,7 @@ int oracle_sweeps2(const oracle_system *sys, int n_walkers, double *pos, int32_t
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
-    for (int w = 0; w < S; ++w) {
+    for (int w = w_begin; w < w_end; ++w) {
         oracle_move *tr = trace ? trace + (int64_t)w * n_sweeps * sys->moves_per_sweep : NULL;
         sweep_walker(sys, w, pos + (int64_t)w * sys->nmax * 3, n + w, nb ? nb + w : NULL, energy + w,
                      state_of_walker[w], t0, n_sweeps, hist, tr, counts);

@@ -169,6 +169,11 @@ int    oracle_sweeps2(const oracle_system *sys, int n_walkers, double *pos, int3
                       double *energy, const int32_t *state_of_walker, uint32_t t0,
                       int n_sweeps, oracle_hist *hist, oracle_move *trace,
                       int64_t *counts, int n_threads);
+/* oracle_sweeps2 for walkers [w_begin, w_end) only */
+int    oracle_sweeps_range(const oracle_system *sys, int n_walkers, double *pos, int32_t *n, int32_t *nb,
+                           double *energy, const int32_t *state_of_walker, uint32_t t0,
+                           int n_sweeps, oracle_hist *hist, oracle_move *trace,
+                           int64_t *counts, int n_threads, int w_begin, int w_end);
 int    oracle_exchange2(const oracle_system *sys, uint32_t e, const int32_t *n, const int32_t *nb,
                         const double *energy, int32_t *state_of_walker,
                         int32_t *walker_of_state, int64_t *ex_counts);

@@ -84,6 +84,9 @@ SIGNATURES = {
     "regc_sweep": ([_h, C.c_int], C.c_int),
     "regc_sweep_traced": ([_h, C.c_int, C.c_void_p], C.c_int),
     "regc_exchange": ([_h], C.c_int),
+    "regc_set_shard": ([_h, C.c_int, C.c_int], C.c_int),
+    "regc_get_walker_ne": ([_h, C.c_int, C.c_int, _ip, _ip, _lp], C.c_int),
+    "regc_set_walker_ne": ([_h, C.c_int, C.c_int, _ip, _ip, _lp], C.c_int),
     "regc_cycle": ([_h, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "regc_cycle_traced": ([_h, C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "regc_cycle_md": ([_h, C.c_int, C.c_double, C.c_int, C.c_float, C.c_float, C.POINTER(C.c_int)], C.c_int),

@@ -198,7 +198,7 @@ regc_status check_members(regc_batch* b) {
     for (size_t m = 0; m < b->members.size(); ++m) {
         regc_handle* h = b->members[m];
         if (h->sticky != REGC_OK) return h->sticky;
-        if ((h->P.delayed != 0) != (b->member_da[m] != 0) || h->need_walkers) return REGC_EINVAL;
+        if ((h->P.delayed != 0) != (b->member_da[m] != 0) || h->need_walkers || h->sharded()) return REGC_EINVAL;
         if (h->nmax != b->sys_host[m].nmax || (h->P.n_cluster > 0) != (b->sys_host[m].n_cluster > 0) ||
             h->P.gc2)
             return REGC_EINVAL;
@@ -240,7 +240,7 @@ regc_status regc_batch_create(regc_handle* const* handles, int count, int sweeps
     *out = nullptr;
     if (!handles || count < 1 || sweeps_per_step < 1) return REGC_EINVAL;
     for (int i = 0; i < count; ++i) {
-        if (!handles[i] || handles[i]->need_walkers || handles[i]->P.gc2) return REGC_EINVAL;
+        if (!handles[i] || handles[i]->need_walkers || handles[i]->P.gc2 || handles[i]->sharded()) return REGC_EINVAL;
         if (handles[i]->P.delayed && !handles[i]->has_sur) return REGC_EINVAL;
         if (handles[i]->sticky != REGC_OK) return handles[i]->sticky;
         for (int j = 0; j < i; ++j)

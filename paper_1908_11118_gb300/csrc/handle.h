@@ -49,6 +49,8 @@ struct StructureStore {
 };
 
 struct regc_handle {
+    // a shard (regc_set_shard) steps only walkers [P.w_begin, P.w_end)
+    bool sharded() const { return P.w_begin != 0 || P.w_end != S; }
     cudaStream_t stream = nullptr;
     int L = 0, M = 0, S = 0, nmax = 0, mps = 0, n_e_bins = 0;
     double lambda0 = 1.0, e_lo = 0.0, e_bin = 1.0;

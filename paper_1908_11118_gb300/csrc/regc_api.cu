@@ -396,6 +396,8 @@ regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const
     P.max_disp = grid->max_disp;
     P.th_disp = (unsigned long long)floor(grid->p_disp * 4294967296.0);
     P.S = S;
+    P.w_begin = 0;
+    P.w_end = S;
     P.nmax = grid->nmax;
     P.mps = grid->moves_per_sweep;
     P.key0 = (uint32_t)seed;
@@ -579,7 +581,7 @@ regc_status regc_test_expire_waits(regc_handle* h) {
 
 regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* trace) {
     NvtxRange nvtx_("regc_sweep_traced");
-    if (!h || n_sweeps < 0 || (n_sweeps > 0 && !trace)) return REGC_EINVAL;
+    if (!h || n_sweeps < 0 || (n_sweeps > 0 && !trace) || h->sharded()) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
     if (n_sweeps == 0) return REGC_OK;
@@ -612,6 +614,7 @@ regc_status regc_sweep_traced(regc_handle* h, int n_sweeps, regc_move_record* tr
 static regc_status run_cycle(regc_handle* h, int n_steps, double x0, int n_canonical, regc_move_record* trace,
                              int* n_exchanges) {
     if (h && h->P.gc2) return REGC_EINVAL;   // the REGC cycle with one grand-canonical species only
+    if (h && h->sharded()) return REGC_EINVAL;   // its replica exchanges need every walker's N and E
     if (!h || n_steps < 0 || n_canonical < 0 || n_canonical > 1023 || !(x0 >= 0.0 && x0 <= 1.0))
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
@@ -697,7 +700,7 @@ regc_status regc_cycle_md(regc_handle* h, int n_steps, double x0, int md_steps, 
                           int* n_exchanges) {
     NvtxRange nvtx_("regc_cycle_md");
     if (!h || n_steps < 0 || md_steps < 0 || !(x0 >= 0.0 && x0 <= 1.0) || !(dt > 0.0f) || !(tau > 0.0f) ||
-        !std::isfinite(dt) || !std::isfinite(tau) || h->P.gc2)
+        !std::isfinite(dt) || !std::isfinite(tau) || h->P.gc2 || h->sharded())
         return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
@@ -719,7 +722,7 @@ regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kin
     NvtxRange nvtx_("regc_md");
     if (!h || n_steps < 0 || !(dt > 0.0f) || !(tau > 0.0f) || !std::isfinite(dt) || !std::isfinite(tau))
         return REGC_EINVAL;
-    if (h->P.gc2) return REGC_EINVAL;   // MD with one grand-canonical species only
+    if (h->P.gc2 || h->sharded()) return REGC_EINVAL;   // MD: one grand-canonical species, every walker
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->need_walkers) return REGC_EINVAL;
     if (md_smem(h->nmax, h->P.cg.ncell, h->P.cg.cap) > kMaxSmem) return REGC_EINVAL;
@@ -736,6 +739,52 @@ regc_status regc_md(regc_handle* h, int n_steps, float dt, float tau, float* kin
     h->md_seg += 1;
     if (kinetic) return sync_check(h);
     return REGC_OK;
+}
+
+regc_status regc_set_shard(regc_handle* h, int w_begin, int w_end) {
+    if (!h || w_begin < 0 || w_end > h->S || w_begin >= w_end) return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    h->P.w_begin = w_begin;
+    h->P.w_end = w_end;
+    return REGC_OK;
+}
+
+regc_status regc_get_walker_ne(regc_handle* h, int w_begin, int w_end, int32_t* n, int32_t* nb, int64_t* efix) {
+    NvtxRange nvtx_("regc_get_walker_ne");
+    if (!h || w_begin < 0 || w_end > h->S || w_begin > w_end || !n || !efix || (h->P.gc2 && !nb))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const size_t k = (size_t)(w_end - w_begin);
+    if (k == 0) return REGC_OK;
+    cudaError_t e = cudaMemcpyAsync(n, h->P.n + w_begin, k * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(efix, h->P.efix + w_begin, k * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && h->P.gc2)
+        e = cudaMemcpyAsync(nb, h->P.nb + w_begin, k * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
+}
+
+regc_status regc_set_walker_ne(regc_handle* h, int w_begin, int w_end, const int32_t* n, const int32_t* nb,
+                               const int64_t* efix) {
+    NvtxRange nvtx_("regc_set_walker_ne");
+    if (!h || w_begin < 0 || w_end > h->S || w_begin > w_end || !n || !efix || (h->P.gc2 && !nb))
+        return REGC_EINVAL;
+    if (h->sticky != REGC_OK) return h->sticky;
+    const int k = w_end - w_begin;
+    for (int i = 0; i < k; ++i) {
+        if (n[i] < 0 || n[i] > h->nmax) return REGC_EINVAL;
+        if (h->P.gc2 && (nb[i] < 0 || nb[i] > n[i])) return REGC_EINVAL;
+    }
+    if (k == 0) return REGC_OK;
+    // the host buffers may be pageable: the copies complete before the call returns
+    cudaError_t e = cudaMemcpyAsync(h->P.n + w_begin, n, k * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->P.efix + w_begin, efix, k * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->P.gc2)
+        e = cudaMemcpyAsync(h->P.nb + w_begin, nb, k * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return sync_check(h);
 }
 
 regc_status regc_exchange(regc_handle* h) {
@@ -1019,7 +1068,9 @@ regc_status regc_check_energy(regc_handle* h, double* max_drift) {
     st = sync_check(h);
     if (st != REGC_OK) return st;
     double d = 0.0;
-    for (int w = 0; w < h->S; ++w) d = std::max(d, fabs((double)(a[w] - b[w]) * kFixUnit));
+    // under a shard the other walkers' positions here are stale: only the
+    // shard's walkers are checked
+    for (int w = h->P.w_begin; w < h->P.w_end; ++w) d = std::max(d, fabs((double)(a[w] - b[w]) * kFixUnit));
     if (max_drift) *max_drift = d;
     return REGC_OK;
 }
@@ -1315,7 +1366,8 @@ regc_status regc_surrogate_eval(regc_handle* h, int walker, int n_query, const f
 regc_status regc_surrogate_harvest(regc_handle* h, int particles, int probes, float e_clip, int capacity,
                                    int64_t* n_rows) {
     NvtxRange nvtx_("regc_surrogate_harvest");
-    if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip) || h->P.gc2) return REGC_EINVAL;
+    if (!h || particles < 0 || probes < 0 || capacity < 0 || std::isnan(e_clip) || h->P.gc2 || h->sharded())
+        return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     if (h->ds_cap == 0) {
         if (capacity < 1) return REGC_EINVAL;

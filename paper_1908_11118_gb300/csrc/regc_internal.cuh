@@ -144,6 +144,7 @@ struct SweepParams {
     float max_disp;
     unsigned long long th_disp;   // displacement if A0 < th_disp (0 .. 2^32)
     int S, nmax, mps;
+    int w_begin, w_end;    // the walkers a sweep steps: [w_begin, w_end) (a shard; 0, S by default)
     uint32_t key0, key1;
     const double* beta;    // [S] per state
     const double* c_ins;   // [S] ln V - 3 ln Lambda_s + beta_s mu_s

@@ -393,7 +393,7 @@ regc_status regc_structure_sample(regc_handle* h) {
     if (!h) return REGC_EINVAL;
     if (h->sticky != REGC_OK) return h->sticky;
     StructureStore& st = h->stc;
-    if (!st.block || h->need_walkers || st.count + h->S > st.cap) return REGC_EINVAL;
+    if (!st.block || h->need_walkers || h->sharded() || st.count + h->S > st.cap) return REGC_EINVAL;
     SampleParams P;
     P.pos = h->P.pos;
     P.n = h->P.n;

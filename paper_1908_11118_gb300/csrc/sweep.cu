@@ -1033,8 +1033,9 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
 template <int K, bool TRACE, bool DA, bool CL>
 __global__ void __launch_bounds__(32 * K, K == 4 ? 7 : 1) sweep_kernel(const __grid_constant__ SweepParams P) {
     extern __shared__ __align__(16) char smem[];
-    if (blockIdx.x >= (unsigned)P.S) return;
-    walker_sweep<K, TRACE, DA, CL>(P, blockIdx.x, smem, threadIdx.x, 0);
+    const int w = P.w_begin + (int)blockIdx.x;
+    if (w >= P.w_end) return;
+    walker_sweep<K, TRACE, DA, CL>(P, w, smem, threadIdx.x, 0);
 }
 
 // Displacement q - p with the exact minimum image on periodic axes (cell
@@ -1218,17 +1219,19 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const __grid_con
 template <int K, bool DA, bool CL>
 cudaError_t launch_k(const SweepParams& P, cudaStream_t s) {
     const size_t smem = smem_bytes(P.nmax, P.cg.ncell, P.cg.cap, K);
+    const int n_walkers = P.w_end - P.w_begin;   // one CTA per walker of the shard
+    if (n_walkers <= 0) return cudaSuccess;
     cudaError_t err;
     if (P.trace) {
         err = cudaFuncSetAttribute(sweep_kernel<K, true, DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, true, DA, CL><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, true, DA, CL><<<n_walkers, 32 * K, smem, s>>>(P);
     } else {
         err = cudaFuncSetAttribute(sweep_kernel<K, false, DA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
         if (err != cudaSuccess) return err;
-        sweep_kernel<K, false, DA, CL><<<P.S, 32 * K, smem, s>>>(P);
+        sweep_kernel<K, false, DA, CL><<<n_walkers, 32 * K, smem, s>>>(P);
     }
     return cudaGetLastError();
 }

@@ -89,6 +89,7 @@ class Regc:
         self.mps = int(problem.moves_per_sweep)
         self.n_e_bins = int(problem.n_e_bins)
         self.hE_bins = 0
+        self.shard = (0, self.S)
 
     # -- lifetime
     def close(self):
@@ -119,6 +120,33 @@ class Regc:
 
     def exchange(self):
         check(_lib.lib().regc_exchange(self._h), "regc_exchange")
+
+    # -- one grid over several processes (regc_set_shard; see shard.py)
+    def set_shard(self, w_begin: int, w_end: int):
+        """Step only walkers [w_begin, w_end) from now on."""
+        check(_lib.lib().regc_set_shard(self._h, int(w_begin), int(w_end)), "regc_set_shard")
+        self.shard = (int(w_begin), int(w_end))
+
+    def walker_ne(self, w_begin: int, w_end: int):
+        """(N, N_B or None, exact energies as int64 units of 2^-30) of walkers
+        [w_begin, w_end)."""
+        k = int(w_end) - int(w_begin)
+        n = np.zeros(k, np.int32)
+        nb = np.zeros(k, np.int32) if self.two else None
+        e = np.zeros(k, np.int64)
+        check(_lib.lib().regc_get_walker_ne(self._h, int(w_begin), int(w_end), _p(n, C.c_int32),
+                                            _p(nb, C.c_int32),
+                                            _p(e, C.c_int64)), "regc_get_walker_ne")
+        return n, nb, e
+
+    def set_walker_ne(self, w_begin: int, n, nb, efix):
+        """Write another process's walkers' N (N_B) and exact energies from w_begin on."""
+        n = np.ascontiguousarray(n, np.int32)
+        e = np.ascontiguousarray(efix, np.int64)
+        nbc = np.ascontiguousarray(nb, np.int32) if nb is not None else None
+        check(_lib.lib().regc_set_walker_ne(self._h, int(w_begin), int(w_begin) + len(n), _p(n, C.c_int32),
+                                            _p(nbc, C.c_int32),
+                                            _p(e, C.c_int64)), "regc_set_walker_ne")
 
     def cycle(self, n_steps: int, x0: float, n_canonical: int) -> int:
         """n_steps steps of the REGC cycle (regc_cycle); returns the number of
