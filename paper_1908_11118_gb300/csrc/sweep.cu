@@ -697,11 +697,22 @@ __device__ void evaluate_move(const SweepParams& P, const WalkerSmem& S, const S
     }
 }
 
+// floor(d / bin) for d >= 0 and bin >= 1 from the FP64 quotient (inv = 1 / bin
+// in FP64): within one of it while the quotient is below 2^52, so one
+// correction settles it; the integer division remains for anything beyond.
+__device__ __forceinline__ long long floor_div_fp64(long long d, long long bin, double inv) {
+    long long q = (long long)((double)d * inv);
+    if (q * bin > d) --q;
+    else if ((q + 1) * bin <= d) ++q;
+    if (q < 0 || q * bin > d || (q + 1) * bin <= d) q = d / bin;
+    return q;
+}
+
 // One observation of energy E (2^-30 units) into state s's own histogram:
 // bin 0 below the window, k + 1 for window bin k, hE_bins + 1 at or beyond its end.
-__device__ __forceinline__ void observe_state_energy(const SweepParams& P, int s, long long E) {
+__device__ __forceinline__ void observe_state_energy(const SweepParams& P, int s, long long E, double inv_bin) {
     const long long d = E - P.hE_lo_fix[s];
-    const long long kb = d >= 0 ? d / P.hE_bin_fix : -1;
+    const long long kb = d >= 0 ? floor_div_fp64(d, P.hE_bin_fix, inv_bin) : -1;
     const int idx = kb < 0 ? 0 : (kb >= P.hE_bins ? P.hE_bins + 1 : (int)kb + 1);
     atomicAdd(&P.hE[size_t(s) * (P.hE_bins + 2) + idx], 1ull);
 }
@@ -767,6 +778,12 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
     const float rc_guard = P.g.rc2 * 1.0004f + 1e-6f;   // a little beyond rc, conservatively
     int filled = 0;   // moves whose Philox blocks are in the ring
     int m0 = P.m_first;   // first move of the round
+    // the committer's statistics and move place, in its registers
+    WalkerStats sr = WalkerStats{0, 0, 0, 0.0, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, {0, 0, 0}, {0, 0, 0}, 0, 0};
+    int kcur = P.m_first % P.mps;
+    // energy bins of the observations without a 64-bit integer division
+    const double inv_ebin = 1.0 / (double)P.e_bin_fix;
+    const double inv_hebin = P.hE ? 1.0 / (double)P.hE_bin_fix : 0.0;
 
     while (m0 < total_moves) {
         // 3a. Philox blocks of the next 32 moves, drawn by all lanes at once
@@ -793,8 +810,8 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
         group_sync<K>(bar);
 
         // 4. commit in order (thread 0)
+        int committed = 0;
         if (tid == 0) {
-            int committed = 0;
             bool any_acc = false, n_changed = false;
             float chx[2 * K], chy[2 * K], chz[2 * K];   // positions changed by accepted moves
             int nch = 0;
@@ -848,8 +865,8 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                 if (DA && status == 0) {
                     // both stages were decided by the evaluating warp (one warp per walker)
                     accepted = !ovl && r.dec == 1;
-                    S.stats->screened += 1;
-                    S.stats->passed += r.stage1;
+                    sr.screened += 1;
+                    sr.passed += r.stage1;
                     if (TRACE) {
                         double c = 0.0;
                         if (r.type == 1) c = cins[s] - P.ln_tab[gcnt + 1];
@@ -929,14 +946,20 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     E += dfix;
                     N += (r.type == 1) - (r.type == 2);
                 }
-                WalkerStats& st = *S.stats;
-                st.tr[r.type] += 1;
-                st.ac[r.type] += accepted;
+                WalkerStats& st = sr;
+                st.tr[0] += r.type == 0;
+                st.tr[1] += r.type == 1;
+                st.tr[2] += r.type == 2;
+                st.ac[0] += accepted && r.type == 0;
+                st.ac[1] += accepted && r.type == 1;
+                st.ac[2] += accepted && r.type == 2;
                 // pairs that entered dE (a move that became impossible in this
                 // round, status 1, has none, whatever its evaluation counted)
                 if (status != 1) st.pairs += (unsigned)(r.flags >> 1);
-                const int ts = m / P.mps, k = m - ts * P.mps;
+                const int k = kcur;
+                kcur = kcur + 1 == P.mps ? 0 : kcur + 1;
                 if (TRACE) {
+                    const int ts = m / P.mps;
                     regc_move_record t;
                     t.type = r.type;
                     t.index = status == 1 ? 0 : (r.type == 1 ? ((two && r.gy == 0) ? split_before : n_before) : r.idx);
@@ -972,29 +995,41 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     const double e = (double)E * kFixUnit;
                     st.mE2 = fma(e, e, st.mE2);
                     const long long d = E - P.e_lo_fix;
-                    const long long kb = d >= 0 ? d / P.e_bin_fix : -1;
+                    const long long kb = d >= 0 ? floor_div_fp64(d, P.e_bin_fix, inv_ebin) : -1;
                     const size_t row = two ? size_t(NB) * (P.nmax + 1) + NC : size_t(NB);
                     if (kb >= 0 && kb < P.n_e_bins) atomicAdd(&P.hNE[row * P.n_e_bins + (size_t)kb], 1ull);
                     else st.eo += 1;
-                    if (P.hE) observe_state_energy(P, s, E);
+                    if (P.hE) observe_state_energy(P, s, E, inv_hebin);
                 }
                 ++committed;
             }
-            S.hdr->N = N;
-            S.hdr->E = E;
-            S.hdr->split = split;
-            S.hdr->committed = committed;
-            S.stats->rounds += 1;
-            S.stats->evals += min(K, total_moves - m0);
+            if (K > 1) {
+                S.hdr->N = N;
+                S.hdr->E = E;
+                S.hdr->split = split;
+                S.hdr->committed = committed;
+            }
+            sr.rounds += 1;
+            sr.evals += min(K, total_moves - m0);
         }
         group_sync<K>(bar);
-        N = S.hdr->N;
-        E = S.hdr->E;
-        split = S.hdr->split;
-        m0 += S.hdr->committed;
-        group_sync<K>(bar);   // the header and results are rewritten by the next round
+        if (K == 1) {
+            // the committer is lane 0 of the walker's one warp
+            N = __shfl_sync(FULL, N, 0);
+            E = __shfl_sync(FULL, E, 0);
+            split = __shfl_sync(FULL, split, 0);
+            m0 += __shfl_sync(FULL, committed, 0);
+        } else {
+            N = S.hdr->N;
+            E = S.hdr->E;
+            split = S.hdr->split;
+            m0 += S.hdr->committed;
+            group_sync<K>(bar);   // the header and results are rewritten by the next round
+        }
     }
 
+    if (tid == 0) *S.stats = sr;
+    group_sync<K>(bar);
     // 7. write back
     for (int j = tid; j < N; j += 32 * K) gpos[j] = S.pos[j];
     // candidate distances evaluated (all evaluations, kept or not)
