@@ -102,3 +102,34 @@ def test_walker_ne_round_trip_and_refusals():
         g0.md(2, 0.001, 0.1)
     g0.set_shard(0, p.S)                                    # the whole grid again
     g0.sweep_traced(1)
+
+
+def test_sharded_two_species_grid_matches_one_handle():
+    """Two grand-canonical species (N_B carried with N and E, the fifth
+    exchange direction along mu_C): three sharded handles against one."""
+    p = W.two_gas_small(seed=5)
+    rng = np.random.default_rng(5)
+    pos, n, nbv = W.two_gas_initial(p, rng.integers(0, 6, p.S), rng.integers(0, 6, p.S), seed=5)
+    full = Regc(p)
+    full.set_walkers(pos, n, nb=nbv)
+    parts = []
+    for r in range(3):
+        g = Regc(p)
+        g.set_walkers(pos, n, nb=nbv)
+        g.set_shard(*shard.shard_range(p.S, r, 3))
+        parts.append(g)
+    for _ in range(6):
+        full.sweep(10)
+        full.exchange()
+        for g in parts:
+            g.sweep(10)
+        _exchange_all(parts)
+    fp, fn, fe, fs = full.get_walkers()
+    fnb = full.walker_ne(0, p.S)[1]
+    for g in parts:
+        b, e = g.shard
+        gp, gn, ge, gs = g.get_walkers()
+        assert np.array_equal(gs, fs)
+        assert np.array_equal(gn[b:e], fn[b:e]) and np.array_equal(ge[b:e], fe[b:e])
+        assert np.array_equal(g.walker_ne(b, e)[1], fnb[b:e])
+        assert np.array_equal(gp[b:e], fp[b:e])
