@@ -26,15 +26,43 @@ constexpr float kFeatC0 = 0.8f, kFeatDc = 1.7f / 15.0f;
 // exp(-eta (r - c)^2) = exp2(-eta log2(e) (r - c)^2)
 constexpr float kFeatEta2 = 1.4426950408889634f / (2.0f * (1.7f / 15.0f) * (1.7f / 15.0f));
 
+// The 16 Gaussians of one neighbour from six exponentials.  With eta = 1 /
+// (2 dc^2) and u = (r - c_a) / dc at an anchor centre a, the Gaussian there is
+// exp(-u^2 / 2) and neighbouring centres follow by ratios:
+//   g_{k+1} = g_k exp(u_k - 1/2),   g_{k-1} = g_k exp(-u_k - 1/2),
+// with u_{k+1} = u_k - 1, so each ratio is the previous one times e^-1.
+// Anchors 4 and 11 keep every chain within four products; a Gaussian that is
+// reached through many products or from a tiny anchor value is itself tiny
+// (far from r), so its error stays far below the feature tolerance.
+constexpr float kLog2E = 1.4426950408889634f;
+constexpr float kInvE = 0.36787944117144233f;   // e^-1
+
+template <int A, int K0, int K1>
+__device__ __forceinline__ void gaussians_from(float (&g)[kNF], float r) {
+    const float u = (r - (kFeatC0 + kFeatDc * A)) * (1.0f / kFeatDc);
+    g[A] = exp2f(-0.5f * kLog2E * u * u);
+    float up = exp2f(kLog2E * (u - 0.5f)), dn = exp2f(-kLog2E * (u + 0.5f));
+#pragma unroll
+    for (int k = A + 1; k <= K1; ++k) {
+        g[k] = g[k - 1] * up;
+        up *= kInvE;
+    }
+#pragma unroll
+    for (int k = A - 1; k >= K0; --k) {
+        g[k] = g[k + 1] * dn;
+        dn *= kInvE;
+    }
+}
+
 // Add one neighbour at squared distance r2 < rc^2 with weight w to F.
 __device__ __forceinline__ void add_features(float (&F)[kNF], float r2, float w, float rc) {
     const float r = sqrtf(r2);
     const float fc = 0.5f * (__cosf(3.14159265358979f * r / rc) + 1.0f) * w;
+    float g[kNF];
+    gaussians_from<4, 0, 7>(g, r);
+    gaussians_from<11, 8, 15>(g, r);
 #pragma unroll
-    for (int k = 0; k < kNF; ++k) {
-        const float d = r - (kFeatC0 + kFeatDc * k);
-        F[k] = fmaf(fc, exp2f(-kFeatEta2 * d * d), F[k]);
-    }
+    for (int k = 0; k < kNF; ++k) F[k] = fmaf(fc, g[k], F[k]);
 }
 
 // Warp sum of 16 values per lane by recursive halving; afterwards lane l holds
