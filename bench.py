@@ -23,6 +23,7 @@ Under torchrun (N > 1) every rank runs its own independent 1024-replica grid
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -122,7 +123,8 @@ def job_throughput(local_ms, local_moves, world, device):
 
 def fp32_peak(stream=None):
     """FP32 ALU peak: the peaks file's, if it has one; else measured here by the
-    library's FFMA-loop probe; the unit-count figure is printed beside it."""
+    FFMA-loop probe (libregc_probe.so, include/regc_probe.h); the unit-count
+    figure is printed beside it."""
     derived = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -133,8 +135,20 @@ def fp32_peak(stream=None):
                     return float(d[k]), "MEASURED_PEAKS.json (%s)" % k
         except Exception:
             pass
-    from paper_1908_11118_gb300 import probe_fp32_peak
-    best = max(probe_fp32_peak(20000, stream) for _ in range(3))
+    from paper_1908_11118_gb300 import build as B
+    probe = ctypes.CDLL(B.PROBE_LIB)
+    probe.regc_probe_fp32_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    probe.regc_probe_fp32_peak.restype = ctypes.c_int
+    from paper_1908_11118_gb300.regc import _stream_handle
+    handle = _stream_handle(stream)
+
+    def once():
+        t = ctypes.c_double(0.0)
+        rc = probe.regc_probe_fp32_peak(20000, handle, ctypes.byref(t))
+        if rc != 0:
+            raise RuntimeError("regc_probe_fp32_peak returned %d" % rc)
+        return t.value
+    best = max(once() for _ in range(3))
     return best, ("measured on this GPU: FFMA-loop probe (regc_probe_fp32_peak, best of 3); unit-count figure "
                   "152 SMs x 128 lanes x 2 flop x 2070 MHz = %.1f TFLOP/s" % derived)
 

@@ -865,14 +865,6 @@ REGC_API regc_status regc_batch_sync(regc_batch *b);
 /* Release the batch (not its members).  NULL is accepted. */
 REGC_API void regc_batch_free(regc_batch *b);
 
-/* ----------------------------------------------------------- measurement */
-
-/* FP32 peak of the current GPU, measured: an FFMA-loop kernel (8 independent
- * chains per thread, 8 CTAs of 256 threads per SM, `iters` x 128 FMA per
- * thread) timed with CUDA events on cuda_stream after one warm-up launch.
- * *tflops receives 2 x FMAs / time in TFLOP/s.  Synchronous. */
-REGC_API regc_status regc_probe_fp32_peak(int iters, void *cuda_stream, double *tflops);
-
 /* Human-readable name of a status. */
 REGC_API const char *regc_status_string(regc_status s);
 

@@ -5,5 +5,5 @@ library built from ``csrc/`` (C ABI in ``include/regc.h``); ``Regc`` and the
 ``mbar_*`` functions are its Python binding.
 """
 from .regc import (MOVE_DTYPE, SURROGATE_PARAMS, Batch, Regc, mbar_last_info, mbar_query, mbar_solve,  # noqa: F401
-                   mu_of_pressure, pressure_of_mu, probe_fp32_peak, surrogate_gradient)
+                   mu_of_pressure, pressure_of_mu, surrogate_gradient)
 from ._lib import RegcError  # noqa: F401

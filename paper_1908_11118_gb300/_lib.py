@@ -138,7 +138,6 @@ SIGNATURES = {
     "regc_surrogate_gradient": ([C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_void_p], C.c_int),
     "regc_surrogate_gradient_bf16": ([C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_void_p], C.c_int),
     "regc_surrogate_set_dataset": ([_h, C.c_int64, _fp, _fp, C.c_int], C.c_int),
-    "regc_probe_fp32_peak": ([C.c_int, C.c_void_p, _dp], C.c_int),
     "regc_batch_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "regc_batch_run": ([_h, C.c_int], C.c_int),
     "regc_batch_autotune": ([_h, C.c_int], C.c_int),

@@ -5,6 +5,7 @@
 // eight independent chains of fused multiply-adds (enough independent work to
 // hide the FMA latency at full occupancy), on 8 CTAs of 256 threads per SM.
 #include "launch.h"
+#include "../../include/regc_probe.h"
 
 namespace regc {
 namespace {

@@ -530,13 +530,6 @@ def surrogate_gradient(theta, X, y, stream=None, tensor_cores: bool = False):
     return float(loss.value), g
 
 
-def probe_fp32_peak(iters: int = 20000, stream=None) -> float:
-    """Measured FP32 FFMA peak of the current GPU in TFLOP/s."""
-    t = C.c_double(0)
-    check(_lib.lib().regc_probe_fp32_peak(int(iters), _stream_handle(stream), C.byref(t)), "regc_probe_fp32_peak")
-    return t.value
-
-
 def mbar_solve(kT, mu, lambda0, omega, N_b, E_b, H_b, tol=1e-10, max_iter=100000, stream=None):
     """Device MBAR solve over pooled bins; returns (f [S], D [B], iterations)."""
     kT = np.ascontiguousarray(kT, np.float64)

@@ -29,6 +29,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(_lib.SIGNATURES) == set(names)
 
 
+def test_probe_library_exports_its_header():
+    """The FP32 peak probe (measurement tooling) is its own library: it
+    exports what include/regc_probe.h declares, and libregc.so does not."""
+    B.build()
+    probe = C.CDLL(B.PROBE_LIB)
+    names = _lib.declared_symbols(os.path.join(os.path.dirname(_lib.HEADER), "regc_probe.h"))
+    assert names == ["regc_probe_fp32_peak"]
+    assert all(hasattr(probe, n) for n in names)
+    assert not hasattr(_lib.lib(), "regc_probe_fp32_peak")
+
+
 def test_status_strings(lib):
     assert lib.regc_status_string(0) == b"ok"
     assert lib.regc_status_string(-1) == b"invalid argument"
