@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import gc
 import json
 import os
 import statistics
@@ -1010,17 +1011,27 @@ def run_own(args):
     g.get_walkers(out=host)
     pos_h, n_h, e_h, sow_h = host
     e2e_steps = max(1, args.e2e_steps)
-    for _ in range(2):   # warm-up of the host path
-        g.set_walkers(pos_h, n_h, sow_h)
-        g.get_walkers(out=host)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(2):   # warm-up of the host path, whole steps
         g.set_walkers(pos_h, n_h, sow_h)
         g.sweep(SWEEPS_PER_STEP)
         g.exchange()
         g.get_walkers(out=host)
+    torch.cuda.synchronize()
+    # the harness's own garbage collection stays out of the timed loop
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
+    e2e_each = []
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ts = time.perf_counter()
+        g.set_walkers(pos_h, n_h, sow_h)
+        g.sweep(SWEEPS_PER_STEP)
+        g.exchange()
+        g.get_walkers(out=host)
+        e2e_each.append(time.perf_counter() - ts)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if gc_was_enabled:
+        gc.enable()
     h2d = p.S * p.nmax * 12 + p.S * 4 * 2
     d2h = p.S * p.nmax * 12 + p.S * (4 + 8 + 4) + 4
 
@@ -1088,7 +1099,9 @@ def run_own(args):
                          "work": "%d flop/pair x pairs within rc (%.3g per launch)" % (FLOPS_PER_PAIR, pairs / K),
                          "launch_ms": mean_sweep_s * 1e3},
             "e2e": {"value": p.S * SWEEPS_PER_STEP * p.moves_per_sweep * world / e2e_s, "unit": "moves/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "ms_per_step_mean": e2e_s * 1e3,
+                    "ms_per_step_median": statistics.median(e2e_each) * 1e3, "ms_per_step_max": max(e2e_each) * 1e3},
             "speculation": {"warps_per_walker": g.warps_per_walker(),
                             "moves_per_round": moves / max(rounds, 1),
                             "kept_fraction": moves / max(evals, 1)},

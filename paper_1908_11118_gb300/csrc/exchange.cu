@@ -18,7 +18,7 @@ namespace {
 // every k-slice.  With two species the swap rule takes both: the Lambda
 // factor the total N (both wavelengths scale as beta^(1/2)), the mu terms
 // each species' count.
-__device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t e) {
+__device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t e, int first, int stride) {
     const int K = X.K;
     const int n_dir = K > 1 ? 5 : 4;
     const U4 C = philox(e, 0u, 0u, 2u, X.key0, X.key1);
@@ -28,7 +28,7 @@ __device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t 
     const int dl = (type == 1 || type == 4) ? 0 : 1;
     const int dm = (type == 0 || type == 4) ? 0 : (type == 3 ? -1 : 1);
     const int S = X.L * X.M * K;
-    for (int a = threadIdx.x; a < S; a += blockDim.x) {
+    for (int a = first; a < S; a += stride) {
         const int lm = a / K, k = a - lm * K;
         const int l = lm / X.M, m = lm - l * X.M;
         const int key = dk ? k : (dl ? l : m);
@@ -50,7 +50,17 @@ __device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t 
                  (X.bmu[a] - X.bmu[b]) * dn;
         }
         const U4 D = philox(e, (uint32_t)a, 0u, 3u, X.key0, X.key1);
-        const bool acc = log(((double)D.x + 0.5) * 2.3283064365386963e-10) < la;
+        // ln u < ln alpha, decided in binary32 when the two sides are more than
+        // 1e-3 apart (ln u to about 1e-6, and ln alpha's rounding matters only
+        // where it is within a few units of ln u >= -22.2), else in FP64: the
+        // FP64 decision in every case, without an FP64 logarithm per pair on
+        // this part's narrow FP64 pipe
+        const float lu_f = __logf(((float)D.x + 0.5f) * 2.3283064365386963e-10f);
+        const float la_f = (float)la;
+        bool acc;
+        if (lu_f < la_f - 1e-3f) acc = true;
+        else if (lu_f > la_f + 1e-3f) acc = false;
+        else acc = log(((double)D.x + 0.5) * 2.3283064365386963e-10) < la;
         X.ex_counts[2 * n_dir * a + 2 * type] += 1;
         X.ex_counts[2 * n_dir * a + 2 * type + 1] += acc;
         if (acc) {
@@ -62,8 +72,12 @@ __device__ __forceinline__ void exchange_grid(const ExchangeParams& X, uint32_t 
     }
 }
 
-__global__ void __launch_bounds__(1024) exchange_kernel(const __grid_constant__ ExchangeParams X, uint32_t e) {
-    exchange_grid(X, e);
+// The pairs of one attempt are disjoint (every state of the drawn parity with
+// its neighbour in the drawn direction), so they are spread over CTAs.
+constexpr int kExThreads = 128;
+
+__global__ void __launch_bounds__(kExThreads) exchange_kernel(const __grid_constant__ ExchangeParams X, uint32_t e) {
+    exchange_grid(X, e, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // One exchange attempt of every grid of a batch (CTA m: grid m, attempt
@@ -75,7 +89,7 @@ __global__ void __launch_bounds__(256) batch_exchange_kernel(const ExchangeParam
     const int m = blockIdx.x;
     const ExchangeParams X = xs[m];
     const uint32_t e = e_ctr[m];
-    exchange_grid(X, e);
+    exchange_grid(X, e, threadIdx.x, blockDim.x);
     __syncthreads();
     if (threadIdx.x == 0) {
         e_ctr[m] = e + 1u;
@@ -93,7 +107,8 @@ cudaError_t launch_batch_exchange(const ExchangeParams* xs, uint32_t* e_ctr, Swe
 }
 
 cudaError_t launch_exchange(const ExchangeParams& X, uint32_t e, cudaStream_t s) {
-    exchange_kernel<<<1, 1024, 0, s>>>(X, e);
+    const int S = X.L * X.M * X.K;
+    exchange_kernel<<<(S + kExThreads - 1) / kExThreads, kExThreads, 0, s>>>(X, e);
     return cudaGetLastError();
 }
 
