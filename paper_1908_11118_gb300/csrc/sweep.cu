@@ -815,6 +815,9 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
             bool any_acc = false, n_changed = false;
             float chx[2 * K], chy[2 * K], chz[2 * K];   // positions changed by accepted moves
             int nch = 0;
+            // not unrolled: one copy of the commit keeps the speculative kernels'
+            // code small enough for the instruction caches (K = 4: 153 -> 86 KB)
+#pragma unroll 1
             for (int j = 0; j < K && m0 + j < total_moves; ++j) {
                 const MoveRes r = S.res[j];
                 const int m = m0 + j;
