@@ -830,6 +830,7 @@ __device__ __forceinline__ void walker_sweep(const SweepParams& P, int w, char* 
                     // change would differ; the old position of a displacement is
                     // checked whatever its status, since its particle may have moved
                     if (valid && (r.status == 0 || (r.type == 0 && r.status == 2))) {
+#pragma unroll 1   // rolled for the same reason as the commit loop
                         for (int c = 0; c < nch; ++c) {
                             if (r.status == 0 && dist2(P, chx[c], chy[c], chz[c], r.q0x, r.q0y, r.q0z) < rc_guard)
                                 valid = false;
