@@ -192,20 +192,21 @@ regc_status init_grid(const regc_potential* pot, const regc_surface* surf, const
         !(grid->e_bin < 4294967296.0))
         return REGC_EINVAL;
     // warps per walker = moves evaluated speculatively per round (1, 2 or 4).
-    // With many walkers per SM one is best: on the 1024-replica workload two
-    // and four warps keep 93 % and 79 % of their speculative evaluations but
-    // lose more to the round barriers and the serial commit than they gain.
-    // With a walker or two per SM the issue slots are idle and speculation
-    // pays: 160 replicas of the LJ A18 system run 1.24x faster with two warps
-    // and 1.33x with four.  REGC_WARPS_PER_WALKER overrides the choice.
+    // With many walkers per SM one is best: on the 1024-replica fcc(111)
+    // workload two and four warps run at 0.58x and 0.44x of one (instruction
+    // fetch and the round barriers outweigh the kept evaluations).  With about
+    // one walker per SM the issue slots are idle and speculation pays: 160
+    // replicas of the LJ A18 system run 1.33x faster with four warps; at 256
+    // fcc(111) replicas (1.7 per SM) two warps gain 3 % and four lose 18 %.
+    // REGC_WARPS_PER_WALKER overrides the choice.
     int W = 1;
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
             const long long n_rep = (long long)grid->L * grid->M;
-            if (n_rep <= 2LL * sms) W = 4;
-            else if (n_rep <= 4LL * sms) W = 2;
+            if (4 * n_rep <= 5LL * sms) W = 4;
+            else if (n_rep <= 2LL * sms) W = 2;
         }
     }
     if (const char* env = getenv("REGC_WARPS_PER_WALKER")) {
