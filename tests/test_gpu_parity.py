@@ -163,6 +163,31 @@ def test_production_kernel_matches_traced_kernel():
     assert np.array_equal(a.histograms()["hNE"], b.histograms()["hNE"])
 
 
+@pytest.mark.parametrize("warps", [2, 4])
+def test_speculative_walkers_make_the_sequential_chain(warps, monkeypatch):
+    """Two and four warps per walker (moves evaluated speculatively, committed
+    in order) end in the state of one warp per walker, bit for bit, on the
+    fcc(111) slab with 256 replicas (the launch shape is picked at handle
+    creation; REGC_WARPS_PER_WALKER forces it)."""
+    p = W.fcc111_paper_scale(L=8)
+    rng = np.random.default_rng(2)
+    pos, n = W.lattice_walkers(p, rng.integers(0, p.nmax // 2 + 1, p.S), seed=2)
+    monkeypatch.setenv("REGC_WARPS_PER_WALKER", "1")
+    one = Regc(p)
+    monkeypatch.setenv("REGC_WARPS_PER_WALKER", str(warps))
+    spec = Regc(p)
+    assert one.warps_per_walker() == 1 and spec.warps_per_walker() == warps
+    for g in (one, spec):
+        g.set_walkers(pos, n)
+        for _ in range(3):
+            g.sweep(10)
+            g.exchange()
+    for x, y in zip(one.get_walkers(), spec.get_walkers()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(one.histograms()["hNE"], spec.histograms()["hNE"])
+    assert spec.check_energy() == 0.0
+
+
 def test_full_size_fcc111_1024_replicas():
     """The 1024-replica Nmax-512 workload in the benchmark's launch
     configuration: ten traced sweeps of every walker from the benchmark's
