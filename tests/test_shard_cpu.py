@@ -1,5 +1,5 @@
 """The exchange protocol of a grid split over processes (paper_1908_11118_gb300
-/shard.py) on two CPU ranks (gloo), with the FP64 oracle as each rank's
+/shard.py) on two and three CPU ranks (gloo), with the FP64 oracle as each rank's
 engine: every rank sweeps only its own walkers, all-gathers (N, E) before each
 exchange attempt (Sec. II.A.2, Eq. Pacc) and runs the same exchange.  The run
 must be the single-process run walker for walker: the owned walkers'
@@ -79,12 +79,12 @@ def _worker(rank, world, port, out, planted):
     dist.destroy_process_group()
 
 
-def _run_two_ranks(planted):
+def _run_ranks(planted, world=2):
     port = _free_port()
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
-    mp.spawn(_worker, args=(2, port, out, planted), nprocs=2, join=True)
-    return [out[0], out[1]]
+    mp.spawn(_worker, args=(world, port, out, planted), nprocs=world, join=True)
+    return [out[r] for r in range(world)]
 
 
 def _single_run():
@@ -96,10 +96,11 @@ def _single_run():
     return o
 
 
-def test_two_rank_grid_is_the_single_process_run():
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_grid_is_the_single_process_run(world):
     ref = _single_run()
-    ranks = _run_two_ranks(planted=False)
-    assert [r["range"] for r in ranks] == [(0, 8), (8, 16)]
+    ranks = _run_ranks(planted=False, world=world)
+    assert [r["range"] for r in ranks] == ([(0, 8), (8, 16)] if world == 2 else [(0, 5), (5, 10), (10, 16)])
     for r in ranks:
         b, e = r["range"]
         assert np.array_equal(r["sow"], ref.state_of_walker)
@@ -117,7 +118,7 @@ def test_two_rank_grid_is_the_single_process_run():
 
 def test_exchange_on_stale_energies_is_caught():
     ref = _single_run()
-    ranks = _run_two_ranks(planted=True)
+    ranks = _run_ranks(planted=True)
     assert any(not np.array_equal(r["sow"], ref.state_of_walker) for r in ranks)
 
 
