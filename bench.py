@@ -394,7 +394,7 @@ def cluster_production_arm(torch, stream, sweeps, rows_target, train_steps, equi
     g.set_mode(True)
     g.run(equil, exchange_every=SWEEPS_PER_STEP)
     bt = Batch([g], sweeps_per_step=SWEEPS_PER_STEP, stream=stream)
-    bt.autotune(1)
+    bt.autotune(3)   # each shape timed three times, the fastest kept
     plan = bt.plan()
     g.set_state_windows(1024, 0.25, None)
     g.reset_histograms()
@@ -469,7 +469,7 @@ def batched_uneven_arm(torch, steps, seed=0):
     bt = Batch(hs, sweeps_per_step=SWEEPS_PER_STEP, stream=stream)
     plan_default = bt.plan()
     t0 = time.perf_counter()
-    bt.autotune(1)
+    bt.autotune(3)   # each shape timed three times, the fastest kept
     t_tune = time.perf_counter() - t0
     bt.run(3)                                   # warm-up (captures the graph)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
